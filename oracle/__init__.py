@@ -1,0 +1,278 @@
+"""FP64 CPU oracle for the NDGI decode and fit (test infrastructure).
+
+Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never calls it, and it shares no code with that path: the
+arithmetic lives in ``ndgi_oracle.c`` (plain C, FP64), this module only
+marshals numpy arrays into it.
+
+Reduced-precision parity is measured against the *stored* parameters: for an
+FP16 or BF16 decode the MLP weights and biases are rounded to that format
+(round to nearest even) and then evaluated exactly in FP64 here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ndgi_oracle.c")
+_LIB = os.path.join(_HERE, "libndgi_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force=False):
+    """Compile the oracle with gcc (no fast-math, no FP contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Model(C.Structure):
+    _fields_ = [("lm_w", C.c_int32), ("lm_h", C.c_int32), ("feat_w", C.c_int32), ("feat_h", C.c_int32),
+                ("cs", C.c_int32), ("bc4", C.c_void_p), ("t_count", C.c_int32), ("ct", C.c_int32),
+                ("temporal", C.c_void_p), ("hidden", C.c_int32),
+                ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+
+
+class _PageReq(C.Structure):
+    _fields_ = [("model", C.c_int32), ("x0", C.c_int32), ("y0", C.c_int32), ("w", C.c_int32),
+                ("h", C.c_int32), ("t", C.c_float), ("dst_x", C.c_int32), ("dst_y", C.c_int32)]
+
+
+class _FitParams(C.Structure):
+    _fields_ = [("lm_w", C.c_int32), ("lm_h", C.c_int32), ("feat_w", C.c_int32), ("feat_h", C.c_int32),
+                ("cs", C.c_int32), ("t_count", C.c_int32), ("ct", C.c_int32), ("hidden", C.c_int32),
+                ("ea", C.c_void_p), ("eb", C.c_void_p), ("w", C.c_void_p), ("temporal", C.c_void_p),
+                ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+
+
+class _FitGrads(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("ea", "eb", "w", "temporal", "w1", "b1", "w2", "b2", "w3", "b3")]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            vp, i32, i64, f32, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double
+            L.om_bc4_p35.argtypes = [vp, C.c_int]
+            L.om_bc4_p35.restype = C.c_int
+            L.om_p35_value.argtypes = [C.c_int]
+            L.om_p35_value.restype = f32
+            L.om_features.argtypes = [vp, f64, f64, f64, vp, vp]
+            L.om_features_batch.argtypes = [vp, vp, i64, vp, vp, C.c_int]
+            L.om_mlp_batch.argtypes = [vp, vp, i64, vp]
+            L.om_decode_points.argtypes = [vp, vp, i64, vp, C.c_int]
+            L.om_decode_pages.argtypes = [vp, i32, vp, i32, vp, i64, i64, C.c_int]
+            L.om_q255.argtypes = [f32]
+            L.om_q7.argtypes = [f32]
+            L.om_bc_pack.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+            L.om_fit_forward.argtypes = [vp, vp, i64, C.c_int, vp, vp]
+            L.om_fit_loss.argtypes = [vp, vp, i64]
+            L.om_fit_loss.restype = f64
+            L.om_fit_backward.argtypes = [vp, vp, vp, i64, C.c_int, vp]
+            L.om_fit_backward.restype = f64
+            L.om_adam.argtypes = [vp, vp, vp, vp, i64, i32, f64, f64, f64, f64, i32]
+            L.om_fit_draw.argtypes = [C.c_uint64, i64, i64, i64, i32, i32, i32, vp]
+            L.om_max_hidden.restype = C.c_int
+            L.om_splitmix64_next.argtypes = [C.c_uint64]
+            L.om_splitmix64_next.restype = C.c_uint64
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# --------------------------------------------------------------------------
+# Stored-parameter rounding (what a reduced-precision decode actually holds)
+# --------------------------------------------------------------------------
+
+def round_bf16(x):
+    """Round float32 values to bfloat16 (nearest, ties to even), returned as float32."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    b = x.view(np.uint32).astype(np.uint64)
+    rounded = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    nan = np.isnan(x)
+    out = rounded.astype(np.uint32).view(np.float32).copy()
+    out[nan] = np.nan
+    return out
+
+
+def stored_weights(m, precision):
+    """MLP weights/biases as the decode of `precision` stores them, in FP64."""
+    keys = ("w1", "b1", "w2", "b2", "w3", "b3")
+    if precision == "fp32":
+        return {k: np.asarray(m[k], np.float32).astype(np.float64) for k in keys}
+    if precision == "fp16":
+        return {k: np.asarray(m[k], np.float32).astype(np.float16).astype(np.float64) for k in keys}
+    if precision == "bf16":
+        return {k: round_bf16(m[k]).astype(np.float64) for k in keys}
+    raise ValueError(precision)
+
+
+class Model:
+    """A decodable model (dict from synth.model) held in oracle form."""
+
+    def __init__(self, m, precision="fp32"):
+        self.src = m
+        self.cs, self.ct, self.hidden = int(m["cs"]), int(m["ct"]), int(m["hidden"])
+        assert self.hidden <= lib().om_max_hidden()
+        self.bc4 = _c(m["bc4"], np.uint8)
+        self.temporal = _c(np.asarray(m["temporal"]).astype(np.float64), np.float64)
+        w = stored_weights(m, precision)
+        self.w = {k: _c(v, np.float64) for k, v in w.items()}
+        self.s = _Model(int(m["lm_w"]), int(m["lm_h"]), int(m["feat_w"]), int(m["feat_h"]), self.cs,
+                        _ptr(self.bc4), int(m["t_count"]), self.ct, _ptr(self.temporal), self.hidden,
+                        _ptr(self.w["w1"]), _ptr(self.w["b1"]), _ptr(self.w["w2"]), _ptr(self.w["b2"]),
+                        _ptr(self.w["w3"]), _ptr(self.w["b3"]), int(m.get("address_mode", 0)))
+
+
+def _model(m, precision="fp32"):
+    return m if isinstance(m, Model) else Model(m, precision)
+
+
+def nthreads_default():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def bc4_p35(block, p):
+    """Palette numerator (value * 8925) of texel p of one 8-byte BC4 block."""
+    b = _c(np.frombuffer(bytes(block), dtype=np.uint8), np.uint8)
+    return int(lib().om_bc4_p35(_ptr(b), int(p)))
+
+
+def p35_value(p35):
+    return float(lib().om_p35_value(int(p35)))
+
+
+def features(m, uvt, nthreads=None):
+    """x = [v_s, v_t] [n][cs+ct] and tap numerators [n][4][cs]."""
+    M = _model(m)
+    q = _c(uvt, np.float32).reshape(-1, 3)
+    n = q.shape[0]
+    x = np.zeros((n, M.cs + M.ct), np.float64)
+    p = np.zeros((n, 4, M.cs), np.int32)
+    lib().om_features_batch(C.byref(M.s), _ptr(q), n, _ptr(x), _ptr(p), nthreads or nthreads_default())
+    return x, p
+
+
+def mlp(m, x, precision="fp32"):
+    M = _model(m, precision)
+    x = _c(x, np.float64)
+    y = np.zeros((x.shape[0], 3), np.float64)
+    lib().om_mlp_batch(C.byref(M.s), _ptr(x), x.shape[0], _ptr(y))
+    return y
+
+
+def decode_points(m, uvt, precision="fp32", nthreads=None):
+    """FP64 RGB [n][3] of the decode at each (u, v, t)."""
+    M = _model(m, precision)
+    q = _c(uvt, np.float32).reshape(-1, 3)
+    y = np.zeros((q.shape[0], 3), np.float64)
+    lib().om_decode_points(C.byref(M.s), _ptr(q), q.shape[0], _ptr(y), nthreads or nthreads_default())
+    return y
+
+
+def decode_pages(models, reqs, phys_w, phys_h, precision="fp32", nthreads=None, fill=np.nan):
+    """FP64 RGBA physical texture [phys_h][phys_w][4]; untouched texels = fill."""
+    Ms = [_model(m, precision) for m in models]
+    arr = (_Model * len(Ms))(*[M.s for M in Ms])
+    r = np.ascontiguousarray(reqs)
+    out = np.full((phys_h, phys_w, 4), fill, np.float64)
+    lib().om_decode_pages(arr, len(Ms), r.ctypes.data_as(C.c_void_p), len(r), _ptr(out), phys_w, phys_h,
+                          nthreads or nthreads_default())
+    return out
+
+
+def q255(e):
+    return int(lib().om_q255(float(np.float32(e))))
+
+
+def q7(w):
+    return int(lib().om_q7(float(np.float32(w))))
+
+
+def bc_pack(ea, eb, w):
+    """BC4 blocks [bh][bw][cs][8] from endpoints [bh][bw][cs] and weights [bh][bw][cs][16]."""
+    ea, eb, w = _c(ea, np.float32), _c(eb, np.float32), _c(w, np.float32)
+    bh, bw, cs = ea.shape
+    out = np.zeros((bh, bw, cs, 8), np.uint8)
+    lib().om_bc_pack(_ptr(ea), _ptr(eb), _ptr(w), cs, bw * 4, bh * 4, _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Fit
+# --------------------------------------------------------------------------
+
+FIT_KEYS = ("ea", "eb", "w", "temporal", "w1", "b1", "w2", "b2", "w3", "b3")
+
+
+class FitParams:
+    def __init__(self, p, lm_w, lm_h):
+        self.a = {k: _c(p[k], np.float32) for k in FIT_KEYS}
+        bh, bw, cs = self.a["ea"].shape
+        T, ct = self.a["temporal"].shape
+        H = self.a["w2"].shape[0]
+        self.dims = dict(lm_w=lm_w, lm_h=lm_h, feat_w=bw * 4, feat_h=bh * 4, cs=cs, t_count=T, ct=ct, hidden=H)
+        self.s = _FitParams(lm_w, lm_h, bw * 4, bh * 4, cs, T, ct, H,
+                            *[_ptr(self.a[k]) for k in FIT_KEYS], int(p.get("address_mode", 0)))
+
+
+def fit_forward(params, samples, lm_w, lm_h, relaxed=False, want_signs=False):
+    P = params if isinstance(params, FitParams) else FitParams(params, lm_w, lm_h)
+    s = _c(samples, np.int32).reshape(-1, 3)
+    y = np.zeros((s.shape[0], 3), np.float64)
+    signs = np.zeros((s.shape[0], 2 * P.dims["hidden"]), np.uint8) if want_signs else None
+    lib().om_fit_forward(C.byref(P.s), _ptr(s), s.shape[0], int(relaxed), _ptr(y), _ptr(signs))
+    return (y, signs) if want_signs else y
+
+
+def fit_loss(rgb, target):
+    rgb, target = _c(rgb, np.float64), _c(target, np.float64)
+    return float(lib().om_fit_loss(_ptr(rgb), _ptr(target), rgb.shape[0]))
+
+
+def fit_backward(params, samples, target, lm_w, lm_h, relaxed=False):
+    """(loss, grads) with grads a dict of FP64 arrays shaped like the params."""
+    P = params if isinstance(params, FitParams) else FitParams(params, lm_w, lm_h)
+    s = _c(samples, np.int32).reshape(-1, 3)
+    t = _c(target, np.float64).reshape(-1, 3)
+    g = {k: np.zeros(P.a[k].shape, np.float64) for k in FIT_KEYS}
+    G = _FitGrads(*[_ptr(g[k]) for k in FIT_KEYS])
+    loss = lib().om_fit_backward(C.byref(P.s), _ptr(s), _ptr(t), s.shape[0], int(relaxed), C.byref(G))
+    return float(loss), g
+
+
+def adam(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, project=False):
+    """In-place Adam on float32 p with float64 moments m, v."""
+    assert p.dtype == np.float32 and p.flags.c_contiguous
+    g = _c(g, np.float64)
+    lib().om_adam(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.size, int(step), lr, beta1, beta2, eps, int(project))
+
+
+def fit_draw(seed, step, n, lm_w, lm_h, t_count, first=0):
+    out = np.zeros((n, 3), np.int32)
+    lib().om_fit_draw(C.c_uint64(seed), step, first, n, lm_w, lm_h, t_count, _ptr(out))
+    return out

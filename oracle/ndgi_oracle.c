@@ -1,0 +1,535 @@
+/*
+ * ndgi_oracle.c -- plain, slow, FP64 CPU oracle for the NDGI decode and fit.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA path under paper_2604_12625_gb300/;
+ * both sides only read the same seeded input arrays.
+ *
+ * What it computes (paper: "Neural Dynamic GI", arXiv 2604.12625):
+ *   I(u,v,t) = H_Theta(u,v,t)                                  (Sec. 3.1, Eq. 3)
+ * for the simplified decoder used here: one spatial feature map of `cs`
+ * single-channel BC4 planes sampled bilinearly at (u,v), one temporal feature
+ * line of T samples linearly interpolated at t (the linear operator of
+ * Eq. 2 applied to features), their concatenation fed to an MLP with two
+ * hidden ReLU layers and a linear RGB output (Sec. 4).  BC blocks follow the
+ * endpoint/weight form of Eq. 6-7 and supplement S2: f_p = (1-w_p) e1 + w_p e2.
+ *
+ * Readings of the paper used below (the paper gives no BC4 palette, texel
+ * convention or keyframe placement):
+ *   - BC4 palette, full UNORM semantics, kept as the exact integer numerator
+ *     P35 over 8925 = 35*255; feature value = fl32(P35) * fl32(1/8925).
+ *   - Block bytes: byte0 = r0, byte1 = r1, then 48 index bits little-endian,
+ *     texel p = 4*row + col at bit 16 + 3p.  Device layout [by][bx][c][8].
+ *   - Texel-centre sampling x = u*W - 0.5, taps floor(x), floor(x)+1, clamp to
+ *     edge (address mode 0) or mirrored repeat (mode 1).
+ *   - Keyframes at t_j = j/T, periodic: j1 = (j+1) mod T.
+ *   - Straight-through BC simulation for the fit: A = q255(e1), B = q255(e2),
+ *     k = q7(w) decided in FP32 as floor(min(max(s*x + 0.5, 0), s)); the
+ *     backward treats the quantisers as identity and uses quantised factors.
+ *
+ * All interpolation and MLP arithmetic is FP64.  Build with
+ * -ffp-contract=off so the FP32 quantiser decisions are single roundings.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+  int32_t lm_w, lm_h;            /* lightmap size: texel -> (u,v)         */
+  int32_t feat_w, feat_h, cs;    /* BC4 feature planes                     */
+  const uint8_t *bc4;            /* [feat_h/4][feat_w/4][cs][8]            */
+  int32_t t_count, ct;           /* temporal line                          */
+  const double *temporal;        /* [t_count][ct]                          */
+  int32_t hidden;                /* MLP: (cs+ct) -> hidden -> hidden -> 3  */
+  const double *w1, *b1, *w2, *b2, *w3, *b3; /* [in][out] row-major       */
+  int32_t address_mode;          /* 0 clamp, 1 mirrored repeat             */
+} om_model;
+
+typedef struct {
+  int32_t model, x0, y0, w, h;
+  float t;
+  int32_t dst_x, dst_y;
+} om_page_req;
+
+/* ---------------------------------------------------------------------- */
+/* BC4 block decode (Eq. 7 / S2 with the BC4 palette)                       */
+/* ---------------------------------------------------------------------- */
+
+/* 3-bit index of texel p (0..15) of one 8-byte block. */
+static int om_bc4_index(const uint8_t *blk, int p) {
+  uint64_t bits = 0;
+  for (int i = 0; i < 6; ++i) bits |= (uint64_t)blk[2 + i] << (8 * i);
+  return (int)((bits >> (3 * p)) & 7u);
+}
+
+/* Palette numerator over 8925 for texel p: the value is P35 / 8925. */
+int om_bc4_p35(const uint8_t *blk, int p) {
+  int r0 = blk[0], r1 = blk[1];
+  int k = om_bc4_index(blk, p);
+  if (k == 0) return 35 * r0;
+  if (k == 1) return 35 * r1;
+  if (r0 > r1) {
+    /* eight-value mode: ((8-k) r0 + (k-1) r1) / 7 */
+    return 5 * ((8 - k) * r0 + (k - 1) * r1);
+  }
+  /* six-value mode: ((6-k) r0 + (k-1) r1) / 5, then the literals 0 and 255 */
+  if (k <= 5) return 7 * ((6 - k) * r0 + (k - 1) * r1);
+  return k == 6 ? 0 : 35 * 255;
+}
+
+/* Feature value of a palette numerator: one FP32 round-to-nearest multiply. */
+float om_p35_value(int p35) {
+  const float inv = 1.0f / 8925.0f;
+  float f = (float)p35;
+  return f * inv;
+}
+
+/* Map a possibly out-of-range texel index into [0, n). */
+static int om_address(int i, int n, int mode) {
+  if (mode == 1) {
+    int period = 2 * n;
+    int m = i % period;
+    if (m < 0) m += period;
+    return m < n ? m : period - 1 - m;
+  }
+  if (i < 0) return 0;
+  if (i >= n) return n - 1;
+  return i;
+}
+
+/* P35 of feature texel (tx, ty), channel c (indices already in range). */
+static int om_texel_p35(const om_model *m, int tx, int ty, int c) {
+  int bw = m->feat_w / 4;
+  const uint8_t *blk = m->bc4 + ((size_t)((ty >> 2) * bw + (tx >> 2)) * m->cs + c) * 8;
+  return om_bc4_p35(blk, (ty & 3) * 4 + (tx & 3));
+}
+
+/* Bilinear sample setup at texel-centre convention: taps and fractions. */
+static void om_bilinear_setup(double coord, int size, int mode, int *t0, int *t1, double *frac) {
+  double x = coord * (double)size - 0.5;
+  double fl = floor(x);
+  *frac = x - fl;
+  *t0 = om_address((int)fl, size, mode);
+  *t1 = om_address((int)fl + 1, size, mode);
+}
+
+/* Temporal interpolation setup: keyframes at j/T, periodic in t. */
+static void om_temporal_setup(double t, int T, int *j0, int *j1, double *alpha) {
+  double s = t * (double)T;
+  double fl = floor(s);
+  *alpha = s - fl;
+  long j = (long)fl % T;
+  if (j < 0) j += T;
+  *j0 = (int)j;
+  *j1 = (int)((j + 1) % T);
+}
+
+/*
+ * Input feature vector x = [v_s (cs), v_t (ct)] at (u, v, t).
+ * Optionally returns the P35 numerators of the four taps, [4][cs], taps in
+ * the order (x0,y0), (x1,y0), (x0,y1), (x1,y1).
+ */
+void om_features(const om_model *m, double u, double v, double t, double *x, int32_t *p35) {
+  int x0, x1, y0, y1;
+  double fx, fy;
+  om_bilinear_setup(u, m->feat_w, m->address_mode, &x0, &x1, &fx);
+  om_bilinear_setup(v, m->feat_h, m->address_mode, &y0, &y1, &fy);
+  for (int c = 0; c < m->cs; ++c) {
+    int q00 = om_texel_p35(m, x0, y0, c);
+    int q10 = om_texel_p35(m, x1, y0, c);
+    int q01 = om_texel_p35(m, x0, y1, c);
+    int q11 = om_texel_p35(m, x1, y1, c);
+    if (p35) {
+      p35[0 * m->cs + c] = q00;
+      p35[1 * m->cs + c] = q10;
+      p35[2 * m->cs + c] = q01;
+      p35[3 * m->cs + c] = q11;
+    }
+    double f00 = om_p35_value(q00), f10 = om_p35_value(q10);
+    double f01 = om_p35_value(q01), f11 = om_p35_value(q11);
+    x[c] = (1.0 - fy) * ((1.0 - fx) * f00 + fx * f10) + fy * ((1.0 - fx) * f01 + fx * f11);
+  }
+  int j0, j1;
+  double a;
+  om_temporal_setup(t, m->t_count, &j0, &j1, &a);
+  for (int c = 0; c < m->ct; ++c) {
+    double k0 = m->temporal[(size_t)j0 * m->ct + c];
+    double k1 = m->temporal[(size_t)j1 * m->ct + c];
+    x[m->cs + c] = (1.0 - a) * k0 + a * k1;
+  }
+}
+
+/* Dense layer y = act(x W + b), W stored [in][out]. */
+static void om_dense(const double *x, int in, const double *W, const double *b, int out, int relu, double *y) {
+  for (int o = 0; o < out; ++o) {
+    double z = b[o];
+    for (int i = 0; i < in; ++i) z += x[i] * W[(size_t)i * out + o];
+    y[o] = (relu && !(z > 0.0)) ? 0.0 : z;
+  }
+}
+
+/* MLP G: two hidden ReLU layers, linear RGB output (Sec. 4). */
+void om_mlp(const om_model *m, const double *x, double *rgb) {
+  double h1[256], h2[256];
+  int cin = m->cs + m->ct, H = m->hidden;
+  om_dense(x, cin, m->w1, m->b1, H, 1, h1);
+  om_dense(h1, H, m->w2, m->b2, H, 1, h2);
+  om_dense(h2, H, m->w3, m->b3, 3, 0, rgb);
+}
+
+int om_max_hidden(void) { return 256; }
+
+/* Batched feature gather: x [n][cs+ct], p35 [n][4][cs] (may be NULL). */
+void om_features_batch(const om_model *m, const float *uvt, int64_t n, double *x, int32_t *p35, int nthreads) {
+  int cin = m->cs + m->ct;
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+  for (int64_t i = 0; i < n; ++i) {
+    om_features(m, (double)uvt[3 * i], (double)uvt[3 * i + 1], (double)uvt[3 * i + 2], x + i * cin,
+                p35 ? p35 + i * 4 * m->cs : NULL);
+  }
+}
+
+/* Batched MLP on given inputs: x [n][cs+ct] -> rgb [n][3]. */
+void om_mlp_batch(const om_model *m, const double *x, int64_t n, double *rgb) {
+  int cin = m->cs + m->ct;
+  for (int64_t i = 0; i < n; ++i) om_mlp(m, x + i * cin, rgb + 3 * i);
+}
+
+/* Random-access point decode: rgb[i] = H(u_i, v_i, t_i). */
+void om_decode_points(const om_model *m, const float *uvt, int64_t n, double *rgb, int nthreads) {
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+  for (int64_t i = 0; i < n; ++i) {
+    double x[512];
+    om_features(m, (double)uvt[3 * i], (double)uvt[3 * i + 1], (double)uvt[3 * i + 2], x, NULL);
+    om_mlp(m, x, rgb + 3 * i);
+  }
+}
+
+/*
+ * Page decode (Sec. 3.5, supplement S3): every texel (x0+i, y0+j) of each
+ * request is decoded at uv = ((x0+i+0.5)/lm_w, (y0+j+0.5)/lm_h) with the
+ * request's own t and model, and written as RGBA (A = 1) to the physical
+ * texture phys[phys_h][phys_w][4] at (dst_x+i, dst_y+j).  Requests whose
+ * destination overlaps another request's are not supported.
+ */
+void om_decode_pages(const om_model *models, int32_t n_models, const om_page_req *reqs, int32_t n,
+                     double *phys, int64_t phys_w, int64_t phys_h, int nthreads) {
+  (void)n_models;
+  (void)phys_h;
+  for (int32_t r = 0; r < n; ++r) {
+    const om_page_req *q = &reqs[r];
+    const om_model *m = &models[q->model];
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int32_t jj = 0; jj < q->h; ++jj) {
+      double x[512], rgb[3];
+      for (int32_t ii = 0; ii < q->w; ++ii) {
+        double u = ((double)(q->x0 + ii) + 0.5) / (double)m->lm_w;
+        double v = ((double)(q->y0 + jj) + 0.5) / (double)m->lm_h;
+        om_features(m, u, v, (double)q->t, x, NULL);
+        om_mlp(m, x, rgb);
+        double *o = phys + ((int64_t)(q->dst_y + jj) * phys_w + (q->dst_x + ii)) * 4;
+        o[0] = rgb[0];
+        o[1] = rgb[1];
+        o[2] = rgb[2];
+        o[3] = 1.0;
+      }
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+/* BC simulation quantisers and block packing (Eq. 6-7, end of Sec. 3.4)   */
+/* ---------------------------------------------------------------------- */
+
+/* floor(min(max(s*x + 0.5, 0), s)) with each FP32 operation rounded once. */
+static int om_quant(float x, float s) {
+  float y = s * x;
+  y = y + 0.5f;
+  y = fmaxf(y, 0.0f);
+  y = fminf(y, s);
+  return (int)floorf(y);
+}
+int om_q255(float e) { return om_quant(e, 255.0f); }
+int om_q7(float w) { return om_quant(w, 7.0f); }
+
+/*
+ * Pack the straight-through quantised endpoints and weights into BC4 blocks
+ * whose decode reproduces the simulated values exactly:
+ *   A > B : r0 = A, r1 = B, index = k==0 ? 0 : k==7 ? 1 : k+1
+ *   A < B : r0 = B, r1 = A, same map applied to k' = 7 - k
+ *   A == B: r0 = r1 = A, every index 0.
+ * ea, eb: [bh][bw][cs]; w: [bh][bw][cs][16]; out: [bh][bw][cs][8].
+ */
+void om_bc_pack(const float *ea, const float *eb, const float *w, int32_t cs, int32_t feat_w, int32_t feat_h,
+                uint8_t *out) {
+  int64_t nb = (int64_t)(feat_w / 4) * (feat_h / 4) * cs;
+  for (int64_t b = 0; b < nb; ++b) {
+    int A = om_q255(ea[b]), B = om_q255(eb[b]);
+    uint8_t *o = out + b * 8;
+    uint64_t bits = 0;
+    if (A == B) {
+      o[0] = (uint8_t)A;
+      o[1] = (uint8_t)A;
+    } else {
+      int swap = A < B;
+      o[0] = (uint8_t)(swap ? B : A);
+      o[1] = (uint8_t)(swap ? A : B);
+      for (int p = 0; p < 16; ++p) {
+        int k = om_q7(w[b * 16 + p]);
+        if (swap) k = 7 - k;
+        int idx = k == 0 ? 0 : (k == 7 ? 1 : k + 1);
+        bits |= (uint64_t)idx << (3 * p);
+      }
+    }
+    for (int i = 0; i < 6; ++i) o[2 + i] = (uint8_t)(bits >> (8 * i));
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Fit: forward, loss and analytic backward (Sec. 3.4 and Sec. 4)          */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+  int32_t lm_w, lm_h, feat_w, feat_h, cs, t_count, ct, hidden;
+  const float *ea, *eb;          /* [bh][bw][cs]      endpoints in [0,1]   */
+  const float *w;                /* [bh][bw][cs][16]  weights in [0,1]     */
+  const float *temporal;         /* [t_count][ct]                           */
+  const float *w1, *b1, *w2, *b2, *w3, *b3;
+  int32_t address_mode;
+} om_fit_params;
+
+typedef struct {
+  double *ea, *eb, *w, *temporal, *w1, *b1, *w2, *b2, *w3, *b3;
+} om_fit_grads;
+
+/* Simulated feature value of texel p of block b, channel plane c. */
+static double om_sim_value(const om_fit_params *P, int64_t bc, int p, int relaxed,
+                           double *dea, double *deb, double *dw) {
+  float ea = P->ea[bc], eb = P->eb[bc], w = P->w[bc * 16 + p];
+  if (relaxed) {
+    *dea = 1.0 - (double)w;
+    *deb = (double)w;
+    *dw = (double)eb - (double)ea;
+    return (1.0 - (double)w) * ea + (double)w * eb;
+  }
+  int A = om_q255(ea), B = om_q255(eb), k = om_q7(w);
+  *dea = 1.0 - k / 7.0;
+  *deb = k / 7.0;
+  *dw = B / 255.0 - A / 255.0;
+  return (double)om_p35_value(5 * ((7 - k) * A + k * B));
+}
+
+/* Taps and fractions of the fit sample at texel (ix, iy): texel centre uv. */
+static void om_fit_taps(const om_fit_params *P, int ix, int iy, int tx[4], int ty[4], double *fx, double *fy) {
+  int x0, x1, y0, y1;
+  double u = ((double)ix + 0.5) / (double)P->lm_w;
+  double v = ((double)iy + 0.5) / (double)P->lm_h;
+  om_bilinear_setup(u, P->feat_w, P->address_mode, &x0, &x1, fx);
+  om_bilinear_setup(v, P->feat_h, P->address_mode, &y0, &y1, fy);
+  tx[0] = x0; ty[0] = y0;
+  tx[1] = x1; ty[1] = y0;
+  tx[2] = x0; ty[2] = y1;
+  tx[3] = x1; ty[3] = y1;
+}
+
+/*
+ * One sample: texel (ix, iy) of keyframe j (t = j/T, so the temporal feature
+ * is row j).  Returns y [3]; optionally the pre-activations z1, z2 [hidden]
+ * and the input x [cs+ct].
+ */
+static void om_fit_sample_forward(const om_fit_params *P, int ix, int iy, int j, int relaxed,
+                                  double *x, double *z1, double *h1, double *z2, double *h2, double *y) {
+  int tx[4], ty[4];
+  double fx, fy;
+  om_fit_taps(P, ix, iy, tx, ty, &fx, &fy);
+  int bw = P->feat_w / 4, cs = P->cs, ct = P->ct, H = P->hidden, cin = cs + ct;
+  for (int c = 0; c < cs; ++c) {
+    double f[4];
+    for (int q = 0; q < 4; ++q) {
+      int64_t bc = ((int64_t)(ty[q] >> 2) * bw + (tx[q] >> 2)) * cs + c;
+      double d0, d1, d2;
+      f[q] = om_sim_value(P, bc, (ty[q] & 3) * 4 + (tx[q] & 3), relaxed, &d0, &d1, &d2);
+    }
+    x[c] = (1.0 - fy) * ((1.0 - fx) * f[0] + fx * f[1]) + fy * ((1.0 - fx) * f[2] + fx * f[3]);
+  }
+  for (int c = 0; c < ct; ++c) x[cs + c] = (double)P->temporal[(size_t)j * ct + c];
+  for (int o = 0; o < H; ++o) {
+    double z = P->b1[o];
+    for (int i = 0; i < cin; ++i) z += x[i] * (double)P->w1[(size_t)i * H + o];
+    z1[o] = z;
+    h1[o] = z > 0.0 ? z : 0.0;
+  }
+  for (int o = 0; o < H; ++o) {
+    double z = P->b2[o];
+    for (int i = 0; i < H; ++i) z += h1[i] * (double)P->w2[(size_t)i * H + o];
+    z2[o] = z;
+    h2[o] = z > 0.0 ? z : 0.0;
+  }
+  for (int o = 0; o < 3; ++o) {
+    double z = P->b3[o];
+    for (int i = 0; i < H; ++i) z += h2[i] * (double)P->w3[(size_t)i * 3 + o];
+    y[o] = z;
+  }
+}
+
+/*
+ * Fit forward over n samples [n][3] = (ix, iy, j): rgb [n][3].  If `signs`
+ * is non-NULL it receives the ReLU pattern (z > 0) of both hidden layers,
+ * [n][2*hidden] bytes, so finite differences can drop kink crossings.
+ * relaxed = 1 makes every quantiser the identity (continuous relaxation).
+ */
+void om_fit_forward(const om_fit_params *P, const int32_t *samples, int64_t n, int relaxed, double *rgb,
+                    uint8_t *signs) {
+  int H = P->hidden;
+  for (int64_t s = 0; s < n; ++s) {
+    double x[512], z1[256], h1[256], z2[256], h2[256];
+    om_fit_sample_forward(P, samples[3 * s], samples[3 * s + 1], samples[3 * s + 2], relaxed, x, z1, h1, z2, h2,
+                          rgb + 3 * s);
+    if (signs) {
+      for (int o = 0; o < H; ++o) {
+        signs[s * 2 * H + o] = z1[o] > 0.0;
+        signs[s * 2 * H + H + o] = z2[o] > 0.0;
+      }
+    }
+  }
+}
+
+/* Mean squared error over n samples and 3 channels (L2 loss, Sec. 4). */
+double om_fit_loss(const double *rgb, const double *target, int64_t n) {
+  double acc = 0.0;
+  for (int64_t i = 0; i < 3 * n; ++i) {
+    double d = rgb[i] - target[i];
+    acc += d * d;
+  }
+  return acc / (3.0 * (double)n);
+}
+
+/*
+ * Analytic FP64 gradient of the MSE loss with respect to every parameter.
+ * Gradients are accumulated (callers zero them).  Returns the loss.
+ */
+double om_fit_backward(const om_fit_params *P, const int32_t *samples, const double *target, int64_t n,
+                       int relaxed, om_fit_grads *G) {
+  int bw = P->feat_w / 4, cs = P->cs, ct = P->ct, H = P->hidden, cin = cs + ct;
+  double loss = 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    int ix = samples[3 * s], iy = samples[3 * s + 1], j = samples[3 * s + 2];
+    double x[512], z1[256], h1[256], z2[256], h2[256], y[3];
+    om_fit_sample_forward(P, ix, iy, j, relaxed, x, z1, h1, z2, h2, y);
+    double dy[3];
+    for (int o = 0; o < 3; ++o) {
+      double d = y[o] - target[3 * s + o];
+      loss += d * d;
+      dy[o] = 2.0 * d / (3.0 * (double)n);
+    }
+    double gh2[256], gz2[256], gh1[256], gz1[256], gx[512];
+    for (int o = 0; o < 3; ++o) G->b3[o] += dy[o];
+    for (int i = 0; i < H; ++i) {
+      double acc = 0.0;
+      for (int o = 0; o < 3; ++o) {
+        G->w3[(size_t)i * 3 + o] += h2[i] * dy[o];
+        acc += (double)P->w3[(size_t)i * 3 + o] * dy[o];
+      }
+      gh2[i] = acc;
+      gz2[i] = z2[i] > 0.0 ? acc : 0.0;
+    }
+    for (int o = 0; o < H; ++o) G->b2[o] += gz2[o];
+    for (int i = 0; i < H; ++i) {
+      double acc = 0.0;
+      for (int o = 0; o < H; ++o) {
+        G->w2[(size_t)i * H + o] += h1[i] * gz2[o];
+        acc += (double)P->w2[(size_t)i * H + o] * gz2[o];
+      }
+      gh1[i] = acc;
+      gz1[i] = z1[i] > 0.0 ? acc : 0.0;
+    }
+    for (int o = 0; o < H; ++o) G->b1[o] += gz1[o];
+    for (int i = 0; i < cin; ++i) {
+      double acc = 0.0;
+      for (int o = 0; o < H; ++o) {
+        G->w1[(size_t)i * H + o] += x[i] * gz1[o];
+        acc += (double)P->w1[(size_t)i * H + o] * gz1[o];
+      }
+      gx[i] = acc;
+    }
+    (void)gh2;
+    (void)gh1;
+    for (int c = 0; c < ct; ++c) G->temporal[(size_t)j * ct + c] += gx[cs + c];
+    int tx[4], ty[4];
+    double fx, fy;
+    om_fit_taps(P, ix, iy, tx, ty, &fx, &fy);
+    /* d x_c / d f_tap: the bilinear weights of the four taps */
+    double wt[4] = {(1.0 - fx) * (1.0 - fy), fx * (1.0 - fy), (1.0 - fx) * fy, fx * fy};
+    for (int q = 0; q < 4; ++q) {
+      for (int c = 0; c < cs; ++c) {
+        int64_t bc = ((int64_t)(ty[q] >> 2) * bw + (tx[q] >> 2)) * cs + c;
+        int p = (ty[q] & 3) * 4 + (tx[q] & 3);
+        double dea, deb, dw;
+        om_sim_value(P, bc, p, relaxed, &dea, &deb, &dw);
+        double gf = wt[q] * gx[c];
+        G->ea[bc] += dea * gf;
+        G->eb[bc] += deb * gf;
+        G->w[bc * 16 + p] += dw * gf;
+      }
+    }
+  }
+  return loss / (3.0 * (double)n);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Optimiser and sampler for the fit loop                                   */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Adam (Kingma & Ba) on one tensor, with optional projection onto [0,1] for
+ * the BC endpoint and weight parameters (Eq. 6 constrains them there).
+ * Parameters are stored FP32; moments and the update are FP64.
+ */
+void om_adam(float *p, const double *g, double *m, double *v, int64_t n, int32_t step, double lr, double beta1,
+             double beta2, double eps, int32_t project) {
+  double c1 = 1.0 - pow(beta1, (double)step);
+  double c2 = 1.0 - pow(beta2, (double)step);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+    double mh = m[i] / c1, vh = v[i] / c2;
+    double q = (double)p[i] - lr * mh / (sqrt(vh) + eps);
+    if (project) q = q < 0.0 ? 0.0 : (q > 1.0 ? 1.0 : q);
+    p[i] = (float)q;
+  }
+}
+
+/* SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014). */
+static uint64_t om_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* The generator's next() output from state x (exported for its test vector). */
+uint64_t om_splitmix64_next(uint64_t x) { return om_splitmix64(x); }
+
+/*
+ * Counter-based fit sample i of step `step`: two SplitMix64 outputs at
+ * counters c = seed + 2*(step*2^32 + i)*golden and c + golden.
+ * ix = lo32(z1) % lm_w, iy = hi32(z1) % lm_h, j = lo32(z2) % T.
+ */
+void om_fit_draw(uint64_t seed, int64_t step, int64_t first, int64_t n, int32_t lm_w, int32_t lm_h,
+                 int32_t t_count, int32_t *samples) {
+  const uint64_t golden = 0x9E3779B97F4A7C15ull;
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t ctr = ((uint64_t)step << 32) + (uint64_t)(first + i);
+    uint64_t base = seed + 2u * ctr * golden;
+    uint64_t z1 = om_splitmix64(base);
+    uint64_t z2 = om_splitmix64(base + golden);
+    samples[3 * i] = (int32_t)((uint32_t)z1 % (uint32_t)lm_w);
+    samples[3 * i + 1] = (int32_t)((uint32_t)(z1 >> 32) % (uint32_t)lm_h);
+    samples[3 * i + 2] = (int32_t)((uint32_t)z2 % (uint32_t)t_count);
+  }
+}
