@@ -1,0 +1,308 @@
+/*
+ * ndgi.h -- C ABI of libndgi.so: random-access neural decode of temporal
+ * lightmap sets (Neural Dynamic GI, arXiv 2604.12625) on NVIDIA GB300 (sm_103a).
+ *
+ * The library evaluates the compact model of Sec. 3.1, Eq. 3,
+ *     I(u, v, t) = H_Theta(u, v, t),
+ * in the form fixed for this library: one spatial feature map of `cs`
+ * single-channel BC4 planes (4x4 blocks of two 8-bit endpoints and sixteen
+ * 3-bit indices; the endpoint/weight block form of Sec. 3.4, Eq. 6-7 and
+ * supplement S2) sampled bilinearly at (u, v); one temporal feature line of
+ * `t_count` x `ct` values sampled linearly at t (the linear operator of
+ * Sec. 3.1, Eq. 2, applied to features); their concatenation fed to an MLP
+ * with two hidden ReLU layers and a linear RGB output (Sec. 4).
+ *
+ * Conventions for every call
+ *   - Every buffer argument is caller-owned DEVICE memory unless the comment
+ *     says "host".  The library never frees caller memory and keeps no
+ *     pointer to it after the call returns, except a pages plan, which
+ *     records the model descriptors, workspaces and physical texture given
+ *     to ndgi_pages_plan_create until it is destroyed.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     enqueue work on it and return without synchronising; results are
+ *     valid once the stream has reached that point.
+ *   - Every call returns an ndgi_status.  Argument errors are detected on the
+ *     host before anything is enqueued.  No call traps, asserts or aborts;
+ *     ndgi_last_error() gives a message for the most recent failure on the
+ *     calling thread.
+ *   - Feature coordinates use the texel-centre convention x = u*feat_w - 0.5;
+ *     keyframes sit at t_j = j/t_count and the temporal axis is periodic
+ *     (the segment after the last keyframe interpolates back to row 0).
+ */
+#ifndef NDGI_H_
+#define NDGI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NDGI_OK = 0,
+  NDGI_ERR_INVALID_ARG = 1,   /* a pointer, size or enum is out of range   */
+  NDGI_ERR_UNSUPPORTED = 2,   /* valid, but this shape/precision not built */
+  NDGI_ERR_CUDA = 3,          /* a CUDA runtime call failed                */
+  NDGI_ERR_OOM = 4,           /* a library-owned allocation failed         */
+  NDGI_ERR_TIMEOUT = 5,       /* a bounded device wait ran out             */
+  NDGI_ERR_DEVICE_CHECK = 6   /* a device-side argument check failed       */
+} ndgi_status;
+
+typedef enum {
+  NDGI_FP32 = 0,              /* plain FP32 CUDA-core decode               */
+  NDGI_FP16 = 1,              /* tcgen05 tensor cores, FP16 operands, FP32 accumulate */
+  NDGI_BF16 = 2,              /* tcgen05 tensor cores, BF16 operands, FP32 accumulate */
+  NDGI_FP8_E4M3 = 3           /* reserved                                  */
+} ndgi_precision;
+
+/*
+ * A decodable model (Sec. 3.3, Eq. 5 restricted to one BC feature map, one
+ * temporal line and the decoder parameters Phi).  A view: every pointer is
+ * device memory owned by the caller.
+ *   lm_w, lm_h       lightmap size; used to turn page texels into (u, v)
+ *   feat_w, feat_h   feature-plane size, multiples of 4
+ *   cs               number of BC4 planes (spatial feature channels)
+ *   bc4              [feat_h/4][feat_w/4][cs][8] bytes: per block, per plane,
+ *                    byte0 = r0, byte1 = r1, then 48 index bits little-endian,
+ *                    texel p = 4*row + col at bit 16 + 3p of the 64-bit block
+ *   t_count, ct      temporal line: t_count keyframes of ct channels
+ *   temporal         [t_count][ct] of temporal_dtype (NDGI_FP32 or NDGI_FP16)
+ *   hidden           width of both hidden layers
+ *   w1 [cs+ct][hidden], b1 [hidden], w2 [hidden][hidden], b2 [hidden],
+ *   w3 [hidden][3], b3 [3]: FP32, row-major [in][out]
+ *   address_mode     0 = clamp to edge, 1 = mirrored repeat (spatial axes)
+ */
+typedef struct {
+  int32_t lm_w, lm_h;
+  int32_t feat_w, feat_h, cs;
+  const uint8_t *bc4;
+  int32_t t_count, ct;
+  const void *temporal;
+  int32_t temporal_dtype;
+  int32_t hidden;
+  const float *w1, *b1, *w2, *b2, *w3, *b3;
+  int32_t address_mode;
+} ndgi_model_desc;
+
+/* Library version string (static storage). */
+const char *ndgi_version(void);
+
+/*
+ * Copies the message of the calling thread's most recent failed call into
+ * buf (host, NUL-terminated, truncated to buf_len).  Returns the status of
+ * that failure, NDGI_OK if none.
+ */
+ndgi_status ndgi_last_error(char *buf, size_t buf_len);
+
+/*
+ * Synchronises `stream` and reports any asynchronous CUDA error raised by
+ * work enqueued on it (NDGI_ERR_CUDA), else NDGI_OK.
+ */
+ndgi_status ndgi_check(void *stream);
+
+/*
+ * Bytes of device workspace that ndgi_prepare needs for `precision`: the
+ * MLP weights re-packed for the tensor-core decode.  0 for NDGI_FP32.
+ */
+size_t ndgi_prepare_workspace_size(const ndgi_model_desc *model, ndgi_precision precision);
+
+/*
+ * Packs the model's MLP into `ws` (device, caller-owned, ws_bytes >=
+ * ndgi_prepare_workspace_size, 256-byte aligned) for decodes of
+ * `precision`: weights rounded once to FP16/BF16 (round to nearest even),
+ * laid out as the tensor-core operand tiles.  The packed weights are the
+ * parameters such a decode evaluates.  Re-run it whenever the weights change.
+ */
+ndgi_status ndgi_prepare(const ndgi_model_desc *model, ndgi_precision precision, void *ws, size_t ws_bytes,
+                         void *stream);
+
+/*
+ * Random-access point decode (Sec. 3.1, Eq. 3; Sec. 5.5 decodes this way):
+ * for each i < n, rgb[i] = H(u_i, v_i, t_i).
+ *   uvt  [n][3] FP32 (u, v, t); rgb [n][3] FP32 output.
+ *   ws   the prepared workspace for `precision` (ignored for NDGI_FP32).
+ * n == 0 is a no-op.  Non-finite coordinates give unspecified but in-bounds
+ * results.
+ */
+ndgi_status ndgi_decode_points(const ndgi_model_desc *model, ndgi_precision precision, const void *ws,
+                               const float *uvt, int64_t n, float *rgb, void *stream);
+
+/*
+ * The gather stage alone (Sec. 3.3 sampling of the feature map and temporal
+ * line), for validation: x [n][cs+ct] FP32 receives [v_s, v_t]; p35
+ * [n][4][cs] int32 (may be NULL) receives, for the taps (x0,y0), (x1,y0),
+ * (x0,y1), (x1,y1), the BC4 palette numerator P35 (value = P35/8925) of each
+ * plane: the exact integer the decode used.
+ */
+ndgi_status ndgi_debug_features(const ndgi_model_desc *model, const float *uvt, int64_t n, float *x,
+                                int32_t *p35, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Batched virtual-texture page decode (Sec. 3.5, supplement S3)           */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * One page request: decode texels (x0+i, y0+j), 0 <= i < w, 0 <= j < h, of
+ * lightmap `model` at time t into the physical texture at (dst_x+i, dst_y+j).
+ * 1 <= w, h <= 128; the source rectangle lies inside the lightmap and the
+ * destination inside the physical texture.  32 bytes.
+ */
+typedef struct {
+  int32_t model, x0, y0, w, h;
+  float t;
+  int32_t dst_x, dst_y;
+} ndgi_page_req;
+
+typedef enum {
+  NDGI_RGBA32F = 0,           /* 16 bytes per texel, A = 1                 */
+  NDGI_RGBA16F = 1            /* 8 bytes per texel, A = 1                  */
+} ndgi_out_format;
+
+typedef struct ndgi_pages_plan ndgi_pages_plan;
+
+/*
+ * Creates a reusable plan for page decodes: n_models model descriptors
+ * (host array, copied), their prepared workspaces ws[i] (host array of
+ * device pointers; NULL entries allowed for NDGI_FP32), the physical
+ * texture phys (device, [phys_h][phys_w] texels of out_format) and the
+ * maximum number of requests per call.  The plan owns a small device
+ * block (model table, work counter, error word) and the CUDA graph of the
+ * decode.  *plan receives the handle.
+ */
+ndgi_status ndgi_pages_plan_create(const ndgi_model_desc *models, const void *const *ws, int32_t n_models,
+                                   ndgi_precision precision, int32_t max_reqs, int32_t out_format, void *phys,
+                                   int64_t phys_w, int64_t phys_h, ndgi_pages_plan **plan);
+
+/*
+ * Decodes the requests reqs_dev[0 .. *n_dev) (both device memory, so a
+ * frame's request list can be produced on the GPU) with one persistent
+ * launch replayed from the plan's CUDA graph.  reqs_dev must hold at least
+ * *n_dev entries.  Requests that fail the device-side checks (bad model id,
+ * sizes outside 1..128, rectangles outside the lightmap or the physical
+ * texture) are skipped; *n_dev < 0 or > max_reqs rejects the whole frame.
+ * Both are latched in the plan's error word (bit 0: count, bit 1: model or
+ * size, bit 2: rectangle), which ndgi_pages_check reads.  The graph is
+ * rebuilt when reqs_dev or n_dev differ from the previous call.  Requests
+ * with overlapping destinations race.
+ */
+ndgi_status ndgi_decode_pages(ndgi_pages_plan *plan, const ndgi_page_req *reqs_dev, const int32_t *n_dev,
+                              void *stream);
+
+/*
+ * Picks the plan's launch shape (CTAs per SM and texel-tile shape) by timing
+ * each candidate on the given requests (n_host = *n_dev, for sizing) and
+ * keeps the fastest.  The physical texture is overwritten.
+ */
+ndgi_status ndgi_pages_autotune(ndgi_pages_plan *plan, const ndgi_page_req *reqs_dev, const int32_t *n_dev,
+                                int32_t n_host, void *stream);
+
+/*
+ * Synchronises `stream` and reads the plan's device error word into
+ * *device_error (host; 0 = no request was rejected), then clears it.
+ * Returns NDGI_ERR_DEVICE_CHECK if it was set.
+ */
+ndgi_status ndgi_pages_check(ndgi_pages_plan *plan, int32_t *device_error, void *stream);
+
+/* Destroys the plan and its device block and graph.  NULL is a no-op. */
+ndgi_status ndgi_pages_plan_destroy(ndgi_pages_plan *plan);
+
+/* ---------------------------------------------------------------------- */
+/* BC simulation and packing (Sec. 3.4, Eq. 6-7)                          */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Packs trained endpoints and weights into BC4 blocks whose decode equals
+ * the straight-through simulated values exactly (end of Sec. 3.4: after
+ * training, the feature map is rebuilt from E and W, quantised and block
+ * compressed).  Per block and plane: A = q255(ea), B = q255(eb),
+ * k_p = q7(w_p) with q_s(x) = floor(min(max(s*x + 0.5, 0), s)) in FP32;
+ *   A > B : r0 = A, r1 = B, index = (k == 0 ? 0 : k == 7 ? 1 : k + 1)
+ *   A < B : r0 = B, r1 = A, the same map applied to 7 - k
+ *   A == B: r0 = r1 = A, all indices 0.
+ * ea, eb [feat_h/4][feat_w/4][cs] FP32, w [feat_h/4][feat_w/4][cs][16] FP32,
+ * bc4_out [feat_h/4][feat_w/4][cs][8] bytes.
+ */
+ndgi_status ndgi_bc_pack(const float *ea, const float *eb, const float *w, int32_t cs, int32_t feat_w,
+                         int32_t feat_h, uint8_t *bc4_out, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Differentiable fit (Sec. 3.4 BC simulation, Sec. 4 training)           */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Trainable parameters, FP32 device memory owned by the caller.  The BC
+ * planes are held as the simulation's endpoints and weights (Eq. 6):
+ *   ea, eb [feat_h/4][feat_w/4][cs] in [0,1], w [feat_h/4][feat_w/4][cs][16]
+ *   in [0,1]; temporal [t_count][ct]; MLP as in ndgi_model_desc.
+ * A fit sample is an int32 triple (ix, iy, j): texel (ix, iy) of the
+ * lm_w x lm_h target at keyframe j (t = j / t_count).
+ */
+typedef struct {
+  int32_t lm_w, lm_h, feat_w, feat_h, cs, t_count, ct, hidden;
+  float *ea, *eb, *w, *temporal, *w1, *b1, *w2, *b2, *w3, *b3;
+  int32_t address_mode;
+} ndgi_fit_params;
+
+/* Gradient buffers shaped like ndgi_fit_params' tensors (FP32, device). */
+typedef struct {
+  float *ea, *eb, *w, *temporal, *w1, *b1, *w2, *b2, *w3, *b3;
+} ndgi_fit_grads;
+
+/*
+ * Forward of the fit at n samples [n][3]: rgb [n][3] FP32.  relaxed = 0 uses
+ * the straight-through BC simulation (features quantised exactly as the
+ * packed decode would see them); relaxed = 1 uses the continuous Eq. 7 with
+ * unquantised E and W (for finite-difference checks).
+ */
+ndgi_status ndgi_fit_forward(const ndgi_fit_params *params, const int32_t *samples, int64_t n, int32_t relaxed,
+                             float *rgb, void *stream);
+
+/*
+ * Backward of the fit: given dL/drgb [n][3], ADDS dL/dparam into *grads
+ * (caller zeroes them).  Activations are recomputed, not stored.  The
+ * straight-through estimator treats the quantisers as identity and uses
+ * the quantised values as chain-rule factors:
+ *   dL/dea += (1 - q(w)) g_f, dL/deb += q(w) g_f, dL/dw += (q(eb) - q(ea)) g_f.
+ * Accumulation uses FP32 atomics, so results vary in the last bits.
+ */
+ndgi_status ndgi_fit_backward(const ndgi_fit_params *params, const int32_t *samples, int64_t n, int32_t relaxed,
+                              const float *grad_rgb, const ndgi_fit_grads *grads, void *stream);
+
+/* Fit loop settings (Sec. 4: Adam, L2 loss; final stage freezes features). */
+typedef struct {
+  int32_t steps;              /* Adam steps                                 */
+  int32_t batch;              /* samples per step                           */
+  float lr, beta1, beta2, eps;
+  int32_t freeze_steps;       /* last steps update the MLP only             */
+  int32_t loss_every;         /* FP64 loss logged every k steps (0 = never) */
+  uint64_t seed;              /* sample stream (counter-based SplitMix64)   */
+  int32_t relaxed;            /* 1 = no BC quantisation in the forward      */
+} ndgi_fit_config;
+
+/* Bytes of device workspace ndgi_encode_fit needs. */
+size_t ndgi_encode_fit_workspace_size(const ndgi_fit_params *params, const ndgi_fit_config *cfg);
+
+/*
+ * Runs cfg->steps Adam steps of the L2 fit on device.  Each step draws
+ * cfg->batch samples (ix, iy, j) with the counter-based generator
+ *   ctr = step * 2^32 + i, z1 = SplitMix64(seed + (2 ctr + 1) g),
+ *   z2 = SplitMix64(seed + (2 ctr + 2) g), g = 0x9E3779B97F4A7C15,
+ *   ix = lo32(z1) mod lm_w, iy = hi32(z1) mod lm_h, j = lo32(z2) mod t_count,
+ * evaluates the straight-through forward, the MSE against targets
+ * [t_count][lm_h][lm_w][3] FP16 (device), the backward, and Adam (endpoints
+ * and weights projected onto [0,1]).  step_offset continues a previous run
+ * (Adam step numbering and sample stream).  Every loss_every steps the FP64
+ * batch loss is written to loss_log[k] (device, double,
+ * ceil(steps/loss_every) entries).  ws: device workspace of
+ * ndgi_encode_fit_workspace_size bytes, holding the Adam moments (keep it
+ * between calls to resume).  Pack the result with ndgi_bc_pack.
+ */
+ndgi_status ndgi_encode_fit(const ndgi_fit_params *params, const uint16_t *targets, const ndgi_fit_config *cfg,
+                            int32_t step_offset, void *ws, size_t ws_bytes, double *loss_log, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NDGI_H_ */

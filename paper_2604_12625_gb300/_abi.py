@@ -1,0 +1,111 @@
+"""ctypes view of include/ndgi.h (argument marshalling only).
+
+The library is the in-tree libndgi.so built by ``build.py``.  Importing this
+module fails loudly if it is missing: there is no CPU or eager fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libndgi.so")
+
+NDGI_OK, NDGI_ERR_INVALID_ARG, NDGI_ERR_UNSUPPORTED, NDGI_ERR_CUDA, NDGI_ERR_OOM, NDGI_ERR_TIMEOUT, \
+    NDGI_ERR_DEVICE_CHECK = range(7)
+NDGI_FP32, NDGI_FP16, NDGI_BF16, NDGI_FP8_E4M3 = range(4)
+NDGI_RGBA32F, NDGI_RGBA16F = 0, 1
+PRECISIONS = {"fp32": NDGI_FP32, "fp16": NDGI_FP16, "bf16": NDGI_BF16, "fp8": NDGI_FP8_E4M3}
+STATUS_NAMES = {0: "NDGI_OK", 1: "NDGI_ERR_INVALID_ARG", 2: "NDGI_ERR_UNSUPPORTED", 3: "NDGI_ERR_CUDA",
+                4: "NDGI_ERR_OOM", 5: "NDGI_ERR_TIMEOUT", 6: "NDGI_ERR_DEVICE_CHECK"}
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("lm_w", C.c_int32), ("lm_h", C.c_int32), ("feat_w", C.c_int32), ("feat_h", C.c_int32),
+                ("cs", C.c_int32), ("bc4", C.c_void_p), ("t_count", C.c_int32), ("ct", C.c_int32),
+                ("temporal", C.c_void_p), ("temporal_dtype", C.c_int32), ("hidden", C.c_int32),
+                ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+
+
+class PageReq(C.Structure):
+    _fields_ = [("model", C.c_int32), ("x0", C.c_int32), ("y0", C.c_int32), ("w", C.c_int32),
+                ("h", C.c_int32), ("t", C.c_float), ("dst_x", C.c_int32), ("dst_y", C.c_int32)]
+
+
+FIT_TENSORS = ("ea", "eb", "w", "temporal", "w1", "b1", "w2", "b2", "w3", "b3")
+
+
+class FitParams(C.Structure):
+    _fields_ = [("lm_w", C.c_int32), ("lm_h", C.c_int32), ("feat_w", C.c_int32), ("feat_h", C.c_int32),
+                ("cs", C.c_int32), ("t_count", C.c_int32), ("ct", C.c_int32), ("hidden", C.c_int32)] + \
+               [(k, C.c_void_p) for k in FIT_TENSORS] + [("address_mode", C.c_int32)]
+
+
+class FitGrads(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in FIT_TENSORS]
+
+
+class FitConfig(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("freeze_steps", C.c_int32), ("loss_every", C.c_int32),
+                ("seed", C.c_uint64), ("relaxed", C.c_int32)]
+
+
+# (name, restype, argtypes) of every exported entry point in include/ndgi.h
+_vp, _i32, _i64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+SIGNATURES = [
+    ("ndgi_version", C.c_char_p, []),
+    ("ndgi_last_error", C.c_int, [C.c_char_p, _sz]),
+    ("ndgi_check", C.c_int, [_vp]),
+    ("ndgi_prepare_workspace_size", _sz, [_vp, C.c_int]),
+    ("ndgi_prepare", C.c_int, [_vp, C.c_int, _vp, _sz, _vp]),
+    ("ndgi_decode_points", C.c_int, [_vp, C.c_int, _vp, _vp, _i64, _vp, _vp]),
+    ("ndgi_debug_features", C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    ("ndgi_pages_plan_create", C.c_int, [_vp, _vp, _i32, C.c_int, _i32, _i32, _vp, _i64, _i64, _vp]),
+    ("ndgi_decode_pages", C.c_int, [_vp, _vp, _vp, _vp]),
+    ("ndgi_pages_autotune", C.c_int, [_vp, _vp, _vp, _i32, _vp]),
+    ("ndgi_pages_check", C.c_int, [_vp, _vp, _vp]),
+    ("ndgi_pages_plan_destroy", C.c_int, [_vp]),
+    ("ndgi_bc_pack", C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    ("ndgi_fit_forward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
+    ("ndgi_fit_backward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),
+    ("ndgi_encode_fit_workspace_size", _sz, [_vp, _vp]),
+    ("ndgi_encode_fit", C.c_int, [_vp, _vp, _vp, _i32, _vp, _sz, _vp, _vp]),
+]
+
+_lib = None
+
+
+class NdgiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """The loaded libndgi.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libndgi.so is not built ({LIB_PATH}); run paper_2604_12625_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error():
+    buf = C.create_string_buffer(1024)
+    st = lib().ndgi_last_error(buf, len(buf))
+    return st, buf.value.decode(errors="replace")
+
+
+def check(status):
+    if status != NDGI_OK:
+        _, msg = last_error()
+        raise NdgiError(status, msg)
+    return status

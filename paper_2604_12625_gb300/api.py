@@ -1,0 +1,273 @@
+"""Python binding of libndgi.so: the entry points of include/ndgi.h under the
+same names, taking torch CUDA tensors.  Argument marshalling only; every
+step of the decode and the fit runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi as A
+from ._abi import check, lib
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    return t
+
+
+def _prec(p):
+    return A.PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+# ---------------------------------------------------------------------------
+# Model
+# ---------------------------------------------------------------------------
+class Model:
+    """A decodable model resident on the GPU plus its ndgi_model_desc.
+
+    Tensors: bc4 uint8 [feat_h/4][feat_w/4][cs][8], temporal [T][ct] float32 or
+    float16, MLP weights float32 [in][out].  Prepared tensor-core workspaces
+    are kept per precision in ``self.ws``.
+    """
+
+    def __init__(self, lm_w, lm_h, bc4, temporal, w1, b1, w2, b2, w3, b3, address_mode=0):
+        self.lm_w, self.lm_h = int(lm_w), int(lm_h)
+        self.bc4 = _need(bc4, torch.uint8, "bc4")
+        bh, bw, cs, eight = bc4.shape
+        assert eight == 8
+        self.feat_w, self.feat_h, self.cs = bw * 4, bh * 4, cs
+        if temporal.dtype not in (torch.float32, torch.float16):
+            raise ValueError("temporal must be float32 or float16")
+        self.temporal = _need(temporal, temporal.dtype, "temporal")
+        self.t_count, self.ct = temporal.shape
+        self.w = {k: _need(v, torch.float32, k) for k, v in
+                  dict(w1=w1, b1=b1, w2=w2, b2=b2, w3=w3, b3=b3).items()}
+        self.hidden = w2.shape[0]
+        self.address_mode = int(address_mode)
+        self.desc = A.ModelDesc(self.lm_w, self.lm_h, self.feat_w, self.feat_h, self.cs, self.bc4.data_ptr(),
+                                self.t_count, self.ct, self.temporal.data_ptr(),
+                                A.NDGI_FP16 if temporal.dtype == torch.float16 else A.NDGI_FP32, self.hidden,
+                                *[self.w[k].data_ptr() for k in ("w1", "b1", "w2", "b2", "w3", "b3")],
+                                self.address_mode)
+        self.ws = {}
+
+    @classmethod
+    def from_arrays(cls, m, device="cuda"):
+        """From a dict of numpy arrays (the layout of synth.model)."""
+        def t(a):
+            return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return cls(m["lm_w"], m["lm_h"], t(m["bc4"]), t(m["temporal"]), t(m["w1"]), t(m["b1"]), t(m["w2"]),
+                   t(m["b2"]), t(m["w3"]), t(m["b3"]), m.get("address_mode", 0))
+
+    def workspace(self, precision):
+        precision = _prec(precision)
+        if precision == A.NDGI_FP32:
+            return None
+        if precision not in self.ws:
+            self.ws[precision] = ndgi_prepare(self, precision)
+        return self.ws[precision]
+
+
+def ndgi_version():
+    return lib().ndgi_version().decode()
+
+
+def ndgi_check(stream=None):
+    return check(lib().ndgi_check(_stream(stream)))
+
+
+def ndgi_prepare_workspace_size(model, precision):
+    return int(lib().ndgi_prepare_workspace_size(C.byref(model.desc), _prec(precision)))
+
+
+def ndgi_prepare(model, precision, ws=None, stream=None):
+    """Packs the MLP for a tensor-core decode; returns the workspace tensor."""
+    n = ndgi_prepare_workspace_size(model, precision)
+    if ws is None:
+        ws = torch.empty(max(n, 256), dtype=torch.uint8, device=model.bc4.device)
+    check(lib().ndgi_prepare(C.byref(model.desc), _prec(precision), _p(ws), ws.numel(), _stream(stream)))
+    return ws
+
+
+def ndgi_decode_points(model, uvt, precision="fp32", ws=None, out=None, stream=None):
+    """rgb [n][3] float32 of the decode at each (u, v, t) row of uvt."""
+    uvt = _need(uvt, torch.float32, "uvt")
+    n = uvt.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=uvt.device)
+    _need(out, torch.float32, "out")
+    pr = _prec(precision)
+    if ws is None and pr != A.NDGI_FP32:
+        ws = model.workspace(pr)
+    check(lib().ndgi_decode_points(C.byref(model.desc), pr, _p(ws), _p(uvt), n, _p(out), _stream(stream)))
+    return out
+
+
+def ndgi_debug_features(model, uvt, stream=None):
+    """(x [n][cs+ct] float32, p35 [n][4][cs] int32) of the gather stage."""
+    uvt = _need(uvt, torch.float32, "uvt")
+    n = uvt.shape[0]
+    x = torch.empty((n, model.cs + model.ct), dtype=torch.float32, device=uvt.device)
+    p35 = torch.empty((n, 4, model.cs), dtype=torch.int32, device=uvt.device)
+    check(lib().ndgi_debug_features(C.byref(model.desc), _p(uvt), n, _p(x), _p(p35), _stream(stream)))
+    return x, p35
+
+
+# ---------------------------------------------------------------------------
+# Pages
+# ---------------------------------------------------------------------------
+PAGE_REQ_DTYPE = np.dtype([("model", "<i4"), ("x0", "<i4"), ("y0", "<i4"), ("w", "<i4"), ("h", "<i4"),
+                           ("t", "<f4"), ("dst_x", "<i4"), ("dst_y", "<i4")])
+
+
+def page_requests_to_device(reqs, device="cuda"):
+    """Structured numpy array (PAGE_REQ_DTYPE) -> (int32 [n][8] CUDA tensor, n tensor)."""
+    r = np.ascontiguousarray(reqs).view(np.int32).reshape(-1, 8)
+    t = torch.from_numpy(r.copy()).to(device)
+    n = torch.tensor([len(reqs)], dtype=torch.int32, device=device)
+    return t, n
+
+
+class PagesPlan:
+    """ndgi_pages_plan_* wrapper.  `phys` is [phys_h][phys_w][4] float32 or float16."""
+
+    def __init__(self, models, precision, max_reqs, phys):
+        self.models = list(models)
+        self.precision = _prec(precision)
+        self.phys = phys
+        if phys.dtype == torch.float32:
+            fmt = A.NDGI_RGBA32F
+        elif phys.dtype == torch.float16:
+            fmt = A.NDGI_RGBA16F
+        else:
+            raise ValueError("phys must be float32 or float16 RGBA")
+        assert phys.is_cuda and phys.is_contiguous() and phys.shape[-1] == 4
+        descs = (A.ModelDesc * len(self.models))(*[m.desc for m in self.models])
+        ws = [m.workspace(self.precision) for m in self.models]
+        ws_arr = (C.c_void_p * len(ws))(*[w.data_ptr() if w is not None else None for w in ws])
+        self._keep = (descs, ws_arr, ws)
+        h = C.c_void_p()
+        check(lib().ndgi_pages_plan_create(descs, ws_arr, len(self.models), self.precision, int(max_reqs), fmt,
+                                           _p(phys), phys.shape[1], phys.shape[0], C.byref(h)))
+        self.handle = h
+
+    def decode(self, reqs, n_dev, stream=None):
+        check(lib().ndgi_decode_pages(self.handle, _p(reqs), _p(n_dev), _stream(stream)))
+
+    def autotune(self, reqs, n_dev, n_host, stream=None):
+        check(lib().ndgi_pages_autotune(self.handle, _p(reqs), _p(n_dev), int(n_host), _stream(stream)))
+
+    def check(self, stream=None):
+        err = C.c_int32(0)
+        st = lib().ndgi_pages_check(self.handle, C.byref(err), _stream(stream))
+        return st, err.value
+
+    def close(self):
+        if self.handle:
+            check(lib().ndgi_pages_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ndgi_decode_pages(plan, reqs, n_dev, stream=None):
+    plan.decode(reqs, n_dev, stream)
+
+
+# ---------------------------------------------------------------------------
+# BC pack and fit
+# ---------------------------------------------------------------------------
+def ndgi_bc_pack(ea, eb, w, out=None, stream=None):
+    """BC4 blocks uint8 [bh][bw][cs][8] from endpoints [bh][bw][cs] and weights [bh][bw][cs][16]."""
+    _need(ea, torch.float32, "ea")
+    _need(eb, torch.float32, "eb")
+    _need(w, torch.float32, "w")
+    bh, bw, cs = ea.shape
+    if out is None:
+        out = torch.empty((bh, bw, cs, 8), dtype=torch.uint8, device=ea.device)
+    check(lib().ndgi_bc_pack(_p(ea), _p(eb), _p(w), cs, bw * 4, bh * 4, _p(out), _stream(stream)))
+    return out
+
+
+class FitState:
+    """Trainable parameters of the fit (float32 CUDA tensors) and their struct."""
+
+    def __init__(self, tensors, lm_w, lm_h, address_mode=0):
+        self.t = {k: _need(tensors[k], torch.float32, k) for k in A.FIT_TENSORS}
+        bh, bw, cs = self.t["ea"].shape
+        T, ct = self.t["temporal"].shape
+        H = self.t["w2"].shape[0]
+        self.lm_w, self.lm_h = int(lm_w), int(lm_h)
+        self.dims = dict(feat_w=bw * 4, feat_h=bh * 4, cs=cs, t_count=T, ct=ct, hidden=H)
+        self.params = A.FitParams(self.lm_w, self.lm_h, bw * 4, bh * 4, cs, T, ct, H,
+                                  *[self.t[k].data_ptr() for k in A.FIT_TENSORS], int(address_mode))
+
+    @classmethod
+    def from_arrays(cls, p, lm_w, lm_h, device="cuda"):
+        return cls({k: torch.from_numpy(np.ascontiguousarray(p[k], np.float32)).to(device) for k in A.FIT_TENSORS},
+                   lm_w, lm_h, p.get("address_mode", 0))
+
+    def zeros_like(self):
+        return {k: torch.zeros_like(v) for k, v in self.t.items()}
+
+
+def ndgi_fit_forward(state, samples, relaxed=False, out=None, stream=None):
+    _need(samples, torch.int32, "samples")
+    n = samples.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=samples.device)
+    check(lib().ndgi_fit_forward(C.byref(state.params), _p(samples), n, int(relaxed), _p(out), _stream(stream)))
+    return out
+
+
+def ndgi_fit_backward(state, samples, grad_rgb, grads=None, relaxed=False, stream=None):
+    """Adds dL/dparams into `grads` (dict of tensors, created zeroed if None) and returns it."""
+    _need(samples, torch.int32, "samples")
+    _need(grad_rgb, torch.float32, "grad_rgb")
+    if grads is None:
+        grads = state.zeros_like()
+    g = A.FitGrads(*[grads[k].data_ptr() for k in A.FIT_TENSORS])
+    check(lib().ndgi_fit_backward(C.byref(state.params), _p(samples), samples.shape[0], int(relaxed),
+                                  _p(grad_rgb), C.byref(g), _stream(stream)))
+    return grads
+
+
+def fit_config(steps, batch, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, freeze_steps=0, loss_every=0, seed=0,
+               relaxed=False):
+    return A.FitConfig(int(steps), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(freeze_steps),
+                       int(loss_every), int(seed), int(relaxed))
+
+
+def ndgi_encode_fit_workspace_size(state, cfg):
+    return int(lib().ndgi_encode_fit_workspace_size(C.byref(state.params), C.byref(cfg)))
+
+
+def ndgi_encode_fit(state, targets, cfg, step_offset=0, ws=None, loss_log=None, stream=None):
+    """Runs cfg.steps Adam steps in place on state's tensors.  targets: float16
+    [T][lm_h][lm_w][3] CUDA.  Returns (ws, loss_log)."""
+    _need(targets, torch.float16, "targets")
+    if ws is None:
+        ws = torch.empty(ndgi_encode_fit_workspace_size(state, cfg), dtype=torch.uint8, device=targets.device)
+    if loss_log is None and cfg.loss_every > 0:
+        loss_log = torch.zeros((cfg.steps + cfg.loss_every - 1) // cfg.loss_every, dtype=torch.float64,
+                               device=targets.device)
+    check(lib().ndgi_encode_fit(C.byref(state.params), _p(targets), C.byref(cfg), int(step_offset), _p(ws),
+                                ws.numel(), _p(loss_log), _stream(stream)))
+    return ws, loss_log

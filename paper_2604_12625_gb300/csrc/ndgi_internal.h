@@ -1,0 +1,69 @@
+// Internal declarations shared by the CUDA translation units of libndgi.so.
+// Not part of the ABI (that is include/ndgi.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/ndgi.h"
+
+namespace ndgi {
+
+// Launch-time copy of a model descriptor (passed to kernels by value).
+struct DevModel {
+  int lm_w, lm_h, feat_w, feat_h, cs, bw;
+  const uint8_t* bc4;
+  int t_count, ct;
+  const void* temporal;
+  int temporal_f16;
+  int hidden;
+  const float *w1, *b1, *w2, *b2, *w3, *b3;
+  int address_mode;
+  float sx, sy;        // feat_w / lm_w, feat_h / lm_h (page texel -> feature coordinate)
+};
+
+inline DevModel to_dev(const ndgi_model_desc& d) {
+  DevModel m;
+  m.lm_w = d.lm_w; m.lm_h = d.lm_h; m.feat_w = d.feat_w; m.feat_h = d.feat_h; m.cs = d.cs;
+  m.bw = d.feat_w / 4; m.bc4 = d.bc4; m.t_count = d.t_count; m.ct = d.ct; m.temporal = d.temporal;
+  m.temporal_f16 = d.temporal_dtype == NDGI_FP16; m.hidden = d.hidden;
+  m.w1 = d.w1; m.b1 = d.b1; m.w2 = d.w2; m.b2 = d.b2; m.w3 = d.w3; m.b3 = d.b3;
+  m.address_mode = d.address_mode;
+  m.sx = (float)d.feat_w / (float)d.lm_w;
+  m.sy = (float)d.feat_h / (float)d.lm_h;
+  return m;
+}
+
+// Error reporting (thread-local message + status).
+ndgi_status set_error(ndgi_status s, const char* fmt, ...);
+ndgi_status cuda_status(cudaError_t e, const char* what);
+
+int num_sms();
+
+// ---- FP32 CUDA-core decode (decode_simt.cu) ----
+bool simt_supported(int cs, int ct, int hidden);
+cudaError_t launch_points_f32(const DevModel& m, const float* uvt, int64_t n, float* rgb, cudaStream_t s);
+cudaError_t launch_debug_features(const DevModel& m, const float* uvt, int64_t n, float* x, int32_t* p35,
+                                  cudaStream_t s);
+
+// Device-side page-decode context (shared by the SIMT and tensor-core page kernels).
+struct PagesCtx {
+  const DevModel* models;       // device array [n_models]
+  const void* const* ws;        // device array of prepared workspaces
+  int n_models;
+  int max_reqs;
+  int out_format;
+  void* phys;
+  int64_t phys_w, phys_h;
+  unsigned int* work_counter;   // device
+  int* error_word;              // device
+};
+cudaError_t launch_pages_f32(const PagesCtx& c, int cs, int ct, int hidden, const ndgi_page_req* reqs,
+                             const int32_t* n_dev, int grid, cudaStream_t s);
+
+// ---- BC pack (pack.cu) ----
+cudaError_t launch_bc_pack(const float* ea, const float* eb, const float* w, int cs, int feat_w, int feat_h,
+                           uint8_t* out, cudaStream_t s);
+
+}  // namespace ndgi

@@ -1,0 +1,25 @@
+// Tensor-core (tcgen05) decode: declarations used by the C ABI layer.
+#pragma once
+
+#include <vector>
+#include "ndgi_internal.h"
+
+namespace ndgi {
+
+// Launch shape of the persistent page-decode kernel (picked by the autotuner).
+struct TcPagesShape {
+  int ctas_per_sm;    // resident CTAs per SM in the persistent grid
+  int tile_w;         // texel tile: tile_w x (128 / tile_w) texels per MMA tile
+};
+
+bool tc_supported(int cs, int ct, int hidden);
+size_t tc_workspace_bytes(int cs, int ct, int hidden);
+cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream_t s);
+cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const float* uvt, int64_t n, float* rgb,
+                             cudaStream_t s);
+cudaError_t launch_tc_pages(const PagesCtx& c, bool bf16, int cs, int ct, int hidden, const TcPagesShape& shape,
+                            const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s);
+TcPagesShape tc_default_pages_shape();
+std::vector<TcPagesShape> tc_pages_candidates(int sms);
+
+}  // namespace ndgi
