@@ -207,6 +207,31 @@ ndgi_status ndgi_pages_check(ndgi_pages_plan *plan, int32_t *device_error, void 
 /* Destroys the plan and its device block and graph.  NULL is a no-op. */
 ndgi_status ndgi_pages_plan_destroy(ndgi_pages_plan *plan);
 
+/*
+ * Page decode that allocates nothing (the paper has no counterpart; this is
+ * a library service).  For callers that cannot call cudaMalloc, such as code
+ * that runs inside a fixed memory arena or a real-time frame loop where an
+ * allocation could block on the driver: the same FP32 page decode as a plan
+ * with NDGI_FP32, but the model table and error word live in a static
+ * device array of the library instead of a plan's allocated block.
+ *   models       host array of n_models descriptors, 1 <= n_models <= 64
+ *                (more is rejected with NDGI_ERR_INVALID_ARG)
+ *   reqs_dev, n_dev, max_reqs, out_format, phys, phys_w, phys_h
+ *                as for ndgi_pages_plan_create / ndgi_decode_pages
+ *   device_error device int32 (may be NULL) that receives the error word of
+ *                this call (same bits as ndgi_pages_check reports)
+ * The static array is shared by every call and keeps the last call's
+ * contents; each call rewrites it on `stream` before its decode, so calls
+ * that overlap on the GPU race.  The first call on a device looks up the
+ * array's device address (once per device); make that first call before
+ * any stream capture.  Copies the model table from host memory with a
+ * pageable cudaMemcpyAsync, so the call waits for `stream` to drain first.
+ */
+ndgi_status ndgi_decode_pages_static(const ndgi_model_desc *models, int32_t n_models,
+                                     const ndgi_page_req *reqs_dev, const int32_t *n_dev, int32_t max_reqs,
+                                     int32_t out_format, void *phys, int64_t phys_w, int64_t phys_h,
+                                     int32_t *device_error, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* BC simulation and packing (Sec. 3.4, Eq. 6-7)                          */
 /* ---------------------------------------------------------------------- */

@@ -67,6 +67,7 @@ SIGNATURES = [
     ("ndgi_pages_autotune", C.c_int, [_vp, _vp, _vp, _i32, _vp]),
     ("ndgi_pages_check", C.c_int, [_vp, _vp, _vp]),
     ("ndgi_pages_plan_destroy", C.c_int, [_vp]),
+    ("ndgi_decode_pages_static", C.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _i64, _i64, _vp, _vp]),
     ("ndgi_bc_pack", C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     ("ndgi_fit_forward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("ndgi_fit_backward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),

@@ -191,6 +191,16 @@ def ndgi_decode_pages(plan, reqs, n_dev, stream=None):
     plan.decode(reqs, n_dev, stream)
 
 
+def ndgi_decode_pages_static(models, reqs, n_dev, max_reqs, phys, device_error=None, stream=None):
+    """FP32 page decode that allocates nothing on the device (library-held
+    static scratch); for callers that cannot use cudaMalloc.  Same output as
+    a PagesPlan with "fp32"."""
+    fmt = A.NDGI_RGBA32F if phys.dtype == torch.float32 else A.NDGI_RGBA16F
+    descs = (A.ModelDesc * len(models))(*[m.desc for m in models])
+    check(lib().ndgi_decode_pages_static(descs, len(models), _p(reqs), _p(n_dev), int(max_reqs), fmt, _p(phys),
+                                         phys.shape[1], phys.shape[0], _p(device_error), _stream(stream)))
+
+
 # ---------------------------------------------------------------------------
 # BC pack and fit
 # ---------------------------------------------------------------------------
