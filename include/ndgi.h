@@ -97,7 +97,9 @@ ndgi_status ndgi_last_error(char *buf, size_t buf_len);
 
 /*
  * Synchronises `stream` and reports any asynchronous CUDA error raised by
- * work enqueued on it (NDGI_ERR_CUDA), else NDGI_OK.
+ * work enqueued on it (NDGI_ERR_CUDA), then reads and clears the library's
+ * device error word: a tensor-core kernel whose bounded barrier wait ran out
+ * unwinds, frees its tensor memory and latches it (NDGI_ERR_TIMEOUT).
  */
 ndgi_status ndgi_check(void *stream);
 

@@ -90,7 +90,11 @@ ndgi_status ndgi_last_error(char* buf, size_t buf_len) {
 ndgi_status ndgi_check(void* stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaGetLastError();
-  return cuda_status(e, "ndgi_check");
+  if (e != cudaSuccess) return cuda_status(e, "ndgi_check");
+  const int dev_err = tc_take_error();
+  if (dev_err < 0) return set_error(NDGI_ERR_CUDA, "ndgi_check: cannot read the device error word");
+  if (dev_err) return set_error(NDGI_ERR_TIMEOUT, "ndgi_check: a tensor-core barrier wait timed out (0x%x)", dev_err);
+  return NDGI_OK;
 }
 
 size_t ndgi_prepare_workspace_size(const ndgi_model_desc* model, ndgi_precision precision) {

@@ -1,0 +1,52 @@
+// FP32 feature gather shared by the CUDA-core and tensor-core decodes.
+#pragma once
+
+#include "ndgi_internal.h"
+#include "bc4.cuh"
+
+namespace ndgi {
+
+// Feature gather at (u, v, t) in FP32: x = [v_s (CS), v_t (CT)].
+// If p35 != nullptr, the tap numerators are written there ([4][CS]).
+template <int CS, int CT>
+__device__ __forceinline__ void gather_f32(const DevModel& m, float u, float v, float t, float (&x)[CS + CT],
+                                           int32_t* p35) {
+  int x0, x1, y0, y1;
+  float fx, fy;
+  axis_setup(u, m.feat_w, m.address_mode, x0, x1, fx);
+  axis_setup(v, m.feat_h, m.address_mode, y0, y1, fy);
+  const int tx[4] = {x0, x1, x0, x1};
+  const int ty[4] = {y0, y0, y1, y1};
+  const uint2* line[4];
+  uint32_t shift[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    line[q] = reinterpret_cast<const uint2*>(m.bc4) + ((size_t)(ty[q] >> 2) * m.bw + (tx[q] >> 2)) * CS;
+    shift[q] = 16u + 3u * (uint32_t)(((ty[q] & 3) << 2) | (tx[q] & 3));
+  }
+  const float gx = 1.0f - fx, gy = 1.0f - fy;
+#pragma unroll
+  for (int c = 0; c < CS; ++c) {
+    float f[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint2 b = __ldg(line[q] + c);
+      const int p = bc4_p35(b.x, b.y, shift[q]);
+      if (p35) p35[q * CS + c] = p;
+      f[q] = p35_value(p);
+    }
+    x[c] = gy * (gx * f[0] + fx * f[1]) + fy * (gx * f[2] + fx * f[3]);
+  }
+  int j0, j1;
+  float a;
+  temporal_setup(t, m.t_count, j0, j1, a);
+  const float ga = 1.0f - a;
+#pragma unroll
+  for (int c = 0; c < CT; ++c) {
+    const float k0 = load_temporal(m.temporal, m.temporal_f16, j0 * CT + c);
+    const float k1 = load_temporal(m.temporal, m.temporal_f16, j1 * CT + c);
+    x[CS + c] = ga * k0 + a * k1;
+  }
+}
+
+}  // namespace ndgi

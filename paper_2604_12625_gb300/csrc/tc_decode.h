@@ -8,8 +8,9 @@ namespace ndgi {
 
 // Launch shape of the persistent page-decode kernel (picked by the autotuner).
 struct TcPagesShape {
-  int ctas_per_sm;    // resident CTAs per SM in the persistent grid
-  int tile_w;         // texel tile: tile_w x (128 / tile_w) texels per MMA tile
+  int ctas_per_sm;     // resident CTAs per SM in the persistent grid (<= 4)
+  int tile_w;          // texel tile: tile_w x (128 / tile_w) texels per MMA tile
+  int tiles_per_item;  // tiles of one request per work item (1..128)
 };
 
 bool tc_supported(int cs, int ct, int hidden);
@@ -20,6 +21,8 @@ cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const
 cudaError_t launch_tc_pages(const PagesCtx& c, bool bf16, int cs, int ct, int hidden, const TcPagesShape& shape,
                             const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s);
 TcPagesShape tc_default_pages_shape();
+// Reads and clears the tensor-core kernels' device error word (-1 if unreadable).
+int tc_take_error();
 std::vector<TcPagesShape> tc_pages_candidates(int sms);
 
 }  // namespace ndgi

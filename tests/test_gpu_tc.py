@@ -1,0 +1,137 @@
+"""GPU parity of the tensor-core (tcgen05) decode against the FP64 oracle.
+
+The oracle is evaluated on the parameters the decode stores (MLP weights and
+biases rounded once to FP16 or BF16).  FP16 is gated at max |err| / range <=
+2e-3; BF16 (8-bit significand, about 4e-3 per rounding) is reported and only
+sanity-gated at 2e-2.  Features are gathered exactly as in the FP32 path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import edge_queries, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GATE = {"fp16": 2e-3, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def ndgi():
+    import paper_2604_12625_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def decode(ndgi, m, q, prec):
+    model = ndgi.Model.from_arrays(m)
+    out = ndgi.ndgi_decode_points(model, torch.from_numpy(q).cuda(), prec).cpu().numpy()
+    ndgi.ndgi_check()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tc_small_points_config(ndgi, prec):
+    m, q = synth.small_points_config(1)
+    got = decode(ndgi, m, q, prec)
+    ref = oracle.decode_points(m, q, precision=prec)
+    err = rel_err(got, ref)
+    print(f"{prec} small config max|err|/range = {err:.3e}")
+    assert err <= GATE[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tc_2048_atlas_ragged(ndgi, prec):
+    m = synth.points_model_2048(2)
+    q = edge_queries(70_001, 21)
+    got = decode(ndgi, m, q, prec)
+    ref = oracle.decode_points(m, q, precision=prec)
+    err = rel_err(got, ref)
+    ref32 = oracle.decode_points(m, q, precision="fp32")
+    print(f"{prec}: vs stored weights {err:.3e}, vs FP32 master {rel_err(got, ref32):.3e}")
+    assert err <= GATE[prec]
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 32), (16, 8, 16), (16, 16, 64), (4, 4, 16), (8, 8, 16), (16, 8, 32)])
+def test_tc_shapes(ndgi, shape):
+    cs, ct, H = shape
+    m = synth.model(31, 512, 512, 128, 128, cs, 12, ct, H, temporal_dtype="f32")
+    q = edge_queries(5000, 22)
+    got = decode(ndgi, m, q, "fp16")
+    assert rel_err(got, oracle.decode_points(m, q, precision="fp16")) <= GATE["fp16"]
+
+
+def test_tc_tiny_and_tail(ndgi):
+    m = synth.points_model_2048(2)
+    for n in (1, 127, 129, 1000):
+        q = synth.random_queries(40 + n, n)
+        got = decode(ndgi, m, q, "fp16")
+        ref = oracle.decode_points(m, q, precision="fp16")
+        assert np.abs(got - ref).max() <= 2e-3 * 4.0   # range of this model's outputs is > 4
+
+
+def test_tc_full_size_sampled(ndgi):
+    m = synth.points_model_2048(2)
+    q = synth.random_queries(2, 1 << 24)
+    got = decode(ndgi, m, q, "fp16")
+    idx = np.random.default_rng(1).choice(q.shape[0], 1 << 15, replace=False)
+    ref = oracle.decode_points(m, q[idx], precision="fp16")
+    assert rel_err(got[idx], ref) <= GATE["fp16"]
+    assert np.all(np.isfinite(got))
+
+
+def test_tc_deterministic(ndgi):
+    m = synth.points_model_2048(2)
+    q = synth.random_queries(5, 100_000)
+    assert np.array_equal(decode(ndgi, m, q, "fp16"), decode(ndgi, m, q, "fp16"))
+
+
+SIZES = (256, 256, 512, 1024)
+
+
+def page_err(phys, ref, reqs):
+    worst = 0.0
+    for r in reqs:
+        sl = (slice(r["dst_y"], r["dst_y"] + r["h"]), slice(r["dst_x"], r["dst_x"] + r["w"]))
+        a, b = phys[sl][..., :3].astype(np.float64), ref[sl][..., :3]
+        worst = max(worst, float(np.abs(a - b).max() / max(b.max() - b.min(), 1e-6)))
+    return worst
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tc_pages_ragged_and_zipf(ndgi, prec):
+    maps = synth.page_models(41, sizes=SIZES, temporal_dtype="f16")
+    models = [ndgi.Model.from_arrays(m) for m in maps]
+    phys = torch.full((1024, 1024, 4), float("nan"), dtype=torch.float32, device="cuda")
+    plan = ndgi.PagesPlan(models, prec, 4096, phys)
+    for reqs in (synth.ragged_page_requests(5, SIZES, 40, slots_x=8, slot=128),
+                 synth.zipf_page_requests(6, SIZES, 64, page=128, slots_x=8)):
+        phys.fill_(float("nan"))
+        r, n = ndgi.page_requests_to_device(reqs)
+        plan.decode(r, n)
+        st, err = plan.check()
+        assert st == 0 and err == 0
+        ndgi.ndgi_check()
+        ref = oracle.decode_pages(maps, reqs, 1024, 1024, precision=prec)
+        got = phys.cpu().numpy()
+        assert page_err(got, ref, reqs) <= GATE[prec]
+        assert np.all(np.isnan(got[..., 0][np.isnan(ref[..., 0])]))
+    plan.close()
+
+
+def test_tc_pages_autotune_and_rgba16f(ndgi):
+    maps = synth.page_models(42, sizes=SIZES, temporal_dtype="f16")
+    models = [ndgi.Model.from_arrays(m) for m in maps]
+    phys = torch.zeros((1024, 1024, 4), dtype=torch.float16, device="cuda")
+    plan = ndgi.PagesPlan(models, "fp16", 64, phys)
+    reqs = synth.zipf_page_requests(7, SIZES, 64, page=128, slots_x=8)
+    r, n = ndgi.page_requests_to_device(reqs)
+    plan.autotune(r, n, len(reqs))
+    phys.zero_()
+    plan.decode(r, n)
+    ndgi.ndgi_check()
+    ref = oracle.decode_pages(maps, reqs, 1024, 1024, precision="fp16")
+    assert page_err(phys.float().cpu().numpy(), ref, reqs) <= 2e-3 + 2.0 ** -11 * 4
+    plan.close()
