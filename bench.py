@@ -156,6 +156,57 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+PAGE_FLOP_PER_TEXEL = 2 * (16 * 64 + 64 * 64 + 64 * 3)   # 10,624: temporal term folded per page
+PAGES_WORKLOAD = ("pages: 8 lightmaps (2x 512^2, 1024^2, 2048^2, 4096^2), BC4 half-res x16, temporal 24x8 fp16, "
+                  "MLP 24-64-64-3; 4096 Zipf(1.1) requests of 128^2 per frame, own t each; RGBA16F 8192^2 texture")
+
+
+def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True):
+    """Virtual-texture page decode: one step = one frame of 4096 page requests."""
+    maps = synth.page_models(4)
+    models = [ndgi.Model.from_arrays(m) for m in maps]
+    reqs = synth.zipf_page_requests(4, synth.PAGE_LIGHTMAP_SIZES, 4096, page=128, slots_x=64)
+    r_dev, n_dev = ndgi.page_requests_to_device(reqs)
+    phys = torch.empty((8192, 8192, 4), dtype=torch.float16, device="cuda")
+    texels = int(len(reqs)) * 128 * 128
+    out = {}
+    for prec in ("fp16", "fp32"):
+        plan = ndgi.PagesPlan(models, prec, len(reqs), phys)
+        plan.autotune(r_dev, n_dev, len(reqs))
+        steps = args.steps if prec == "fp16" else max(3, min(args.steps, 10))
+        ms, clocks = timed(lambda: plan.decode(r_dev, n_dev), steps, args.warmup, sample_clocks=(prec == "fp16"))
+        st, err_word = plan.check()
+        entry = {"value": texels / (ms / steps * 1e-3) / 1e9, "unit": "Gtexels/s", "ms_per_frame": ms / steps,
+                 "device_error_word": err_word}
+        if prec == "fp16":
+            entry["clocks"] = clocks
+        if check_err and rank == 0:
+            import oracle
+            pick = np.random.default_rng(5).choice(len(reqs), 12, replace=False)
+            sub = reqs[pick]
+            got = phys.float().cpu().numpy()
+            ref = oracle.decode_pages(maps, sub, 8192, 8192, precision="fp16" if prec == "fp16" else "fp32",
+                                      fill=0.0)
+            worst = 0.0
+            for q in sub:
+                sl = (slice(q["dst_y"], q["dst_y"] + 128), slice(q["dst_x"], q["dst_x"] + 128))
+                a, b = got[sl][..., :3].astype(np.float64), ref[sl][..., :3]
+                worst = max(worst, float(np.abs(a - b).max() / (b.max() - b.min())))
+            entry["max_err_over_page_range"] = worst
+            entry["err_sample"] = "12 seeded requests, per-page range; RGBA16F storage rounding included"
+        out[prec] = entry
+        plan.close()
+    kernel_s = out["fp16"]["ms_per_frame"] * 1e-3
+    achieved = texels * PAGE_FLOP_PER_TEXEL / kernel_s / 1e12
+    out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                       "frac": achieved / peaks["bf16_tflops"], "traffic": None, "kernel": "k_pages_tc",
+                       "peak_source": f"{peak_kind} bf16 burst (fp16 has the same dense rate)",
+                       "flop_per_texel": PAGE_FLOP_PER_TEXEL}
+    out["workload"] = PAGES_WORKLOAD
+    out["texels_per_frame"] = texels
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,6 +215,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp16", "bf16", "fp32"])
+    ap.add_argument("--no-pages", action="store_true", help="skip the page-decode measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -265,6 +317,10 @@ def main():
     ms_e2e, _ = timed(step_e2e, ke, 3)
     e2e_val = world * N_QUERIES / (ms_e2e / ke * 1e-3) / 1e9
 
+    pages = None
+    if not args.no_pages:
+        pages = bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -303,6 +359,7 @@ def main():
         "e2e": {"value": e2e_val, "unit": "Gtexels/s", "h2d_bytes_per_step": N_QUERIES * 12,
                 "d2h_bytes_per_step": N_QUERIES * 12},
         "gpu_launches": args.steps, "clocks": clocks,
+        "pages": pages,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -256,8 +256,8 @@ ndgi_status ndgi_pages_plan_create(const ndgi_model_desc* models, const void* co
         return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_create: model %d has no prepared workspace", i);
     }
   }
-  if (precision != NDGI_FP32 && !tc_supported(models[0].cs, models[0].ct, models[0].hidden))
-    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_pages_plan_create: tensor-core shape not built");
+  if (precision != NDGI_FP32 && !tc_pages_supported(models[0].cs, models[0].ct, models[0].hidden))
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_pages_plan_create: tensor-core page shape not built (cs must be 16)");
 
   ndgi_pages_plan* p = new (std::nothrow) ndgi_pages_plan();
   if (!p) return set_error(NDGI_ERR_OOM, "ndgi_pages_plan_create: host allocation failed");

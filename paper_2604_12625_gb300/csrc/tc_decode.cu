@@ -1,19 +1,33 @@
-// Tensor-core decode: the MLP of the decoder on tcgen05 (FP16 or BF16
-// operands, FP32 accumulation in tensor memory).
+// Tensor-core decode: the decoder MLP on tcgen05 (FP16 or BF16 operands,
+// FP32 accumulation in tensor memory), for random points and for batched
+// virtual-texture pages.
 //
-// A CTA of 128 threads owns one 128-row MMA tile at a time: thread r gathers
-// the features of query (or page texel) r in FP32 exactly as the CUDA-core
-// decode does, rounds them to FP16/BF16 and writes row r of the A tile in
-// shared memory.  One thread then issues the layer-1 MMAs
-//   D1[128 x H] = [x, 1, 0...] [128 x K1]  *  [W1; b1; 0]^T       (bias folded into K padding)
-// and commits them to an mbarrier; every thread reads its row of D1 from
-// tensor memory, applies ReLU, rounds and writes row r of the next A tile;
-// layer 2 (D2 = H1 W2, bias added in FP32 in the epilogue) and the output
-// layer (N padded from 3 to 16) follow the same pattern.  Several CTAs are
-// resident per SM, so the gathers and epilogues of one CTA overlap the MMAs
-// of the others.  Every mbarrier wait is bounded; a timeout is latched in a
-// device error word that ndgi_check reports, and the CTA unwinds and frees
-// its tensor memory.
+// Structure.  A CTA holds NWG independent "lanes" (warpgroups of 4 warps).
+// A lane owns one 128-row MMA tile at a time: its 128 threads write the
+// tile's features (one row each) into a K-major shared-memory A tile, one
+// thread issues the layer's tcgen05.mma chain into the lane's 64 tensor-
+// memory columns and commits to the lane's mbarrier, and the 128 threads read
+// their rows back (tcgen05.ld), apply ReLU with the FP16/BF16 conversion in
+// one instruction, and write the next layer's A tile.  The MLP weights are
+// shared by the lanes; the lanes of a CTA interleave, so one lane's gather
+// and epilogues overlap the others' MMAs.
+//
+// Biases never touch the CUDA cores: before a layer's MMAs the issuing
+// thread copies a 32-row broadcast image of the bias from shared memory into
+// all 128 accumulator lanes (tcgen05.cp 32x128b.warpx4) and the MMAs
+// accumulate onto it.  For points, layer 1 still carries b1 in the K padding
+// (24 inputs pad to 32 anyway).  For pages, t is constant per request, so the
+// temporal part of layer 1 is folded into a per-request bias
+// b1' = b1 + W1_t v_t (FP32) and layer 1 only contracts the 16 spatial
+// channels (K = 16).
+//
+// Page features: a lane decodes each BC4 feature row of its page quadrant
+// once (exact integer palette numerator, scaled once in FP32, stored as FP16)
+// into a ring of 8 rows in shared memory and blends the four taps of each
+// texel with packed half2 arithmetic from there.
+//
+// Every mbarrier wait is bounded; a timeout is latched in a device error word
+// that ndgi_check reports, and the CTA unwinds and frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -28,27 +42,34 @@ namespace ndgi {
 // Device error word of the tensor-core kernels (bit 0: an mbarrier wait timed out).
 static __device__ int g_tc_error;
 
-constexpr int kTcThreads = 128;
-constexpr int kTcMinSmem = 48 * 1024;   // caps residency at 4 CTAs/SM, so 4 x TMEM allocation <= 512 columns
+constexpr int kLaneThreads = 128;
+constexpr int kRingRows = 8;      // decoded feature rows kept per lane (page path)
+constexpr int kRingCols = 40;     // feature columns per ring row
+constexpr int kQuad = 64;         // page quadrant side (texels)
 
+// ---------------------------------------------------------------------------
+// Weight image (built by ndgi_prepare), identical layout in global and shared
+// memory so a CTA copies it with 16-byte loads.
+// ---------------------------------------------------------------------------
 template <int CS, int CT, int H>
 struct TcLayout {
   static constexpr int CIN = CS + CT;
-  static constexpr int K1 = ((CIN + 1 + 15) / 16) * 16;   // inputs + ones column, padded to the MMA K step
-  static constexpr int N3 = 16;                           // output layer N (3 used)
-  static constexpr uint32_t kB1 = 0;                      // [H][K1]
-  static constexpr uint32_t kB2 = kB1 + H * K1 * 2;       // [H][H]
-  static constexpr uint32_t kB3 = kB2 + H * H * 2;        // [16][H]
-  static constexpr uint32_t kBias2 = kB3 + N3 * H * 2;    // H floats
-  static constexpr uint32_t kBias3 = kBias2 + H * 4;      // 4 floats
-  static constexpr uint32_t kWsBytes = kBias3 + 16;
-  static constexpr uint32_t kA1 = (kWsBytes + 127) / 128 * 128;
-  static constexpr uint32_t kA2 = kA1 + 128 * K1 * 2;
-  static constexpr uint32_t kUsed = kA2 + 128 * H * 2;
-  static constexpr uint32_t kSmem = kUsed > (uint32_t)kTcMinSmem ? kUsed : (uint32_t)kTcMinSmem;
-  static constexpr uint32_t kTmemCols = 2 * H <= 32 ? 32 : (2 * H <= 64 ? 64 : (2 * H <= 128 ? 128 : 256));
+  static constexpr int K1P = ((CIN + 1 + 15) / 16) * 16;   // points: inputs + ones column, padded
+  static constexpr int K1G = ((CS + 15) / 16) * 16;        // pages: spatial channels only
+  static constexpr int N3 = 16;                            // output layer N (3 used)
+  static constexpr uint32_t kB2 = 0;                       // [H][H]      K-major
+  static constexpr uint32_t kB3 = kB2 + H * H * 2;         // [16][H]     rows 3..15 zero
+  static constexpr uint32_t kB2Src = kB3 + N3 * H * 2;     // [H/4][32][4] f32 bias-2 broadcast image
+  static constexpr uint32_t kB3Src = kB2Src + H * 32 * 4;  // [1][32][4]   f32 bias-3 broadcast image
+  static constexpr uint32_t kShared = kB3Src + 32 * 4 * 4; // end of the part both kernels use
+  static constexpr uint32_t kB1P = kShared;                // [H][K1P]    points layer 1 (+ b1 row)
+  static constexpr uint32_t kB1G = kB1P + H * K1P * 2;     // [H][K1G]    pages layer 1 (spatial)
+  static constexpr uint32_t kW1T = kB1G + H * K1G * 2;     // [CT][H] f32 stored temporal weights
+  static constexpr uint32_t kB1 = kW1T + CT * H * 4;       // [H] f32 stored b1
+  static constexpr uint32_t kWsBytes = kB1 + H * 4;
+  static constexpr uint32_t kTmemCols = H <= 32 ? 32 : (H <= 64 ? 64 : 128);
   static_assert(H % 16 == 0 && H <= 128, "hidden width must be a multiple of 16, at most 128");
-  static_assert(kWsBytes % 16 == 0, "weight image must be 16-byte granular");
+  static_assert(kShared % 16 == 0 && kB1G % 16 == 0 && kW1T % 16 == 0, "16-byte granular image");
 };
 
 template <bool BF16>
@@ -67,48 +88,276 @@ __device__ __forceinline__ float round_stored(float x) {
   return __half2float(__float2half_rn(x));
 }
 
-// Two floats -> packed pair (first value in the low half).
+// Two floats -> packed pair, `lo` in the low half.
 template <bool BF16>
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
-  return (uint32_t)to_bits<BF16>(a) | ((uint32_t)to_bits<BF16>(b) << 16);
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  uint32_t d;
+  if (BF16) asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  else asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// Same with ReLU fused into the conversion.
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
+  uint32_t d;
+  if (BF16) asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  else asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 
-// ---------------------------------------------------------------------------
-// Weight image: the shared-memory operand tiles, built once per model.
-// ---------------------------------------------------------------------------
 template <int CS, int CT, int H, bool BF16>
 __global__ void k_tc_prepare(DevModel m, unsigned char* __restrict__ ws) {
   using L = TcLayout<CS, CT, H>;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-  for (int i = tid; i < H * L::K1; i += nt) {      // B1[n][k] = W1[k][n], row CIN = b1
-    const int n = i / L::K1, k = i % L::K1;
-    const float v = k < L::CIN ? m.w1[k * H + n] : (k == L::CIN ? m.b1[n] : 0.0f);
-    *reinterpret_cast<uint16_t*>(ws + L::kB1 + kmajor_offset(n, k, L::K1)) = to_bits<BF16>(v);
-  }
   for (int i = tid; i < H * H; i += nt) {          // B2[n][k] = W2[k][n]
     const int n = i / H, k = i % H;
     *reinterpret_cast<uint16_t*>(ws + L::kB2 + kmajor_offset(n, k, H)) = to_bits<BF16>(m.w2[k * H + n]);
   }
-  for (int i = tid; i < L::N3 * H; i += nt) {      // B3[n][k] = W3[k][n], rows 3..15 zero
+  for (int i = tid; i < L::N3 * H; i += nt) {      // B3[n][k] = W3[k][n]
     const int n = i / H, k = i % H;
-    const float v = n < 3 ? m.w3[k * 3 + n] : 0.0f;
-    *reinterpret_cast<uint16_t*>(ws + L::kB3 + kmajor_offset(n, k, H)) = to_bits<BF16>(v);
+    *reinterpret_cast<uint16_t*>(ws + L::kB3 + kmajor_offset(n, k, H)) =
+        to_bits<BF16>(n < 3 ? m.w3[k * 3 + n] : 0.0f);
   }
-  for (int i = tid; i < H; i += nt) reinterpret_cast<float*>(ws + L::kBias2)[i] = round_stored<BF16>(m.b2[i]);
-  if (tid < 4) reinterpret_cast<float*>(ws + L::kBias3)[tid] = tid < 3 ? round_stored<BF16>(m.b3[tid]) : 0.0f;
+  for (int i = tid; i < H * 32; i += nt) {         // bias-2 broadcast image: chunk j = n/4, row r, element n%4
+    const int n = i % H, r = i / H;
+    reinterpret_cast<float*>(ws + L::kB2Src)[((n >> 2) * 32 + r) * 4 + (n & 3)] = round_stored<BF16>(m.b2[n]);
+  }
+  for (int i = tid; i < 32 * 4; i += nt) {
+    const int e = i & 3;
+    reinterpret_cast<float*>(ws + L::kB3Src)[i] = e < 3 ? round_stored<BF16>(m.b3[e]) : 0.0f;
+  }
+  for (int i = tid; i < H * L::K1P; i += nt) {     // points: B1[n][k] = W1[k][n], row CIN = b1
+    const int n = i / L::K1P, k = i % L::K1P;
+    const float v = k < L::CIN ? m.w1[k * H + n] : (k == L::CIN ? m.b1[n] : 0.0f);
+    *reinterpret_cast<uint16_t*>(ws + L::kB1P + kmajor_offset(n, k, L::K1P)) = to_bits<BF16>(v);
+  }
+  for (int i = tid; i < H * L::K1G; i += nt) {     // pages: spatial rows of W1 only
+    const int n = i / L::K1G, k = i % L::K1G;
+    *reinterpret_cast<uint16_t*>(ws + L::kB1G + kmajor_offset(n, k, L::K1G)) =
+        to_bits<BF16>(k < CS ? m.w1[k * H + n] : 0.0f);
+  }
+  for (int i = tid; i < CT * H; i += nt)
+    reinterpret_cast<float*>(ws + L::kW1T)[i] = round_stored<BF16>(m.w1[(CS + i / H) * H + i % H]);
+  for (int i = tid; i < H; i += nt) reinterpret_cast<float*>(ws + L::kB1)[i] = round_stored<BF16>(m.b1[i]);
 }
 
 // ---------------------------------------------------------------------------
-// Shared pieces of the tile pipeline
+// tcgen05 helpers specific to this file
 // ---------------------------------------------------------------------------
-template <int CS, int CT, int H, bool BF16>
-struct TcTile {
-  using L = TcLayout<CS, CT, H>;
+// Broadcast copy of a 32-row x 4-column FP32 image into all 128 lanes.
+__device__ __forceinline__ void tmem_cp_bcast4(uint32_t taddr, uint32_t src_smem) {
+  asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc(src_smem, 0, 128))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+// Barrier over the 128 threads of lane `wg` (ids 1.. ; 0 is __syncthreads).
+__device__ __forceinline__ void lane_sync(int wg) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + wg), "r"(kLaneThreads) : "memory");
+}
+// Lane barrier that also returns whether any of the lane's threads passed v = true.
+__device__ __forceinline__ bool lane_any(int wg, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(1 + wg), "r"(kLaneThreads)
+      : "memory");
+  return r != 0;
+}
+constexpr uint32_t tmem_alloc_cols(int cols) {
+  return cols <= 32 ? 32u : (cols <= 64 ? 64u : (cols <= 128 ? 128u : (cols <= 256 ? 256u : 512u)));
+}
 
-  // Row `row` of the layer-1 A tile from the FP32 features (ones column for the bias).
-  static __device__ __forceinline__ void write_a1(unsigned char* sm, int row, const float (&x)[L::CIN]) {
+// ---------------------------------------------------------------------------
+// One lane's MLP over a 128-row tile whose A1 is in shared memory.
+// ---------------------------------------------------------------------------
+template <int H, bool BF16>
+struct Lane {
+  uint32_t tmem;         // this lane's 64 accumulator columns (lane 0)
+  uint64_t* bar;
+  uint32_t phase;
+  int wg, t;             // lane index, thread index within the lane
+  unsigned char* a1;     // A tiles of this lane
+  unsigned char* a2;
+
+  // Issue (one thread): bias images then `K/16` MMAs, then commit.
+  __device__ __forceinline__ void issue(uint32_t bias_src, int bias_chunks, uint32_t a_smem, uint32_t b_smem, int K,
+                                        int N) {
+    tc_fence_after();
+    for (int j = 0; j < bias_chunks; ++j) tmem_cp_bcast4(tmem + 4u * j, bias_src + 512u * j);
+    const uint32_t sbo = (uint32_t)K * 16u, id = idesc_f16(128, N, BF16);
+    for (int ks = 0; ks < K / 16; ++ks)
+      umma_f16(tmem, sdesc(a_smem + 256u * ks, 128u, sbo), sdesc(b_smem + 256u * ks, 128u, sbo), id,
+               (bias_chunks > 0 || ks > 0) ? 1u : 0u);
+    umma_commit(bar);
+  }
+
+  // Publish generic-proxy smem writes and reach the lane barrier.
+  __device__ __forceinline__ void publish() {
+    fence_async_smem();
+    tc_fence_before();
+    lane_sync(wg);
+  }
+
+  // Wait for the committed MMAs; false (uniform over the lane) on timeout, in
+  // which case `phase` keeps the parity still outstanding so the teardown can
+  // drain it.
+  __device__ __forceinline__ bool wait() {
+    const bool ok = mbar_wait(bar, phase);
+    if (lane_any(wg, !ok)) return false;
+    phase ^= 1u;
+    tc_fence_after();
+    return true;
+  }
+
+  // This thread's row of D (H columns) -> ReLU -> FP16/BF16 -> row t of A2.
+  __device__ __forceinline__ void store_chunk(const uint32_t (&r)[16], int c16) {
 #pragma unroll
-    for (int c = 0; c < L::K1 / 8; ++c) {
+    for (int h = 0; h < 2; ++h) {
+      const int o = 8 * h;
+      uint4 p;
+      p.x = pack2_relu<BF16>(__uint_as_float(r[o + 0]), __uint_as_float(r[o + 1]));
+      p.y = pack2_relu<BF16>(__uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
+      p.z = pack2_relu<BF16>(__uint_as_float(r[o + 4]), __uint_as_float(r[o + 5]));
+      p.w = pack2_relu<BF16>(__uint_as_float(r[o + 6]), __uint_as_float(r[o + 7]));
+      *reinterpret_cast<uint4*>(a2 + kmajor_offset(t, 16 * c16 + o, H)) = p;
+    }
+  }
+  __device__ __forceinline__ void hidden_epilogue() {
+    const uint32_t row = tmem + ((uint32_t)((t >> 5) * 32) << 16);
+#pragma unroll
+    for (int c = 0; c < H / 16; c += 2) {
+      uint32_t r0[16], r1[16];
+      tmem_ld16(row + 16u * c, r0);
+      if (c + 1 < H / 16) tmem_ld16(row + 16u * (c + 1), r1);
+      tmem_ld_wait();
+      store_chunk(r0, c);
+      if (c + 1 < H / 16) store_chunk(r1, c + 1);
+    }
+  }
+
+  // Layers 1..3 after A1 is written; y = this thread's RGB.  false on timeout.
+  __device__ __forceinline__ bool run(uint32_t b1_smem, int K1, uint32_t b1src, int b1_chunks, uint32_t b2_smem,
+                                      uint32_t b2src, uint32_t b3_smem, uint32_t b3src, float& y0, float& y1,
+                                      float& y2) {
+    publish();
+    if (t == 0) issue(b1src, b1_chunks, smem_addr(a1), b1_smem, K1, H);
+    if (!wait()) return false;
+    hidden_epilogue();
+    publish();
+    if (t == 0) issue(b2src, H / 4, smem_addr(a2), b2_smem, H, H);
+    if (!wait()) return false;
+    hidden_epilogue();
+    publish();
+    if (t == 0) issue(b3src, 1, smem_addr(a2), b3_smem, H, 16);
+    if (!wait()) return false;
+    uint32_t r[4];
+    tmem_ld4(tmem + ((uint32_t)((t >> 5) * 32) << 16), r);
+    tmem_ld_wait();
+    y0 = __uint_as_float(r[0]);
+    y1 = __uint_as_float(r[1]);
+    y2 = __uint_as_float(r[2]);
+    tc_fence_before();
+    return true;
+  }
+};
+
+// CTA set-up: TMEM for all lanes, one mbarrier per lane.
+template <int NWG, int COLS>
+__device__ __forceinline__ uint32_t cta_setup(uint64_t* bars, uint32_t* slot, int tid) {
+  if ((tid >> 5) == 0) {
+    tmem_alloc(slot, tmem_alloc_cols(NWG * COLS));
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < NWG; ++i) mbar_init(&bars[i], 1);
+    mbar_fence_init();
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *slot;
+}
+
+// CTA end.  A lane whose wait timed out latches the error word and waits
+// (bounded) for its MMAs still in flight before the tensor memory is freed.
+template <int NWG, int COLS>
+__device__ __forceinline__ void cta_teardown(uint32_t tmem, uint64_t* bar, uint32_t phase, bool lane_timed_out,
+                                             int tid) {
+  if (lane_timed_out) {
+    if ((tid & (kLaneThreads - 1)) == 0) atomicOr(&g_tc_error, 1);
+    mbar_wait(bar, phase);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if ((tid >> 5) == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, tmem_alloc_cols(NWG * COLS));
+  }
+}
+
+__device__ __forceinline__ void copy16(unsigned char* dst, const unsigned char* src, uint32_t bytes, int tid,
+                                       int nthreads) {
+  for (uint32_t i = tid * 16; i < bytes; i += nthreads * 16)
+    *reinterpret_cast<uint4*>(dst + i) = *reinterpret_cast<const uint4*>(src + i);
+}
+
+// ---------------------------------------------------------------------------
+// Random-access points
+// ---------------------------------------------------------------------------
+template <int CS, int CT, int H, int NWG>
+struct PointsSmem {
+  using L = TcLayout<CS, CT, H>;
+  static constexpr uint32_t kW = 0;                                  // shared part of the image
+  static constexpr uint32_t kB1 = kW + L::kShared;                   // points B1
+  static constexpr uint32_t kLanes = (kB1 + H * L::K1P * 2 + 127) / 128 * 128;
+  static constexpr uint32_t kA1 = 0, kA2 = 128 * L::K1P * 2, kLaneBytes = kA2 + 128 * H * 2;
+  static constexpr uint32_t kBytes = kLanes + NWG * kLaneBytes;
+};
+
+template <int CS, int CT, int H, bool BF16, int NWG>
+__global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, const unsigned char* __restrict__ ws,
+                                                                    const float* __restrict__ uvt, int64_t n,
+                                                                    float* __restrict__ rgb) {
+  using L = TcLayout<CS, CT, H>;
+  using S = PointsSmem<CS, CT, H, NWG>;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t bars[NWG];
+  __shared__ uint32_t slot;
+  const int tid = threadIdx.x, wg = tid >> 7;
+  copy16(sm + S::kW, ws, L::kShared, tid, kLaneThreads * NWG);
+  copy16(sm + S::kB1, ws + L::kB1P, H * L::K1P * 2, tid, kLaneThreads * NWG);
+  const uint32_t tbase = cta_setup<NWG, L::kTmemCols>(bars, &slot, tid);
+  Lane<H, BF16> lane;
+  lane.tmem = tbase + (uint32_t)(wg * L::kTmemCols);
+  lane.bar = &bars[wg];
+  lane.phase = 0;
+  lane.wg = wg;
+  lane.t = tid & (kLaneThreads - 1);
+  lane.a1 = sm + S::kLanes + wg * S::kLaneBytes + S::kA1;
+  lane.a2 = sm + S::kLanes + wg * S::kLaneBytes + S::kA2;
+  const uint32_t base = smem_addr(sm);
+  bool failed = false;
+  const int64_t tiles = (n + 127) / 128;
+  for (int64_t tile = (int64_t)blockIdx.x * NWG + wg; tile < tiles; tile += (int64_t)gridDim.x * NWG) {
+    const int64_t q = tile * 128 + lane.t;
+    float x[L::CIN];
+    if (q < n) {
+      gather_f32<CS, CT>(m, uvt[3 * q], uvt[3 * q + 1], uvt[3 * q + 2], x, nullptr);
+    } else {
+#pragma unroll
+      for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < L::K1P / 8; ++c) {
       float v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
@@ -120,159 +369,11 @@ struct TcTile {
       p.y = pack2<BF16>(v[2], v[3]);
       p.z = pack2<BF16>(v[4], v[5]);
       p.w = pack2<BF16>(v[6], v[7]);
-      *reinterpret_cast<uint4*>(sm + L::kA1 + kmajor_offset(row, 8 * c, L::K1)) = p;
+      *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(lane.t, 8 * c, L::K1P)) = p;
     }
-  }
-
-  // Issue one layer's MMAs (single thread) and commit to the barrier.
-  static __device__ __forceinline__ void mma_layer(uint32_t d_tmem, uint32_t a_smem, uint32_t b_smem, int K, int N,
-                                                   uint64_t* bar) {
-    tc_fence_after();
-    const uint32_t sbo = (uint32_t)K * 16u;
-    const uint32_t id = idesc_f16(128, N, BF16);
-    for (int ks = 0; ks < K / 16; ++ks)
-      umma_f16(d_tmem, sdesc(a_smem + 256u * ks, 128u, sbo), sdesc(b_smem + 256u * ks, 128u, sbo), id, ks > 0);
-    umma_commit(bar);
-  }
-
-  // Epilogue of a hidden layer: this thread's row of D (H columns) -> ReLU(D + bias) -> A2 row.
-  static __device__ __forceinline__ void hidden_epilogue(unsigned char* sm, uint32_t taddr, int row,
-                                                         const float* bias) {
-#pragma unroll
-    for (int c = 0; c < H / 16; ++c) {
-      uint32_t r[16];
-      tmem_ld16(taddr + 16u * c, r);
-      tmem_ld_wait();
-      float v[16];
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const float b = bias ? bias[16 * c + e] : 0.0f;
-        v[e] = fmaxf(__uint_as_float(r[e]) + b, 0.0f);
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        uint4 p;
-        p.x = pack2<BF16>(v[8 * h + 0], v[8 * h + 1]);
-        p.y = pack2<BF16>(v[8 * h + 2], v[8 * h + 3]);
-        p.z = pack2<BF16>(v[8 * h + 4], v[8 * h + 5]);
-        p.w = pack2<BF16>(v[8 * h + 6], v[8 * h + 7]);
-        *reinterpret_cast<uint4*>(sm + L::kA2 + kmajor_offset(row, 16 * c + 8 * h, H)) = p;
-      }
-    }
-  }
-
-  // Runs layers 1-3 on the A1 tile already in shared memory; y = this thread's RGB.
-  // Returns false if a barrier wait timed out (uniform across the CTA).
-  static __device__ __forceinline__ bool mlp(unsigned char* sm, uint32_t tmem, uint64_t* bar, uint32_t& phase,
-                                             int tid, float& y0, float& y1, float& y2) {
-    const uint32_t lane = (uint32_t)((tid >> 5) * 32) << 16;
-    const uint32_t base = smem_addr(sm);
-    const float* bias2 = reinterpret_cast<const float*>(sm + L::kBias2);
-    const float* bias3 = reinterpret_cast<const float*>(sm + L::kBias3);
-    // layer 1
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) mma_layer(tmem, base + L::kA1, base + L::kB1, L::K1, H, bar);
-    bool ok = mbar_wait(bar, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) return false;
-    tc_fence_after();
-    hidden_epilogue(sm, tmem + lane, tid, nullptr);
-    // layer 2
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) mma_layer(tmem + H, base + L::kA2, base + L::kB2, H, H, bar);
-    ok = mbar_wait(bar, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) return false;
-    tc_fence_after();
-    hidden_epilogue(sm, tmem + H + lane, tid, bias2);
-    // output layer (N = 16, columns 0..2 used), into the columns of D1
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) mma_layer(tmem, base + L::kA2, base + L::kB3, H, L::N3, bar);
-    ok = mbar_wait(bar, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) return false;
-    tc_fence_after();
-    uint32_t r[16];
-    tmem_ld16(tmem + lane, r);
-    tmem_ld_wait();
-    y0 = __uint_as_float(r[0]) + bias3[0];
-    y1 = __uint_as_float(r[1]) + bias3[1];
-    y2 = __uint_as_float(r[2]) + bias3[2];
-    tc_fence_before();
-    return true;
-  }
-
-  // CTA start: weight image -> smem, TMEM allocation, barrier init.
-  static __device__ __forceinline__ uint32_t setup(unsigned char* sm, const unsigned char* ws, uint64_t* bar,
-                                                   uint32_t* slot, int tid) {
-    for (uint32_t i = tid * 16; i < L::kWsBytes; i += kTcThreads * 16)
-      *reinterpret_cast<uint4*>(sm + i) = *reinterpret_cast<const uint4*>(ws + i);
-    if ((tid >> 5) == 0) {
-      tmem_alloc(slot, L::kTmemCols);
-      tmem_relinquish();
-    }
-    if (tid == 0) {
-      mbar_init(bar, 1);
-      mbar_fence_init();
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    return *slot;
-  }
-
-  // CTA end: after a timeout, wait (bounded) for the MMAs still in flight; free TMEM.
-  static __device__ __forceinline__ void teardown(uint32_t tmem, uint64_t* bar, uint32_t phase, bool failed,
-                                                  int tid) {
-    if (failed) {
-      if (tid == 0) atomicOr(&g_tc_error, 1);
-      mbar_wait(bar, phase);
-    }
-    tc_fence_before();
-    __syncthreads();
-    if ((tid >> 5) == 0) {
-      tc_fence_after();
-      tmem_dealloc(tmem, L::kTmemCols);
-    }
-  }
-};
-
-// ---------------------------------------------------------------------------
-// Random-access points
-// ---------------------------------------------------------------------------
-template <int CS, int CT, int H, bool BF16>
-__global__ void __launch_bounds__(kTcThreads, 4) k_points_tc(DevModel m, const unsigned char* __restrict__ ws,
-                                                             const float* __restrict__ uvt, int64_t n,
-                                                             float* __restrict__ rgb) {
-  using T = TcTile<CS, CT, H, BF16>;
-  using L = TcLayout<CS, CT, H>;
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint64_t bar;
-  __shared__ uint32_t slot;
-  const int tid = threadIdx.x;
-  const uint32_t tmem = T::setup(sm, ws, &bar, &slot, tid);
-  uint32_t phase = 0;
-  bool failed = false;
-  const int64_t tiles = (n + 127) / 128;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t q = tile * 128 + tid;
-    float x[L::CIN];
-    if (q < n) {
-      gather_f32<CS, CT>(m, uvt[3 * q], uvt[3 * q + 1], uvt[3 * q + 2], x, nullptr);
-    } else {
-#pragma unroll
-      for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
-    }
-    T::write_a1(sm, tid, x);
     float y0, y1, y2;
-    if (!T::mlp(sm, tmem, &bar, phase, tid, y0, y1, y2)) {
+    if (!lane.run(base + S::kB1, L::K1P, 0, 0, base + S::kW + L::kB2, base + S::kW + L::kB2Src,
+                  base + S::kW + L::kB3, base + S::kW + L::kB3Src, y0, y1, y2)) {
       failed = true;
       break;
     }
@@ -282,102 +383,258 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_points_tc(DevModel m, const u
       rgb[3 * q + 2] = y2;
     }
   }
-  T::teardown(tmem, &bar, phase, failed, tid);
+  cta_teardown<NWG, L::kTmemCols>(tbase, lane.bar, lane.phase, failed, tid);
 }
 
 // ---------------------------------------------------------------------------
-// Batched pages: persistent CTAs pull work items (request, group of tiles)
-// from an atomic counter; a tile is tile_w x (128 / tile_w) texels of the page.
+// Batched pages
 // ---------------------------------------------------------------------------
-template <int CS, int CT, int H, bool BF16>
-__global__ void __launch_bounds__(kTcThreads, 4) k_pages_tc(PagesCtx c, const ndgi_page_req* __restrict__ reqs,
-                                                            const int32_t* __restrict__ n_dev, int tile_w,
-                                                            int tiles_per_item) {
-  using T = TcTile<CS, CT, H, BF16>;
+template <int CS, int CT, int H, int NWG>
+struct PagesSmem {
   using L = TcLayout<CS, CT, H>;
+  static constexpr uint32_t kW = 0;
+  static constexpr uint32_t kB1 = kW + L::kShared;                      // pages B1 [H][K1G]
+  static constexpr uint32_t kW1T = kB1 + H * L::K1G * 2;                // [CT][H] f32
+  static constexpr uint32_t kBias1 = kW1T + CT * H * 4;                 // [H] f32 stored b1
+  static constexpr uint32_t kB1Src = (kBias1 + H * 4 + 127) / 128 * 128;   // folded b1' broadcast image
+  static constexpr uint32_t kLanes = kB1Src + H * 32 * 4;
+  // per lane
+  static constexpr uint32_t kA1 = 0;
+  static constexpr uint32_t kA2 = kA1 + 128 * L::K1G * 2;
+  static constexpr uint32_t kRing = kA2 + 128 * H * 2;                  // [8 rows][40 cols][CS] fp16
+  static constexpr uint32_t kRowTab = kRing + kRingRows * kRingCols * CS * 2;   // [64] int4
+  static constexpr uint32_t kLaneBytes = (kRowTab + kQuad * 16 + 127) / 128 * 128;
+  static constexpr uint32_t kBytes = kLanes + NWG * kLaneBytes;
+};
+
+// Per-CTA state shared by the lanes for the current request.
+struct PageItem {
+  ndgi_page_req r;
+  int valid;          // 1 decode, 0 skip
+  int staged;         // 1 ring path, 0 direct per-texel gather
+};
+
+// Decodes feature row `fr` (columns fc0 .. fc0+ncols-1) of channel pairs into ring slot fr & 7.
+template <int CS>
+__device__ __forceinline__ void decode_row(const DevModel& m, unsigned char* ring, int fr, int fc0, int ncols, int t) {
+  constexpr int CG = CS / 8;   // 8-channel groups
+  __half* slot = reinterpret_cast<__half*>(ring) + (size_t)(fr & (kRingRows - 1)) * kRingCols * CS;
+  const int by = fr >> 2, py = (fr & 3) << 2;
+  for (int u = t; u < ncols * CG; u += kLaneThreads) {
+    const int col = u / CG, g = u % CG;
+    const int fc = fc0 + col;
+    const uint32_t shift = 16u + 3u * (uint32_t)(py | (fc & 3));
+    const uint4* line = reinterpret_cast<const uint4*>(m.bc4 + (((size_t)by * m.bw + (fc >> 2)) * CS + 8 * g) * 8);
+    uint32_t h[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 b = __ldg(line + q);                 // two planes: (x, y) and (z, w)
+      const float f0 = p35_value(bc4_p35(b.x, b.y, shift));
+      const float f1 = p35_value(bc4_p35(b.z, b.w, shift));
+      h[q] = pack2<false>(f0, f1);
+    }
+    *reinterpret_cast<uint4*>(slot + (size_t)col * CS + 8 * g) = make_uint4(h[0], h[1], h[2], h[3]);
+  }
+}
+
+template <int CS, int CT, int H, bool BF16, int NWG>
+__global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, const ndgi_page_req* __restrict__ reqs,
+                                                                   const int32_t* __restrict__ n_dev) {
+  using L = TcLayout<CS, CT, H>;
+  using S = PagesSmem<CS, CT, H, NWG>;
+  static_assert(CS == 16, "the staged page path is built for 16 spatial channels");
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bars[NWG];
   __shared__ uint32_t slot;
   __shared__ int s_item;
-  const int tid = threadIdx.x;
+  __shared__ PageItem s_req;
+  __shared__ float s_vt[CT];
+  constexpr int NT = kLaneThreads * NWG;
+  const int tid = threadIdx.x, wg = tid >> 7, t = tid & (kLaneThreads - 1);
   int n = *n_dev;
   if (n > c.max_reqs || n < 0) {   // reject the whole frame: the request buffer may be shorter
     if (blockIdx.x == 0 && tid == 0) atomicOr(c.error_word, 1);
     n = 0;
   }
-  const int tile_h = 128 / tile_w;
-  const int items_per_req = (128 / tiles_per_item);     // 128 tiles cover the largest (128 x 128) page
-  const int64_t items = (int64_t)n * items_per_req;
-  // the first model's weights; reloaded when a work item's model differs
-  const uint32_t tmem = T::setup(sm, static_cast<const unsigned char*>(c.ws[0]), &bar, &slot, tid);
-  int loaded = 0;
-  uint32_t phase = 0;
-  bool failed = false;
+  const uint32_t tbase = cta_setup<NWG, L::kTmemCols>(bars, &slot, tid);
+  Lane<H, BF16> lane;
+  lane.tmem = tbase + (uint32_t)(wg * L::kTmemCols);
+  lane.bar = &bars[wg];
+  lane.phase = 0;
+  lane.wg = wg;
+  lane.t = t;
+  unsigned char* lb = sm + S::kLanes + wg * S::kLaneBytes;
+  lane.a1 = lb + S::kA1;
+  lane.a2 = lb + S::kA2;
+  unsigned char* ring = lb + S::kRing;
+  int4* rowtab = reinterpret_cast<int4*>(lb + S::kRowTab);
+  const uint32_t base = smem_addr(sm);
+  int loaded = -1;
+  bool failed = false;          // this lane timed out
   for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(c.work_counter, 1u);
+    // ---- CTA: next request (the barrier keeps thread 0 from overwriting the
+    // shared request slot while a skipped request is still being read) ----
     __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if ((int64_t)item >= items) break;
-    const ndgi_page_req r = reqs[item / items_per_req];
-    const bool valid = r.model >= 0 && r.model < c.n_models && r.w >= 1 && r.w <= 128 && r.h >= 1 && r.h <= 128;
-    const int first_tile = (item % items_per_req) * tiles_per_item;
-    if (!valid) {
-      if (first_tile == 0 && tid == 0) atomicOr(c.error_word, 2);
-      continue;
+    if (tid == 0) {
+      const int item = (int)atomicAdd(c.work_counter, 1u);
+      s_item = item;
+      if (item < n) {
+        const ndgi_page_req r = reqs[item];
+        s_req.r = r;
+        int ok = r.model >= 0 && r.model < c.n_models && r.w >= 1 && r.w <= 128 && r.h >= 1 && r.h <= 128;
+        if (!ok) atomicOr(c.error_word, 2);
+        if (ok) {
+          const DevModel& mm = c.models[r.model];
+          ok = r.x0 >= 0 && r.y0 >= 0 && (int64_t)r.x0 + r.w <= mm.lm_w && (int64_t)r.y0 + r.h <= mm.lm_h &&
+               r.dst_x >= 0 && r.dst_y >= 0 && (int64_t)r.dst_x + r.w <= c.phys_w &&
+               (int64_t)r.dst_y + r.h <= c.phys_h;
+          if (!ok) atomicOr(c.error_word, 4);
+          // ring path when features are at most half the lightmap resolution: a
+          // 64-texel quadrant side then spans <= 34 feature columns and 8 output
+          // rows span <= 6 feature rows
+          s_req.staged = 2 * mm.feat_w <= mm.lm_w && 2 * mm.feat_h <= mm.lm_h;
+        }
+        s_req.valid = ok;
+      }
     }
+    __syncthreads();
+    if (s_item >= n) break;
+    if (!s_req.valid) continue;
+    const ndgi_page_req r = s_req.r;
     const DevModel& m = c.models[r.model];
-    const bool inside = r.x0 >= 0 && r.y0 >= 0 && (int64_t)r.x0 + r.w <= m.lm_w && (int64_t)r.y0 + r.h <= m.lm_h &&
-                        r.dst_x >= 0 && r.dst_y >= 0 && (int64_t)r.dst_x + r.w <= c.phys_w &&
-                        (int64_t)r.dst_y + r.h <= c.phys_h;
-    if (!inside) {
-      if (first_tile == 0 && tid == 0) atomicOr(c.error_word, 4);
-      continue;
-    }
-    const int tiles_x = (r.w + tile_w - 1) / tile_w, tiles_y = (r.h + tile_h - 1) / tile_h;
-    const int tiles = tiles_x * tiles_y;
-    if (first_tile >= tiles) continue;
-    if (r.model != loaded) {        // block-uniform: swap in this model's weight image
+    if (r.model != loaded) {   // swap in this model's weights (no MMA is in flight here)
       const unsigned char* w = static_cast<const unsigned char*>(c.ws[r.model]);
-      for (uint32_t i = tid * 16; i < L::kWsBytes; i += kTcThreads * 16)
-        *reinterpret_cast<uint4*>(sm + i) = *reinterpret_cast<const uint4*>(w + i);
-      loaded = r.model;            // the next MLP's fence + barrier publishes it to the tensor core
+      copy16(sm + S::kW, w, L::kShared, tid, NT);
+      copy16(sm + S::kB1, w + L::kB1G, H * L::K1G * 2 + CT * H * 4 + H * 4, tid, NT);
+      loaded = r.model;
     }
-    const int last_tile = min(first_tile + tiles_per_item, tiles);
-    for (int t = first_tile; t < last_tile; ++t) {
-      const int i = (t % tiles_x) * tile_w + tid % tile_w;
-      const int j = (t / tiles_x) * tile_h + tid / tile_w;
-      const bool in = i < r.w && j < r.h;
-      float x[L::CIN];
-      if (in) {
-        const float u = ((float)(r.x0 + i) + 0.5f) / (float)m.lm_w;
-        const float v = ((float)(r.y0 + j) + 0.5f) / (float)m.lm_h;
-        gather_f32<CS, CT>(m, u, v, r.t, x, nullptr);
-      } else {
+    // temporal line at this request's t
+    if (tid < CT) {
+      int j0, j1;
+      float a;
+      temporal_setup(r.t, m.t_count, j0, j1, a);
+      s_vt[tid] = (1.0f - a) * load_temporal(m.temporal, m.temporal_f16, j0 * CT + tid) +
+                  a * load_temporal(m.temporal, m.temporal_f16, j1 * CT + tid);
+    }
+    __syncthreads();
+    // folded layer-1 bias b1' = b1 + W1_t v_t (FP32), as a 32-row broadcast image
+    for (int i = tid; i < H * 32; i += NT) {
+      const int nn = i % H, row = i / H;
+      const float* w1t = reinterpret_cast<const float*>(sm + S::kW1T);
+      float b = reinterpret_cast<const float*>(sm + S::kBias1)[nn];
 #pragma unroll
-        for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
+      for (int cc = 0; cc < CT; ++cc) b = fmaf(w1t[cc * H + nn], s_vt[cc], b);
+      reinterpret_cast<float*>(sm + S::kB1Src)[((nn >> 2) * 32 + row) * 4 + (nn & 3)] = b;
+    }
+    __syncthreads();
+    // ---- lane: one 64 x 64 quadrant of the request ----
+    for (int quad = wg; quad < 4 && !failed; quad += NWG) {
+      const int ox = (quad & 1) * kQuad, oy = (quad >> 1) * kQuad;
+      const int qw = min(kQuad, r.w - ox), qh = min(kQuad, r.h - oy);
+      if (qw <= 0 || qh <= 0) continue;
+      // column set-up (fixed per thread): texel column ox + (t % 64)
+      const int col = t & (kQuad - 1);
+      int cx0, cx1;
+      float fx;
+      axis_setup(((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w, m.feat_w, m.address_mode, cx0, cx1, fx);
+      // feature columns touched by the quadrant (taps of its first and last column)
+      int fa0, fa1, fb0, fb1;
+      float fdum;
+      axis_setup(((float)(r.x0 + ox) + 0.5f) / (float)m.lm_w, m.feat_w, m.address_mode, fa0, fa1, fdum);
+      axis_setup(((float)(r.x0 + ox + qw - 1) + 0.5f) / (float)m.lm_w, m.feat_w, m.address_mode, fb0, fb1, fdum);
+      const int fc0 = min(min(fa0, fa1), min(fb0, fb1));
+      const int ncols = max(max(fa0, fa1), max(fb0, fb1)) - fc0 + 1;
+      // row set-up table for the quadrant's rows
+      if (t < qh) {
+        int ry0, ry1;
+        float fy;
+        axis_setup(((float)(r.y0 + oy + t) + 0.5f) / (float)m.lm_h, m.feat_h, m.address_mode, ry0, ry1, fy);
+        rowtab[t] = make_int4(ry0, ry1, __float_as_int(fy), 0);
       }
-      T::write_a1(sm, tid, x);
-      float y0, y1, y2;
-      if (!T::mlp(sm, tmem, &bar, phase, tid, y0, y1, y2)) {
-        failed = true;
-        break;
-      }
-      if (in) {
-        const int64_t o = (int64_t)(r.dst_y + j) * c.phys_w + (r.dst_x + i);
-        if (c.out_format == NDGI_RGBA32F) {
-          reinterpret_cast<float4*>(c.phys)[o] = make_float4(y0, y1, y2, 1.0f);
-        } else {
-          uint2 p;
-          p.x = pack2<false>(y0, y1);
-          p.y = pack2<false>(y2, 1.0f);
-          reinterpret_cast<uint2*>(c.phys)[o] = p;
+      lane_sync(wg);
+      const bool staged = s_req.staged && ncols <= kRingCols;
+      const __half2 wx1 = __float2half2_rn(fx), wx0 = __float2half2_rn(1.0f - fx);
+      int decoded_hi = -1000000;   // highest feature row decoded into the ring
+      for (int row0 = 0; row0 < qh && !failed; row0 += 8) {
+        if (staged) {
+          // rows needed by output rows row0 .. row0+7 (monotone in the row)
+          const int need_lo = rowtab[row0].x, need_hi = rowtab[min(row0 + 7, qh - 1)].y;
+          const int from = max(decoded_hi + 1, need_lo);
+          for (int fr = from; fr <= need_hi; ++fr) decode_row<CS>(m, ring, fr, fc0, ncols, t);
+          decoded_hi = max(decoded_hi, need_hi);
+          lane_sync(wg);
+        }
+        for (int sub = 0; sub < 8 && row0 + sub < qh; sub += 2) {
+          const int orow = row0 + sub + (t >> 6);
+          const bool in = col < qw && orow < qh;
+          uint4 p0 = make_uint4(0, 0, 0, 0), p1 = p0;
+          if (in) {
+            const int4 rt = rowtab[orow];
+            if (staged) {
+              const float fy = __int_as_float(rt.z);
+              const __half2 wy1 = __float2half2_rn(fy), wy0 = __float2half2_rn(1.0f - fy);
+              const __half2 w00 = __hmul2(wx0, wy0), w10 = __hmul2(wx1, wy0), w01 = __hmul2(wx0, wy1),
+                            w11 = __hmul2(wx1, wy1);
+              const __half* rr = reinterpret_cast<const __half*>(ring);
+              const uint4* t00 = reinterpret_cast<const uint4*>(rr + ((size_t)(rt.x & 7) * kRingCols + (cx0 - fc0)) * CS);
+              const uint4* t10 = reinterpret_cast<const uint4*>(rr + ((size_t)(rt.x & 7) * kRingCols + (cx1 - fc0)) * CS);
+              const uint4* t01 = reinterpret_cast<const uint4*>(rr + ((size_t)(rt.y & 7) * kRingCols + (cx0 - fc0)) * CS);
+              const uint4* t11 = reinterpret_cast<const uint4*>(rr + ((size_t)(rt.y & 7) * kRingCols + (cx1 - fc0)) * CS);
+              uint32_t out[8];
+#pragma unroll
+              for (int g = 0; g < 2; ++g) {
+                const uint4 a = t00[g], b = t10[g], cq = t01[g], d = t11[g];
+                const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w},
+                               cv[4] = {cq.x, cq.y, cq.z, cq.w}, dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  __half2 v = __hmul2(w00, *reinterpret_cast<const __half2*>(&av[e]));
+                  v = __hfma2(w10, *reinterpret_cast<const __half2*>(&bv[e]), v);
+                  v = __hfma2(w01, *reinterpret_cast<const __half2*>(&cv[e]), v);
+                  v = __hfma2(w11, *reinterpret_cast<const __half2*>(&dv[e]), v);
+                  if (BF16) {
+                    const float2 f = __half22float2(v);
+                    out[4 * g + e] = pack2<true>(f.x, f.y);
+                  } else {
+                    out[4 * g + e] = *reinterpret_cast<const uint32_t*>(&v);
+                  }
+                }
+              }
+              p0 = make_uint4(out[0], out[1], out[2], out[3]);
+              p1 = make_uint4(out[4], out[5], out[6], out[7]);
+            } else {
+              float x[CS + CT];
+              gather_f32<CS, CT>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
+                                 ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr);
+              p0 = make_uint4(pack2<BF16>(x[0], x[1]), pack2<BF16>(x[2], x[3]), pack2<BF16>(x[4], x[5]),
+                              pack2<BF16>(x[6], x[7]));
+              p1 = make_uint4(pack2<BF16>(x[8], x[9]), pack2<BF16>(x[10], x[11]), pack2<BF16>(x[12], x[13]),
+                              pack2<BF16>(x[14], x[15]));
+            }
+          }
+          *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, 0, L::K1G)) = p0;
+          *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, 8, L::K1G)) = p1;
+          float y0, y1, y2;
+          if (!lane.run(base + S::kB1, L::K1G, base + S::kB1Src, H / 4, base + S::kW + L::kB2,
+                        base + S::kW + L::kB2Src, base + S::kW + L::kB3, base + S::kW + L::kB3Src, y0, y1, y2)) {
+            failed = true;
+            break;
+          }
+          if (in) {
+            const int64_t o = (int64_t)(r.dst_y + oy + orow) * c.phys_w + (r.dst_x + ox + col);
+            if (c.out_format == NDGI_RGBA32F) {
+              reinterpret_cast<float4*>(c.phys)[o] = make_float4(y0, y1, y2, 1.0f);
+            } else {
+              reinterpret_cast<uint2*>(c.phys)[o] = make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f));
+            }
+          }
         }
       }
     }
-    if (failed) break;
+    // every lane must be done with the weights and b1' before the next request
+    if (__syncthreads_or(failed)) break;
   }
-  T::teardown(tmem, &bar, phase, failed, tid);
+  cta_teardown<NWG, L::kTmemCols>(tbase, lane.bar, lane.phase, failed, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -399,6 +656,8 @@ bool tc_supported(int cs, int ct, int hidden) {
   return false;
 }
 
+bool tc_pages_supported(int cs, int ct, int hidden) { return tc_supported(cs, ct, hidden) && cs == 16; }
+
 size_t tc_workspace_bytes(int cs, int ct, int hidden) {
 #define X(A, B, C) if (cs == A && ct == B && hidden == C) return TcLayout<A, B, C>::kWsBytes;
   NDGI_TC_SHAPES(X)
@@ -409,8 +668,8 @@ size_t tc_workspace_bytes(int cs, int ct, int hidden) {
 cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream_t s) {
 #define X(A, B, C)                                                                                       \
   if (m.cs == A && m.ct == B && m.hidden == C) {                                                         \
-    if (bf16) k_tc_prepare<A, B, C, true><<<8, 256, 0, s>>>(m, static_cast<unsigned char*>(ws));        \
-    else k_tc_prepare<A, B, C, false><<<8, 256, 0, s>>>(m, static_cast<unsigned char*>(ws));            \
+    if (bf16) k_tc_prepare<A, B, C, true><<<16, 256, 0, s>>>(m, static_cast<unsigned char*>(ws));       \
+    else k_tc_prepare<A, B, C, false><<<16, 256, 0, s>>>(m, static_cast<unsigned char*>(ws));           \
     return cudaGetLastError();                                                                           \
   }
   NDGI_TC_SHAPES(X)
@@ -423,19 +682,23 @@ static cudaError_t set_smem(K kern, uint32_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+constexpr int kPointsLanes = 4;
+
 cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const float* uvt, int64_t n, float* rgb,
                              cudaStream_t s) {
   const int64_t tiles = (n + 127) / 128;
-  const int64_t cap = (int64_t)num_sms() * 4;
-  const int grid = (int)(tiles < cap ? tiles : cap);
-#define X(A, B, C)                                                                                    \
-  if (m.cs == A && m.ct == B && m.hidden == C) {                                                      \
-    using L = TcLayout<A, B, C>;                                                                      \
-    auto kern = bf16 ? k_points_tc<A, B, C, true> : k_points_tc<A, B, C, false>;                       \
-    cudaError_t e = set_smem(kern, L::kSmem);                                                         \
-    if (e != cudaSuccess) return e;                                                                   \
-    kern<<<grid, kTcThreads, L::kSmem, s>>>(m, static_cast<const unsigned char*>(ws), uvt, n, rgb);   \
-    return cudaGetLastError();                                                                        \
+  const int64_t need = (tiles + kPointsLanes - 1) / kPointsLanes;
+  const int64_t cap = num_sms();
+  const int grid = (int)(need < cap ? need : cap);
+#define X(A, B, C)                                                                                           \
+  if (m.cs == A && m.ct == B && m.hidden == C) {                                                             \
+    using S = PointsSmem<A, B, C, kPointsLanes>;                                                             \
+    auto kern = bf16 ? k_points_tc<A, B, C, true, kPointsLanes> : k_points_tc<A, B, C, false, kPointsLanes>;  \
+    cudaError_t e = set_smem(kern, S::kBytes);                                                               \
+    if (e != cudaSuccess) return e;                                                                          \
+    kern<<<grid, kLaneThreads * kPointsLanes, S::kBytes, s>>>(m, static_cast<const unsigned char*>(ws), uvt, n, \
+                                                              rgb);                                          \
+    return cudaGetLastError();                                                                               \
   }
   NDGI_TC_SHAPES(X)
 #undef X
@@ -445,28 +708,26 @@ cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const
 cudaError_t launch_tc_pages(const PagesCtx& c, bool bf16, int cs, int ct, int hidden, const TcPagesShape& shape,
                             const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s) {
   const int grid = num_sms() * shape.ctas_per_sm;
-#define X(A, B, C)                                                                                         \
-  if (cs == A && ct == B && hidden == C) {                                                                 \
-    using L = TcLayout<A, B, C>;                                                                           \
-    auto kern = bf16 ? k_pages_tc<A, B, C, true> : k_pages_tc<A, B, C, false>;                              \
-    cudaError_t e = set_smem(kern, L::kSmem);                                                              \
-    if (e != cudaSuccess) return e;                                                                        \
-    kern<<<grid, kTcThreads, L::kSmem, s>>>(c, reqs, n_dev, shape.tile_w, shape.tiles_per_item);           \
-    return cudaGetLastError();                                                                             \
+#define X(A, B, C, NW)                                                                                      \
+  if (cs == A && ct == B && hidden == C && shape.lanes == NW) {                                             \
+    using S = PagesSmem<A, B, C, NW>;                                                                       \
+    auto kern = bf16 ? k_pages_tc<A, B, C, true, NW> : k_pages_tc<A, B, C, false, NW>;                        \
+    cudaError_t e = set_smem(kern, S::kBytes);                                                              \
+    if (e != cudaSuccess) return e;                                                                         \
+    kern<<<grid, kLaneThreads * NW, S::kBytes, s>>>(c, reqs, n_dev);                                        \
+    return cudaGetLastError();                                                                              \
   }
-  NDGI_TC_SHAPES(X)
+  X(16, 8, 16, 4) X(16, 8, 32, 4) X(16, 8, 64, 4) X(16, 16, 64, 4)
+  X(16, 8, 16, 2) X(16, 8, 32, 2) X(16, 8, 64, 2) X(16, 16, 64, 2)
 #undef X
   return cudaErrorInvalidValue;
 }
 
-TcPagesShape tc_default_pages_shape() { return TcPagesShape{4, 16, 16}; }
+TcPagesShape tc_default_pages_shape() { return TcPagesShape{1, 4}; }
+
 
 std::vector<TcPagesShape> tc_pages_candidates(int) {
-  std::vector<TcPagesShape> v;
-  for (int cps : {2, 3, 4})
-    for (int tw : {128, 32, 16})
-      for (int tpi : {4, 16, 128}) v.push_back(TcPagesShape{cps, tw, tpi});
-  return v;
+  return {TcPagesShape{1, 4}, TcPagesShape{1, 2}, TcPagesShape{2, 2}};
 }
 
 int tc_take_error() {

@@ -8,12 +8,12 @@ namespace ndgi {
 
 // Launch shape of the persistent page-decode kernel (picked by the autotuner).
 struct TcPagesShape {
-  int ctas_per_sm;     // resident CTAs per SM in the persistent grid (<= 4)
-  int tile_w;          // texel tile: tile_w x (128 / tile_w) texels per MMA tile
-  int tiles_per_item;  // tiles of one request per work item (1..128)
+  int ctas_per_sm;     // CTAs per SM in the persistent grid
+  int lanes;           // warpgroup lanes per CTA (2 or 4); the lanes split a request's 64x64 quadrants
 };
 
 bool tc_supported(int cs, int ct, int hidden);
+bool tc_pages_supported(int cs, int ct, int hidden);
 size_t tc_workspace_bytes(int cs, int ct, int hidden);
 cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream_t s);
 cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const float* uvt, int64_t n, float* rgb,
