@@ -161,6 +161,15 @@ PAGES_WORKLOAD = ("pages: 8 lightmaps (2x 512^2, 1024^2, 2048^2, 4096^2), BC4 ha
                   "MLP 24-64-64-3; 4096 Zipf(1.1) requests of 128^2 per frame, own t each; RGBA16F 8192^2 texture")
 
 
+def check_status(ndgi):
+    """'ok', or the library's report of a device-side failure (e.g. a timed-out barrier wait)."""
+    try:
+        ndgi.ndgi_check()
+        return "ok"
+    except Exception as ex:  # reported in the JSON line, never hidden
+        return str(ex)[:200]
+
+
 def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True):
     """Virtual-texture page decode: one step = one frame of 4096 page requests."""
     maps = synth.page_models(4)
@@ -177,7 +186,7 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
         ms, clocks = timed(lambda: plan.decode(r_dev, n_dev), steps, args.warmup, sample_clocks=(prec == "fp16"))
         st, err_word = plan.check()
         entry = {"value": texels / (ms / steps * 1e-3) / 1e9, "unit": "Gtexels/s", "ms_per_frame": ms / steps,
-                 "device_error_word": err_word}
+                 "device_error_word": err_word, "device_check": check_status(ndgi)}
         if prec == "fp16":
             entry["clocks"] = clocks
         if check_err and rank == 0:
@@ -284,6 +293,7 @@ def main():
 
     ms_main, clocks = timed(step_main, args.steps, args.warmup, sample_clocks=True)
     ms_step = ms_main / args.steps
+    device_check = {"points": check_status(ndgi)}
     value = world * N_QUERIES / (ms_step * 1e-3) / 1e9
 
     # FP32 plain decode beside it (fewer steps: it is ~10x slower)
@@ -353,7 +363,7 @@ def main():
         "config": {"workload": WORKLOAD, "queries_per_rank": N_QUERIES, "precision": prec,
                    "l2": "inputs larger than L2: 201 MB of queries + 201 MB of output per step; the 8 MiB "
                          "feature map stays L2-resident as in a steady frame"},
-        "max_err_over_range": errs, "fp32_plain": {"value": fp32_gt, "unit": "Gtexels/s",
+        "device_check": device_check, "max_err_over_range": errs, "fp32_plain": {"value": fp32_gt, "unit": "Gtexels/s",
                                                   "err": errs.get("fp32")},
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "Gtexels/s", "h2d_bytes_per_step": N_QUERIES * 12,

@@ -44,6 +44,27 @@ __device__ __forceinline__ int bc4_p35(uint32_t lo, uint32_t hi, uint32_t shift)
   return (int)(ca * r0 + cb * r1 + cc);
 }
 
+// Table form of the same palette for kernels that keep a 16-entry table in
+// shared memory: entry (m8 << 3 | k) holds {ca | cb << 16, cc} (m8 = 1 when
+// r0 > r1), so P35 = ca*r0 + cb*r1 + cc is one 2-way byte dot product of the
+// block's low word (bytes r0, r1) with the packed coefficients.
+__device__ __forceinline__ void init_p35_lut(uint2* lut, int tid) {
+  if (tid < 16) {
+    const uint32_t k = tid & 7u;
+    const bool m8 = tid >= 8;
+    const uint32_t ca = __byte_perm(m8 ? kCa8Lo : kCa6Lo, m8 ? kCa8Hi : kCa6Hi, k) & 0xffu;
+    const uint32_t cb = __byte_perm(m8 ? kCb8Lo : kCb6Lo, m8 ? kCb8Hi : kCb6Hi, k) & 0xffu;
+    lut[tid] = make_uint2(ca | (cb << 16), (!m8 && k == 7u) ? 8925u : 0u);
+  }
+}
+
+__device__ __forceinline__ int bc4_p35_lut(uint32_t lo, uint32_t hi, uint32_t shift, const uint2* lut) {
+  const uint32_t k = bc4_index(lo, hi, shift);
+  const uint32_t m8 = (lo & 0xffu) > ((lo >> 8) & 0xffu) ? 8u : 0u;
+  const uint2 e = lut[k | m8];
+  return (int)__dp2a_lo(e.x, lo, e.y);
+}
+
 __device__ __forceinline__ float p35_value(int p35) {
   return __fmul_rn(__int2float_rn(p35), kInv8925);
 }

@@ -101,12 +101,14 @@ __global__ void __launch_bounds__(kSimtThreads) k_points_f32(DevModel m, const f
                                                              float* __restrict__ rgb) {
   using Mlp = SimtMlp<CS + CT, H>;
   extern __shared__ __align__(16) float s_mlp[];
+  __shared__ uint2 lut[16];
+  init_p35_lut(lut, threadIdx.x);
   Mlp::load(s_mlp, m);
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float u = uvt[3 * i], v = uvt[3 * i + 1], t = uvt[3 * i + 2];
     float x[CS + CT];
-    gather_f32<CS, CT>(m, u, v, t, x, nullptr);
+    gather_f32<CS, CT>(m, u, v, t, x, nullptr, lut);
     float y0, y1, y2;
     Mlp::eval(s_mlp, x, y0, y1, y2);
     rgb[3 * i] = y0;
@@ -118,9 +120,12 @@ __global__ void __launch_bounds__(kSimtThreads) k_points_f32(DevModel m, const f
 template <int CS, int CT>
 __global__ void __launch_bounds__(kSimtThreads) k_debug_features(DevModel m, const float* __restrict__ uvt, int64_t n,
                                                                  float* __restrict__ xo, int32_t* __restrict__ p35) {
+  __shared__ uint2 lut[16];
+  init_p35_lut(lut, threadIdx.x);
+  __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float x[CS + CT];
-    gather_f32<CS, CT>(m, uvt[3 * i], uvt[3 * i + 1], uvt[3 * i + 2], x, p35 ? p35 + i * 4 * CS : nullptr);
+    gather_f32<CS, CT>(m, uvt[3 * i], uvt[3 * i + 1], uvt[3 * i + 2], x, p35 ? p35 + i * 4 * CS : nullptr, lut);
 #pragma unroll
     for (int c = 0; c < CS + CT; ++c) xo[i * (CS + CT) + c] = x[c];
   }
@@ -133,6 +138,9 @@ __global__ void __launch_bounds__(kSimtThreads) k_pages_f32(PagesCtx c, const nd
                                                             const int32_t* __restrict__ n_dev) {
   using Mlp = SimtMlp<CS + CT, H>;
   extern __shared__ __align__(16) float s_mlp[];
+  __shared__ uint2 lut[16];
+  init_p35_lut(lut, threadIdx.x);
+  __syncthreads();
   int n = *n_dev;
   if (n > c.max_reqs || n < 0) {   // reject the whole frame: the request buffer may be shorter
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(c.error_word, 1);
@@ -171,7 +179,7 @@ __global__ void __launch_bounds__(kSimtThreads) k_pages_f32(PagesCtx c, const nd
     const float u = ((float)(r.x0 + i) + 0.5f) / (float)m.lm_w;
     const float v = ((float)(r.y0 + j) + 0.5f) / (float)m.lm_h;
     float x[CS + CT];
-    gather_f32<CS, CT>(m, u, v, r.t, x, nullptr);
+    gather_f32<CS, CT>(m, u, v, r.t, x, nullptr, lut);
     float y0, y1, y2;
     Mlp::eval(s_mlp, x, y0, y1, y2);
     const int64_t o = (int64_t)(r.dst_y + j) * c.phys_w + (r.dst_x + i);

@@ -7,35 +7,45 @@
 namespace ndgi {
 
 // Feature gather at (u, v, t) in FP32: x = [v_s (CS), v_t (CT)].
-// If p35 != nullptr, the tap numerators are written there ([4][CS]).
+// If p35 != nullptr, the tap numerators are written there ([4][CS]).  `lut`
+// is the 16-entry palette table in shared memory (init_p35_lut).  Block lines
+// are read 16 bytes (two planes) at a time.
 template <int CS, int CT>
 __device__ __forceinline__ void gather_f32(const DevModel& m, float u, float v, float t, float (&x)[CS + CT],
-                                           int32_t* p35) {
+                                           int32_t* p35, const uint2* lut) {
+  static_assert(CS % 2 == 0, "planes are read in pairs");
   int x0, x1, y0, y1;
   float fx, fy;
   axis_setup(u, m.feat_w, m.address_mode, x0, x1, fx);
   axis_setup(v, m.feat_h, m.address_mode, y0, y1, fy);
   const int tx[4] = {x0, x1, x0, x1};
   const int ty[4] = {y0, y0, y1, y1};
-  const uint2* line[4];
+  const uint4* line[4];
   uint32_t shift[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    line[q] = reinterpret_cast<const uint2*>(m.bc4) + ((size_t)(ty[q] >> 2) * m.bw + (tx[q] >> 2)) * CS;
+    line[q] = reinterpret_cast<const uint4*>(m.bc4 + ((size_t)(ty[q] >> 2) * m.bw + (tx[q] >> 2)) * CS * 8);
     shift[q] = 16u + 3u * (uint32_t)(((ty[q] & 3) << 2) | (tx[q] & 3));
   }
   const float gx = 1.0f - fx, gy = 1.0f - fy;
 #pragma unroll
-  for (int c = 0; c < CS; ++c) {
-    float f[4];
+  for (int c = 0; c < CS; c += 2) {
+    float f[2][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const uint2 b = __ldg(line[q] + c);
-      const int p = bc4_p35(b.x, b.y, shift[q]);
-      if (p35) p35[q * CS + c] = p;
-      f[q] = p35_value(p);
+      const uint4 b = __ldg(line[q] + c / 2);
+      const int p0 = bc4_p35_lut(b.x, b.y, shift[q], lut);
+      const int p1 = bc4_p35_lut(b.z, b.w, shift[q], lut);
+      if (p35) {
+        p35[q * CS + c] = p0;
+        p35[q * CS + c + 1] = p1;
+      }
+      f[0][q] = p35_value(p0);
+      f[1][q] = p35_value(p1);
     }
-    x[c] = gy * (gx * f[0] + fx * f[1]) + fy * (gx * f[2] + fx * f[3]);
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      x[c + e] = gy * (gx * f[e][0] + fx * f[e][1]) + fy * (gx * f[e][2] + fx * f[e][3]);
   }
   int j0, j1;
   float a;

@@ -12,19 +12,18 @@
 // shared by the lanes; the lanes of a CTA interleave, so one lane's gather
 // and epilogues overlap the others' MMAs.
 //
-// Biases never touch the CUDA cores: before a layer's MMAs the issuing
-// thread copies a 32-row broadcast image of the bias from shared memory into
-// all 128 accumulator lanes (tcgen05.cp 32x128b.warpx4) and the MMAs
-// accumulate onto it.  For points, layer 1 still carries b1 in the K padding
-// (24 inputs pad to 32 anyway).  For pages, t is constant per request, so the
-// temporal part of layer 1 is folded into a per-request bias
-// b1' = b1 + W1_t v_t (FP32) and layer 1 only contracts the 16 spatial
-// channels (K = 16).
+// Biases never touch the CUDA cores: every A tile carries a ones column in
+// its K padding and the matching B row holds the bias, so the MMA adds it.
+// For pages, t is constant per request, so the temporal part of layer 1 is
+// folded into a per-request bias b1' = b1 + W1_t v_t (FP32), stored in B1 as
+// a hi + lo pair of FP16/BF16 values against two ones columns; layer 1 then
+// contracts only the 16 spatial channels plus those two columns (K = 32).
 //
 // Page features: a lane decodes each BC4 feature row of its page quadrant
-// once (exact integer palette numerator, scaled once in FP32, stored as FP16)
-// into a ring of 8 rows in shared memory and blends the four taps of each
-// texel with packed half2 arithmetic from there.
+// once (exact integer palette numerator from a 16-entry table and a byte dot
+// product, scaled once in FP32, stored as FP16) into a 16-row ring in shared
+// memory, in batches of up to 8 rows, and blends the four taps of each texel
+// with packed half2 arithmetic from there.
 //
 // Every mbarrier wait is bounded; a timeout is latched in a device error word
 // that ndgi_check reports, and the CTA unwinds and frees its tensor memory.
@@ -43,9 +42,6 @@ namespace ndgi {
 static __device__ int g_tc_error;
 
 constexpr int kLaneThreads = 128;
-constexpr int kRingRows = 8;      // decoded feature rows kept per lane (page path)
-constexpr int kRingCols = 40;     // feature columns per ring row
-constexpr int kQuad = 64;         // page quadrant side (texels)
 
 // ---------------------------------------------------------------------------
 // Weight image (built by ndgi_prepare), identical layout in global and shared
@@ -54,16 +50,15 @@ constexpr int kQuad = 64;         // page quadrant side (texels)
 template <int CS, int CT, int H>
 struct TcLayout {
   static constexpr int CIN = CS + CT;
-  static constexpr int K1P = ((CIN + 1 + 15) / 16) * 16;   // points: inputs + ones column, padded
-  static constexpr int K1G = ((CS + 15) / 16) * 16;        // pages: spatial channels only
+  static constexpr int K1P = ((CIN + 1 + 15) / 16) * 16;   // points: inputs + ones column (b1)
+  static constexpr int K1G = ((CS + 2 + 15) / 16) * 16;    // pages: spatial channels + two ones columns (b1' hi, lo)
+  static constexpr int K2 = H + 16;                        // hidden + ones column (b2 / b3)
   static constexpr int N3 = 16;                            // output layer N (3 used)
-  static constexpr uint32_t kB2 = 0;                       // [H][H]      K-major
-  static constexpr uint32_t kB3 = kB2 + H * H * 2;         // [16][H]     rows 3..15 zero
-  static constexpr uint32_t kB2Src = kB3 + N3 * H * 2;     // [H/4][32][4] f32 bias-2 broadcast image
-  static constexpr uint32_t kB3Src = kB2Src + H * 32 * 4;  // [1][32][4]   f32 bias-3 broadcast image
-  static constexpr uint32_t kShared = kB3Src + 32 * 4 * 4; // end of the part both kernels use
-  static constexpr uint32_t kB1P = kShared;                // [H][K1P]    points layer 1 (+ b1 row)
-  static constexpr uint32_t kB1G = kB1P + H * K1P * 2;     // [H][K1G]    pages layer 1 (spatial)
+  static constexpr uint32_t kB2 = 0;                       // [H][K2]     K-major, column H = b2
+  static constexpr uint32_t kB3 = kB2 + H * K2 * 2;        // [16][K2]    rows 3..15 zero, column H = b3
+  static constexpr uint32_t kShared = kB3 + N3 * K2 * 2;   // end of the part both kernels use
+  static constexpr uint32_t kB1P = kShared;                // [H][K1P]    points layer 1, column CIN = b1
+  static constexpr uint32_t kB1G = kB1P + H * K1P * 2;     // [H][K1G]    pages layer 1 (spatial; bias columns per request)
   static constexpr uint32_t kW1T = kB1G + H * K1G * 2;     // [CT][H] f32 stored temporal weights
   static constexpr uint32_t kB1 = kW1T + CT * H * 4;       // [H] f32 stored b1
   static constexpr uint32_t kWsBytes = kB1 + H * 4;
@@ -109,29 +104,22 @@ template <int CS, int CT, int H, bool BF16>
 __global__ void k_tc_prepare(DevModel m, unsigned char* __restrict__ ws) {
   using L = TcLayout<CS, CT, H>;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-  for (int i = tid; i < H * H; i += nt) {          // B2[n][k] = W2[k][n]
-    const int n = i / H, k = i % H;
-    *reinterpret_cast<uint16_t*>(ws + L::kB2 + kmajor_offset(n, k, H)) = to_bits<BF16>(m.w2[k * H + n]);
+  for (int i = tid; i < H * L::K2; i += nt) {      // B2[n][k] = W2[k][n], column H = b2
+    const int n = i / L::K2, k = i % L::K2;
+    const float v = k < H ? m.w2[k * H + n] : (k == H ? m.b2[n] : 0.0f);
+    *reinterpret_cast<uint16_t*>(ws + L::kB2 + kmajor_offset(n, k, L::K2)) = to_bits<BF16>(v);
   }
-  for (int i = tid; i < L::N3 * H; i += nt) {      // B3[n][k] = W3[k][n]
-    const int n = i / H, k = i % H;
-    *reinterpret_cast<uint16_t*>(ws + L::kB3 + kmajor_offset(n, k, H)) =
-        to_bits<BF16>(n < 3 ? m.w3[k * 3 + n] : 0.0f);
+  for (int i = tid; i < L::N3 * L::K2; i += nt) {  // B3[n][k] = W3[k][n], column H = b3
+    const int n = i / L::K2, k = i % L::K2;
+    const float v = n >= 3 ? 0.0f : (k < H ? m.w3[k * 3 + n] : (k == H ? m.b3[n] : 0.0f));
+    *reinterpret_cast<uint16_t*>(ws + L::kB3 + kmajor_offset(n, k, L::K2)) = to_bits<BF16>(v);
   }
-  for (int i = tid; i < H * 32; i += nt) {         // bias-2 broadcast image: chunk j = n/4, row r, element n%4
-    const int n = i % H, r = i / H;
-    reinterpret_cast<float*>(ws + L::kB2Src)[((n >> 2) * 32 + r) * 4 + (n & 3)] = round_stored<BF16>(m.b2[n]);
-  }
-  for (int i = tid; i < 32 * 4; i += nt) {
-    const int e = i & 3;
-    reinterpret_cast<float*>(ws + L::kB3Src)[i] = e < 3 ? round_stored<BF16>(m.b3[e]) : 0.0f;
-  }
-  for (int i = tid; i < H * L::K1P; i += nt) {     // points: B1[n][k] = W1[k][n], row CIN = b1
+  for (int i = tid; i < H * L::K1P; i += nt) {     // points: B1[n][k] = W1[k][n], column CIN = b1
     const int n = i / L::K1P, k = i % L::K1P;
     const float v = k < L::CIN ? m.w1[k * H + n] : (k == L::CIN ? m.b1[n] : 0.0f);
     *reinterpret_cast<uint16_t*>(ws + L::kB1P + kmajor_offset(n, k, L::K1P)) = to_bits<BF16>(v);
   }
-  for (int i = tid; i < H * L::K1G; i += nt) {     // pages: spatial rows of W1 only
+  for (int i = tid; i < H * L::K1G; i += nt) {     // pages: spatial rows of W1; bias columns filled per request
     const int n = i / L::K1G, k = i % L::K1G;
     *reinterpret_cast<uint16_t*>(ws + L::kB1G + kmajor_offset(n, k, L::K1G)) =
         to_bits<BF16>(k < CS ? m.w1[k * H + n] : 0.0f);
@@ -144,11 +132,6 @@ __global__ void k_tc_prepare(DevModel m, unsigned char* __restrict__ ws) {
 // ---------------------------------------------------------------------------
 // tcgen05 helpers specific to this file
 // ---------------------------------------------------------------------------
-// Broadcast copy of a 32-row x 4-column FP32 image into all 128 lanes.
-__device__ __forceinline__ void tmem_cp_bcast4(uint32_t taddr, uint32_t src_smem) {
-  asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc(src_smem, 0, 128))
-               : "memory");
-}
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -178,24 +161,26 @@ constexpr uint32_t tmem_alloc_cols(int cols) {
 // ---------------------------------------------------------------------------
 // One lane's MLP over a 128-row tile whose A1 is in shared memory.
 // ---------------------------------------------------------------------------
+// Descriptor start-address step: 256 B per K step of an operand tile (the
+// field holds the address >> 4).
+constexpr uint64_t kDescK = 256 >> 4;
+
 template <int H, bool BF16>
 struct Lane {
-  uint32_t tmem;         // this lane's 64 accumulator columns (lane 0)
+  uint32_t tmem;         // this lane's accumulator columns (lane 0)
   uint64_t* bar;
   uint32_t phase;
   int wg, t;             // lane index, thread index within the lane
   unsigned char* a1;     // A tiles of this lane
   unsigned char* a2;
 
-  // Issue (one thread): bias images then `K/16` MMAs, then commit.
-  __device__ __forceinline__ void issue(uint32_t bias_src, int bias_chunks, uint32_t a_smem, uint32_t b_smem, int K,
-                                        int N) {
+  // Issue (one thread): KSTEPS MMAs (the bias rides in the ones column of A), then commit.
+  template <int KSTEPS, int N>
+  __device__ __forceinline__ void issue(uint64_t a_desc, uint64_t b_desc) {
     tc_fence_after();
-    for (int j = 0; j < bias_chunks; ++j) tmem_cp_bcast4(tmem + 4u * j, bias_src + 512u * j);
-    const uint32_t sbo = (uint32_t)K * 16u, id = idesc_f16(128, N, BF16);
-    for (int ks = 0; ks < K / 16; ++ks)
-      umma_f16(tmem, sdesc(a_smem + 256u * ks, 128u, sbo), sdesc(b_smem + 256u * ks, 128u, sbo), id,
-               (bias_chunks > 0 || ks > 0) ? 1u : 0u);
+#pragma unroll
+    for (int ks = 0; ks < KSTEPS; ++ks)
+      umma_f16(tmem, a_desc + kDescK * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16), ks > 0 ? 1u : 0u);
     umma_commit(bar);
   }
 
@@ -206,11 +191,12 @@ struct Lane {
     lane_sync(wg);
   }
 
-  // Wait for the committed MMAs; false (uniform over the lane) on timeout, in
-  // which case `phase` keeps the parity still outstanding so the teardown can
-  // drain it.
+  // The issuing thread waits for the committed MMAs; the others block in the
+  // lane barrier.  false (uniform over the lane) on timeout, in which case
+  // `phase` keeps the parity still outstanding so the teardown can drain it.
   __device__ __forceinline__ bool wait() {
-    const bool ok = mbar_wait(bar, phase);
+    bool ok = true;
+    if (t == 0) ok = mbar_wait(bar, phase);
     if (lane_any(wg, !ok)) return false;
     phase ^= 1u;
     tc_fence_after();
@@ -227,7 +213,7 @@ struct Lane {
       p.y = pack2_relu<BF16>(__uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
       p.z = pack2_relu<BF16>(__uint_as_float(r[o + 4]), __uint_as_float(r[o + 5]));
       p.w = pack2_relu<BF16>(__uint_as_float(r[o + 6]), __uint_as_float(r[o + 7]));
-      *reinterpret_cast<uint4*>(a2 + kmajor_offset(t, 16 * c16 + o, H)) = p;
+      *reinterpret_cast<uint4*>(a2 + kmajor_offset(t, 16 * c16 + o, H + 16)) = p;
     }
   }
   __device__ __forceinline__ void hidden_epilogue() {
@@ -243,20 +229,31 @@ struct Lane {
     }
   }
 
+  // Row t of A2 ends in the constant columns H..H+15 = (1, 0, ..., 0) that
+  // carry the layer-2 and layer-3 biases; written once per lane.
+  __device__ __forceinline__ void init_a2_ones() {
+    const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
+    *reinterpret_cast<uint4*>(a2 + kmajor_offset(t, H, H + 16)) = make_uint4(one, 0, 0, 0);
+    *reinterpret_cast<uint4*>(a2 + kmajor_offset(t, H + 8, H + 16)) = make_uint4(0, 0, 0, 0);
+  }
+
   // Layers 1..3 after A1 is written; y = this thread's RGB.  false on timeout.
-  __device__ __forceinline__ bool run(uint32_t b1_smem, int K1, uint32_t b1src, int b1_chunks, uint32_t b2_smem,
-                                      uint32_t b2src, uint32_t b3_smem, uint32_t b3src, float& y0, float& y1,
-                                      float& y2) {
+  // d.* are the shared-memory descriptors of the operand tiles.
+  struct Descs {
+    uint64_t a1, a2, b1, b2, b3;
+  };
+  template <int K1>
+  __device__ __forceinline__ bool run(const Descs& d, float& y0, float& y1, float& y2) {
     publish();
-    if (t == 0) issue(b1src, b1_chunks, smem_addr(a1), b1_smem, K1, H);
+    if (t == 0) issue<K1 / 16, H>(d.a1, d.b1);
     if (!wait()) return false;
     hidden_epilogue();
     publish();
-    if (t == 0) issue(b2src, H / 4, smem_addr(a2), b2_smem, H, H);
+    if (t == 0) issue<H / 16 + 1, H>(d.a2, d.b2);
     if (!wait()) return false;
     hidden_epilogue();
     publish();
-    if (t == 0) issue(b3src, 1, smem_addr(a2), b3_smem, H, 16);
+    if (t == 0) issue<H / 16 + 1, 16>(d.a2, d.b3);
     if (!wait()) return false;
     uint32_t r[4];
     tmem_ld4(tmem + ((uint32_t)((t >> 5) * 32) << 16), r);
@@ -318,8 +315,9 @@ struct PointsSmem {
   using L = TcLayout<CS, CT, H>;
   static constexpr uint32_t kW = 0;                                  // shared part of the image
   static constexpr uint32_t kB1 = kW + L::kShared;                   // points B1
-  static constexpr uint32_t kLanes = (kB1 + H * L::K1P * 2 + 127) / 128 * 128;
-  static constexpr uint32_t kA1 = 0, kA2 = 128 * L::K1P * 2, kLaneBytes = kA2 + 128 * H * 2;
+  static constexpr uint32_t kLut = kB1 + H * L::K1P * 2;             // 16 x uint2 palette table
+  static constexpr uint32_t kLanes = (kLut + 128 + 127) / 128 * 128;
+  static constexpr uint32_t kA1 = 0, kA2 = 128 * L::K1P * 2, kLaneBytes = kA2 + 128 * L::K2 * 2;
   static constexpr uint32_t kBytes = kLanes + NWG * kLaneBytes;
 };
 
@@ -335,6 +333,8 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
   const int tid = threadIdx.x, wg = tid >> 7;
   copy16(sm + S::kW, ws, L::kShared, tid, kLaneThreads * NWG);
   copy16(sm + S::kB1, ws + L::kB1P, H * L::K1P * 2, tid, kLaneThreads * NWG);
+  const uint2* lut = reinterpret_cast<const uint2*>(sm + S::kLut);
+  init_p35_lut(reinterpret_cast<uint2*>(sm + S::kLut), tid);
   const uint32_t tbase = cta_setup<NWG, L::kTmemCols>(bars, &slot, tid);
   Lane<H, BF16> lane;
   lane.tmem = tbase + (uint32_t)(wg * L::kTmemCols);
@@ -345,13 +345,20 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
   lane.a1 = sm + S::kLanes + wg * S::kLaneBytes + S::kA1;
   lane.a2 = sm + S::kLanes + wg * S::kLaneBytes + S::kA2;
   const uint32_t base = smem_addr(sm);
+  typename Lane<H, BF16>::Descs d;
+  d.a1 = sdesc(smem_addr(lane.a1), 128u, L::K1P * 16u);
+  d.a2 = sdesc(smem_addr(lane.a2), 128u, L::K2 * 16u);
+  d.b1 = sdesc(base + S::kB1, 128u, L::K1P * 16u);
+  d.b2 = sdesc(base + S::kW + L::kB2, 128u, L::K2 * 16u);
+  d.b3 = sdesc(base + S::kW + L::kB3, 128u, L::K2 * 16u);
+  lane.init_a2_ones();
   bool failed = false;
   const int64_t tiles = (n + 127) / 128;
   for (int64_t tile = (int64_t)blockIdx.x * NWG + wg; tile < tiles; tile += (int64_t)gridDim.x * NWG) {
     const int64_t q = tile * 128 + lane.t;
     float x[L::CIN];
     if (q < n) {
-      gather_f32<CS, CT>(m, uvt[3 * q], uvt[3 * q + 1], uvt[3 * q + 2], x, nullptr);
+      gather_f32<CS, CT>(m, uvt[3 * q], uvt[3 * q + 1], uvt[3 * q + 2], x, nullptr, lut);
     } else {
 #pragma unroll
       for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
@@ -372,8 +379,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
       *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(lane.t, 8 * c, L::K1P)) = p;
     }
     float y0, y1, y2;
-    if (!lane.run(base + S::kB1, L::K1P, 0, 0, base + S::kW + L::kB2, base + S::kW + L::kB2Src,
-                  base + S::kW + L::kB3, base + S::kW + L::kB3Src, y0, y1, y2)) {
+    if (!lane.template run<L::K1P>(d, y0, y1, y2)) {
       failed = true;
       break;
     }
@@ -389,6 +395,11 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
 // ---------------------------------------------------------------------------
 // Batched pages
 // ---------------------------------------------------------------------------
+constexpr int kRingRows = 16;     // decoded feature rows kept per lane
+constexpr int kRingCols = 40;     // feature columns per ring row (>= 64 * 1/2 + 2)
+constexpr int kQuad = 64;         // page quadrant side (texels)
+constexpr int kDecodeAhead = 4;   // extra feature rows decoded per batch
+
 template <int CS, int CT, int H, int NWG>
 struct PagesSmem {
   using L = TcLayout<CS, CT, H>;
@@ -396,13 +407,14 @@ struct PagesSmem {
   static constexpr uint32_t kB1 = kW + L::kShared;                      // pages B1 [H][K1G]
   static constexpr uint32_t kW1T = kB1 + H * L::K1G * 2;                // [CT][H] f32
   static constexpr uint32_t kBias1 = kW1T + CT * H * 4;                 // [H] f32 stored b1
-  static constexpr uint32_t kB1Src = (kBias1 + H * 4 + 127) / 128 * 128;   // folded b1' broadcast image
-  static constexpr uint32_t kLanes = kB1Src + H * 32 * 4;
+  static constexpr uint32_t kLut = (kBias1 + H * 4 + 127) / 128 * 128;
+  static constexpr uint32_t kLanes = kLut + 128;
   // per lane
   static constexpr uint32_t kA1 = 0;
   static constexpr uint32_t kA2 = kA1 + 128 * L::K1G * 2;
-  static constexpr uint32_t kRing = kA2 + 128 * H * 2;                  // [8 rows][40 cols][CS] fp16
-  static constexpr uint32_t kRowTab = kRing + kRingRows * kRingCols * CS * 2;   // [64] int4
+  static constexpr uint32_t kRing = kA2 + 128 * L::K2 * 2;   // [CS/8 planes][16 rows][40 cols] x 8 halves
+  static constexpr uint32_t kPlane = kRingRows * kRingCols * 16;
+  static constexpr uint32_t kRowTab = kRing + (CS / 8) * kPlane;   // [64] int4
   static constexpr uint32_t kLaneBytes = (kRowTab + kQuad * 16 + 127) / 128 * 128;
   static constexpr uint32_t kBytes = kLanes + NWG * kLaneBytes;
 };
@@ -414,26 +426,33 @@ struct PageItem {
   int staged;         // 1 ring path, 0 direct per-texel gather
 };
 
-// Decodes feature row `fr` (columns fc0 .. fc0+ncols-1) of channel pairs into ring slot fr & 7.
+// Decodes feature rows r_from..r_to, columns fc0..fc0+ncols-1, into the ring:
+// one work unit = (row, column, 8-plane group), read as four 16-byte block
+// loads, written as one 16-byte ring entry of 8 FP16 values.
 template <int CS>
-__device__ __forceinline__ void decode_row(const DevModel& m, unsigned char* ring, int fr, int fc0, int ncols, int t) {
-  constexpr int CG = CS / 8;   // 8-channel groups
-  __half* slot = reinterpret_cast<__half*>(ring) + (size_t)(fr & (kRingRows - 1)) * kRingCols * CS;
-  const int by = fr >> 2, py = (fr & 3) << 2;
-  for (int u = t; u < ncols * CG; u += kLaneThreads) {
-    const int col = u / CG, g = u % CG;
-    const int fc = fc0 + col;
-    const uint32_t shift = 16u + 3u * (uint32_t)(py | (fc & 3));
-    const uint4* line = reinterpret_cast<const uint4*>(m.bc4 + (((size_t)by * m.bw + (fc >> 2)) * CS + 8 * g) * 8);
+__device__ __forceinline__ void decode_rows(const DevModel& m, unsigned char* ring, int r_from, int r_to, int fc0,
+                                            int ncols, int t, const uint2* lut) {
+  constexpr int G = CS / 8;
+  const int per_row = ncols * G;
+  const int total = (r_to - r_from + 1) * per_row;
+  for (int u = t; u < total; u += kLaneThreads) {
+    const int rr = u / per_row, rem = u - rr * per_row;
+    const int col = rem / G, g = rem - col * G;
+    const int fr = r_from + rr, fc = fc0 + col;
+    const uint32_t shift = 16u + 3u * (uint32_t)(((fr & 3) << 2) | (fc & 3));
+    const uint4* line = reinterpret_cast<const uint4*>(m.bc4 + (((size_t)(fr >> 2) * m.bw + (fc >> 2)) * CS + 8 * g) * 8);
+    uint4 b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = __ldg(line + q);
     uint32_t h[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const uint4 b = __ldg(line + q);                 // two planes: (x, y) and (z, w)
-      const float f0 = p35_value(bc4_p35(b.x, b.y, shift));
-      const float f1 = p35_value(bc4_p35(b.z, b.w, shift));
+      const float f0 = p35_value(bc4_p35_lut(b[q].x, b[q].y, shift, lut));
+      const float f1 = p35_value(bc4_p35_lut(b[q].z, b[q].w, shift, lut));
       h[q] = pack2<false>(f0, f1);
     }
-    *reinterpret_cast<uint4*>(slot + (size_t)col * CS + 8 * g) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(ring + g * PagesSmem<CS, 0, 16, 1>::kPlane +
+                              ((fr & (kRingRows - 1)) * kRingCols + col) * 16) = make_uint4(h[0], h[1], h[2], h[3]);
   }
 }
 
@@ -456,6 +475,8 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
     if (blockIdx.x == 0 && tid == 0) atomicOr(c.error_word, 1);
     n = 0;
   }
+  const uint2* lut = reinterpret_cast<const uint2*>(sm + S::kLut);
+  init_p35_lut(reinterpret_cast<uint2*>(sm + S::kLut), tid);
   const uint32_t tbase = cta_setup<NWG, L::kTmemCols>(bars, &slot, tid);
   Lane<H, BF16> lane;
   lane.tmem = tbase + (uint32_t)(wg * L::kTmemCols);
@@ -469,6 +490,18 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   unsigned char* ring = lb + S::kRing;
   int4* rowtab = reinterpret_cast<int4*>(lb + S::kRowTab);
   const uint32_t base = smem_addr(sm);
+  typename Lane<H, BF16>::Descs d;
+  d.a1 = sdesc(smem_addr(lane.a1), 128u, L::K1G * 16u);
+  d.a2 = sdesc(smem_addr(lane.a2), 128u, L::K2 * 16u);
+  d.b1 = sdesc(base + S::kB1, 128u, L::K1G * 16u);
+  d.b2 = sdesc(base + S::kW + L::kB2, 128u, L::K2 * 16u);
+  d.b3 = sdesc(base + S::kW + L::kB3, 128u, L::K2 * 16u);
+  lane.init_a2_ones();
+  {   // A1 columns CS, CS+1 = 1 (b1' hi, lo), the rest of the padding 0; columns < CS change per tile
+    const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
+    *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, CS, L::K1G)) = make_uint4(one | (one << 16), 0, 0, 0);
+    *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, CS + 8, L::K1G)) = make_uint4(0, 0, 0, 0);
+  }
   int loaded = -1;
   bool failed = false;          // this lane timed out
   for (;;) {
@@ -490,8 +523,8 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
                (int64_t)r.dst_y + r.h <= c.phys_h;
           if (!ok) atomicOr(c.error_word, 4);
           // ring path when features are at most half the lightmap resolution: a
-          // 64-texel quadrant side then spans <= 34 feature columns and 8 output
-          // rows span <= 6 feature rows
+          // 64-texel quadrant side then spans <= 34 feature columns and a batch
+          // of 8 output rows plus the look-ahead fits the 16-row ring
           s_req.staged = 2 * mm.feat_w <= mm.lm_w && 2 * mm.feat_h <= mm.lm_h;
         }
         s_req.valid = ok;
@@ -517,17 +550,20 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
                   a * load_temporal(m.temporal, m.temporal_f16, j1 * CT + tid);
     }
     __syncthreads();
-    // folded layer-1 bias b1' = b1 + W1_t v_t (FP32), as a 32-row broadcast image
-    for (int i = tid; i < H * 32; i += NT) {
-      const int nn = i % H, row = i / H;
+    // folded layer-1 bias b1' = b1 + W1_t v_t (FP32), stored in B1's columns
+    // CS and CS+1 as a hi + lo pair so the MMA adds it at FP32 accuracy
+    if (tid < H) {
       const float* w1t = reinterpret_cast<const float*>(sm + S::kW1T);
-      float b = reinterpret_cast<const float*>(sm + S::kBias1)[nn];
+      float b = reinterpret_cast<const float*>(sm + S::kBias1)[tid];
 #pragma unroll
-      for (int cc = 0; cc < CT; ++cc) b = fmaf(w1t[cc * H + nn], s_vt[cc], b);
-      reinterpret_cast<float*>(sm + S::kB1Src)[((nn >> 2) * 32 + row) * 4 + (nn & 3)] = b;
+      for (int cc = 0; cc < CT; ++cc) b = fmaf(w1t[cc * H + tid], s_vt[cc], b);
+      const uint16_t hi = to_bits<BF16>(b);
+      const float hif = BF16 ? __uint_as_float((uint32_t)hi << 16) : __half2float(*reinterpret_cast<const __half*>(&hi));
+      const uint16_t lo = to_bits<BF16>(b - hif);
+      *reinterpret_cast<uint32_t*>(sm + S::kB1 + kmajor_offset(tid, CS, L::K1G)) = (uint32_t)hi | ((uint32_t)lo << 16);
     }
     __syncthreads();
-    // ---- lane: one 64 x 64 quadrant of the request ----
+    // ---- lane: 64 x 64 quadrants of the request ----
     for (int quad = wg; quad < 4 && !failed; quad += NWG) {
       const int ox = (quad & 1) * kQuad, oy = (quad >> 1) * kQuad;
       const int qw = min(kQuad, r.w - ox), qh = min(kQuad, r.h - oy);
@@ -553,16 +589,21 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
       }
       lane_sync(wg);
       const bool staged = s_req.staged && ncols <= kRingCols;
+      const int fr_last = rowtab[qh - 1].y;
       const __half2 wx1 = __float2half2_rn(fx), wx0 = __float2half2_rn(1.0f - fx);
+      const int c0 = (cx0 - fc0) * 16, c1 = (cx1 - fc0) * 16;   // byte offsets within a ring row
       int decoded_hi = -1000000;   // highest feature row decoded into the ring
       for (int row0 = 0; row0 < qh && !failed; row0 += 8) {
         if (staged) {
           // rows needed by output rows row0 .. row0+7 (monotone in the row)
           const int need_lo = rowtab[row0].x, need_hi = rowtab[min(row0 + 7, qh - 1)].y;
-          const int from = max(decoded_hi + 1, need_lo);
-          for (int fr = from; fr <= need_hi; ++fr) decode_row<CS>(m, ring, fr, fc0, ncols, t);
-          decoded_hi = max(decoded_hi, need_hi);
-          lane_sync(wg);
+          if (need_hi > decoded_hi) {
+            const int from = max(decoded_hi + 1, need_lo);
+            const int to = min(need_hi + kDecodeAhead, fr_last);
+            decode_rows<CS>(m, ring, from, to, fc0, ncols, t, lut);
+            decoded_hi = to;
+            lane_sync(wg);
+          }
         }
         for (int sub = 0; sub < 8 && row0 + sub < qh; sub += 2) {
           const int orow = row0 + sub + (t >> 6);
@@ -575,17 +616,18 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
               const __half2 wy1 = __float2half2_rn(fy), wy0 = __float2half2_rn(1.0f - fy);
               const __half2 w00 = __hmul2(wx0, wy0), w10 = __hmul2(wx1, wy0), w01 = __hmul2(wx0, wy1),
                             w11 = __hmul2(wx1, wy1);
-              const __half* rr = reinterpret_cast<const __half*>(ring);
-              const uint4* t00 = reinterpret_cast<const uint4*>(rr + ((size_t)(rt.x & 7) * kRingCols + (cx0 - fc0)) * CS);
-              const uint4* t10 = reinterpret_cast<const uint4*>(rr + ((size_t)(rt.x & 7) * kRingCols + (cx1 - fc0)) * CS);
-              const uint4* t01 = reinterpret_cast<const uint4*>(rr + ((size_t)(rt.y & 7) * kRingCols + (cx0 - fc0)) * CS);
-              const uint4* t11 = reinterpret_cast<const uint4*>(rr + ((size_t)(rt.y & 7) * kRingCols + (cx1 - fc0)) * CS);
+              const unsigned char* r0p = ring + (rt.x & (kRingRows - 1)) * (kRingCols * 16);
+              const unsigned char* r1p = ring + (rt.y & (kRingRows - 1)) * (kRingCols * 16);
               uint32_t out[8];
 #pragma unroll
               for (int g = 0; g < 2; ++g) {
-                const uint4 a = t00[g], b = t10[g], cq = t01[g], d = t11[g];
+                const int po = g * (int)S::kPlane;
+                const uint4 a = *reinterpret_cast<const uint4*>(r0p + po + c0);
+                const uint4 b = *reinterpret_cast<const uint4*>(r0p + po + c1);
+                const uint4 cq = *reinterpret_cast<const uint4*>(r1p + po + c0);
+                const uint4 dd = *reinterpret_cast<const uint4*>(r1p + po + c1);
                 const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w},
-                               cv[4] = {cq.x, cq.y, cq.z, cq.w}, dv[4] = {d.x, d.y, d.z, d.w};
+                               cv[4] = {cq.x, cq.y, cq.z, cq.w}, dv[4] = {dd.x, dd.y, dd.z, dd.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                   __half2 v = __hmul2(w00, *reinterpret_cast<const __half2*>(&av[e]));
@@ -605,7 +647,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
             } else {
               float x[CS + CT];
               gather_f32<CS, CT>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
-                                 ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr);
+                                 ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr, lut);
               p0 = make_uint4(pack2<BF16>(x[0], x[1]), pack2<BF16>(x[2], x[3]), pack2<BF16>(x[4], x[5]),
                               pack2<BF16>(x[6], x[7]));
               p1 = make_uint4(pack2<BF16>(x[8], x[9]), pack2<BF16>(x[10], x[11]), pack2<BF16>(x[12], x[13]),
@@ -615,8 +657,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
           *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, 0, L::K1G)) = p0;
           *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, 8, L::K1G)) = p1;
           float y0, y1, y2;
-          if (!lane.run(base + S::kB1, L::K1G, base + S::kB1Src, H / 4, base + S::kW + L::kB2,
-                        base + S::kW + L::kB2Src, base + S::kW + L::kB3, base + S::kW + L::kB3Src, y0, y1, y2)) {
+          if (!lane.template run<L::K1G>(d, y0, y1, y2)) {
             failed = true;
             break;
           }
