@@ -159,122 +159,135 @@ constexpr uint32_t tmem_alloc_cols(int cols) {
 }
 
 // ---------------------------------------------------------------------------
-// One lane's MLP over a 128-row tile whose A1 is in shared memory.
+// One lane's MLP engine with SL tile slots.
+//
+// A slot is one 128-row tile in flight: a region of tensor memory holding the
+// accumulator D (H columns, FP32) followed by the A operand of the next MMA
+// (rows in lanes, two 16-bit K elements per column), and an mbarrier.  The
+// layer-1 A tile (K1 columns of features, bias ones column(s), zeros) and the
+// hidden tiles (H ReLU values, then (1, 0, ...) carrying the bias in the
+// K padding, K2 = H + 16) take turns in the A region, written from registers
+// with tcgen05.st.  Only the small weight tiles B are read from shared
+// memory.  With SL = 2 the lane interleaves its slots so that one slot's
+// gather or epilogue runs while the other slot's MMAs are in flight.
 // ---------------------------------------------------------------------------
-// Descriptor start-address step: 256 B per K step of an operand tile (the
-// field holds the address >> 4).
-constexpr uint64_t kDescK = 256 >> 4;
+constexpr uint64_t kDescK = 256 >> 4;   // B descriptor start-address step per K step (256 B)
 
-template <int H, bool BF16>
-struct Lane {
-  uint32_t tmem;         // this lane's accumulator columns (lane 0)
-  uint64_t* bar;
-  uint32_t phase;
-  int wg, t;             // lane index, thread index within the lane
-  unsigned char* a1;     // A tiles of this lane
-  unsigned char* a2;
+template <int H, bool BF16, int K1, int SL>
+struct Engine {
+  static constexpr int K2 = H + 16;
+  static constexpr uint32_t kACol = H;                        // A region starts after D
+  static constexpr uint32_t kSlotCols = tmem_alloc_cols(H + K2 / 2);
+  static_assert(K1 / 2 <= K2 / 2 + 8, "layer-1 tile must fit the A region");
+  int wg, t;
+  uint32_t tmem[SL];     // slot base, lane 0
+  uint32_t lane_off;     // this warp's lane quadrant, in the TMEM address
+  uint64_t* bar[SL];
+  uint32_t phase[SL];
+  uint64_t db1, db2, db3;
 
-  // Issue (one thread): KSTEPS MMAs (the bias rides in the ones column of A), then commit.
   template <int KSTEPS, int N>
-  __device__ __forceinline__ void issue(uint64_t a_desc, uint64_t b_desc) {
+  __device__ __forceinline__ void issue(int s, uint64_t b_desc) {
     tc_fence_after();
 #pragma unroll
     for (int ks = 0; ks < KSTEPS; ++ks)
-      umma_f16(tmem, a_desc + kDescK * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16), ks > 0 ? 1u : 0u);
-    umma_commit(bar);
+      umma_f16_ts(tmem[s], tmem[s] + kACol + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16),
+                  ks > 0 ? 1u : 0u);
+    umma_commit(bar[s]);
   }
-
-  // Publish generic-proxy smem writes and reach the lane barrier.
+  // Make this lane's tcgen05.st writes visible, then reach the lane barrier.
   __device__ __forceinline__ void publish() {
-    fence_async_smem();
+    tmem_st_wait();
     tc_fence_before();
     lane_sync(wg);
   }
-
-  // The issuing thread waits for the committed MMAs; the others block in the
-  // lane barrier.  false (uniform over the lane) on timeout, in which case
-  // `phase` keeps the parity still outstanding so the teardown can drain it.
-  __device__ __forceinline__ bool wait() {
+  __device__ __forceinline__ void layer1(int s) {
+    publish();
+    if (t == 0) issue<K1 / 16, H>(s, db1);
+  }
+  __device__ __forceinline__ void layer2(int s) {
+    publish();
+    if (t == 0) issue<K2 / 16, H>(s, db2);
+  }
+  __device__ __forceinline__ void layer3(int s) {
+    publish();
+    if (t == 0) issue<K2 / 16, 16>(s, db3);
+  }
+  // Thread 0 waits for slot s's MMAs, the lane blocks in its barrier.  false
+  // (uniform) on timeout; the phase then keeps the parity still outstanding.
+  __device__ __forceinline__ bool wait(int s) {
     bool ok = true;
-    if (t == 0) ok = mbar_wait(bar, phase);
+    if (t == 0) ok = mbar_wait(bar[s], phase[s]);
     if (lane_any(wg, !ok)) return false;
-    phase ^= 1u;
+    phase[s] ^= 1u;
     tc_fence_after();
     return true;
   }
-
-  // This thread's row of D (H columns) -> ReLU -> FP16/BF16 -> row t of A2.
-  __device__ __forceinline__ void store_chunk(const uint32_t (&r)[16], int c16) {
+  // Layer-1 row of this thread: K1/2 packed words.
+  __device__ __forceinline__ void write_a1(int s, const uint32_t* w) {
+    const uint32_t a = tmem[s] + lane_off + kACol;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int o = 8 * h;
-      uint4 p;
-      p.x = pack2_relu<BF16>(__uint_as_float(r[o + 0]), __uint_as_float(r[o + 1]));
-      p.y = pack2_relu<BF16>(__uint_as_float(r[o + 2]), __uint_as_float(r[o + 3]));
-      p.z = pack2_relu<BF16>(__uint_as_float(r[o + 4]), __uint_as_float(r[o + 5]));
-      p.w = pack2_relu<BF16>(__uint_as_float(r[o + 6]), __uint_as_float(r[o + 7]));
-      *reinterpret_cast<uint4*>(a2 + kmajor_offset(t, 16 * c16 + o, H + 16)) = p;
+    for (int c = 0; c < K1 / 2; c += 8) {
+      if (c + 16 <= K1 / 2 && (c % 16) == 0) {
+        uint32_t r[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = w[c + j];
+        tmem_st16(a + c, r);
+        c += 8;
+      } else {
+        uint32_t r[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) r[j] = w[c + j];
+        tmem_st8(a + c, r);
+      }
     }
   }
-  __device__ __forceinline__ void hidden_epilogue() {
-    const uint32_t row = tmem + ((uint32_t)((t >> 5) * 32) << 16);
+  // Slot s: this thread's row of D -> ReLU -> FP16/BF16 -> the hidden A tile,
+  // plus the (1, 0, ...) bias columns.
+  __device__ __forceinline__ void epilogue(int s) {
+    const uint32_t d = tmem[s] + lane_off, a = d + kACol;
 #pragma unroll
-    for (int c = 0; c < H / 16; c += 2) {
-      uint32_t r0[16], r1[16];
-      tmem_ld16(row + 16u * c, r0);
-      if (c + 1 < H / 16) tmem_ld16(row + 16u * (c + 1), r1);
-      tmem_ld_wait();
-      store_chunk(r0, c);
-      if (c + 1 < H / 16) store_chunk(r1, c + 1);
+    for (int c = 0; c < H; c += 32) {
+      if (H - c >= 32) {
+        uint32_t r[32], w[16];
+        tmem_ld32(d + c, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+        tmem_st16(a + c / 2, w);
+      } else {
+        uint32_t r[16], w[8];
+        tmem_ld16(d + c, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+        tmem_st8(a + c / 2, w);
+      }
     }
-  }
-
-  // Row t of A2 ends in the constant columns H..H+15 = (1, 0, ..., 0) that
-  // carry the layer-2 and layer-3 biases; written once per lane.
-  __device__ __forceinline__ void init_a2_ones() {
     const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
-    *reinterpret_cast<uint4*>(a2 + kmajor_offset(t, H, H + 16)) = make_uint4(one, 0, 0, 0);
-    *reinterpret_cast<uint4*>(a2 + kmajor_offset(t, H + 8, H + 16)) = make_uint4(0, 0, 0, 0);
+    const uint32_t ones[8] = {one, 0, 0, 0, 0, 0, 0, 0};
+    tmem_st8(a + H / 2, ones);
   }
-
-  // Layers 1..3 after A1 is written; y = this thread's RGB.  false on timeout.
-  // d.* are the shared-memory descriptors of the operand tiles.
-  struct Descs {
-    uint64_t a1, a2, b1, b2, b3;
-  };
-  template <int K1>
-  __device__ __forceinline__ bool run(const Descs& d, float& y0, float& y1, float& y2) {
-    publish();
-    if (t == 0) issue<K1 / 16, H>(d.a1, d.b1);
-    if (!wait()) return false;
-    hidden_epilogue();
-    publish();
-    if (t == 0) issue<H / 16 + 1, H>(d.a2, d.b2);
-    if (!wait()) return false;
-    hidden_epilogue();
-    publish();
-    if (t == 0) issue<H / 16 + 1, 16>(d.a2, d.b3);
-    if (!wait()) return false;
+  // Slot s after layer 3: this thread's RGB.
+  __device__ __forceinline__ void output(int s, float& y0, float& y1, float& y2) {
     uint32_t r[4];
-    tmem_ld4(tmem + ((uint32_t)((t >> 5) * 32) << 16), r);
+    tmem_ld4(tmem[s] + lane_off, r);
     tmem_ld_wait();
     y0 = __uint_as_float(r[0]);
     y1 = __uint_as_float(r[1]);
     y2 = __uint_as_float(r[2]);
-    tc_fence_before();
-    return true;
   }
 };
 
-// CTA set-up: TMEM for all lanes, one mbarrier per lane.
-template <int NWG, int COLS>
+// CTA set-up: TMEM for all slots, one mbarrier per slot.
+template <int NSLOTS, int COLS>
 __device__ __forceinline__ uint32_t cta_setup(uint64_t* bars, uint32_t* slot, int tid) {
   if ((tid >> 5) == 0) {
-    tmem_alloc(slot, tmem_alloc_cols(NWG * COLS));
+    tmem_alloc(slot, tmem_alloc_cols(NSLOTS * COLS));
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int i = 0; i < NWG; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < NSLOTS; ++i) mbar_init(&bars[i], 1);
     mbar_fence_init();
   }
   fence_async_smem();
@@ -285,19 +298,21 @@ __device__ __forceinline__ uint32_t cta_setup(uint64_t* bars, uint32_t* slot, in
 }
 
 // CTA end.  A lane whose wait timed out latches the error word and waits
-// (bounded) for its MMAs still in flight before the tensor memory is freed.
-template <int NWG, int COLS>
-__device__ __forceinline__ void cta_teardown(uint32_t tmem, uint64_t* bar, uint32_t phase, bool lane_timed_out,
+// (bounded) for the MMAs it still has in flight before the tensor memory is
+// freed.
+template <int NSLOTS, int COLS, typename E, int SL>
+__device__ __forceinline__ void cta_teardown(uint32_t tbase, E& e, const bool (&inflight)[SL], bool timed_out,
                                              int tid) {
-  if (lane_timed_out) {
-    if ((tid & (kLaneThreads - 1)) == 0) atomicOr(&g_tc_error, 1);
-    mbar_wait(bar, phase);
+  if (timed_out && e.t == 0) {
+    atomicOr(&g_tc_error, 1);
+    for (int s = 0; s < SL; ++s)
+      if (inflight[s]) mbar_wait(e.bar[s], e.phase[s]);
   }
   tc_fence_before();
   __syncthreads();
   if ((tid >> 5) == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, tmem_alloc_cols(NWG * COLS));
+    tmem_dealloc(tbase, tmem_alloc_cols(NSLOTS * COLS));
   }
 }
 
@@ -307,89 +322,143 @@ __device__ __forceinline__ void copy16(unsigned char* dst, const unsigned char* 
     *reinterpret_cast<uint4*>(dst + i) = *reinterpret_cast<const uint4*>(src + i);
 }
 
+template <int H, bool BF16, int K1, int SL>
+__device__ __forceinline__ void engine_init(Engine<H, BF16, K1, SL>& e, uint32_t tbase, uint64_t* bars, int tid,
+                                            uint32_t b1_smem, uint32_t b2_smem, uint32_t b3_smem) {
+  using E = Engine<H, BF16, K1, SL>;
+  e.wg = tid >> 7;
+  e.t = tid & (kLaneThreads - 1);
+  e.lane_off = (uint32_t)(((e.t >> 5) * 32) << 16);
+#pragma unroll
+  for (int s = 0; s < SL; ++s) {
+    e.tmem[s] = tbase + (uint32_t)((SL * e.wg + s) * E::kSlotCols);
+    e.bar[s] = &bars[SL * e.wg + s];
+    e.phase[s] = 0;
+  }
+  e.db1 = sdesc(b1_smem, 128u, K1 * 16u);
+  e.db2 = sdesc(b2_smem, 128u, E::K2 * 16u);
+  e.db3 = sdesc(b3_smem, 128u, E::K2 * 16u);
+}
+
 // ---------------------------------------------------------------------------
 // Random-access points
 // ---------------------------------------------------------------------------
-template <int CS, int CT, int H, int NWG>
+template <int CS, int CT, int H>
 struct PointsSmem {
   using L = TcLayout<CS, CT, H>;
   static constexpr uint32_t kW = 0;                                  // shared part of the image
   static constexpr uint32_t kB1 = kW + L::kShared;                   // points B1
   static constexpr uint32_t kLut = kB1 + H * L::K1P * 2;             // 16 x uint2 palette table
-  static constexpr uint32_t kLanes = (kLut + 128 + 127) / 128 * 128;
-  static constexpr uint32_t kA1 = 0, kA2 = 128 * L::K1P * 2, kLaneBytes = kA2 + 128 * L::K2 * 2;
-  static constexpr uint32_t kBytes = kLanes + NWG * kLaneBytes;
+  static constexpr uint32_t kBytes = kLut + 128;
 };
 
-template <int CS, int CT, int H, bool BF16, int NWG>
+// Layer-1 words of one query: features, the ones column for b1, zeros.
+template <int CIN, int K1, bool BF16>
+__device__ __forceinline__ void pack_a1(const float (&x)[CIN], uint32_t (&w)[K1 / 2]) {
+#pragma unroll
+  for (int j = 0; j < K1 / 2; ++j) {
+    float v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k = 2 * j + e;
+      v[e] = k < CIN ? x[k < CIN ? k : 0] : (k == CIN ? 1.0f : 0.0f);
+    }
+    w[j] = pack2<BF16>(v[0], v[1]);
+  }
+}
+
+template <int CS, int CT, int H, bool BF16, int NWG, int SL>
 __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, const unsigned char* __restrict__ ws,
                                                                     const float* __restrict__ uvt, int64_t n,
                                                                     float* __restrict__ rgb) {
   using L = TcLayout<CS, CT, H>;
-  using S = PointsSmem<CS, CT, H, NWG>;
+  using S = PointsSmem<CS, CT, H>;
+  using E = Engine<H, BF16, L::K1P, SL>;
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint64_t bars[NWG];
+  __shared__ uint64_t bars[SL * NWG];
   __shared__ uint32_t slot;
-  const int tid = threadIdx.x, wg = tid >> 7;
+  const int tid = threadIdx.x;
   copy16(sm + S::kW, ws, L::kShared, tid, kLaneThreads * NWG);
   copy16(sm + S::kB1, ws + L::kB1P, H * L::K1P * 2, tid, kLaneThreads * NWG);
   const uint2* lut = reinterpret_cast<const uint2*>(sm + S::kLut);
   init_p35_lut(reinterpret_cast<uint2*>(sm + S::kLut), tid);
-  const uint32_t tbase = cta_setup<NWG, L::kTmemCols>(bars, &slot, tid);
-  Lane<H, BF16> lane;
-  lane.tmem = tbase + (uint32_t)(wg * L::kTmemCols);
-  lane.bar = &bars[wg];
-  lane.phase = 0;
-  lane.wg = wg;
-  lane.t = tid & (kLaneThreads - 1);
-  lane.a1 = sm + S::kLanes + wg * S::kLaneBytes + S::kA1;
-  lane.a2 = sm + S::kLanes + wg * S::kLaneBytes + S::kA2;
+  const uint32_t tbase = cta_setup<SL * NWG, E::kSlotCols>(bars, &slot, tid);
   const uint32_t base = smem_addr(sm);
-  typename Lane<H, BF16>::Descs d;
-  d.a1 = sdesc(smem_addr(lane.a1), 128u, L::K1P * 16u);
-  d.a2 = sdesc(smem_addr(lane.a2), 128u, L::K2 * 16u);
-  d.b1 = sdesc(base + S::kB1, 128u, L::K1P * 16u);
-  d.b2 = sdesc(base + S::kW + L::kB2, 128u, L::K2 * 16u);
-  d.b3 = sdesc(base + S::kW + L::kB3, 128u, L::K2 * 16u);
-  lane.init_a2_ones();
-  bool failed = false;
+  E e;
+  engine_init<H, BF16, L::K1P, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
+  const int t = e.t;
+  // inflight[s]: slot s has MMAs issued and not yet waited for; need_out[s]:
+  // its layer-3 result is still to be read out (one round later).
+  bool inflight[SL], need_out[SL], timed_out = false;
+  int64_t prev_q[SL];
+#pragma unroll
+  for (int s = 0; s < SL; ++s) {
+    inflight[s] = need_out[s] = false;
+    prev_q[s] = -1;
+  }
   const int64_t tiles = (n + 127) / 128;
-  for (int64_t tile = (int64_t)blockIdx.x * NWG + wg; tile < tiles; tile += (int64_t)gridDim.x * NWG) {
-    const int64_t q = tile * 128 + lane.t;
-    float x[L::CIN];
-    if (q < n) {
-      gather_f32<CS, CT>(m, uvt[3 * q], uvt[3 * q + 1], uvt[3 * q + 2], x, nullptr, lut);
-    } else {
+  const int64_t lanes = (int64_t)gridDim.x * NWG, lane_id = (int64_t)blockIdx.x * NWG + e.wg;
+  for (int64_t round = 0; !timed_out; ++round) {
+    bool active[SL], any = false;
 #pragma unroll
-      for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
-    }
-#pragma unroll
-    for (int c = 0; c < L::K1P / 8; ++c) {
-      float v[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = 8 * c + e;
-        v[e] = k < L::CIN ? x[k < L::CIN ? k : 0] : (k == L::CIN ? 1.0f : 0.0f);
+    for (int s = 0; s < SL; ++s) {
+      const int64_t tile = lane_id + (SL * round + s) * lanes;
+      active[s] = tile < tiles;
+      any = any || active[s];
+      if (timed_out) continue;
+      if (need_out[s]) {   // finish this slot's previous tile
+        if (!e.wait(s)) {
+          timed_out = true;
+          continue;
+        }
+        inflight[s] = need_out[s] = false;
+        float y0, y1, y2;
+        e.output(s, y0, y1, y2);
+        if (prev_q[s] < n) {
+          rgb[3 * prev_q[s]] = y0;
+          rgb[3 * prev_q[s] + 1] = y1;
+          rgb[3 * prev_q[s] + 2] = y2;
+        }
       }
-      uint4 p;
-      p.x = pack2<BF16>(v[0], v[1]);
-      p.y = pack2<BF16>(v[2], v[3]);
-      p.z = pack2<BF16>(v[4], v[5]);
-      p.w = pack2<BF16>(v[6], v[7]);
-      *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(lane.t, 8 * c, L::K1P)) = p;
+      if (!active[s]) continue;
+      const int64_t q = tile * 128 + t;
+      float x[L::CIN];
+      if (q < n) {
+        gather_f32<CS, CT>(m, uvt[3 * q], uvt[3 * q + 1], uvt[3 * q + 2], x, nullptr, lut);
+      } else {
+#pragma unroll
+        for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
+      }
+      uint32_t w[L::K1P / 2];
+      pack_a1<L::CIN, L::K1P, BF16>(x, w);
+      e.write_a1(s, w);
+      e.layer1(s);
+      inflight[s] = true;
+      prev_q[s] = q;
     }
-    float y0, y1, y2;
-    if (!lane.template run<L::K1P>(d, y0, y1, y2)) {
-      failed = true;
-      break;
-    }
-    if (q < n) {
-      rgb[3 * q] = y0;
-      rgb[3 * q + 1] = y1;
-      rgb[3 * q + 2] = y2;
+    if (timed_out || !any) break;
+#pragma unroll
+    for (int layer = 2; layer <= 3; ++layer) {
+#pragma unroll
+      for (int s = 0; s < SL; ++s) {
+        if (!active[s] || timed_out) continue;
+        if (!e.wait(s)) {
+          timed_out = true;
+          continue;
+        }
+        inflight[s] = false;
+        e.epilogue(s);
+        if (layer == 2) {
+          e.layer2(s);
+        } else {
+          e.layer3(s);
+          need_out[s] = true;
+        }
+        inflight[s] = true;
+      }
     }
   }
-  cta_teardown<NWG, L::kTmemCols>(tbase, lane.bar, lane.phase, failed, tid);
+  cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -399,6 +468,7 @@ constexpr int kRingRows = 16;     // decoded feature rows kept per lane
 constexpr int kRingCols = 40;     // feature columns per ring row (>= 64 * 1/2 + 2)
 constexpr int kQuad = 64;         // page quadrant side (texels)
 constexpr int kDecodeAhead = 4;   // extra feature rows decoded per batch
+constexpr uint32_t kRingPlane = kRingRows * kRingCols * 16;   // one 8-channel plane
 
 template <int CS, int CT, int H, int NWG>
 struct PagesSmem {
@@ -409,12 +479,9 @@ struct PagesSmem {
   static constexpr uint32_t kBias1 = kW1T + CT * H * 4;                 // [H] f32 stored b1
   static constexpr uint32_t kLut = (kBias1 + H * 4 + 127) / 128 * 128;
   static constexpr uint32_t kLanes = kLut + 128;
-  // per lane
-  static constexpr uint32_t kA1 = 0;
-  static constexpr uint32_t kA2 = kA1 + 128 * L::K1G * 2;
-  static constexpr uint32_t kRing = kA2 + 128 * L::K2 * 2;   // [CS/8 planes][16 rows][40 cols] x 8 halves
-  static constexpr uint32_t kPlane = kRingRows * kRingCols * 16;
-  static constexpr uint32_t kRowTab = kRing + (CS / 8) * kPlane;   // [64] int4
+  // per lane: the feature ring and the row table
+  static constexpr uint32_t kRing = 0;
+  static constexpr uint32_t kRowTab = kRing + (CS / 8) * kRingPlane;   // [64] int4
   static constexpr uint32_t kLaneBytes = (kRowTab + kQuad * 16 + 127) / 128 * 128;
   static constexpr uint32_t kBytes = kLanes + NWG * kLaneBytes;
 };
@@ -440,7 +507,8 @@ __device__ __forceinline__ void decode_rows(const DevModel& m, unsigned char* ri
     const int col = rem / G, g = rem - col * G;
     const int fr = r_from + rr, fc = fc0 + col;
     const uint32_t shift = 16u + 3u * (uint32_t)(((fr & 3) << 2) | (fc & 3));
-    const uint4* line = reinterpret_cast<const uint4*>(m.bc4 + (((size_t)(fr >> 2) * m.bw + (fc >> 2)) * CS + 8 * g) * 8);
+    const uint4* line =
+        reinterpret_cast<const uint4*>(m.bc4 + (((size_t)(fr >> 2) * m.bw + (fc >> 2)) * CS + 8 * g) * 8);
     uint4 b[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) b[q] = __ldg(line + q);
@@ -451,25 +519,69 @@ __device__ __forceinline__ void decode_rows(const DevModel& m, unsigned char* ri
       const float f1 = p35_value(bc4_p35_lut(b[q].z, b[q].w, shift, lut));
       h[q] = pack2<false>(f0, f1);
     }
-    *reinterpret_cast<uint4*>(ring + g * PagesSmem<CS, 0, 16, 1>::kPlane +
-                              ((fr & (kRingRows - 1)) * kRingCols + col) * 16) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(ring + g * kRingPlane + ((fr & (kRingRows - 1)) * kRingCols + col) * 16) =
+        make_uint4(h[0], h[1], h[2], h[3]);
   }
 }
 
-template <int CS, int CT, int H, bool BF16, int NWG>
+// Layer-1 words of one page texel from the ring: bilinear blend of the four
+// taps in half2 (16 channels), the two ones columns for b1' (hi, lo), zeros.
+template <int CS, bool BF16, int K1>
+__device__ __forceinline__ void ring_texel(uint32_t (&w)[K1 / 2], const unsigned char* ring, int4 rt, int c0, int c1,
+                                           __half2 wx0, __half2 wx1) {
+  const float fy = __int_as_float(rt.z);
+  const __half2 wy1 = __float2half2_rn(fy), wy0 = __float2half2_rn(1.0f - fy);
+  const __half2 w00 = __hmul2(wx0, wy0), w10 = __hmul2(wx1, wy0), w01 = __hmul2(wx0, wy1), w11 = __hmul2(wx1, wy1);
+  const unsigned char* r0p = ring + (rt.x & (kRingRows - 1)) * (kRingCols * 16);
+  const unsigned char* r1p = ring + (rt.y & (kRingRows - 1)) * (kRingCols * 16);
+#pragma unroll
+  for (int g = 0; g < CS / 8; ++g) {
+    const int po = g * (int)kRingPlane;
+    const uint4 a = *reinterpret_cast<const uint4*>(r0p + po + c0);
+    const uint4 b = *reinterpret_cast<const uint4*>(r0p + po + c1);
+    const uint4 cq = *reinterpret_cast<const uint4*>(r1p + po + c0);
+    const uint4 dd = *reinterpret_cast<const uint4*>(r1p + po + c1);
+    const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w}, cv[4] = {cq.x, cq.y, cq.z, cq.w},
+                   dv[4] = {dd.x, dd.y, dd.z, dd.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __half2 v = __hmul2(w00, *reinterpret_cast<const __half2*>(&av[k]));
+      v = __hfma2(w10, *reinterpret_cast<const __half2*>(&bv[k]), v);
+      v = __hfma2(w01, *reinterpret_cast<const __half2*>(&cv[k]), v);
+      v = __hfma2(w11, *reinterpret_cast<const __half2*>(&dv[k]), v);
+      if (BF16) {
+        const float2 f = __half22float2(v);
+        w[4 * g + k] = pack2<true>(f.x, f.y);
+      } else {
+        w[4 * g + k] = *reinterpret_cast<const uint32_t*>(&v);
+      }
+    }
+  }
+}
+
+template <int CS, bool BF16, int K1>
+__device__ __forceinline__ void a1_bias_words(uint32_t (&w)[K1 / 2]) {
+  const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
+  w[CS / 2] = one | (one << 16);
+#pragma unroll
+  for (int j = CS / 2 + 1; j < K1 / 2; ++j) w[j] = 0u;
+}
+
+template <int CS, int CT, int H, bool BF16, int NWG, int SL>
 __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, const ndgi_page_req* __restrict__ reqs,
                                                                    const int32_t* __restrict__ n_dev) {
   using L = TcLayout<CS, CT, H>;
   using S = PagesSmem<CS, CT, H, NWG>;
+  using E = Engine<H, BF16, L::K1G, SL>;
   static_assert(CS == 16, "the staged page path is built for 16 spatial channels");
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint64_t bars[NWG];
+  __shared__ uint64_t bars[SL * NWG];
   __shared__ uint32_t slot;
   __shared__ int s_item;
   __shared__ PageItem s_req;
   __shared__ float s_vt[CT];
   constexpr int NT = kLaneThreads * NWG;
-  const int tid = threadIdx.x, wg = tid >> 7, t = tid & (kLaneThreads - 1);
+  const int tid = threadIdx.x;
   int n = *n_dev;
   if (n > c.max_reqs || n < 0) {   // reject the whole frame: the request buffer may be shorter
     if (blockIdx.x == 0 && tid == 0) atomicOr(c.error_word, 1);
@@ -477,33 +589,18 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   }
   const uint2* lut = reinterpret_cast<const uint2*>(sm + S::kLut);
   init_p35_lut(reinterpret_cast<uint2*>(sm + S::kLut), tid);
-  const uint32_t tbase = cta_setup<NWG, L::kTmemCols>(bars, &slot, tid);
-  Lane<H, BF16> lane;
-  lane.tmem = tbase + (uint32_t)(wg * L::kTmemCols);
-  lane.bar = &bars[wg];
-  lane.phase = 0;
-  lane.wg = wg;
-  lane.t = t;
+  const uint32_t tbase = cta_setup<SL * NWG, E::kSlotCols>(bars, &slot, tid);
+  const uint32_t base = smem_addr(sm);
+  E e;
+  engine_init<H, BF16, L::K1G, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
+  const int wg = e.wg, t = e.t;
   unsigned char* lb = sm + S::kLanes + wg * S::kLaneBytes;
-  lane.a1 = lb + S::kA1;
-  lane.a2 = lb + S::kA2;
   unsigned char* ring = lb + S::kRing;
   int4* rowtab = reinterpret_cast<int4*>(lb + S::kRowTab);
-  const uint32_t base = smem_addr(sm);
-  typename Lane<H, BF16>::Descs d;
-  d.a1 = sdesc(smem_addr(lane.a1), 128u, L::K1G * 16u);
-  d.a2 = sdesc(smem_addr(lane.a2), 128u, L::K2 * 16u);
-  d.b1 = sdesc(base + S::kB1, 128u, L::K1G * 16u);
-  d.b2 = sdesc(base + S::kW + L::kB2, 128u, L::K2 * 16u);
-  d.b3 = sdesc(base + S::kW + L::kB3, 128u, L::K2 * 16u);
-  lane.init_a2_ones();
-  {   // A1 columns CS, CS+1 = 1 (b1' hi, lo), the rest of the padding 0; columns < CS change per tile
-    const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
-    *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, CS, L::K1G)) = make_uint4(one | (one << 16), 0, 0, 0);
-    *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, CS + 8, L::K1G)) = make_uint4(0, 0, 0, 0);
-  }
   int loaded = -1;
-  bool failed = false;          // this lane timed out
+  bool inflight[SL], need_out[SL], timed_out = false;   // per slot: MMAs not yet waited for / result to read out
+#pragma unroll
+  for (int s = 0; s < SL; ++s) inflight[s] = need_out[s] = false;
   for (;;) {
     // ---- CTA: next request (the barrier keeps thread 0 from overwriting the
     // shared request slot while a skipped request is still being read) ----
@@ -558,29 +655,29 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
 #pragma unroll
       for (int cc = 0; cc < CT; ++cc) b = fmaf(w1t[cc * H + tid], s_vt[cc], b);
       const uint16_t hi = to_bits<BF16>(b);
-      const float hif = BF16 ? __uint_as_float((uint32_t)hi << 16) : __half2float(*reinterpret_cast<const __half*>(&hi));
+      const float hif =
+          BF16 ? __uint_as_float((uint32_t)hi << 16) : __half2float(*reinterpret_cast<const __half*>(&hi));
       const uint16_t lo = to_bits<BF16>(b - hif);
-      *reinterpret_cast<uint32_t*>(sm + S::kB1 + kmajor_offset(tid, CS, L::K1G)) = (uint32_t)hi | ((uint32_t)lo << 16);
+      *reinterpret_cast<uint32_t*>(sm + S::kB1 + kmajor_offset(tid, CS, L::K1G)) =
+          (uint32_t)hi | ((uint32_t)lo << 16);
     }
+    fence_async_smem();   // weights and b1' are read by the tensor core
     __syncthreads();
-    // ---- lane: 64 x 64 quadrants of the request ----
-    for (int quad = wg; quad < 4 && !failed; quad += NWG) {
+    // ---- lane: 64 x 64 quadrants of the request; a tile = 64 columns x 2 rows ----
+    for (int quad = wg; quad < 4 && !timed_out; quad += NWG) {
       const int ox = (quad & 1) * kQuad, oy = (quad >> 1) * kQuad;
       const int qw = min(kQuad, r.w - ox), qh = min(kQuad, r.h - oy);
       if (qw <= 0 || qh <= 0) continue;
-      // column set-up (fixed per thread): texel column ox + (t % 64)
       const int col = t & (kQuad - 1);
       int cx0, cx1;
       float fx;
       axis_setup(((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w, m.feat_w, m.address_mode, cx0, cx1, fx);
-      // feature columns touched by the quadrant (taps of its first and last column)
       int fa0, fa1, fb0, fb1;
       float fdum;
       axis_setup(((float)(r.x0 + ox) + 0.5f) / (float)m.lm_w, m.feat_w, m.address_mode, fa0, fa1, fdum);
       axis_setup(((float)(r.x0 + ox + qw - 1) + 0.5f) / (float)m.lm_w, m.feat_w, m.address_mode, fb0, fb1, fdum);
       const int fc0 = min(min(fa0, fa1), min(fb0, fb1));
       const int ncols = max(max(fa0, fa1), max(fb0, fb1)) - fc0 + 1;
-      // row set-up table for the quadrant's rows
       if (t < qh) {
         int ry0, ry1;
         float fy;
@@ -591,91 +688,99 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
       const bool staged = s_req.staged && ncols <= kRingCols;
       const int fr_last = rowtab[qh - 1].y;
       const __half2 wx1 = __float2half2_rn(fx), wx0 = __float2half2_rn(1.0f - fx);
-      const int c0 = (cx0 - fc0) * 16, c1 = (cx1 - fc0) * 16;   // byte offsets within a ring row
-      int decoded_hi = -1000000;   // highest feature row decoded into the ring
-      for (int row0 = 0; row0 < qh && !failed; row0 += 8) {
-        if (staged) {
-          // rows needed by output rows row0 .. row0+7 (monotone in the row)
-          const int need_lo = rowtab[row0].x, need_hi = rowtab[min(row0 + 7, qh - 1)].y;
-          if (need_hi > decoded_hi) {
-            const int from = max(decoded_hi + 1, need_lo);
-            const int to = min(need_hi + kDecodeAhead, fr_last);
-            decode_rows<CS>(m, ring, from, to, fc0, ncols, t, lut);
-            decoded_hi = to;
-            lane_sync(wg);
-          }
-        }
-        for (int sub = 0; sub < 8 && row0 + sub < qh; sub += 2) {
-          const int orow = row0 + sub + (t >> 6);
-          const bool in = col < qw && orow < qh;
-          uint4 p0 = make_uint4(0, 0, 0, 0), p1 = p0;
-          if (in) {
-            const int4 rt = rowtab[orow];
-            if (staged) {
-              const float fy = __int_as_float(rt.z);
-              const __half2 wy1 = __float2half2_rn(fy), wy0 = __float2half2_rn(1.0f - fy);
-              const __half2 w00 = __hmul2(wx0, wy0), w10 = __hmul2(wx1, wy0), w01 = __hmul2(wx0, wy1),
-                            w11 = __hmul2(wx1, wy1);
-              const unsigned char* r0p = ring + (rt.x & (kRingRows - 1)) * (kRingCols * 16);
-              const unsigned char* r1p = ring + (rt.y & (kRingRows - 1)) * (kRingCols * 16);
-              uint32_t out[8];
+      const int c0 = (cx0 - fc0) * 16, c1 = (cx1 - fc0) * 16;
+      int decoded_hi = -1000000;
+      int prev_row[SL];
 #pragma unroll
-              for (int g = 0; g < 2; ++g) {
-                const int po = g * (int)S::kPlane;
-                const uint4 a = *reinterpret_cast<const uint4*>(r0p + po + c0);
-                const uint4 b = *reinterpret_cast<const uint4*>(r0p + po + c1);
-                const uint4 cq = *reinterpret_cast<const uint4*>(r1p + po + c0);
-                const uint4 dd = *reinterpret_cast<const uint4*>(r1p + po + c1);
-                const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w},
-                               cv[4] = {cq.x, cq.y, cq.z, cq.w}, dv[4] = {dd.x, dd.y, dd.z, dd.w};
+      for (int s = 0; s < SL; ++s) prev_row[s] = -1;
+      const int ntiles = (qh + 1) / 2;
+      for (int round = 0; !timed_out; ++round) {
+        bool active[SL], any = false;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  __half2 v = __hmul2(w00, *reinterpret_cast<const __half2*>(&av[e]));
-                  v = __hfma2(w10, *reinterpret_cast<const __half2*>(&bv[e]), v);
-                  v = __hfma2(w01, *reinterpret_cast<const __half2*>(&cv[e]), v);
-                  v = __hfma2(w11, *reinterpret_cast<const __half2*>(&dv[e]), v);
-                  if (BF16) {
-                    const float2 f = __half22float2(v);
-                    out[4 * g + e] = pack2<true>(f.x, f.y);
-                  } else {
-                    out[4 * g + e] = *reinterpret_cast<const uint32_t*>(&v);
-                  }
-                }
+        for (int s = 0; s < SL; ++s) {
+          const int tile = SL * round + s;
+          active[s] = tile < ntiles;
+          any = any || active[s];
+          if (timed_out) continue;
+          if (need_out[s]) {   // finish this slot's previous tile
+            if (!e.wait(s)) {
+              timed_out = true;
+              continue;
+            }
+            inflight[s] = need_out[s] = false;
+            float y0, y1, y2;
+            e.output(s, y0, y1, y2);
+            const int orow = prev_row[s];
+            if (col < qw && orow < qh) {
+              const int64_t o = (int64_t)(r.dst_y + oy + orow) * c.phys_w + (r.dst_x + ox + col);
+              if (c.out_format == NDGI_RGBA32F) {
+                reinterpret_cast<float4*>(c.phys)[o] = make_float4(y0, y1, y2, 1.0f);
+              } else {
+                reinterpret_cast<uint2*>(c.phys)[o] = make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f));
               }
-              p0 = make_uint4(out[0], out[1], out[2], out[3]);
-              p1 = make_uint4(out[4], out[5], out[6], out[7]);
+            }
+          }
+          if (!active[s]) continue;
+          const int row_base = 2 * tile;
+          if (staged) {   // feature rows needed by output rows row_base, row_base + 1
+            const int need_hi = rowtab[min(row_base + 1, qh - 1)].y;
+            if (need_hi > decoded_hi) {
+              const int from = max(decoded_hi + 1, rowtab[row_base].x);
+              const int to = min(need_hi + kDecodeAhead, fr_last);
+              decode_rows<CS>(m, ring, from, to, fc0, ncols, t, lut);
+              decoded_hi = to;
+              lane_sync(wg);
+            }
+          }
+          const int orow = row_base + (t >> 6);
+          uint32_t w[L::K1G / 2];
+          if (col < qw && orow < qh) {
+            if (staged) {
+              ring_texel<CS, BF16, L::K1G>(w, ring, rowtab[orow], c0, c1, wx0, wx1);
             } else {
               float x[CS + CT];
               gather_f32<CS, CT>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
                                  ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr, lut);
-              p0 = make_uint4(pack2<BF16>(x[0], x[1]), pack2<BF16>(x[2], x[3]), pack2<BF16>(x[4], x[5]),
-                              pack2<BF16>(x[6], x[7]));
-              p1 = make_uint4(pack2<BF16>(x[8], x[9]), pack2<BF16>(x[10], x[11]), pack2<BF16>(x[12], x[13]),
-                              pack2<BF16>(x[14], x[15]));
+#pragma unroll
+              for (int j = 0; j < CS / 2; ++j) w[j] = pack2<BF16>(x[2 * j], x[2 * j + 1]);
             }
+          } else {
+#pragma unroll
+            for (int j = 0; j < CS / 2; ++j) w[j] = 0u;
           }
-          *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, 0, L::K1G)) = p0;
-          *reinterpret_cast<uint4*>(lane.a1 + kmajor_offset(t, 8, L::K1G)) = p1;
-          float y0, y1, y2;
-          if (!lane.template run<L::K1G>(d, y0, y1, y2)) {
-            failed = true;
-            break;
-          }
-          if (in) {
-            const int64_t o = (int64_t)(r.dst_y + oy + orow) * c.phys_w + (r.dst_x + ox + col);
-            if (c.out_format == NDGI_RGBA32F) {
-              reinterpret_cast<float4*>(c.phys)[o] = make_float4(y0, y1, y2, 1.0f);
+          a1_bias_words<CS, BF16, L::K1G>(w);
+          e.write_a1(s, w);
+          e.layer1(s);
+          inflight[s] = true;
+          prev_row[s] = orow;
+        }
+        if (timed_out || !any) break;
+#pragma unroll
+        for (int layer = 2; layer <= 3; ++layer) {
+#pragma unroll
+          for (int s = 0; s < SL; ++s) {
+            if (!active[s] || timed_out) continue;
+            if (!e.wait(s)) {
+              timed_out = true;
+              continue;
+            }
+            inflight[s] = false;
+            e.epilogue(s);
+            if (layer == 2) {
+              e.layer2(s);
             } else {
-              reinterpret_cast<uint2*>(c.phys)[o] = make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f));
+              e.layer3(s);
+              need_out[s] = true;
             }
+            inflight[s] = true;
           }
         }
       }
     }
     // every lane must be done with the weights and b1' before the next request
-    if (__syncthreads_or(failed)) break;
+    if (__syncthreads_or(timed_out)) break;
   }
-  cta_teardown<NWG, L::kTmemCols>(tbase, lane.bar, lane.phase, failed, tid);
+  cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -723,23 +828,26 @@ static cudaError_t set_smem(K kern, uint32_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-constexpr int kPointsLanes = 4;
+// Points: 4 lanes x 1 slot per CTA, one CTA per SM (4 tiles in flight: the
+// tensor memory holds 4 slots of 128 columns).
+constexpr int kPointsLanes = 4, kPointsSlots = 1;
 
 cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const float* uvt, int64_t n, float* rgb,
                              cudaStream_t s) {
   const int64_t tiles = (n + 127) / 128;
-  const int64_t need = (tiles + kPointsLanes - 1) / kPointsLanes;
+  const int64_t need = (tiles + kPointsLanes * kPointsSlots - 1) / (kPointsLanes * kPointsSlots);
   const int64_t cap = num_sms();
   const int grid = (int)(need < cap ? need : cap);
-#define X(A, B, C)                                                                                           \
-  if (m.cs == A && m.ct == B && m.hidden == C) {                                                             \
-    using S = PointsSmem<A, B, C, kPointsLanes>;                                                             \
-    auto kern = bf16 ? k_points_tc<A, B, C, true, kPointsLanes> : k_points_tc<A, B, C, false, kPointsLanes>;  \
-    cudaError_t e = set_smem(kern, S::kBytes);                                                               \
-    if (e != cudaSuccess) return e;                                                                          \
-    kern<<<grid, kLaneThreads * kPointsLanes, S::kBytes, s>>>(m, static_cast<const unsigned char*>(ws), uvt, n, \
-                                                              rgb);                                          \
-    return cudaGetLastError();                                                                               \
+#define X(A, B, C)                                                                                              \
+  if (m.cs == A && m.ct == B && m.hidden == C) {                                                                \
+    using S = PointsSmem<A, B, C>;                                                                              \
+    auto kern = bf16 ? k_points_tc<A, B, C, true, kPointsLanes, kPointsSlots>                                   \
+                     : k_points_tc<A, B, C, false, kPointsLanes, kPointsSlots>;                                 \
+    cudaError_t e = set_smem(kern, S::kBytes);                                                                  \
+    if (e != cudaSuccess) return e;                                                                             \
+    kern<<<grid, kLaneThreads * kPointsLanes, S::kBytes, s>>>(m, static_cast<const unsigned char*>(ws), uvt, n,  \
+                                                              rgb);                                             \
+    return cudaGetLastError();                                                                                  \
   }
   NDGI_TC_SHAPES(X)
 #undef X
@@ -749,27 +857,24 @@ cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const
 cudaError_t launch_tc_pages(const PagesCtx& c, bool bf16, int cs, int ct, int hidden, const TcPagesShape& shape,
                             const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s) {
   const int grid = num_sms() * shape.ctas_per_sm;
-#define X(A, B, C, NW)                                                                                      \
-  if (cs == A && ct == B && hidden == C && shape.lanes == NW) {                                             \
-    using S = PagesSmem<A, B, C, NW>;                                                                       \
-    auto kern = bf16 ? k_pages_tc<A, B, C, true, NW> : k_pages_tc<A, B, C, false, NW>;                        \
-    cudaError_t e = set_smem(kern, S::kBytes);                                                              \
-    if (e != cudaSuccess) return e;                                                                         \
-    kern<<<grid, kLaneThreads * NW, S::kBytes, s>>>(c, reqs, n_dev);                                        \
-    return cudaGetLastError();                                                                              \
+#define X(A, B, C, NW, SL)                                                                                      \
+  if (cs == A && ct == B && hidden == C && shape.lanes == NW && shape.slots == SL) {                            \
+    using S = PagesSmem<A, B, C, NW>;                                                                           \
+    auto kern = bf16 ? k_pages_tc<A, B, C, true, NW, SL> : k_pages_tc<A, B, C, false, NW, SL>;                   \
+    cudaError_t e = set_smem(kern, S::kBytes);                                                                  \
+    if (e != cudaSuccess) return e;                                                                             \
+    kern<<<grid, kLaneThreads * NW, S::kBytes, s>>>(c, reqs, n_dev);                                            \
+    return cudaGetLastError();                                                                                  \
   }
-  X(16, 8, 16, 4) X(16, 8, 32, 4) X(16, 8, 64, 4) X(16, 16, 64, 4)
-  X(16, 8, 16, 2) X(16, 8, 32, 2) X(16, 8, 64, 2) X(16, 16, 64, 2)
+  X(16, 8, 16, 4, 1) X(16, 8, 32, 4, 1) X(16, 8, 64, 4, 1) X(16, 16, 64, 4, 1)
+  X(16, 8, 16, 2, 2) X(16, 8, 32, 2, 2) X(16, 8, 64, 2, 2) X(16, 16, 64, 2, 2)
 #undef X
   return cudaErrorInvalidValue;
 }
 
-TcPagesShape tc_default_pages_shape() { return TcPagesShape{1, 4}; }
+TcPagesShape tc_default_pages_shape() { return TcPagesShape{1, 4, 1}; }
 
-
-std::vector<TcPagesShape> tc_pages_candidates(int) {
-  return {TcPagesShape{1, 4}, TcPagesShape{1, 2}, TcPagesShape{2, 2}};
-}
+std::vector<TcPagesShape> tc_pages_candidates(int) { return {TcPagesShape{1, 4, 1}, TcPagesShape{1, 2, 2}}; }
 
 int tc_take_error() {
   int h = 0;

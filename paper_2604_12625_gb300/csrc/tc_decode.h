@@ -9,7 +9,8 @@ namespace ndgi {
 // Launch shape of the persistent page-decode kernel (picked by the autotuner).
 struct TcPagesShape {
   int ctas_per_sm;     // CTAs per SM in the persistent grid
-  int lanes;           // warpgroup lanes per CTA (2 or 4); the lanes split a request's 64x64 quadrants
+  int lanes;           // warpgroup lanes per CTA; the lanes split a request's 64x64 quadrants
+  int slots;           // 128-row tiles in flight per lane (lanes x slots <= 4: tensor-memory bound)
 };
 
 bool tc_supported(int cs, int ct, int hidden);
