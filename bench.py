@@ -186,7 +186,7 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
         ms, clocks = timed(lambda: plan.decode(r_dev, n_dev), steps, args.warmup, sample_clocks=(prec == "fp16"))
         st, err_word = plan.check()
         entry = {"value": texels / (ms / steps * 1e-3) / 1e9, "unit": "Gtexels/s", "ms_per_frame": ms / steps,
-                 "device_error_word": err_word, "device_check": check_status(ndgi)}
+                 "device_error_word": err_word, "device_check": check_status(ndgi), "plan_shape": plan.info()}
         if prec == "fp16":
             entry["clocks"] = clocks
         if check_err and rank == 0:

@@ -206,6 +206,22 @@ ndgi_status ndgi_pages_autotune(ndgi_pages_plan *plan, const ndgi_page_req *reqs
  */
 ndgi_status ndgi_pages_check(ndgi_pages_plan *plan, int32_t *device_error, void *stream);
 
+/*
+ * The plan's current launch shape (host int32[4]): precision, CTAs per SM,
+ * warpgroup lanes per CTA, tiles in flight per lane (the last three describe
+ * the tensor-core kernel; for NDGI_FP32 plans info[1] is the grid size).
+ */
+ndgi_status ndgi_pages_plan_info(const ndgi_pages_plan *plan, int32_t info[4]);
+
+/*
+ * Pins the tensor-core plan's launch shape (CTAs per SM, warpgroup lanes per
+ * CTA, tiles in flight per lane) instead of the autotuner's choice.  A CTA
+ * holds most of its SM's tensor memory, so ctas_per_sm must be 1.
+ * NDGI_ERR_UNSUPPORTED if that shape is not built for the plan's model
+ * shape; NDGI_ERR_INVALID_ARG for NDGI_FP32 plans or other ctas_per_sm.
+ */
+ndgi_status ndgi_pages_plan_set_shape(ndgi_pages_plan *plan, int32_t ctas_per_sm, int32_t lanes, int32_t slots);
+
 /* Destroys the plan and its device block and graph.  NULL is a no-op. */
 ndgi_status ndgi_pages_plan_destroy(ndgi_pages_plan *plan);
 

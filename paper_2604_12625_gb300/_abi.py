@@ -67,6 +67,8 @@ SIGNATURES = [
     ("ndgi_pages_autotune", C.c_int, [_vp, _vp, _vp, _i32, _vp]),
     ("ndgi_pages_check", C.c_int, [_vp, _vp, _vp]),
     ("ndgi_pages_plan_destroy", C.c_int, [_vp]),
+    ("ndgi_pages_plan_info", C.c_int, [_vp, _vp]),
+    ("ndgi_pages_plan_set_shape", C.c_int, [_vp, _i32, _i32, _i32]),
     ("ndgi_decode_pages_static", C.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _i64, _i64, _vp, _vp]),
     ("ndgi_bc_pack", C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     ("ndgi_fit_forward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),

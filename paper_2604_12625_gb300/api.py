@@ -170,6 +170,15 @@ class PagesPlan:
     def autotune(self, reqs, n_dev, n_host, stream=None):
         check(lib().ndgi_pages_autotune(self.handle, _p(reqs), _p(n_dev), int(n_host), _stream(stream)))
 
+    def info(self):
+        """(precision, ctas_per_sm or grid, lanes, slots) of the current launch shape."""
+        a = (C.c_int32 * 4)()
+        check(lib().ndgi_pages_plan_info(self.handle, a))
+        return tuple(a)
+
+    def set_shape(self, ctas_per_sm, lanes, slots):
+        check(lib().ndgi_pages_plan_set_shape(self.handle, int(ctas_per_sm), int(lanes), int(slots)))
+
     def check(self, stream=None):
         err = C.c_int32(0)
         st = lib().ndgi_pages_check(self.handle, C.byref(err), _stream(stream))

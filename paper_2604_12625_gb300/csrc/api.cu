@@ -175,6 +175,7 @@ struct ndgi_pages_plan {
   ndgi_precision precision = NDGI_FP32;
   int n_models = 0, max_reqs = 0, out_format = 0;
   int cs = 0, ct = 0, hidden = 0;
+  bool staged = false;   // every model's features at most half its lightmap resolution
   void* phys = nullptr;
   int64_t phys_w = 0, phys_h = 0;
   void* dblock = nullptr;
@@ -197,7 +198,8 @@ static cudaError_t enqueue_pages(ndgi_pages_plan* p, const ndgi_page_req* reqs, 
   if (e != cudaSuccess) return e;
   if (p->precision == NDGI_FP32)
     return launch_pages_f32(p->ctx, p->cs, p->ct, p->hidden, reqs, n_dev, p->simt_grid, s);
-  return launch_tc_pages(p->ctx, p->precision == NDGI_BF16, p->cs, p->ct, p->hidden, p->shape, reqs, n_dev, s);
+  return launch_tc_pages(p->ctx, p->precision == NDGI_BF16, p->cs, p->ct, p->hidden, p->shape, p->staged, reqs,
+                         n_dev, s);
 }
 
 static ndgi_status ensure_graph(ndgi_pages_plan* p, const ndgi_page_req* reqs, const int32_t* n_dev) {
@@ -272,6 +274,9 @@ ndgi_status ndgi_pages_plan_create(const ndgi_model_desc* models, const void* co
   p->phys = phys;
   p->phys_w = phys_w;
   p->phys_h = phys_h;
+  p->staged = true;
+  for (int i = 0; i < n_models; ++i)
+    p->staged = p->staged && 2 * models[i].feat_w <= models[i].lm_w && 2 * models[i].feat_h <= models[i].lm_h;
   const size_t models_bytes = sizeof(DevModel) * n_models;
   const size_t ws_off = (models_bytes + 255) / 256 * 256;
   const size_t ctr_off = ws_off + (sizeof(void*) * n_models + 255) / 256 * 256;
@@ -379,6 +384,33 @@ ndgi_status ndgi_pages_check(ndgi_pages_plan* plan, int32_t* device_error, void*
   if (e != cudaSuccess) return cuda_status(e, "ndgi_pages_check");
   if (device_error) *device_error = err;
   if (err) return set_error(NDGI_ERR_DEVICE_CHECK, "ndgi_decode_pages: device checks rejected requests (0x%x)", err);
+  return NDGI_OK;
+}
+
+ndgi_status ndgi_pages_plan_info(const ndgi_pages_plan* plan, int32_t info[4]) {
+  if (!plan || !info) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_info: NULL argument");
+  info[0] = plan->precision;
+  if (plan->precision == NDGI_FP32) {
+    info[1] = plan->simt_grid;
+    info[2] = info[3] = 0;
+  } else {
+    info[1] = plan->shape.ctas_per_sm;
+    info[2] = plan->shape.lanes;
+    info[3] = plan->shape.slots;
+  }
+  return NDGI_OK;
+}
+
+ndgi_status ndgi_pages_plan_set_shape(ndgi_pages_plan* plan, int32_t ctas_per_sm, int32_t lanes, int32_t slots) {
+  if (!plan || plan->precision == NDGI_FP32)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_set_shape: needs a tensor-core plan");
+  if (ctas_per_sm != 1)   // each CTA holds most of its SM's tensor memory for the whole launch
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_set_shape: ctas_per_sm must be 1");
+  bool built = false;
+  for (const TcPagesShape& c : tc_pages_candidates(num_sms()))
+    built = built || (c.lanes == lanes && c.slots == slots);
+  if (!built) return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_pages_plan_set_shape: %d lanes x %d slots not built", lanes, slots);
+  plan->shape = TcPagesShape{ctas_per_sm, lanes, slots};
   return NDGI_OK;
 }
 

@@ -10,7 +10,10 @@ namespace ndgi {
 // If p35 != nullptr, the tap numerators are written there ([4][CS]).  `lut`
 // is the 16-entry palette table in shared memory (init_p35_lut).  Block lines
 // are read 16 bytes (two planes) at a time.
-template <int CS, int CT>
+// BATCHED = false reads one plane pair of the four taps at a time and never
+// skips a load: fewer live registers, for kernels where the gather is a cold
+// path and register pressure matters more.
+template <int CS, int CT, bool BATCHED = true>
 __device__ __forceinline__ void gather_f32(const DevModel& m, float u, float v, float t, float (&x)[CS + CT],
                                            int32_t* p35, const uint2* lut) {
   static_assert(CS % 2 == 0, "planes are read in pairs");
@@ -28,24 +31,72 @@ __device__ __forceinline__ void gather_f32(const DevModel& m, float u, float v, 
     shift[q] = 16u + 3u * (uint32_t)(((ty[q] & 3) << 2) | (tx[q] & 3));
   }
   const float gx = 1.0f - fx, gy = 1.0f - fy;
+  // Planes in groups of up to 8: all of a group's block loads (4 taps x 16
+  // bytes per plane pair) are issued before any of them is decoded, so a
+  // query waits on the memory system once per group rather than per pair.
+  if (BATCHED) {
+    // Taps that fall in a block already loaded reuse its line instead of
+    // loading it again (the two x taps share a block 3 times in 4, likewise y),
+    // which cuts the L1 requests of random queries from 4 lines to ~1.6; the
+    // loads of a group of up to 8 planes are all issued before decoding.
+    constexpr int G = CS < 8 ? CS : 8;
+    const bool same_x = (x0 >> 2) == (x1 >> 2), same_y = (y0 >> 2) == (y1 >> 2);
 #pragma unroll
-  for (int c = 0; c < CS; c += 2) {
-    float f[2][4];
+    for (int c0 = 0; c0 < CS; c0 += G) {
+      uint4 b[4][G / 2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 b = __ldg(line[q] + c / 2);
-      const int p0 = bc4_p35_lut(b.x, b.y, shift[q], lut);
-      const int p1 = bc4_p35_lut(b.z, b.w, shift[q], lut);
-      if (p35) {
-        p35[q * CS + c] = p0;
-        p35[q * CS + c + 1] = p1;
+      for (int e = 0; e < G / 2; ++e) {
+        b[0][e] = __ldg(line[0] + c0 / 2 + e);
+        if (!same_x) b[1][e] = __ldg(line[1] + c0 / 2 + e);
+        if (!same_y) b[2][e] = __ldg(line[2] + c0 / 2 + e);
+        if (!same_x && !same_y) b[3][e] = __ldg(line[3] + c0 / 2 + e);
       }
-      f[0][q] = p35_value(p0);
-      f[1][q] = p35_value(p1);
-    }
 #pragma unroll
-    for (int e = 0; e < 2; ++e)
-      x[c + e] = gy * (gx * f[e][0] + fx * f[e][1]) + fy * (gx * f[e][2] + fx * f[e][3]);
+      for (int e = 0; e < G / 2; ++e) {
+        if (same_x) b[1][e] = b[0][e];
+        if (same_y) b[2][e] = b[0][e];
+        if (same_x || same_y) b[3][e] = same_x ? b[2][e] : b[1][e];
+      }
+#pragma unroll
+      for (int e = 0; e < G / 2; ++e) {
+        const int c = c0 + 2 * e;
+        float f[2][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int p0 = bc4_p35_lut(b[q][e].x, b[q][e].y, shift[q], lut);
+          const int p1 = bc4_p35_lut(b[q][e].z, b[q][e].w, shift[q], lut);
+          if (p35) {
+            p35[q * CS + c] = p0;
+            p35[q * CS + c + 1] = p1;
+          }
+          f[0][q] = p35_value(p0);
+          f[1][q] = p35_value(p1);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          x[c + k] = gy * (gx * f[k][0] + fx * f[k][1]) + fy * (gx * f[k][2] + fx * f[k][3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CS; c += 2) {
+      float f[2][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 b = __ldg(line[q] + c / 2);
+        const int p0 = bc4_p35_lut(b.x, b.y, shift[q], lut);
+        const int p1 = bc4_p35_lut(b.z, b.w, shift[q], lut);
+        if (p35) {
+          p35[q * CS + c] = p0;
+          p35[q * CS + c + 1] = p1;
+        }
+        f[0][q] = p35_value(p0);
+        f[1][q] = p35_value(p1);
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        x[c + k] = gy * (gx * f[k][0] + fx * f[k][1]) + fy * (gx * f[k][2] + fx * f[k][3]);
+    }
   }
   int j0, j1;
   float a;

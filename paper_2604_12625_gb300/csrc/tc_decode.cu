@@ -490,7 +490,6 @@ struct PagesSmem {
 struct PageItem {
   ndgi_page_req r;
   int valid;          // 1 decode, 0 skip
-  int staged;         // 1 ring path, 0 direct per-texel gather
 };
 
 // Decodes feature rows r_from..r_to, columns fc0..fc0+ncols-1, into the ring:
@@ -567,9 +566,14 @@ __device__ __forceinline__ void a1_bias_words(uint32_t (&w)[K1 / 2]) {
   for (int j = CS / 2 + 1; j < K1 / 2; ++j) w[j] = 0u;
 }
 
+// staged (host-side plan flag): features are at most half the lightmap
+// resolution in every model of the plan, so each quadrant's feature rows are
+// decoded once into the ring; otherwise each texel gathers its taps directly
+// with the lighter gather (its register needs shape the whole kernel's
+// allocation, and the hot staged loop must not spill).
 template <int CS, int CT, int H, bool BF16, int NWG, int SL>
 __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, const ndgi_page_req* __restrict__ reqs,
-                                                                   const int32_t* __restrict__ n_dev) {
+                                                                   const int32_t* __restrict__ n_dev, int plan_staged) {
   using L = TcLayout<CS, CT, H>;
   using S = PagesSmem<CS, CT, H, NWG>;
   using E = Engine<H, BF16, L::K1G, SL>;
@@ -619,10 +623,6 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
                r.dst_x >= 0 && r.dst_y >= 0 && (int64_t)r.dst_x + r.w <= c.phys_w &&
                (int64_t)r.dst_y + r.h <= c.phys_h;
           if (!ok) atomicOr(c.error_word, 4);
-          // ring path when features are at most half the lightmap resolution: a
-          // 64-texel quadrant side then spans <= 34 feature columns and a batch
-          // of 8 output rows plus the look-ahead fits the 16-row ring
-          s_req.staged = 2 * mm.feat_w <= mm.lm_w && 2 * mm.feat_h <= mm.lm_h;
         }
         s_req.valid = ok;
       }
@@ -685,7 +685,9 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
         rowtab[t] = make_int4(ry0, ry1, __float_as_int(fy), 0);
       }
       lane_sync(wg);
-      const bool staged = s_req.staged && ncols <= kRingCols;
+      // at most half resolution: a 64-texel quadrant side spans <= 34 feature
+      // columns and two output rows plus the look-ahead fit the 16-row ring
+      const bool staged = plan_staged && ncols <= kRingCols;
       const int fr_last = rowtab[qh - 1].y;
       const __half2 wx1 = __float2half2_rn(fx), wx0 = __float2half2_rn(1.0f - fx);
       const int c0 = (cx0 - fc0) * 16, c1 = (cx1 - fc0) * 16;
@@ -739,8 +741,8 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
               ring_texel<CS, BF16, L::K1G>(w, ring, rowtab[orow], c0, c1, wx0, wx1);
             } else {
               float x[CS + CT];
-              gather_f32<CS, CT>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
-                                 ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr, lut);
+              gather_f32<CS, CT, false>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
+                                        ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr, lut);
 #pragma unroll
               for (int j = 0; j < CS / 2; ++j) w[j] = pack2<BF16>(x[2 * j], x[2 * j + 1]);
             }
@@ -823,6 +825,13 @@ cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream
   return cudaErrorInvalidValue;
 }
 
+// A tensor-core CTA allocates most of its SM's tensor memory for the whole
+// (persistent) kernel, so a second CTA placed on the same SM would block in
+// tcgen05.alloc until the first exits.  Asking for more than half of the
+// SM's shared memory keeps the placement at one CTA per SM.
+constexpr uint32_t kOneCtaPerSmSmem = 116 * 1024;
+constexpr uint32_t tc_smem(uint32_t need) { return need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem; }
+
 template <typename K>
 static cudaError_t set_smem(K kern, uint32_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -843,10 +852,10 @@ cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const
     using S = PointsSmem<A, B, C>;                                                                              \
     auto kern = bf16 ? k_points_tc<A, B, C, true, kPointsLanes, kPointsSlots>                                   \
                      : k_points_tc<A, B, C, false, kPointsLanes, kPointsSlots>;                                 \
-    cudaError_t e = set_smem(kern, S::kBytes);                                                                  \
+    cudaError_t e = set_smem(kern, tc_smem(S::kBytes));                                                         \
     if (e != cudaSuccess) return e;                                                                             \
-    kern<<<grid, kLaneThreads * kPointsLanes, S::kBytes, s>>>(m, static_cast<const unsigned char*>(ws), uvt, n,  \
-                                                              rgb);                                             \
+    kern<<<grid, kLaneThreads * kPointsLanes, tc_smem(S::kBytes), s>>>(m, static_cast<const unsigned char*>(ws), \
+                                                                       uvt, n, rgb);                            \
     return cudaGetLastError();                                                                                  \
   }
   NDGI_TC_SHAPES(X)
@@ -855,15 +864,15 @@ cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const
 }
 
 cudaError_t launch_tc_pages(const PagesCtx& c, bool bf16, int cs, int ct, int hidden, const TcPagesShape& shape,
-                            const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s) {
+                            bool staged, const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s) {
   const int grid = num_sms() * shape.ctas_per_sm;
 #define X(A, B, C, NW, SL)                                                                                      \
   if (cs == A && ct == B && hidden == C && shape.lanes == NW && shape.slots == SL) {                            \
     using S = PagesSmem<A, B, C, NW>;                                                                           \
     auto kern = bf16 ? k_pages_tc<A, B, C, true, NW, SL> : k_pages_tc<A, B, C, false, NW, SL>;                   \
-    cudaError_t e = set_smem(kern, S::kBytes);                                                                  \
+    cudaError_t e = set_smem(kern, tc_smem(S::kBytes));                                                         \
     if (e != cudaSuccess) return e;                                                                             \
-    kern<<<grid, kLaneThreads * NW, S::kBytes, s>>>(c, reqs, n_dev);                                            \
+    kern<<<grid, kLaneThreads * NW, tc_smem(S::kBytes), s>>>(c, reqs, n_dev, staged ? 1 : 0);                   \
     return cudaGetLastError();                                                                                  \
   }
   X(16, 8, 16, 4, 1) X(16, 8, 32, 4, 1) X(16, 8, 64, 4, 1) X(16, 16, 64, 4, 1)

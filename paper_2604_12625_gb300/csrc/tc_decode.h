@@ -19,8 +19,9 @@ size_t tc_workspace_bytes(int cs, int ct, int hidden);
 cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream_t s);
 cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const float* uvt, int64_t n, float* rgb,
                              cudaStream_t s);
+// staged: every model's features are at most half its lightmap resolution.
 cudaError_t launch_tc_pages(const PagesCtx& c, bool bf16, int cs, int ct, int hidden, const TcPagesShape& shape,
-                            const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s);
+                            bool staged, const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s);
 TcPagesShape tc_default_pages_shape();
 // Reads and clears the tensor-core kernels' device error word (-1 if unreadable).
 int tc_take_error();

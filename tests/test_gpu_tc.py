@@ -121,6 +121,21 @@ def test_tc_pages_ragged_and_zipf(ndgi, prec):
     plan.close()
 
 
+def test_tc_pages_full_resolution_features(ndgi):
+    # features at the lightmap's own resolution: the per-texel gather path
+    maps = [synth.model(60 + i, s, s, s, s, 16, 24, 8, 64, temporal_dtype="f16") for i, s in enumerate((256, 512))]
+    models = [ndgi.Model.from_arrays(m) for m in maps]
+    phys = torch.full((512, 512, 4), float("nan"), dtype=torch.float32, device="cuda")
+    plan = ndgi.PagesPlan(models, "fp16", 64, phys)
+    reqs = synth.ragged_page_requests(9, (256, 512), 12, slots_x=4, slot=128)
+    r, n = ndgi.page_requests_to_device(reqs)
+    plan.decode(r, n)
+    ndgi.ndgi_check()
+    ref = oracle.decode_pages(maps, reqs, 512, 512, precision="fp16")
+    assert page_err(phys.cpu().numpy(), ref, reqs) <= GATE["fp16"]
+    plan.close()
+
+
 def test_tc_pages_autotune_and_rgba16f(ndgi):
     maps = synth.page_models(42, sizes=SIZES, temporal_dtype="f16")
     models = [ndgi.Model.from_arrays(m) for m in maps]
@@ -129,6 +144,20 @@ def test_tc_pages_autotune_and_rgba16f(ndgi):
     reqs = synth.zipf_page_requests(7, SIZES, 64, page=128, slots_x=8)
     r, n = ndgi.page_requests_to_device(reqs)
     plan.autotune(r, n, len(reqs))
+    prec, cps, lanes, slots = plan.info()
+    assert prec == 1 and cps == 1 and lanes * slots <= 4
+    with pytest.raises(ndgi.NdgiError):
+        plan.set_shape(1, 3, 3)
+    with pytest.raises(ndgi.NdgiError):
+        plan.set_shape(2, 4, 1)
+    for shape in ((1, 2, 2), (1, 4, 1), (1, lanes, slots)):   # every built shape decodes the same texels
+        plan.set_shape(*shape)
+        assert plan.info()[1:] == shape
+        phys.zero_()
+        plan.decode(r, n)
+        ndgi.ndgi_check()
+        ref = oracle.decode_pages(maps, reqs, 1024, 1024, precision="fp16")
+        assert page_err(phys.float().cpu().numpy(), ref, reqs) <= 2e-3 + 2.0 ** -11 * 4
     phys.zero_()
     plan.decode(r, n)
     ndgi.ndgi_check()
