@@ -216,6 +216,88 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
     return out
 
 
+FIT_WORKLOAD = ("fit: 1024^2 x T=24 FP16 targets (32 Gaussians x sun term + 0.05), straight-through BC4 "
+                "512^2x16 features, temporal 24x8, MLP 24-64-64-3, Adam lr 1e-2, 2^20 samples/step, 2000 steps "
+                "(last 200 freeze the features)")
+
+
+def bench_fit(args, ndgi, torch):
+    """Differentiation: the full 2000-step fit, timed end to end on the device."""
+    targets = synth.fit_targets(3, 1024, 1024, 24)
+    p = synth.fit_init(3, 512, 512, 16, 24, 8, 64)
+    st = ndgi.FitState.from_arrays(p, 1024, 1024)
+    tg = torch.from_numpy(targets).cuda()
+    batch, steps = 1 << 20, 2000
+    # warm-up (graph capture, kernel load) on a throw-away copy of the parameters
+    warm = ndgi.FitState({k: v.clone() for k, v in st.t.items()}, 1024, 1024)
+    ndgi.ndgi_encode_fit(warm, tg, ndgi.fit_config(steps=3, batch=batch, seed=1))
+    torch.cuda.synchronize()
+    cfg = ndgi.fit_config(steps=steps, batch=batch, lr=1e-2, freeze_steps=200, loss_every=100, seed=7)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, log = ndgi.ndgi_encode_fit(st, tg, cfg)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    log = log.cpu().numpy()
+    rng = float(targets.max()) - float(targets.min())
+    return {"workload": FIT_WORKLOAD, "steps": steps, "batch": batch, "seconds": ms / 1e3,
+            "ms_per_step": ms / steps, "samples_per_s": steps * batch / (ms / 1e3),
+            "loss_first": float(log[0]), "loss_last": float(log[-1]),
+            "loss_every_100": [float(x) for x in log],
+            "psnr_db_last": float(10 * np.log10(rng * rng / max(log[-1], 1e-30))),
+            "device_check": check_status(ndgi)}
+
+
+SCALE_WORKLOAD = ("scale: 16384^2 atlas (268M texels) decoded at one t per frame as 128^2 pages; BC4 8192^2x16 "
+                  "(512 MiB), temporal 48x16 fp16, MLP 32-64-64-3; RGBA16F 16384^2 texture")
+
+
+def bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank):
+    m = synth.model(5, 16384, 16384, 8192, 8192, 16, 48, 16, 64, temporal_dtype="f16")
+    model = ndgi.Model.from_arrays(m)
+    n_side = 128
+    reqs = np.zeros(n_side * n_side, dtype=synth.PAGE_REQ_DTYPE)
+    for i in range(n_side * n_side):
+        x0, y0 = (i % n_side) * 128, (i // n_side) * 128
+        reqs[i] = (0, x0, y0, 128, 128, np.float32(0.37), x0, y0)
+    r_dev, n_dev = ndgi.page_requests_to_device(reqs)
+    phys = torch.empty((16384, 16384, 4), dtype=torch.float16, device="cuda")
+    texels = 16384 * 16384
+    out = {"workload": SCALE_WORKLOAD, "texels_per_frame": texels}
+    for prec in ("fp16", "fp32"):
+        plan = ndgi.PagesPlan([model], prec, len(reqs), phys)
+        if prec == "fp16":
+            plan.autotune(r_dev, n_dev, len(reqs))
+        steps = max(3, min(args.steps, 10)) if prec == "fp16" else 3
+        ms, _ = timed(lambda: plan.decode(r_dev, n_dev), steps, 2)
+        entry = {"value": texels / (ms / steps * 1e-3) / 1e9, "unit": "Gtexels/s", "ms_per_frame": ms / steps,
+                 "device_check": check_status(ndgi)}
+        if rank == 0:
+            import oracle
+            pick = np.random.default_rng(6).choice(len(reqs), 3, replace=False)
+            sub = reqs[pick]
+            got = phys.float().cpu().numpy()
+            ref = oracle.decode_pages([m], sub, 16384, 16384, precision="fp16" if prec == "fp16" else "fp32", fill=0.0)
+            worst = 0.0
+            for q in sub:
+                sl = (slice(q["dst_y"], q["dst_y"] + 128), slice(q["dst_x"], q["dst_x"] + 128))
+                a, b = got[sl][..., :3].astype(np.float64), ref[sl][..., :3]
+                worst = max(worst, float(np.abs(a - b).max() / (b.max() - b.min())))
+            entry["max_err_over_page_range"] = worst
+        out[prec] = entry
+        plan.close()
+    achieved = texels * PAGE_FLOP_PER_TEXEL / (out["fp16"]["ms_per_frame"] * 1e-3) / 1e12
+    out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                       "frac": achieved / peaks["bf16_tflops"], "kernel": "k_pages_tc",
+                       "peak_source": f"{peak_kind} bf16 burst (fp16 has the same dense rate)"}
+    out["fp8"] = "not built: FP8 E4M3 weights with per-layer scales are a later step"
+    del phys
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,6 +307,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp16", "bf16", "fp32"])
     ap.add_argument("--no-pages", action="store_true", help="skip the page-decode measurement")
+    ap.add_argument("--no-extra", action="store_true", help="skip the fit and scale measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -330,6 +413,10 @@ def main():
     pages = None
     if not args.no_pages:
         pages = bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank)
+    fit = scale = None
+    if not args.no_extra:
+        scale = bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank)
+        fit = bench_fit(args, ndgi, torch)
 
     if rank != 0:
         if dist is not None:
@@ -369,7 +456,7 @@ def main():
         "e2e": {"value": e2e_val, "unit": "Gtexels/s", "h2d_bytes_per_step": N_QUERIES * 12,
                 "d2h_bytes_per_step": N_QUERIES * 12},
         "gpu_launches": args.steps, "clocks": clocks,
-        "pages": pages,
+        "pages": pages, "scale": scale, "fit": fit,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
