@@ -37,6 +37,35 @@ WORKLOAD = "points 2^24 random (u,v,t); atlas 2048^2, BC4 1024^2x16, temporal 24
 METRIC = "Gtexels/s decoded (BC fetch+temporal lerp+MLP), FP16-TC vs FP32 plain @err"
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of a smaller case
+# of the same kernel, scaled to a full launch by the units processed.  Valid only while the kernel sources are
+# the ones captured: the hash below is compared at run time and the figure drops to null once they change.
+TRAFFIC_SOURCES = ("tc_decode.cu", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h")
+NCU_TRAFFIC = {
+    "k_points_tc": {"src": "6b9dfecde7717628", "read": 109112832, "write": 64917760, "units": 1 << 23,
+                    "profile": "profiles/k_points_tc_points_2048_atlas.md"},
+    "k_pages_tc": {"src": "6b9dfecde7717628", "read": 14556672, "write": 75104768, "units": 1024 * 128 * 128,
+                   "profile": "profiles/k_pages_tc_pages_8_lightmaps.md"},
+}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2604_12625_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, units):
+    """Scaled ncu DRAM bytes for one launch over `units` texels, or None if the kernel changed since capture."""
+    rec = NCU_TRAFFIC.get(kernel)
+    if rec is None or rec["src"] != kernel_source_hash():
+        return None
+    return (rec["read"] + rec["write"]) * units / rec["units"]
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -174,7 +203,7 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
     """Virtual-texture page decode: one step = one frame of 4096 page requests."""
     maps = synth.page_models(4)
     models = [ndgi.Model.from_arrays(m) for m in maps]
-    reqs = synth.zipf_page_requests(4, synth.PAGE_LIGHTMAP_SIZES, 4096, page=128, slots_x=64)
+    reqs = synth.zipf_page_requests(4, synth.PAGE_LIGHTMAP_SIZES, args.page_requests, page=128, slots_x=64)
     r_dev, n_dev = ndgi.page_requests_to_device(reqs)
     phys = torch.empty((8192, 8192, 4), dtype=torch.float16, device="cuda")
     texels = int(len(reqs)) * 128 * 128
@@ -207,11 +236,15 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
         plan.close()
     kernel_s = out["fp16"]["ms_per_frame"] * 1e-3
     achieved = texels * PAGE_FLOP_PER_TEXEL / kernel_s / 1e12
+    traffic = traffic_for("k_pages_tc", texels)
     out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                       "frac": achieved / peaks["bf16_tflops"], "traffic": None, "kernel": "k_pages_tc",
+                       "frac": achieved / peaks["bf16_tflops"], "traffic": traffic, "kernel": "k_pages_tc",
                        "peak_source": f"{peak_kind} bf16 burst (fp16 has the same dense rate)",
                        "flop_per_texel": PAGE_FLOP_PER_TEXEL}
-    out["workload"] = PAGES_WORKLOAD
+    if traffic is not None:
+        out["roofline"]["traffic_note"] = ("ncu DRAM bytes of a 1024-request frame scaled by texels; output lines "
+                                           "still dirty in L2 at kernel end are not counted")
+    out["workload"] = PAGES_WORKLOAD.replace("4096 Zipf", f"{args.page_requests} Zipf")
     out["texels_per_frame"] = texels
     return out
 
@@ -308,8 +341,13 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp16", "bf16", "fp32"])
     ap.add_argument("--no-pages", action="store_true", help="skip the page-decode measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the fit and scale measurements")
+    ap.add_argument("--queries-log2", type=int, default=24,
+                    help="point queries per step = 2^this (24 = the headline workload; smaller for profiling)")
+    ap.add_argument("--page-requests", type=int, default=4096,
+                    help="page requests per frame (4096 = the page workload; smaller for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    nq = 1 << args.queries_log2
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
@@ -329,10 +367,10 @@ def main():
 
     peaks, peak_kind = load_peaks()
     m = synth.points_model_2048(2)
-    q = synth.random_queries(2 + 1000 * rank, N_QUERIES)
+    q = synth.random_queries(2 + 1000 * rank, nq)
     model = ndgi.Model.from_arrays(m)
     uvt = torch.from_numpy(q).cuda()
-    out = torch.empty((N_QUERIES, 3), dtype=torch.float32, device="cuda")
+    out = torch.empty((nq, 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     tc = ndgi.ndgi_prepare_workspace_size(model, "fp16") > 0
@@ -377,18 +415,18 @@ def main():
     ms_main, clocks = timed(step_main, args.steps, args.warmup, sample_clocks=True)
     ms_step = ms_main / args.steps
     device_check = {"points": check_status(ndgi)}
-    value = world * N_QUERIES / (ms_step * 1e-3) / 1e9
+    value = world * nq / (ms_step * 1e-3) / 1e9
 
     # FP32 plain decode beside it (fewer steps: it is ~10x slower)
     k32 = max(3, min(args.steps, 20))
     ms32, _ = timed(step_fp32, k32, 3)
-    fp32_gt = world * N_QUERIES / (ms32 / k32 * 1e-3) / 1e9
+    fp32_gt = world * nq / (ms32 / k32 * 1e-3) / 1e9
 
     # Accuracy on a seeded sample, against the FP64 oracle (rank 0)
     errs = {}
     if rank == 0:
         import oracle
-        idx = np.random.default_rng(0).choice(N_QUERIES, 1 << 14, replace=False)
+        idx = np.random.default_rng(0).choice(nq, 1 << 14, replace=False)
         idx_t = torch.from_numpy(idx).cuda()
         for p in sorted({prec, "fp32"}):
             ndgi.ndgi_decode_points(model, uvt, p, ws=model.workspace(p), out=out)
@@ -399,7 +437,7 @@ def main():
     # End to end through the public API with host buffers: pinned H2D of the
     # step's queries, the decode, D2H of the result, all inside the timed region.
     q_host = torch.from_numpy(q).pin_memory()
-    out_host = torch.empty((N_QUERIES, 3), dtype=torch.float32).pin_memory()
+    out_host = torch.empty((nq, 3), dtype=torch.float32).pin_memory()
 
     def step_e2e():
         uvt.copy_(q_host, non_blocking=True)
@@ -408,7 +446,7 @@ def main():
 
     ke = max(3, min(args.steps, 20))
     ms_e2e, _ = timed(step_e2e, ke, 3)
-    e2e_val = world * N_QUERIES / (ms_e2e / ke * 1e-3) / 1e9
+    e2e_val = world * nq / (ms_e2e / ke * 1e-3) / 1e9
 
     pages = None
     if not args.no_pages:
@@ -427,34 +465,38 @@ def main():
     kernel_s = ms_step * 1e-3
     if prec == "fp32":
         peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0), torch.cuda.get_device_properties(local).multi_processor_count)
-        roof = {"bound": "alu", "achieved": N_QUERIES * FLOP_PER_TEXEL / kernel_s / 1e12, "peak": peak,
+        roof = {"bound": "alu", "achieved": nq * FLOP_PER_TEXEL / kernel_s / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "peak_source": "derived: SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
     else:
         peak = peaks["bf16_tflops"]
-        roof = {"bound": "tensor", "achieved": N_QUERIES * FLOP_PER_TEXEL / kernel_s / 1e12, "peak": peak,
+        roof = {"bound": "tensor", "achieved": nq * FLOP_PER_TEXEL / kernel_s / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "peak_source": f"{peak_kind} bf16 burst (fp16 has the same dense rate)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
     roof["kernel"] = "k_points_tc" if prec != "fp32" else "k_points_f32"
+    roof["traffic"] = traffic_for(roof["kernel"], nq)
+    if roof["traffic"] is not None:
+        roof["traffic_note"] = (f"ncu DRAM bytes of a 2^23-query launch scaled x{nq / (1 << 23):g}; output lines "
+                                "still dirty in L2 at kernel end are not counted; algorithmic "
+                                f"{(nq * 24 + (8 << 20)) / 1e6:.0f} MB")
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         gt, n_s, dt, nt = time_oracle(m, q, 12.0)
         cpu = {"value": gt, "unit": "Gtexels/s", "cores": nt, "kind": "oracle",
-               "sample": f"first {n_s} of the 2^24 queries, FP64 oracle ({dt:.1f} s)"}
+               "sample": f"first {n_s} of the 2^{args.queries_log2} queries, FP64 oracle ({dt:.1f} s)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "Gtexels/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp16": "f16", "bf16": "bf16", "fp32": "f32"}[prec], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "queries_per_rank": N_QUERIES, "precision": prec,
-                   "l2": "inputs larger than L2: 201 MB of queries + 201 MB of output per step; the 8 MiB "
-                         "feature map stays L2-resident as in a steady frame"},
+        "config": {"workload": WORKLOAD.replace("2^24", f"2^{args.queries_log2}"), "queries_per_rank": nq, "precision": prec,
+                   "l2": f"inputs larger than L2: {nq * 12 / 1e6:.0f} MB of queries + {nq * 12 / 1e6:.0f} MB of "
+                         "output per step; the 8 MiB feature map stays L2-resident as in a steady frame"},
         "device_check": device_check, "max_err_over_range": errs, "fp32_plain": {"value": fp32_gt, "unit": "Gtexels/s",
                                                   "err": errs.get("fp32")},
         "roofline": roof, "cpu_baseline": cpu,
-        "e2e": {"value": e2e_val, "unit": "Gtexels/s", "h2d_bytes_per_step": N_QUERIES * 12,
-                "d2h_bytes_per_step": N_QUERIES * 12},
+        "e2e": {"value": e2e_val, "unit": "Gtexels/s", "h2d_bytes_per_step": nq * 12,
+                "d2h_bytes_per_step": nq * 12},
         "gpu_launches": args.steps, "clocks": clocks,
         "pages": pages, "scale": scale, "fit": fit,
     }
