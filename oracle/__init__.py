@@ -8,7 +8,9 @@ marshals numpy arrays into it.
 
 Reduced-precision parity is measured against the *stored* parameters: for an
 FP16 or BF16 decode the MLP weights and biases are rounded to that format
-(round to nearest even) and then evaluated exactly in FP64 here.
+(round to nearest even) and then evaluated exactly in FP64 here.  The FP8
+(E4M3) page decode also quantises the activations at each layer input, with
+the power-of-two scales described in ndgi_oracle.c.
 """
 from __future__ import annotations
 
@@ -90,6 +92,14 @@ def lib():
             L.om_adam.argtypes = [vp, vp, vp, vp, i64, i32, f64, f64, f64, f64, i32]
             L.om_fit_draw.argtypes = [C.c_uint64, i64, i64, i64, i32, i32, i32, vp]
             L.om_max_hidden.restype = C.c_int
+            L.om_e4m3_batch.argtypes = [vp, i64, vp, vp]
+            L.om_p2.argtypes = [f64]
+            L.om_p2.restype = f64
+            L.om_fp8_scales.argtypes = [vp, vp, vp]
+            L.om_fp8_bias.argtypes = [vp, C.c_int, f64, vp, vp, vp]
+            L.om_fp8_weights.argtypes = [vp, vp, vp, vp, vp]
+            L.om_fp8_calibrate.argtypes = [vp, vp, i64, vp]
+            L.om_decode_pages_fp8.argtypes = [vp, vp, vp, i32, vp, i64, C.c_int]
             L.om_splitmix64_next.argtypes = [C.c_uint64]
             L.om_splitmix64_next.restype = C.c_uint64
             _lib = L
@@ -194,15 +204,83 @@ def decode_points(m, uvt, precision="fp32", nthreads=None):
     return y
 
 
-def decode_pages(models, reqs, phys_w, phys_h, precision="fp32", nthreads=None, fill=np.nan):
-    """FP64 RGBA physical texture [phys_h][phys_w][4]; untouched texels = fill."""
-    Ms = [_model(m, precision) for m in models]
-    arr = (_Model * len(Ms))(*[M.s for M in Ms])
+def decode_pages(models, reqs, phys_w, phys_h, precision="fp32", nthreads=None, fill=np.nan, act_max=None):
+    """FP64 RGBA physical texture [phys_h][phys_w][4]; untouched texels = fill.
+
+    precision "fp8": the E4M3 decode with scales from act_max ([n_models][3]
+    calibration maxima; see fp8_scales), evaluated on the FP32 master weights.
+    """
     r = np.ascontiguousarray(reqs)
     out = np.full((phys_h, phys_w, 4), fill, np.float64)
+    if precision == "fp8":
+        Ms = [_model(m, "fp32") for m in models]
+        arr = (_Model * len(Ms))(*[M.s for M in Ms])
+        am = _c(np.asarray(act_max, np.float64).reshape(len(Ms), 3), np.float64)
+        lib().om_decode_pages_fp8(arr, _ptr(am), r.ctypes.data_as(C.c_void_p), len(r), _ptr(out), phys_w,
+                                  nthreads or nthreads_default())
+        return out
+    Ms = [_model(m, precision) for m in models]
+    arr = (_Model * len(Ms))(*[M.s for M in Ms])
     lib().om_decode_pages(arr, len(Ms), r.ctypes.data_as(C.c_void_p), len(r), _ptr(out), phys_w, phys_h,
                           nthreads or nthreads_default())
     return out
+
+
+# --------------------------------------------------------------------------
+# FP8 E4M3 (see ndgi_oracle.c for the scale reading)
+# --------------------------------------------------------------------------
+
+def e4m3(x):
+    """Round to E4M3 (nearest, ties to even, saturating at +-448): (values, codes)."""
+    x = _c(np.asarray(x, np.float64).reshape(-1), np.float64)
+    y = np.zeros_like(x)
+    codes = np.zeros(x.shape, np.int32)
+    lib().om_e4m3_batch(_ptr(x), x.size, _ptr(y), _ptr(codes))
+    return y, codes
+
+
+def p2(y):
+    """Smallest power of two P with y <= 448 P."""
+    return float(lib().om_p2(float(y)))
+
+
+def fp8_scales(m, act_max):
+    """{a1, s1, a2, s2, a3, s3, out} of a model for calibration maxima (m1, m2, m3)."""
+    M = _model(m, "fp32")
+    am = _c(np.asarray(act_max, np.float64).reshape(3), np.float64)
+    sc = np.zeros(7, np.float64)
+    lib().om_fp8_scales(C.byref(M.s), _ptr(am), _ptr(sc))
+    return dict(zip(("a1", "s1", "a2", "s2", "a3", "s3", "out"), sc.tolist()))
+
+
+def fp8_weights(m, act_max):
+    """Stored FP8 weights s_l e4m3(W_l / s_l) as FP64 arrays shaped like w1, w2, w3."""
+    M = _model(m, "fp32")
+    am = _c(np.asarray(act_max, np.float64).reshape(3), np.float64)
+    sc = np.zeros(7, np.float64)
+    lib().om_fp8_scales(C.byref(M.s), _ptr(am), _ptr(sc))
+    out = {k: np.zeros(np.asarray(m[k]).shape, np.float64) for k in ("w1", "w2", "w3")}
+    lib().om_fp8_weights(C.byref(M.s), _ptr(sc), _ptr(out["w1"]), _ptr(out["w2"]), _ptr(out["w3"]))
+    return out
+
+
+def fp8_bias(b, u):
+    """Three-term E4M3 bias in units u: (terms [n][3], v, stored values)."""
+    b = _c(np.asarray(b, np.float64).reshape(-1), np.float64)
+    terms = np.zeros((b.size, 3), np.float64)
+    stored = np.zeros(b.size, np.float64)
+    v = C.c_double(0.0)
+    lib().om_fp8_bias(_ptr(b), b.size, float(u), _ptr(terms), C.byref(v), _ptr(stored))
+    return terms, v.value, stored
+
+
+def fp8_calibrate(m, uvt):
+    """Calibration maxima (max|x|, max relu(z1), max relu(z2)) of the FP64 decode at the queries."""
+    M = _model(m, "fp32")
+    q = _c(uvt, np.float32).reshape(-1, 3)
+    am = np.zeros(3, np.float64)
+    lib().om_fp8_calibrate(C.byref(M.s), _ptr(q), q.shape[0], _ptr(am))
+    return am
 
 
 def q255(e):

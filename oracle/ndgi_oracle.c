@@ -243,6 +243,196 @@ void om_decode_pages(const om_model *models, int32_t n_models, const om_page_req
 }
 
 /* ---------------------------------------------------------------------- */
+/* FP8 E4M3 decode (the largest configuration's reduced precision)          */
+/* ---------------------------------------------------------------------- */
+/*
+ * E4M3: 1 sign bit, 4 exponent bits (bias 7), 3 mantissa bits, no
+ * infinities; the largest finite magnitude is 1.75 * 2^8 = 448, exponent
+ * field 0 holds the subnormals m/8 * 2^-6.  Rounding is to nearest with ties
+ * to even, saturating at +-448 ("satfinite").
+ *
+ * Reading of the paper's "FP8 weights with per-layer scales" (the paper
+ * names the format only): every scale is a power of two, so rescaling is
+ * exact.  With act_max = (m1, m2, m3), the maxima of |layer-1 input|,
+ * relu(z1) and relu(z2) over a calibration set, and p2(y) the smallest
+ * power of two P with y <= 448 P (exact comparisons):
+ *   a1 = p2(m1);  s1 = p2(max(max|W1|, m2/a1));  a2 = a1 s1;
+ *   s2 = p2(max(max|W2|, m3/a2));  a3 = a2 s2;  s3 = p2(max|W3|).
+ * Weights are stored as s_l * e4m3(W_l / s_l); the input of layer l is
+ * quantised as a_l * e4m3(x / a_l), so a layer's accumulator is already in
+ * the next layer's activation units.  A bias b of a layer whose output unit
+ * is u (a2, a3, a3 s3) is stored as u * v * (t1 + t2 + t3): beta = b / u,
+ * v = max(1, p2(max|beta| over the layer)), t1 = e4m3(beta/v),
+ * t2 = e4m3(beta/v - t1), t3 = e4m3(beta/v - t1 - t2).
+ */
+double om_e4m3(double x) {
+  if (isnan(x)) return x;
+  const double a = fabs(x);
+  double r;
+  if (a >= 448.0) {
+    r = 448.0;
+  } else {
+    int e;
+    frexp(a, &e);                               /* a = f * 2^e, f in [0.5, 1) */
+    const int ex = e - 1;                       /* a in [2^ex, 2^(ex+1))      */
+    const double q = ex < -6 ? ldexp(1.0, -9) : ldexp(1.0, ex - 3);   /* spacing */
+    r = nearbyint(a / q) * q;                   /* default mode: ties to even */
+  }
+  return signbit(x) ? -r : r;
+}
+
+int om_e4m3_code(double x) {
+  if (isnan(x)) return 0x7F;
+  const double v = fabs(om_e4m3(x));
+  int code;
+  if (v < ldexp(1.0, -6)) {
+    code = (int)(v / ldexp(1.0, -9));
+  } else {
+    int e;
+    const double f = frexp(v, &e);             /* v = f 2^e, f in [0.5, 1) */
+    code = ((e - 1 + 7) << 3) | (int)(f * 16.0 - 8.0);
+  }
+  return (signbit(x) ? 0x80 : 0) | code;
+}
+
+void om_e4m3_batch(const double *x, int64_t n, double *y, int32_t *codes) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (y) y[i] = om_e4m3(x[i]);
+    if (codes) codes[i] = om_e4m3_code(x[i]);
+  }
+}
+
+/* Smallest power of two P with y <= 448 P (1 for y <= 0). */
+double om_p2(double y) {
+  if (!(y > 0.0)) return 1.0;
+  int e;
+  frexp(y / 448.0, &e);
+  double P = ldexp(1.0, e);
+  while (y > 448.0 * P) P *= 2.0;
+  while (y <= 448.0 * (P * 0.5)) P *= 0.5;
+  return P;
+}
+
+/* scales = {a1, s1, a2, s2, a3, s3, out = a3 s3} */
+void om_fp8_scales(const om_model *m, const double *act_max, double *scales) {
+  const int cin = m->cs + m->ct, H = m->hidden;
+  double w1 = 0, w2 = 0, w3 = 0;
+  for (int i = 0; i < cin * H; ++i) w1 = fmax(w1, fabs(m->w1[i]));
+  for (int i = 0; i < H * H; ++i) w2 = fmax(w2, fabs(m->w2[i]));
+  for (int i = 0; i < H * 3; ++i) w3 = fmax(w3, fabs(m->w3[i]));
+  const double a1 = om_p2(act_max[0]);
+  const double s1 = om_p2(fmax(w1, act_max[1] / a1)), a2 = a1 * s1;
+  const double s2 = om_p2(fmax(w2, act_max[2] / a2)), a3 = a2 * s2;
+  const double s3 = om_p2(w3);
+  scales[0] = a1; scales[1] = s1; scales[2] = a2; scales[3] = s2; scales[4] = a3; scales[5] = s3;
+  scales[6] = a3 * s3;
+}
+
+/* Three-term E4M3 bias of n outputs in units u: terms [n][3], v; returns the stored values. */
+void om_fp8_bias(const double *b, int n, double u, double *terms, double *v_out, double *stored) {
+  double bmax = 0.0;
+  for (int i = 0; i < n; ++i) bmax = fmax(bmax, fabs(b[i] / u));
+  const double v = fmax(1.0, om_p2(bmax));
+  for (int i = 0; i < n; ++i) {
+    const double r0 = b[i] / u / v;
+    const double t1 = om_e4m3(r0), t2 = om_e4m3(r0 - t1), t3 = om_e4m3(r0 - t1 - t2);
+    if (terms) { terms[3 * i] = t1; terms[3 * i + 1] = t2; terms[3 * i + 2] = t3; }
+    if (stored) stored[i] = u * v * (t1 + t2 + t3);
+  }
+  if (v_out) *v_out = v;
+}
+
+/* Stored FP8 weights s_l e4m3(W_l / s_l), [in][out], for the three layers. */
+void om_fp8_weights(const om_model *m, const double *scales, double *w1q, double *w2q, double *w3q) {
+  const int cin = m->cs + m->ct, H = m->hidden;
+  for (int i = 0; i < cin * H; ++i) w1q[i] = scales[1] * om_e4m3(m->w1[i] / scales[1]);
+  for (int i = 0; i < H * H; ++i) w2q[i] = scales[3] * om_e4m3(m->w2[i] / scales[3]);
+  for (int i = 0; i < H * 3; ++i) w3q[i] = scales[5] * om_e4m3(m->w3[i] / scales[5]);
+}
+
+/* Calibration maxima (m1, m2, m3) of the FP64 decode at the given queries. */
+void om_fp8_calibrate(const om_model *m, const float *uvt, int64_t n, double *act_max) {
+  const int cin = m->cs + m->ct, H = m->hidden;
+  double m1 = 0, m2 = 0, m3 = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double x[512], h1[256], h2[256];
+    om_features(m, (double)uvt[3 * i], (double)uvt[3 * i + 1], (double)uvt[3 * i + 2], x, NULL);
+    om_dense(x, cin, m->w1, m->b1, H, 1, h1);
+    om_dense(h1, H, m->w2, m->b2, H, 1, h2);
+    for (int k = 0; k < cin; ++k) m1 = fmax(m1, fabs(x[k]));
+    for (int k = 0; k < H; ++k) { m2 = fmax(m2, h1[k]); m3 = fmax(m3, h2[k]); }
+  }
+  act_max[0] = m1; act_max[1] = m2; act_max[2] = m3;
+}
+
+/*
+ * FP8 page decode.  As in the reduced-precision page path, t is constant per
+ * request, so layer 1's temporal part is folded into a per-request bias:
+ * b1' = b1 + sum_c W1q[cs+c] vtq[c] with vtq = a1 e4m3(v_t / a1) (the same
+ * value the unfused layer would see), then b1' is stored as three E4M3
+ * terms in units a2 like the other biases.  The spatial features are
+ * quantised a1 e4m3(x / a1).  act_max: [n_models][3].
+ */
+void om_decode_pages_fp8(const om_model *models, const double *act_max, const om_page_req *reqs, int32_t n,
+                         double *phys, int64_t phys_w, int nthreads) {
+  for (int32_t r = 0; r < n; ++r) {
+    const om_page_req *q = &reqs[r];
+    const om_model *m = &models[q->model];
+    const int cs = m->cs, ct = m->ct, cin = cs + ct, H = m->hidden;
+    double sc[7];
+    om_fp8_scales(m, act_max + 3 * q->model, sc);
+    double *w1q = malloc(sizeof(double) * (size_t)cin * H), *w2q = malloc(sizeof(double) * (size_t)H * H);
+    double *w3q = malloc(sizeof(double) * (size_t)H * 3);
+    double b1s[256], b2s[256], b3s[3];
+    om_fp8_weights(m, sc, w1q, w2q, w3q);
+    om_fp8_bias(m->b2, H, sc[4], NULL, NULL, b2s);
+    om_fp8_bias(m->b3, 3, sc[6], NULL, NULL, b3s);
+    /* temporal term at the request's t (the features at any texel carry it) */
+    {
+      double x[512];
+      om_features(m, 0.5, 0.5, (double)q->t, x, NULL);
+      double b1f[256];
+      for (int o = 0; o < H; ++o) {
+        double z = m->b1[o];
+        for (int c = 0; c < ct; ++c) z += sc[0] * om_e4m3(x[cs + c] / sc[0]) * w1q[(size_t)(cs + c) * H + o];
+        b1f[o] = z;
+      }
+      om_fp8_bias(b1f, H, sc[2], NULL, NULL, b1s);
+    }
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int32_t jj = 0; jj < q->h; ++jj) {
+      double x[512], h1[256], h2[256];
+      for (int32_t ii = 0; ii < q->w; ++ii) {
+        const double u = ((double)(q->x0 + ii) + 0.5) / (double)m->lm_w;
+        const double v = ((double)(q->y0 + jj) + 0.5) / (double)m->lm_h;
+        om_features(m, u, v, (double)q->t, x, NULL);
+        for (int k = 0; k < cs; ++k) x[k] = sc[0] * om_e4m3(x[k] / sc[0]);
+        for (int o = 0; o < H; ++o) {
+          double z = b1s[o];
+          for (int k = 0; k < cs; ++k) z += x[k] * w1q[(size_t)k * H + o];
+          h1[o] = z > 0.0 ? sc[2] * om_e4m3(z / sc[2]) : 0.0;
+        }
+        for (int o = 0; o < H; ++o) {
+          double z = b2s[o];
+          for (int k = 0; k < H; ++k) z += h1[k] * w2q[(size_t)k * H + o];
+          h2[o] = z > 0.0 ? sc[4] * om_e4m3(z / sc[4]) : 0.0;
+        }
+        double *o = phys + ((int64_t)(q->dst_y + jj) * phys_w + (q->dst_x + ii)) * 4;
+        for (int c = 0; c < 3; ++c) {
+          double z = b3s[c];
+          for (int k = 0; k < H; ++k) z += h2[k] * w3q[(size_t)k * 3 + c];
+          o[c] = z;
+        }
+        o[3] = 1.0;
+      }
+    }
+    free(w1q);
+    free(w2q);
+    free(w3q);
+  }
+}
+
+/* ---------------------------------------------------------------------- */
 /* BC simulation quantisers and block packing (Eq. 6-7, end of Sec. 3.4)   */
 /* ---------------------------------------------------------------------- */
 
