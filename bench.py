@@ -284,7 +284,8 @@ def bench_fit(args, ndgi, torch):
 
 
 SCALE_WORKLOAD = ("scale: 16384^2 atlas (268M texels) decoded at one t per frame as 128^2 pages; BC4 8192^2x16 "
-                  "(512 MiB), temporal 48x16 fp16, MLP 32-64-64-3; RGBA16F 16384^2 texture")
+                  "(512 MiB), temporal 48x16 fp16, MLP 32-64-64-3 in FP16, FP8 E4M3 (per-layer power-of-two "
+                  "scales) and FP32; RGBA16F 16384^2 texture")
 
 
 def bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank):
@@ -299,33 +300,50 @@ def bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank):
     phys = torch.empty((16384, 16384, 4), dtype=torch.float16, device="cuda")
     texels = 16384 * 16384
     out = {"workload": SCALE_WORKLOAD, "texels_per_frame": texels}
-    for prec in ("fp16", "fp32"):
+    act_max = None
+    for prec in ("fp16", "fp8", "fp32"):
+        if prec == "fp8":
+            # per-layer FP8 scales from the library's own FP32 calibration pass over 2^16 seeded queries
+            cal = torch.from_numpy(synth.random_queries(7, 1 << 16)).cuda()
+            act_max = ndgi.ndgi_calibrate_fp8(model, cal).cpu().numpy().astype(np.float64)
+            ndgi.ndgi_prepare_fp8(model, act_max)
         plan = ndgi.PagesPlan([model], prec, len(reqs), phys)
-        if prec == "fp16":
+        if prec != "fp32":
             plan.autotune(r_dev, n_dev, len(reqs))
-        steps = max(3, min(args.steps, 10)) if prec == "fp16" else 3
+        steps = max(3, min(args.steps, 10)) if prec != "fp32" else 3
         ms, _ = timed(lambda: plan.decode(r_dev, n_dev), steps, 2)
         entry = {"value": texels / (ms / steps * 1e-3) / 1e9, "unit": "Gtexels/s", "ms_per_frame": ms / steps,
-                 "device_check": check_status(ndgi)}
+                 "device_check": check_status(ndgi), "plan_shape": plan.info()}
         if rank == 0:
             import oracle
             pick = np.random.default_rng(6).choice(len(reqs), 3, replace=False)
             sub = reqs[pick]
             got = phys.float().cpu().numpy()
-            ref = oracle.decode_pages([m], sub, 16384, 16384, precision="fp16" if prec == "fp16" else "fp32", fill=0.0)
-            worst = 0.0
-            for q in sub:
-                sl = (slice(q["dst_y"], q["dst_y"] + 128), slice(q["dst_x"], q["dst_x"] + 128))
-                a, b = got[sl][..., :3].astype(np.float64), ref[sl][..., :3]
-                worst = max(worst, float(np.abs(a - b).max() / (b.max() - b.min())))
-            entry["max_err_over_page_range"] = worst
+            refs = {"oracle": oracle.decode_pages([m], sub, 16384, 16384, precision=prec, fill=0.0,
+                                                  act_max=None if act_max is None else act_max[None])}
+            if prec == "fp8":
+                refs["fp32_master"] = oracle.decode_pages([m], sub, 16384, 16384, precision="fp32", fill=0.0)
+            for key, ref in refs.items():
+                worst = rms = 0.0
+                for q in sub:
+                    sl = (slice(q["dst_y"], q["dst_y"] + 128), slice(q["dst_x"], q["dst_x"] + 128))
+                    a, b = got[sl][..., :3].astype(np.float64), ref[sl][..., :3]
+                    rng_ = b.max() - b.min()
+                    worst = max(worst, float(np.abs(a - b).max() / rng_))
+                    rms = max(rms, float(np.sqrt(((a - b) ** 2).mean()) / rng_))
+                name = "max_err_over_page_range" if key == "oracle" else "vs_fp32_master_max_err"
+                entry[name] = worst
+                entry[name.replace("max_err", "rms_err")] = rms
+            if prec == "fp8":
+                entry["act_max"] = act_max.tolist()
+                entry["err_note"] = ("oracle = the FP8 decode with the same scales (E4M3 rounding of activations "
+                                     "computed in different arithmetic may flip); fp32_master = the unquantised model")
         out[prec] = entry
         plan.close()
     achieved = texels * PAGE_FLOP_PER_TEXEL / (out["fp16"]["ms_per_frame"] * 1e-3) / 1e12
     out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                        "frac": achieved / peaks["bf16_tflops"], "kernel": "k_pages_tc",
                        "peak_source": f"{peak_kind} bf16 burst (fp16 has the same dense rate)"}
-    out["fp8"] = "not built: FP8 E4M3 weights with per-layer scales are a later step"
     del phys
     torch.cuda.empty_cache()
     return out

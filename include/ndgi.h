@@ -53,7 +53,8 @@ typedef enum {
   NDGI_FP32 = 0,              /* plain FP32 CUDA-core decode               */
   NDGI_FP16 = 1,              /* tcgen05 tensor cores, FP16 operands, FP32 accumulate */
   NDGI_BF16 = 2,              /* tcgen05 tensor cores, BF16 operands, FP32 accumulate */
-  NDGI_FP8_E4M3 = 3           /* reserved                                  */
+  NDGI_FP8_E4M3 = 3           /* tcgen05 kind::f8f6f4, E4M3 weights and activations, FP32 accumulate
+                                 (page decode only; prepared with ndgi_prepare_fp8) */
 } ndgi_precision;
 
 /*
@@ -120,6 +121,48 @@ ndgi_status ndgi_prepare(const ndgi_model_desc *model, ndgi_precision precision,
                          void *stream);
 
 /*
+ * FP8 calibration for ndgi_prepare_fp8: runs the FP32 decode at the n
+ * queries uvt [n][3] (device) and writes act_max[0..2] (device, 3 floats) =
+ * the maxima of |layer-1 input| (spatial and temporal features), relu(z1) and
+ * relu(z2) over them.  Asynchronous on `stream`.
+ */
+ndgi_status ndgi_calibrate_fp8(const ndgi_model_desc *model, const float *uvt, int64_t n, float *act_max,
+                               void *stream);
+
+/*
+ * Packs the model for the FP8 (E4M3) page decode.  The paper names FP8
+ * weights with per-layer scales but not their choice; this library uses
+ * powers of two throughout, so that each layer's FP32 accumulator is already
+ * in the next layer's activation unit.  With act_max = (m1, m2, m3) (host
+ * array, e.g. copied from ndgi_calibrate_fp8) and p2(y) the smallest power
+ * of two P with y <= 448 P:
+ *   a1 = p2(m1), s1 = p2(max(max|W1|, m2/a1)), a2 = a1 s1,
+ *   s2 = p2(max(max|W2|, m3/a2)), a3 = a2 s2, s3 = p2(max|W3|).
+ * Stored weights are s_l e4m3(W_l / s_l) (round to nearest even,
+ * saturating); layer inputs are quantised as a_l e4m3(x / a_l); a bias b of
+ * a layer with output unit u (a2, a3, a3 s3) is stored as u v (t1 + t2 + t3),
+ * three E4M3 terms of b/(u v) with v = max(1, p2(max|b/u|)).  For pages the
+ * layer-1 temporal term (quantised v_t) is folded per request into b1'.
+ * ws: device, >= ndgi_prepare_workspace_size(model, NDGI_FP8_E4M3) bytes,
+ * 256-byte aligned.  Synchronises `stream` to read the image's status:
+ * NDGI_ERR_UNSUPPORTED if a bias needs v > 256 or 1/a1 > 2^14.  Shapes:
+ * cs = 16 and hidden a multiple of 32.
+ */
+ndgi_status ndgi_prepare_fp8(const ndgi_model_desc *model, const float act_max[3], void *ws, size_t ws_bytes,
+                             void *stream);
+
+/*
+ * Validation helper: the parameters an FP8 image stores, as FP32 values in
+ * out (host): [16] header {a1, a2, a3, out = a3 s3, s1, s2, s3, v2, v3,
+ * status, 0...}, then W1 [cs+ct][hidden] (spatial rows s1 * E4M3; temporal
+ * rows the stored FP32 values), W2 [hidden][hidden], W3 [hidden][3], b2
+ * [hidden], b3 [3].  *needed (may be NULL) receives the float count; out ==
+ * NULL only queries it.  Copies ws (device) synchronously.
+ */
+ndgi_status ndgi_fp8_unpack(const ndgi_model_desc *model, const void *ws, float *out, size_t out_len,
+                            size_t *needed);
+
+/*
  * Random-access point decode (Sec. 3.1, Eq. 3; Sec. 5.5 decodes this way):
  * for each i < n, rgb[i] = H(u_i, v_i, t_i).
  *   uvt  [n][3] FP32 (u, v, t); rgb [n][3] FP32 output.
@@ -184,7 +227,9 @@ ndgi_status ndgi_pages_plan_create(const ndgi_model_desc *models, const void *co
  * sizes outside 1..128, rectangles outside the lightmap or the physical
  * texture) are skipped; *n_dev < 0 or > max_reqs rejects the whole frame.
  * Both are latched in the plan's error word (bit 0: count, bit 1: model or
- * size, bit 2: rectangle), which ndgi_pages_check reads.  The graph is
+ * size, bit 2: rectangle; FP8 plans also bit 3: a request's folded bias
+ * needed a ones value above 256 and was clamped), which ndgi_pages_check
+ * reads.  The graph is
  * rebuilt when reqs_dev or n_dev differ from the previous call.  Requests
  * with overlapping destinations race.
  */

@@ -60,6 +60,9 @@ SIGNATURES = [
     ("ndgi_check", C.c_int, [_vp]),
     ("ndgi_prepare_workspace_size", _sz, [_vp, C.c_int]),
     ("ndgi_prepare", C.c_int, [_vp, C.c_int, _vp, _sz, _vp]),
+    ("ndgi_calibrate_fp8", C.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    ("ndgi_prepare_fp8", C.c_int, [_vp, _vp, _vp, _sz, _vp]),
+    ("ndgi_fp8_unpack", C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     ("ndgi_decode_points", C.c_int, [_vp, C.c_int, _vp, _vp, _i64, _vp, _vp]),
     ("ndgi_debug_features", C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     ("ndgi_pages_plan_create", C.c_int, [_vp, _vp, _i32, C.c_int, _i32, _i32, _vp, _i64, _i64, _vp]),

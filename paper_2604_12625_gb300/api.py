@@ -77,6 +77,8 @@ class Model:
         if precision == A.NDGI_FP32:
             return None
         if precision not in self.ws:
+            if precision == A.NDGI_FP8_E4M3:
+                raise ValueError("the FP8 workspace needs calibration maxima: call ndgi_prepare_fp8 first")
             self.ws[precision] = ndgi_prepare(self, precision)
         return self.ws[precision]
 
@@ -100,6 +102,48 @@ def ndgi_prepare(model, precision, ws=None, stream=None):
         ws = torch.empty(max(n, 256), dtype=torch.uint8, device=model.bc4.device)
     check(lib().ndgi_prepare(C.byref(model.desc), _prec(precision), _p(ws), ws.numel(), _stream(stream)))
     return ws
+
+
+def ndgi_calibrate_fp8(model, uvt, act_max=None, stream=None):
+    """Maxima (|layer-1 input|, relu(z1), relu(z2)) of the FP32 decode at the queries: float32 [3] on the GPU."""
+    uvt = _need(uvt, torch.float32, "uvt")
+    if act_max is None:
+        act_max = torch.empty(3, dtype=torch.float32, device=uvt.device)
+    _need(act_max, torch.float32, "act_max")
+    check(lib().ndgi_calibrate_fp8(C.byref(model.desc), _p(uvt), uvt.shape[0], _p(act_max), _stream(stream)))
+    return act_max
+
+
+def ndgi_prepare_fp8(model, act_max, ws=None, stream=None):
+    """Packs the FP8 (E4M3) page-decode image from calibration maxima (3 values, any host or CUDA array);
+    the workspace is kept as the model's FP8 workspace and returned."""
+    am = torch.as_tensor(act_max, dtype=torch.float32).detach().cpu().numpy().reshape(3)
+    arr = (C.c_float * 3)(*[float(x) for x in am])
+    n = ndgi_prepare_workspace_size(model, A.NDGI_FP8_E4M3)
+    if ws is None:
+        ws = torch.empty(max(n, 256), dtype=torch.uint8, device=model.bc4.device)
+    check(lib().ndgi_prepare_fp8(C.byref(model.desc), arr, _p(ws), ws.numel(), _stream(stream)))
+    model.ws[A.NDGI_FP8_E4M3] = ws
+    return ws
+
+
+def ndgi_fp8_unpack(model, ws=None):
+    """The stored FP8 parameters as float32 numpy arrays: scales, w1, w2, w3, b2, b3."""
+    ws = ws if ws is not None else model.workspace(A.NDGI_FP8_E4M3)
+    need = C.c_size_t(0)
+    check(lib().ndgi_fp8_unpack(C.byref(model.desc), _p(ws), None, 0, C.byref(need)))
+    out = np.zeros(need.value, np.float32)
+    check(lib().ndgi_fp8_unpack(C.byref(model.desc), _p(ws), out.ctypes.data_as(C.c_void_p), out.size, None))
+    H, cin = model.hidden, model.cs + model.ct
+    head = out[:16]
+    o = 16
+    parts = {}
+    for k, shape in (("w1", (cin, H)), ("w2", (H, H)), ("w3", (H, 3)), ("b2", (H,)), ("b3", (3,))):
+        size = int(np.prod(shape))
+        parts[k] = out[o:o + size].reshape(shape)
+        o += size
+    parts["scales"] = dict(zip(("a1", "a2", "a3", "out", "s1", "s2", "s3", "v2", "v3", "status"), head[:10].tolist()))
+    return parts
 
 
 def ndgi_decode_points(model, uvt, precision="fp32", ws=None, out=None, stream=None):

@@ -100,7 +100,67 @@ ndgi_status ndgi_check(void* stream) {
 size_t ndgi_prepare_workspace_size(const ndgi_model_desc* model, ndgi_precision precision) {
   if (!model) return 0;
   if (precision == NDGI_FP16 || precision == NDGI_BF16) return tc_workspace_bytes(model->cs, model->ct, model->hidden);
+  if (precision == NDGI_FP8_E4M3) return tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden);
   return 0;
+}
+
+ndgi_status ndgi_calibrate_fp8(const ndgi_model_desc* model, const float* uvt, int64_t n, float* act_max,
+                               void* stream) {
+  ndgi_status st = check_model(model, "ndgi_calibrate_fp8");
+  if (st != NDGI_OK) return st;
+  if (n <= 0 || !uvt || !act_max || !aligned(uvt, 4) || !aligned(act_max, 4))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_calibrate_fp8: need n > 0 queries and a 3-float act_max");
+  if (!simt_supported(model->cs, model->ct, model->hidden))
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_calibrate_fp8: shape cs=%d ct=%d hidden=%d not built", model->cs,
+                     model->ct, model->hidden);
+  return cuda_status(launch_fp8_calibrate(to_dev(*model), uvt, n, act_max, (cudaStream_t)stream),
+                     "ndgi_calibrate_fp8");
+}
+
+ndgi_status ndgi_prepare_fp8(const ndgi_model_desc* model, const float act_max[3], void* ws, size_t ws_bytes,
+                             void* stream) {
+  ndgi_status st = check_model(model, "ndgi_prepare_fp8");
+  if (st != NDGI_OK) return st;
+  if (!act_max) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_prepare_fp8: act_max is NULL");
+  for (int i = 0; i < 3; ++i)
+    if (!(act_max[i] >= 0.0f && act_max[i] <= 3.0e38f))
+      return set_error(NDGI_ERR_INVALID_ARG, "ndgi_prepare_fp8: act_max[%d] must be finite and >= 0", i);
+  if (!tc_fp8_pages_supported(model->cs, model->ct, model->hidden))
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_prepare_fp8: FP8 shape cs=%d ct=%d hidden=%d not built (cs = 16, "
+                     "hidden a multiple of 32)", model->cs, model->ct, model->hidden);
+  const size_t need = tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden);
+  if (!ws || ws_bytes < need || !aligned(ws, 256))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_prepare_fp8: ws must be 256-byte aligned with >= %zu bytes", need);
+  cudaStream_t s = (cudaStream_t)stream;
+  st = cuda_status(launch_tc_prepare8(to_dev(*model), act_max, ws, s), "ndgi_prepare_fp8");
+  if (st != NDGI_OK) return st;
+  uint32_t status = 0;
+  const unsigned char* sp = static_cast<const unsigned char*>(ws) + tc_fp8_status_offset(model->cs, model->ct,
+                                                                                         model->hidden);
+  cudaError_t e = cudaMemcpyAsync(&status, sp, sizeof status, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, "ndgi_prepare_fp8: status read");
+  if (status & 1u)
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_prepare_fp8: a bias is too large for its layer's output unit");
+  if (status & 2u)
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_prepare_fp8: act_max[0] too small (1/a1 above 2^14)");
+  return NDGI_OK;
+}
+
+ndgi_status ndgi_fp8_unpack(const ndgi_model_desc* model, const void* ws, float* out, size_t out_len,
+                            size_t* needed) {
+  if (!model || !ws) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fp8_unpack: NULL argument");
+  const size_t bytes = tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden);
+  if (!bytes) return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_fp8_unpack: no FP8 image for this shape");
+  const size_t n = tc_fp8_unpack(model->cs, model->ct, model->hidden, nullptr, nullptr, 0);
+  if (needed) *needed = n;
+  if (!out) return NDGI_OK;
+  if (out_len < n) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fp8_unpack: out needs %zu floats", n);
+  std::vector<unsigned char> img(bytes);
+  cudaError_t e = cudaMemcpy(img.data(), ws, bytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e, "ndgi_fp8_unpack: copy");
+  tc_fp8_unpack(model->cs, model->ct, model->hidden, img.data(), out, out_len);
+  return NDGI_OK;
 }
 
 ndgi_status ndgi_prepare(const ndgi_model_desc* model, ndgi_precision precision, void* ws, size_t ws_bytes,
@@ -108,6 +168,8 @@ ndgi_status ndgi_prepare(const ndgi_model_desc* model, ndgi_precision precision,
   ndgi_status st = check_model(model, "ndgi_prepare");
   if (st != NDGI_OK) return st;
   if (precision == NDGI_FP32) return NDGI_OK;
+  if (precision == NDGI_FP8_E4M3)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_prepare: FP8 needs calibration maxima; use ndgi_prepare_fp8");
   if (precision != NDGI_FP16 && precision != NDGI_BF16)
     return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_prepare: precision %d not supported", (int)precision);
   if (!tc_supported(model->cs, model->ct, model->hidden))
@@ -141,6 +203,8 @@ ndgi_status ndgi_decode_points(const ndgi_model_desc* model, ndgi_precision prec
     return cuda_status(launch_tc_points(m, precision == NDGI_BF16, ws, uvt, n, rgb, (cudaStream_t)stream),
                        "ndgi_decode_points");
   }
+  if (precision == NDGI_FP8_E4M3)
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_decode_points: FP8 is built for the page decode only");
   return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_decode_points: precision %d not supported", (int)precision);
 }
 
@@ -198,8 +262,8 @@ static cudaError_t enqueue_pages(ndgi_pages_plan* p, const ndgi_page_req* reqs, 
   if (e != cudaSuccess) return e;
   if (p->precision == NDGI_FP32)
     return launch_pages_f32(p->ctx, p->cs, p->ct, p->hidden, reqs, n_dev, p->simt_grid, s);
-  return launch_tc_pages(p->ctx, p->precision == NDGI_BF16, p->cs, p->ct, p->hidden, p->shape, p->staged, reqs,
-                         n_dev, s);
+  const int prec = p->precision == NDGI_BF16 ? 1 : (p->precision == NDGI_FP8_E4M3 ? 2 : 0);
+  return launch_tc_pages(p->ctx, prec, p->cs, p->ct, p->hidden, p->shape, p->staged, reqs, n_dev, s);
 }
 
 static ndgi_status ensure_graph(ndgi_pages_plan* p, const ndgi_page_req* reqs, const int32_t* n_dev) {
@@ -246,8 +310,10 @@ ndgi_status ndgi_pages_plan_create(const ndgi_model_desc* models, const void* co
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_create: bad out_format");
   if (!phys || phys_w <= 0 || phys_h <= 0 || !aligned(phys, 16))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_create: phys must be a 16-byte aligned texture");
-  if (precision != NDGI_FP32 && precision != NDGI_FP16 && precision != NDGI_BF16)
+  if (precision != NDGI_FP32 && precision != NDGI_FP16 && precision != NDGI_BF16 && precision != NDGI_FP8_E4M3)
     return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_pages_plan_create: precision %d not supported", (int)precision);
+  if (precision == NDGI_FP8_E4M3 && !tc_fp8_pages_supported(models[0].cs, models[0].ct, models[0].hidden))
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_pages_plan_create: FP8 needs cs = 16 and hidden a multiple of 32");
   for (int i = 0; i < n_models; ++i) {
     ndgi_status st = check_model(&models[i], "ndgi_pages_plan_create");
     if (st != NDGI_OK) return st;

@@ -197,6 +197,56 @@ __global__ void __launch_bounds__(kSimtThreads) k_pages_f32(PagesCtx c, const nd
 
 // ---------------------------------------------------------------------------
 // Dispatch over the built (cs, ct, hidden) shapes.
+// FP8 calibration: the maxima of |layer-1 input|, relu(z1) and relu(z2) of the
+// FP32 decode over the given queries (act_max must hold zeros on entry; the
+// values are non-negative, so their float bits order like the floats).
+template <int CS, int CT, int H>
+__global__ void __launch_bounds__(kSimtThreads) k_fp8_calibrate(DevModel m, const float* __restrict__ uvt, int64_t n,
+                                                                float* __restrict__ act_max) {
+  using Mlp = SimtMlp<CS + CT, H>;
+  extern __shared__ __align__(16) float s_mlp[];
+  __shared__ uint2 lut[16];
+  init_p35_lut(lut, threadIdx.x);
+  Mlp::load(s_mlp, m);
+  __syncthreads();
+  float m1 = 0.0f, m2 = 0.0f, m3 = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float x[CS + CT];
+    gather_f32<CS, CT>(m, uvt[3 * i], uvt[3 * i + 1], uvt[3 * i + 2], x, nullptr, lut);
+    float h1[H];
+#pragma unroll
+    for (int o = 0; o < H; ++o) h1[o] = s_mlp[Mlp::kB1 + o];
+#pragma unroll
+    for (int k = 0; k < CS + CT; ++k) {
+      m1 = fmaxf(m1, fabsf(x[k]));
+#pragma unroll
+      for (int o = 0; o < H; ++o) h1[o] = fmaf(x[k], s_mlp[Mlp::kW1 + k * H + o], h1[o]);
+    }
+#pragma unroll
+    for (int o = 0; o < H; ++o) {
+      h1[o] = fmaxf(h1[o], 0.0f);
+      m2 = fmaxf(m2, h1[o]);
+    }
+    for (int o = 0; o < H; ++o) {
+      float z = s_mlp[Mlp::kB2 + o];
+#pragma unroll
+      for (int k = 0; k < H; ++k) z = fmaf(h1[k], s_mlp[Mlp::kW2t + o * H + k], z);
+      m3 = fmaxf(m3, z);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, off));
+    m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, off));
+    m3 = fmaxf(m3, __shfl_xor_sync(0xffffffffu, m3, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(reinterpret_cast<unsigned int*>(act_max), __float_as_uint(m1));
+    atomicMax(reinterpret_cast<unsigned int*>(act_max) + 1, __float_as_uint(m2));
+    atomicMax(reinterpret_cast<unsigned int*>(act_max) + 2, __float_as_uint(m3));
+  }
+}
+
 // ---------------------------------------------------------------------------
 #define NDGI_SIMT_SHAPES(X) \
   X(4, 4, 16)               \
@@ -231,6 +281,25 @@ cudaError_t launch_points_f32(const DevModel& m, const float* uvt, int64_t n, fl
       if (e != cudaSuccess) return e;                                                           \
     }                                                                                           \
     k_points_f32<A, B, C><<<grid, kSimtThreads, smem, s>>>(m, uvt, n, rgb);                     \
+    return cudaGetLastError();                                                                  \
+  }
+  NDGI_SIMT_SHAPES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fp8_calibrate(const DevModel& m, const float* uvt, int64_t n, float* act_max, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(act_max, 0, 3 * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  const int grid = grid_for(n, kSimtThreads, 8);
+#define X(A, B, C)                                                                              \
+  if (m.cs == A && m.ct == B && m.hidden == C) {                                                \
+    constexpr size_t smem = SimtMlp<A + B, C>::kBytes;                                          \
+    if (smem > 48 * 1024) {                                                                     \
+      e = cudaFuncSetAttribute(k_fp8_calibrate<A, B, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+      if (e != cudaSuccess) return e;                                                           \
+    }                                                                                           \
+    k_fp8_calibrate<A, B, C><<<grid, kSimtThreads, smem, s>>>(m, uvt, n, act_max);              \
     return cudaGetLastError();                                                                  \
   }
   NDGI_SIMT_SHAPES(X)

@@ -44,6 +44,7 @@ int num_sms();
 // ---- FP32 CUDA-core decode (decode_simt.cu) ----
 bool simt_supported(int cs, int ct, int hidden);
 cudaError_t launch_points_f32(const DevModel& m, const float* uvt, int64_t n, float* rgb, cudaStream_t s);
+cudaError_t launch_fp8_calibrate(const DevModel& m, const float* uvt, int64_t n, float* act_max, cudaStream_t s);
 cudaError_t launch_debug_features(const DevModel& m, const float* uvt, int64_t n, float* x, int32_t* p35,
                                   cudaStream_t s);
 

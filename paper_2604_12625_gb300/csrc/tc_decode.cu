@@ -1,6 +1,7 @@
 // Tensor-core decode: the decoder MLP on tcgen05 (FP16 or BF16 operands,
 // FP32 accumulation in tensor memory), for random points and for batched
-// virtual-texture pages.
+// virtual-texture pages; the page decode also runs with FP8 (E4M3) weights
+// and activations (kind::f8f6f4).
 //
 // Structure.  A CTA holds NWG independent "lanes" (warpgroups of 4 warps).
 // A lane owns one 128-row MMA tile at a time: its 128 threads write the
@@ -25,10 +26,20 @@
 // memory, in batches of up to 8 rows, and blends the four taps of each texel
 // with packed half2 arithmetic from there.
 //
+// FP8 pages.  Every scale is a power of two (see k_tc_prepare8), chosen so that
+// a layer's FP32 accumulator is already in the next layer's activation unit:
+// the epilogue is then one ReLU + E4M3 conversion per pair of values, exactly
+// like the FP16 one.  Biases ride in the K padding as three E4M3 terms against
+// ones columns of value v (a power of two), which keeps about 12 significant
+// bits of each bias.
+//
 // Every mbarrier wait is bounded; a timeout is latched in a device error word
 // that ndgi_check reports, and the CTA unwinds and frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+
+#include <cstring>
+#include <type_traits>
 
 #include "ndgi_internal.h"
 #include "bc4.cuh"
@@ -42,6 +53,9 @@ namespace ndgi {
 static __device__ int g_tc_error;
 
 constexpr int kLaneThreads = 128;
+
+// Operand kinds of the tensor-core decode.
+constexpr int kF16 = 0, kBF16 = 1, kE4M3 = 2;
 
 // ---------------------------------------------------------------------------
 // Weight image (built by ndgi_prepare), identical layout in global and shared
@@ -62,10 +76,100 @@ struct TcLayout {
   static constexpr uint32_t kW1T = kB1G + H * K1G * 2;     // [CT][H] f32 stored temporal weights
   static constexpr uint32_t kB1 = kW1T + CT * H * 4;       // [H] f32 stored b1
   static constexpr uint32_t kWsBytes = kB1 + H * 4;
+  static constexpr int EB = 2;                             // bytes per operand element
   static constexpr uint32_t kTmemCols = H <= 32 ? 32 : (H <= 64 ? 64 : 128);
   static_assert(H % 16 == 0 && H <= 128, "hidden width must be a multiple of 16, at most 128");
   static_assert(kShared % 16 == 0 && kB1G % 16 == 0 && kW1T % 16 == 0, "16-byte granular image");
 };
+
+// FP8 scales of one model (the tail of its FP8 image), all powers of two:
+// layer-1 inputs are quantised in units a1, layer-1 outputs (= layer-2
+// inputs) are in units a2, the RGB accumulator in units `out`.
+struct Fp8Scales {
+  float a1, inv_a1, inv_a2, out;
+  uint32_t ones2, ones3;   // A-side ones word of layers 2 / 3: E4M3 code of v in bytes 0..2, byte 3 zero
+  float a2;
+  uint32_t status;         // bit 0: a bias needs a ones value above 256; bit 1: 1/a1 too large for FP16
+  float s1, s2, s3, a3;    // weight scales and the layer-2 output unit
+  float v2, v3, pad0, pad1;
+};
+static_assert(sizeof(Fp8Scales) == 64, "FP8 scale block");
+
+// FP8 (E4M3) image for the page decode: one-byte codes, a K step of 32.
+// Layer 1 contracts the 16 spatial channels plus three ones columns that
+// carry the per-request bias b1' (K = 32); layers 2 and 3 carry their biases
+// the same way in K2 = H + 32.
+template <int CS, int CT, int H>
+struct TcLayout8 {
+  static constexpr int EB = 1;
+  static constexpr int K1G = 32;
+  static constexpr int K2 = H + 32;
+  static constexpr int N3 = 16;
+  static constexpr uint32_t kB2 = 0;                       // [H][K2]  codes of W2^T / s2; columns H..H+2 = b2 terms
+  static constexpr uint32_t kB3 = kB2 + H * K2;            // [16][K2] codes of W3^T / s3; columns H..H+2 = b3 terms
+  static constexpr uint32_t kShared = kB3 + N3 * K2;
+  static constexpr uint32_t kB1G = kShared;                // [H][K1G] codes of W1_s^T / s1; b1' terms per request
+  static constexpr uint32_t kW1T = kB1G + H * K1G;         // [CT][H] f32 stored temporal weights s1 e4m3(W1_t / s1)
+  static constexpr uint32_t kB1 = kW1T + CT * H * 4;       // [H] f32 b1
+  static constexpr uint32_t kScale = kB1 + H * 4;          // Fp8Scales
+  static constexpr uint32_t kWsBytes = kScale + sizeof(Fp8Scales);
+  static_assert(CS + 3 <= K1G && H % 32 == 0 && H <= 128, "FP8 pages: cs <= 29, hidden a multiple of 32");
+  static_assert(kShared % 16 == 0 && kW1T % 16 == 0 && kScale % 16 == 0 && kWsBytes % 16 == 0, "granularity");
+};
+
+// ---- E4M3 helpers ----------------------------------------------------------
+// Two floats -> two E4M3 codes (nearest even, saturating at +-448), `lo` in bits 0..7.
+__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
+  uint16_t d;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ uint32_t e4m3x2_relu(float lo, float hi) {
+  uint16_t d;
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// Packed half2 -> two E4M3 codes, the low half in bits 0..7.
+__device__ __forceinline__ uint32_t e4m3x2_h(uint32_t h2) {
+  uint16_t d;
+  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(d) : "r"(h2));
+  return d;
+}
+// Value of an E4M3 code, from the format (exact in FP32): exponent field e,
+// mantissa m: (1 + m/8) 2^(e-7), or m/8 2^-6 when e = 0.
+__device__ __forceinline__ float e4m3_value(uint32_t c) {
+  const uint32_t e = (c >> 3) & 15u, m = c & 7u;
+  const float v = e == 0 ? (float)m * 0x1p-9f : __uint_as_float(((e + 120u) << 23) | (m << 20));
+  return (c & 0x80u) ? -v : v;
+}
+// Smallest power of two P with y <= 448 P (1 for y <= 0 or not finite); the
+// comparisons are exact.
+__device__ float fp8_p2(float y) {
+  if (!(y > 0.0f) || !(y <= 3.4e38f)) return 1.0f;
+  int e;
+  frexpf(y / 448.0f, &e);
+  float P = ldexpf(1.0f, e);
+  while (y > 448.0f * P) P *= 2.0f;
+  while (y <= 448.0f * (P * 0.5f)) P *= 0.5f;
+  return P;
+}
+// beta / v as three E4M3 terms t1 + t2 + t3 (each the rounding of what the
+// previous terms left; the residuals are exact in FP32): codes in bytes 0..2.
+__device__ uint32_t fp8_terms(float beta, float v) {
+  const float r0 = beta * (1.0f / v);
+  const uint32_t c1 = e4m3x2(r0, 0.0f) & 0xFFu;
+  const float r1 = __fsub_rn(r0, e4m3_value(c1));
+  const uint32_t c2 = e4m3x2(r1, 0.0f) & 0xFFu;
+  const float r2 = __fsub_rn(r1, e4m3_value(c2));
+  const uint32_t c3 = e4m3x2(r2, 0.0f) & 0xFFu;
+  return c1 | (c2 << 8) | (c3 << 16);
+}
+// E4M3 code of a power of two 2^k, k in -6..8.
+__device__ __forceinline__ uint32_t e4m3_pow2_code(float v) {
+  int e;
+  frexpf(v, &e);
+  return (uint32_t)(e - 1 + 7) << 3;
+}
 
 template <bool BF16>
 __device__ __forceinline__ uint16_t to_bits(float x) {
@@ -129,6 +233,96 @@ __global__ void k_tc_prepare(DevModel m, unsigned char* __restrict__ ws) {
   for (int i = tid; i < H; i += nt) reinterpret_cast<float*>(ws + L::kB1)[i] = round_stored<BF16>(m.b1[i]);
 }
 
+// FP8 image from the FP32 master weights and the calibration maxima
+// m1 = max|layer-1 input|, m2 = max relu(z1), m3 = max relu(z2).  With p2(y) the
+// smallest power of two P with y <= 448 P:
+//   a1 = p2(m1), s1 = p2(max(max|W1|, m2/a1)), a2 = a1 s1,
+//   s2 = p2(max(max|W2|, m3/a2)), a3 = a2 s2, s3 = p2(max|W3|), out = a3 s3.
+// Weights are stored as codes of W_l / s_l; a layer's accumulator is then the
+// layer output in units a_(l+1).  Bias b of a layer with output unit u:
+// v = max(1, p2(max|b/u|)) and the codes of the three terms of b/u/v.
+// One CTA of 256 threads.
+template <int CS, int CT, int H>
+__global__ void __launch_bounds__(256) k_tc_prepare8(DevModel m, float m1, float m2, float m3,
+                                                     unsigned char* __restrict__ ws) {
+  using L = TcLayout8<CS, CT, H>;
+  constexpr int CIN = CS + CT;
+  __shared__ unsigned int s_max[5];   // float bits (non-negative): |W1|, |W2|, |W3|, |b2/a3|, |b3/out|
+  __shared__ float s_sc[8];           // a1, s1, a2, s2, a3, s3, out, -
+  __shared__ float s_v[2];            // v2, v3
+  const int tid = threadIdx.x;
+  if (tid < 5) s_max[tid] = 0u;
+  __syncthreads();
+  float w1 = 0.0f, w2 = 0.0f, w3 = 0.0f;
+  for (int i = tid; i < CIN * H; i += 256) w1 = fmaxf(w1, fabsf(m.w1[i]));
+  for (int i = tid; i < H * H; i += 256) w2 = fmaxf(w2, fabsf(m.w2[i]));
+  for (int i = tid; i < H * 3; i += 256) w3 = fmaxf(w3, fabsf(m.w3[i]));
+  atomicMax(&s_max[0], __float_as_uint(w1));
+  atomicMax(&s_max[1], __float_as_uint(w2));
+  atomicMax(&s_max[2], __float_as_uint(w3));
+  __syncthreads();
+  if (tid == 0) {
+    const float a1 = fp8_p2(m1);
+    const float s1 = fp8_p2(fmaxf(__uint_as_float(s_max[0]), m2 / a1)), a2 = a1 * s1;
+    const float s2 = fp8_p2(fmaxf(__uint_as_float(s_max[1]), m3 / a2)), a3 = a2 * s2;
+    const float s3 = fp8_p2(__uint_as_float(s_max[2]));
+    s_sc[0] = a1; s_sc[1] = s1; s_sc[2] = a2; s_sc[3] = s2; s_sc[4] = a3; s_sc[5] = s3; s_sc[6] = a3 * s3;
+  }
+  __syncthreads();
+  const float s1 = s_sc[1], s2 = s_sc[3], s3 = s_sc[5], a3 = s_sc[4], out = s_sc[6];
+  if (tid < H) atomicMax(&s_max[3], __float_as_uint(fabsf(m.b2[tid] / a3)));
+  if (tid < 3) atomicMax(&s_max[4], __float_as_uint(fabsf(m.b3[tid] / out)));
+  __syncthreads();
+  if (tid == 0) {
+    const float v2 = fmaxf(1.0f, fp8_p2(__uint_as_float(s_max[3]))), v3 = fmaxf(1.0f, fp8_p2(__uint_as_float(s_max[4])));
+    s_v[0] = v2;
+    s_v[1] = v3;
+    Fp8Scales sc;
+    sc.a1 = s_sc[0];
+    sc.inv_a1 = 1.0f / s_sc[0];
+    sc.inv_a2 = 1.0f / s_sc[2];
+    sc.out = out;
+    const uint32_t c2 = e4m3_pow2_code(fminf(v2, 256.0f)), c3 = e4m3_pow2_code(fminf(v3, 256.0f));
+    sc.ones2 = c2 | (c2 << 8) | (c2 << 16);
+    sc.ones3 = c3 | (c3 << 8) | (c3 << 16);
+    sc.a2 = s_sc[2];
+    sc.status = (v2 > 256.0f || v3 > 256.0f ? 1u : 0u) | (sc.inv_a1 > 16384.0f ? 2u : 0u);
+    sc.s1 = s_sc[1];
+    sc.s2 = s_sc[3];
+    sc.s3 = s_sc[5];
+    sc.a3 = s_sc[4];
+    sc.v2 = v2;
+    sc.v3 = v3;
+    sc.pad0 = sc.pad1 = 0.0f;
+    *reinterpret_cast<Fp8Scales*>(ws + L::kScale) = sc;
+  }
+  __syncthreads();
+  const float v2 = s_v[0], v3 = s_v[1];
+  for (int i = tid; i < H * L::K2; i += 256) {      // B2[n][k]: W2[k][n] / s2, then the b2 terms
+    const int n = i / L::K2, k = i % L::K2;
+    uint32_t c = 0u;
+    if (k < H) c = e4m3x2(m.w2[k * H + n] * (1.0f / s2), 0.0f) & 0xFFu;
+    else if (k < H + 3) c = (fp8_terms(m.b2[n] / a3, v2) >> (8 * (k - H))) & 0xFFu;
+    ws[L::kB2 + kmajor_offset8(n, k, L::K2)] = (unsigned char)c;
+  }
+  for (int i = tid; i < L::N3 * L::K2; i += 256) {  // B3[n][k]: W3[k][n] / s3, then the b3 terms
+    const int n = i / L::K2, k = i % L::K2;
+    uint32_t c = 0u;
+    if (n < 3 && k < H) c = e4m3x2(m.w3[k * 3 + n] * (1.0f / s3), 0.0f) & 0xFFu;
+    else if (n < 3 && k < H + 3) c = (fp8_terms(m.b3[n] / out, v3) >> (8 * (k - H))) & 0xFFu;
+    ws[L::kB3 + kmajor_offset8(n, k, L::K2)] = (unsigned char)c;
+  }
+  for (int i = tid; i < H * L::K1G; i += 256) {     // B1[n][k]: spatial W1[k][n] / s1; bias columns per request
+    const int n = i / L::K1G, k = i % L::K1G;
+    const uint32_t c = k < CS ? e4m3x2(m.w1[k * H + n] * (1.0f / s1), 0.0f) & 0xFFu : 0u;
+    ws[L::kB1G + kmajor_offset8(n, k, L::K1G)] = (unsigned char)c;
+  }
+  for (int i = tid; i < CT * H; i += 256)
+    reinterpret_cast<float*>(ws + L::kW1T)[i] =
+        s1 * e4m3_value(e4m3x2(m.w1[(CS + i / H) * H + i % H] * (1.0f / s1), 0.0f) & 0xFFu);
+  for (int i = tid; i < H; i += 256) reinterpret_cast<float*>(ws + L::kB1)[i] = m.b1[i];
+}
+
 // ---------------------------------------------------------------------------
 // tcgen05 helpers specific to this file
 // ---------------------------------------------------------------------------
@@ -163,22 +357,29 @@ constexpr uint32_t tmem_alloc_cols(int cols) {
 //
 // A slot is one 128-row tile in flight: a region of tensor memory holding the
 // accumulator D (H columns, FP32) followed by the A operand of the next MMA
-// (rows in lanes, two 16-bit K elements per column), and an mbarrier.  The
-// layer-1 A tile (K1 columns of features, bias ones column(s), zeros) and the
-// hidden tiles (H ReLU values, then (1, 0, ...) carrying the bias in the
-// K padding, K2 = H + 16) take turns in the A region, written from registers
-// with tcgen05.st.  Only the small weight tiles B are read from shared
-// memory.  With SL = 2 the lane interleaves its slots so that one slot's
-// gather or epilogue runs while the other slot's MMAs are in flight.
+// (rows in lanes; two 16-bit or four 8-bit K elements per column), and an
+// mbarrier.  The layer-1 A tile (features, bias ones column(s), zeros) and the
+// hidden tiles (H ReLU values, then the ones columns carrying the bias in the
+// K padding, K2 = H + one K step) take turns in the A region, written from
+// registers with tcgen05.st.  Only the small weight tiles B are read from
+// shared memory.  With SL = 2 the lane interleaves its slots so that one
+// slot's gather or epilogue runs while the other slot's MMAs are in flight.
+// P: kF16 / kBF16 (kind::f16, K step 16) or kE4M3 (kind::f8f6f4, K step 32);
+// either way a K step is 32 bytes of a row: 8 TMEM columns, 256 B of B.
 // ---------------------------------------------------------------------------
 constexpr uint64_t kDescK = 256 >> 4;   // B descriptor start-address step per K step (256 B)
 
-template <int H, bool BF16, int K1, int SL>
+template <int H, int P, int K1, int SL>
 struct Engine {
-  static constexpr int K2 = H + 16;
-  static constexpr uint32_t kACol = H;                        // A region starts after D
-  static constexpr uint32_t kSlotCols = tmem_alloc_cols(H + K2 / 2);
-  static_assert(K1 / 2 <= K2 / 2 + 8, "layer-1 tile must fit the A region");
+  static constexpr bool BF16 = P == kBF16, F8 = P == kE4M3;
+  static constexpr int KS = F8 ? 32 : 16;                    // K elements per MMA
+  static constexpr int EB = F8 ? 1 : 2;                      // bytes per element
+  static constexpr int K2 = H + KS;
+  static constexpr uint32_t kACol = H;                       // A region starts after D
+  static constexpr uint32_t kSlotCols = tmem_alloc_cols(H + K2 * EB / 4);
+  static constexpr int kA1Words = K1 * EB / 4;               // 32-bit words of a layer-1 row
+  static_assert(kA1Words <= K2 * EB / 4 + 8, "layer-1 tile must fit the A region");
+  static_assert(!F8 || H % 32 == 0, "FP8 epilogue works on 32-column chunks");
   int wg, t;
   uint32_t tmem[SL];     // slot base, lane 0
   uint32_t lane_off;     // this warp's lane quadrant, in the TMEM address
@@ -190,9 +391,14 @@ struct Engine {
   __device__ __forceinline__ void issue(int s, uint64_t b_desc) {
     tc_fence_after();
 #pragma unroll
-    for (int ks = 0; ks < KSTEPS; ++ks)
-      umma_f16_ts(tmem[s], tmem[s] + kACol + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16),
-                  ks > 0 ? 1u : 0u);
+    for (int ks = 0; ks < KSTEPS; ++ks) {
+      if constexpr (F8)
+        umma_f8_ts(tmem[s], tmem[s] + kACol + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, false),
+                   ks > 0 ? 1u : 0u);
+      else
+        umma_f16_ts(tmem[s], tmem[s] + kACol + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16),
+                    ks > 0 ? 1u : 0u);
+    }
     umma_commit(bar[s]);
   }
   // Make this lane's tcgen05.st writes visible, then reach the lane barrier.
@@ -203,15 +409,15 @@ struct Engine {
   }
   __device__ __forceinline__ void layer1(int s) {
     publish();
-    if (t == 0) issue<K1 / 16, H>(s, db1);
+    if (t == 0) issue<K1 / KS, H>(s, db1);
   }
   __device__ __forceinline__ void layer2(int s) {
     publish();
-    if (t == 0) issue<K2 / 16, H>(s, db2);
+    if (t == 0) issue<K2 / KS, H>(s, db2);
   }
   __device__ __forceinline__ void layer3(int s) {
     publish();
-    if (t == 0) issue<K2 / 16, 16>(s, db3);
+    if (t == 0) issue<K2 / KS, 16>(s, db3);
   }
   // Thread 0 waits for slot s's MMAs, the lane blocks in its barrier.  false
   // (uniform) on timeout; the phase then keeps the parity still outstanding.
@@ -223,12 +429,12 @@ struct Engine {
     tc_fence_after();
     return true;
   }
-  // Layer-1 row of this thread: K1/2 packed words.
+  // Layer-1 row of this thread: kA1Words packed words.
   __device__ __forceinline__ void write_a1(int s, const uint32_t* w) {
     const uint32_t a = tmem[s] + lane_off + kACol;
 #pragma unroll
-    for (int c = 0; c < K1 / 2; c += 8) {
-      if (c + 16 <= K1 / 2 && (c % 16) == 0) {
+    for (int c = 0; c < kA1Words; c += 8) {
+      if (c + 16 <= kA1Words && (c % 16) == 0) {
         uint32_t r[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) r[j] = w[c + j];
@@ -242,33 +448,52 @@ struct Engine {
       }
     }
   }
-  // Slot s: this thread's row of D -> ReLU -> FP16/BF16 -> the hidden A tile,
-  // plus the (1, 0, ...) bias columns.
-  __device__ __forceinline__ void epilogue(int s) {
+  // Slot s: this thread's row of D -> ReLU -> FP16/BF16/E4M3 -> the hidden A
+  // tile, then the bias ones columns (for FP8 `ones` holds the three codes of
+  // the next layer's ones value; FP16/BF16 use 1.0).
+  __device__ __forceinline__ void epilogue(int s, uint32_t ones = 0u) {
     const uint32_t d = tmem[s] + lane_off, a = d + kACol;
+    if constexpr (F8) {
 #pragma unroll
-    for (int c = 0; c < H; c += 32) {
-      if (H - c >= 32) {
-        uint32_t r[32], w[16];
+      for (int c = 0; c < H; c += 32) {
+        uint32_t r[32], w[8];
         tmem_ld32(d + c, r);
         tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-        tmem_st16(a + c / 2, w);
-      } else {
-        uint32_t r[16], w[8];
-        tmem_ld16(d + c, r);
-        tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 8; ++j) w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-        tmem_st8(a + c / 2, w);
+        for (int j = 0; j < 8; ++j)
+          w[j] = e4m3x2_relu(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1])) |
+                 (e4m3x2_relu(__uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])) << 16);
+        tmem_st8(a + c / 4, w);
       }
+      const uint32_t ow[8] = {ones, 0, 0, 0, 0, 0, 0, 0};
+      tmem_st8(a + H / 4, ow);
+    } else {
+#pragma unroll
+      for (int c = 0; c < H; c += 32) {
+        if (H - c >= 32) {
+          uint32_t r[32], w[16];
+          tmem_ld32(d + c, r);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+          tmem_st16(a + c / 2, w);
+        } else {
+          uint32_t r[16], w[8];
+          tmem_ld16(d + c, r);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+          tmem_st8(a + c / 2, w);
+        }
+      }
+      const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
+      const uint32_t ow[8] = {one, 0, 0, 0, 0, 0, 0, 0};
+      tmem_st8(a + H / 2, ow);
     }
-    const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
-    const uint32_t ones[8] = {one, 0, 0, 0, 0, 0, 0, 0};
-    tmem_st8(a + H / 2, ones);
   }
-  // Slot s after layer 3: this thread's RGB.
+  // Slot s after layer 3: this thread's RGB accumulator.
   __device__ __forceinline__ void output(int s, float& y0, float& y1, float& y2) {
     uint32_t r[4];
     tmem_ld4(tmem[s] + lane_off, r);
@@ -322,10 +547,10 @@ __device__ __forceinline__ void copy16(unsigned char* dst, const unsigned char* 
     *reinterpret_cast<uint4*>(dst + i) = *reinterpret_cast<const uint4*>(src + i);
 }
 
-template <int H, bool BF16, int K1, int SL>
-__device__ __forceinline__ void engine_init(Engine<H, BF16, K1, SL>& e, uint32_t tbase, uint64_t* bars, int tid,
+template <int H, int P, int K1, int SL>
+__device__ __forceinline__ void engine_init(Engine<H, P, K1, SL>& e, uint32_t tbase, uint64_t* bars, int tid,
                                             uint32_t b1_smem, uint32_t b2_smem, uint32_t b3_smem) {
-  using E = Engine<H, BF16, K1, SL>;
+  using E = Engine<H, P, K1, SL>;
   e.wg = tid >> 7;
   e.t = tid & (kLaneThreads - 1);
   e.lane_off = (uint32_t)(((e.t >> 5) * 32) << 16);
@@ -335,9 +560,9 @@ __device__ __forceinline__ void engine_init(Engine<H, BF16, K1, SL>& e, uint32_t
     e.bar[s] = &bars[SL * e.wg + s];
     e.phase[s] = 0;
   }
-  e.db1 = sdesc(b1_smem, 128u, K1 * 16u);
-  e.db2 = sdesc(b2_smem, 128u, E::K2 * 16u);
-  e.db3 = sdesc(b3_smem, 128u, E::K2 * 16u);
+  e.db1 = sdesc(b1_smem, 128u, K1 * E::EB * 8u);       // 8-row group stride: (row bytes / 16) x 128 B
+  e.db2 = sdesc(b2_smem, 128u, E::K2 * E::EB * 8u);
+  e.db3 = sdesc(b3_smem, 128u, E::K2 * E::EB * 8u);
 }
 
 // ---------------------------------------------------------------------------
@@ -373,7 +598,8 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
                                                                     float* __restrict__ rgb) {
   using L = TcLayout<CS, CT, H>;
   using S = PointsSmem<CS, CT, H>;
-  using E = Engine<H, BF16, L::K1P, SL>;
+  constexpr int P = BF16 ? kBF16 : kF16;
+  using E = Engine<H, P, L::K1P, SL>;
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint64_t bars[SL * NWG];
   __shared__ uint32_t slot;
@@ -385,7 +611,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
   const uint32_t tbase = cta_setup<SL * NWG, E::kSlotCols>(bars, &slot, tid);
   const uint32_t base = smem_addr(sm);
   E e;
-  engine_init<H, BF16, L::K1P, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
+  engine_init<H, P, L::K1P, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
   const int t = e.t;
   // inflight[s]: slot s has MMAs issued and not yet waited for; need_out[s]:
   // its layer-3 result is still to be read out (one round later).
@@ -470,14 +696,18 @@ constexpr int kQuad = 64;         // page quadrant side (texels)
 constexpr int kDecodeAhead = 4;   // extra feature rows decoded per batch
 constexpr uint32_t kRingPlane = kRingRows * kRingCols * 16;   // one 8-channel plane
 
-template <int CS, int CT, int H, int NWG>
+template <int CS, int CT, int H, int P>
+using PagesLayout = std::conditional_t<P == kE4M3, TcLayout8<CS, CT, H>, TcLayout<CS, CT, H>>;
+
+template <int CS, int CT, int H, int NWG, int P>
 struct PagesSmem {
-  using L = TcLayout<CS, CT, H>;
+  using L = PagesLayout<CS, CT, H, P>;
   static constexpr uint32_t kW = 0;
   static constexpr uint32_t kB1 = kW + L::kShared;                      // pages B1 [H][K1G]
-  static constexpr uint32_t kW1T = kB1 + H * L::K1G * 2;                // [CT][H] f32
-  static constexpr uint32_t kBias1 = kW1T + CT * H * 4;                 // [H] f32 stored b1
-  static constexpr uint32_t kLut = (kBias1 + H * 4 + 127) / 128 * 128;
+  static constexpr uint32_t kTail = L::kWsBytes - L::kB1G;              // B1, W1T, b1 (and FP8 scales) of the image
+  static constexpr uint32_t kW1T = kB1 + (L::kW1T - L::kB1G);           // [CT][H] f32
+  static constexpr uint32_t kBias1 = kB1 + (L::kB1 - L::kB1G);          // [H] f32 stored b1
+  static constexpr uint32_t kLut = (kB1 + kTail + 127) / 128 * 128;
   static constexpr uint32_t kLanes = kLut + 128;
   // per lane: the feature ring and the row table
   static constexpr uint32_t kRing = 0;
@@ -524,10 +754,12 @@ __device__ __forceinline__ void decode_rows(const DevModel& m, unsigned char* ri
 }
 
 // Layer-1 words of one page texel from the ring: bilinear blend of the four
-// taps in half2 (16 channels), the two ones columns for b1' (hi, lo), zeros.
-template <int CS, bool BF16, int K1>
-__device__ __forceinline__ void ring_texel(uint32_t (&w)[K1 / 2], const unsigned char* ring, int4 rt, int c0, int c1,
+// taps in half2 (16 channels).  FP16/BF16: one channel pair per word; E4M3
+// (the x weights then carry the 1/a1 scale): four channels per word.
+template <int CS, int P, int NW>
+__device__ __forceinline__ void ring_texel(uint32_t (&w)[NW], const unsigned char* ring, int4 rt, int c0, int c1,
                                            __half2 wx0, __half2 wx1) {
+  constexpr bool BF16 = P == kBF16;
   const float fy = __int_as_float(rt.z);
   const __half2 wy1 = __float2half2_rn(fy), wy0 = __float2half2_rn(1.0f - fy);
   const __half2 w00 = __hmul2(wx0, wy0), w10 = __hmul2(wx1, wy0), w01 = __hmul2(wx0, wy1), w11 = __hmul2(wx1, wy1);
@@ -548,7 +780,11 @@ __device__ __forceinline__ void ring_texel(uint32_t (&w)[K1 / 2], const unsigned
       v = __hfma2(w10, *reinterpret_cast<const __half2*>(&bv[k]), v);
       v = __hfma2(w01, *reinterpret_cast<const __half2*>(&cv[k]), v);
       v = __hfma2(w11, *reinterpret_cast<const __half2*>(&dv[k]), v);
-      if (BF16) {
+      if constexpr (P == kE4M3) {
+        const uint32_t q = e4m3x2_h(*reinterpret_cast<const uint32_t*>(&v));
+        if (k & 1) w[2 * g + k / 2] |= q << 16;
+        else w[2 * g + k / 2] = q;
+      } else if constexpr (BF16) {
         const float2 f = __half22float2(v);
         w[4 * g + k] = pack2<true>(f.x, f.y);
       } else {
@@ -558,12 +794,19 @@ __device__ __forceinline__ void ring_texel(uint32_t (&w)[K1 / 2], const unsigned
   }
 }
 
-template <int CS, bool BF16, int K1>
-__device__ __forceinline__ void a1_bias_words(uint32_t (&w)[K1 / 2]) {
-  const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
-  w[CS / 2] = one | (one << 16);
+// The layer-1 bias columns after the CS feature channels: FP16/BF16 two ones
+// (b1' hi, lo); E4M3 the per-request ones word (three codes of v1); zeros.
+template <int CS, int P, int NW>
+__device__ __forceinline__ void a1_bias_words(uint32_t (&w)[NW], uint32_t ones8) {
+  constexpr int first = P == kE4M3 ? CS / 4 : CS / 2;
+  if constexpr (P == kE4M3) {
+    w[first] = ones8;
+  } else {
+    const uint32_t one = P == kBF16 ? 0x3F80u : 0x3C00u;
+    w[first] = one | (one << 16);
+  }
 #pragma unroll
-  for (int j = CS / 2 + 1; j < K1 / 2; ++j) w[j] = 0u;
+  for (int j = first + 1; j < NW; ++j) w[j] = 0u;
 }
 
 // staged (host-side plan flag): features are at most half the lightmap
@@ -571,12 +814,14 @@ __device__ __forceinline__ void a1_bias_words(uint32_t (&w)[K1 / 2]) {
 // decoded once into the ring; otherwise each texel gathers its taps directly
 // with the lighter gather (its register needs shape the whole kernel's
 // allocation, and the hot staged loop must not spill).
-template <int CS, int CT, int H, bool BF16, int NWG, int SL>
+template <int CS, int CT, int H, int P, int NWG, int SL>
 __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, const ndgi_page_req* __restrict__ reqs,
                                                                    const int32_t* __restrict__ n_dev, int plan_staged) {
-  using L = TcLayout<CS, CT, H>;
-  using S = PagesSmem<CS, CT, H, NWG>;
-  using E = Engine<H, BF16, L::K1G, SL>;
+  using L = PagesLayout<CS, CT, H, P>;
+  using S = PagesSmem<CS, CT, H, NWG, P>;
+  using E = Engine<H, P, L::K1G, SL>;
+  constexpr bool BF16 = P == kBF16, F8 = P == kE4M3;
+  constexpr int NW = E::kA1Words;
   static_assert(CS == 16, "the staged page path is built for 16 spatial channels");
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint64_t bars[SL * NWG];
@@ -584,6 +829,10 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   __shared__ int s_item;
   __shared__ PageItem s_req;
   __shared__ float s_vt[CT];
+  __shared__ float s_beta[F8 ? H : 1];
+  __shared__ uint32_t s_bmax, s_ones1;   // FP8: max |b1'/a2| of the request, its ones word
+  const Fp8Scales* sc = nullptr;
+  if constexpr (F8) sc = reinterpret_cast<const Fp8Scales*>(sm + S::kB1 + (L::kScale - L::kB1G));
   constexpr int NT = kLaneThreads * NWG;
   const int tid = threadIdx.x;
   int n = *n_dev;
@@ -596,7 +845,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   const uint32_t tbase = cta_setup<SL * NWG, E::kSlotCols>(bars, &slot, tid);
   const uint32_t base = smem_addr(sm);
   E e;
-  engine_init<H, BF16, L::K1G, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
+  engine_init<H, P, L::K1G, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
   const int wg = e.wg, t = e.t;
   unsigned char* lb = sm + S::kLanes + wg * S::kLaneBytes;
   unsigned char* ring = lb + S::kRing;
@@ -635,21 +884,50 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
     if (r.model != loaded) {   // swap in this model's weights (no MMA is in flight here)
       const unsigned char* w = static_cast<const unsigned char*>(c.ws[r.model]);
       copy16(sm + S::kW, w, L::kShared, tid, NT);
-      copy16(sm + S::kB1, w + L::kB1G, H * L::K1G * 2 + CT * H * 4 + H * 4, tid, NT);
+      copy16(sm + S::kB1, w + L::kB1G, S::kTail, tid, NT);
       loaded = r.model;
     }
-    // temporal line at this request's t
+    if constexpr (F8) {
+      if (tid == 0) s_bmax = 0u;
+      __syncthreads();   // the scales are read below
+    }
+    // temporal line at this request's t (FP8: quantised like any layer-1 input)
     if (tid < CT) {
       int j0, j1;
       float a;
       temporal_setup(r.t, m.t_count, j0, j1, a);
-      s_vt[tid] = (1.0f - a) * load_temporal(m.temporal, m.temporal_f16, j0 * CT + tid) +
-                  a * load_temporal(m.temporal, m.temporal_f16, j1 * CT + tid);
+      float vt = (1.0f - a) * load_temporal(m.temporal, m.temporal_f16, j0 * CT + tid) +
+                 a * load_temporal(m.temporal, m.temporal_f16, j1 * CT + tid);
+      if constexpr (F8) vt = sc->a1 * e4m3_value(e4m3x2(vt * sc->inv_a1, 0.0f) & 0xFFu);
+      s_vt[tid] = vt;
     }
     __syncthreads();
-    // folded layer-1 bias b1' = b1 + W1_t v_t (FP32), stored in B1's columns
-    // CS and CS+1 as a hi + lo pair so the MMA adds it at FP32 accuracy
-    if (tid < H) {
+    if constexpr (F8) {
+      // folded layer-1 bias b1' = b1 + W1_t vq (FP32) in units a2, stored in
+      // B1's columns CS..CS+2 as three E4M3 terms against ones value v1 =
+      // max(1, p2(max |b1'/a2|)) (one per request)
+      if (tid < H) {
+        const float* w1t = reinterpret_cast<const float*>(sm + S::kW1T);
+        float b = reinterpret_cast<const float*>(sm + S::kBias1)[tid];
+#pragma unroll
+        for (int cc = 0; cc < CT; ++cc) b = fmaf(w1t[cc * H + tid], s_vt[cc], b);
+        const float beta = b * sc->inv_a2;
+        s_beta[tid] = beta;
+        atomicMax(&s_bmax, __float_as_uint(fabsf(beta)));
+      }
+      __syncthreads();
+      if (tid < H) {
+        const float v1 = fmaxf(1.0f, fp8_p2(__uint_as_float(s_bmax)));
+        *reinterpret_cast<uint32_t*>(sm + S::kB1 + kmajor_offset8(tid, CS, L::K1G)) = fp8_terms(s_beta[tid], v1);
+        if (tid == 0) {
+          const uint32_t oc = e4m3_pow2_code(fminf(v1, 256.0f));
+          s_ones1 = oc | (oc << 8) | (oc << 16);
+          if (v1 > 256.0f) atomicOr(c.error_word, 8);
+        }
+      }
+    } else if (tid < H) {
+      // folded layer-1 bias b1' = b1 + W1_t v_t (FP32), stored in B1's columns
+      // CS and CS+1 as a hi + lo pair so the MMA adds it at FP32 accuracy
       const float* w1t = reinterpret_cast<const float*>(sm + S::kW1T);
       float b = reinterpret_cast<const float*>(sm + S::kBias1)[tid];
 #pragma unroll
@@ -689,7 +967,8 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
       // columns and two output rows plus the look-ahead fit the 16-row ring
       const bool staged = plan_staged && ncols <= kRingCols;
       const int fr_last = rowtab[qh - 1].y;
-      const __half2 wx1 = __float2half2_rn(fx), wx0 = __float2half2_rn(1.0f - fx);
+      const float xs = F8 ? sc->inv_a1 : 1.0f;   // FP8: the blend lands in units a1
+      const __half2 wx1 = __float2half2_rn(fx * xs), wx0 = __float2half2_rn((1.0f - fx) * xs);
       const int c0 = (cx0 - fc0) * 16, c1 = (cx1 - fc0) * 16;
       int decoded_hi = -1000000;
       int prev_row[SL];
@@ -712,6 +991,12 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
             inflight[s] = need_out[s] = false;
             float y0, y1, y2;
             e.output(s, y0, y1, y2);
+            if constexpr (F8) {
+              const float so = sc->out;
+              y0 *= so;
+              y1 *= so;
+              y2 *= so;
+            }
             const int orow = prev_row[s];
             if (col < qw && orow < qh) {
               const int64_t o = (int64_t)(r.dst_y + oy + orow) * c.phys_w + (r.dst_x + ox + col);
@@ -735,22 +1020,28 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
             }
           }
           const int orow = row_base + (t >> 6);
-          uint32_t w[L::K1G / 2];
+          uint32_t w[NW];
           if (col < qw && orow < qh) {
             if (staged) {
-              ring_texel<CS, BF16, L::K1G>(w, ring, rowtab[orow], c0, c1, wx0, wx1);
+              ring_texel<CS, P, NW>(w, ring, rowtab[orow], c0, c1, wx0, wx1);
             } else {
               float x[CS + CT];
               gather_f32<CS, CT, false>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
                                         ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr, lut);
+              if constexpr (F8) {
 #pragma unroll
-              for (int j = 0; j < CS / 2; ++j) w[j] = pack2<BF16>(x[2 * j], x[2 * j + 1]);
+                for (int j = 0; j < CS / 4; ++j)
+                  w[j] = e4m3x2(x[4 * j] * xs, x[4 * j + 1] * xs) | (e4m3x2(x[4 * j + 2] * xs, x[4 * j + 3] * xs) << 16);
+              } else {
+#pragma unroll
+                for (int j = 0; j < CS / 2; ++j) w[j] = pack2<BF16>(x[2 * j], x[2 * j + 1]);
+              }
             }
           } else {
 #pragma unroll
-            for (int j = 0; j < CS / 2; ++j) w[j] = 0u;
+            for (int j = 0; j < CS * E::EB / 4; ++j) w[j] = 0u;
           }
-          a1_bias_words<CS, BF16, L::K1G>(w);
+          a1_bias_words<CS, P, NW>(w, F8 ? s_ones1 : 0u);
           e.write_a1(s, w);
           e.layer1(s);
           inflight[s] = true;
@@ -767,7 +1058,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
               continue;
             }
             inflight[s] = false;
-            e.epilogue(s);
+            e.epilogue(s, F8 ? (layer == 2 ? sc->ones2 : sc->ones3) : 0u);
             if (layer == 2) {
               e.layer2(s);
             } else {
@@ -863,22 +1154,133 @@ cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tc_pages(const PagesCtx& c, bool bf16, int cs, int ct, int hidden, const TcPagesShape& shape,
+template <int CS, int CT, int H, int P, int NW, int SL>
+static cudaError_t launch_pages_kind(const PagesCtx& c, bool staged, const ndgi_page_req* reqs, const int32_t* n_dev,
+                                     cudaStream_t s, int grid) {
+  using S = PagesSmem<CS, CT, H, NW, P>;
+  auto kern = k_pages_tc<CS, CT, H, P, NW, SL>;
+  cudaError_t e = set_smem(kern, tc_smem(S::kBytes));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kLaneThreads * NW, tc_smem(S::kBytes), s>>>(c, reqs, n_dev, staged ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <int CS, int CT, int H, int NW, int SL>
+static cudaError_t launch_pages_shape(const PagesCtx& c, int prec, bool staged, const ndgi_page_req* reqs,
+                                      const int32_t* n_dev, cudaStream_t s, int grid) {
+  if (prec == kF16) return launch_pages_kind<CS, CT, H, kF16, NW, SL>(c, staged, reqs, n_dev, s, grid);
+  if (prec == kBF16) return launch_pages_kind<CS, CT, H, kBF16, NW, SL>(c, staged, reqs, n_dev, s, grid);
+  if constexpr (H % 32 == 0) {
+    if (prec == kE4M3) return launch_pages_kind<CS, CT, H, kE4M3, NW, SL>(c, staged, reqs, n_dev, s, grid);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_pages(const PagesCtx& c, int prec, int cs, int ct, int hidden, const TcPagesShape& shape,
                             bool staged, const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s) {
   const int grid = num_sms() * shape.ctas_per_sm;
-#define X(A, B, C, NW, SL)                                                                                      \
-  if (cs == A && ct == B && hidden == C && shape.lanes == NW && shape.slots == SL) {                            \
-    using S = PagesSmem<A, B, C, NW>;                                                                           \
-    auto kern = bf16 ? k_pages_tc<A, B, C, true, NW, SL> : k_pages_tc<A, B, C, false, NW, SL>;                   \
-    cudaError_t e = set_smem(kern, tc_smem(S::kBytes));                                                         \
-    if (e != cudaSuccess) return e;                                                                             \
-    kern<<<grid, kLaneThreads * NW, tc_smem(S::kBytes), s>>>(c, reqs, n_dev, staged ? 1 : 0);                   \
-    return cudaGetLastError();                                                                                  \
-  }
+#define X(A, B, C, NW, SL)                                                                           \
+  if (cs == A && ct == B && hidden == C && shape.lanes == NW && shape.slots == SL)                   \
+    return launch_pages_shape<A, B, C, NW, SL>(c, prec, staged, reqs, n_dev, s, grid);
   X(16, 8, 16, 4, 1) X(16, 8, 32, 4, 1) X(16, 8, 64, 4, 1) X(16, 16, 64, 4, 1)
   X(16, 8, 16, 2, 2) X(16, 8, 32, 2, 2) X(16, 8, 64, 2, 2) X(16, 16, 64, 2, 2)
 #undef X
   return cudaErrorInvalidValue;
+}
+
+bool tc_fp8_pages_supported(int cs, int ct, int hidden) { return tc_pages_supported(cs, ct, hidden) && hidden % 32 == 0; }
+
+// Per-shape FP8 helpers (only shapes with cs = 16 and hidden % 32 == 0 have an FP8 image).
+template <int CS, int CT, int H>
+static size_t fp8_ws_bytes() {
+  if constexpr (CS == 16 && H % 32 == 0) return TcLayout8<CS, CT, H>::kWsBytes;
+  else return 0;
+}
+template <int CS, int CT, int H>
+static uint32_t fp8_status_offset() {
+  if constexpr (CS == 16 && H % 32 == 0) return TcLayout8<CS, CT, H>::kScale + offsetof(Fp8Scales, status);
+  else return 0;
+}
+template <int CS, int CT, int H>
+static cudaError_t fp8_prepare(const DevModel& m, const float act_max[3], void* ws, cudaStream_t s) {
+  if constexpr (CS == 16 && H % 32 == 0) {
+    k_tc_prepare8<CS, CT, H><<<1, 256, 0, s>>>(m, act_max[0], act_max[1], act_max[2], static_cast<unsigned char*>(ws));
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+// E4M3 code -> value on the host (the format definition, exact in FP32).
+static float e4m3_host(uint32_t c) {
+  const uint32_t e = (c >> 3) & 15u, m = c & 7u;
+  const float v = e == 0 ? (float)m * 0x1p-9f : ldexpf(1.0f + (float)m * 0.125f, (int)e - 7);
+  return (c & 0x80u) ? -v : v;
+}
+
+template <int CS, int CT, int H>
+static size_t fp8_unpack(const unsigned char* img, float* out, size_t len) {
+  if constexpr (CS == 16 && H % 32 == 0) {
+    using L = TcLayout8<CS, CT, H>;
+    constexpr int CIN = CS + CT;
+    const size_t need = 16 + (size_t)CIN * H + (size_t)H * H + H * 3 + H + 3;
+    if (!out || len < need) return need;
+    Fp8Scales sc;
+    memcpy(&sc, img + L::kScale, sizeof sc);
+    const float head[16] = {sc.a1, sc.a2, sc.a3, sc.out, sc.s1, sc.s2, sc.s3, sc.v2, sc.v3, (float)sc.status,
+                            0, 0, 0, 0, 0, 0};
+    size_t o = 0;
+    for (int i = 0; i < 16; ++i) out[o++] = head[i];
+    for (int k = 0; k < CIN; ++k)
+      for (int n = 0; n < H; ++n)
+        out[o++] = k < CS ? sc.s1 * e4m3_host(img[L::kB1G + kmajor_offset8(n, k, L::K1G)])
+                          : reinterpret_cast<const float*>(img + L::kW1T)[(k - CS) * H + n];
+    for (int k = 0; k < H; ++k)
+      for (int n = 0; n < H; ++n) out[o++] = sc.s2 * e4m3_host(img[L::kB2 + kmajor_offset8(n, k, L::K2)]);
+    for (int k = 0; k < H; ++k)
+      for (int n = 0; n < 3; ++n) out[o++] = sc.s3 * e4m3_host(img[L::kB3 + kmajor_offset8(n, k, L::K2)]);
+    for (int n = 0; n < H; ++n) {
+      float t = 0.0f;
+      for (int j = 0; j < 3; ++j) t += e4m3_host(img[L::kB2 + kmajor_offset8(n, H + j, L::K2)]);
+      out[o++] = sc.a3 * sc.v2 * t;
+    }
+    for (int n = 0; n < 3; ++n) {
+      float t = 0.0f;
+      for (int j = 0; j < 3; ++j) t += e4m3_host(img[L::kB3 + kmajor_offset8(n, H + j, L::K2)]);
+      out[o++] = sc.out * sc.v3 * t;
+    }
+    return o;
+  } else {
+    return 0;
+  }
+}
+
+size_t tc_fp8_unpack(int cs, int ct, int hidden, const unsigned char* image, float* out, size_t len) {
+#define X(A, B, C) if (cs == A && ct == B && hidden == C) return fp8_unpack<A, B, C>(image, out, len);
+  NDGI_TC_SHAPES(X)
+#undef X
+  return 0;
+}
+
+size_t tc_fp8_workspace_bytes(int cs, int ct, int hidden) {
+#define X(A, B, C) if (cs == A && ct == B && hidden == C) return fp8_ws_bytes<A, B, C>();
+  NDGI_TC_SHAPES(X)
+#undef X
+  return 0;
+}
+
+cudaError_t launch_tc_prepare8(const DevModel& m, const float act_max[3], void* ws, cudaStream_t s) {
+#define X(A, B, C) if (m.cs == A && m.ct == B && m.hidden == C) return fp8_prepare<A, B, C>(m, act_max, ws, s);
+  NDGI_TC_SHAPES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+uint32_t tc_fp8_status_offset(int cs, int ct, int hidden) {
+#define X(A, B, C) if (cs == A && ct == B && hidden == C) return fp8_status_offset<A, B, C>();
+  NDGI_TC_SHAPES(X)
+#undef X
+  return 0;
 }
 
 TcPagesShape tc_default_pages_shape() { return TcPagesShape{1, 4, 1}; }

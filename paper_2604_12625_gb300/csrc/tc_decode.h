@@ -20,8 +20,19 @@ cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream
 cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const float* uvt, int64_t n, float* rgb,
                              cudaStream_t s);
 // staged: every model's features are at most half its lightmap resolution.
-cudaError_t launch_tc_pages(const PagesCtx& c, bool bf16, int cs, int ct, int hidden, const TcPagesShape& shape,
+// prec: 0 FP16, 1 BF16, 2 E4M3 (the workspace then comes from launch_tc_prepare8).
+cudaError_t launch_tc_pages(const PagesCtx& c, int prec, int cs, int ct, int hidden, const TcPagesShape& shape,
                             bool staged, const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s);
+// FP8 (E4M3) page decode: supported shapes, image size, image builder from the
+// calibration maxima (host array of 3), and the byte offset of the image's
+// status word (bit 0: a bias out of the representable range; bit 1: 1/a1 too large).
+bool tc_fp8_pages_supported(int cs, int ct, int hidden);
+size_t tc_fp8_workspace_bytes(int cs, int ct, int hidden);
+cudaError_t launch_tc_prepare8(const DevModel& m, const float act_max[3], void* ws, cudaStream_t s);
+uint32_t tc_fp8_status_offset(int cs, int ct, int hidden);
+// Stored FP8 parameters of a host copy of the image as FP32 (see ndgi_fp8_unpack);
+// returns the number of floats (written only if len is enough).
+size_t tc_fp8_unpack(int cs, int ct, int hidden, const unsigned char* image, float* out, size_t len);
 TcPagesShape tc_default_pages_shape();
 // Reads and clears the tensor-core kernels' device error word (-1 if unreadable).
 int tc_take_error();

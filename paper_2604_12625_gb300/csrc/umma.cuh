@@ -128,7 +128,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo_bytes, ui
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulate, A and B K-major,
-// both FP16 (bf16 = false) or both BF16, M x N tile.
+// both FP16 (bf16 = false) or both BF16, M x N tile.  kind::f8f6f4 keeps the
+// same fields, and E4M3 has format code 0 like FP16, so idesc_f16(M, N,
+// false) also describes an E4M3 x E4M3 -> FP32 MMA.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
   return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
@@ -157,6 +159,19 @@ __device__ __forceinline__ void umma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, ui
       : "memory");
 }
 
+// kind::f8f6f4 (E4M3 x E4M3 -> FP32): A[tmem] holds four 8-bit K elements per
+// 32-bit column (byte q of column j = element 4j + q), so one K step of 32
+// is again 8 columns; B is the 8-bit K-major shared-memory tile.
+__device__ __forceinline__ void umma_f8_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Arrives on the mbarrier once every previously issued MMA of this thread completes.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -167,6 +182,10 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 // Byte offset of element (row, k) in a K-major no-swizzle tile with K columns.
 __host__ __device__ constexpr uint32_t kmajor_offset(int row, int k, int K) {
   return (uint32_t)(((row >> 3) * (K >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+// The same for 8-bit elements: a core matrix is 8 rows x 16 elements.
+__host__ __device__ constexpr uint32_t kmajor_offset8(int row, int k, int K) {
+  return (uint32_t)(((row >> 3) * (K >> 4) + (k >> 4)) * 128 + (row & 7) * 16 + (k & 15));
 }
 
 }  // namespace ndgi

@@ -1,0 +1,136 @@
+"""GPU parity of the FP8 (E4M3) page decode against the oracle's FP8 decode.
+
+Bit-exact: the stored FP8 image (scales, weight codes, three-term biases) and
+the decode of a model on which every quantisation is exact.  Elsewhere the
+decode quantises activations that the two sides compute in different
+arithmetic (FP16 ring features and FP32 accumulation here, FP64 there), so an
+activation near an E4M3 rounding boundary may round to the neighbouring
+value: the gate is on the error distribution, and the error against the FP32
+master weights is reported beside it.  The calibration maxima are passed to
+both sides (rounded to FP32 first), so both derive the same scales.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _models import fp8_exact_model
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ndgi():
+    import paper_2604_12625_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def f32(a):
+    return np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("shape", [(16, 8, 64), (16, 16, 64), (16, 8, 32)])
+def test_fp8_image_matches_oracle(ndgi, shape):
+    cs, ct, H = shape
+    m = synth.model(70 + H + ct, 256, 256, 128, 128, cs, 24, ct, H, temporal_dtype="f16")
+    am = f32(oracle.fp8_calibrate(m, synth.random_queries(71, 1 << 12)))
+    model = ndgi.Model.from_arrays(m)
+    ndgi.ndgi_prepare_fp8(model, am)
+    got = ndgi.ndgi_fp8_unpack(model)
+    sc = oracle.fp8_scales(m, am)
+    for k in ("a1", "a2", "a3", "out", "s1", "s2", "s3"):
+        assert got["scales"][k] == sc[k], k
+    assert got["scales"]["status"] == 0
+    wq = oracle.fp8_weights(m, am)
+    for k in ("w1", "w2", "w3"):
+        assert np.array_equal(got[k].astype(np.float64), wq[k]), k
+    _, v2, b2 = oracle.fp8_bias(np.asarray(m["b2"], np.float64), sc["a3"])
+    _, v3, b3 = oracle.fp8_bias(np.asarray(m["b3"], np.float64), sc["out"])
+    assert got["scales"]["v2"] == v2 and got["scales"]["v3"] == v3
+    assert np.array_equal(got["b2"].astype(np.float64), b2)
+    assert np.array_equal(got["b3"].astype(np.float64), b3)
+
+
+def test_fp8_calibration_matches_oracle(ndgi):
+    m = synth.model(72, 256, 256, 128, 128, 16, 24, 8, 64, temporal_dtype="f16")
+    q = synth.random_queries(73, 1 << 14)
+    got = ndgi.ndgi_calibrate_fp8(ndgi.Model.from_arrays(m), torch.from_numpy(q).cuda()).cpu().numpy()
+    ref = oracle.fp8_calibrate(m, q)
+    assert np.all(np.abs(got - ref) <= 1e-5 * ref)
+
+
+def test_fp8_exact_model_is_bit_exact(ndgi):
+    m = fp8_exact_model()
+    model = ndgi.Model.from_arrays(m)
+    am = np.array([1.0, 3.5, 1.875])
+    ndgi.ndgi_prepare_fp8(model, am)
+    phys = torch.zeros((16, 48, 4), dtype=torch.float32, device="cuda")
+    plan = ndgi.PagesPlan([model], "fp8", 8, phys)
+    reqs = np.zeros(3, dtype=synth.PAGE_REQ_DTYPE)
+    for i, (t, x0) in enumerate(((0.0, 0), (0.375, 8), (0.875, 16))):
+        reqs[i] = (0, x0, 4, 16, 12, np.float32(t), 16 * i, 0)
+    r, n = ndgi.page_requests_to_device(reqs)
+    plan.decode(r, n)
+    assert plan.check() == (0, 0)
+    ndgi.ndgi_check()
+    ref = oracle.decode_pages([m], reqs, 48, 16, precision="fp8", act_max=am[None], fill=0.0)
+    assert np.array_equal(phys.cpu().numpy().astype(np.float64), ref)
+    assert np.array_equal(ref, oracle.decode_pages([m], reqs, 48, 16, precision="fp32", fill=0.0))
+    plan.close()
+
+
+def page_errors(got, ref, reqs):
+    """Per request: (max, rms) of |got - ref| over RGB, relative to the page's range."""
+    out = []
+    for r in reqs:
+        sl = (slice(r["dst_y"], r["dst_y"] + r["h"]), slice(r["dst_x"], r["dst_x"] + r["w"]))
+        a, b = got[sl][..., :3].astype(np.float64), ref[sl][..., :3]
+        rng = max(b.max() - b.min(), 1e-6)
+        out.append((np.abs(a - b).max() / rng, np.sqrt(((a - b) ** 2).mean()) / rng))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("ct", [8, 16])
+def test_fp8_pages_error_distribution(ndgi, ct):
+    sizes = (256, 256, 512, 1024)
+    maps = [synth.model(80 + i, s, s, s // 2, s // 2, 16, 24, ct, 64, temporal_dtype="f16")
+            for i, s in enumerate(sizes)]
+    am = np.stack([f32(oracle.fp8_calibrate(mm, synth.random_queries(90 + i, 1 << 14))) for i, mm in enumerate(maps)])
+    models = [ndgi.Model.from_arrays(mm) for mm in maps]
+    for mod, a in zip(models, am):
+        ndgi.ndgi_prepare_fp8(mod, a)
+    phys = torch.zeros((1024, 1024, 4), dtype=torch.float32, device="cuda")
+    plan = ndgi.PagesPlan(models, "fp8", 256, phys)
+    reqs = synth.ragged_page_requests(95, sizes, 40, slots_x=8, slot=128)
+    r, n = ndgi.page_requests_to_device(reqs)
+    plan.decode(r, n)
+    assert plan.check() == (0, 0)
+    ndgi.ndgi_check()
+    got = phys.cpu().numpy()
+    ref = oracle.decode_pages(maps, reqs, 1024, 1024, precision="fp8", act_max=am, fill=0.0)
+    e = page_errors(got, ref, reqs)
+    e32 = page_errors(got, oracle.decode_pages(maps, reqs, 1024, 1024, precision="fp32", fill=0.0), reqs)
+    print(f"ct={ct}: vs oracle FP8 max {e[:, 0].max():.3e} rms {e[:, 1].mean():.3e}; "
+          f"vs FP32 master max {e32[:, 0].max():.3e} rms {e32[:, 1].mean():.3e}")
+    # rounding flips of single activations give isolated errors of a few percent; the bulk agrees closely
+    assert e[:, 1].mean() <= 0.01 and e[:, 0].max() <= 0.2
+    assert e32[:, 1].mean() <= 0.08
+
+
+def test_fp8_refusals(ndgi):
+    m = synth.model(74, 64, 64, 32, 32, 16, 8, 8, 16, temporal_dtype="f32")
+    model = ndgi.Model.from_arrays(m)
+    with pytest.raises(ndgi.NdgiError):          # hidden 16: no FP8 image
+        ndgi.ndgi_prepare_fp8(model, [1.0, 1.0, 1.0])
+    m = synth.model(75, 64, 64, 32, 32, 16, 8, 8, 64, temporal_dtype="f32")
+    model = ndgi.Model.from_arrays(m)
+    with pytest.raises(ndgi.NdgiError):          # FP8 needs ndgi_prepare_fp8
+        ndgi.ndgi_prepare(model, "fp8")
+    with pytest.raises(ndgi.NdgiError):          # negative maximum
+        ndgi.ndgi_prepare_fp8(model, [1.0, -1.0, 1.0])
+    ndgi.ndgi_prepare_fp8(model, [1.0, 4.0, 4.0])
+    q = torch.from_numpy(synth.random_queries(76, 100)).cuda()
+    with pytest.raises(ndgi.NdgiError):          # points: FP8 is built for pages
+        ndgi.ndgi_decode_points(model, q, "fp8")
