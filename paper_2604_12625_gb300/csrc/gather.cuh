@@ -110,4 +110,119 @@ __device__ __forceinline__ void gather_f32(const DevModel& m, float u, float v, 
   }
 }
 
+// Palette table for gather_tc: as init_p35_lut, with the exponent bits of
+// 2^23 added to the constant term, so the byte dot product's integer result
+// read as a float is exactly 2^23 + P35 (P35 < 2^23 never carries into them).
+__device__ __forceinline__ void init_p35_lut_f(uint2* lut, int tid) {
+  init_p35_lut(lut, tid);
+  if (tid < 16) lut[tid].y += 0x4B000000u;
+}
+
+__device__ __forceinline__ float p35_plus_2p23(uint32_t lo, uint32_t hi, uint32_t shift, const uint2* lutf) {
+  const uint32_t k = bc4_index(lo, hi, shift);
+  const uint32_t m8 = (lo & 0xffu) > ((lo >> 8) & 0xffu) ? 8u : 0u;
+  const uint2 e = lutf[k | m8];
+  return __uint_as_float(__dp2a_lo(e.x, lo, e.y));
+}
+
+// Feature gather for the tensor-core decode, whose features are rounded to
+// FP16/BF16 right after: same taps and fractions as gather_f32, but the FP32
+// arithmetic is reassociated.  P35 comes out of the dot product as the float
+// 2^23 + P35 (lutf from init_p35_lut_f; one exact subtraction, no integer
+// conversion), the 1/8925 scale is folded into the four bilinear weights, and
+// the temporal rows are read 16 bytes at a time when the line is 16-byte
+// aligned and its rows are whole 16-byte units.
+template <int CS, int CT>
+__device__ __forceinline__ void gather_tc(const DevModel& m, float u, float v, float t, float (&x)[CS + CT],
+                                          const uint2* lutf) {
+  static_assert(CS % 2 == 0, "planes are read in pairs");
+  int x0, x1, y0, y1;
+  float fx, fy;
+  axis_setup(u, m.feat_w, m.address_mode, x0, x1, fx);
+  axis_setup(v, m.feat_h, m.address_mode, y0, y1, fy);
+  const int tx[4] = {x0, x1, x0, x1};
+  const int ty[4] = {y0, y0, y1, y1};
+  const uint4* line[4];
+  uint32_t shift[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    line[q] = reinterpret_cast<const uint4*>(m.bc4 + ((size_t)(ty[q] >> 2) * m.bw + (tx[q] >> 2)) * CS * 8);
+    shift[q] = 16u + 3u * (uint32_t)(((ty[q] & 3) << 2) | (tx[q] & 3));
+  }
+  const float gx = 1.0f - fx, gy = 1.0f - fy;
+  const float wq[4] = {gx * gy * kInv8925, fx * gy * kInv8925, gx * fy * kInv8925, fx * fy * kInv8925};
+  constexpr int G = CS < 8 ? CS : 8;
+  const bool same_x = (x0 >> 2) == (x1 >> 2), same_y = (y0 >> 2) == (y1 >> 2);
+#pragma unroll
+  for (int c0 = 0; c0 < CS; c0 += G) {
+    uint4 b[4][G / 2];
+#pragma unroll
+    for (int e = 0; e < G / 2; ++e) {
+      b[0][e] = __ldg(line[0] + c0 / 2 + e);
+      if (!same_x) b[1][e] = __ldg(line[1] + c0 / 2 + e);
+      if (!same_y) b[2][e] = __ldg(line[2] + c0 / 2 + e);
+      if (!same_x && !same_y) b[3][e] = __ldg(line[3] + c0 / 2 + e);
+    }
+#pragma unroll
+    for (int e = 0; e < G / 2; ++e) {
+      if (same_x) b[1][e] = b[0][e];
+      if (same_y) b[2][e] = b[0][e];
+      if (same_x || same_y) b[3][e] = same_x ? b[2][e] : b[1][e];
+    }
+#pragma unroll
+    for (int e = 0; e < G / 2; ++e) {
+      const int c = c0 + 2 * e;
+      float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float p0 = p35_plus_2p23(b[q][e].x, b[q][e].y, shift[q], lutf) - 8388608.0f;
+        const float p1 = p35_plus_2p23(b[q][e].z, b[q][e].w, shift[q], lutf) - 8388608.0f;
+        a0 = fmaf(wq[q], p0, a0);
+        a1 = fmaf(wq[q], p1, a1);
+      }
+      x[c] = a0;
+      x[c + 1] = a1;
+    }
+  }
+  int j0, j1;
+  float a;
+  temporal_setup(t, m.t_count, j0, j1, a);
+  const float ga = 1.0f - a;
+  const bool vec = (reinterpret_cast<uintptr_t>(m.temporal) & 15u) == 0u;
+  if (CT % 8 == 0 && m.temporal_f16 && vec) {
+    const uint4* r0 = reinterpret_cast<const uint4*>(static_cast<const __half*>(m.temporal) + (size_t)j0 * CT);
+    const uint4* r1 = reinterpret_cast<const uint4*>(static_cast<const __half*>(m.temporal) + (size_t)j1 * CT);
+#pragma unroll
+    for (int g = 0; g < (CT % 8 == 0 ? CT / 8 : 0); ++g) {
+      const uint4 k0 = __ldg(r0 + g), k1 = __ldg(r1 + g);
+      const uint32_t w0[4] = {k0.x, k0.y, k0.z, k0.w}, w1[4] = {k1.x, k1.y, k1.z, k1.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&w0[h]));
+        const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&w1[h]));
+        x[CS + 8 * g + 2 * h] = ga * f0.x + a * f1.x;
+        x[CS + 8 * g + 2 * h + 1] = ga * f0.y + a * f1.y;
+      }
+    }
+  } else if (CT % 4 == 0 && !m.temporal_f16 && vec) {
+    const float4* r0 = reinterpret_cast<const float4*>(static_cast<const float*>(m.temporal) + (size_t)j0 * CT);
+    const float4* r1 = reinterpret_cast<const float4*>(static_cast<const float*>(m.temporal) + (size_t)j1 * CT);
+#pragma unroll
+    for (int g = 0; g < (CT % 4 == 0 ? CT / 4 : 0); ++g) {
+      const float4 k0 = __ldg(r0 + g), k1 = __ldg(r1 + g);
+      x[CS + 4 * g] = ga * k0.x + a * k1.x;
+      x[CS + 4 * g + 1] = ga * k0.y + a * k1.y;
+      x[CS + 4 * g + 2] = ga * k0.z + a * k1.z;
+      x[CS + 4 * g + 3] = ga * k0.w + a * k1.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CT; ++c) {
+      const float k0 = load_temporal(m.temporal, m.temporal_f16, j0 * CT + c);
+      const float k1 = load_temporal(m.temporal, m.temporal_f16, j1 * CT + c);
+      x[CS + c] = ga * k0 + a * k1;
+    }
+  }
+}
+
 }  // namespace ndgi

@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
   copy16(sm + S::kW, ws, L::kShared, tid, kLaneThreads * NWG);
   copy16(sm + S::kB1, ws + L::kB1P, H * L::K1P * 2, tid, kLaneThreads * NWG);
   const uint2* lut = reinterpret_cast<const uint2*>(sm + S::kLut);
-  init_p35_lut(reinterpret_cast<uint2*>(sm + S::kLut), tid);
+  init_p35_lut_f(reinterpret_cast<uint2*>(sm + S::kLut), tid);
   const uint32_t tbase = cta_setup<SL * NWG, E::kSlotCols>(bars, &slot, tid);
   const uint32_t base = smem_addr(sm);
   E e;
@@ -624,6 +624,21 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
   }
   const int64_t tiles = (n + 127) / 128;
   const int64_t lanes = (int64_t)gridDim.x * NWG, lane_id = (int64_t)blockIdx.x * NWG + e.wg;
+  const int64_t qstep = (int64_t)SL * lanes * 128;   // from a slot's tile to its next tile, per query
+  // Each slot's next query coordinates are loaded one tile ahead, so their
+  // DRAM latency overlaps the current tile.  (Prefetching the next tile's
+  // block lines into L1 as well measured 6% slower.)
+  float nu[SL], nv[SL], nt[SL];
+#pragma unroll
+  for (int s = 0; s < SL; ++s) {
+    const int64_t q0 = (lane_id + (int64_t)s * lanes) * 128 + t;
+    nu[s] = nv[s] = nt[s] = 0.0f;
+    if (q0 < n) {
+      nu[s] = __ldcs(uvt + 3 * q0);
+      nv[s] = __ldcs(uvt + 3 * q0 + 1);
+      nt[s] = __ldcs(uvt + 3 * q0 + 2);
+    }
+  }
   for (int64_t round = 0; !timed_out; ++round) {
     bool active[SL], any = false;
 #pragma unroll
@@ -647,10 +662,16 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
         }
       }
       if (!active[s]) continue;
-      const int64_t q = tile * 128 + t;
+      const int64_t q = tile * 128 + t, qn = q + qstep;
+      const float qu = nu[s], qv = nv[s], qt = nt[s];
+      if (qn < n) {
+        nu[s] = __ldcs(uvt + 3 * qn);
+        nv[s] = __ldcs(uvt + 3 * qn + 1);
+        nt[s] = __ldcs(uvt + 3 * qn + 2);
+      }
       float x[L::CIN];
       if (q < n) {
-        gather_f32<CS, CT>(m, uvt[3 * q], uvt[3 * q + 1], uvt[3 * q + 2], x, nullptr, lut);
+        gather_tc<CS, CT>(m, qu, qv, qt, x, lut);
       } else {
 #pragma unroll
         for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
@@ -1143,10 +1164,10 @@ cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const
     using S = PointsSmem<A, B, C>;                                                                              \
     auto kern = bf16 ? k_points_tc<A, B, C, true, kPointsLanes, kPointsSlots>                                   \
                      : k_points_tc<A, B, C, false, kPointsLanes, kPointsSlots>;                                 \
-    cudaError_t e = set_smem(kern, tc_smem(S::kBytes));                                                         \
+    const uint32_t smem = tc_smem(S::kBytes);                                                                   \
+    cudaError_t e = set_smem(kern, smem);                                                                       \
     if (e != cudaSuccess) return e;                                                                             \
-    kern<<<grid, kLaneThreads * kPointsLanes, tc_smem(S::kBytes), s>>>(m, static_cast<const unsigned char*>(ws), \
-                                                                       uvt, n, rgb);                            \
+    kern<<<grid, kLaneThreads * kPointsLanes, smem, s>>>(m, static_cast<const unsigned char*>(ws), uvt, n, rgb); \
     return cudaGetLastError();                                                                                  \
   }
   NDGI_TC_SHAPES(X)
