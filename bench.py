@@ -152,6 +152,26 @@ def time_oracle(m, q_all, target_s, min_n=1 << 14):
     return n2 / dt / 1e9, n2, dt, nt
 
 
+def max_over_ranks(ms, dist, device):
+    """The step time every rank reports: the maximum over ranks (weak scaling, replicas)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms_per_step):
+    """Whole-job throughput in G units/s: the units all ranks processed over the slowest rank's step time."""
+    return world * units_per_rank / (ms_per_step * 1e-3) / 1e9
+
+
+def rank_query_seed(rank):
+    """Each rank decodes its own queries (replicas, no data-path exchange)."""
+    return 2 + 1000 * rank
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle, timed on the host cores (rank 0 only)."""
     if rank != 0:
@@ -166,7 +186,7 @@ def run_reference(args, rank, world):
     oracle.decode_points(m, q[:probe], nthreads=nt)
     per_q = (time.perf_counter() - t0) / probe
     total_steps = max(1, args.steps + args.warmup)
-    per_step = int(np.clip(60.0 / total_steps / max(per_q, 1e-9), 1 << 12, N_QUERIES))
+    per_step = int(np.clip(args.ref_seconds / total_steps / max(per_q, 1e-9), 1 << 12, N_QUERIES))
     for w in range(args.warmup):
         oracle.decode_points(m, q[:per_step], nthreads=nt)
     t0 = time.perf_counter()
@@ -214,7 +234,7 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
         steps = args.steps if prec == "fp16" else max(3, min(args.steps, 10))
         ms, clocks = timed(lambda: plan.decode(r_dev, n_dev), steps, args.warmup, sample_clocks=(prec == "fp16"))
         st, err_word = plan.check()
-        entry = {"value": texels / (ms / steps * 1e-3) / 1e9, "unit": "Gtexels/s", "ms_per_frame": ms / steps,
+        entry = {"value": job_value(texels, args.world, ms / steps), "unit": "Gtexels/s", "ms_per_frame": ms / steps,
                  "device_error_word": err_word, "device_check": check_status(ndgi), "plan_shape": plan.info()}
         if prec == "fp16":
             entry["clocks"] = clocks
@@ -280,6 +300,7 @@ def bench_fit(args, ndgi, torch):
             "loss_first": float(log[0]), "loss_last": float(log[-1]),
             "loss_every_100": [float(x) for x in log],
             "psnr_db_last": float(10 * np.log10(rng * rng / max(log[-1], 1e-30))),
+            "scope": "one rank (under torchrun every rank fits its own replica; no gradient exchange)",
             "device_check": check_status(ndgi)}
 
 
@@ -312,7 +333,7 @@ def bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank):
             plan.autotune(r_dev, n_dev, len(reqs))
         steps = max(3, min(args.steps, 10)) if prec != "fp32" else 3
         ms, _ = timed(lambda: plan.decode(r_dev, n_dev), steps, 2)
-        entry = {"value": texels / (ms / steps * 1e-3) / 1e9, "unit": "Gtexels/s", "ms_per_frame": ms / steps,
+        entry = {"value": job_value(texels, args.world, ms / steps), "unit": "Gtexels/s", "ms_per_frame": ms / steps,
                  "device_check": check_status(ndgi), "plan_shape": plan.info()}
         if rank == 0:
             import oracle
@@ -361,6 +382,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the fit and scale measurements")
     ap.add_argument("--queries-log2", type=int, default=24,
                     help="point queries per step = 2^this (24 = the headline workload; smaller for profiling)")
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="reference arm: seconds of oracle work over the warm-up and timed steps")
     ap.add_argument("--page-requests", type=int, default=4096,
                     help="page requests per frame (4096 = the page workload; smaller for profiling)")
     args = ap.parse_args()
@@ -368,6 +391,7 @@ def main():
     nq = 1 << args.queries_log2
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    args.world = world
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -385,7 +409,7 @@ def main():
 
     peaks, peak_kind = load_peaks()
     m = synth.points_model_2048(2)
-    q = synth.random_queries(2 + 1000 * rank, nq)
+    q = synth.random_queries(rank_query_seed(rank), nq)
     model = ndgi.Model.from_arrays(m)
     uvt = torch.from_numpy(q).cuda()
     out = torch.empty((nq, 3), dtype=torch.float32, device="cuda")
@@ -415,11 +439,7 @@ def main():
         e1.synchronize()
         barrier()
         clocks = sampler.stop() if sampler else None
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         return ms, clocks
 
     ws = model.workspace(prec)
@@ -433,12 +453,12 @@ def main():
     ms_main, clocks = timed(step_main, args.steps, args.warmup, sample_clocks=True)
     ms_step = ms_main / args.steps
     device_check = {"points": check_status(ndgi)}
-    value = world * nq / (ms_step * 1e-3) / 1e9
+    value = job_value(nq, world, ms_step)
 
     # FP32 plain decode beside it (fewer steps: it is ~10x slower)
     k32 = max(3, min(args.steps, 20))
     ms32, _ = timed(step_fp32, k32, 3)
-    fp32_gt = world * nq / (ms32 / k32 * 1e-3) / 1e9
+    fp32_gt = job_value(nq, world, ms32 / k32)
 
     # Accuracy on a seeded sample, against the FP64 oracle (rank 0)
     errs = {}
@@ -464,7 +484,7 @@ def main():
 
     ke = max(3, min(args.steps, 20))
     ms_e2e, _ = timed(step_e2e, ke, 3)
-    e2e_val = world * nq / (ms_e2e / ke * 1e-3) / 1e9
+    e2e_val = job_value(nq, world, ms_e2e / ke)
 
     pages = None
     if not args.no_pages:
