@@ -42,9 +42,9 @@ METRIC = "Gtexels/s decoded (BC fetch+temporal lerp+MLP), FP16-TC vs FP32 plain 
 # the ones captured: the hash below is compared at run time and the figure drops to null once they change.
 TRAFFIC_SOURCES = ("tc_decode.cu", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h")
 NCU_TRAFFIC = {
-    "k_points_tc": {"src": "6b9dfecde7717628", "read": 109112832, "write": 64917760, "units": 1 << 23,
+    "k_points_tc": {"src": "cd5025f03db090c5", "read": 109111040, "write": 44435200, "units": 1 << 23,
                     "profile": "profiles/k_points_tc_points_2048_atlas.md"},
-    "k_pages_tc": {"src": "6b9dfecde7717628", "read": 14556672, "write": 75104768, "units": 1024 * 128 * 128,
+    "k_pages_tc": {"src": "cd5025f03db090c5", "read": 14567168, "write": 75292160, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_tc_pages_8_lightmaps.md"},
 }
 
@@ -280,12 +280,13 @@ def bench_fit(args, ndgi, torch):
     p = synth.fit_init(3, 512, 512, 16, 24, 8, 64)
     st = ndgi.FitState.from_arrays(p, 1024, 1024)
     tg = torch.from_numpy(targets).cuda()
-    batch, steps = 1 << 20, 2000
+    batch, steps = 1 << 20, args.fit_steps
     # warm-up (graph capture, kernel load) on a throw-away copy of the parameters
     warm = ndgi.FitState({k: v.clone() for k, v in st.t.items()}, 1024, 1024)
     ndgi.ndgi_encode_fit(warm, tg, ndgi.fit_config(steps=3, batch=batch, seed=1))
     torch.cuda.synchronize()
-    cfg = ndgi.fit_config(steps=steps, batch=batch, lr=1e-2, freeze_steps=200, loss_every=100, seed=7)
+    cfg = ndgi.fit_config(steps=steps, batch=batch, lr=1e-2, freeze_steps=steps // 10,
+                          loss_every=max(1, min(100, steps // 4)), seed=7)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -295,10 +296,10 @@ def bench_fit(args, ndgi, torch):
     ms = e0.elapsed_time(e1)
     log = log.cpu().numpy()
     rng = float(targets.max()) - float(targets.min())
-    return {"workload": FIT_WORKLOAD, "steps": steps, "batch": batch, "seconds": ms / 1e3,
+    return {"workload": FIT_WORKLOAD.replace("2000 steps", f"{steps} steps"), "steps": steps, "batch": batch, "seconds": ms / 1e3,
             "ms_per_step": ms / steps, "samples_per_s": steps * batch / (ms / 1e3),
             "loss_first": float(log[0]), "loss_last": float(log[-1]),
-            "loss_every_100": [float(x) for x in log],
+            "loss_every": cfg.loss_every, "loss_log": [float(x) for x in log],
             "psnr_db_last": float(10 * np.log10(rng * rng / max(log[-1], 1e-30))),
             "scope": "one rank (under torchrun every rank fits its own replica; no gradient exchange)",
             "device_check": check_status(ndgi)}
@@ -380,6 +381,8 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp16", "bf16", "fp32"])
     ap.add_argument("--no-pages", action="store_true", help="skip the page-decode measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the fit and scale measurements")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 16384^2 scale frame")
+    ap.add_argument("--fit-steps", type=int, default=2000, help="fit steps (2000 = the fit workload)")
     ap.add_argument("--queries-log2", type=int, default=24,
                     help="point queries per step = 2^this (24 = the headline workload; smaller for profiling)")
     ap.add_argument("--ref-seconds", type=float, default=60.0,
@@ -491,7 +494,8 @@ def main():
         pages = bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank)
     fit = scale = None
     if not args.no_extra:
-        scale = bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank)
+        if not args.no_scale:
+            scale = bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank)
         fit = bench_fit(args, ndgi, torch)
 
     if rank != 0:
