@@ -137,6 +137,30 @@ def cpu_cores():
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def time_oracle_one_core(m, q_all, target_s=3.0, min_n=1 << 11):
+    """The FP64 oracle on a single host core (queries per second)."""
+    import oracle
+    n = min_n
+    t0 = time.perf_counter()
+    oracle.decode_points(m, q_all[:n], nthreads=1)
+    dt = time.perf_counter() - t0
+    n2 = int(min(q_all.shape[0], max(min_n, n * target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.decode_points(m, q_all[:n2], nthreads=1)
+    return n2 / (time.perf_counter() - t0)
+
+
 def time_oracle(m, q_all, target_s, min_n=1 << 14):
     """Times the FP64 oracle on a bounded prefix of the queries sized for ~target_s seconds."""
     import oracle
@@ -238,6 +262,12 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
                  "device_error_word": err_word, "device_check": check_status(ndgi), "plan_shape": plan.info()}
         if prec == "fp16":
             entry["clocks"] = clocks
+            scratch = torch.empty(1 << 28, dtype=torch.float32, device="cuda")   # 1 GiB, written before each frame
+            med = args.per_step_median(lambda: plan.decode(r_dev, n_dev), 20, flush=lambda: scratch.fill_(1.0))
+            entry["cold_l2"] = {"ms_per_frame_median_of_20": med, "value": job_value(texels, args.world, med),
+                                "unit": "Gtexels/s", "flush": "1 GiB scratch write before each frame"}
+            entry["warm_ms_per_frame_median_of_20"] = args.per_step_median(lambda: plan.decode(r_dev, n_dev), 20)
+            del scratch
         if check_err and rank == 0:
             import oracle
             pick = np.random.default_rng(5).choice(len(reqs), 12, replace=False)
@@ -445,6 +475,22 @@ def main():
         ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         return ms, clocks
 
+    def per_step_median(fn, k, flush=None):
+        """Median of k individually timed steps (events around each); flush() runs before each, untimed."""
+        times = []
+        for _ in range(k):
+            if flush is not None:
+                flush()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        return float(np.median(times))
+
+    args.per_step_median = per_step_median
     ws = model.workspace(prec)
 
     def step_main():
@@ -454,6 +500,7 @@ def main():
         ndgi.ndgi_decode_points(model, uvt, "fp32", out=out)
 
     ms_main, clocks = timed(step_main, args.steps, args.warmup, sample_clocks=True)
+    ms_median = per_step_median(step_main, 20)
     ms_step = ms_main / args.steps
     device_check = {"points": check_status(ndgi)}
     value = job_value(nq, world, ms_step)
@@ -524,8 +571,10 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         gt, n_s, dt, nt = time_oracle(m, q, 12.0)
+        one = time_oracle_one_core(m, q)
         cpu = {"value": gt, "unit": "Gtexels/s", "cores": nt, "kind": "oracle",
-               "sample": f"first {n_s} of the 2^{args.queries_log2} queries, FP64 oracle ({dt:.1f} s)"}
+               "sample": f"first {n_s} of the 2^{args.queries_log2} queries, FP64 oracle ({dt:.1f} s)",
+               "per_core_gtexels_s": one / 1e9, "cpu_model": cpu_model()}
 
     line = {
         "metric": METRIC, "value": value, "unit": "Gtexels/s", "n_gpus": world, "steps": args.steps,
@@ -539,6 +588,7 @@ def main():
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "Gtexels/s", "h2d_bytes_per_step": nq * 12,
                 "d2h_bytes_per_step": nq * 12},
+        "ms_per_step_median_of_20": ms_median,
         "gpu_launches": args.steps, "clocks": clocks,
         "pages": pages, "scale": scale, "fit": fit,
     }

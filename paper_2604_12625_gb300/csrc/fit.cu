@@ -31,6 +31,7 @@ struct FitArgs {
   const float *ea, *eb, *w, *temporal, *w1, *b1, *w2, *b2, *w3, *b3;
   float *g_ea, *g_eb, *g_w, *g_temporal, *g_w1, *g_b1, *g_w2, *g_b2, *g_w3, *g_b3;
   int relaxed;
+  int vec_red;                  // g_ea, g_eb 16-byte aligned: endpoint gradients use vector reductions
   int64_t n;
   const int32_t* samples;       // mode 0
   const float* grad_rgb;        // mode 0
@@ -156,35 +157,78 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_forward(FitArgs a, float* _
 }
 
 // ---------------------------------------------------------------------------
-// Backward (persistent, tiles of 128 samples).  MODE 0: samples + dL/drgb
-// given.  MODE 1: samples drawn on device, dL/drgb from the MSE against the
-// FP16 targets, FP64 loss accumulated.
+// Backward (persistent, tiles of kFitTile samples, kFitQ threads per sample).
+// MODE 0: samples + dL/drgb given.  MODE 1: samples drawn on device, dL/drgb
+// from the MSE against the FP16 targets, FP64 loss accumulated.
+//
+// Each sample's forward and backward is split over kFitQ = 4 threads (q),
+// each computing HQ = H/4 of the hidden units, which gives 16 warps per SM
+// (the per-tile buffers the weight-gradient contraction reads, about 1 KB per
+// sample, bound the tile).  Shared-memory layouts are chosen so that the four
+// threads of a sample never hit the same bank with different addresses:
+// weight rows are stored "skewed" (4 padding floats after each quarter's HQ
+// columns) so the quarters' float4 reads fall in distinct banks, the backward
+// reads transposed skewed copies (W2^T, W1^T) so every thread of a sample
+// walks the same row, and activation rows are padded to whole float4s.
 // ---------------------------------------------------------------------------
+constexpr int kBwdThreads = 512;
+constexpr int kFitQ = kBwdThreads / kFitTile;
+
 template <int CS, int CT, int H>
 struct FitSmem {
   static constexpr int CIN = CS + CT;
-  static constexpr int LX = CIN + 1, LH = H + 1;
-  static constexpr int kW1 = 0, kB1 = kW1 + CIN * H, kW2 = kB1 + H, kW2t = kW2 + H * H, kB2 = kW2t + H * H;
+  static constexpr int HQ = H / kFitQ;
+  static constexpr int HS = H + 4 * kFitQ;          // skewed row: HQ columns + 4 padding floats per quarter
+  static constexpr int LX = CIN + 4, LH = H + 4;    // activation rows (float4-aligned)
+  static constexpr int kW1s = 0;                     // [CIN][HS]  W1, skewed columns
+  static constexpr int kW2s = kW1s + CIN * HS;       // [H][HS]    W2, skewed columns
+  static constexpr int kW2t = kW2s + H * HS;         // [H][HS]    W2^T (row o, skewed columns i)
+  static constexpr int kW1t = kW2t + H * HS;         // [H][CIN]   W1^T (row o, columns k)
+  static constexpr int kB1 = kW1t + H * CIN, kB2 = kB1 + H;
   static constexpr int kW3 = kB2 + H, kB3 = kW3 + H * 4;
   static constexpr int kX = kB3 + 4, kH1 = kX + kFitTile * LX, kH2 = kH1 + kFitTile * LH;
-  static constexpr int kG1 = kH2 + kFitTile * LH, kDY = kG1 + kFitTile * LH, kGK = kDY + kFitTile * 4;
+  static constexpr int kG1 = kH2 + kFitTile * LH, kY = kG1 + kFitTile * LH, kDY = kY + kFitTile * kFitQ * 4;
+  static constexpr int kGK = kDY + kFitTile * 4;
   static constexpr int kFloatsNoGK = kGK;
+  static_assert(kW2s % 4 == 0 && kW2t % 4 == 0 && kW1t % 4 == 0 && kW3 % 4 == 0 && kX % 4 == 0 && kH1 % 4 == 0 &&
+                    kY % 4 == 0 && kDY % 4 == 0 && HS % 4 == 0 && CIN % 4 == 0,
+                "float4 rows");
+  __host__ __device__ static constexpr int skew(int o) { return o + 4 * (o / HQ); }
 };
 
+// N consecutive floats of shared memory (N = 1, 2, 4; 4N-byte aligned).
+template <int N>
+__device__ __forceinline__ void lds(const float* p, float (&v)[N]) {
+  if constexpr (N == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (N == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = p[i];
+  }
+}
+
 template <int CS, int CT, int H, int MODE>
-__global__ void __launch_bounds__(kFitThreads, 1) k_fit_backward(FitArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
   using L = FitSmem<CS, CT, H>;
   constexpr int CIN = CS + CT;
-  constexpr int LX = L::LX, LH = L::LH;
-  constexpr int RPT = kFitThreads / H;          // row stride of owned weight-gradient entries
-  constexpr int K2 = H * H / kFitThreads;       // owned entries of dW2
-  constexpr int K1 = CIN * H / kFitThreads;     // owned entries of dW1
-  static_assert(kFitThreads % H == 0 && (CIN * H) % kFitThreads == 0 && (H * H) % kFitThreads == 0, "shape");
+  constexpr int LX = L::LX, LH = L::LH, HS = L::HS, HQ = L::HQ;
+  constexpr int SC = CS / kFitQ, TC = CT / kFitQ;   // spatial / temporal channels per thread of a sample
+  static_assert(CS % kFitQ == 0 && CT % kFitQ == 0 && SC <= 4 && TC <= 4 && (SC & (SC - 1)) == 0 &&
+                    (TC & (TC - 1)) == 0 && H % kFitQ == 0 && HQ % 4 == 0 && kBwdThreads % H == 0,
+                "shape");
+  constexpr bool kBlocked = H == 64;                 // dW2 as 2 x 4 register blocks per thread
+  constexpr int K2 = (H * H + kBwdThreads - 1) / kBwdThreads;     // generic dW2 ownership (other H)
+  constexpr int K1 = (CIN * H + kBwdThreads - 1) / kBwdThreads;   // dW1 entries per thread (rows k < CIN)
   extern __shared__ __align__(16) float sm[];
-  float* sW1 = sm + L::kW1;
-  float* sB1 = sm + L::kB1;
-  float* sW2 = sm + L::kW2;
+  float* sW1s = sm + L::kW1s;
+  float* sW2s = sm + L::kW2s;
   float* sW2t = sm + L::kW2t;
+  float* sW1t = sm + L::kW1t;
+  float* sB1 = sm + L::kB1;
   float* sB2 = sm + L::kB2;
   float* sW3 = sm + L::kW3;
   float* sB3 = sm + L::kB3;
@@ -192,26 +236,40 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_backward(FitArgs a) {
   float* sH1 = sm + L::kH1;
   float* sH2 = sm + L::kH2;     // H2, then dZ2
   float* sG1 = sm + L::kG1;     // dZ1
+  float* sY = sm + L::kY;       // [tile][Q][4] partial outputs
   float* sDY = sm + L::kDY;
   float* sGK = sm + L::kGK;     // [T][CT] temporal gradient
   const int tid = threadIdx.x;
-  for (int i = tid; i < CIN * H; i += kFitThreads) sW1[i] = a.w1[i];
-  for (int i = tid; i < H * H; i += kFitThreads) {
-    sW2[i] = a.w2[i];
-    sW2t[(i % H) * H + i / H] = a.w2[i];
+  for (int i = tid; i < CIN * HS; i += kBwdThreads) sW1s[i] = 0.0f;
+  for (int i = tid; i < 2 * H * HS; i += kBwdThreads) sW2s[i] = 0.0f;   // W2s and W2t
+  __syncthreads();
+  for (int i = tid; i < CIN * H; i += kBwdThreads) {
+    const int k = i / H, o = i % H;
+    const float w = a.w1[i];
+    sW1s[k * HS + L::skew(o)] = w;
+    sW1t[o * CIN + k] = w;
   }
-  for (int i = tid; i < H; i += kFitThreads) {
+  for (int i = tid; i < H * H; i += kBwdThreads) {
+    const int r = i / H, c = i % H;
+    const float w = a.w2[i];   // W2[r][c]: input r, output c
+    sW2s[r * HS + L::skew(c)] = w;
+    sW2t[c * HS + L::skew(r)] = w;
+  }
+  for (int i = tid; i < H; i += kBwdThreads) {
     sB1[i] = a.b1[i];
     sB2[i] = a.b2[i];
   }
-  for (int i = tid; i < H * 4; i += kFitThreads) sW3[i] = (i % 4) < 3 ? a.w3[(i / 4) * 3 + (i % 4)] : 0.0f;
+  for (int i = tid; i < H * 4; i += kBwdThreads) sW3[i] = (i % 4) < 3 ? a.w3[(i / 4) * 3 + (i % 4)] : 0.0f;
   if (tid < 4) sB3[tid] = tid < 3 ? a.b3[tid] : 0.0f;
-  for (int i = tid; i < a.t_count * CT; i += kFitThreads) sGK[i] = 0.0f;
+  for (int i = tid; i < a.t_count * CT; i += kBwdThreads) sGK[i] = 0.0f;
   __syncthreads();
 
-  float acc2[K2], acc1[K1], acc3[3] = {0, 0, 0}, accb = 0.0f, accb12 = 0.0f;
+  const int r = tid / kFitQ, q = tid % kFitQ;   // this thread's sample in the tile and its quarter
+  const int o0 = q * HQ;                         // its hidden units o0 .. o0+HQ-1
+  const int c0 = L::skew(o0);                    // their first column in a skewed row
+  float acc2[kBlocked ? 8 : K2], acc1[K1], acc3 = 0.0f, accb2[4] = {0, 0, 0, 0}, accb1 = 0.0f;
 #pragma unroll
-  for (int k = 0; k < K2; ++k) acc2[k] = 0.0f;
+  for (int k = 0; k < (kBlocked ? 8 : K2); ++k) acc2[k] = 0.0f;
 #pragma unroll
   for (int k = 0; k < K1; ++k) acc1[k] = 0.0f;
   double loss = 0.0;
@@ -220,12 +278,9 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_backward(FitArgs a) {
 
   const int64_t n_tiles = (a.n + kFitTile - 1) / kFitTile;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int64_t s = tile * kFitTile + tid;
+    const int64_t s = tile * kFitTile + r;
     const bool valid = s < a.n;
     int ix = 0, iy = 0, j = 0;
-    float h1[H];
-    float dy0 = 0.f, dy1 = 0.f, dy2 = 0.f;
-    // ---- phase A: forward of this thread's sample ----
     if (valid) {
       if (MODE == 0) {
         ix = a.samples[3 * s];
@@ -234,204 +289,337 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_backward(FitArgs a) {
       } else {
         draw_sample(a.seed, step, s, a.lm_w, a.lm_h, a.t_count, ix, iy, j);
       }
-      float x[CIN];
-      fit_gather<CS, CT>(a, ix, iy, j, x);
-#pragma unroll
-      for (int i = 0; i < CIN; ++i) sX[tid * LX + i] = x[i];
-#pragma unroll
-      for (int o = 0; o < H; ++o) h1[o] = sB1[o];
-#pragma unroll
-      for (int i = 0; i < CIN; ++i) {
-#pragma unroll
-        for (int o = 0; o < H; ++o) h1[o] = fmaf(x[i], sW1[i * H + o], h1[o]);
-      }
-#pragma unroll
-      for (int o = 0; o < H; ++o) {
-        h1[o] = fmaxf(h1[o], 0.0f);
-        sH1[tid * LH + o] = h1[o];
-      }
-      float y0 = sB3[0], y1 = sB3[1], y2 = sB3[2];
-#pragma unroll 4
-      for (int o = 0; o < H; ++o) {
-        float z = sB2[o];
-#pragma unroll
-        for (int i = 0; i < H; ++i) z = fmaf(h1[i], sW2t[o * H + i], z);
-        const float h = fmaxf(z, 0.0f);
-        sH2[tid * LH + o] = h;
-        y0 = fmaf(h, sW3[o * 4 + 0], y0);
-        y1 = fmaf(h, sW3[o * 4 + 1], y1);
-        y2 = fmaf(h, sW3[o * 4 + 2], y2);
-      }
-      if (MODE == 0) {
-        dy0 = a.grad_rgb[3 * s];
-        dy1 = a.grad_rgb[3 * s + 1];
-        dy2 = a.grad_rgb[3 * s + 2];
-      } else {
-        const __half* tg = a.targets + (((int64_t)j * a.lm_h + iy) * a.lm_w + ix) * 3;
-        const float d0 = y0 - __half2float(tg[0]), d1 = y1 - __half2float(tg[1]), d2 = y2 - __half2float(tg[2]);
-        loss += (double)d0 * d0 + (double)d1 * d1 + (double)d2 * d2;
-        const float sc = 2.0f / (3.0f * (float)a.n);
-        dy0 = sc * d0;
-        dy1 = sc * d1;
-        dy2 = sc * d2;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < CIN; ++i) sX[tid * LX + i] = 0.0f;
-#pragma unroll
-      for (int o = 0; o < H; ++o) {
-        sH1[tid * LH + o] = 0.0f;
-        sH2[tid * LH + o] = 0.0f;
-      }
     }
-    sDY[tid * 4 + 0] = dy0;
-    sDY[tid * 4 + 1] = dy1;
-    sDY[tid * 4 + 2] = dy2;
-    sDY[tid * 4 + 3] = 0.0f;
-    __syncthreads();
-    // ---- phase B: dW3 += H2^T dY, db3 += colsum dY ----
-    if (tid < H) {
-      for (int r = 0; r < kFitTile; ++r) {
-        const float h = sH2[r * LH + tid];
-        acc3[0] = fmaf(h, sDY[r * 4 + 0], acc3[0]);
-        acc3[1] = fmaf(h, sDY[r * 4 + 1], acc3[1]);
-        acc3[2] = fmaf(h, sDY[r * 4 + 2], acc3[2]);
-      }
-    } else if (tid >= kFitThreads - 3) {
-      const int c = tid - (kFitThreads - 3);
-      for (int r = 0; r < kFitTile; ++r) accb += sDY[r * 4 + c];
-    }
-    __syncthreads();
-    // ---- phase C: per-sample backward through layers 2, 1 and the gather ----
-    if (valid) {
-      float gz2[H];
-#pragma unroll
-      for (int o = 0; o < H; ++o) {
-        const float h = sH2[tid * LH + o];
-        const float g = sW3[o * 4] * dy0 + sW3[o * 4 + 1] * dy1 + sW3[o * 4 + 2] * dy2;
-        gz2[o] = h > 0.0f ? g : 0.0f;
-        sH2[tid * LH + o] = gz2[o];
-      }
-      float gz1[H];
-#pragma unroll 4
-      for (int i = 0; i < H; ++i) {
-        const float4* row = reinterpret_cast<const float4*>(sW2 + i * H);
-        float g = 0.0f;
-#pragma unroll
-        for (int o4 = 0; o4 < H / 4; ++o4) {
-          const float4 w = row[o4];
-          g = fmaf(w.x, gz2[4 * o4], g);
-          g = fmaf(w.y, gz2[4 * o4 + 1], g);
-          g = fmaf(w.z, gz2[4 * o4 + 2], g);
-          g = fmaf(w.w, gz2[4 * o4 + 3], g);
-        }
-        gz1[i] = sH1[tid * LH + i] > 0.0f ? g : 0.0f;
-        sG1[tid * LH + i] = gz1[i];
-      }
-      float gx[CIN];
-#pragma unroll
-      for (int k = 0; k < CIN; ++k) {
-        const float4* row = reinterpret_cast<const float4*>(sW1 + k * H);
-        float g = 0.0f;
-#pragma unroll
-        for (int o4 = 0; o4 < H / 4; ++o4) {
-          const float4 w = row[o4];
-          g = fmaf(w.x, gz1[4 * o4], g);
-          g = fmaf(w.y, gz1[4 * o4 + 1], g);
-          g = fmaf(w.z, gz1[4 * o4 + 2], g);
-          g = fmaf(w.w, gz1[4 * o4 + 3], g);
-        }
-        gx[k] = g;
-      }
-#pragma unroll
-      for (int c = 0; c < CT; ++c) atomicAdd(&sGK[j * CT + c], gx[CS + c]);
+    // ---- A1: features (spatial channels q*SC.., temporal q*TC.. of this thread) ----
+    {
       TapInfo t[4];
       float fx, fy;
       fit_taps(a, ix, iy, t, fx, fy);
+      const float gx = 1.0f - fx, gy = 1.0f - fy;
 #pragma unroll
-      for (int c = 0; c < CS; ++c) {
-        float gea[4], geb[4];
+      for (int kk = 0; kk < SC; ++kk) {
+        const int k = q * SC + kk;
+        float xv = 0.0f;
+        if (valid) {
+          float f[4], d0, d1, d2;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float dea, deb, dw;
-          const int64_t bc = t[q].blk + c;
-          sim_value(a, bc, t[q].p, dea, deb, dw);
-          const float gf = t[q].wt * gx[c];
-          gea[q] = dea * gf;
-          geb[q] = deb * gf;
-          atomicAdd(&a.g_w[bc * 16 + t[q].p], dw * gf);
+          for (int tq = 0; tq < 4; ++tq) f[tq] = sim_value(a, t[tq].blk + k, t[tq].p, d0, d1, d2);
+          xv = gy * (gx * f[0] + fx * f[1]) + fy * (gx * f[2] + fx * f[3]);   // the decode's blend order
         }
-        // merge the endpoint gradients of taps in the same block
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          bool first = true;
-#pragma unroll
-          for (int r = 0; r < q; ++r) first = first && (t[r].blk != t[q].blk);
-          if (!first) continue;
-          float sa = gea[q], sb = geb[q];
-#pragma unroll
-          for (int r = q + 1; r < 4; ++r) {
-            if (t[r].blk == t[q].blk) {
-              sa += gea[r];
-              sb += geb[r];
-            }
-          }
-          atomicAdd(&a.g_ea[t[q].blk + c], sa);
-          atomicAdd(&a.g_eb[t[q].blk + c], sb);
-        }
+        sX[r * LX + k] = xv;
       }
-    } else {
 #pragma unroll
-      for (int o = 0; o < H; ++o) {
-        sH2[tid * LH + o] = 0.0f;
-        sG1[tid * LH + o] = 0.0f;
+      for (int kk = 0; kk < TC; ++kk) {
+        const int c = q * TC + kk;
+        sX[r * LX + CS + c] = valid ? a.temporal[j * CT + c] : 0.0f;
       }
     }
     __syncthreads();
-    // ---- phase D: dW2 += H1^T dZ2, dW1 += X^T dZ1, db1, db2 ----
+    // ---- A2: layer 1, this thread's HQ units ----
     {
+      float h[HQ];
+#pragma unroll
+      for (int u = 0; u < HQ; ++u) h[u] = sB1[o0 + u];
+#pragma unroll 4
+      for (int k = 0; k < CIN; ++k) {
+        const float xv = sX[r * LX + k];
+#pragma unroll
+        for (int u4 = 0; u4 < HQ / 4; ++u4) {
+          const float4 wv = *reinterpret_cast<const float4*>(sW1s + k * HS + c0 + 4 * u4);
+          h[4 * u4] = fmaf(xv, wv.x, h[4 * u4]);
+          h[4 * u4 + 1] = fmaf(xv, wv.y, h[4 * u4 + 1]);
+          h[4 * u4 + 2] = fmaf(xv, wv.z, h[4 * u4 + 2]);
+          h[4 * u4 + 3] = fmaf(xv, wv.w, h[4 * u4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int u4 = 0; u4 < HQ / 4; ++u4)
+        *reinterpret_cast<float4*>(sH1 + r * LH + o0 + 4 * u4) =
+            valid ? make_float4(fmaxf(h[4 * u4], 0.0f), fmaxf(h[4 * u4 + 1], 0.0f), fmaxf(h[4 * u4 + 2], 0.0f),
+                                fmaxf(h[4 * u4 + 3], 0.0f))
+                  : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncthreads();
+    // ---- A3: layer 2 (this thread's HQ units) and its share of the output layer ----
+    {
+      float h[HQ];
+#pragma unroll
+      for (int u = 0; u < HQ; ++u) h[u] = sB2[o0 + u];
+#pragma unroll 4
+      for (int i = 0; i < H; ++i) {
+        const float hv = sH1[r * LH + i];
+#pragma unroll
+        for (int u4 = 0; u4 < HQ / 4; ++u4) {
+          const float4 wv = *reinterpret_cast<const float4*>(sW2s + i * HS + c0 + 4 * u4);
+          h[4 * u4] = fmaf(hv, wv.x, h[4 * u4]);
+          h[4 * u4 + 1] = fmaf(hv, wv.y, h[4 * u4 + 1]);
+          h[4 * u4 + 2] = fmaf(hv, wv.z, h[4 * u4 + 2]);
+          h[4 * u4 + 3] = fmaf(hv, wv.w, h[4 * u4 + 3]);
+        }
+      }
+      float y0 = 0.0f, y1 = 0.0f, y2 = 0.0f;
+#pragma unroll
+      for (int u = 0; u < HQ; ++u) {
+        h[u] = valid ? fmaxf(h[u], 0.0f) : 0.0f;
+        const float4 w3 = *reinterpret_cast<const float4*>(sW3 + (o0 + u) * 4);
+        y0 = fmaf(h[u], w3.x, y0);
+        y1 = fmaf(h[u], w3.y, y1);
+        y2 = fmaf(h[u], w3.z, y2);
+      }
+#pragma unroll
+      for (int u4 = 0; u4 < HQ / 4; ++u4)
+        *reinterpret_cast<float4*>(sH2 + r * LH + o0 + 4 * u4) =
+            make_float4(h[4 * u4], h[4 * u4 + 1], h[4 * u4 + 2], h[4 * u4 + 3]);
+      *reinterpret_cast<float4*>(sY + (r * kFitQ + q) * 4) = make_float4(y0, y1, y2, 0.0f);
+    }
+    __syncthreads();
+    // ---- A4: output and dL/dy (one thread per sample) ----
+    if (q == 0) {
+      float dy0 = 0.f, dy1 = 0.f, dy2 = 0.f;
+      if (valid) {
+        float y0 = sB3[0], y1 = sB3[1], y2 = sB3[2];
+#pragma unroll
+        for (int qq = 0; qq < kFitQ; ++qq) {
+          const float4 p = *reinterpret_cast<const float4*>(sY + (r * kFitQ + qq) * 4);
+          y0 += p.x;
+          y1 += p.y;
+          y2 += p.z;
+        }
+        if (MODE == 0) {
+          dy0 = a.grad_rgb[3 * s];
+          dy1 = a.grad_rgb[3 * s + 1];
+          dy2 = a.grad_rgb[3 * s + 2];
+        } else {
+          const __half* tg = a.targets + (((int64_t)j * a.lm_h + iy) * a.lm_w + ix) * 3;
+          const float d0 = y0 - __half2float(tg[0]), d1 = y1 - __half2float(tg[1]), d2 = y2 - __half2float(tg[2]);
+          loss += (double)d0 * d0 + (double)d1 * d1 + (double)d2 * d2;
+          const float sc = 2.0f / (3.0f * (float)a.n);
+          dy0 = sc * d0;
+          dy1 = sc * d1;
+          dy2 = sc * d2;
+        }
+      }
+      *reinterpret_cast<float4*>(sDY + r * 4) = make_float4(dy0, dy1, dy2, 0.0f);
+    }
+    __syncthreads();
+    // ---- B: dW3 += H2^T dY (3H owners), db3 (3 owners) ----
+    if (tid < 3 * H) {
+      const int o = tid / 3, c = tid % 3;
+      for (int rr = 0; rr < kFitTile; ++rr) acc3 = fmaf(sH2[rr * LH + o], sDY[rr * 4 + c], acc3);
+    } else if (tid < 3 * H + 3) {
+      const int c = tid - 3 * H;
+      for (int rr = 0; rr < kFitTile; ++rr) acc3 += sDY[rr * 4 + c];
+    }
+    __syncthreads();
+    // ---- C1: dZ2 for this thread's units ----
+    {
+      const float4 dy = *reinterpret_cast<const float4*>(sDY + r * 4);
+#pragma unroll
+      for (int u4 = 0; u4 < HQ / 4; ++u4) {
+        const float4 h = *reinterpret_cast<const float4*>(sH2 + r * LH + o0 + 4 * u4);
+        const float hv[4] = {h.x, h.y, h.z, h.w};
+        float g[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float4 w3 = *reinterpret_cast<const float4*>(sW3 + (o0 + 4 * u4 + e) * 4);
+          const float gg = w3.x * dy.x + w3.y * dy.y + w3.z * dy.z;
+          g[e] = (valid && hv[e] > 0.0f) ? gg : 0.0f;
+        }
+        *reinterpret_cast<float4*>(sH2 + r * LH + o0 + 4 * u4) = make_float4(g[0], g[1], g[2], g[3]);
+      }
+    }
+    __syncthreads();
+    // ---- C2: dZ1 for this thread's units: dZ1[i] = [h1_i > 0] sum_o W2[i][o] dZ2[o] ----
+    {
+      float g[HQ];
+#pragma unroll
+      for (int u = 0; u < HQ; ++u) g[u] = 0.0f;
+#pragma unroll 4
+      for (int o = 0; o < H; ++o) {
+        const float gz = sH2[r * LH + o];
+#pragma unroll
+        for (int u4 = 0; u4 < HQ / 4; ++u4) {
+          const float4 wv = *reinterpret_cast<const float4*>(sW2t + o * HS + c0 + 4 * u4);
+          g[4 * u4] = fmaf(gz, wv.x, g[4 * u4]);
+          g[4 * u4 + 1] = fmaf(gz, wv.y, g[4 * u4 + 1]);
+          g[4 * u4 + 2] = fmaf(gz, wv.z, g[4 * u4 + 2]);
+          g[4 * u4 + 3] = fmaf(gz, wv.w, g[4 * u4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int u4 = 0; u4 < HQ / 4; ++u4) {
+        const float4 h = *reinterpret_cast<const float4*>(sH1 + r * LH + o0 + 4 * u4);
+        *reinterpret_cast<float4*>(sG1 + r * LH + o0 + 4 * u4) =
+            make_float4(h.x > 0.0f ? g[4 * u4] : 0.0f, h.y > 0.0f ? g[4 * u4 + 1] : 0.0f,
+                        h.z > 0.0f ? g[4 * u4 + 2] : 0.0f, h.w > 0.0f ? g[4 * u4 + 3] : 0.0f);
+      }
+    }
+    __syncthreads();
+    // ---- C3: dx for this thread's channels (W1^T rows), then the feature / temporal scatter ----
+    if (valid) {
+      float gs[SC], gt[TC];
+#pragma unroll
+      for (int kk = 0; kk < SC; ++kk) gs[kk] = 0.0f;
+#pragma unroll
+      for (int kk = 0; kk < TC; ++kk) gt[kk] = 0.0f;
+#pragma unroll 4
+      for (int o = 0; o < H; ++o) {
+        const float gz = sG1[r * LH + o];
+        float ws[SC], wt[TC];
+        lds<SC>(sW1t + o * CIN + q * SC, ws);
+        lds<TC>(sW1t + o * CIN + CS + q * TC, wt);
+#pragma unroll
+        for (int kk = 0; kk < SC; ++kk) gs[kk] = fmaf(gz, ws[kk], gs[kk]);
+#pragma unroll
+        for (int kk = 0; kk < TC; ++kk) gt[kk] = fmaf(gz, wt[kk], gt[kk]);
+      }
+#pragma unroll
+      for (int kk = 0; kk < TC; ++kk) atomicAdd(&sGK[j * CT + q * TC + kk], gt[kk]);
+      TapInfo t[4];
+      float fx, fy;
+      fit_taps(a, ix, iy, t, fx, fy);
+      // per tap: the weight-index gradients (one texel each), and the endpoint
+      // gradients of this thread's SC channels
+      float gea[4][SC], geb[4][SC];
+#pragma unroll
+      for (int tq = 0; tq < 4; ++tq) {
+#pragma unroll
+        for (int kk = 0; kk < SC; ++kk) {
+          float dea, deb, dw;
+          const int64_t bc = t[tq].blk + q * SC + kk;
+          sim_value(a, bc, t[tq].p, dea, deb, dw);
+          const float gf = t[tq].wt * gs[kk];
+          gea[tq][kk] = dea * gf;
+          geb[tq][kk] = deb * gf;
+          atomicAdd(&a.g_w[bc * 16 + t[tq].p], dw * gf);
+        }
+      }
+      // merge the endpoint gradients of taps in the same block, one reduction per block
+#pragma unroll
+      for (int tq = 0; tq < 4; ++tq) {
+        bool first = true;
+#pragma unroll
+        for (int rq = 0; rq < tq; ++rq) first = first && (t[rq].blk != t[tq].blk);
+        if (!first) continue;
+        float sa[SC], sb[SC];
+#pragma unroll
+        for (int kk = 0; kk < SC; ++kk) {
+          sa[kk] = gea[tq][kk];
+          sb[kk] = geb[tq][kk];
+        }
+#pragma unroll
+        for (int rq = tq + 1; rq < 4; ++rq) {
+          if (t[rq].blk == t[tq].blk) {
+#pragma unroll
+            for (int kk = 0; kk < SC; ++kk) {
+              sa[kk] += gea[rq][kk];
+              sb[kk] += geb[rq][kk];
+            }
+          }
+        }
+        float* pa = a.g_ea + t[tq].blk + q * SC;
+        float* pb = a.g_eb + t[tq].blk + q * SC;
+        if constexpr (SC == 4) {
+          if (a.vec_red) {
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(pa), "f"(sa[0]), "f"(sa[1]),
+                         "f"(sa[2]), "f"(sa[3]) : "memory");
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(pb), "f"(sb[0]), "f"(sb[1]),
+                         "f"(sb[2]), "f"(sb[3]) : "memory");
+            continue;
+          }
+        } else if constexpr (SC == 2) {
+          if (a.vec_red) {
+            asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(pa), "f"(sa[0]), "f"(sa[1]) : "memory");
+            asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(pb), "f"(sb[0]), "f"(sb[1]) : "memory");
+            continue;
+          }
+        }
+#pragma unroll
+        for (int kk = 0; kk < SC; ++kk) {
+          atomicAdd(pa + kk, sa[kk]);
+          atomicAdd(pb + kk, sb[kk]);
+        }
+      }
+    }
+    // ---- D: dW2 += H1^T dZ2, dW1 += X^T dZ1, db2, db1 (sH1, sX, sH2 = dZ2, sG1 = dZ1 are final) ----
+    if constexpr (kBlocked) {
+      const int ob = tid % 16, ib = tid / 16;   // dW2 rows 2ib, 2ib+1 x columns 4ob .. 4ob+3
+      for (int rr = 0; rr < kFitTile; ++rr) {
+        const float2 h = *reinterpret_cast<const float2*>(sH1 + rr * LH + 2 * ib);
+        const float4 g = *reinterpret_cast<const float4*>(sH2 + rr * LH + 4 * ob);
+        acc2[0] = fmaf(h.x, g.x, acc2[0]);
+        acc2[1] = fmaf(h.x, g.y, acc2[1]);
+        acc2[2] = fmaf(h.x, g.z, acc2[2]);
+        acc2[3] = fmaf(h.x, g.w, acc2[3]);
+        acc2[4] = fmaf(h.y, g.x, acc2[4]);
+        acc2[5] = fmaf(h.y, g.y, acc2[5]);
+        acc2[6] = fmaf(h.y, g.z, acc2[6]);
+        acc2[7] = fmaf(h.y, g.w, acc2[7]);
+        if (ib == 0) {   // db2 = colsum dZ2
+          accb2[0] += g.x;
+          accb2[1] += g.y;
+          accb2[2] += g.z;
+          accb2[3] += g.w;
+        }
+      }
+    } else {
       const int o = tid % H, i0 = tid / H;
-      for (int r = 0; r < kFitTile; ++r) {
-        const float g2 = sH2[r * LH + o];
-        const float g1 = sG1[r * LH + o];
+      constexpr int RPT = kBwdThreads / H;
+      for (int rr = 0; rr < kFitTile; ++rr) {
+        const float g2 = sH2[rr * LH + o];
 #pragma unroll
-        for (int k = 0; k < K2; ++k) acc2[k] = fmaf(sH1[r * LH + i0 + RPT * k], g2, acc2[k]);
+        for (int k = 0; k < K2; ++k)
+          if (i0 + RPT * k < H) acc2[k] = fmaf(sH1[rr * LH + i0 + RPT * k], g2, acc2[k]);
+        if (i0 == 0) accb2[0] += g2;
+      }
+    }
+    {
+      const int o = tid % H, k0 = tid / H;   // dW1 rows k0 + (512/H) m, column o; db1 by the first H threads
+      constexpr int RPT = kBwdThreads / H;
+      for (int rr = 0; rr < kFitTile; ++rr) {
+        const float g1 = sG1[rr * LH + o];
 #pragma unroll
-        for (int k = 0; k < K1; ++k) acc1[k] = fmaf(sX[r * LX + i0 + RPT * k], g1, acc1[k]);
-        if (i0 == 0) accb12 += g2;        // db2 = colsum dZ2
-        else if (i0 == 1) accb12 += g1;   // db1 = colsum dZ1
+        for (int m = 0; m < K1; ++m)
+          if (k0 + RPT * m < CIN) acc1[m] = fmaf(sX[rr * LX + k0 + RPT * m], g1, acc1[m]);
+        if (k0 == 0) accb1 += g1;
       }
     }
     __syncthreads();
   }
   // ---- flush per-CTA accumulators ----
-  {
-    const int o = tid % H, i0 = tid / H;
+  if constexpr (kBlocked) {
+    const int ob = tid % 16, ib = tid / 16;
 #pragma unroll
-    for (int k = 0; k < K2; ++k) atomicAdd(&a.g_w2[(i0 + RPT * k) * H + o], acc2[k]);
+    for (int e = 0; e < 8; ++e) atomicAdd(&a.g_w2[(2 * ib + e / 4) * H + 4 * ob + e % 4], acc2[e]);
+    if (ib == 0) {
 #pragma unroll
-    for (int k = 0; k < K1; ++k) atomicAdd(&a.g_w1[(i0 + RPT * k) * H + o], acc1[k]);
-  }
-  if (tid < H) {
-    atomicAdd(&a.g_w3[tid * 3 + 0], acc3[0]);
-    atomicAdd(&a.g_w3[tid * 3 + 1], acc3[1]);
-    atomicAdd(&a.g_w3[tid * 3 + 2], acc3[2]);
-  } else if (tid >= kFitThreads - 3) {
-    atomicAdd(&a.g_b3[tid - (kFitThreads - 3)], accb);
+      for (int e = 0; e < 4; ++e) atomicAdd(&a.g_b2[4 * ob + e], accb2[e]);
+    }
+  } else {
+    const int o = tid % H, i0 = tid / H;
+    constexpr int RPT = kBwdThreads / H;
+#pragma unroll
+    for (int k = 0; k < K2; ++k)
+      if (i0 + RPT * k < H) atomicAdd(&a.g_w2[(i0 + RPT * k) * H + o], acc2[k]);
+    if (i0 == 0) atomicAdd(&a.g_b2[o], accb2[0]);
   }
   {
-    const int o = tid % H, i0 = tid / H;
-    if (i0 == 0) atomicAdd(&a.g_b2[o], accb12);
-    else if (i0 == 1) atomicAdd(&a.g_b1[o], accb12);
+    const int o = tid % H, k0 = tid / H;
+    constexpr int RPT = kBwdThreads / H;
+#pragma unroll
+    for (int m = 0; m < K1; ++m)
+      if (k0 + RPT * m < CIN) atomicAdd(&a.g_w1[(k0 + RPT * m) * H + o], acc1[m]);
+    if (k0 == 0) atomicAdd(&a.g_b1[o], accb1);
   }
+  if (tid < 3 * H) atomicAdd(&a.g_w3[(tid / 3) * 3 + tid % 3], acc3);
+  else if (tid < 3 * H + 3) atomicAdd(&a.g_b3[tid - 3 * H], acc3);
   __syncthreads();
-  for (int i = tid; i < a.t_count * CT; i += kFitThreads) atomicAdd(&a.g_temporal[i], sGK[i]);
+  for (int i = tid; i < a.t_count * CT; i += kBwdThreads) atomicAdd(&a.g_temporal[i], sGK[i]);
   if (MODE == 1) {
     for (int off = 16; off > 0; off >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, off);
     if ((tid & 31) == 0) atomicAdd(a.loss_acc, loss);
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // Adam over all ten parameter tensors in one launch (Kingma & Ba).  The step
@@ -513,7 +701,9 @@ static size_t fit_smem_bytes(int t_count) {
   return (size_t)(FitSmem<CS, CT, H>::kFloatsNoGK + t_count * CT) * sizeof(float);
 }
 
-static cudaError_t launch_fit_backward(const FitArgs& a, int mode, cudaStream_t s) {
+static cudaError_t launch_fit_backward(const FitArgs& args, int mode, cudaStream_t s) {
+  FitArgs a = args;
+  a.vec_red = ((reinterpret_cast<uintptr_t>(a.g_ea) | reinterpret_cast<uintptr_t>(a.g_eb)) & 15u) == 0u;
   const int64_t tiles = (a.n + kFitTile - 1) / kFitTile;
   const int64_t cap = num_sms();
   const int grid = (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
@@ -523,7 +713,7 @@ static cudaError_t launch_fit_backward(const FitArgs& a, int mode, cudaStream_t 
     auto kern = mode == 0 ? k_fit_backward<A, B, C, 0> : k_fit_backward<A, B, C, 1>;                  \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                  \
-    kern<<<grid, kFitThreads, smem, s>>>(a);                                                         \
+    kern<<<grid, kBwdThreads, smem, s>>>(a);                                                         \
     return cudaGetLastError();                                                                       \
   }
   NDGI_FIT_SHAPES(X)
