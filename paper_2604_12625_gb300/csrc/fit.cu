@@ -32,6 +32,7 @@ struct FitArgs {
   float *g_ea, *g_eb, *g_w, *g_temporal, *g_w1, *g_b1, *g_w2, *g_b2, *g_w3, *g_b3;
   int relaxed;
   int vec_red;                  // g_ea, g_eb 16-byte aligned: endpoint gradients use vector reductions
+  int vec_ld;                   // ea, eb 16-byte aligned: endpoints are read with vector loads
   int64_t n;
   const int32_t* samples;       // mode 0
   const float* grad_rgb;        // mode 0
@@ -103,6 +104,54 @@ __device__ __forceinline__ float sim_value(const FitArgs& a, int64_t bc, int p, 
   deb = qw;
   dw = (float)(B - A) * (1.0f / 255.0f);
   return p35_value(5 * ((7 - k) * A + k * B));
+}
+
+// The same for N consecutive channels k0 .. k0+N-1 of one tap (N = 1, 2, 4;
+// the endpoints of the N channels are read with one vector load each).
+template <int N>
+__device__ __forceinline__ void sim_values(const FitArgs& a, int64_t blk, int k0, int p, float (&f)[N],
+                                           float (&dea)[N], float (&deb)[N], float (&dw)[N]) {
+  float ea[N], eb[N];
+  if (!a.vec_ld) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      ea[i] = __ldg(a.ea + blk + k0 + i);
+      eb[i] = __ldg(a.eb + blk + k0 + i);
+    }
+  } else if constexpr (N == 4) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(a.ea + blk + k0));
+    const float4 y = __ldg(reinterpret_cast<const float4*>(a.eb + blk + k0));
+    ea[0] = x.x; ea[1] = x.y; ea[2] = x.z; ea[3] = x.w;
+    eb[0] = y.x; eb[1] = y.y; eb[2] = y.z; eb[3] = y.w;
+  } else if constexpr (N == 2) {
+    const float2 x = __ldg(reinterpret_cast<const float2*>(a.ea + blk + k0));
+    const float2 y = __ldg(reinterpret_cast<const float2*>(a.eb + blk + k0));
+    ea[0] = x.x; ea[1] = x.y;
+    eb[0] = y.x; eb[1] = y.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      ea[i] = __ldg(a.ea + blk + k0 + i);
+      eb[i] = __ldg(a.eb + blk + k0 + i);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float w = __ldg(a.w + (blk + k0 + i) * 16 + p);
+    if (a.relaxed) {
+      dea[i] = 1.0f - w;
+      deb[i] = w;
+      dw[i] = eb[i] - ea[i];
+      f[i] = (1.0f - w) * ea[i] + w * eb[i];
+    } else {
+      const int A = quant(ea[i], 255.0f), B = quant(eb[i], 255.0f), k = quant(w, 7.0f);
+      const float qw = (float)k * (1.0f / 7.0f);
+      dea[i] = 1.0f - qw;
+      deb[i] = qw;
+      dw[i] = (float)(B - A) * (1.0f / 255.0f);
+      f[i] = p35_value(5 * ((7 - k) * A + k * B));
+    }
+  }
 }
 
 template <int CS, int CT>
@@ -296,18 +345,16 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
       float fx, fy;
       fit_taps(a, ix, iy, t, fx, fy);
       const float gx = 1.0f - fx, gy = 1.0f - fy;
+      float f[4][SC];
 #pragma unroll
-      for (int kk = 0; kk < SC; ++kk) {
-        const int k = q * SC + kk;
-        float xv = 0.0f;
-        if (valid) {
-          float f[4], d0, d1, d2;
-#pragma unroll
-          for (int tq = 0; tq < 4; ++tq) f[tq] = sim_value(a, t[tq].blk + k, t[tq].p, d0, d1, d2);
-          xv = gy * (gx * f[0] + fx * f[1]) + fy * (gx * f[2] + fx * f[3]);   // the decode's blend order
-        }
-        sX[r * LX + k] = xv;
+      for (int tq = 0; tq < 4; ++tq) {
+        float d0[SC], d1[SC], d2[SC];
+        if (valid) sim_values<SC>(a, t[tq].blk, q * SC, t[tq].p, f[tq], d0, d1, d2);
       }
+#pragma unroll
+      for (int kk = 0; kk < SC; ++kk)   // the decode's blend order
+        sX[r * LX + q * SC + kk] =
+            valid ? gy * (gx * f[0][kk] + fx * f[1][kk]) + fy * (gx * f[2][kk] + fx * f[3][kk]) : 0.0f;
 #pragma unroll
       for (int kk = 0; kk < TC; ++kk) {
         const int c = q * TC + kk;
@@ -483,15 +530,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
       float gea[4][SC], geb[4][SC];
 #pragma unroll
       for (int tq = 0; tq < 4; ++tq) {
+        float fv[SC], dea[SC], deb[SC], dw[SC];
+        sim_values<SC>(a, t[tq].blk, q * SC, t[tq].p, fv, dea, deb, dw);
 #pragma unroll
         for (int kk = 0; kk < SC; ++kk) {
-          float dea, deb, dw;
-          const int64_t bc = t[tq].blk + q * SC + kk;
-          sim_value(a, bc, t[tq].p, dea, deb, dw);
           const float gf = t[tq].wt * gs[kk];
-          gea[tq][kk] = dea * gf;
-          geb[tq][kk] = deb * gf;
-          atomicAdd(&a.g_w[bc * 16 + t[tq].p], dw * gf);
+          gea[tq][kk] = dea[kk] * gf;
+          geb[tq][kk] = deb[kk] * gf;
+          atomicAdd(&a.g_w[(t[tq].blk + q * SC + kk) * 16 + t[tq].p], dw[kk] * gf);
         }
       }
       // merge the endpoint gradients of taps in the same block, one reduction per block
@@ -704,6 +750,7 @@ static size_t fit_smem_bytes(int t_count) {
 static cudaError_t launch_fit_backward(const FitArgs& args, int mode, cudaStream_t s) {
   FitArgs a = args;
   a.vec_red = ((reinterpret_cast<uintptr_t>(a.g_ea) | reinterpret_cast<uintptr_t>(a.g_eb)) & 15u) == 0u;
+  a.vec_ld = ((reinterpret_cast<uintptr_t>(a.ea) | reinterpret_cast<uintptr_t>(a.eb)) & 15u) == 0u;
   const int64_t tiles = (a.n + kFitTile - 1) / kFitTile;
   const int64_t cap = num_sms();
   const int grid = (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
