@@ -114,8 +114,12 @@ size_t ndgi_prepare_workspace_size(const ndgi_model_desc *model, ndgi_precision 
  * Packs the model's MLP into `ws` (device, caller-owned, ws_bytes >=
  * ndgi_prepare_workspace_size, 256-byte aligned) for decodes of
  * `precision`: weights rounded once to FP16/BF16 (round to nearest even),
- * laid out as the tensor-core operand tiles.  The packed weights are the
- * parameters such a decode evaluates.  Re-run it whenever the weights change.
+ * laid out as the tensor-core operand tiles, followed by a texel-sliced copy
+ * of the BC4 planes for the point decode (the same bits regrouped so that a
+ * texel of every plane is two short reads: per block the cs endpoint pairs,
+ * then per texel one 8-byte word of the planes' 3-bit indices; 1.25x the
+ * planes' size for cs = 16).  The packed weights are the parameters such a
+ * decode evaluates.  Re-run it whenever the weights or the planes change.
  */
 ndgi_status ndgi_prepare(const ndgi_model_desc *model, ndgi_precision precision, void *ws, size_t ws_bytes,
                          void *stream);
@@ -182,6 +186,17 @@ ndgi_status ndgi_decode_points(const ndgi_model_desc *model, ndgi_precision prec
  */
 ndgi_status ndgi_debug_features(const ndgi_model_desc *model, const float *uvt, int64_t n, float *x,
                                 int32_t *p35, void *stream);
+
+/*
+ * The gather of the FP16/BF16 point decode alone, for validation: the same
+ * x [n][cs+ct] as ndgi_debug_features (identical taps, fractions and
+ * palette integers; FP32 arithmetic reassociated), computed from the
+ * texel-sliced copy of the planes that ndgi_prepare keeps in `ws` (a
+ * workspace prepared for NDGI_FP16 or NDGI_BF16; re-run ndgi_prepare after the
+ * planes change).
+ */
+ndgi_status ndgi_debug_features_tc(const ndgi_model_desc *model, const void *ws, const float *uvt, int64_t n,
+                                   float *x, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Batched virtual-texture page decode (Sec. 3.5, supplement S3)           */

@@ -65,6 +65,7 @@ SIGNATURES = [
     ("ndgi_fp8_unpack", C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     ("ndgi_decode_points", C.c_int, [_vp, C.c_int, _vp, _vp, _i64, _vp, _vp]),
     ("ndgi_debug_features", C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    ("ndgi_debug_features_tc", C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
     ("ndgi_pages_plan_create", C.c_int, [_vp, _vp, _i32, C.c_int, _i32, _i32, _vp, _i64, _i64, _vp]),
     ("ndgi_decode_pages", C.c_int, [_vp, _vp, _vp, _vp]),
     ("ndgi_pages_autotune", C.c_int, [_vp, _vp, _vp, _i32, _vp]),

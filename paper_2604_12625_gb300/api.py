@@ -170,6 +170,16 @@ def ndgi_debug_features(model, uvt, stream=None):
     return x, p35
 
 
+def ndgi_debug_features_tc(model, uvt, precision="fp16", stream=None):
+    """x [n][cs+ct] float32 of the tensor-core point decode's gather (texel-sliced planes)."""
+    uvt = _need(uvt, torch.float32, "uvt")
+    n = uvt.shape[0]
+    x = torch.empty((n, model.cs + model.ct), dtype=torch.float32, device=uvt.device)
+    ws = model.workspace(precision)
+    check(lib().ndgi_debug_features_tc(C.byref(model.desc), _p(ws), _p(uvt), n, _p(x), _stream(stream)))
+    return x
+
+
 # ---------------------------------------------------------------------------
 # Pages
 # ---------------------------------------------------------------------------

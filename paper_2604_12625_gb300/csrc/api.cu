@@ -99,7 +99,8 @@ ndgi_status ndgi_check(void* stream) {
 
 size_t ndgi_prepare_workspace_size(const ndgi_model_desc* model, ndgi_precision precision) {
   if (!model) return 0;
-  if (precision == NDGI_FP16 || precision == NDGI_BF16) return tc_workspace_bytes(model->cs, model->ct, model->hidden);
+  if (precision == NDGI_FP16 || precision == NDGI_BF16)
+    return tc_workspace_bytes(model->cs, model->ct, model->hidden, model->feat_w, model->feat_h);
   if (precision == NDGI_FP8_E4M3) return tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden);
   return 0;
 }
@@ -175,7 +176,7 @@ ndgi_status ndgi_prepare(const ndgi_model_desc* model, ndgi_precision precision,
   if (!tc_supported(model->cs, model->ct, model->hidden))
     return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_prepare: tensor-core shape cs=%d ct=%d hidden=%d not built",
                      model->cs, model->ct, model->hidden);
-  const size_t need = tc_workspace_bytes(model->cs, model->ct, model->hidden);
+  const size_t need = tc_workspace_bytes(model->cs, model->ct, model->hidden, model->feat_w, model->feat_h);
   if (!ws || ws_bytes < need || !aligned(ws, 256))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_prepare: ws must be 256-byte aligned with >= %zu bytes", need);
   return cuda_status(launch_tc_prepare(to_dev(*model), precision == NDGI_BF16, ws, (cudaStream_t)stream),
@@ -217,6 +218,20 @@ ndgi_status ndgi_debug_features(const ndgi_model_desc* model, const float* uvt, 
   if (!uvt || !x) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_debug_features: uvt or x is NULL");
   return cuda_status(launch_debug_features(to_dev(*model), uvt, n, x, p35, (cudaStream_t)stream),
                      "ndgi_debug_features");
+}
+
+ndgi_status ndgi_debug_features_tc(const ndgi_model_desc* model, const void* ws, const float* uvt, int64_t n,
+                                   float* x, void* stream) {
+  ndgi_status st = check_model(model, "ndgi_debug_features_tc");
+  if (st != NDGI_OK) return st;
+  if (n < 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_debug_features_tc: n < 0");
+  if (n == 0) return NDGI_OK;
+  if (!uvt || !x || !ws || !aligned(ws, 256))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_debug_features_tc: NULL argument or unaligned workspace");
+  if (!tc_supported(model->cs, model->ct, model->hidden))
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_debug_features_tc: tensor-core shape not built");
+  return cuda_status(launch_debug_features_tc(to_dev(*model), ws, uvt, n, x, (cudaStream_t)stream),
+                     "ndgi_debug_features_tc");
 }
 
 ndgi_status ndgi_bc_pack(const float* ea, const float* eb, const float* w, int32_t cs, int32_t feat_w,

@@ -225,4 +225,198 @@ __device__ __forceinline__ void gather_tc(const DevModel& m, float u, float v, f
   }
 }
 
+// ---------------------------------------------------------------------------
+// Texel-sliced copy of the BC4 planes (built by ndgi_prepare for the tensor-
+// core point decode).  The same bits, regrouped per 4x4 block so that one
+// texel of every plane is two short reads instead of a whole 128-byte line
+// and a variable 64-bit shift per plane.  Block (by, bx) starts at
+// (by * bw + bx) * BLOCK bytes:
+//   [0, EP)          the (r0, r1) endpoint bytes of planes 0..CS-1 (plane c at
+//                    bytes 2c, 2c+1), zero padded;
+//   [EP, EP + 128)   16 words of 8 bytes: texel p's word holds plane c's
+//                    3-bit index at bit 3c.
+// ---------------------------------------------------------------------------
+template <int CS>
+struct Sliced {
+  static_assert(CS <= 16, "at most 16 planes per sliced block");
+  static constexpr int EP = CS <= 8 ? 16 : 32;
+  static constexpr int BLOCK = EP + 128;
+};
+
+// Palette table for gather_sliced: entry (n8 << 3 | k) with n8 = 1 when
+// r0 <= r1 (the six-value mode), constant term carrying 2^23's exponent bits
+// as in init_p35_lut_f.
+__device__ __forceinline__ void init_p35_lut_sliced(uint2* lut, int tid) {
+  if (tid < 16) {
+    const uint32_t k = tid & 7u;
+    const bool m8 = tid < 8;   // n8 = 0: r0 > r1
+    const uint32_t ca = __byte_perm(m8 ? kCa8Lo : kCa6Lo, m8 ? kCa8Hi : kCa6Hi, k) & 0xffu;
+    const uint32_t cb = __byte_perm(m8 ? kCb8Lo : kCb6Lo, m8 ? kCb8Hi : kCb6Hi, k) & 0xffu;
+    lut[tid] = make_uint2(ca | (cb << 16), ((!m8 && k == 7u) ? 8925u : 0u) + 0x4B000000u);
+  }
+}
+
+// 3-bit field at compile-time bit S of the 64-bit word {lo, hi}.
+template <int S>
+__device__ __forceinline__ uint32_t field3(uint2 w) {
+  if constexpr (S + 3 <= 32) return (w.x >> S) & 7u;
+  else if constexpr (S >= 32) return (w.y >> (S - 32)) & 7u;
+  else return __funnelshift_r(w.x, w.y, S) & 7u;
+}
+
+// Plane c's palette value at one tap, as the float 2^23 + P35: w is the
+// endpoint word of planes 2*(c/2), 2*(c/2)+1, t its two modes (bit 8 / bit 24
+// set when r0 <= r1), k the texel's index.
+template <int C>
+__device__ __forceinline__ float sliced_value(uint32_t w, uint32_t t, uint32_t k, const uint2* lut) {
+  if constexpr ((C & 1) == 0) {
+    const uint2 e = lut[k | ((t >> 5) & 8u)];
+    return __uint_as_float(__dp2a_lo(e.x, w, e.y));
+  } else {
+    const uint2 e = lut[k | ((t >> 21) & 8u)];
+    return __uint_as_float(__dp2a_hi(e.x, w, e.y));
+  }
+}
+
+template <int CS, int CT, int C>
+__device__ __forceinline__ void sliced_plane(const uint32_t (&ew)[4][Sliced<CS>::EP / 4], const uint32_t (&tm)[4][Sliced<CS>::EP / 4],
+                                             const uint2 (&ix)[4], const float (&wq)[4], float (&x)[CS + CT],
+                                             const uint2* lut) {
+  if constexpr (C < CS) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float p = sliced_value<C>(ew[q][C / 2], tm[q][C / 2], field3<3 * C>(ix[q]), lut) - 8388608.0f;
+      acc = fmaf(wq[q], p, acc);
+    }
+    x[C] = acc;
+    sliced_plane<CS, CT, C + 1>(ew, tm, ix, wq, x, lut);
+  }
+}
+
+// gather_tc on the texel-sliced copy `sl` (identical taps, fractions and P35).
+template <int CS, int CT>
+__device__ __forceinline__ void gather_sliced(const DevModel& m, const uint8_t* sl, float u, float v, float t,
+                                              float (&x)[CS + CT], const uint2* lut) {
+  using SL = Sliced<CS>;
+  constexpr int EW = SL::EP / 16;   // uint4 endpoint words per block
+  int x0, x1, y0, y1;
+  float fx, fy;
+  axis_setup(u, m.feat_w, m.address_mode, x0, x1, fx);
+  axis_setup(v, m.feat_h, m.address_mode, y0, y1, fy);
+  const int tx[4] = {x0, x1, x0, x1};
+  const int ty[4] = {y0, y0, y1, y1};
+  const float gx = 1.0f - fx, gy = 1.0f - fy;
+  const float wq[4] = {gx * gy * kInv8925, fx * gy * kInv8925, gx * fy * kInv8925, fx * fy * kInv8925};
+  const bool same_x = (x0 >> 2) == (x1 >> 2), same_y = (y0 >> 2) == (y1 >> 2);
+  const uint8_t* base[4];
+  uint2 ix[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    base[q] = sl + ((size_t)(ty[q] >> 2) * m.bw + (tx[q] >> 2)) * SL::BLOCK;
+    const int p = ((ty[q] & 3) << 2) | (tx[q] & 3);
+    ix[q] = __ldg(reinterpret_cast<const uint2*>(base[q] + SL::EP) + p);
+  }
+  uint4 e[4][EW];
+#pragma unroll
+  for (int h = 0; h < EW; ++h) {
+    e[0][h] = __ldg(reinterpret_cast<const uint4*>(base[0]) + h);
+    if (!same_x) e[1][h] = __ldg(reinterpret_cast<const uint4*>(base[1]) + h);
+    if (!same_y) e[2][h] = __ldg(reinterpret_cast<const uint4*>(base[2]) + h);
+    if (!same_x && !same_y) e[3][h] = __ldg(reinterpret_cast<const uint4*>(base[3]) + h);
+  }
+#pragma unroll
+  for (int h = 0; h < EW; ++h) {
+    if (same_x) e[1][h] = e[0][h];
+    if (same_y) e[2][h] = e[0][h];
+    if (same_x || same_y) e[3][h] = same_x ? e[2][h] : e[1][h];
+  }
+  // endpoint words and their two modes: t = r1 + 256 - r0 per 16-bit half
+  uint32_t ew[4][SL::EP / 4], tm[4][SL::EP / 4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int h = 0; h < EW; ++h) {
+      const uint32_t w4[4] = {e[q][h].x, e[q][h].y, e[q][h].z, e[q][h].w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t w = w4[i];
+        ew[q][4 * h + i] = w;
+        tm[q][4 * h + i] = ((w >> 8) & 0x00FF00FFu) + 0x01000100u - (w & 0x00FF00FFu);
+      }
+    }
+  }
+  sliced_plane<CS, CT, 0>(ew, tm, ix, wq, x, lut);
+  int j0, j1;
+  float a;
+  temporal_setup(t, m.t_count, j0, j1, a);
+  const float ga = 1.0f - a;
+  const bool vec = (reinterpret_cast<uintptr_t>(m.temporal) & 15u) == 0u;
+  if (CT % 8 == 0 && m.temporal_f16 && vec) {
+    const uint4* r0 = reinterpret_cast<const uint4*>(static_cast<const __half*>(m.temporal) + (size_t)j0 * CT);
+    const uint4* r1 = reinterpret_cast<const uint4*>(static_cast<const __half*>(m.temporal) + (size_t)j1 * CT);
+#pragma unroll
+    for (int g = 0; g < (CT % 8 == 0 ? CT / 8 : 0); ++g) {
+      const uint4 k0 = __ldg(r0 + g), k1 = __ldg(r1 + g);
+      const uint32_t w0[4] = {k0.x, k0.y, k0.z, k0.w}, w1[4] = {k1.x, k1.y, k1.z, k1.w};
+#pragma unroll
+      for (int hh = 0; hh < 4; ++hh) {
+        const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&w0[hh]));
+        const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&w1[hh]));
+        x[CS + 8 * g + 2 * hh] = ga * f0.x + a * f1.x;
+        x[CS + 8 * g + 2 * hh + 1] = ga * f0.y + a * f1.y;
+      }
+    }
+  } else if (CT % 4 == 0 && !m.temporal_f16 && vec) {
+    const float4* r0 = reinterpret_cast<const float4*>(static_cast<const float*>(m.temporal) + (size_t)j0 * CT);
+    const float4* r1 = reinterpret_cast<const float4*>(static_cast<const float*>(m.temporal) + (size_t)j1 * CT);
+#pragma unroll
+    for (int g = 0; g < (CT % 4 == 0 ? CT / 4 : 0); ++g) {
+      const float4 k0 = __ldg(r0 + g), k1 = __ldg(r1 + g);
+      x[CS + 4 * g] = ga * k0.x + a * k1.x;
+      x[CS + 4 * g + 1] = ga * k0.y + a * k1.y;
+      x[CS + 4 * g + 2] = ga * k0.z + a * k1.z;
+      x[CS + 4 * g + 3] = ga * k0.w + a * k1.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CT; ++c) {
+      const float k0 = load_temporal(m.temporal, m.temporal_f16, j0 * CT + c);
+      const float k1 = load_temporal(m.temporal, m.temporal_f16, j1 * CT + c);
+      x[CS + c] = ga * k0 + a * k1;
+    }
+  }
+}
+
+// Builds the texel-sliced copy of the BC4 planes (one thread per block).
+template <int CS>
+__global__ void k_slice_features(const uint8_t* __restrict__ bc4, int64_t nblocks, uint8_t* __restrict__ out) {
+  using SL = Sliced<CS>;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nblocks; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t* src = bc4 + i * CS * 8;
+    uint8_t* dst = out + i * SL::BLOCK;
+    uint32_t ep[SL::EP / 4];
+#pragma unroll
+    for (int w = 0; w < SL::EP / 4; ++w) ep[w] = 0u;
+    uint64_t idx[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) idx[p] = 0u;
+#pragma unroll
+    for (int c = 0; c < CS; ++c) {
+      uint64_t b = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) b |= (uint64_t)src[c * 8 + k] << (8 * k);
+      ep[c / 2] |= (uint32_t)(b & 0xFFFFu) << (16 * (c & 1));
+#pragma unroll
+      for (int p = 0; p < 16; ++p) idx[p] |= ((b >> (16 + 3 * p)) & 7u) << (3 * c);
+    }
+#pragma unroll
+    for (int w = 0; w < SL::EP / 16; ++w)
+      reinterpret_cast<uint4*>(dst)[w] = make_uint4(ep[4 * w], ep[4 * w + 1], ep[4 * w + 2], ep[4 * w + 3]);
+#pragma unroll
+    for (int p = 0; p < 16; ++p)
+      reinterpret_cast<uint2*>(dst + SL::EP)[p] = make_uint2((uint32_t)idx[p], (uint32_t)(idx[p] >> 32));
+  }
+}
+
 }  // namespace ndgi

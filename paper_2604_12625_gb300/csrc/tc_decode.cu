@@ -38,6 +38,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <type_traits>
 
@@ -76,6 +77,7 @@ struct TcLayout {
   static constexpr uint32_t kW1T = kB1G + H * K1G * 2;     // [CT][H] f32 stored temporal weights
   static constexpr uint32_t kB1 = kW1T + CT * H * 4;       // [H] f32 stored b1
   static constexpr uint32_t kWsBytes = kB1 + H * 4;
+  static constexpr uint32_t kSliceOff = (kWsBytes + 255) / 256 * 256;   // then the texel-sliced BC4 copy (points)
   static constexpr int EB = 2;                             // bytes per operand element
   static constexpr uint32_t kTmemCols = H <= 32 ? 32 : (H <= 64 ? 64 : 128);
   static_assert(H % 16 == 0 && H <= 128, "hidden width must be a multiple of 16, at most 128");
@@ -607,7 +609,8 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
   copy16(sm + S::kW, ws, L::kShared, tid, kLaneThreads * NWG);
   copy16(sm + S::kB1, ws + L::kB1P, H * L::K1P * 2, tid, kLaneThreads * NWG);
   const uint2* lut = reinterpret_cast<const uint2*>(sm + S::kLut);
-  init_p35_lut_f(reinterpret_cast<uint2*>(sm + S::kLut), tid);
+  init_p35_lut_sliced(reinterpret_cast<uint2*>(sm + S::kLut), tid);
+  const uint8_t* sliced = ws + L::kSliceOff;
   const uint32_t tbase = cta_setup<SL * NWG, E::kSlotCols>(bars, &slot, tid);
   const uint32_t base = smem_addr(sm);
   E e;
@@ -671,7 +674,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
       }
       float x[L::CIN];
       if (q < n) {
-        gather_tc<CS, CT>(m, qu, qv, qt, x, lut);
+        gather_sliced<CS, CT>(m, sliced, qu, qv, qt, x, lut);
       } else {
 #pragma unroll
         for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
@@ -1097,6 +1100,24 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid);
 }
 
+// The tensor-core point decode's feature gather alone (on the texel-sliced
+// copy in a prepared workspace), for validation.
+template <int CS, int CT, int H>
+__global__ void __launch_bounds__(128) k_debug_features_tc(DevModel m, const unsigned char* __restrict__ ws,
+                                                           const float* __restrict__ uvt, int64_t n,
+                                                           float* __restrict__ xo) {
+  __shared__ uint2 lut[16];
+  init_p35_lut_sliced(lut, threadIdx.x);
+  __syncthreads();
+  const uint8_t* sliced = ws + TcLayout<CS, CT, H>::kSliceOff;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float x[CS + CT];
+    gather_sliced<CS, CT>(m, sliced, uvt[3 * i], uvt[3 * i + 1], uvt[3 * i + 2], x, lut);
+#pragma unroll
+    for (int c = 0; c < CS + CT; ++c) xo[i * (CS + CT) + c] = x[c];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Dispatch
 // ---------------------------------------------------------------------------
@@ -1118,18 +1139,26 @@ bool tc_supported(int cs, int ct, int hidden) {
 
 bool tc_pages_supported(int cs, int ct, int hidden) { return tc_supported(cs, ct, hidden) && cs == 16; }
 
-size_t tc_workspace_bytes(int cs, int ct, int hidden) {
-#define X(A, B, C) if (cs == A && ct == B && hidden == C) return TcLayout<A, B, C>::kWsBytes;
+size_t tc_workspace_bytes(int cs, int ct, int hidden, int feat_w, int feat_h) {
+  const size_t nblocks = (size_t)(feat_w / 4) * (size_t)(feat_h / 4);
+#define X(A, B, C) \
+  if (cs == A && ct == B && hidden == C) return TcLayout<A, B, C>::kSliceOff + nblocks * Sliced<A>::BLOCK;
   NDGI_TC_SHAPES(X)
 #undef X
   return 0;
 }
 
 cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream_t s) {
+  const int64_t nblocks = (int64_t)(m.feat_w / 4) * (m.feat_h / 4);
+  const int grid = (int)std::min<int64_t>((nblocks + 255) / 256, (int64_t)num_sms() * 8);
 #define X(A, B, C)                                                                                       \
   if (m.cs == A && m.ct == B && m.hidden == C) {                                                         \
     if (bf16) k_tc_prepare<A, B, C, true><<<16, 256, 0, s>>>(m, static_cast<unsigned char*>(ws));       \
     else k_tc_prepare<A, B, C, false><<<16, 256, 0, s>>>(m, static_cast<unsigned char*>(ws));           \
+    cudaError_t e = cudaGetLastError();                                                                  \
+    if (e != cudaSuccess) return e;                                                                      \
+    k_slice_features<A><<<grid > 0 ? grid : 1, 256, 0, s>>>(                                             \
+        m.bc4, nblocks, static_cast<unsigned char*>(ws) + TcLayout<A, B, C>::kSliceOff);                 \
     return cudaGetLastError();                                                                           \
   }
   NDGI_TC_SHAPES(X)
@@ -1292,6 +1321,20 @@ size_t tc_fp8_workspace_bytes(int cs, int ct, int hidden) {
 
 cudaError_t launch_tc_prepare8(const DevModel& m, const float act_max[3], void* ws, cudaStream_t s) {
 #define X(A, B, C) if (m.cs == A && m.ct == B && m.hidden == C) return fp8_prepare<A, B, C>(m, act_max, ws, s);
+  NDGI_TC_SHAPES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_debug_features_tc(const DevModel& m, const void* ws, const float* uvt, int64_t n, float* x,
+                                     cudaStream_t s) {
+  const int64_t blocks = (n + 127) / 128;
+  const int grid = (int)std::min<int64_t>(blocks > 0 ? blocks : 1, (int64_t)num_sms() * 16);
+#define X(A, B, C)                                                                                              \
+  if (m.cs == A && m.ct == B && m.hidden == C) {                                                                \
+    k_debug_features_tc<A, B, C><<<grid, 128, 0, s>>>(m, static_cast<const unsigned char*>(ws), uvt, n, x);     \
+    return cudaGetLastError();                                                                                  \
+  }
   NDGI_TC_SHAPES(X)
 #undef X
   return cudaErrorInvalidValue;

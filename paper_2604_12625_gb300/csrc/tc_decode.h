@@ -15,7 +15,12 @@ struct TcPagesShape {
 
 bool tc_supported(int cs, int ct, int hidden);
 bool tc_pages_supported(int cs, int ct, int hidden);
-size_t tc_workspace_bytes(int cs, int ct, int hidden);
+// The tensor-core point decode's gather alone, from a prepared FP16/BF16 workspace.
+cudaError_t launch_debug_features_tc(const DevModel& m, const void* ws, const float* uvt, int64_t n, float* x,
+                                     cudaStream_t s);
+// FP16/BF16 workspace: the weight image, then the texel-sliced copy of the
+// feature planes the point decode reads.
+size_t tc_workspace_bytes(int cs, int ct, int hidden, int feat_w, int feat_h);
 cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream_t s);
 cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const float* uvt, int64_t n, float* rgb,
                              cudaStream_t s);

@@ -164,3 +164,43 @@ def test_tc_pages_autotune_and_rgba16f(ndgi):
     ref = oracle.decode_pages(maps, reqs, 1024, 1024, precision="fp16")
     assert page_err(phys.float().cpu().numpy(), ref, reqs) <= 2e-3 + 2.0 ** -11 * 4
     plan.close()
+
+
+def test_tc_gather_exhaustive_endpoint_pairs(ndgi):
+    # Every (r0, r1) pair x every index through the texel-sliced copy ndgi_prepare builds: at texel
+    # centres the tensor-core gather returns fl32(P35) * fl32(1/8925) exactly, like the FP32 gather.
+    bits = 0
+    for p in range(16):
+        bits |= (p % 8) << (3 * p)
+    idx = np.frombuffer(bits.to_bytes(6, "little"), np.uint8)
+    pairs = np.arange(65536)
+    blocks = np.zeros((65536, 8), np.uint8)
+    blocks[:, 0] = pairs & 255
+    blocks[:, 1] = pairs >> 8
+    blocks[:, 2:] = idx
+    m = synth.model(1, 512, 512, 512, 512, 4, 4, 4, 16)
+    m["bc4"] = blocks.reshape(128, 128, 4, 8)
+    ix, iy = np.meshgrid(np.arange(512), np.arange(512))
+    q = np.stack([(ix.ravel() + 0.5) / 512, (iy.ravel() + 0.5) / 512, np.zeros(ix.size)], 1).astype(np.float32)
+    x = ndgi.ndgi_debug_features_tc(ndgi.Model.from_arrays(m), torch.from_numpy(q).cuda()).cpu().numpy()
+    _, p35_ref = oracle.features(m, q)
+    vals = np.float32(p35_ref[:, 0, :]) * (np.float32(1) / np.float32(8925))
+    assert np.array_equal(x[:, :4], vals.astype(np.float32))
+
+
+@pytest.mark.parametrize("shape", [(16, 8, 64, "f16", 0), (16, 16, 64, "f32", 0), (8, 8, 32, "f32", 1),
+                                   (4, 4, 16, "f32", 0), (16, 8, 32, "f16", 1)])
+def test_tc_gather_matches_fp32_gather(ndgi, shape):
+    cs, ct, H, tdt, mode = shape
+    m = synth.model(13, 1000, 700, 256, 128, cs, 24, ct, H, temporal_dtype=tdt, address_mode=mode)
+    q = edge_queries(30000, 14)
+    if mode == 1:
+        q[:5000, :2] = np.random.default_rng(15).uniform(-2.0, 3.0, (5000, 2)).astype(np.float32)
+    model = ndgi.Model.from_arrays(m)
+    qt = torch.from_numpy(q).cuda()
+    x_tc = ndgi.ndgi_debug_features_tc(model, qt).cpu().numpy()
+    x32, _ = ndgi.ndgi_debug_features(model, qt)
+    x32 = x32.cpu().numpy()
+    xr, _ = oracle.features(m, q)
+    assert np.max(np.abs(x_tc - x32)) <= 2e-6 * max(1.0, np.abs(x32).max())
+    assert np.max(np.abs(x_tc - xr)) <= 4e-6 * max(1.0, np.abs(xr).max())
