@@ -101,7 +101,8 @@ size_t ndgi_prepare_workspace_size(const ndgi_model_desc* model, ndgi_precision 
   if (!model) return 0;
   if (precision == NDGI_FP16 || precision == NDGI_BF16)
     return tc_workspace_bytes(model->cs, model->ct, model->hidden, model->feat_w, model->feat_h);
-  if (precision == NDGI_FP8_E4M3) return tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden);
+  if (precision == NDGI_FP8_E4M3)
+    return tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden, model->feat_w, model->feat_h);
   return 0;
 }
 
@@ -129,7 +130,7 @@ ndgi_status ndgi_prepare_fp8(const ndgi_model_desc* model, const float act_max[3
   if (!tc_fp8_pages_supported(model->cs, model->ct, model->hidden))
     return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_prepare_fp8: FP8 shape cs=%d ct=%d hidden=%d not built (cs = 16, "
                      "hidden a multiple of 32)", model->cs, model->ct, model->hidden);
-  const size_t need = tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden);
+  const size_t need = tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden, model->feat_w, model->feat_h);
   if (!ws || ws_bytes < need || !aligned(ws, 256))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_prepare_fp8: ws must be 256-byte aligned with >= %zu bytes", need);
   cudaStream_t s = (cudaStream_t)stream;
@@ -151,7 +152,7 @@ ndgi_status ndgi_prepare_fp8(const ndgi_model_desc* model, const float act_max[3
 ndgi_status ndgi_fp8_unpack(const ndgi_model_desc* model, const void* ws, float* out, size_t out_len,
                             size_t* needed) {
   if (!model || !ws) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fp8_unpack: NULL argument");
-  const size_t bytes = tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden);
+  const size_t bytes = tc_fp8_workspace_bytes(model->cs, model->ct, model->hidden, 0, 0);   // the image, not the slice
   if (!bytes) return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_fp8_unpack: no FP8 image for this shape");
   const size_t n = tc_fp8_unpack(model->cs, model->ct, model->hidden, nullptr, nullptr, 0);
   if (needed) *needed = n;

@@ -115,6 +115,7 @@ struct TcLayout8 {
   static constexpr uint32_t kB1 = kW1T + CT * H * 4;       // [H] f32 b1
   static constexpr uint32_t kScale = kB1 + H * 4;          // Fp8Scales
   static constexpr uint32_t kWsBytes = kScale + sizeof(Fp8Scales);
+  static constexpr uint32_t kSliceOff = (kWsBytes + 255) / 256 * 256;   // then the texel-sliced BC4 copy
   static_assert(CS + 3 <= K1G && H % 32 == 0 && H <= 128, "FP8 pages: cs <= 29, hidden a multiple of 32");
   static_assert(kShared % 16 == 0 && kW1T % 16 == 0 && kScale % 16 == 0 && kWsBytes % 16 == 0, "granularity");
 };
@@ -732,7 +733,8 @@ struct PagesSmem {
   static constexpr uint32_t kW1T = kB1 + (L::kW1T - L::kB1G);           // [CT][H] f32
   static constexpr uint32_t kBias1 = kB1 + (L::kB1 - L::kB1G);          // [H] f32 stored b1
   static constexpr uint32_t kLut = (kB1 + kTail + 127) / 128 * 128;
-  static constexpr uint32_t kLanes = kLut + 128;
+  static constexpr uint32_t kLutS = kLut + 128;                         // palette table of the sliced decode
+  static constexpr uint32_t kLanes = kLutS + 128;
   // per lane: the feature ring and the row table
   static constexpr uint32_t kRing = 0;
   static constexpr uint32_t kRowTab = kRing + (CS / 8) * kRingPlane;   // [64] int4
@@ -774,6 +776,47 @@ __device__ __forceinline__ void decode_rows(const DevModel& m, unsigned char* ri
     }
     *reinterpret_cast<uint4*>(ring + g * kRingPlane + ((fr & (kRingRows - 1)) * kRingCols + col) * 16) =
         make_uint4(h[0], h[1], h[2], h[3]);
+  }
+}
+
+// The same from the texel-sliced copy of the planes: one work unit = one
+// feature texel of all 16 planes (two 16-byte endpoint loads and one 8-byte
+// index word), written as the two 16-byte ring entries.  The values are the
+// same FP16 roundings of fl32(P35) * fl32(1/8925).
+__device__ __forceinline__ uint32_t field3_at(uint2 w, int s) {
+  return __funnelshift_r(s < 32 ? w.x : w.y, s < 32 ? w.y : 0u, s & 31) & 7u;
+}
+
+template <int CS>
+__device__ __forceinline__ void decode_rows_sliced(const DevModel& m, const uint8_t* sl, unsigned char* ring,
+                                                   int r_from, int r_to, int fc0, int ncols, int t,
+                                                   const uint2* luts) {
+  static_assert(CS == 16, "two ring planes of 8 channels");
+  using SLc = Sliced<CS>;
+  const int total = (r_to - r_from + 1) * ncols;
+  for (int u = t; u < total; u += kLaneThreads) {
+    const int rr = u / ncols, col = u - rr * ncols;
+    const int fr = r_from + rr, fc = fc0 + col;
+    const uint8_t* base = sl + ((size_t)(fr >> 2) * m.bw + (fc >> 2)) * SLc::BLOCK;
+    const int p = ((fr & 3) << 2) | (fc & 3);
+    const uint4 e0 = __ldg(reinterpret_cast<const uint4*>(base));
+    const uint4 e1 = __ldg(reinterpret_cast<const uint4*>(base) + 1);
+    const uint2 ix = __ldg(reinterpret_cast<const uint2*>(base + SLc::EP) + p);
+    const uint32_t ew[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+    uint32_t h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t w = ew[j];
+      const uint32_t tm = ((w >> 8) & 0x00FF00FFu) + 0x01000100u - (w & 0x00FF00FFu);
+      const uint2 el = luts[field3_at(ix, 6 * j) | ((tm >> 5) & 8u)];
+      const uint2 eh = luts[field3_at(ix, 6 * j + 3) | ((tm >> 21) & 8u)];
+      const float f0 = __fmul_rn(__uint_as_float(__dp2a_lo(el.x, w, el.y)) - 8388608.0f, kInv8925);
+      const float f1 = __fmul_rn(__uint_as_float(__dp2a_hi(eh.x, w, eh.y)) - 8388608.0f, kInv8925);
+      h[j] = pack2<false>(f0, f1);
+    }
+    unsigned char* dst = ring + ((fr & (kRingRows - 1)) * kRingCols + col) * 16;
+    *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(dst + kRingPlane) = make_uint4(h[4], h[5], h[6], h[7]);
   }
 }
 
@@ -865,7 +908,9 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
     n = 0;
   }
   const uint2* lut = reinterpret_cast<const uint2*>(sm + S::kLut);
+  const uint2* luts = reinterpret_cast<const uint2*>(sm + S::kLutS);
   init_p35_lut(reinterpret_cast<uint2*>(sm + S::kLut), tid);
+  if (tid >= 32 && tid < 48) init_p35_lut_sliced(reinterpret_cast<uint2*>(sm + S::kLutS), tid - 32);
   const uint32_t tbase = cta_setup<SL * NWG, E::kSlotCols>(bars, &slot, tid);
   const uint32_t base = smem_addr(sm);
   E e;
@@ -1038,7 +1083,8 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
             if (need_hi > decoded_hi) {
               const int from = max(decoded_hi + 1, rowtab[row_base].x);
               const int to = min(need_hi + kDecodeAhead, fr_last);
-              decode_rows<CS>(m, ring, from, to, fc0, ncols, t, lut);
+              decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
+                                     fc0, ncols, t, luts);
               decoded_hi = to;
               lane_sync(wg);
             }
@@ -1242,8 +1288,8 @@ bool tc_fp8_pages_supported(int cs, int ct, int hidden) { return tc_pages_suppor
 
 // Per-shape FP8 helpers (only shapes with cs = 16 and hidden % 32 == 0 have an FP8 image).
 template <int CS, int CT, int H>
-static size_t fp8_ws_bytes() {
-  if constexpr (CS == 16 && H % 32 == 0) return TcLayout8<CS, CT, H>::kWsBytes;
+static size_t fp8_ws_bytes(size_t nblocks) {
+  if constexpr (CS == 16 && H % 32 == 0) return TcLayout8<CS, CT, H>::kSliceOff + nblocks * Sliced<CS>::BLOCK;
   else return 0;
 }
 template <int CS, int CT, int H>
@@ -1255,6 +1301,12 @@ template <int CS, int CT, int H>
 static cudaError_t fp8_prepare(const DevModel& m, const float act_max[3], void* ws, cudaStream_t s) {
   if constexpr (CS == 16 && H % 32 == 0) {
     k_tc_prepare8<CS, CT, H><<<1, 256, 0, s>>>(m, act_max[0], act_max[1], act_max[2], static_cast<unsigned char*>(ws));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nblocks = (int64_t)(m.feat_w / 4) * (m.feat_h / 4);
+    const int grid = (int)std::min<int64_t>((nblocks + 255) / 256, (int64_t)num_sms() * 8);
+    k_slice_features<CS><<<grid > 0 ? grid : 1, 256, 0, s>>>(m.bc4, nblocks,
+                                                            static_cast<unsigned char*>(ws) + TcLayout8<CS, CT, H>::kSliceOff);
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;
@@ -1312,8 +1364,9 @@ size_t tc_fp8_unpack(int cs, int ct, int hidden, const unsigned char* image, flo
   return 0;
 }
 
-size_t tc_fp8_workspace_bytes(int cs, int ct, int hidden) {
-#define X(A, B, C) if (cs == A && ct == B && hidden == C) return fp8_ws_bytes<A, B, C>();
+size_t tc_fp8_workspace_bytes(int cs, int ct, int hidden, int feat_w, int feat_h) {
+  const size_t nblocks = (size_t)(feat_w / 4) * (size_t)(feat_h / 4);
+#define X(A, B, C) if (cs == A && ct == B && hidden == C) return fp8_ws_bytes<A, B, C>(nblocks);
   NDGI_TC_SHAPES(X)
 #undef X
   return 0;

@@ -32,7 +32,7 @@ cudaError_t launch_tc_pages(const PagesCtx& c, int prec, int cs, int ct, int hid
 // calibration maxima (host array of 3), and the byte offset of the image's
 // status word (bit 0: a bias out of the representable range; bit 1: 1/a1 too large).
 bool tc_fp8_pages_supported(int cs, int ct, int hidden);
-size_t tc_fp8_workspace_bytes(int cs, int ct, int hidden);
+size_t tc_fp8_workspace_bytes(int cs, int ct, int hidden, int feat_w, int feat_h);
 cudaError_t launch_tc_prepare8(const DevModel& m, const float act_max[3], void* ws, cudaStream_t s);
 uint32_t tc_fp8_status_offset(int cs, int ct, int hidden);
 // Stored FP8 parameters of a host copy of the image as FP32 (see ndgi_fp8_unpack);
