@@ -378,10 +378,12 @@ struct Engine {
   static constexpr int KS = F8 ? 32 : 16;                    // K elements per MMA
   static constexpr int EB = F8 ? 1 : 2;                      // bytes per element
   static constexpr int K2 = H + KS;
-  static constexpr uint32_t kACol = H;                       // A region starts after D
-  static constexpr uint32_t kSlotCols = tmem_alloc_cols(H + K2 * EB / 4);
+  static constexpr uint32_t kACol = H;                       // hidden A region starts after D
   static constexpr int kA1Words = K1 * EB / 4;               // 32-bit words of a layer-1 row
-  static_assert(kA1Words <= K2 * EB / 4 + 8, "layer-1 tile must fit the A region");
+  // The layer-1 tile has its own columns after the hidden A region, so the
+  // next tile's features can be written while this tile's layers 2 and 3 run.
+  static constexpr uint32_t kA1Col = kACol + K2 * EB / 4;
+  static constexpr uint32_t kSlotCols = tmem_alloc_cols(kA1Col + kA1Words);
   static_assert(!F8 || H % 32 == 0, "FP8 epilogue works on 32-column chunks");
   int wg, t;
   uint32_t tmem[SL];     // slot base, lane 0
@@ -391,15 +393,15 @@ struct Engine {
   uint64_t db1, db2, db3;
 
   template <int KSTEPS, int N>
-  __device__ __forceinline__ void issue(int s, uint64_t b_desc) {
+  __device__ __forceinline__ void issue(int s, uint32_t a_col, uint64_t b_desc) {
     tc_fence_after();
 #pragma unroll
     for (int ks = 0; ks < KSTEPS; ++ks) {
       if constexpr (F8)
-        umma_f8_ts(tmem[s], tmem[s] + kACol + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, false),
+        umma_f8_ts(tmem[s], tmem[s] + a_col + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, false),
                    ks > 0 ? 1u : 0u);
       else
-        umma_f16_ts(tmem[s], tmem[s] + kACol + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16),
+        umma_f16_ts(tmem[s], tmem[s] + a_col + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16),
                     ks > 0 ? 1u : 0u);
     }
     umma_commit(bar[s]);
@@ -412,15 +414,15 @@ struct Engine {
   }
   __device__ __forceinline__ void layer1(int s) {
     publish();
-    if (t == 0) issue<K1 / KS, H>(s, db1);
+    if (t == 0) issue<K1 / KS, H>(s, kA1Col, db1);
   }
   __device__ __forceinline__ void layer2(int s) {
     publish();
-    if (t == 0) issue<K2 / KS, H>(s, db2);
+    if (t == 0) issue<K2 / KS, H>(s, kACol, db2);
   }
   __device__ __forceinline__ void layer3(int s) {
     publish();
-    if (t == 0) issue<K2 / KS, 16>(s, db3);
+    if (t == 0) issue<K2 / KS, 16>(s, kACol, db3);
   }
   // Thread 0 waits for slot s's MMAs, the lane blocks in its barrier.  false
   // (uniform) on timeout; the phase then keeps the parity still outstanding.
@@ -432,9 +434,10 @@ struct Engine {
     tc_fence_after();
     return true;
   }
-  // Layer-1 row of this thread: kA1Words packed words.
+  // Layer-1 row of this thread: kA1Words packed words (once the slot's
+  // previous layer-1 MMA has completed).
   __device__ __forceinline__ void write_a1(int s, const uint32_t* w) {
-    const uint32_t a = tmem[s] + lane_off + kACol;
+    const uint32_t a = tmem[s] + lane_off + kA1Col;
 #pragma unroll
     for (int c = 0; c < kA1Words; c += 8) {
       if (c + 16 <= kA1Words && (c % 16) == 0) {
@@ -617,15 +620,10 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
   E e;
   engine_init<H, P, L::K1P, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
   const int t = e.t;
-  // inflight[s]: slot s has MMAs issued and not yet waited for; need_out[s]:
-  // its layer-3 result is still to be read out (one round later).
-  bool inflight[SL], need_out[SL], timed_out = false;
-  int64_t prev_q[SL];
+  // inflight[s]: slot s has MMAs issued and not yet waited for.
+  bool inflight[SL], timed_out = false;
 #pragma unroll
-  for (int s = 0; s < SL; ++s) {
-    inflight[s] = need_out[s] = false;
-    prev_q[s] = -1;
-  }
+  for (int s = 0; s < SL; ++s) inflight[s] = false;
   const int64_t tiles = (n + 127) / 128;
   const int64_t lanes = (int64_t)gridDim.x * NWG, lane_id = (int64_t)blockIdx.x * NWG + e.wg;
   const int64_t qstep = (int64_t)SL * lanes * 128;   // from a slot's tile to its next tile, per query
@@ -643,35 +641,32 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
       nt[s] = __ldcs(uvt + 3 * q0 + 2);
     }
   }
-  for (int64_t round = 0; !timed_out; ++round) {
-    bool active[SL], any = false;
-#pragma unroll
-    for (int s = 0; s < SL; ++s) {
-      const int64_t tile = lane_id + (SL * round + s) * lanes;
-      active[s] = tile < tiles;
-      any = any || active[s];
-      if (timed_out) continue;
-      if (need_out[s]) {   // finish this slot's previous tile
-        if (!e.wait(s)) {
-          timed_out = true;
-          continue;
-        }
-        inflight[s] = need_out[s] = false;
-        float y0, y1, y2;
-        e.output(s, y0, y1, y2);
-        if (prev_q[s] < n) {
-          rgb[3 * prev_q[s]] = y0;
-          rgb[3 * prev_q[s] + 1] = y1;
-          rgb[3 * prev_q[s] + 2] = y2;
-        }
+  // One tile in flight per lane, software-pipelined so that the next tile's
+  // gather runs while this tile's layers 2 and 3 are on the tensor core:
+  //   [layer-1 result -> ReLU -> layer 2] [gather the next tile into the
+  //   layer-1 columns] [layer-2 result -> layer 3 -> RGB out] [next layer 1]
+  static_assert(SL == 1, "the point decode pipelines one tile per lane");
+  int64_t tile = lane_id, q_cur = -1;
+  bool have = false;   // a tile whose layer 1 has been issued
+  for (;;) {
+    if (have) {
+      if (!e.wait(0)) {
+        timed_out = true;
+        break;
       }
-      if (!active[s]) continue;
+      inflight[0] = false;
+      e.epilogue(0);
+      e.layer2(0);
+      inflight[0] = true;
+    }
+    const bool more = tile < tiles;
+    if (more) {   // the slot's layer-1 MMA has completed: its columns are free
       const int64_t q = tile * 128 + t, qn = q + qstep;
-      const float qu = nu[s], qv = nv[s], qt = nt[s];
+      const float qu = nu[0], qv = nv[0], qt = nt[0];
       if (qn < n) {
-        nu[s] = __ldcs(uvt + 3 * qn);
-        nv[s] = __ldcs(uvt + 3 * qn + 1);
-        nt[s] = __ldcs(uvt + 3 * qn + 2);
+        nu[0] = __ldcs(uvt + 3 * qn);
+        nv[0] = __ldcs(uvt + 3 * qn + 1);
+        nt[0] = __ldcs(uvt + 3 * qn + 2);
       }
       float x[L::CIN];
       if (q < n) {
@@ -682,32 +677,36 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
       }
       uint32_t w[L::K1P / 2];
       pack_a1<L::CIN, L::K1P, BF16>(x, w);
-      e.write_a1(s, w);
-      e.layer1(s);
-      inflight[s] = true;
-      prev_q[s] = q;
+      e.write_a1(0, w);
     }
-    if (timed_out || !any) break;
-#pragma unroll
-    for (int layer = 2; layer <= 3; ++layer) {
-#pragma unroll
-      for (int s = 0; s < SL; ++s) {
-        if (!active[s] || timed_out) continue;
-        if (!e.wait(s)) {
-          timed_out = true;
-          continue;
-        }
-        inflight[s] = false;
-        e.epilogue(s);
-        if (layer == 2) {
-          e.layer2(s);
-        } else {
-          e.layer3(s);
-          need_out[s] = true;
-        }
-        inflight[s] = true;
+    if (have) {
+      if (!e.wait(0)) {
+        timed_out = true;
+        break;
+      }
+      inflight[0] = false;
+      e.epilogue(0);
+      e.layer3(0);
+      inflight[0] = true;
+      if (!e.wait(0)) {
+        timed_out = true;
+        break;
+      }
+      inflight[0] = false;
+      float y0, y1, y2;
+      e.output(0, y0, y1, y2);
+      if (q_cur < n) {
+        rgb[3 * q_cur] = y0;
+        rgb[3 * q_cur + 1] = y1;
+        rgb[3 * q_cur + 2] = y2;
       }
     }
+    if (!more) break;
+    e.layer1(0);
+    inflight[0] = true;
+    have = true;
+    q_cur = tile * 128 + t;
+    tile += lanes;
   }
   cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid);
 }
