@@ -1043,6 +1043,106 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
 #pragma unroll
       for (int s = 0; s < SL; ++s) prev_row[s] = -1;
       const int ntiles = (qh + 1) / 2;
+      if constexpr (SL == 1) {
+        // One tile in flight per lane, software-pipelined: the next tile's
+        // layer-1 rows are written (ring decode and blend) while this tile's
+        // layers 2 and 3 run.
+        int tile = 0, cur_row = -1;
+        bool have = false;   // a tile whose layer 1 has been issued
+        for (;;) {
+          if (have) {
+            if (!e.wait(0)) {
+              timed_out = true;
+              break;
+            }
+            inflight[0] = false;
+            e.epilogue(0, F8 ? sc->ones2 : 0u);
+            e.layer2(0);
+            inflight[0] = true;
+          }
+          const bool more = tile < ntiles;
+          int next_row = -1;
+          if (more) {   // the slot's layer-1 MMA has completed: its columns are free
+            const int row_base = 2 * tile;
+            if (staged) {   // feature rows needed by output rows row_base, row_base + 1
+              const int need_hi = rowtab[min(row_base + 1, qh - 1)].y;
+              if (need_hi > decoded_hi) {
+                const int from = max(decoded_hi + 1, rowtab[row_base].x);
+                const int to = min(need_hi + kDecodeAhead, fr_last);
+                decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
+                                       fc0, ncols, t, luts);
+                decoded_hi = to;
+                lane_sync(wg);
+              }
+            }
+            const int orow = row_base + (t >> 6);
+            uint32_t w[NW];
+            if (col < qw && orow < qh) {
+              if (staged) {
+                ring_texel<CS, P, NW>(w, ring, rowtab[orow], c0, c1, wx0, wx1);
+              } else {
+                float x[CS + CT];
+                gather_f32<CS, CT, false>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
+                                          ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr, lut);
+                if constexpr (F8) {
+#pragma unroll
+                  for (int j = 0; j < CS / 4; ++j)
+                    w[j] = e4m3x2(x[4 * j] * xs, x[4 * j + 1] * xs) |
+                           (e4m3x2(x[4 * j + 2] * xs, x[4 * j + 3] * xs) << 16);
+                } else {
+#pragma unroll
+                  for (int j = 0; j < CS / 2; ++j) w[j] = pack2<BF16>(x[2 * j], x[2 * j + 1]);
+                }
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < CS * E::EB / 4; ++j) w[j] = 0u;
+            }
+            a1_bias_words<CS, P, NW>(w, F8 ? s_ones1 : 0u);
+            e.write_a1(0, w);
+            next_row = orow;
+          }
+          if (have) {
+            if (!e.wait(0)) {
+              timed_out = true;
+              break;
+            }
+            inflight[0] = false;
+            e.epilogue(0, F8 ? sc->ones3 : 0u);
+            e.layer3(0);
+            inflight[0] = true;
+            if (!e.wait(0)) {
+              timed_out = true;
+              break;
+            }
+            inflight[0] = false;
+            float y0, y1, y2;
+            e.output(0, y0, y1, y2);
+            if constexpr (F8) {
+              const float so = sc->out;
+              y0 *= so;
+              y1 *= so;
+              y2 *= so;
+            }
+            if (col < qw && cur_row < qh) {
+              const int64_t o = (int64_t)(r.dst_y + oy + cur_row) * c.phys_w + (r.dst_x + ox + col);
+              if (c.out_format == NDGI_RGBA32F) {
+                reinterpret_cast<float4*>(c.phys)[o] = make_float4(y0, y1, y2, 1.0f);
+              } else {
+                reinterpret_cast<uint2*>(c.phys)[o] = make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f));
+              }
+            }
+          }
+          if (!more) break;
+          e.layer1(0);
+          inflight[0] = true;
+          have = true;
+          cur_row = next_row;
+          ++tile;
+        }
+        (void)prev_row;
+      } else {
+      const int ntiles = (qh + 1) / 2;
       for (int round = 0; !timed_out; ++round) {
         bool active[SL], any = false;
 #pragma unroll
@@ -1137,6 +1237,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
             inflight[s] = true;
           }
         }
+      }
       }
     }
     // every lane must be done with the weights and b1' before the next request
