@@ -115,10 +115,11 @@ size_t ndgi_prepare_workspace_size(const ndgi_model_desc *model, ndgi_precision 
  * ndgi_prepare_workspace_size, 256-byte aligned) for decodes of
  * `precision`: weights rounded once to FP16/BF16 (round to nearest even),
  * laid out as the tensor-core operand tiles, followed by a texel-sliced copy
- * of the BC4 planes for the point decode (the same bits regrouped so that a
- * texel of every plane is two short reads: per block the cs endpoint pairs,
- * then per texel one 8-byte word of the planes' 3-bit indices; 1.25x the
- * planes' size for cs = 16).  The packed weights are the parameters such a
+ * of the BC4 planes for the tensor-core decodes (the same information
+ * regrouped so that a texel of every plane is two short reads: per block the
+ * cs endpoint pairs, then per texel one 8-byte word holding, per plane, its
+ * 3-bit index and the block's palette mode (r0 <= r1) as a 4-bit nibble;
+ * 1.25x the planes' size for cs = 16).  The packed weights are the parameters such a
  * decode evaluates.  Re-run it whenever the weights or the planes change.
  */
 ndgi_status ndgi_prepare(const ndgi_model_desc *model, ndgi_precision precision, void *ws, size_t ws_bytes,

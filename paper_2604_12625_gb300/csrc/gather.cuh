@@ -227,14 +227,16 @@ __device__ __forceinline__ void gather_tc(const DevModel& m, float u, float v, f
 
 // ---------------------------------------------------------------------------
 // Texel-sliced copy of the BC4 planes (built by ndgi_prepare for the tensor-
-// core point decode).  The same bits, regrouped per 4x4 block so that one
+// core decodes).  The same information, regrouped per 4x4 block so that one
 // texel of every plane is two short reads instead of a whole 128-byte line
 // and a variable 64-bit shift per plane.  Block (by, bx) starts at
 // (by * bw + bx) * BLOCK bytes:
 //   [0, EP)          the (r0, r1) endpoint bytes of planes 0..CS-1 (plane c at
 //                    bytes 2c, 2c+1), zero padded;
-//   [EP, EP + 128)   16 words of 8 bytes: texel p's word holds plane c's
-//                    3-bit index at bit 3c.
+//   [EP, EP + 128)   16 words of 8 bytes: texel p's word holds, for plane c,
+//                    the nibble (n8 << 3 | k) at bit 4c, k the texel's 3-bit
+//                    index and n8 = 1 when r0 <= r1 (the block's palette mode,
+//                    derived from its endpoints), i.e. the palette-table entry.
 // ---------------------------------------------------------------------------
 template <int CS>
 struct Sliced {
@@ -256,41 +258,36 @@ __device__ __forceinline__ void init_p35_lut_sliced(uint2* lut, int tid) {
   }
 }
 
-// 3-bit field at compile-time bit S of the 64-bit word {lo, hi}.
-template <int S>
-__device__ __forceinline__ uint32_t field3(uint2 w) {
-  if constexpr (S + 3 <= 32) return (w.x >> S) & 7u;
-  else if constexpr (S >= 32) return (w.y >> (S - 32)) & 7u;
-  else return __funnelshift_r(w.x, w.y, S) & 7u;
+// Plane c's palette-table entry (nibble at bit 4c of the texel word {lo, hi}).
+template <int C>
+__device__ __forceinline__ uint32_t nibble(uint2 w) {
+  if constexpr (C < 8) return (w.x >> (4 * C)) & 15u;
+  else return (w.y >> (4 * (C - 8))) & 15u;
+}
+__device__ __forceinline__ uint32_t nibble_at(uint2 w, int c) {
+  return ((c < 8 ? w.x : w.y) >> (4 * (c & 7))) & 15u;
 }
 
 // Plane c's palette value at one tap, as the float 2^23 + P35: w is the
-// endpoint word of planes 2*(c/2), 2*(c/2)+1, t its two modes (bit 8 / bit 24
-// set when r0 <= r1), k the texel's index.
+// endpoint word of planes 2*(c/2), 2*(c/2)+1, e its table entry.
 template <int C>
-__device__ __forceinline__ float sliced_value(uint32_t w, uint32_t t, uint32_t k, const uint2* lut) {
-  if constexpr ((C & 1) == 0) {
-    const uint2 e = lut[k | ((t >> 5) & 8u)];
-    return __uint_as_float(__dp2a_lo(e.x, w, e.y));
-  } else {
-    const uint2 e = lut[k | ((t >> 21) & 8u)];
-    return __uint_as_float(__dp2a_hi(e.x, w, e.y));
-  }
+__device__ __forceinline__ float sliced_value(uint32_t w, uint2 e) {
+  if constexpr ((C & 1) == 0) return __uint_as_float(__dp2a_lo(e.x, w, e.y));
+  else return __uint_as_float(__dp2a_hi(e.x, w, e.y));
 }
 
 template <int CS, int CT, int C>
-__device__ __forceinline__ void sliced_plane(const uint32_t (&ew)[4][Sliced<CS>::EP / 4], const uint32_t (&tm)[4][Sliced<CS>::EP / 4],
-                                             const uint2 (&ix)[4], const float (&wq)[4], float (&x)[CS + CT],
-                                             const uint2* lut) {
+__device__ __forceinline__ void sliced_plane(const uint32_t (&ew)[4][Sliced<CS>::EP / 4], const uint2 (&ix)[4],
+                                             const float (&wq)[4], float (&x)[CS + CT], const uint2* lut) {
   if constexpr (C < CS) {
     float acc = 0.0f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float p = sliced_value<C>(ew[q][C / 2], tm[q][C / 2], field3<3 * C>(ix[q]), lut) - 8388608.0f;
+      const float p = sliced_value<C>(ew[q][C / 2], lut[nibble<C>(ix[q])]) - 8388608.0f;
       acc = fmaf(wq[q], p, acc);
     }
     x[C] = acc;
-    sliced_plane<CS, CT, C + 1>(ew, tm, ix, wq, x, lut);
+    sliced_plane<CS, CT, C + 1>(ew, ix, wq, x, lut);
   }
 }
 
@@ -331,22 +328,18 @@ __device__ __forceinline__ void gather_sliced(const DevModel& m, const uint8_t* 
     if (same_y) e[2][h] = e[0][h];
     if (same_x || same_y) e[3][h] = same_x ? e[2][h] : e[1][h];
   }
-  // endpoint words and their two modes: t = r1 + 256 - r0 per 16-bit half
-  uint32_t ew[4][SL::EP / 4], tm[4][SL::EP / 4];
+  uint32_t ew[4][SL::EP / 4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
 #pragma unroll
     for (int h = 0; h < EW; ++h) {
-      const uint32_t w4[4] = {e[q][h].x, e[q][h].y, e[q][h].z, e[q][h].w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const uint32_t w = w4[i];
-        ew[q][4 * h + i] = w;
-        tm[q][4 * h + i] = ((w >> 8) & 0x00FF00FFu) + 0x01000100u - (w & 0x00FF00FFu);
-      }
+      ew[q][4 * h] = e[q][h].x;
+      ew[q][4 * h + 1] = e[q][h].y;
+      ew[q][4 * h + 2] = e[q][h].z;
+      ew[q][4 * h + 3] = e[q][h].w;
     }
   }
-  sliced_plane<CS, CT, 0>(ew, tm, ix, wq, x, lut);
+  sliced_plane<CS, CT, 0>(ew, ix, wq, x, lut);
   int j0, j1;
   float a;
   temporal_setup(t, m.t_count, j0, j1, a);
@@ -407,8 +400,9 @@ __global__ void k_slice_features(const uint8_t* __restrict__ bc4, int64_t nblock
 #pragma unroll
       for (int k = 0; k < 8; ++k) b |= (uint64_t)src[c * 8 + k] << (8 * k);
       ep[c / 2] |= (uint32_t)(b & 0xFFFFu) << (16 * (c & 1));
+      const uint64_t n8 = (b & 0xFFu) <= ((b >> 8) & 0xFFu) ? 8u : 0u;   // r0 <= r1: six-value palette
 #pragma unroll
-      for (int p = 0; p < 16; ++p) idx[p] |= ((b >> (16 + 3 * p)) & 7u) << (3 * c);
+      for (int p = 0; p < 16; ++p) idx[p] |= (((b >> (16 + 3 * p)) & 7u) | n8) << (4 * c);
     }
 #pragma unroll
     for (int w = 0; w < SL::EP / 16; ++w)

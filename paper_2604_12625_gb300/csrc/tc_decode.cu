@@ -782,10 +782,6 @@ __device__ __forceinline__ void decode_rows(const DevModel& m, unsigned char* ri
 // feature texel of all 16 planes (two 16-byte endpoint loads and one 8-byte
 // index word), written as the two 16-byte ring entries.  The values are the
 // same FP16 roundings of fl32(P35) * fl32(1/8925).
-__device__ __forceinline__ uint32_t field3_at(uint2 w, int s) {
-  return __funnelshift_r(s < 32 ? w.x : w.y, s < 32 ? w.y : 0u, s & 31) & 7u;
-}
-
 template <int CS>
 __device__ __forceinline__ void decode_rows_sliced(const DevModel& m, const uint8_t* sl, unsigned char* ring,
                                                    int r_from, int r_to, int fc0, int ncols, int t,
@@ -806,9 +802,8 @@ __device__ __forceinline__ void decode_rows_sliced(const DevModel& m, const uint
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const uint32_t w = ew[j];
-      const uint32_t tm = ((w >> 8) & 0x00FF00FFu) + 0x01000100u - (w & 0x00FF00FFu);
-      const uint2 el = luts[field3_at(ix, 6 * j) | ((tm >> 5) & 8u)];
-      const uint2 eh = luts[field3_at(ix, 6 * j + 3) | ((tm >> 21) & 8u)];
+      const uint2 el = luts[nibble_at(ix, 2 * j)];
+      const uint2 eh = luts[nibble_at(ix, 2 * j + 1)];
       const float f0 = __fmul_rn(__uint_as_float(__dp2a_lo(el.x, w, el.y)) - 8388608.0f, kInv8925);
       const float f1 = __fmul_rn(__uint_as_float(__dp2a_hi(eh.x, w, eh.y)) - 8388608.0f, kInv8925);
       h[j] = pack2<false>(f0, f1);
