@@ -207,6 +207,14 @@ __device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
   return d;
 }
 
+// Stored b3 of an FP16/BF16 image (column H of the B3 tile) as FP32.
+template <bool BF16>
+__device__ __forceinline__ float stored_b3(const unsigned char* b3_img, int n, int H, int K2) {
+  const uint16_t b = *reinterpret_cast<const uint16_t*>(b3_img + kmajor_offset(n, H, K2));
+  if (BF16) return __uint_as_float((uint32_t)b << 16);
+  return __half2float(__ushort_as_half(b));
+}
+
 template <int CS, int CT, int H, bool BF16>
 __global__ void k_tc_prepare(DevModel m, unsigned char* __restrict__ ws) {
   using L = TcLayout<CS, CT, H>;
@@ -358,17 +366,30 @@ constexpr uint32_t tmem_alloc_cols(int cols) {
 // ---------------------------------------------------------------------------
 // One lane's MLP engine with SL tile slots.
 //
-// A slot is one 128-row tile in flight: a region of tensor memory holding the
-// accumulator D (H columns, FP32) followed by the A operand of the next MMA
-// (rows in lanes; two 16-bit or four 8-bit K elements per column), and an
-// mbarrier.  The layer-1 A tile (features, bias ones column(s), zeros) and the
-// hidden tiles (H ReLU values, then the ones columns carrying the bias in the
-// K padding, K2 = H + one K step) take turns in the A region, written from
-// registers with tcgen05.st.  Only the small weight tiles B are read from
-// shared memory.  With SL = 2 the lane interleaves its slots so that one
-// slot's gather or epilogue runs while the other slot's MMAs are in flight.
+// A slot is one 128-row tile in flight: a region of tensor memory and an
+// mbarrier.  Its columns (FP16 example, H = 64):
+//   [0, H)             accumulator D of layers 1 and 2 (FP32)
+//   [H, H + K2/2)      A operand of layer 2 (ReLU(H1), then the ones column
+//                      that carries b2 in the K padding) and of layer 3
+//                      (ReLU(H2) only: b3 is added when D3 is read)
+//   [kD3Col, +16)      layer-3 accumulator (N = 16, 3 used)
+//   [kA1Col, ...)      A operand of layer 1 (features, bias ones columns)
+// Layer 3 of a tile and layer 1 of the slot's next tile touch disjoint
+// columns, so they are issued back to back under one commit: a tile costs
+// two MMA round trips (layer 1 with the previous tile's layer 3, then
+// layer 2), not three.  D3 shares columns with the tail of the layer-2 A
+// region only across time: each thread reads its D3 row before it writes
+// its next layer-2 row.
+// All operands but the small weight tiles B live in tensor memory, written
+// from registers with tcgen05.st.  Every thread of the lane waits on the
+// slot's mbarrier itself (no barrier round trip after completion); a wait
+// that times out is carried to the lane's next barrier, where the lane
+// decides uniformly to stop.  The thread that issues (one per lane, in a
+// different warp of each lane so the four issuers sit on different SM
+// sub-partitions) waits like the others.
 // P: kF16 / kBF16 (kind::f16, K step 16) or kE4M3 (kind::f8f6f4, K step 32);
 // either way a K step is 32 bytes of a row: 8 TMEM columns, 256 B of B.
+// E4M3 keeps b3 in the K padding (three E4M3 terms), as for layer 2.
 // ---------------------------------------------------------------------------
 constexpr uint64_t kDescK = 256 >> 4;   // B descriptor start-address step per K step (256 B)
 
@@ -377,62 +398,90 @@ struct Engine {
   static constexpr bool BF16 = P == kBF16, F8 = P == kE4M3;
   static constexpr int KS = F8 ? 32 : 16;                    // K elements per MMA
   static constexpr int EB = F8 ? 1 : 2;                      // bytes per element
-  static constexpr int K2 = H + KS;
+  static constexpr int K2 = H + KS;                          // layer 2: hidden + the bias K step
+  static constexpr int K3 = F8 ? K2 : H;                     // layer 3 (FP16/BF16: b3 added on read)
   static constexpr uint32_t kACol = H;                       // hidden A region starts after D
   static constexpr int kA1Words = K1 * EB / 4;               // 32-bit words of a layer-1 row
-  // The layer-1 tile has its own columns after the hidden A region, so the
-  // next tile's features can be written while this tile's layers 2 and 3 run.
-  static constexpr uint32_t kA1Col = kACol + K2 * EB / 4;
+  static constexpr uint32_t kA2End = kACol + K2 * EB / 4;   // end of the hidden A region
+  // Merged layout: D3 after the layer-3 A columns, the layer-1 rows after D3.
+  static constexpr uint32_t kD3Merged = (kACol + K3 * EB / 4 + 15) / 16 * 16;
+  static constexpr uint32_t kA1Merged = kD3Merged + 16 > kA2End ? kD3Merged + 16 : kA2End;
+  // Layer 3 is merged with the next tile's layer 1 only when that layout
+  // fits a quarter of the SM's tensor memory (the kernels run four slots per
+  // CTA); otherwise D3 goes to D's columns and the layer-1 rows follow the
+  // hidden A region.  Not merged: 32 inputs at H = 64.
+  static constexpr bool kMerge = kA1Merged + kA1Words <= 128;
+  static constexpr uint32_t kD3Col = kMerge ? kD3Merged : 0u;
+  static constexpr uint32_t kA1Col = kMerge ? kA1Merged : kA2End;
   static constexpr uint32_t kSlotCols = tmem_alloc_cols(kA1Col + kA1Words);
   static_assert(!F8 || H % 32 == 0, "FP8 epilogue works on 32-column chunks");
-  int wg, t;
+  int wg, t, it;         // lane, thread in lane, the lane's issuing thread
+  bool late;             // a wait of this thread timed out
   uint32_t tmem[SL];     // slot base, lane 0
   uint32_t lane_off;     // this warp's lane quadrant, in the TMEM address
   uint64_t* bar[SL];
   uint32_t phase[SL];
   uint64_t db1, db2, db3;
+  const float* b3;       // shared: stored b3 (FP16/BF16)
 
   template <int KSTEPS, int N>
-  __device__ __forceinline__ void issue(int s, uint32_t a_col, uint64_t b_desc) {
-    tc_fence_after();
+  __device__ __forceinline__ void mma(int s, uint32_t d_col, uint32_t a_col, uint64_t b_desc) {
 #pragma unroll
     for (int ks = 0; ks < KSTEPS; ++ks) {
       if constexpr (F8)
-        umma_f8_ts(tmem[s], tmem[s] + a_col + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, false),
+        umma_f8_ts(tmem[s] + d_col, tmem[s] + a_col + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, false),
                    ks > 0 ? 1u : 0u);
       else
-        umma_f16_ts(tmem[s], tmem[s] + a_col + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16),
+        umma_f16_ts(tmem[s] + d_col, tmem[s] + a_col + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16),
                     ks > 0 ? 1u : 0u);
     }
-    umma_commit(bar[s]);
   }
-  // Make this lane's tcgen05.st writes visible, then reach the lane barrier.
-  __device__ __forceinline__ void publish() {
+  // Make this lane's tcgen05.st writes visible and meet at the lane barrier;
+  // false (uniform over the lane) if any of its threads saw a wait time out.
+  __device__ __forceinline__ bool publish() {
     tmem_st_wait();
     tc_fence_before();
-    lane_sync(wg);
+    return !lane_any(wg, late);
   }
-  __device__ __forceinline__ void layer1(int s) {
-    publish();
-    if (t == 0) issue<K1 / KS, H>(s, kA1Col, db1);
-  }
-  __device__ __forceinline__ void layer2(int s) {
-    publish();
-    if (t == 0) issue<K2 / KS, H>(s, kACol, db2);
-  }
-  __device__ __forceinline__ void layer3(int s) {
-    publish();
-    if (t == 0) issue<K2 / KS, 16>(s, kACol, db3);
-  }
-  // Thread 0 waits for slot s's MMAs, the lane blocks in its barrier.  false
-  // (uniform) on timeout; the phase then keeps the parity still outstanding.
-  __device__ __forceinline__ bool wait(int s) {
-    bool ok = true;
-    if (t == 0) ok = mbar_wait(bar[s], phase[s]);
-    if (lane_any(wg, !ok)) return false;
-    phase[s] ^= 1u;
-    tc_fence_after();
+  __device__ __forceinline__ bool layer1(int s) {
+    if (!publish()) return false;
+    if (t == it) {
+      tc_fence_after();
+      mma<K1 / KS, H>(s, 0u, kA1Col, db1);
+      umma_commit(bar[s]);
+    }
     return true;
+  }
+  __device__ __forceinline__ bool layer2(int s) {
+    if (!publish()) return false;
+    if (t == it) {
+      tc_fence_after();
+      mma<K2 / KS, H>(s, 0u, kACol, db2);
+      umma_commit(bar[s]);
+    }
+    return true;
+  }
+  // Layer 3 of the slot's tile and, if `next` (lane-uniform; only with
+  // kMerge), layer 1 of the slot's next tile, whose rows are already in the
+  // layer-1 columns.
+  __device__ __forceinline__ bool layer3(int s, bool next) {
+    if (!publish()) return false;
+    if (t == it) {
+      tc_fence_after();
+      mma<K3 / KS, 16>(s, kD3Col, kACol, db3);
+      if (kMerge && next) mma<K1 / KS, H>(s, 0u, kA1Col, db1);
+      umma_commit(bar[s]);
+    }
+    return true;
+  }
+  // Waits (bounded) for slot s's MMAs; returns this thread's own result,
+  // which callers use for bookkeeping only (never to branch the lane).
+  __device__ __forceinline__ bool wait(int s) {
+    const bool ok = mbar_wait(bar[s], phase[s]);
+    if (ok) phase[s] ^= 1u;
+    late = late || !ok;
+    tc_fence_after();
+    return ok;
   }
   // Layer-1 row of this thread: kA1Words packed words (once the slot's
   // previous layer-1 MMA has completed).
@@ -455,8 +504,9 @@ struct Engine {
     }
   }
   // Slot s: this thread's row of D -> ReLU -> FP16/BF16/E4M3 -> the hidden A
-  // tile, then the bias ones columns (for FP8 `ones` holds the three codes of
-  // the next layer's ones value; FP16/BF16 use 1.0).
+  // tile; with ONES also the bias ones columns (for FP8 `ones` holds the
+  // three codes of the next layer's ones value; FP16/BF16 use 1.0).
+  template <bool ONES>
   __device__ __forceinline__ void epilogue(int s, uint32_t ones = 0u) {
     const uint32_t d = tmem[s] + lane_off, a = d + kACol;
     if constexpr (F8) {
@@ -471,8 +521,10 @@ struct Engine {
                  (e4m3x2_relu(__uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])) << 16);
         tmem_st8(a + c / 4, w);
       }
-      const uint32_t ow[8] = {ones, 0, 0, 0, 0, 0, 0, 0};
-      tmem_st8(a + H / 4, ow);
+      if constexpr (ONES) {
+        const uint32_t ow[8] = {ones, 0, 0, 0, 0, 0, 0, 0};
+        tmem_st8(a + H / 4, ow);
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < H; c += 32) {
@@ -494,19 +546,27 @@ struct Engine {
           tmem_st8(a + c / 2, w);
         }
       }
-      const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
-      const uint32_t ow[8] = {one, 0, 0, 0, 0, 0, 0, 0};
-      tmem_st8(a + H / 2, ow);
+      if constexpr (ONES) {
+        const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
+        const uint32_t ow[8] = {one, 0, 0, 0, 0, 0, 0, 0};
+        tmem_st8(a + H / 2, ow);
+      }
     }
   }
-  // Slot s after layer 3: this thread's RGB accumulator.
+  // Slot s after layer 3: this thread's RGB (FP16/BF16: + stored b3; E4M3:
+  // still in the output unit, the caller scales it).
   __device__ __forceinline__ void output(int s, float& y0, float& y1, float& y2) {
     uint32_t r[4];
-    tmem_ld4(tmem[s] + lane_off, r);
+    tmem_ld4(tmem[s] + lane_off + kD3Col, r);
     tmem_ld_wait();
     y0 = __uint_as_float(r[0]);
     y1 = __uint_as_float(r[1]);
     y2 = __uint_as_float(r[2]);
+    if constexpr (!F8) {
+      y0 += b3[0];
+      y1 += b3[1];
+      y2 += b3[2];
+    }
   }
 };
 
@@ -528,16 +588,16 @@ __device__ __forceinline__ uint32_t cta_setup(uint64_t* bars, uint32_t* slot, in
   return *slot;
 }
 
-// CTA end.  A lane whose wait timed out latches the error word and waits
-// (bounded) for the MMAs it still has in flight before the tensor memory is
-// freed.
+// CTA end.  A thread whose wait timed out latches the error word; the issuer
+// of each lane first waits (bounded) for the MMAs it has not seen complete,
+// so the tensor memory is freed with nothing in flight.
 template <int NSLOTS, int COLS, typename E, int SL>
 __device__ __forceinline__ void cta_teardown(uint32_t tbase, E& e, const bool (&inflight)[SL], bool timed_out,
                                              int tid) {
-  if (timed_out && e.t == 0) {
-    atomicOr(&g_tc_error, 1);
+  if (timed_out || e.late) atomicOr(&g_tc_error, 1);
+  if (e.t == e.it) {
     for (int s = 0; s < SL; ++s)
-      if (inflight[s]) mbar_wait(e.bar[s], e.phase[s]);
+      if (inflight[s] && !mbar_wait(e.bar[s], e.phase[s])) atomicOr(&g_tc_error, 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -559,6 +619,9 @@ __device__ __forceinline__ void engine_init(Engine<H, P, K1, SL>& e, uint32_t tb
   using E = Engine<H, P, K1, SL>;
   e.wg = tid >> 7;
   e.t = tid & (kLaneThreads - 1);
+  e.it = 32 * (e.wg & 3);
+  e.late = false;
+  e.b3 = nullptr;
   e.lane_off = (uint32_t)(((e.t >> 5) * 32) << 16);
 #pragma unroll
   for (int s = 0; s < SL; ++s) {
@@ -615,6 +678,8 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
   const uint2* lut = reinterpret_cast<const uint2*>(sm + S::kLut);
   init_p35_lut_sliced(reinterpret_cast<uint2*>(sm + S::kLut), tid);
   const uint8_t* sliced = ws + L::kSliceOff;
+  __shared__ float s_b3[3];
+  if (tid < 3) s_b3[tid] = stored_b3<BF16>(ws + L::kB3, tid, H, L::K2);
   const uint32_t tbase = cta_setup<SL * NWG, E::kSlotCols>(bars, &slot, tid);
   const uint32_t base = smem_addr(sm);
   E e;
@@ -641,72 +706,99 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, 
       nt[s] = __ldcs(uvt + 3 * q0 + 2);
     }
   }
-  // One tile in flight per lane, software-pipelined so that the next tile's
-  // gather runs while this tile's layers 2 and 3 are on the tensor core:
-  //   [layer-1 result -> ReLU -> layer 2] [gather the next tile into the
-  //   layer-1 columns] [layer-2 result -> layer 3 -> RGB out] [next layer 1]
+  // One tile in flight per lane, software-pipelined: the next tile's gather
+  // runs while this tile's layer 2 is on the tensor core, and its layer 1 is
+  // issued with this tile's layer 3 (two MMA round trips per tile):
+  //   [wait: layer 1 (+ previous layer 3)] [previous RGB out] [ReLU -> layer 2]
+  //   [gather the next tile] [wait: layer 2] [ReLU -> layer 3 + next layer 1]
   static_assert(SL == 1, "the point decode pipelines one tile per lane");
-  int64_t tile = lane_id, q_cur = -1;
-  bool have = false;   // a tile whose layer 1 has been issued
-  for (;;) {
-    if (have) {
-      if (!e.wait(0)) {
-        timed_out = true;
-        break;
-      }
-      inflight[0] = false;
-      e.epilogue(0);
-      e.layer2(0);
-      inflight[0] = true;
+  static_assert(SL * NWG * E::kSlotCols <= 512, "slots exceed the SM's tensor memory");
+  e.b3 = s_b3;
+  // Gathers tile `tl` into the slot's layer-1 columns (their previous MMA has completed).
+  auto produce = [&](int64_t tl) {
+    const int64_t q = tl * 128 + t, qn = q + qstep;
+    const float qu = nu[0], qv = nv[0], qt = nt[0];
+    if (qn < n) {
+      nu[0] = __ldcs(uvt + 3 * qn);
+      nv[0] = __ldcs(uvt + 3 * qn + 1);
+      nt[0] = __ldcs(uvt + 3 * qn + 2);
     }
-    const bool more = tile < tiles;
-    if (more) {   // the slot's layer-1 MMA has completed: its columns are free
-      const int64_t q = tile * 128 + t, qn = q + qstep;
-      const float qu = nu[0], qv = nv[0], qt = nt[0];
-      if (qn < n) {
-        nu[0] = __ldcs(uvt + 3 * qn);
-        nv[0] = __ldcs(uvt + 3 * qn + 1);
-        nt[0] = __ldcs(uvt + 3 * qn + 2);
-      }
-      float x[L::CIN];
-      if (q < n) {
-        gather_sliced<CS, CT>(m, sliced, qu, qv, qt, x, lut);
-      } else {
+    float x[L::CIN];
+    if (q < n) {
+      gather_sliced<CS, CT>(m, sliced, qu, qv, qt, x, lut);
+    } else {
 #pragma unroll
-        for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
-      }
-      uint32_t w[L::K1P / 2];
-      pack_a1<L::CIN, L::K1P, BF16>(x, w);
-      e.write_a1(0, w);
+      for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
     }
-    if (have) {
-      if (!e.wait(0)) {
+    uint32_t w[L::K1P / 2];
+    pack_a1<L::CIN, L::K1P, BF16>(x, w);
+    e.write_a1(0, w);
+  };
+  int64_t tile = lane_id;
+  if (tile < tiles) {
+    produce(tile);
+    e.layer1(0);   // no wait has run yet: cannot report a timeout
+    inflight[0] = true;
+    int64_t q_cur = tile * 128 + t, q_prev = -1;
+    tile += lanes;
+    for (;;) {
+      inflight[0] = !e.wait(0);   // layer 1 of q_cur (and layer 3 of q_prev)
+      if (q_prev >= 0) {   // false only on the first tile, for every thread (tcgen05.ld is warp-wide)
+        float y0, y1, y2;
+        e.output(0, y0, y1, y2);
+        if (q_prev < n) {
+          rgb[3 * q_prev] = y0;
+          rgb[3 * q_prev + 1] = y1;
+          rgb[3 * q_prev + 2] = y2;
+        }
+      }
+      e.template epilogue<true>(0);
+      if (!e.layer2(0)) {
         timed_out = true;
         break;
       }
-      inflight[0] = false;
-      e.epilogue(0);
-      e.layer3(0);
       inflight[0] = true;
-      if (!e.wait(0)) {
+      const bool more = tile < tiles;
+      if (more) produce(tile);
+      inflight[0] = !e.wait(0);   // layer 2
+      e.template epilogue<false>(0);
+      if (!e.layer3(0, more)) {
         timed_out = true;
         break;
       }
-      inflight[0] = false;
+      inflight[0] = true;
+      if constexpr (!E::kMerge) {   // layer 3 alone, then the next tile's layer 1
+        inflight[0] = !e.wait(0);
+        float y0, y1, y2;
+        e.output(0, y0, y1, y2);
+        if (q_cur < n) {
+          rgb[3 * q_cur] = y0;
+          rgb[3 * q_cur + 1] = y1;
+          rgb[3 * q_cur + 2] = y2;
+        }
+        if (!more) break;
+        if (!e.layer1(0)) {
+          timed_out = true;
+          break;
+        }
+        inflight[0] = true;
+      } else {
+        q_prev = q_cur;
+        if (!more) break;
+      }
+      q_cur = tile * 128 + t;
+      tile += lanes;
+    }
+    if (E::kMerge && !timed_out) {   // the last tile's layer 3
+      inflight[0] = !e.wait(0);
       float y0, y1, y2;
       e.output(0, y0, y1, y2);
-      if (q_cur < n) {
-        rgb[3 * q_cur] = y0;
-        rgb[3 * q_cur + 1] = y1;
-        rgb[3 * q_cur + 2] = y2;
+      if (q_prev < n) {
+        rgb[3 * q_prev] = y0;
+        rgb[3 * q_prev + 1] = y1;
+        rgb[3 * q_prev + 2] = y2;
       }
     }
-    if (!more) break;
-    e.layer1(0);
-    inflight[0] = true;
-    have = true;
-    q_cur = tile * 128 + t;
-    tile += lanes;
   }
   cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid);
 }
@@ -884,6 +976,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   constexpr bool BF16 = P == kBF16, F8 = P == kE4M3;
   constexpr int NW = E::kA1Words;
   static_assert(CS == 16, "the staged page path is built for 16 spatial channels");
+  static_assert(SL * NWG * E::kSlotCols <= 512, "slots exceed the SM's tensor memory");
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint64_t bars[SL * NWG];
   __shared__ uint32_t slot;
@@ -892,6 +985,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   __shared__ float s_vt[CT];
   __shared__ float s_beta[F8 ? H : 1];
   __shared__ uint32_t s_bmax, s_ones1;   // FP8: max |b1'/a2| of the request, its ones word
+  __shared__ float s_b3[3];              // FP16/BF16: stored b3 of the loaded model
   const Fp8Scales* sc = nullptr;
   if constexpr (F8) sc = reinterpret_cast<const Fp8Scales*>(sm + S::kB1 + (L::kScale - L::kB1G));
   constexpr int NT = kLaneThreads * NWG;
@@ -909,6 +1003,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   const uint32_t base = smem_addr(sm);
   E e;
   engine_init<H, P, L::K1G, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
+  e.b3 = s_b3;
   const int wg = e.wg, t = e.t;
   unsigned char* lb = sm + S::kLanes + wg * S::kLaneBytes;
   unsigned char* ring = lb + S::kRing;
@@ -948,6 +1043,9 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
       const unsigned char* w = static_cast<const unsigned char*>(c.ws[r.model]);
       copy16(sm + S::kW, w, L::kShared, tid, NT);
       copy16(sm + S::kB1, w + L::kB1G, S::kTail, tid, NT);
+      if constexpr (!F8) {
+        if (tid < 3) s_b3[tid] = stored_b3<BF16>(w + L::kB3, tid, H, L::K2);
+      }
       loaded = r.model;
     }
     if constexpr (F8) {
@@ -1038,205 +1136,159 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
 #pragma unroll
       for (int s = 0; s < SL; ++s) prev_row[s] = -1;
       const int ntiles = (qh + 1) / 2;
+      // Writes tile tl's layer-1 rows (two output rows of 64 texels) into
+      // slot s, decoding the feature rows they need into the ring first;
+      // returns this thread's output row.
+      auto produce = [&](int s, int tl) -> int {
+        const int row_base = 2 * tl;
+        if (staged) {   // feature rows needed by output rows row_base, row_base + 1
+          const int need_hi = rowtab[min(row_base + 1, qh - 1)].y;
+          if (need_hi > decoded_hi) {
+            const int from = max(decoded_hi + 1, rowtab[row_base].x);
+            const int to = min(need_hi + kDecodeAhead, fr_last);
+            decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
+                                   fc0, ncols, t, luts);
+            decoded_hi = to;
+            lane_sync(wg);
+          }
+        }
+        const int orow = row_base + (t >> 6);
+        uint32_t w[NW];
+        if (col < qw && orow < qh) {
+          if (staged) {
+            ring_texel<CS, P, NW>(w, ring, rowtab[orow], c0, c1, wx0, wx1);
+          } else {
+            float x[CS + CT];
+            gather_f32<CS, CT, false>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
+                                      ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr, lut);
+            if constexpr (F8) {
+#pragma unroll
+              for (int j = 0; j < CS / 4; ++j)
+                w[j] = e4m3x2(x[4 * j] * xs, x[4 * j + 1] * xs) | (e4m3x2(x[4 * j + 2] * xs, x[4 * j + 3] * xs) << 16);
+            } else {
+#pragma unroll
+              for (int j = 0; j < CS / 2; ++j) w[j] = pack2<BF16>(x[2 * j], x[2 * j + 1]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < CS * E::EB / 4; ++j) w[j] = 0u;
+        }
+        a1_bias_words<CS, P, NW>(w, F8 ? s_ones1 : 0u);
+        e.write_a1(s, w);
+        return orow;
+      };
+      // Reads slot s's RGB (every thread: tcgen05.ld is warp-wide) and stores
+      // the texel of output row orow.
+      auto store = [&](int s, int orow) {
+        float y0, y1, y2;
+        e.output(s, y0, y1, y2);
+        if constexpr (F8) {
+          const float so = sc->out;
+          y0 *= so;
+          y1 *= so;
+          y2 *= so;
+        }
+        if (col < qw && orow < qh) {
+          const int64_t o = (int64_t)(r.dst_y + oy + orow) * c.phys_w + (r.dst_x + ox + col);
+          if (c.out_format == NDGI_RGBA32F) {
+            reinterpret_cast<float4*>(c.phys)[o] = make_float4(y0, y1, y2, 1.0f);
+          } else {
+            reinterpret_cast<uint2*>(c.phys)[o] = make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f));
+          }
+        }
+      };
       if constexpr (SL == 1) {
+        static_assert(E::kMerge, "16 spatial channels: layer 3 always merges with the next layer 1");
         // One tile in flight per lane, software-pipelined: the next tile's
         // layer-1 rows are written (ring decode and blend) while this tile's
-        // layers 2 and 3 run.
-        int tile = 0, cur_row = -1;
-        bool have = false;   // a tile whose layer 1 has been issued
-        for (;;) {
-          if (have) {
-            if (!e.wait(0)) {
-              timed_out = true;
-              break;
-            }
-            inflight[0] = false;
-            e.epilogue(0, F8 ? sc->ones2 : 0u);
-            e.layer2(0);
-            inflight[0] = true;
-          }
-          const bool more = tile < ntiles;
-          int next_row = -1;
-          if (more) {   // the slot's layer-1 MMA has completed: its columns are free
-            const int row_base = 2 * tile;
-            if (staged) {   // feature rows needed by output rows row_base, row_base + 1
-              const int need_hi = rowtab[min(row_base + 1, qh - 1)].y;
-              if (need_hi > decoded_hi) {
-                const int from = max(decoded_hi + 1, rowtab[row_base].x);
-                const int to = min(need_hi + kDecodeAhead, fr_last);
-                decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
-                                       fc0, ncols, t, luts);
-                decoded_hi = to;
-                lane_sync(wg);
-              }
-            }
-            const int orow = row_base + (t >> 6);
-            uint32_t w[NW];
-            if (col < qw && orow < qh) {
-              if (staged) {
-                ring_texel<CS, P, NW>(w, ring, rowtab[orow], c0, c1, wx0, wx1);
-              } else {
-                float x[CS + CT];
-                gather_f32<CS, CT, false>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
-                                          ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr, lut);
-                if constexpr (F8) {
-#pragma unroll
-                  for (int j = 0; j < CS / 4; ++j)
-                    w[j] = e4m3x2(x[4 * j] * xs, x[4 * j + 1] * xs) |
-                           (e4m3x2(x[4 * j + 2] * xs, x[4 * j + 3] * xs) << 16);
-                } else {
-#pragma unroll
-                  for (int j = 0; j < CS / 2; ++j) w[j] = pack2<BF16>(x[2 * j], x[2 * j + 1]);
-                }
-              }
-            } else {
-#pragma unroll
-              for (int j = 0; j < CS * E::EB / 4; ++j) w[j] = 0u;
-            }
-            a1_bias_words<CS, P, NW>(w, F8 ? s_ones1 : 0u);
-            e.write_a1(0, w);
-            next_row = orow;
-          }
-          if (have) {
-            if (!e.wait(0)) {
-              timed_out = true;
-              break;
-            }
-            inflight[0] = false;
-            e.epilogue(0, F8 ? sc->ones3 : 0u);
-            e.layer3(0);
-            inflight[0] = true;
-            if (!e.wait(0)) {
-              timed_out = true;
-              break;
-            }
-            inflight[0] = false;
-            float y0, y1, y2;
-            e.output(0, y0, y1, y2);
-            if constexpr (F8) {
-              const float so = sc->out;
-              y0 *= so;
-              y1 *= so;
-              y2 *= so;
-            }
-            if (col < qw && cur_row < qh) {
-              const int64_t o = (int64_t)(r.dst_y + oy + cur_row) * c.phys_w + (r.dst_x + ox + col);
-              if (c.out_format == NDGI_RGBA32F) {
-                reinterpret_cast<float4*>(c.phys)[o] = make_float4(y0, y1, y2, 1.0f);
-              } else {
-                reinterpret_cast<uint2*>(c.phys)[o] = make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f));
-              }
-            }
-          }
-          if (!more) break;
-          e.layer1(0);
+        // layer 2 runs, and its layer 1 is issued with this tile's layer 3.
+        int cur_row = produce(0, 0), prev = -1;
+        bool pending = false;   // the previous tile's layer 3 was issued with this tile's layer 1
+        if (!e.layer1(0)) {
+          timed_out = true;
+        } else {
           inflight[0] = true;
-          have = true;
-          cur_row = next_row;
-          ++tile;
-        }
-        (void)prev_row;
-      } else {
-      const int ntiles = (qh + 1) / 2;
-      for (int round = 0; !timed_out; ++round) {
-        bool active[SL], any = false;
-#pragma unroll
-        for (int s = 0; s < SL; ++s) {
-          const int tile = SL * round + s;
-          active[s] = tile < ntiles;
-          any = any || active[s];
-          if (timed_out) continue;
-          if (need_out[s]) {   // finish this slot's previous tile
-            if (!e.wait(s)) {
+          for (int tile = 1;; ++tile) {
+            inflight[0] = !e.wait(0);   // layer 1 (+ the previous tile's layer 3)
+            if (pending) store(0, prev);
+            e.template epilogue<true>(0, F8 ? sc->ones2 : 0u);
+            if (!e.layer2(0)) {
               timed_out = true;
-              continue;
+              break;
             }
-            inflight[s] = need_out[s] = false;
-            float y0, y1, y2;
-            e.output(s, y0, y1, y2);
-            if constexpr (F8) {
-              const float so = sc->out;
-              y0 *= so;
-              y1 *= so;
-              y2 *= so;
+            inflight[0] = true;
+            const bool more = tile < ntiles;
+            const int next_row = more ? produce(0, tile) : -1;
+            inflight[0] = !e.wait(0);   // layer 2
+            e.template epilogue<F8>(0, F8 ? sc->ones3 : 0u);
+            if (!e.layer3(0, more)) {
+              timed_out = true;
+              break;
             }
-            const int orow = prev_row[s];
-            if (col < qw && orow < qh) {
-              const int64_t o = (int64_t)(r.dst_y + oy + orow) * c.phys_w + (r.dst_x + ox + col);
-              if (c.out_format == NDGI_RGBA32F) {
-                reinterpret_cast<float4*>(c.phys)[o] = make_float4(y0, y1, y2, 1.0f);
-              } else {
-                reinterpret_cast<uint2*>(c.phys)[o] = make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f));
-              }
-            }
+            inflight[0] = true;
+            prev = cur_row;
+            pending = true;
+            if (!more) break;
+            cur_row = next_row;
           }
-          if (!active[s]) continue;
-          const int row_base = 2 * tile;
-          if (staged) {   // feature rows needed by output rows row_base, row_base + 1
-            const int need_hi = rowtab[min(row_base + 1, qh - 1)].y;
-            if (need_hi > decoded_hi) {
-              const int from = max(decoded_hi + 1, rowtab[row_base].x);
-              const int to = min(need_hi + kDecodeAhead, fr_last);
-              decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
-                                     fc0, ncols, t, luts);
-              decoded_hi = to;
-              lane_sync(wg);
-            }
+          if (!timed_out) {   // the last tile's layer 3
+            inflight[0] = !e.wait(0);
+            store(0, prev);
           }
-          const int orow = row_base + (t >> 6);
-          uint32_t w[NW];
-          if (col < qw && orow < qh) {
-            if (staged) {
-              ring_texel<CS, P, NW>(w, ring, rowtab[orow], c0, c1, wx0, wx1);
-            } else {
-              float x[CS + CT];
-              gather_f32<CS, CT, false>(m, ((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w,
-                                        ((float)(r.y0 + oy + orow) + 0.5f) / (float)m.lm_h, r.t, x, nullptr, lut);
-              if constexpr (F8) {
-#pragma unroll
-                for (int j = 0; j < CS / 4; ++j)
-                  w[j] = e4m3x2(x[4 * j] * xs, x[4 * j + 1] * xs) | (e4m3x2(x[4 * j + 2] * xs, x[4 * j + 3] * xs) << 16);
-              } else {
-#pragma unroll
-                for (int j = 0; j < CS / 2; ++j) w[j] = pack2<BF16>(x[2 * j], x[2 * j + 1]);
-              }
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < CS * E::EB / 4; ++j) w[j] = 0u;
-          }
-          a1_bias_words<CS, P, NW>(w, F8 ? s_ones1 : 0u);
-          e.write_a1(s, w);
-          e.layer1(s);
-          inflight[s] = true;
-          prev_row[s] = orow;
         }
-        if (timed_out || !any) break;
-#pragma unroll
-        for (int layer = 2; layer <= 3; ++layer) {
+      } else {
+        // SL slots per lane in rounds: each round starts one tile per slot and
+        // runs the slots' layers interleaved.
+        for (int round = 0; !timed_out; ++round) {
+          bool active[SL], any = false;
 #pragma unroll
           for (int s = 0; s < SL; ++s) {
-            if (!active[s] || timed_out) continue;
-            if (!e.wait(s)) {
+            const int tile = SL * round + s;
+            active[s] = tile < ntiles;
+            any = any || active[s];
+            if (timed_out) continue;
+            if (need_out[s]) {   // finish this slot's previous tile
+              inflight[s] = !e.wait(s);
+              need_out[s] = false;
+              store(s, prev_row[s]);
+            }
+            if (!active[s]) continue;
+            prev_row[s] = produce(s, tile);
+            if (!e.layer1(s)) {
               timed_out = true;
               continue;
-            }
-            inflight[s] = false;
-            e.epilogue(s, F8 ? (layer == 2 ? sc->ones2 : sc->ones3) : 0u);
-            if (layer == 2) {
-              e.layer2(s);
-            } else {
-              e.layer3(s);
-              need_out[s] = true;
             }
             inflight[s] = true;
           }
+          if (timed_out || !any) break;
+#pragma unroll
+          for (int layer = 2; layer <= 3; ++layer) {
+#pragma unroll
+            for (int s = 0; s < SL; ++s) {
+              if (!active[s] || timed_out) continue;
+              inflight[s] = !e.wait(s);
+              bool ok;
+              if (layer == 2) {
+                e.template epilogue<true>(s, F8 ? sc->ones2 : 0u);
+                ok = e.layer2(s);
+              } else {
+                e.template epilogue<F8>(s, F8 ? sc->ones3 : 0u);
+                ok = e.layer3(s, false);
+              }
+              if (!ok) {
+                timed_out = true;
+                continue;
+              }
+              inflight[s] = true;
+              if (layer == 3) need_out[s] = true;
+            }
+          }
         }
-      }
       }
     }
     // every lane must be done with the weights and b1' before the next request
-    if (__syncthreads_or(timed_out)) break;
+    if (__syncthreads_or(timed_out || e.late)) break;
   }
   cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid);
 }
