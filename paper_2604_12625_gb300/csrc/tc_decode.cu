@@ -4,17 +4,23 @@
 // and activations (kind::f8f6f4).
 //
 // Structure.  A CTA holds NWG independent "lanes" (warpgroups of 4 warps).
-// A lane owns one 128-row MMA tile at a time: its 128 threads write the
-// tile's features (one row each) into a K-major shared-memory A tile, one
-// thread issues the layer's tcgen05.mma chain into the lane's 64 tensor-
-// memory columns and commits to the lane's mbarrier, and the 128 threads read
-// their rows back (tcgen05.ld), apply ReLU with the FP16/BF16 conversion in
-// one instruction, and write the next layer's A tile.  The MLP weights are
-// shared by the lanes; the lanes of a CTA interleave, so one lane's gather
-// and epilogues overlap the others' MMAs.
+// A lane owns one 128-row MMA tile at a time in a slot of tensor memory: its
+// 128 threads write the tile's layer-1 rows (one row each) into the slot's
+// columns with tcgen05.st, one thread issues the layer's tcgen05.mma chain
+// (A from tensor memory, the small weight tile B from shared memory) and
+// commits to the slot's mbarrier, and the 128 threads read their rows of the
+// FP32 accumulator back (tcgen05.ld), apply ReLU with the FP16/BF16
+// conversion in one instruction, and write the next layer's A rows.  Layer 3
+// of a tile is issued together with layer 1 of the lane's next tile, so a tile
+// costs two dependent MMA round trips.  The MLP weights are shared by the
+// lanes; the lanes of a CTA interleave, so one lane's gather and epilogues
+// overlap the others' MMAs.
 //
-// Biases never touch the CUDA cores: every A tile carries a ones column in
-// its K padding and the matching B row holds the bias, so the MMA adds it.
+// Biases ride in the MMA: an A tile carries a ones column in its K padding
+// and the matching B row holds the bias, so the MMA adds it.  The exception
+// is b3 of the FP16/BF16 paths (the same stored value), added in FP32 when the
+// layer-3 accumulator is read: it frees layer 3's last K step and the TMEM
+// columns that let layer 3 share a commit with the next layer 1.
 // For pages, t is constant per request, so the temporal part of layer 1 is
 // folded into a per-request bias b1' = b1 + W1_t v_t (FP32), stored in B1 as
 // a hi + lo pair of FP16/BF16 values against two ones columns; layer 1 then
