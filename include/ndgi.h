@@ -271,6 +271,11 @@ ndgi_status ndgi_pages_check(ndgi_pages_plan *plan, int32_t *device_error, void 
  * The plan's current launch shape (host int32[4]): precision, CTAs per SM,
  * warpgroup lanes per CTA, tiles in flight per lane (the last three describe
  * the tensor-core kernel; for NDGI_FP32 plans info[1] is the grid size).
+ * Built tensor-core shapes: 4 x 1 and 2 x 2 (every lane runs its own MMA
+ * chain and writes its own layer-1 rows), and 8 x 1, the warp-specialised
+ * kernel: four MMA lanes, each paired with a warpgroup that writes the
+ * layer-1 rows of the lane's next tile (plans whose features are at most
+ * half the lightmap resolution; other plans run 4 x 1 under that shape).
  */
 ndgi_status ndgi_pages_plan_info(const ndgi_pages_plan *plan, int32_t info[4]);
 

@@ -559,6 +559,26 @@ struct Engine {
       }
     }
   }
+  // The same in 16-column chunks (fewer live registers; FP16/BF16 only).
+  template <bool ONES>
+  __device__ __forceinline__ void epilogue16(int s) {
+    static_assert(!F8 && H % 16 == 0, "16-column FP16/BF16 epilogue");
+    const uint32_t d = tmem[s] + lane_off, a = d + kACol;
+#pragma unroll
+    for (int c = 0; c < H; c += 16) {
+      uint32_t r[16], w[8];
+      tmem_ld16(d + c, r);
+      tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+      tmem_st8(a + c / 2, w);
+    }
+    if constexpr (ONES) {
+      const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
+      const uint32_t ow[8] = {one, 0, 0, 0, 0, 0, 0, 0};
+      tmem_st8(a + H / 2, ow);
+    }
+  }
   // Slot s after layer 3: this thread's RGB (FP16/BF16: + stored b3; E4M3:
   // still in the output unit, the caller scales it).
   __device__ __forceinline__ void output(int s, float& y0, float& y1, float& y2) {
@@ -968,6 +988,121 @@ __device__ __forceinline__ void a1_bias_words(uint32_t (&w)[NW], uint32_t ones8)
   for (int j = first + 1; j < NW; ++j) w[j] = 0u;
 }
 
+// Shared-memory state of the request a page-decode CTA is working on.
+template <int CT, int H, bool F8>
+struct PageReqState {
+  int item;
+  PageItem req;
+  float vt[CT];
+  float beta[F8 ? H : 1];
+  uint32_t bmax, ones1;   // FP8: max |b1'/a2| of the request, its ones word
+  float b3[3];            // FP16/BF16: stored b3 of the loaded model
+};
+
+// The CTA takes its next request (all NT threads call this; it holds CTA
+// barriers): thread 0 pulls and validates it.  Returns -1 once the frame is
+// done, 0 for a rejected request (skip it), 1 to decode it; then the
+// request's model is in shared memory (swapped in if it changed) and its
+// folded layer-1 bias b1' sits in B1's bias columns.
+template <int CS, int CT, int H, int P, int NT, typename S>
+__device__ __forceinline__ int page_take_request(const PagesCtx& c, const ndgi_page_req* __restrict__ reqs, int n,
+                                                 int tid, unsigned char* sm, PageReqState<CT, H, P == kE4M3>& st,
+                                                 int& loaded, const Fp8Scales* sc) {
+  using L = PagesLayout<CS, CT, H, P>;
+  constexpr bool BF16 = P == kBF16, F8 = P == kE4M3;
+  (void)sc;
+  // ---- CTA: next request (the barrier keeps thread 0 from overwriting the
+  // shared request slot while a skipped request is still being read) ----
+  __syncthreads();
+  if (tid == 0) {
+    const int item = (int)atomicAdd(c.work_counter, 1u);
+    st.item = item;
+    if (item < n) {
+      const ndgi_page_req r = reqs[item];
+      st.req.r = r;
+      int ok = r.model >= 0 && r.model < c.n_models && r.w >= 1 && r.w <= 128 && r.h >= 1 && r.h <= 128;
+      if (!ok) atomicOr(c.error_word, 2);
+      if (ok) {
+        const DevModel& mm = c.models[r.model];
+        ok = r.x0 >= 0 && r.y0 >= 0 && (int64_t)r.x0 + r.w <= mm.lm_w && (int64_t)r.y0 + r.h <= mm.lm_h &&
+             r.dst_x >= 0 && r.dst_y >= 0 && (int64_t)r.dst_x + r.w <= c.phys_w &&
+             (int64_t)r.dst_y + r.h <= c.phys_h;
+        if (!ok) atomicOr(c.error_word, 4);
+      }
+      st.req.valid = ok;
+    }
+  }
+  __syncthreads();
+  if (st.item >= n) return -1;
+  if (!st.req.valid) return 0;
+  const ndgi_page_req r = st.req.r;
+  const DevModel& m = c.models[r.model];
+  if (r.model != loaded) {   // swap in this model's weights (no MMA is in flight here)
+    const unsigned char* w = static_cast<const unsigned char*>(c.ws[r.model]);
+    copy16(sm + S::kW, w, L::kShared, tid, NT);
+    copy16(sm + S::kB1, w + L::kB1G, S::kTail, tid, NT);
+    if constexpr (!F8) {
+      if (tid < 3) st.b3[tid] = stored_b3<BF16>(w + L::kB3, tid, H, L::K2);
+    }
+    loaded = r.model;
+  }
+  if constexpr (F8) {
+    if (tid == 0) st.bmax = 0u;
+    __syncthreads();   // the scales are read below
+  }
+  // temporal line at this request's t (FP8: quantised like any layer-1 input)
+  if (tid < CT) {
+    int j0, j1;
+    float a;
+    temporal_setup(r.t, m.t_count, j0, j1, a);
+    float vt = (1.0f - a) * load_temporal(m.temporal, m.temporal_f16, j0 * CT + tid) +
+               a * load_temporal(m.temporal, m.temporal_f16, j1 * CT + tid);
+    if constexpr (F8) vt = sc->a1 * e4m3_value(e4m3x2(vt * sc->inv_a1, 0.0f) & 0xFFu);
+    st.vt[tid] = vt;
+  }
+  __syncthreads();
+  if constexpr (F8) {
+    // folded layer-1 bias b1' = b1 + W1_t vq (FP32) in units a2, stored in
+    // B1's columns CS..CS+2 as three E4M3 terms against ones value v1 =
+    // max(1, p2(max |b1'/a2|)) (one per request)
+    if (tid < H) {
+      const float* w1t = reinterpret_cast<const float*>(sm + S::kW1T);
+      float b = reinterpret_cast<const float*>(sm + S::kBias1)[tid];
+#pragma unroll
+      for (int cc = 0; cc < CT; ++cc) b = fmaf(w1t[cc * H + tid], st.vt[cc], b);
+      const float beta = b * sc->inv_a2;
+      st.beta[tid] = beta;
+      atomicMax(&st.bmax, __float_as_uint(fabsf(beta)));
+    }
+    __syncthreads();
+    if (tid < H) {
+      const float v1 = fmaxf(1.0f, fp8_p2(__uint_as_float(st.bmax)));
+      *reinterpret_cast<uint32_t*>(sm + S::kB1 + kmajor_offset8(tid, CS, L::K1G)) = fp8_terms(st.beta[tid], v1);
+      if (tid == 0) {
+        const uint32_t oc = e4m3_pow2_code(fminf(v1, 256.0f));
+        st.ones1 = oc | (oc << 8) | (oc << 16);
+        if (v1 > 256.0f) atomicOr(c.error_word, 8);
+      }
+    }
+  } else if (tid < H) {
+    // folded layer-1 bias b1' = b1 + W1_t v_t (FP32), stored in B1's columns
+    // CS and CS+1 as a hi + lo pair so the MMA adds it at FP32 accuracy
+    const float* w1t = reinterpret_cast<const float*>(sm + S::kW1T);
+    float b = reinterpret_cast<const float*>(sm + S::kBias1)[tid];
+#pragma unroll
+    for (int cc = 0; cc < CT; ++cc) b = fmaf(w1t[cc * H + tid], st.vt[cc], b);
+    const uint16_t hi = to_bits<BF16>(b);
+    const float hif =
+        BF16 ? __uint_as_float((uint32_t)hi << 16) : __half2float(*reinterpret_cast<const __half*>(&hi));
+    const uint16_t lo = to_bits<BF16>(b - hif);
+    *reinterpret_cast<uint32_t*>(sm + S::kB1 + kmajor_offset(tid, CS, L::K1G)) =
+        (uint32_t)hi | ((uint32_t)lo << 16);
+  }
+  fence_async_smem();   // weights and b1' are read by the tensor core
+  __syncthreads();
+  return 1;
+}
+
 // staged (host-side plan flag): features are at most half the lightmap
 // resolution in every model of the plan, so each quadrant's feature rows are
 // decoded once into the ring; otherwise each texel gathers its taps directly
@@ -986,12 +1121,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint64_t bars[SL * NWG];
   __shared__ uint32_t slot;
-  __shared__ int s_item;
-  __shared__ PageItem s_req;
-  __shared__ float s_vt[CT];
-  __shared__ float s_beta[F8 ? H : 1];
-  __shared__ uint32_t s_bmax, s_ones1;   // FP8: max |b1'/a2| of the request, its ones word
-  __shared__ float s_b3[3];              // FP16/BF16: stored b3 of the loaded model
+  __shared__ PageReqState<CT, H, F8> st;
   const Fp8Scales* sc = nullptr;
   if constexpr (F8) sc = reinterpret_cast<const Fp8Scales*>(sm + S::kB1 + (L::kScale - L::kB1G));
   constexpr int NT = kLaneThreads * NWG;
@@ -1009,7 +1139,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   const uint32_t base = smem_addr(sm);
   E e;
   engine_init<H, P, L::K1G, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
-  e.b3 = s_b3;
+  e.b3 = st.b3;
   const int wg = e.wg, t = e.t;
   unsigned char* lb = sm + S::kLanes + wg * S::kLaneBytes;
   unsigned char* ring = lb + S::kRing;
@@ -1019,95 +1149,11 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
 #pragma unroll
   for (int s = 0; s < SL; ++s) inflight[s] = need_out[s] = false;
   for (;;) {
-    // ---- CTA: next request (the barrier keeps thread 0 from overwriting the
-    // shared request slot while a skipped request is still being read) ----
-    __syncthreads();
-    if (tid == 0) {
-      const int item = (int)atomicAdd(c.work_counter, 1u);
-      s_item = item;
-      if (item < n) {
-        const ndgi_page_req r = reqs[item];
-        s_req.r = r;
-        int ok = r.model >= 0 && r.model < c.n_models && r.w >= 1 && r.w <= 128 && r.h >= 1 && r.h <= 128;
-        if (!ok) atomicOr(c.error_word, 2);
-        if (ok) {
-          const DevModel& mm = c.models[r.model];
-          ok = r.x0 >= 0 && r.y0 >= 0 && (int64_t)r.x0 + r.w <= mm.lm_w && (int64_t)r.y0 + r.h <= mm.lm_h &&
-               r.dst_x >= 0 && r.dst_y >= 0 && (int64_t)r.dst_x + r.w <= c.phys_w &&
-               (int64_t)r.dst_y + r.h <= c.phys_h;
-          if (!ok) atomicOr(c.error_word, 4);
-        }
-        s_req.valid = ok;
-      }
-    }
-    __syncthreads();
-    if (s_item >= n) break;
-    if (!s_req.valid) continue;
-    const ndgi_page_req r = s_req.r;
+    const int take = page_take_request<CS, CT, H, P, NT, S>(c, reqs, n, tid, sm, st, loaded, sc);
+    if (take < 0) break;
+    if (take == 0) continue;
+    const ndgi_page_req r = st.req.r;
     const DevModel& m = c.models[r.model];
-    if (r.model != loaded) {   // swap in this model's weights (no MMA is in flight here)
-      const unsigned char* w = static_cast<const unsigned char*>(c.ws[r.model]);
-      copy16(sm + S::kW, w, L::kShared, tid, NT);
-      copy16(sm + S::kB1, w + L::kB1G, S::kTail, tid, NT);
-      if constexpr (!F8) {
-        if (tid < 3) s_b3[tid] = stored_b3<BF16>(w + L::kB3, tid, H, L::K2);
-      }
-      loaded = r.model;
-    }
-    if constexpr (F8) {
-      if (tid == 0) s_bmax = 0u;
-      __syncthreads();   // the scales are read below
-    }
-    // temporal line at this request's t (FP8: quantised like any layer-1 input)
-    if (tid < CT) {
-      int j0, j1;
-      float a;
-      temporal_setup(r.t, m.t_count, j0, j1, a);
-      float vt = (1.0f - a) * load_temporal(m.temporal, m.temporal_f16, j0 * CT + tid) +
-                 a * load_temporal(m.temporal, m.temporal_f16, j1 * CT + tid);
-      if constexpr (F8) vt = sc->a1 * e4m3_value(e4m3x2(vt * sc->inv_a1, 0.0f) & 0xFFu);
-      s_vt[tid] = vt;
-    }
-    __syncthreads();
-    if constexpr (F8) {
-      // folded layer-1 bias b1' = b1 + W1_t vq (FP32) in units a2, stored in
-      // B1's columns CS..CS+2 as three E4M3 terms against ones value v1 =
-      // max(1, p2(max |b1'/a2|)) (one per request)
-      if (tid < H) {
-        const float* w1t = reinterpret_cast<const float*>(sm + S::kW1T);
-        float b = reinterpret_cast<const float*>(sm + S::kBias1)[tid];
-#pragma unroll
-        for (int cc = 0; cc < CT; ++cc) b = fmaf(w1t[cc * H + tid], s_vt[cc], b);
-        const float beta = b * sc->inv_a2;
-        s_beta[tid] = beta;
-        atomicMax(&s_bmax, __float_as_uint(fabsf(beta)));
-      }
-      __syncthreads();
-      if (tid < H) {
-        const float v1 = fmaxf(1.0f, fp8_p2(__uint_as_float(s_bmax)));
-        *reinterpret_cast<uint32_t*>(sm + S::kB1 + kmajor_offset8(tid, CS, L::K1G)) = fp8_terms(s_beta[tid], v1);
-        if (tid == 0) {
-          const uint32_t oc = e4m3_pow2_code(fminf(v1, 256.0f));
-          s_ones1 = oc | (oc << 8) | (oc << 16);
-          if (v1 > 256.0f) atomicOr(c.error_word, 8);
-        }
-      }
-    } else if (tid < H) {
-      // folded layer-1 bias b1' = b1 + W1_t v_t (FP32), stored in B1's columns
-      // CS and CS+1 as a hi + lo pair so the MMA adds it at FP32 accuracy
-      const float* w1t = reinterpret_cast<const float*>(sm + S::kW1T);
-      float b = reinterpret_cast<const float*>(sm + S::kBias1)[tid];
-#pragma unroll
-      for (int cc = 0; cc < CT; ++cc) b = fmaf(w1t[cc * H + tid], s_vt[cc], b);
-      const uint16_t hi = to_bits<BF16>(b);
-      const float hif =
-          BF16 ? __uint_as_float((uint32_t)hi << 16) : __half2float(*reinterpret_cast<const __half*>(&hi));
-      const uint16_t lo = to_bits<BF16>(b - hif);
-      *reinterpret_cast<uint32_t*>(sm + S::kB1 + kmajor_offset(tid, CS, L::K1G)) =
-          (uint32_t)hi | ((uint32_t)lo << 16);
-    }
-    fence_async_smem();   // weights and b1' are read by the tensor core
-    __syncthreads();
     // ---- lane: 64 x 64 quadrants of the request; a tile = 64 columns x 2 rows ----
     for (int quad = wg; quad < 4 && !timed_out; quad += NWG) {
       const int ox = (quad & 1) * kQuad, oy = (quad >> 1) * kQuad;
@@ -1180,7 +1226,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
 #pragma unroll
           for (int j = 0; j < CS * E::EB / 4; ++j) w[j] = 0u;
         }
-        a1_bias_words<CS, P, NW>(w, F8 ? s_ones1 : 0u);
+        a1_bias_words<CS, P, NW>(w, F8 ? st.ones1 : 0u);
         e.write_a1(s, w);
         return orow;
       };
@@ -1297,6 +1343,268 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
     if (__syncthreads_or(timed_out || e.late)) break;
   }
   cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised page decode.  Each of the CTA's four lanes (one 64 x 64
+// quadrant of the request, one tensor-memory slot) has two warpgroups:
+//   consumer  runs the MMA chain and the epilogues: [layer 3 of the previous
+//             tile + layer 1] -> RGB out, ReLU -> [layer 2] -> ReLU -> A3;
+//   producer  writes the layer-1 rows of the lane's next tile (ring decode,
+//             half2 blend, tcgen05.st) as soon as the slot's previous layer 1
+//             has completed, so the feature work leaves the consumer's
+//             critical path and the SM has eight warps per sub-partition.
+// Warp w of either warpgroup reaches the same TMEM lane quarter (w mod 4),
+// so both address the slot's rows alike.  The two meet at a named barrier
+// per tile (the producer arrives, the consumer waits); the producer learns
+// that the layer-1 columns are free from the slot's layer-1 mbarrier.
+// Waits are bounded and never leave the loop: a wait that gives up sets a
+// CTA abort flag, after which every wait returns at once and no more MMAs
+// are issued, so every named barrier still sees all its threads and the CTA
+// drains quickly with the error latched.
+// ---------------------------------------------------------------------------
+constexpr int kWsLanes = 4;
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// Bounded wait that gives up at once when the CTA has aborted; false if it
+// did not see the phase complete.
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t& phase, volatile int* abort) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, phase)) {
+      phase ^= 1u;
+      tc_fence_after();
+      return true;
+    }
+    if (*abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+template <int CS, int CT, int H, int P>
+__global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
+    k_pages_ws(PagesCtx c, const ndgi_page_req* __restrict__ reqs, const int32_t* __restrict__ n_dev) {
+  constexpr int NL = kWsLanes;
+  using L = PagesLayout<CS, CT, H, P>;
+  using S = PagesSmem<CS, CT, H, NL, P>;
+  using E = Engine<H, P, L::K1G, 1>;
+  constexpr bool BF16 = P == kBF16, F8 = P == kE4M3;
+  constexpr int NW = E::kA1Words;
+  constexpr int NT = 2 * kLaneThreads * NL;
+  static_assert(CS == 16, "the staged page path is built for 16 spatial channels");
+  static_assert(E::kMerge && NL * E::kSlotCols <= 512, "one merged slot per lane");
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t bar1[NL], bar2[NL];   // per lane: layer-1 (+ layer-3) and layer-2 completion
+  __shared__ uint32_t slot;
+  __shared__ int s_abort;
+  __shared__ PageReqState<CT, H, F8> st;
+  const Fp8Scales* sc = nullptr;
+  if constexpr (F8) sc = reinterpret_cast<const Fp8Scales*>(sm + S::kB1 + (L::kScale - L::kB1G));
+  const int tid = threadIdx.x, wg = tid >> 7, lane = wg & (NL - 1), t = tid & (kLaneThreads - 1);
+  const bool producer = wg >= NL;
+  // named barriers: 1 + lane ready (256), 5 + lane consumer (128), 9 + lane producer (128)
+  const int bar_ready = 1 + lane, bar_cons = 1 + NL + lane, bar_prod = 1 + 2 * NL + lane;
+  int n = *n_dev;
+  if (n > c.max_reqs || n < 0) {   // reject the whole frame: the request buffer may be shorter
+    if (blockIdx.x == 0 && tid == 0) atomicOr(c.error_word, 1);
+    n = 0;
+  }
+  const uint2* luts = reinterpret_cast<const uint2*>(sm + S::kLutS);
+  if (tid < 16) init_p35_lut_sliced(reinterpret_cast<uint2*>(sm + S::kLutS), tid);
+  if ((tid >> 5) == 0) {
+    tmem_alloc(&slot, tmem_alloc_cols(NL * E::kSlotCols));
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < NL; ++i) {
+      mbar_init(&bar1[i], 1);
+      mbar_init(&bar2[i], 1);
+    }
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = slot, base = smem_addr(sm);
+  volatile int* abort = &s_abort;
+  E e;   // this lane's slot, seen from either warpgroup
+  e.wg = lane;
+  e.t = t;
+  e.it = 32 * lane;
+  e.late = false;
+  e.b3 = st.b3;
+  e.lane_off = (uint32_t)(((t >> 5) * 32) << 16);
+  e.tmem[0] = tbase + (uint32_t)(lane * E::kSlotCols);
+  e.bar[0] = &bar1[lane];
+  e.phase[0] = 0;
+  e.db1 = sdesc(base + S::kB1, 128u, L::K1G * E::EB * 8u);
+  e.db2 = sdesc(base + S::kW + L::kB2, 128u, E::K2 * E::EB * 8u);
+  e.db3 = sdesc(base + S::kW + L::kB3, 128u, E::K2 * E::EB * 8u);
+  const bool issuer = !producer && t == e.it;
+  uint32_t ph1 = 0, ph2 = 0;   // parity of the next bar1 / bar2 phase this thread waits for
+  bool out1 = false, out2 = false;   // issuer: a commit whose completion it has not seen
+  unsigned char* lb = sm + S::kLanes + lane * S::kLaneBytes;
+  unsigned char* ring = lb + S::kRing;
+  int4* rowtab = reinterpret_cast<int4*>(lb + S::kRowTab);
+  int loaded = -1;
+  for (;;) {
+    const int take = page_take_request<CS, CT, H, P, NT, S>(c, reqs, n, tid, sm, st, loaded, sc);
+    if (take < 0) break;
+    if (take == 0) continue;
+    const ndgi_page_req r = st.req.r;
+    const DevModel& m = c.models[r.model];
+    const int ox = (lane & 1) * kQuad, oy = (lane >> 1) * kQuad;
+    const int qw = min(kQuad, r.w - ox), qh = min(kQuad, r.h - oy);
+    const int col = t & (kQuad - 1);
+    if (qw > 0 && qh > 0) {   // uniform over the lane's two warpgroups
+      const int ntiles = (qh + 1) / 2;
+      if (producer) {
+        // ---- producer: the layer-1 rows of every tile of the quadrant ----
+        int cx0, cx1;
+        float fx;
+        axis_setup(((float)(r.x0 + ox + col) + 0.5f) / (float)m.lm_w, m.feat_w, m.address_mode, cx0, cx1, fx);
+        int fa0, fa1, fb0, fb1;
+        float fdum;
+        axis_setup(((float)(r.x0 + ox) + 0.5f) / (float)m.lm_w, m.feat_w, m.address_mode, fa0, fa1, fdum);
+        axis_setup(((float)(r.x0 + ox + qw - 1) + 0.5f) / (float)m.lm_w, m.feat_w, m.address_mode, fb0, fb1, fdum);
+        const int fc0 = min(min(fa0, fa1), min(fb0, fb1));
+        const int ncols = max(max(fa0, fa1), max(fb0, fb1)) - fc0 + 1;
+        if (t < qh) {
+          int ry0, ry1;
+          float fy;
+          axis_setup(((float)(r.y0 + oy + t) + 0.5f) / (float)m.lm_h, m.feat_h, m.address_mode, ry0, ry1, fy);
+          rowtab[t] = make_int4(ry0, ry1, __float_as_int(fy), 0);
+        }
+        named_sync(bar_prod, kLaneThreads);
+        const int fr_last = rowtab[qh - 1].y;
+        const float xs = F8 ? sc->inv_a1 : 1.0f;   // FP8: the blend lands in units a1
+        const __half2 wx1 = __float2half2_rn(fx * xs), wx0 = __float2half2_rn((1.0f - fx) * xs);
+        const int c0 = (cx0 - fc0) * 16, c1 = (cx1 - fc0) * 16;
+        int decoded_hi = -1000000;
+        for (int tile = 0; tile < ntiles; ++tile) {
+          // the slot's layer-1 columns are free once the previous tile's layer 1 has completed
+          if (tile > 0) ws_wait(&bar1[lane], ph1, abort);
+          const int row_base = 2 * tile;
+          const int need_hi = rowtab[min(row_base + 1, qh - 1)].y;   // feature rows of output rows row_base, +1
+          if (need_hi > decoded_hi) {
+            const int from = max(decoded_hi + 1, rowtab[row_base].x);
+            const int to = min(need_hi + kDecodeAhead, fr_last);
+            decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
+                                   fc0, ncols, t, luts);
+            decoded_hi = to;
+            named_sync(bar_prod, kLaneThreads);
+          }
+          const int orow = row_base + (t >> 6);
+          uint32_t w[NW];
+          if (col < qw && orow < qh) {
+            ring_texel<CS, P, NW>(w, ring, rowtab[orow], c0, c1, wx0, wx1);
+          } else {
+#pragma unroll
+            for (int j = 0; j < CS * E::EB / 4; ++j) w[j] = 0u;
+          }
+          a1_bias_words<CS, P, NW>(w, F8 ? st.ones1 : 0u);
+          e.write_a1(0, w);
+          tmem_st_wait();
+          tc_fence_before();
+          named_arrive(bar_ready, 2 * kLaneThreads);
+        }
+        // bar1 completes ntiles + 1 phases per quadrant (the last one carries
+        // the last tile's layer 3 alone); the producer waited ntiles - 1 of
+        // them, and the consumer has seen the other two complete before the
+        // CTA barrier that ends the request, so the parity skips both.
+      } else {
+        // ---- consumer: the MMA chain and the epilogues ----
+        auto put = [&](int orow, float y0, float y1, float y2) {
+          if constexpr (F8) {
+            const float so = sc->out;
+            y0 *= so;
+            y1 *= so;
+            y2 *= so;
+          }
+          if (col < qw && orow < qh) {
+            const int64_t o = (int64_t)(r.dst_y + oy + orow) * c.phys_w + (r.dst_x + ox + col);
+            if (c.out_format == NDGI_RGBA32F) {
+              reinterpret_cast<float4*>(c.phys)[o] = make_float4(y0, y1, y2, 1.0f);
+            } else {
+              reinterpret_cast<uint2*>(c.phys)[o] = make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f));
+            }
+          }
+        };
+        int prev_row = 0;
+        for (int tile = 0; tile < ntiles; ++tile) {
+          // this lane's layer-3 rows (previous tile) and the producer's layer-1 rows are written
+          tmem_st_wait();
+          tc_fence_before();
+          named_sync(bar_ready, 2 * kLaneThreads);
+          if (issuer && !*abort) {
+            tc_fence_after();
+            if (tile > 0) e.template mma<E::K3 / E::KS, 16>(0, E::kD3Col, E::kACol, e.db3);
+            e.template mma<L::K1G / E::KS, H>(0, 0u, E::kA1Col, e.db1);
+            umma_commit(&bar1[lane]);
+            out1 = true;
+          }
+          if (ws_wait(&bar1[lane], ph1, abort) && issuer) out1 = false;
+          if (tile > 0) {   // the previous tile's RGB leaves tensor memory before the layer-2 rows overwrite it
+            float y0, y1, y2;
+            e.output(0, y0, y1, y2);
+            put(prev_row, y0, y1, y2);
+          }
+          if constexpr (F8) e.template epilogue<true>(0, sc->ones2);
+          else e.template epilogue16<true>(0);
+          tmem_st_wait();
+          tc_fence_before();
+          named_sync(bar_cons, kLaneThreads);
+          if (issuer && !*abort) {
+            tc_fence_after();
+            e.template mma<E::K2 / E::KS, H>(0, 0u, E::kACol, e.db2);
+            umma_commit(&bar2[lane]);
+            out2 = true;
+          }
+          if (ws_wait(&bar2[lane], ph2, abort) && issuer) out2 = false;
+          if constexpr (F8) e.template epilogue<true>(0, sc->ones3);
+          else e.template epilogue16<false>(0);
+          prev_row = 2 * tile + (t >> 6);
+        }
+        // the last tile's layer 3 alone
+        tmem_st_wait();
+        tc_fence_before();
+        named_sync(bar_cons, kLaneThreads);
+        if (issuer && !*abort) {
+          tc_fence_after();
+          e.template mma<E::K3 / E::KS, 16>(0, E::kD3Col, E::kACol, e.db3);
+          umma_commit(&bar1[lane]);
+          out1 = true;
+        }
+        if (ws_wait(&bar1[lane], ph1, abort) && issuer) out1 = false;
+        float y0, y1, y2;
+        e.output(0, y0, y1, y2);
+        put(prev_row, y0, y1, y2);
+      }
+    }
+    // every lane is done with the weights and b1' before the next request
+    __syncthreads();
+    if (*abort) break;
+  }
+  // teardown: an issuer that gave up waiting waits (bounded) for its MMAs
+  // before the tensor memory is freed
+  if (issuer) {
+    if (out1 && !mbar_wait(&bar1[lane], ph1)) atomicOr(&g_tc_error, 1);
+    if (out2 && !mbar_wait(&bar2[lane], ph2)) atomicOr(&g_tc_error, 1);
+  }
+  if (tid == 0 && *abort) atomicOr(&g_tc_error, 1);
+  tc_fence_before();
+  __syncthreads();
+  if ((tid >> 5) == 0) {
+    tc_fence_after();
+    tmem_dealloc(tbase, tmem_alloc_cols(NL * E::kSlotCols));
+  }
 }
 
 // The tensor-core point decode's feature gather alone (on the texel-sliced
@@ -1425,11 +1733,43 @@ static cudaError_t launch_pages_shape(const PagesCtx& c, int prec, bool staged, 
   return cudaErrorInvalidValue;
 }
 
+template <int CS, int CT, int H, int P>
+static cudaError_t launch_pages_ws_kind(const PagesCtx& c, const ndgi_page_req* reqs,
+                                        const int32_t* n_dev, cudaStream_t s, int grid) {
+  using S = PagesSmem<CS, CT, H, kWsLanes, P>;
+  auto kern = k_pages_ws<CS, CT, H, P>;
+  cudaError_t e = set_smem(kern, tc_smem(S::kBytes));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 2 * kLaneThreads * kWsLanes, tc_smem(S::kBytes), s>>>(c, reqs, n_dev);
+  return cudaGetLastError();
+}
+
+template <int CS, int CT, int H>
+static cudaError_t launch_pages_ws(const PagesCtx& c, int prec, const ndgi_page_req* reqs,
+                                   const int32_t* n_dev, cudaStream_t s, int grid) {
+  if (prec == kF16) return launch_pages_ws_kind<CS, CT, H, kF16>(c, reqs, n_dev, s, grid);
+  if (prec == kBF16) return launch_pages_ws_kind<CS, CT, H, kBF16>(c, reqs, n_dev, s, grid);
+  if constexpr (H % 32 == 0) {
+    if (prec == kE4M3) return launch_pages_ws_kind<CS, CT, H, kE4M3>(c, reqs, n_dev, s, grid);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_tc_pages(const PagesCtx& c, int prec, int cs, int ct, int hidden, const TcPagesShape& shape,
                             bool staged, const ndgi_page_req* reqs, const int32_t* n_dev, cudaStream_t s) {
   const int grid = num_sms() * shape.ctas_per_sm;
+  // warp-specialised: 4 lanes, each with a producer; its ring needs features
+  // at most half the lightmap resolution (otherwise the 4 x 1 shape runs)
+  if (shape.lanes == 2 * kWsLanes && shape.slots == 1 && staged) {
+#define X(A, B, C) \
+  if (cs == A && ct == B && hidden == C) return launch_pages_ws<A, B, C>(c, prec, reqs, n_dev, s, grid);
+    X(16, 8, 16) X(16, 8, 32) X(16, 8, 64) X(16, 16, 64)
+#undef X
+    return cudaErrorInvalidValue;
+  }
+  const TcPagesShape sh = shape.lanes == 2 * kWsLanes ? TcPagesShape{shape.ctas_per_sm, 4, 1} : shape;
 #define X(A, B, C, NW, SL)                                                                           \
-  if (cs == A && ct == B && hidden == C && shape.lanes == NW && shape.slots == SL)                   \
+  if (cs == A && ct == B && hidden == C && sh.lanes == NW && sh.slots == SL)                         \
     return launch_pages_shape<A, B, C, NW, SL>(c, prec, staged, reqs, n_dev, s, grid);
   X(16, 8, 16, 4, 1) X(16, 8, 32, 4, 1) X(16, 8, 64, 4, 1) X(16, 16, 64, 4, 1)
   X(16, 8, 16, 2, 2) X(16, 8, 32, 2, 2) X(16, 8, 64, 2, 2) X(16, 16, 64, 2, 2)
@@ -1555,7 +1895,9 @@ uint32_t tc_fp8_status_offset(int cs, int ct, int hidden) {
 
 TcPagesShape tc_default_pages_shape() { return TcPagesShape{1, 4, 1}; }
 
-std::vector<TcPagesShape> tc_pages_candidates(int) { return {TcPagesShape{1, 4, 1}, TcPagesShape{1, 2, 2}}; }
+std::vector<TcPagesShape> tc_pages_candidates(int) {
+  return {TcPagesShape{1, 4, 1}, TcPagesShape{1, 2, 2}, TcPagesShape{1, 2 * kWsLanes, 1}};
+}
 
 int tc_take_error() {
   int h = 0;

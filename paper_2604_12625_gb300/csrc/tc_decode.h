@@ -10,7 +10,8 @@ namespace ndgi {
 struct TcPagesShape {
   int ctas_per_sm;     // CTAs per SM in the persistent grid
   int lanes;           // warpgroup lanes per CTA; the lanes split a request's 64x64 quadrants
-  int slots;           // 128-row tiles in flight per lane (lanes x slots <= 4: tensor-memory bound)
+                       // (8: four MMA lanes, each with a producer warpgroup for its layer-1 rows)
+  int slots;           // 128-row tiles in flight per lane (at most 4 per CTA: tensor-memory bound)
 };
 
 bool tc_supported(int cs, int ct, int hidden);

@@ -109,6 +109,14 @@ def test_fp8_pages_error_distribution(ndgi, ct):
     assert plan.check() == (0, 0)
     ndgi.ndgi_check()
     got = phys.cpu().numpy()
+    # the warp-specialised kernel (four MMA lanes, each with a producer warpgroup)
+    # runs the same arithmetic: identical texels
+    plan.set_shape(1, 8, 1)
+    phys.zero_()
+    plan.decode(r, n)
+    assert plan.check() == (0, 0)
+    ndgi.ndgi_check()
+    assert np.array_equal(phys.cpu().numpy(), got)
     ref = oracle.decode_pages(maps, reqs, 1024, 1024, precision="fp8", act_max=am, fill=0.0)
     e = page_errors(got, ref, reqs)
     e32 = page_errors(got, oracle.decode_pages(maps, reqs, 1024, 1024, precision="fp32", fill=0.0), reqs)

@@ -121,6 +121,48 @@ def test_tc_pages_ragged_and_zipf(ndgi, prec):
     plan.close()
 
 
+# (lanes, slots) of the warp-specialised page kernel: four MMA lanes, each with
+# a producer warpgroup that writes the layer-1 rows of its next tile.
+WS_SHAPES = ((8, 1),)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tc_pages_warp_specialised(ndgi, prec):
+    # The warp-specialised kernel runs the same arithmetic as the 4 x 1 kernel
+    # (same ring values, blend, MMAs and epilogue conversions), so its texels
+    # equal that kernel's bit for bit; both are checked against the oracle.
+    maps = synth.page_models(43, sizes=SIZES, temporal_dtype="f16")
+    models = [ndgi.Model.from_arrays(m) for m in maps]
+    phys = torch.full((1024, 1024, 4), float("nan"), dtype=torch.float32, device="cuda")
+    plan = ndgi.PagesPlan(models, prec, 4096, phys)
+    for reqs in (synth.ragged_page_requests(15, SIZES, 40, slots_x=8, slot=128),
+                 synth.zipf_page_requests(16, SIZES, 64, page=128, slots_x=8),
+                 synth.zipf_page_requests(17, SIZES, 1, page=128, slots_x=8)):
+        r, n = ndgi.page_requests_to_device(reqs)
+        out = {}
+        for shape in ((1, 4, 1), (1, 8, 1)):
+            plan.set_shape(*shape)
+            phys.fill_(float("nan"))
+            plan.decode(r, n)
+            st, err = plan.check()
+            assert st == 0 and err == 0
+            ndgi.ndgi_check()
+            out[shape] = phys.cpu().numpy()
+        a, b = out[(1, 4, 1)], out[(1, 8, 1)]
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+        assert np.array_equal(np.nan_to_num(a), np.nan_to_num(b))
+        ref = oracle.decode_pages(maps, reqs, 1024, 1024, precision=prec)
+        assert page_err(b, ref, reqs) <= GATE[prec]
+    # an empty frame leaves the texture untouched
+    phys.fill_(float("nan"))
+    r, n = ndgi.page_requests_to_device(synth.zipf_page_requests(18, SIZES, 4, page=128, slots_x=8))
+    n.zero_()
+    plan.decode(r, n)
+    ndgi.ndgi_check()
+    assert torch.isnan(phys).all()
+    plan.close()
+
+
 def test_tc_pages_full_resolution_features(ndgi):
     # features at the lightmap's own resolution: the per-texel gather path
     maps = [synth.model(60 + i, s, s, s, s, 16, 24, 8, 64, temporal_dtype="f16") for i, s in enumerate((256, 512))]
@@ -145,12 +187,12 @@ def test_tc_pages_autotune_and_rgba16f(ndgi):
     r, n = ndgi.page_requests_to_device(reqs)
     plan.autotune(r, n, len(reqs))
     prec, cps, lanes, slots = plan.info()
-    assert prec == 1 and cps == 1 and lanes * slots <= 4
+    assert prec == 1 and cps == 1 and (lanes, slots) in WS_SHAPES + ((4, 1), (2, 2))
     with pytest.raises(ndgi.NdgiError):
         plan.set_shape(1, 3, 3)
     with pytest.raises(ndgi.NdgiError):
         plan.set_shape(2, 4, 1)
-    for shape in ((1, 2, 2), (1, 4, 1), (1, lanes, slots)):   # every built shape decodes the same texels
+    for shape in ((1, 2, 2), (1, 4, 1), (1, 8, 1), (1, lanes, slots)):   # every built shape decodes the same texels
         plan.set_shape(*shape)
         assert plan.info()[1:] == shape
         phys.zero_()
