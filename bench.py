@@ -42,10 +42,12 @@ METRIC = "Gtexels/s decoded (BC fetch+temporal lerp+MLP), FP16-TC vs FP32 plain 
 # the ones captured: the hash below is compared at run time and the figure drops to null once they change.
 TRAFFIC_SOURCES = ("tc_decode.cu", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h")
 NCU_TRAFFIC = {
-    "k_points_tc": {"src": "e6116925bedfffb7", "read": 111232512, "write": 44287232, "units": 1 << 23,
+    "k_points_tc": {"src": "36d64324ef0dc70e", "read": 111226112, "write": 44448768, "units": 1 << 23,
                     "profile": "profiles/k_points_tc_points_2048_atlas.md"},
-    "k_pages_tc": {"src": "e6116925bedfffb7", "read": 19479808, "write": 75010816, "units": 1024 * 128 * 128,
+    "k_pages_tc": {"src": "36d64324ef0dc70e", "read": 19508480, "write": 75900672, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_tc_pages_8_lightmaps.md"},
+    "k_pages_ws": {"src": "36d64324ef0dc70e", "read": 19202816, "write": 74750720, "units": 1024 * 128 * 128,
+                   "profile": "profiles/k_pages_ws_pages_8_lightmaps.md"},
 }
 
 
@@ -248,6 +250,11 @@ def check_status(ndgi):
         return str(ex)[:200]
 
 
+def page_kernel(plan_shape):
+    """Name of the tensor-core page kernel a plan shape (precision, ctas/SM, lanes, slots) runs."""
+    return "k_pages_ws" if tuple(plan_shape)[2:] == (8, 1) else "k_pages_tc"
+
+
 def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True):
     """Virtual-texture page decode: one step = one frame of 4096 page requests."""
     maps = synth.page_models(4)
@@ -259,7 +266,10 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
     out = {}
     for prec in ("fp16", "fp32"):
         plan = ndgi.PagesPlan(models, prec, len(reqs), phys)
-        plan.autotune(r_dev, n_dev, len(reqs))
+        if prec != "fp32" and args.page_shape:
+            plan.set_shape(1, *args.page_shape)
+        else:
+            plan.autotune(r_dev, n_dev, len(reqs))
         steps = args.steps if prec == "fp16" else max(3, min(args.steps, 10))
         ms, clocks = timed(lambda: plan.decode(r_dev, n_dev), steps, args.warmup, sample_clocks=(prec == "fp16"))
         st, err_word = plan.check()
@@ -291,9 +301,10 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
         plan.close()
     kernel_s = out["fp16"]["ms_per_frame"] * 1e-3
     achieved = texels * PAGE_FLOP_PER_TEXEL / kernel_s / 1e12
-    traffic = traffic_for("k_pages_tc", texels)
+    kernel = page_kernel(out["fp16"]["plan_shape"])
+    traffic = traffic_for(kernel, texels)
     out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                       "frac": achieved / peaks["bf16_tflops"], "traffic": traffic, "kernel": "k_pages_tc",
+                       "frac": achieved / peaks["bf16_tflops"], "traffic": traffic, "kernel": kernel,
                        "peak_source": f"{peak_kind} bf16 burst (fp16 has the same dense rate)",
                        "flop_per_texel": PAGE_FLOP_PER_TEXEL}
     if traffic is not None:
@@ -365,7 +376,9 @@ def bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank):
             act_max = ndgi.ndgi_calibrate_fp8(model, cal).cpu().numpy().astype(np.float64)
             ndgi.ndgi_prepare_fp8(model, act_max)
         plan = ndgi.PagesPlan([model], prec, len(reqs), phys)
-        if prec != "fp32":
+        if prec != "fp32" and args.page_shape:
+            plan.set_shape(1, *args.page_shape)
+        elif prec != "fp32":
             plan.autotune(r_dev, n_dev, len(reqs))
         steps = max(3, min(args.steps, 10)) if prec != "fp32" else 3
         ms, _ = timed(lambda: plan.decode(r_dev, n_dev), steps, 2)
@@ -399,7 +412,7 @@ def bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank):
         plan.close()
     achieved = texels * PAGE_FLOP_PER_TEXEL / (out["fp16"]["ms_per_frame"] * 1e-3) / 1e12
     out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                       "frac": achieved / peaks["bf16_tflops"], "kernel": "k_pages_tc",
+                       "frac": achieved / peaks["bf16_tflops"], "kernel": page_kernel(out["fp16"]["plan_shape"]),
                        "peak_source": f"{peak_kind} bf16 burst (fp16 has the same dense rate)"}
     del phys
     torch.cuda.empty_cache()
@@ -424,7 +437,11 @@ def main():
                     help="reference arm: seconds of oracle work over the warm-up and timed steps")
     ap.add_argument("--page-requests", type=int, default=4096,
                     help="page requests per frame (4096 = the page workload; smaller for profiling)")
+    ap.add_argument("--page-shape", default=None,
+                    help="lanes,slots of the tensor-core page kernel instead of the autotuner's pick "
+                         "(4,1 / 2,2 / 8,1; for profiling one kernel)")
     args = ap.parse_args()
+    args.page_shape = tuple(int(x) for x in args.page_shape.split(",")) if args.page_shape else None
     args.warmup = max(args.warmup, 3)
     nq = 1 << args.queries_log2
     rank = int(os.environ.get("RANK", "0"))
