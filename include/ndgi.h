@@ -179,6 +179,44 @@ ndgi_status ndgi_decode_points(const ndgi_model_desc *model, ndgi_precision prec
                                const float *uvt, int64_t n, float *rgb, void *stream);
 
 /*
+ * Point decode from HOST buffers (the paper decodes on the device only;
+ * this is a serving service around ndgi_decode_points).  A pipe overlaps,
+ * chunk by chunk, the copy of queries to the device, the decode, and the
+ * copy of results back to the host: while chunk k is decoded on the
+ * caller's stream, chunk k + 1 is copied in and chunk k - 1 copied out on
+ * the pipe's two copy streams.
+ *
+ * ndgi_host_pipe_staging_size: bytes of device staging a pipe with this
+ *   chunk (queries per chunk, >= 1) needs: three chunk buffers of queries and
+ *   results (24 bytes per query each, rounded up to 256-byte boundaries).
+ * ndgi_host_pipe_create: makes a pipe on the current device.  `staging` is
+ *   caller-owned device memory of at least that size, 256-byte aligned, used
+ *   by the pipe until it is destroyed.  The pipe creates its two copy
+ *   streams and its events here (never during a decode).
+ *   NDGI_ERR_INVALID_ARG for chunk < 1, a NULL, short or unaligned staging.
+ * ndgi_decode_points_host: the decode of ndgi_decode_points with
+ *   uvt_host [n][3] and rgb_host [n][3] FP32 in host memory.  Enqueues all
+ *   work and returns: the results are in rgb_host once `stream` has reached
+ *   this point (synchronise it).  uvt_host must stay unchanged and rgb_host
+ *   untouched until then.  Page-locked (pinned) host buffers give the
+ *   overlap; pageable ones still decode correctly but the copies then
+ *   serialise.  Call on the pipe's device; one host thread at a time per
+ *   pipe; successive calls on a pipe are ordered (a call's first copy waits
+ *   for the previous call's last one).  n == 0 is a no-op.  Errors as for
+ *   ndgi_decode_points, and NDGI_ERR_INVALID_ARG for a pipe of another
+ *   device or NULL host buffers.
+ * ndgi_host_pipe_destroy: synchronises the pipe's streams and frees them and
+ *   its events (not the staging).  NULL is a no-op.
+ */
+typedef struct ndgi_host_pipe ndgi_host_pipe;
+size_t ndgi_host_pipe_staging_size(int64_t chunk);
+ndgi_status ndgi_host_pipe_create(int64_t chunk, void *staging, size_t staging_bytes, ndgi_host_pipe **pipe);
+ndgi_status ndgi_decode_points_host(ndgi_host_pipe *pipe, const ndgi_model_desc *model, ndgi_precision precision,
+                                    const void *ws, const float *uvt_host, int64_t n, float *rgb_host,
+                                    void *stream);
+ndgi_status ndgi_host_pipe_destroy(ndgi_host_pipe *pipe);
+
+/*
  * The gather stage alone (Sec. 3.3 sampling of the feature map and temporal
  * line), for validation: x [n][cs+ct] FP32 receives [v_s, v_t]; p35
  * [n][4][cs] int32 (may be NULL) receives, for the taps (x0,y0), (x1,y0),

@@ -64,6 +64,10 @@ SIGNATURES = [
     ("ndgi_prepare_fp8", C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     ("ndgi_fp8_unpack", C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     ("ndgi_decode_points", C.c_int, [_vp, C.c_int, _vp, _vp, _i64, _vp, _vp]),
+    ("ndgi_host_pipe_staging_size", _sz, [_i64]),
+    ("ndgi_host_pipe_create", C.c_int, [_i64, _vp, _sz, _vp]),
+    ("ndgi_decode_points_host", C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _i64, _vp, _vp]),
+    ("ndgi_host_pipe_destroy", C.c_int, [_vp]),
     ("ndgi_debug_features", C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     ("ndgi_debug_features_tc", C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
     ("ndgi_pages_plan_create", C.c_int, [_vp, _vp, _i32, C.c_int, _i32, _i32, _vp, _i64, _i64, _vp]),

@@ -160,6 +160,52 @@ def ndgi_decode_points(model, uvt, precision="fp32", ws=None, out=None, stream=N
     return out
 
 
+class HostPipe:
+    """ndgi_host_pipe_* wrapper: point decode from host (CPU) tensors with the
+    copies in, the decode and the copies out overlapped chunk by chunk.  The
+    pipe's device staging is a torch allocation made here, at creation."""
+
+    def __init__(self, chunk=1 << 20, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.chunk = int(chunk)
+        nbytes = int(lib().ndgi_host_pipe_staging_size(self.chunk))
+        if nbytes == 0:
+            raise ValueError("chunk must be >= 1")
+        self.staging = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        h = C.c_void_p()
+        with torch.cuda.device(dev):
+            check(lib().ndgi_host_pipe_create(self.chunk, _p(self.staging), nbytes, C.byref(h)))
+        self.handle = h
+
+    def decode_points(self, model, uvt_host, precision="fp32", ws=None, out=None, stream=None):
+        """rgb [n][3] float32 (host) of the decode at each (u, v, t) row of the host tensor uvt_host.
+        Asynchronous on `stream`: synchronise it before reading `out`."""
+        if uvt_host.is_cuda or uvt_host.dtype != torch.float32 or not uvt_host.is_contiguous():
+            raise ValueError("uvt_host must be a contiguous float32 host tensor")
+        n = uvt_host.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, pin_memory=uvt_host.is_pinned())
+        if out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous() or out.shape[0] != n:
+            raise ValueError("out must be a contiguous float32 host tensor [n][3]")
+        pr = _prec(precision)
+        if ws is None and pr != A.NDGI_FP32:
+            ws = model.workspace(pr)
+        check(lib().ndgi_decode_points_host(self.handle, C.byref(model.desc), pr, _p(ws), uvt_host.data_ptr(), n,
+                                            out.data_ptr(), _stream(stream)))
+        return out
+
+    def close(self):
+        if self.handle:
+            check(lib().ndgi_host_pipe_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def ndgi_debug_features(model, uvt, stream=None):
     """(x [n][cs+ct] float32, p35 [n][4][cs] int32) of the gather stage."""
     uvt = _need(uvt, torch.float32, "uvt")

@@ -51,3 +51,12 @@ def test_host_side_argument_errors_without_gpu(libpath):
     st, msg = _abi.last_error()
     assert st == _abi.NDGI_ERR_INVALID_ARG and "ndgi_bc_pack" in msg
     assert L.ndgi_version().startswith(b"ndgi")
+    # host-buffer pipe: sizes and refusals before any CUDA call
+    assert L.ndgi_host_pipe_staging_size(0) == 0
+    assert L.ndgi_host_pipe_staging_size(1) == 3 * 2 * 256
+    assert L.ndgi_host_pipe_staging_size(1 << 20) == 3 * 2 * (12 << 20)
+    h = ctypes.c_void_p()
+    assert L.ndgi_host_pipe_create(16, None, 0, ctypes.byref(h)) == _abi.NDGI_ERR_INVALID_ARG and not h.value
+    assert L.ndgi_host_pipe_create(0, None, 0, ctypes.byref(h)) == _abi.NDGI_ERR_INVALID_ARG
+    assert L.ndgi_host_pipe_destroy(None) == _abi.NDGI_OK
+    assert L.ndgi_decode_points_host(None, None, 0, None, None, 1, None, None) == _abi.NDGI_ERR_INVALID_ARG
