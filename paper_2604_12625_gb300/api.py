@@ -368,6 +368,36 @@ def ndgi_fit_backward(state, samples, grad_rgb, grads=None, relaxed=False, strea
     return grads
 
 
+class NdgiDecodeFunction(torch.autograd.Function):
+    """The fit's decode as a differentiable torch op: the straight-through
+    BC4 forward of ndgi_fit_forward and the hand-written CUDA backward of
+    ndgi_fit_backward (through the MLP, the temporal and bilinear sampling
+    and the BC4 quantisation, treated as identity).  Inputs after the four
+    settings are the FIT_TENSORS in order; samples carry no gradient."""
+
+    @staticmethod
+    def forward(ctx, samples, relaxed, lm_w, lm_h, address_mode, *tensors):
+        state = FitState(dict(zip(A.FIT_TENSORS, tensors)), lm_w, lm_h, address_mode)
+        ctx.save_for_backward(samples, *tensors)
+        ctx.settings = (bool(relaxed), int(lm_w), int(lm_h), int(address_mode))
+        return ndgi_fit_forward(state, samples, relaxed)
+
+    @staticmethod
+    def backward(ctx, grad_rgb):
+        samples, *tensors = ctx.saved_tensors
+        relaxed, lm_w, lm_h, address_mode = ctx.settings
+        state = FitState(dict(zip(A.FIT_TENSORS, tensors)), lm_w, lm_h, address_mode)
+        grads = ndgi_fit_backward(state, samples, grad_rgb.contiguous(), relaxed=relaxed)
+        return (None, None, None, None, None) + tuple(grads[k] for k in A.FIT_TENSORS)
+
+
+def ndgi_decode_fit(params, samples, lm_w, lm_h, relaxed=False, address_mode=0):
+    """rgb [n][3] of the fit's decode at samples [n][3] int32 (ix, iy, keyframe j),
+    differentiable w.r.t. params (dict of float32 CUDA tensors keyed by FIT_TENSORS)."""
+    return NdgiDecodeFunction.apply(samples, relaxed, lm_w, lm_h, address_mode,
+                                    *[params[k] for k in A.FIT_TENSORS])
+
+
 def fit_config(steps, batch, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, freeze_steps=0, loss_every=0, seed=0,
                relaxed=False):
     return A.FitConfig(int(steps), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(freeze_steps),

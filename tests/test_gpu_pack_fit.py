@@ -161,3 +161,28 @@ def test_encode_fit_reduces_loss(ndgi):
     for k in ("ea", "eb", "w"):
         v = st.t[k]
         assert float(v.min()) >= 0.0 and float(v.max()) <= 1.0
+
+
+@pytest.mark.parametrize("relaxed", [False, True])
+def test_autograd_function_matches_torch_reference(ndgi, relaxed):
+    # loss.backward() through ndgi.NdgiDecodeFunction (hand-written CUDA backward)
+    # against PyTorch FP64 autograd of an independent statement of the STE forward
+    from _fit_ref import tiny_problem, torch_forward
+    lm, T = 64, 6
+    p, s, tgt = tiny_problem(21, feat=32, lm=lm, cs=4, T=T, ct=4, H=16, n=700)
+    params = {k: torch.from_numpy(np.ascontiguousarray(p[k], np.float32)).cuda().requires_grad_()
+              for k in KEYS}
+    y = ndgi.ndgi_decode_fit(params, torch.from_numpy(s).cuda(), lm, lm, relaxed=relaxed)
+    loss = ((y.double() - torch.from_numpy(tgt).cuda()) ** 2).mean()
+    loss.backward()
+    if relaxed:   # the continuous relaxation: the oracle's analytic FP64 gradient
+        yr = oracle.fit_forward(p, s, lm, lm, relaxed=True)
+        _, gr = oracle.fit_backward(p, s, tgt, lm, lm, relaxed=True)
+        ref_y, ref_g = yr, gr
+    else:
+        y_t, t = torch_forward(p, s, lm, T)
+        ((y_t - torch.from_numpy(tgt)) ** 2).mean().backward()
+        ref_y, ref_g = y_t.detach().numpy(), {k: t[k].grad.numpy() for k in KEYS}
+    assert rel_err(y.detach().cpu().numpy(), ref_y) <= 1e-5
+    for k in KEYS:
+        assert norm_err(params[k].grad.cpu().numpy(), ref_g[k]) <= 1e-3, k

@@ -9,14 +9,7 @@ import oracle
 import synth
 
 torch = pytest.importorskip("torch")
-
-
-def tiny_problem(seed=0, feat=8, lm=16, cs=2, T=3, ct=2, H=6, n=40):
-    p = synth.fit_init(seed, feat, feat, cs, T, ct, H)
-    p["b1"] = p["b1"] + 0.3  # keep most units active so FD sees a smooth function
-    s = synth.fit_samples(seed + 1, n, lm, lm, T)
-    tgt = np.random.default_rng(seed + 2).normal(size=(n, 3))
-    return p, s, tgt
+from _fit_ref import tiny_problem, torch_forward  # noqa: E402
 
 
 def _flat_loss(p, s, tgt, lm, relaxed):
@@ -55,41 +48,6 @@ def test_backward_matches_finite_differences_relaxed(seed):
         ref = max(np.linalg.norm(fd[keep]), 1e-6)
         assert err / ref < 1e-3, (key, err, ref)
         assert keep.mean() > 0.5
-
-
-def torch_forward(p, s, lm, T):
-    """Independent PyTorch FP64 statement of the straight-through fit forward."""
-    t = {k: torch.tensor(np.asarray(v, np.float64), requires_grad=True) for k, v in p.items()
-         if k in oracle.FIT_KEYS}
-    bh, bw, cs = p["ea"].shape
-    fw, fh = bw * 4, bh * 4
-
-    def ste(x, scale):
-        xs = torch.tensor(np.asarray(x.detach().numpy(), np.float32))
-        q = torch.floor(torch.clamp(xs * scale + 0.5, 0, scale)).double() / scale
-        return x + (q - x).detach()
-
-    qa, qb, qw = ste(t["ea"], 255.0), ste(t["eb"], 255.0), ste(t["w"], 7.0)
-    # full-resolution feature planes F[c][ty][tx] from blocks (Eq. 7)
-    f = (1 - qw) * qa[..., None] + qw * qb[..., None]               # [bh][bw][cs][16]
-    f = f.reshape(bh, bw, cs, 4, 4).permute(2, 0, 3, 1, 4).reshape(cs, fh, fw)
-    ix = torch.tensor(s[:, 0], dtype=torch.float64)
-    iy = torch.tensor(s[:, 1], dtype=torch.float64)
-    x = (ix + 0.5) / lm * fw - 0.5
-    y = (iy + 0.5) / lm * fh - 0.5
-    x0, y0 = torch.floor(x), torch.floor(y)
-    fx, fy = x - x0, y - y0
-    cx0 = x0.long().clamp(0, fw - 1)
-    cx1 = (x0.long() + 1).clamp(0, fw - 1)
-    cy0 = y0.long().clamp(0, fh - 1)
-    cy1 = (y0.long() + 1).clamp(0, fh - 1)
-    vs = ((1 - fy) * ((1 - fx) * f[:, cy0, cx0] + fx * f[:, cy0, cx1])
-          + fy * ((1 - fx) * f[:, cy1, cx0] + fx * f[:, cy1, cx1])).T
-    vt = t["temporal"][torch.tensor(s[:, 2]).long()]
-    xin = torch.cat([vs, vt], 1)
-    h1 = torch.relu(xin @ t["w1"] + t["b1"])
-    h2 = torch.relu(h1 @ t["w2"] + t["b2"])
-    return h2 @ t["w3"] + t["b3"], t
 
 
 def test_backward_matches_torch_autograd_ste():
