@@ -124,3 +124,30 @@ def test_unsupported_shape_rejected(ndgi):
     with pytest.raises(ndgi.NdgiError) as e:
         ndgi.ndgi_decode_points(ndgi.Model.from_arrays(m), torch.zeros((4, 3), device="cuda"), "fp32")
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_non_finite_and_out_of_range_queries(ndgi, prec):
+    # Coordinates outside [0, 1) sample the clamped edge texels (the default
+    # address mode); NaN, +-inf and huge values give in-bounds taps and finite
+    # results without any error, and the queries around them decode as usual.
+    m = synth.model(33, 256, 256, 128, 128, 16, 24, 8, 64, temporal_dtype="f16")
+    model = ndgi.Model.from_arrays(m)
+    q = synth.random_queries(34, 4000)
+    q[:1000, :2] = q[:1000, :2] * 3.0 - 1.0                 # u, v in [-1, 2): clamped taps
+    bad = np.array([np.nan, np.inf, -np.inf, 1e30, -1e30], np.float32)
+    rows = []
+    for i, b in enumerate(bad):
+        for axis in range(3):
+            r = 1000 + 3 * i + axis
+            q[r, axis] = b
+            rows.append(r)
+    q[1100, :] = np.nan
+    rows.append(1100)
+    got = ndgi.ndgi_decode_points(model, torch.from_numpy(q).cuda(), prec).cpu().numpy()
+    ndgi.ndgi_check()
+    assert np.all(np.isfinite(got))
+    ok = np.ones(len(q), bool)
+    ok[rows] = False
+    ref = oracle.decode_points(m, q[ok], precision=prec if prec != "fp32" else "fp32")
+    assert rel_err(got[ok], ref) <= (FP32_TOL if prec == "fp32" else 2e-3)
