@@ -246,3 +246,32 @@ def test_tc_gather_matches_fp32_gather(ndgi, shape):
     xr, _ = oracle.features(m, q)
     assert np.max(np.abs(x_tc - x32)) <= 2e-6 * max(1.0, np.abs(x32).max())
     assert np.max(np.abs(x_tc - xr)) <= 4e-6 * max(1.0, np.abs(xr).max())
+
+
+@pytest.mark.parametrize("shape", [(1, 4, 1), (1, 8, 1)])
+def test_tc_pages_mirror_address_mode(ndgi, shape):
+    # The page kernels with mirrored-repeat addressing (mode 1).  A page texel's
+    # taps overhang the map by at most one feature texel, which the mirror maps
+    # back to the edge texel (as clamping does), so this checks the mode-1 path
+    # of the ring's column range and the taps, including full pages at the corners.
+    sizes = (256, 512)
+    maps = [synth.model(50 + i, s, s, s // 2, s // 2, 16, 24, 8, 64, temporal_dtype="f16", address_mode=1)
+            for i, s in enumerate(sizes)]
+    models = [ndgi.Model.from_arrays(mm) for mm in maps]
+    phys = torch.full((512, 512, 4), float("nan"), dtype=torch.float32, device="cuda")
+    plan = ndgi.PagesPlan(models, "fp16", 64, phys)
+    plan.set_shape(*shape)
+    reqs = synth.ragged_page_requests(51, sizes, 12, slots_x=4, slot=128)
+    corners = np.zeros(4, dtype=synth.PAGE_REQ_DTYPE)   # full pages at the corners of both maps
+    for i, (mi, cx, cy) in enumerate(((0, 0, 0), (0, 1, 1), (1, 0, 1), (1, 1, 0))):
+        sz = sizes[mi]
+        corners[i] = (mi, cx * (sz - 128), cy * (sz - 128), 128, 128, np.float32(0.3 + 0.1 * i),
+                      ((12 + i) % 4) * 128, ((12 + i) // 4) * 128)
+    reqs = np.concatenate([reqs, corners])
+    r, n = ndgi.page_requests_to_device(reqs)
+    plan.decode(r, n)
+    assert plan.check() == (0, 0)
+    ndgi.ndgi_check()
+    ref = oracle.decode_pages(maps, reqs, 512, 512, precision="fp16")
+    assert page_err(phys.cpu().numpy(), ref, reqs) <= GATE["fp16"]
+    plan.close()
