@@ -1191,19 +1191,22 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
       // Writes tile tl's layer-1 rows (two output rows of 64 texels) into
       // slot s, decoding the feature rows they need into the ring first;
       // returns this thread's output row.
+      // Decodes into the ring the feature rows tile tl's output rows need,
+      // plus kDecodeAhead (lane-uniform; ends with a lane barrier).
+      auto decode_ahead = [&](int tl) {
+        const int need_hi = rowtab[min(2 * tl + 1, qh - 1)].y;
+        if (need_hi > decoded_hi) {
+          const int from = max(decoded_hi + 1, rowtab[2 * tl].x);
+          const int to = min(need_hi + kDecodeAhead, fr_last);
+          decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to, fc0,
+                                 ncols, t, luts);
+          decoded_hi = to;
+          lane_sync(wg);
+        }
+      };
       auto produce = [&](int s, int tl) -> int {
         const int row_base = 2 * tl;
-        if (staged) {   // feature rows needed by output rows row_base, row_base + 1
-          const int need_hi = rowtab[min(row_base + 1, qh - 1)].y;
-          if (need_hi > decoded_hi) {
-            const int from = max(decoded_hi + 1, rowtab[row_base].x);
-            const int to = min(need_hi + kDecodeAhead, fr_last);
-            decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
-                                   fc0, ncols, t, luts);
-            decoded_hi = to;
-            lane_sync(wg);
-          }
-        }
+        if (staged) decode_ahead(tl);   // feature rows needed by output rows row_base, row_base + 1
         const int orow = row_base + (t >> 6);
         uint32_t w[NW];
         if (col < qw && orow < qh) {
@@ -1364,6 +1367,9 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
 // drains quickly with the error latched.
 // ---------------------------------------------------------------------------
 constexpr int kWsLanes = 4;
+// Look-ahead of the warp-specialised producer's ring decode: small batches,
+// each decoded while the consumer runs the previous tile's MMA chain.
+constexpr int kWsDecodeAhead = 2;
 
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -1488,19 +1494,27 @@ __global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
         const __half2 wx1 = __float2half2_rn(fx * xs), wx0 = __float2half2_rn((1.0f - fx) * xs);
         const int c0 = (cx0 - fc0) * 16, c1 = (cx1 - fc0) * 16;
         int decoded_hi = -1000000;
+        // Decodes into the ring the feature rows that tile tl's output rows
+        // need, plus a short look-ahead (lane-uniform; the caller syncs).
+        // The rows written never share a ring slot with the rows of the tile
+        // before it (a span of at most kWsDecodeAhead + 3 < 16 rows), so one
+        // thread may decode while another still blends that tile.
+        auto decode_for = [&](int tl) {
+          const int need_hi = rowtab[min(2 * tl + 1, qh - 1)].y;
+          if (need_hi > decoded_hi) {
+            const int from = max(decoded_hi + 1, rowtab[2 * tl].x);
+            const int to = min(need_hi + kWsDecodeAhead, fr_last);
+            decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
+                                   fc0, ncols, t, luts);
+            decoded_hi = to;
+          }
+        };
+        decode_for(0);
+        named_sync(bar_prod, kLaneThreads);
         for (int tile = 0; tile < ntiles; ++tile) {
           // the slot's layer-1 columns are free once the previous tile's layer 1 has completed
           if (tile > 0) ws_wait(&bar1[lane], ph1, abort);
           const int row_base = 2 * tile;
-          const int need_hi = rowtab[min(row_base + 1, qh - 1)].y;   // feature rows of output rows row_base, +1
-          if (need_hi > decoded_hi) {
-            const int from = max(decoded_hi + 1, rowtab[row_base].x);
-            const int to = min(need_hi + kDecodeAhead, fr_last);
-            decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
-                                   fc0, ncols, t, luts);
-            decoded_hi = to;
-            named_sync(bar_prod, kLaneThreads);
-          }
           const int orow = row_base + (t >> 6);
           uint32_t w[NW];
           if (col < qw && orow < qh) {
@@ -1514,6 +1528,11 @@ __global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
           tmem_st_wait();
           tc_fence_before();
           named_arrive(bar_ready, 2 * kLaneThreads);
+          // the next tile's rows are decoded while the consumer runs this tile's MMA chain
+          if (tile + 1 < ntiles) {
+            decode_for(tile + 1);
+            named_sync(bar_prod, kLaneThreads);
+          }
         }
         // bar1 completes ntiles + 1 phases per quadrant (the last one carries
         // the last tile's layer 3 alone); the producer waited ntiles - 1 of
