@@ -1367,9 +1367,11 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
 // drains quickly with the error latched.
 // ---------------------------------------------------------------------------
 constexpr int kWsLanes = 4;
-// Look-ahead of the warp-specialised producer's ring decode: small batches,
-// each decoded while the consumer runs the previous tile's MMA chain.
-constexpr int kWsDecodeAhead = 2;
+// Look-ahead of the warp-specialised producer's ring decode: batches of up to
+// five rows, each decoded while the consumer runs the previous tile's MMA
+// chain; a quadrant's first batch holds only the first tile's rows, so the
+// first MMA starts early.
+constexpr int kWsDecodeAhead = 4;
 
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -1503,7 +1505,7 @@ __global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
           const int need_hi = rowtab[min(2 * tl + 1, qh - 1)].y;
           if (need_hi > decoded_hi) {
             const int from = max(decoded_hi + 1, rowtab[2 * tl].x);
-            const int to = min(need_hi + kWsDecodeAhead, fr_last);
+            const int to = min(need_hi + (tl == 0 ? 0 : kWsDecodeAhead), fr_last);
             decode_rows_sliced<CS>(m, static_cast<const uint8_t*>(c.ws[r.model]) + L::kSliceOff, ring, from, to,
                                    fc0, ncols, t, luts);
             decoded_hi = to;
