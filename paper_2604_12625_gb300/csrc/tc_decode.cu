@@ -1353,10 +1353,12 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
 // quadrant of the request, one tensor-memory slot) has two warpgroups:
 //   consumer  runs the MMA chain and the epilogues: [layer 3 of the previous
 //             tile + layer 1] -> RGB out, ReLU -> [layer 2] -> ReLU -> A3;
-//   producer  writes the layer-1 rows of the lane's next tile (ring decode,
-//             half2 blend, tcgen05.st) as soon as the slot's previous layer 1
-//             has completed, so the feature work leaves the consumer's
-//             critical path and the SM has eight warps per sub-partition.
+//   producer  writes the layer-1 rows of the lane's next tile (half2 blend
+//             from the ring, tcgen05.st) as soon as the slot's previous layer 1
+//             has completed, arrives, and then decodes the ring rows of the
+//             tile after it while the consumer runs the MMA chain, so the
+//             feature work leaves the consumer's critical path and the SM has
+//             eight warps per sub-partition.
 // Warp w of either warpgroup reaches the same TMEM lane quarter (w mod 4),
 // so both address the slot's rows alike.  The two meet at a named barrier
 // per tile (the producer arrives, the consumer waits); the producer learns
