@@ -366,39 +366,30 @@ void om_fp8_calibrate(const om_model *m, const float *uvt, int64_t n, double *ac
 }
 
 /*
- * FP8 page decode.  As in the reduced-precision page path, t is constant per
- * request, so layer 1's temporal part is folded into a per-request bias:
- * b1' = b1 + sum_c W1q[cs+c] vtq[c] with vtq = a1 e4m3(v_t / a1) (the same
- * value the unfused layer would see), then b1' is stored as three E4M3
- * terms in units a2 like the other biases.  The spatial features are
- * quantised a1 e4m3(x / a1).  act_max: [n_models][3].
+ * FP8 page decode: every layer is a plain FP8 layer of the stored
+ * parameters.  Layer l contracts its quantised inputs a_l e4m3(x / a_l) with
+ * the stored weights s_l e4m3(W_l / s_l) and adds its stored bias (three
+ * E4M3 terms in the layer's output unit, as om_fp8_bias); the output ReLU
+ * is quantised as the next layer's input.  Layer 1's input is the whole
+ * feature vector [v_s, v_t] (Eq. 4 without gamma(t)): the spatial features
+ * and the temporal feature at the request's t are quantised alike, and b1 is
+ * stored in units a2.  act_max: [n_models][3].
  */
 void om_decode_pages_fp8(const om_model *models, const double *act_max, const om_page_req *reqs, int32_t n,
                          double *phys, int64_t phys_w, int nthreads) {
   for (int32_t r = 0; r < n; ++r) {
     const om_page_req *q = &reqs[r];
     const om_model *m = &models[q->model];
-    const int cs = m->cs, ct = m->ct, cin = cs + ct, H = m->hidden;
+    const int cin = m->cs + m->ct, H = m->hidden;
     double sc[7];
     om_fp8_scales(m, act_max + 3 * q->model, sc);
     double *w1q = malloc(sizeof(double) * (size_t)cin * H), *w2q = malloc(sizeof(double) * (size_t)H * H);
     double *w3q = malloc(sizeof(double) * (size_t)H * 3);
     double b1s[256], b2s[256], b3s[3];
     om_fp8_weights(m, sc, w1q, w2q, w3q);
+    om_fp8_bias(m->b1, H, sc[2], NULL, NULL, b1s);
     om_fp8_bias(m->b2, H, sc[4], NULL, NULL, b2s);
     om_fp8_bias(m->b3, 3, sc[6], NULL, NULL, b3s);
-    /* temporal term at the request's t (the features at any texel carry it) */
-    {
-      double x[512];
-      om_features(m, 0.5, 0.5, (double)q->t, x, NULL);
-      double b1f[256];
-      for (int o = 0; o < H; ++o) {
-        double z = m->b1[o];
-        for (int c = 0; c < ct; ++c) z += sc[0] * om_e4m3(x[cs + c] / sc[0]) * w1q[(size_t)(cs + c) * H + o];
-        b1f[o] = z;
-      }
-      om_fp8_bias(b1f, H, sc[2], NULL, NULL, b1s);
-    }
 #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
     for (int32_t jj = 0; jj < q->h; ++jj) {
       double x[512], h1[256], h2[256];
@@ -406,10 +397,10 @@ void om_decode_pages_fp8(const om_model *models, const double *act_max, const om
         const double u = ((double)(q->x0 + ii) + 0.5) / (double)m->lm_w;
         const double v = ((double)(q->y0 + jj) + 0.5) / (double)m->lm_h;
         om_features(m, u, v, (double)q->t, x, NULL);
-        for (int k = 0; k < cs; ++k) x[k] = sc[0] * om_e4m3(x[k] / sc[0]);
+        for (int k = 0; k < cin; ++k) x[k] = sc[0] * om_e4m3(x[k] / sc[0]);
         for (int o = 0; o < H; ++o) {
           double z = b1s[o];
-          for (int k = 0; k < cs; ++k) z += x[k] * w1q[(size_t)k * H + o];
+          for (int k = 0; k < cin; ++k) z += x[k] * w1q[(size_t)k * H + o];
           h1[o] = z > 0.0 ? sc[2] * om_e4m3(z / sc[2]) : 0.0;
         }
         for (int o = 0; o < H; ++o) {
