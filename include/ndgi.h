@@ -343,11 +343,13 @@ ndgi_status ndgi_pages_plan_destroy(ndgi_pages_plan *plan);
  *   device_error device int32 (may be NULL) that receives the error word of
  *                this call (same bits as ndgi_pages_check reports)
  * The static array is shared by every call and keeps the last call's
- * contents; each call rewrites it on `stream` before its decode, so calls
- * that overlap on the GPU race.  The first call on a device looks up the
- * array's device address (once per device); make that first call before
- * any stream capture.  Copies the model table from host memory with a
- * pageable cudaMemcpyAsync, so the call waits for `stream` to drain first.
+ * contents; each call rewrites it on `stream` before its decode (a small
+ * kernel that receives the descriptors by value and clears the error word),
+ * so calls that overlap on the GPU race.  The call returns without waiting
+ * for `stream`.  The first call on a device looks up the array's device
+ * address (once per device); make that first call before any stream
+ * capture.  Descriptors are checked like ndgi_pages_plan_create's; all must
+ * share cs, ct and hidden (NDGI_ERR_UNSUPPORTED otherwise).
  */
 ndgi_status ndgi_decode_pages_static(const ndgi_model_desc *models, int32_t n_models,
                                      const ndgi_page_req *reqs_dev, const int32_t *n_dev, int32_t max_reqs,

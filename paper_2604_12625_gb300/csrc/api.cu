@@ -48,7 +48,7 @@ int num_sms() {
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 // Host-side checks of a model descriptor common to every decode.
-static ndgi_status check_model(const ndgi_model_desc* m, const char* who) {
+ndgi_status check_model(const ndgi_model_desc* m, const char* who) {
   if (!m) return set_error(NDGI_ERR_INVALID_ARG, "%s: model is NULL", who);
   if (m->lm_w <= 0 || m->lm_h <= 0) return set_error(NDGI_ERR_INVALID_ARG, "%s: lightmap size must be > 0", who);
   if (m->feat_w <= 0 || m->feat_h <= 0 || m->feat_w % 4 || m->feat_h % 4)

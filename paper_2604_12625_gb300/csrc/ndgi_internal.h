@@ -41,6 +41,9 @@ ndgi_status cuda_status(cudaError_t e, const char* what);
 
 int num_sms();
 
+// Host-side checks of a model descriptor common to every decode (NDGI_OK or the status it set).
+ndgi_status check_model(const ndgi_model_desc* m, const char* who);
+
 // ---- FP32 CUDA-core decode (decode_simt.cu) ----
 bool simt_supported(int cs, int ct, int hidden);
 cudaError_t launch_points_f32(const DevModel& m, const float* uvt, int64_t n, float* rgb, cudaStream_t s);

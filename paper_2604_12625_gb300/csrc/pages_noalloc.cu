@@ -12,8 +12,11 @@
 // Limits and sharing: the array holds at most kMaxStaticModels model
 // descriptors.  Every call shares it and it keeps the last call's contents;
 // each call rewrites the model table and clears the error word on its
-// stream before the decode, so calls that overlap on the GPU (on different
-// streams, or on the same stream from different host threads) race on it.
+// stream before the decode (one small kernel that receives the descriptors
+// by value, so no host memory is read after the call returns and the host
+// never waits for the stream), so calls that overlap on the GPU (on
+// different streams, or on the same stream from different host threads)
+// race on it.
 //
 // Set-up: the device address of the array is looked up with
 // cudaGetSymbolAddress once per device, on the first call made while that
@@ -33,6 +36,19 @@ constexpr size_t kScratchBytes = kErrorOffset + 256;
 
 // Model table [kMaxStaticModels] followed by the error word.
 static __device__ __align__(256) unsigned char g_pages_scratch[kScratchBytes];
+
+// The descriptors of one call, passed by value to the set-up kernel.
+struct StaticTable {
+  DevModel m[kMaxStaticModels];
+};
+static_assert(sizeof(StaticTable) <= 16 * 1024, "kernel parameter block");
+
+// Writes the model table into the static array and clears the error word.
+__global__ void k_static_setup(const StaticTable tbl, int n, unsigned char* base) {
+  DevModel* dst = reinterpret_cast<DevModel*>(base);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = tbl.m[i];
+  if (threadIdx.x == 0) *reinterpret_cast<int32_t*>(base + kErrorOffset) = 0;
+}
 
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
@@ -77,31 +93,24 @@ extern "C" ndgi_status ndgi_decode_pages_static(const ndgi_model_desc* models, i
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_decode_pages_static: bad out_format");
   if (!phys || phys_w <= 0 || phys_h <= 0 || ((uintptr_t)phys % 16))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_decode_pages_static: phys must be a 16-byte aligned texture");
-  DevModel table[kMaxStaticModels];
+  StaticTable table;
   for (int i = 0; i < n_models; ++i) {
     const ndgi_model_desc& m = models[i];
-    if (m.lm_w <= 0 || m.lm_h <= 0 || m.feat_w <= 0 || m.feat_h <= 0 || m.feat_w % 4 || m.feat_h % 4 ||
-        m.cs <= 0 || m.ct < 0 || m.t_count <= 0 || m.hidden <= 0 || !m.bc4 || !m.w1 || !m.b1 || !m.w2 || !m.b2 ||
-        !m.w3 || !m.b3 || (m.ct > 0 && !m.temporal) || ((uintptr_t)m.bc4 % 16) ||
-        (m.temporal_dtype != NDGI_FP32 && m.temporal_dtype != NDGI_FP16) ||
-        (m.address_mode != 0 && m.address_mode != 1))
-      return set_error(NDGI_ERR_INVALID_ARG, "ndgi_decode_pages_static: model %d is invalid", i);
+    ndgi_status st = check_model(&m, "ndgi_decode_pages_static");
+    if (st != NDGI_OK) return st;
     if (m.cs != models[0].cs || m.ct != models[0].ct || m.hidden != models[0].hidden)
       return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_decode_pages_static: all models must share cs, ct and hidden");
-    table[i] = to_dev(m);
+    table.m[i] = to_dev(m);
   }
-  if (!simt_supported(models[0].cs, models[0].ct, models[0].hidden))
-    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_decode_pages_static: shape cs=%d ct=%d hidden=%d is not built",
-                     models[0].cs, models[0].ct, models[0].hidden);
   void* base = nullptr;
   ndgi_status st = scratch_address(&base);
   if (st != NDGI_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* b = static_cast<unsigned char*>(base);
-  // The table is pageable host memory on this stack frame: a pageable
-  // host-to-device copy has been staged by the time it returns.
-  cudaError_t e = cudaMemcpyAsync(b, table, sizeof(DevModel) * n_models, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b + kErrorOffset, 0, sizeof(int32_t), s);
+  // The descriptors travel in the kernel's parameter block: nothing on this
+  // stack frame is read after the launch returns.
+  k_static_setup<<<1, 64, 0, s>>>(table, n_models, b);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "ndgi_decode_pages_static: scratch set-up");
   PagesCtx c{};
   c.models = reinterpret_cast<const DevModel*>(b);

@@ -48,6 +48,36 @@ def test_static_scratch_page_decode_matches_plan():
         rng = float(ref[..., :3].max() - ref[..., :3].min())
         assert np.max(np.abs(got - ref)) <= 1e-5 * rng, call
         assert np.count_nonzero(got[..., 3]) == int(sum(q["w"] * q["h"] for q in reqs))
+    # the call allocates nothing: device free memory is unchanged around a call
+    # (the first calls above have already loaded the kernels' code)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    st = A.lib().ndgi_decode_pages_static(descs, len(models), C.c_void_p(r.data_ptr()), C.c_void_p(n.data_ptr()),
+                                          64, A.NDGI_RGBA32F, C.c_void_p(phys.data_ptr()), 512, 512,
+                                          C.c_void_p(err.data_ptr()), stream)
+    assert st == A.NDGI_OK, A.last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    # a request naming a model the call was not given is skipped and latched
+    # (bit 1 of the error word); the next call starts from a cleared word
+    bad = reqs.copy()
+    bad["model"][0] = len(models)
+    rb, nb = ndgi.page_requests_to_device(bad)
+    for rq, nq, want in ((rb, nb, 2), (r, n, 0)):
+        st = A.lib().ndgi_decode_pages_static(descs, len(models), C.c_void_p(rq.data_ptr()),
+                                              C.c_void_p(nq.data_ptr()), 64, A.NDGI_RGBA32F,
+                                              C.c_void_p(phys.data_ptr()), 512, 512, C.c_void_p(err.data_ptr()),
+                                              stream)
+        assert st == A.NDGI_OK, A.last_error()
+        torch.cuda.synchronize()
+        assert int(err.item()) == want
+    # RGBA16F output with no error word requested: the FP32 result rounded to FP16
+    phys16 = torch.zeros((512, 512, 4), dtype=torch.float16, device="cuda")
+    st = A.lib().ndgi_decode_pages_static(descs, len(models), C.c_void_p(r.data_ptr()), C.c_void_p(n.data_ptr()),
+                                          64, A.NDGI_RGBA16F, C.c_void_p(phys16.data_ptr()), 512, 512, None, stream)
+    assert st == A.NDGI_OK, A.last_error()
+    torch.cuda.synchronize()
+    assert torch.equal(phys16, phys.to(torch.float16))
     plan.close()
     # more models than the static maximum is rejected with a clear error
     many = (A.ModelDesc * 65)(*([models[0].desc] * 65))
