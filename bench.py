@@ -355,8 +355,9 @@ def bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank, check_err=True
     return out
 
 
-FIT_WORKLOAD = ("fit: 1024^2 x T=24 FP16 targets (32 Gaussians x sun term + 0.05), straight-through BC4 "
-                "512^2x16 features, temporal 24x8, MLP 24-64-64-3, Adam lr 1e-2, 2^20 samples/step, 2000 steps "
+FIT_WORKLOAD = ("fit: 1024^2 x T=24 FP16 keyframe targets (32 Gaussians x sun term + 0.05), straight-through BC4 "
+                "512^2x16 features, temporal 24x8, MLP 24-64-64-3, Adam lr 1e-2, 2^20 samples/step of (texel, t) "
+                "with t ~ U[0,1) (temporal lerp differentiated; targets interpolated between keyframes), 2000 steps "
                 "(last 200 freeze the features)")
 
 

@@ -384,8 +384,11 @@ ndgi_status ndgi_bc_pack(const float *ea, const float *eb, const float *w, int32
  * planes are held as the simulation's endpoints and weights (Eq. 6):
  *   ea, eb [feat_h/4][feat_w/4][cs] in [0,1], w [feat_h/4][feat_w/4][cs][16]
  *   in [0,1]; temporal [t_count][ct]; MLP as in ndgi_model_desc.
- * A fit sample is an int32 triple (ix, iy, j): texel (ix, iy) of the
- * lm_w x lm_h target at keyframe j (t = j / t_count).
+ * A fit sample is a query (u, v, t), three FP32 values exactly as for
+ * ndgi_decode_points (texel (ix, iy) of the lm_w x lm_h target is u =
+ * (ix + 0.5) / lm_w, v = (iy + 0.5) / lm_h); t is continuous, so the
+ * temporal feature is the linear interpolation (Sec. 3.1, Eq. 2) of the two
+ * keyframe rows j0, j1 around t with weight alpha, as in the decode.
  */
 typedef struct {
   int32_t lm_w, lm_h, feat_w, feat_h, cs, t_count, ct, hidden;
@@ -399,12 +402,12 @@ typedef struct {
 } ndgi_fit_grads;
 
 /*
- * Forward of the fit at n samples [n][3]: rgb [n][3] FP32.  relaxed = 0 uses
+ * Forward of the fit at n queries uvt [n][3]: rgb [n][3] FP32.  relaxed = 0 uses
  * the straight-through BC simulation (features quantised exactly as the
  * packed decode would see them); relaxed = 1 uses the continuous Eq. 7 with
  * unquantised E and W (for finite-difference checks).
  */
-ndgi_status ndgi_fit_forward(const ndgi_fit_params *params, const int32_t *samples, int64_t n, int32_t relaxed,
+ndgi_status ndgi_fit_forward(const ndgi_fit_params *params, const float *uvt, int64_t n, int32_t relaxed,
                              float *rgb, void *stream);
 
 /*
@@ -413,9 +416,11 @@ ndgi_status ndgi_fit_forward(const ndgi_fit_params *params, const int32_t *sampl
  * straight-through estimator treats the quantisers as identity and uses
  * the quantised values as chain-rule factors:
  *   dL/dea += (1 - q(w)) g_f, dL/deb += q(w) g_f, dL/dw += (q(eb) - q(ea)) g_f.
+ * The temporal feature's gradient g_t splits between the keyframe rows
+ * around t: dL/dK[j0] += (1 - alpha) g_t, dL/dK[j1] += alpha g_t.
  * Accumulation uses FP32 atomics, so results vary in the last bits.
  */
-ndgi_status ndgi_fit_backward(const ndgi_fit_params *params, const int32_t *samples, int64_t n, int32_t relaxed,
+ndgi_status ndgi_fit_backward(const ndgi_fit_params *params, const float *uvt, int64_t n, int32_t relaxed,
                               const float *grad_rgb, const ndgi_fit_grads *grads, void *stream);
 
 /* Fit loop settings (Sec. 4: Adam, L2 loss; final stage freezes features). */
@@ -434,12 +439,18 @@ size_t ndgi_encode_fit_workspace_size(const ndgi_fit_params *params, const ndgi_
 
 /*
  * Runs cfg->steps Adam steps of the L2 fit on device.  Each step draws
- * cfg->batch samples (ix, iy, j) with the counter-based generator
+ * cfg->batch samples (texel ix, iy and time t) with the counter-based
+ * generator
  *   ctr = step * 2^32 + i, z1 = SplitMix64(seed + (2 ctr + 1) g),
  *   z2 = SplitMix64(seed + (2 ctr + 2) g), g = 0x9E3779B97F4A7C15,
- *   ix = lo32(z1) mod lm_w, iy = hi32(z1) mod lm_h, j = lo32(z2) mod t_count,
- * evaluates the straight-through forward, the MSE against targets
- * [t_count][lm_h][lm_w][3] FP16 (device), the backward, and Adam (endpoints
+ *   ix = lo32(z1) mod lm_w, iy = hi32(z1) mod lm_h, t = (z2 >> 40) 2^-24,
+ * evaluates the straight-through forward at ((ix + 0.5) / lm_w,
+ * (iy + 0.5) / lm_h, t), the MSE against the target at t, which is the
+ * keyframe targets [t_count][lm_h][lm_w][3] FP16 (device; keyframe j at
+ * t = j / t_count) of that texel interpolated linearly between the two
+ * keyframes around t, exactly as the temporal features are (Sec. 3.1,
+ * Eq. 2: the lightmap between keyframes is their linear interpolation),
+ * the backward, and Adam (endpoints
  * and weights projected onto [0,1]).  step_offset continues a previous run
  * (Adam step numbering and sample stream).  Every loss_every steps the FP64
  * batch loss is written to loss_log[k] (device, double,

@@ -90,7 +90,8 @@ def lib():
             L.om_fit_backward.argtypes = [vp, vp, vp, i64, C.c_int, vp]
             L.om_fit_backward.restype = f64
             L.om_adam.argtypes = [vp, vp, vp, vp, i64, i32, f64, f64, f64, f64, i32]
-            L.om_fit_draw.argtypes = [C.c_uint64, i64, i64, i64, i32, i32, i32, vp]
+            L.om_fit_draw.argtypes = [C.c_uint64, i64, i64, i64, i32, i32, vp, vp]
+            L.om_temporal_weights.argtypes = [f64, i32, vp, vp, vp]
             L.om_max_hidden.restype = C.c_int
             L.om_e4m3_batch.argtypes = [vp, i64, vp, vp]
             L.om_p2.argtypes = [f64]
@@ -318,9 +319,10 @@ class FitParams:
                             *[_ptr(self.a[k]) for k in FIT_KEYS], int(p.get("address_mode", 0)))
 
 
-def fit_forward(params, samples, lm_w, lm_h, relaxed=False, want_signs=False):
+def fit_forward(params, uvt, lm_w, lm_h, relaxed=False, want_signs=False):
+    """Straight-through (or relaxed) forward at the queries uvt [n][3] float32: rgb [n][3]."""
     P = params if isinstance(params, FitParams) else FitParams(params, lm_w, lm_h)
-    s = _c(samples, np.int32).reshape(-1, 3)
+    s = _c(uvt, np.float32).reshape(-1, 3)
     y = np.zeros((s.shape[0], 3), np.float64)
     signs = np.zeros((s.shape[0], 2 * P.dims["hidden"]), np.uint8) if want_signs else None
     lib().om_fit_forward(C.byref(P.s), _ptr(s), s.shape[0], int(relaxed), _ptr(y), _ptr(signs))
@@ -332,10 +334,10 @@ def fit_loss(rgb, target):
     return float(lib().om_fit_loss(_ptr(rgb), _ptr(target), rgb.shape[0]))
 
 
-def fit_backward(params, samples, target, lm_w, lm_h, relaxed=False):
-    """(loss, grads) with grads a dict of FP64 arrays shaped like the params."""
+def fit_backward(params, uvt, target, lm_w, lm_h, relaxed=False):
+    """(loss, grads) at the queries uvt [n][3] float32, grads a dict of FP64 arrays shaped like the params."""
     P = params if isinstance(params, FitParams) else FitParams(params, lm_w, lm_h)
-    s = _c(samples, np.int32).reshape(-1, 3)
+    s = _c(uvt, np.float32).reshape(-1, 3)
     t = _c(target, np.float64).reshape(-1, 3)
     g = {k: np.zeros(P.a[k].shape, np.float64) for k in FIT_KEYS}
     G = _FitGrads(*[_ptr(g[k]) for k in FIT_KEYS])
@@ -350,7 +352,29 @@ def adam(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, project=False):
     lib().om_adam(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.size, int(step), lr, beta1, beta2, eps, int(project))
 
 
-def fit_draw(seed, step, n, lm_w, lm_h, t_count, first=0):
-    out = np.zeros((n, 3), np.int32)
-    lib().om_fit_draw(C.c_uint64(seed), step, first, n, lm_w, lm_h, t_count, _ptr(out))
+def fit_draw(seed, step, n, lm_w, lm_h, first=0):
+    """The fit loop's samples of one step: (texel int32 [n][2], uvt float32 [n][3])."""
+    texel = np.zeros((n, 2), np.int32)
+    uvt = np.zeros((n, 3), np.float32)
+    lib().om_fit_draw(C.c_uint64(seed), step, first, n, lm_w, lm_h, _ptr(texel), _ptr(uvt))
+    return texel, uvt
+
+
+def temporal_weights(t, t_count):
+    """(j0, j1, alpha) of time t: keyframes at j / t_count, periodic (the decode's temporal lerp)."""
+    j0, j1, a = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+    lib().om_temporal_weights(float(t), int(t_count), C.byref(j0), C.byref(j1), C.byref(a))
+    return j0.value, j1.value, a.value
+
+
+def fit_targets_at(targets, texel, uvt):
+    """Target of each fit sample: the keyframe targets [T][H][W][3] at its texel, interpolated linearly in t
+    between the two keyframes around it (the lightmap at time t is the interpolation of its keyframes,
+    Eq. 2), in FP64."""
+    T = targets.shape[0]
+    out = np.zeros((texel.shape[0], 3), np.float64)
+    for i in range(texel.shape[0]):
+        j0, j1, a = temporal_weights(float(uvt[i, 2]), T)
+        ix, iy = int(texel[i, 0]), int(texel[i, 1])
+        out[i] = (1.0 - a) * targets[j0, iy, ix].astype(np.float64) + a * targets[j1, iy, ix].astype(np.float64)
     return out

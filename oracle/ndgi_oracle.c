@@ -129,6 +129,14 @@ static void om_temporal_setup(double t, int T, int *j0, int *j1, double *alpha) 
   *j1 = (int)((j + 1) % T);
 }
 
+/* The keyframe segment of t: rows j0, j1 and the lerp weight alpha (exported for the fit's targets). */
+void om_temporal_weights(double t, int32_t T, int32_t *j0, int32_t *j1, double *alpha) {
+  int a, b;
+  om_temporal_setup(t, T, &a, &b, alpha);
+  *j0 = a;
+  *j1 = b;
+}
+
 /*
  * Input feature vector x = [v_s (cs), v_t (ct)] at (u, v, t).
  * Optionally returns the P35 numerators of the four taps, [4][cs], taps in
@@ -505,11 +513,9 @@ static double om_sim_value(const om_fit_params *P, int64_t bc, int p, int relaxe
   return (double)om_p35_value(5 * ((7 - k) * A + k * B));
 }
 
-/* Taps and fractions of the fit sample at texel (ix, iy): texel centre uv. */
-static void om_fit_taps(const om_fit_params *P, int ix, int iy, int tx[4], int ty[4], double *fx, double *fy) {
+/* Taps and fractions of the fit sample at (u, v) (the decode's texel-centre convention). */
+static void om_fit_taps(const om_fit_params *P, double u, double v, int tx[4], int ty[4], double *fx, double *fy) {
   int x0, x1, y0, y1;
-  double u = ((double)ix + 0.5) / (double)P->lm_w;
-  double v = ((double)iy + 0.5) / (double)P->lm_h;
   om_bilinear_setup(u, P->feat_w, P->address_mode, &x0, &x1, fx);
   om_bilinear_setup(v, P->feat_h, P->address_mode, &y0, &y1, fy);
   tx[0] = x0; ty[0] = y0;
@@ -519,15 +525,16 @@ static void om_fit_taps(const om_fit_params *P, int ix, int iy, int tx[4], int t
 }
 
 /*
- * One sample: texel (ix, iy) of keyframe j (t = j/T, so the temporal feature
- * is row j).  Returns y [3]; optionally the pre-activations z1, z2 [hidden]
- * and the input x [cs+ct].
+ * One sample: the decode at the query (u, v, t) with the straight-through
+ * BC simulation: spatial taps bilinear at (u, v), temporal feature the
+ * linear interpolation (Eq. 2) of rows j0 and j1 at t.  Returns y [3] and
+ * the input x [cs+ct], pre-activations z1, z2 and activations h1, h2.
  */
-static void om_fit_sample_forward(const om_fit_params *P, int ix, int iy, int j, int relaxed,
+static void om_fit_sample_forward(const om_fit_params *P, double u, double v, double t, int relaxed,
                                   double *x, double *z1, double *h1, double *z2, double *h2, double *y) {
   int tx[4], ty[4];
   double fx, fy;
-  om_fit_taps(P, ix, iy, tx, ty, &fx, &fy);
+  om_fit_taps(P, u, v, tx, ty, &fx, &fy);
   int bw = P->feat_w / 4, cs = P->cs, ct = P->ct, H = P->hidden, cin = cs + ct;
   for (int c = 0; c < cs; ++c) {
     double f[4];
@@ -538,7 +545,11 @@ static void om_fit_sample_forward(const om_fit_params *P, int ix, int iy, int j,
     }
     x[c] = (1.0 - fy) * ((1.0 - fx) * f[0] + fx * f[1]) + fy * ((1.0 - fx) * f[2] + fx * f[3]);
   }
-  for (int c = 0; c < ct; ++c) x[cs + c] = (double)P->temporal[(size_t)j * ct + c];
+  int j0, j1;
+  double al;
+  om_temporal_setup(t, P->t_count, &j0, &j1, &al);
+  for (int c = 0; c < ct; ++c)
+    x[cs + c] = (1.0 - al) * (double)P->temporal[(size_t)j0 * ct + c] + al * (double)P->temporal[(size_t)j1 * ct + c];
   for (int o = 0; o < H; ++o) {
     double z = P->b1[o];
     for (int i = 0; i < cin; ++i) z += x[i] * (double)P->w1[(size_t)i * H + o];
@@ -559,18 +570,18 @@ static void om_fit_sample_forward(const om_fit_params *P, int ix, int iy, int j,
 }
 
 /*
- * Fit forward over n samples [n][3] = (ix, iy, j): rgb [n][3].  If `signs`
+ * Fit forward over n queries uvt [n][3] = (u, v, t): rgb [n][3].  If `signs`
  * is non-NULL it receives the ReLU pattern (z > 0) of both hidden layers,
  * [n][2*hidden] bytes, so finite differences can drop kink crossings.
  * relaxed = 1 makes every quantiser the identity (continuous relaxation).
  */
-void om_fit_forward(const om_fit_params *P, const int32_t *samples, int64_t n, int relaxed, double *rgb,
+void om_fit_forward(const om_fit_params *P, const float *uvt, int64_t n, int relaxed, double *rgb,
                     uint8_t *signs) {
   int H = P->hidden;
   for (int64_t s = 0; s < n; ++s) {
     double x[512], z1[256], h1[256], z2[256], h2[256];
-    om_fit_sample_forward(P, samples[3 * s], samples[3 * s + 1], samples[3 * s + 2], relaxed, x, z1, h1, z2, h2,
-                          rgb + 3 * s);
+    om_fit_sample_forward(P, (double)uvt[3 * s], (double)uvt[3 * s + 1], (double)uvt[3 * s + 2], relaxed, x, z1,
+                          h1, z2, h2, rgb + 3 * s);
     if (signs) {
       for (int o = 0; o < H; ++o) {
         signs[s * 2 * H + o] = z1[o] > 0.0;
@@ -594,14 +605,14 @@ double om_fit_loss(const double *rgb, const double *target, int64_t n) {
  * Analytic FP64 gradient of the MSE loss with respect to every parameter.
  * Gradients are accumulated (callers zero them).  Returns the loss.
  */
-double om_fit_backward(const om_fit_params *P, const int32_t *samples, const double *target, int64_t n,
+double om_fit_backward(const om_fit_params *P, const float *uvt, const double *target, int64_t n,
                        int relaxed, om_fit_grads *G) {
   int bw = P->feat_w / 4, cs = P->cs, ct = P->ct, H = P->hidden, cin = cs + ct;
   double loss = 0.0;
   for (int64_t s = 0; s < n; ++s) {
-    int ix = samples[3 * s], iy = samples[3 * s + 1], j = samples[3 * s + 2];
+    const double u = (double)uvt[3 * s], v = (double)uvt[3 * s + 1], t = (double)uvt[3 * s + 2];
     double x[512], z1[256], h1[256], z2[256], h2[256], y[3];
-    om_fit_sample_forward(P, ix, iy, j, relaxed, x, z1, h1, z2, h2, y);
+    om_fit_sample_forward(P, u, v, t, relaxed, x, z1, h1, z2, h2, y);
     double dy[3];
     for (int o = 0; o < 3; ++o) {
       double d = y[o] - target[3 * s + o];
@@ -640,10 +651,17 @@ double om_fit_backward(const om_fit_params *P, const int32_t *samples, const dou
     }
     (void)gh2;
     (void)gh1;
-    for (int c = 0; c < ct; ++c) G->temporal[(size_t)j * ct + c] += gx[cs + c];
+    /* v_t = (1 - alpha) K[j0] + alpha K[j1]: the gradient splits between the two rows */
+    int j0, j1;
+    double al;
+    om_temporal_setup(t, P->t_count, &j0, &j1, &al);
+    for (int c = 0; c < ct; ++c) {
+      G->temporal[(size_t)j0 * ct + c] += (1.0 - al) * gx[cs + c];
+      G->temporal[(size_t)j1 * ct + c] += al * gx[cs + c];
+    }
     int tx[4], ty[4];
     double fx, fy;
-    om_fit_taps(P, ix, iy, tx, ty, &fx, &fy);
+    om_fit_taps(P, u, v, tx, ty, &fx, &fy);
     /* d x_c / d f_tap: the bilinear weights of the four taps */
     double wt[4] = {(1.0 - fx) * (1.0 - fy), fx * (1.0 - fy), (1.0 - fx) * fy, fx * fy};
     for (int q = 0; q < 4; ++q) {
@@ -699,18 +717,25 @@ uint64_t om_splitmix64_next(uint64_t x) { return om_splitmix64(x); }
 /*
  * Counter-based fit sample i of step `step`: two SplitMix64 outputs at
  * counters c = seed + 2*(step*2^32 + i)*golden and c + golden.
- * ix = lo32(z1) % lm_w, iy = hi32(z1) % lm_h, j = lo32(z2) % T.
+ * ix = lo32(z1) % lm_w, iy = hi32(z1) % lm_h, t = (z2 >> 40) 2^-24 (the top
+ * 24 bits as a fraction in [0, 1)).  texel [n][2] receives (ix, iy) and uvt
+ * [n][3] the query ((ix + 0.5) / lm_w, (iy + 0.5) / lm_h, t), each rounded
+ * once to FP32.
  */
 void om_fit_draw(uint64_t seed, int64_t step, int64_t first, int64_t n, int32_t lm_w, int32_t lm_h,
-                 int32_t t_count, int32_t *samples) {
+                 int32_t *texel, float *uvt) {
   const uint64_t golden = 0x9E3779B97F4A7C15ull;
   for (int64_t i = 0; i < n; ++i) {
     uint64_t ctr = ((uint64_t)step << 32) + (uint64_t)(first + i);
     uint64_t base = seed + 2u * ctr * golden;
     uint64_t z1 = om_splitmix64(base);
     uint64_t z2 = om_splitmix64(base + golden);
-    samples[3 * i] = (int32_t)((uint32_t)z1 % (uint32_t)lm_w);
-    samples[3 * i + 1] = (int32_t)((uint32_t)(z1 >> 32) % (uint32_t)lm_h);
-    samples[3 * i + 2] = (int32_t)((uint32_t)z2 % (uint32_t)t_count);
+    const int32_t ix = (int32_t)((uint32_t)z1 % (uint32_t)lm_w);
+    const int32_t iy = (int32_t)((uint32_t)(z1 >> 32) % (uint32_t)lm_h);
+    texel[2 * i] = ix;
+    texel[2 * i + 1] = iy;
+    uvt[3 * i] = (float)(((double)ix + 0.5) / (double)lm_w);
+    uvt[3 * i + 1] = (float)(((double)iy + 0.5) / (double)lm_h);
+    uvt[3 * i + 2] = (float)ldexp((double)(z2 >> 40), -24);
   }
 }

@@ -347,23 +347,24 @@ class FitState:
         return {k: torch.zeros_like(v) for k, v in self.t.items()}
 
 
-def ndgi_fit_forward(state, samples, relaxed=False, out=None, stream=None):
-    _need(samples, torch.int32, "samples")
-    n = samples.shape[0]
+def ndgi_fit_forward(state, uvt, relaxed=False, out=None, stream=None):
+    """rgb [n][3] of the fit's straight-through (or relaxed) decode at queries uvt [n][3] float32 (u, v, t)."""
+    _need(uvt, torch.float32, "uvt")
+    n = uvt.shape[0]
     if out is None:
-        out = torch.empty((n, 3), dtype=torch.float32, device=samples.device)
-    check(lib().ndgi_fit_forward(C.byref(state.params), _p(samples), n, int(relaxed), _p(out), _stream(stream)))
+        out = torch.empty((n, 3), dtype=torch.float32, device=uvt.device)
+    check(lib().ndgi_fit_forward(C.byref(state.params), _p(uvt), n, int(relaxed), _p(out), _stream(stream)))
     return out
 
 
-def ndgi_fit_backward(state, samples, grad_rgb, grads=None, relaxed=False, stream=None):
-    """Adds dL/dparams into `grads` (dict of tensors, created zeroed if None) and returns it."""
-    _need(samples, torch.int32, "samples")
+def ndgi_fit_backward(state, uvt, grad_rgb, grads=None, relaxed=False, stream=None):
+    """Adds dL/dparams at queries uvt [n][3] into `grads` (dict of tensors, created zeroed if None); returns it."""
+    _need(uvt, torch.float32, "uvt")
     _need(grad_rgb, torch.float32, "grad_rgb")
     if grads is None:
         grads = state.zeros_like()
     g = A.FitGrads(*[grads[k].data_ptr() for k in A.FIT_TENSORS])
-    check(lib().ndgi_fit_backward(C.byref(state.params), _p(samples), samples.shape[0], int(relaxed),
+    check(lib().ndgi_fit_backward(C.byref(state.params), _p(uvt), uvt.shape[0], int(relaxed),
                                   _p(grad_rgb), C.byref(g), _stream(stream)))
     return grads
 
@@ -373,28 +374,29 @@ class NdgiDecodeFunction(torch.autograd.Function):
     BC4 forward of ndgi_fit_forward and the hand-written CUDA backward of
     ndgi_fit_backward (through the MLP, the temporal and bilinear sampling
     and the BC4 quantisation, treated as identity).  Inputs after the four
-    settings are the FIT_TENSORS in order; samples carry no gradient."""
+    settings are the FIT_TENSORS in order; the queries carry no gradient."""
 
     @staticmethod
-    def forward(ctx, samples, relaxed, lm_w, lm_h, address_mode, *tensors):
+    def forward(ctx, uvt, relaxed, lm_w, lm_h, address_mode, *tensors):
         state = FitState(dict(zip(A.FIT_TENSORS, tensors)), lm_w, lm_h, address_mode)
-        ctx.save_for_backward(samples, *tensors)
+        ctx.save_for_backward(uvt, *tensors)
         ctx.settings = (bool(relaxed), int(lm_w), int(lm_h), int(address_mode))
-        return ndgi_fit_forward(state, samples, relaxed)
+        return ndgi_fit_forward(state, uvt, relaxed)
 
     @staticmethod
     def backward(ctx, grad_rgb):
-        samples, *tensors = ctx.saved_tensors
+        uvt, *tensors = ctx.saved_tensors
         relaxed, lm_w, lm_h, address_mode = ctx.settings
         state = FitState(dict(zip(A.FIT_TENSORS, tensors)), lm_w, lm_h, address_mode)
-        grads = ndgi_fit_backward(state, samples, grad_rgb.contiguous(), relaxed=relaxed)
+        grads = ndgi_fit_backward(state, uvt, grad_rgb.contiguous(), relaxed=relaxed)
         return (None, None, None, None, None) + tuple(grads[k] for k in A.FIT_TENSORS)
 
 
-def ndgi_decode_fit(params, samples, lm_w, lm_h, relaxed=False, address_mode=0):
-    """rgb [n][3] of the fit's decode at samples [n][3] int32 (ix, iy, keyframe j),
-    differentiable w.r.t. params (dict of float32 CUDA tensors keyed by FIT_TENSORS)."""
-    return NdgiDecodeFunction.apply(samples, relaxed, lm_w, lm_h, address_mode,
+def ndgi_decode_fit(params, uvt, lm_w, lm_h, relaxed=False, address_mode=0):
+    """rgb [n][3] of the fit's decode at arbitrary queries uvt [n][3] float32 (u, v, t), differentiable
+    w.r.t. params (dict of float32 CUDA tensors keyed by FIT_TENSORS), through the temporal interpolation
+    at fractional t as well as the MLP, the bilinear gather and the straight-through BC4 quantisation."""
+    return NdgiDecodeFunction.apply(uvt, relaxed, lm_w, lm_h, address_mode,
                                     *[params[k] for k in A.FIT_TENSORS])
 
 

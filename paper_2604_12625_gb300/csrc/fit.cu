@@ -1,9 +1,10 @@
 // Differentiable fit of the decoder (Sec. 3.4 BC simulation, Sec. 4 training).
 //
-// Forward per sample (texel ix, iy of keyframe j): the four bilinear taps of
-// the feature map are rebuilt from the block endpoints and weights (Eq. 7)
-// with straight-through quantisation, so the features equal the packed BC4
-// decode bit for bit; the temporal feature is keyframe row j; then the MLP.
+// Forward per sample (a query (u, v, t), as for the point decode): the four
+// bilinear taps of the feature map are rebuilt from the block endpoints and
+// weights (Eq. 7) with straight-through quantisation, so the features equal
+// the packed BC4 decode bit for bit; the temporal feature is the linear
+// interpolation (Eq. 2) of the keyframe rows j0, j1 around t; then the MLP.
 //
 // Backward (recompute, nothing stored between passes): a persistent CTA
 // processes tiles of 128 samples.  Per tile each thread runs its sample's
@@ -11,8 +12,8 @@
 // gradients of the tile are the contractions H2^T dY, H1^T dZ2 and X^T dZ1
 // over the tile's samples, done from shared memory into per-thread register
 // accumulators that persist across tiles and are flushed once per CTA.
-// Temporal-line gradients (every sample hits one of T rows) are reduced in
-// shared memory first.  Feature-map gradients go straight to global memory
+// Temporal-line gradients (a sample splits its gradient between rows j0 and
+// j1 in the ratio (1 - alpha) : alpha) are reduced in shared memory first.  Feature-map gradients go straight to global memory
 // with FP32 atomics, after merging the endpoint gradients of taps that fall
 // in the same block.
 #include <cmath>
@@ -34,9 +35,9 @@ struct FitArgs {
   int vec_red;                  // g_ea, g_eb 16-byte aligned: endpoint gradients use vector reductions
   int vec_ld;                   // ea, eb 16-byte aligned: endpoints are read with vector loads
   int64_t n;
-  const int32_t* samples;       // mode 0
+  const float* uvt;             // mode 0: queries [n][3]
   const float* grad_rgb;        // mode 0
-  const __half* targets;        // mode 1: [T][lm_h][lm_w][3]
+  const __half* targets;        // mode 1: keyframe targets [T][lm_h][lm_w][3], interpolated in t
   uint64_t seed;                // mode 1
   const int64_t* step;          // mode 1: device step counter
   double* loss_acc;             // mode 1: sum of squared errors
@@ -52,8 +53,10 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ void draw_sample(uint64_t seed, int64_t step, int64_t i, int lm_w, int lm_h, int T,
-                                            int& ix, int& iy, int& j) {
+// Sample i of step `step`: texel (ix, iy) and t = (z2 >> 40) 2^-24, a 24-bit
+// fraction in [0, 1) (exact in FP32).
+__device__ __forceinline__ void draw_sample(uint64_t seed, int64_t step, int64_t i, int lm_w, int lm_h, int& ix,
+                                            int& iy, float& t) {
   const uint64_t g = 0x9E3779B97F4A7C15ull;
   const uint64_t ctr = ((uint64_t)step << 32) + (uint64_t)i;
   const uint64_t base = seed + 2ull * ctr * g;
@@ -61,7 +64,7 @@ __device__ __forceinline__ void draw_sample(uint64_t seed, int64_t step, int64_t
   const uint64_t z2 = splitmix64(base + g);
   ix = (int)((uint32_t)z1 % (uint32_t)lm_w);
   iy = (int)((uint32_t)(z1 >> 32) % (uint32_t)lm_h);
-  j = (int)((uint32_t)z2 % (uint32_t)T);
+  t = (float)(uint32_t)(z2 >> 40) * 0x1p-24f;
 }
 
 // ---------------------------------------------------------------------------
@@ -73,9 +76,7 @@ struct TapInfo {
   float wt;       // bilinear weight
 };
 
-__device__ __forceinline__ void fit_taps(const FitArgs& a, int ix, int iy, TapInfo (&t)[4], float& fx, float& fy) {
-  const float u = ((float)ix + 0.5f) / (float)a.lm_w;
-  const float v = ((float)iy + 0.5f) / (float)a.lm_h;
+__device__ __forceinline__ void fit_taps(const FitArgs& a, float u, float v, TapInfo (&t)[4], float& fx, float& fy) {
   int x0, x1, y0, y1;
   axis_setup(u, a.feat_w, a.address_mode, x0, x1, fx);
   axis_setup(v, a.feat_h, a.address_mode, y0, y1, fy);
@@ -155,10 +156,10 @@ __device__ __forceinline__ void sim_values(const FitArgs& a, int64_t blk, int k0
 }
 
 template <int CS, int CT>
-__device__ __forceinline__ void fit_gather(const FitArgs& a, int ix, int iy, int j, float (&x)[CS + CT]) {
+__device__ __forceinline__ void fit_gather(const FitArgs& a, float u, float v, float tq, float (&x)[CS + CT]) {
   TapInfo t[4];
   float fx, fy;
-  fit_taps(a, ix, iy, t, fx, fy);
+  fit_taps(a, u, v, t, fx, fy);
   const float gx = 1.0f - fx, gy = 1.0f - fy;
 #pragma unroll
   for (int c = 0; c < CS; ++c) {
@@ -167,8 +168,12 @@ __device__ __forceinline__ void fit_gather(const FitArgs& a, int ix, int iy, int
     for (int q = 0; q < 4; ++q) f[q] = sim_value(a, t[q].blk + c, t[q].p, d0, d1, d2);
     x[c] = gy * (gx * f[0] + fx * f[1]) + fy * (gx * f[2] + fx * f[3]);   // same blend order as the decode
   }
+  int j0, j1;
+  float al;
+  temporal_setup(tq, a.t_count, j0, j1, al);
+  const float ga = 1.0f - al;
 #pragma unroll
-  for (int c = 0; c < CT; ++c) x[CS + c] = a.temporal[j * CT + c];
+  for (int c = 0; c < CT; ++c) x[CS + c] = ga * a.temporal[j0 * CT + c] + al * a.temporal[j1 * CT + c];
 }
 
 // ---------------------------------------------------------------------------
@@ -178,9 +183,8 @@ template <int CS, int CT, int H>
 __global__ void __launch_bounds__(kFitThreads) k_fit_forward(FitArgs a, float* __restrict__ rgb) {
   constexpr int CIN = CS + CT;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += (int64_t)gridDim.x * blockDim.x) {
-    const int ix = a.samples[3 * s], iy = a.samples[3 * s + 1], j = a.samples[3 * s + 2];
     float x[CIN];
-    fit_gather<CS, CT>(a, ix, iy, j, x);
+    fit_gather<CS, CT>(a, a.uvt[3 * s], a.uvt[3 * s + 1], a.uvt[3 * s + 2], x);
     float h1[H];
 #pragma unroll
     for (int o = 0; o < H; ++o) {
@@ -329,21 +333,27 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int64_t s = tile * kFitTile + r;
     const bool valid = s < a.n;
-    int ix = 0, iy = 0, j = 0;
+    int ix = 0, iy = 0;
+    float u = 0.5f, v = 0.5f, tq = 0.0f;
     if (valid) {
       if (MODE == 0) {
-        ix = a.samples[3 * s];
-        iy = a.samples[3 * s + 1];
-        j = a.samples[3 * s + 2];
+        u = a.uvt[3 * s];
+        v = a.uvt[3 * s + 1];
+        tq = a.uvt[3 * s + 2];
       } else {
-        draw_sample(a.seed, step, s, a.lm_w, a.lm_h, a.t_count, ix, iy, j);
+        draw_sample(a.seed, step, s, a.lm_w, a.lm_h, ix, iy, tq);
+        u = ((float)ix + 0.5f) / (float)a.lm_w;
+        v = ((float)iy + 0.5f) / (float)a.lm_h;
       }
     }
+    int j0, j1;
+    float al;
+    temporal_setup(tq, a.t_count, j0, j1, al);
     // ---- A1: features (spatial channels q*SC.., temporal q*TC.. of this thread) ----
     {
       TapInfo t[4];
       float fx, fy;
-      fit_taps(a, ix, iy, t, fx, fy);
+      fit_taps(a, u, v, t, fx, fy);
       const float gx = 1.0f - fx, gy = 1.0f - fy;
       float f[4][SC];
 #pragma unroll
@@ -355,10 +365,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
       for (int kk = 0; kk < SC; ++kk)   // the decode's blend order
         sX[r * LX + q * SC + kk] =
             valid ? gy * (gx * f[0][kk] + fx * f[1][kk]) + fy * (gx * f[2][kk] + fx * f[3][kk]) : 0.0f;
+      const float ga = 1.0f - al;
 #pragma unroll
       for (int kk = 0; kk < TC; ++kk) {
         const int c = q * TC + kk;
-        sX[r * LX + CS + c] = valid ? a.temporal[j * CT + c] : 0.0f;
+        sX[r * LX + CS + c] = valid ? ga * a.temporal[j0 * CT + c] + al * a.temporal[j1 * CT + c] : 0.0f;
       }
     }
     __syncthreads();
@@ -437,8 +448,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
           dy1 = a.grad_rgb[3 * s + 1];
           dy2 = a.grad_rgb[3 * s + 2];
         } else {
-          const __half* tg = a.targets + (((int64_t)j * a.lm_h + iy) * a.lm_w + ix) * 3;
-          const float d0 = y0 - __half2float(tg[0]), d1 = y1 - __half2float(tg[1]), d2 = y2 - __half2float(tg[2]);
+          // the target at t: the keyframe targets around t interpolated like the features (Eq. 2)
+          const int64_t plane = (int64_t)a.lm_h * a.lm_w * 3, px = ((int64_t)iy * a.lm_w + ix) * 3;
+          const __half* t0 = a.targets + j0 * plane + px;
+          const __half* t1 = a.targets + j1 * plane + px;
+          const float ga = 1.0f - al;
+          const float d0 = y0 - (ga * __half2float(t0[0]) + al * __half2float(t1[0]));
+          const float d1 = y1 - (ga * __half2float(t0[1]) + al * __half2float(t1[1]));
+          const float d2 = y2 - (ga * __half2float(t0[2]) + al * __half2float(t1[2]));
           loss += (double)d0 * d0 + (double)d1 * d1 + (double)d2 * d2;
           const float sc = 2.0f / (3.0f * (float)a.n);
           dy0 = sc * d0;
@@ -520,11 +537,15 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
 #pragma unroll
         for (int kk = 0; kk < TC; ++kk) gt[kk] = fmaf(gz, wt[kk], gt[kk]);
       }
+      // v_t = (1 - alpha) K[j0] + alpha K[j1]: the gradient splits between the two rows
 #pragma unroll
-      for (int kk = 0; kk < TC; ++kk) atomicAdd(&sGK[j * CT + q * TC + kk], gt[kk]);
+      for (int kk = 0; kk < TC; ++kk) {
+        atomicAdd(&sGK[j0 * CT + q * TC + kk], (1.0f - al) * gt[kk]);
+        if (al != 0.0f) atomicAdd(&sGK[j1 * CT + q * TC + kk], al * gt[kk]);
+      }
       TapInfo t[4];
       float fx, fy;
-      fit_taps(a, ix, iy, t, fx, fy);
+      fit_taps(a, u, v, t, fx, fy);
       // per tap: the weight-index gradients (one texel each), and the endpoint
       // gradients of this thread's SC channels
       float gea[4][SC], geb[4][SC];
@@ -825,35 +846,35 @@ using namespace ndgi;
 
 extern "C" {
 
-ndgi_status ndgi_fit_forward(const ndgi_fit_params* params, const int32_t* samples, int64_t n, int32_t relaxed,
+ndgi_status ndgi_fit_forward(const ndgi_fit_params* params, const float* uvt, int64_t n, int32_t relaxed,
                              float* rgb, void* stream) {
   ndgi_status st = check_fit(params, "ndgi_fit_forward");
   if (st != NDGI_OK) return st;
   if (n < 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fit_forward: n < 0");
   if (n == 0) return NDGI_OK;
-  if (!samples || !rgb) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fit_forward: samples or rgb is NULL");
+  if (!uvt || !rgb) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fit_forward: uvt or rgb is NULL");
   FitArgs a = make_args(params);
   a.relaxed = relaxed != 0;
   a.n = n;
-  a.samples = samples;
+  a.uvt = uvt;
   return cuda_status(launch_fit_forward(a, rgb, (cudaStream_t)stream), "ndgi_fit_forward");
 }
 
-ndgi_status ndgi_fit_backward(const ndgi_fit_params* params, const int32_t* samples, int64_t n, int32_t relaxed,
+ndgi_status ndgi_fit_backward(const ndgi_fit_params* params, const float* uvt, int64_t n, int32_t relaxed,
                               const float* grad_rgb, const ndgi_fit_grads* grads, void* stream) {
   ndgi_status st = check_fit(params, "ndgi_fit_backward");
   if (st != NDGI_OK) return st;
   if (n < 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fit_backward: n < 0");
   if (n == 0) return NDGI_OK;
-  if (!samples || !grad_rgb || !grads)
-    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fit_backward: samples, grad_rgb or grads is NULL");
+  if (!uvt || !grad_rgb || !grads)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fit_backward: uvt, grad_rgb or grads is NULL");
   if (!grads->ea || !grads->eb || !grads->w || !grads->w1 || !grads->b1 || !grads->w2 || !grads->b2 || !grads->w3 ||
       !grads->b3 || (params->ct > 0 && !grads->temporal))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_fit_backward: a gradient pointer is NULL");
   FitArgs a = make_args(params);
   a.relaxed = relaxed != 0;
   a.n = n;
-  a.samples = samples;
+  a.uvt = uvt;
   a.grad_rgb = grad_rgb;
   a.g_ea = grads->ea; a.g_eb = grads->eb; a.g_w = grads->w; a.g_temporal = grads->temporal;
   a.g_w1 = grads->w1; a.g_b1 = grads->b1; a.g_w2 = grads->w2; a.g_b2 = grads->b2; a.g_w3 = grads->w3;

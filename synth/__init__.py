@@ -20,8 +20,8 @@ PAGE_REQ_DTYPE = np.dtype(
     [("model", "<i4"), ("x0", "<i4"), ("y0", "<i4"), ("w", "<i4"), ("h", "<i4"),
      ("t", "<f4"), ("dst_x", "<i4"), ("dst_y", "<i4")])
 
-# Fit sample record: integer texel coordinates and keyframe index.
-SAMPLE_DTYPE = np.int32
+# Fit sample record: a query (u, v, t), like a point decode's.
+SAMPLE_DTYPE = np.float32
 
 
 def _rng(seed):
@@ -226,11 +226,19 @@ def fit_init(seed, feat_w, feat_h, cs, t_count, ct, hidden, temporal_std=0.1):
     return p
 
 
-def fit_samples(seed, n, width, height, t_count):
-    """n random (texel x, texel y, keyframe j) int32 triples."""
+def fit_samples(seed, n, width, height, t_count, keyframe_every=4):
+    """n fit samples as float32 queries [n][3] (u, v, t): random texel centres
+    ((ix + 0.5) / width, (iy + 0.5) / height) at t ~ U[0,1); every
+    `keyframe_every`-th sample sits exactly on a keyframe time j / t_count."""
     rng = _rng(seed)
-    s = np.empty((n, 3), dtype=np.int32)
-    s[:, 0] = rng.integers(0, width, n)
-    s[:, 1] = rng.integers(0, height, n)
-    s[:, 2] = rng.integers(0, t_count, n)
+    ix = rng.integers(0, width, n)
+    iy = rng.integers(0, height, n)
+    t = rng.random(n)
+    if keyframe_every:
+        kf = np.arange(n) % keyframe_every == 0
+        t[kf] = rng.integers(0, t_count, int(kf.sum())) / t_count
+    s = np.empty((n, 3), dtype=np.float32)
+    s[:, 0] = (ix + 0.5) / width
+    s[:, 1] = (iy + 0.5) / height
+    s[:, 2] = t
     return s
