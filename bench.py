@@ -40,7 +40,7 @@ METRIC = "Gtexels/s decoded (BC fetch+temporal lerp+MLP), FP16-TC vs FP32 plain 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of a smaller case
 # of the same kernel, scaled to a full launch by the units processed.  Valid only while the kernel sources are
 # the ones captured: the hash below is compared at run time and the figure drops to null once they change.
-TRAFFIC_SOURCES = ("tc_decode.cu", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h")
+TRAFFIC_SOURCES = ("tc_decode.cu", "tc_points.cu", "tc_engine.cuh", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h")
 NCU_TRAFFIC = {
     "k_points_tc": {"src": "295f8b14bfbe4b34", "read": 111222272, "write": 44345344, "units": 1 << 23,
                     "profile": "profiles/k_points_tc_points_2048_atlas.md"},
@@ -283,10 +283,15 @@ PAGES_WORKLOAD = ("pages: 8 lightmaps (2x 512^2, 1024^2, 2048^2, 4096^2), BC4 ha
                   "MLP 24-64-64-3; 4096 Zipf(1.1) requests of 128^2 per frame, own t each; RGBA16F 8192^2 texture")
 
 
-def check_status(ndgi):
-    """'ok', or the library's report of a device-side failure (e.g. a timed-out barrier wait)."""
+def check_status(ndgi, model=None, precision=None):
+    """'ok', or the library's report of a CUDA error or, for a tensor-core point decode, of a device-side
+    failure latched in the model's workspace (e.g. a timed-out barrier wait)."""
     try:
         ndgi.ndgi_check()
+        if model is not None and precision in ("fp16", "bf16"):
+            st, word = ndgi.ndgi_workspace_check(model, precision)
+            if st != 0:
+                return f"workspace error word 0x{word:x} (status {st})"
         return "ok"
     except Exception as ex:  # reported in the JSON line, never hidden
         return str(ex)[:200]
@@ -566,7 +571,7 @@ def main():
     ms_main, clocks = timed(step_main, args.steps, args.warmup, sample_clocks=True)
     ms_median = per_step_median(step_main, 20)
     ms_step = ms_main / args.steps
-    device_check = {"points": check_status(ndgi)}
+    device_check = {"points": check_status(ndgi, model, prec)}
     value = job_value(nq, world, ms_step)
 
     # FP32 plain decode beside it (fewer steps: it is ~10x slower)
@@ -629,7 +634,10 @@ def main():
     else:
         # bytes: 24 B of query I/O per query plus the compressed feature map once
         roof = two_term_roofline(nq, FLOP_PER_TEXEL, nq * 24 + m["bc4"].nbytes, kernel_s, peaks, peak_kind)
-    roof["kernel"] = "k_points_tc" if prec != "fp32" else "k_points_f32"
+    path = ndgi.ndgi_decode_points_path(model, prec, nq) if prec != "fp32" else "direct"
+    roof["kernel"] = ("k_points_f32" if prec == "fp32" else
+                      {"direct": "k_points_tc", "cache": "k_points_tc", "cache_ws": "k_points_ws"}[path])
+    roof["gather"] = path
     roof["traffic"] = traffic_for(roof["kernel"], nq)
     if roof["traffic"] is not None:
         roof["traffic_note"] = (f"ncu DRAM bytes of a 2^23-query launch scaled x{nq / (1 << 23):g}; output lines "

@@ -98,15 +98,44 @@ ndgi_status ndgi_last_error(char *buf, size_t buf_len);
 
 /*
  * Synchronises `stream` and reports any asynchronous CUDA error raised by
- * work enqueued on it (NDGI_ERR_CUDA), then reads and clears the library's
- * device error word: a tensor-core kernel whose bounded barrier wait ran out
- * unwinds, frees its tensor memory and latches it (NDGI_ERR_TIMEOUT).
+ * work enqueued on it (NDGI_ERR_CUDA).  Device-side failures are latched per
+ * call in caller-owned error words instead: a tensor-core kernel whose
+ * bounded barrier wait runs out unwinds, frees its tensor memory and sets
+ * bit 4 (16) of the error word of its workspace (point decodes; read with
+ * ndgi_workspace_check) or of its plan (page decodes; ndgi_pages_check).
  */
 ndgi_status ndgi_check(void *stream);
 
 /*
+ * Synchronises `stream`, then reads and clears the error word held in a
+ * prepared FP16/BF16 workspace `ws` (device): every point decode that used
+ * this workspace latches into it.  *device_error (host, may be NULL)
+ * receives the word; bit 4 (16) = a bounded barrier wait ran out
+ * (NDGI_ERR_TIMEOUT is returned).  Decodes that share a workspace share the
+ * word; decodes with different workspaces never see each other's errors.
+ * ndgi_prepare clears the word.  The paper has no counterpart (a library
+ * service).
+ */
+ndgi_status ndgi_workspace_check(const ndgi_model_desc *model, ndgi_precision precision, const void *ws,
+                                 int32_t *device_error, void *stream);
+
+/*
+ * Test hook for the timeout path (no paper counterpart).  flags = 1 makes
+ * every later tensor-core point decode with this workspace wait, with a
+ * short limit, for a barrier phase that nothing completes, before it issues
+ * any MMA; the decode then takes its real timeout path (lanes stop at
+ * their next barrier, tensor memory is freed, bit 4 of the workspace's
+ * error word is set) and its output is unspecified.  flags = 0 restores
+ * normal decodes.  Enqueued on `stream`.
+ */
+ndgi_status ndgi_debug_workspace_inject(const ndgi_model_desc *model, ndgi_precision precision, void *ws,
+                                        int32_t flags, void *stream);
+
+/*
  * Bytes of device workspace that ndgi_prepare needs for `precision`: the
- * MLP weights re-packed for the tensor-core decode.  0 for NDGI_FP32.
+ * MLP weights re-packed for the tensor-core decode, the texel-sliced copy of
+ * the planes, and (FP16/BF16, maps with feat_w * feat_h * cs * 2 <= 64 MiB)
+ * room for the point decode's decoded-texel cache.  0 for NDGI_FP32.
  */
 size_t ndgi_prepare_workspace_size(const ndgi_model_desc *model, ndgi_precision precision);
 
@@ -171,12 +200,32 @@ ndgi_status ndgi_fp8_unpack(const ndgi_model_desc *model, const void *ws, float 
  * Random-access point decode (Sec. 3.1, Eq. 3; Sec. 5.5 decodes this way):
  * for each i < n, rgb[i] = H(u_i, v_i, t_i).
  *   uvt  [n][3] FP32 (u, v, t); rgb [n][3] FP32 output.
- *   ws   the prepared workspace for `precision` (ignored for NDGI_FP32).
+ *   ws   the prepared workspace for `precision` (ignored for NDGI_FP32); the
+ *        decode writes nothing to it but its error word (see
+ *        ndgi_workspace_check) and its decoded-texel cache.
+ * FP16/BF16 gather: when the workspace has room for the cache and n >=
+ * feat_w * feat_h / 2 (many queries per feature texel), the call first
+ * decodes every BC4 texel of the map once into the FP16 cache and then
+ * blends each query's four taps from it in half2 arithmetic (the taps and
+ * fractions are those of the direct gather); otherwise each query decodes
+ * its taps' palette entries directly.  ndgi_decode_points_path tells which.
+ * Decodes that share a workspace and may overlap on the GPU race on its
+ * cache: serialise them on one stream, or give each stream its own
+ * workspace.
  * n == 0 is a no-op.  Non-finite coordinates give unspecified but in-bounds
  * results.
  */
 ndgi_status ndgi_decode_points(const ndgi_model_desc *model, ndgi_precision precision, const void *ws,
                                const float *uvt, int64_t n, float *rgb, void *stream);
+
+/*
+ * How ndgi_decode_points of n queries with this model and precision gathers:
+ * 0 directly (and for FP32), 1 through the decoded-texel cache with four
+ * lanes per SM that each gather and run their MMA chain, 2 through the cache
+ * with the warp-specialised kernel (per lane, a producer warpgroup gathers
+ * the next tile while a consumer warpgroup runs the MMA chain).
+ */
+int32_t ndgi_decode_points_path(const ndgi_model_desc *model, ndgi_precision precision, int64_t n);
 
 /*
  * Point decode from HOST buffers (the paper decodes on the device only;
@@ -236,6 +285,16 @@ ndgi_status ndgi_debug_features(const ndgi_model_desc *model, const float *uvt, 
  */
 ndgi_status ndgi_debug_features_tc(const ndgi_model_desc *model, const void *ws, const float *uvt, int64_t n,
                                    float *x, void *stream);
+
+/*
+ * The gather of the point decode's cache path alone, for validation: builds
+ * the decoded-texel cache in `ws` (FP16/BF16 workspace of a map whose cache
+ * fits; NDGI_ERR_UNSUPPORTED otherwise), then writes x [n][cs+ct] FP32: the
+ * half2 blend of the four cached taps (exactly the FP16 values the decode
+ * feeds the MLP) and the FP32 temporal feature.
+ */
+ndgi_status ndgi_debug_features_cache(const ndgi_model_desc *model, const void *ws, const float *uvt, int64_t n,
+                                      float *x, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Batched virtual-texture page decode (Sec. 3.5, supplement S3)           */
@@ -301,7 +360,8 @@ ndgi_status ndgi_pages_autotune(ndgi_pages_plan *plan, const ndgi_page_req *reqs
 /*
  * Synchronises `stream` and reads the plan's device error word into
  * *device_error (host; 0 = no request was rejected), then clears it.
- * Returns NDGI_ERR_DEVICE_CHECK if it was set.
+ * Returns NDGI_ERR_TIMEOUT if bit 4 (16: a tensor-core kernel's bounded
+ * barrier wait ran out) is set, else NDGI_ERR_DEVICE_CHECK if any bit is.
  */
 ndgi_status ndgi_pages_check(ndgi_pages_plan *plan, int32_t *device_error, void *stream);
 
@@ -325,6 +385,15 @@ ndgi_status ndgi_pages_plan_info(const ndgi_pages_plan *plan, int32_t info[4]);
  * shape; NDGI_ERR_INVALID_ARG for NDGI_FP32 plans or other ctas_per_sm.
  */
 ndgi_status ndgi_pages_plan_set_shape(ndgi_pages_plan *plan, int32_t ctas_per_sm, int32_t lanes, int32_t slots);
+
+/*
+ * Test hook for the timeout path (no paper counterpart): flags = 1 makes the
+ * plan's tensor-core decodes take their timeout path from a short wait on a
+ * barrier phase that nothing completes, before any MMA is issued (bit 4 of
+ * the plan's error word is set; output unspecified); 0 restores normal
+ * decodes.  Copies synchronously; FP32 plans ignore it.
+ */
+ndgi_status ndgi_pages_plan_set_debug(ndgi_pages_plan *plan, int32_t flags);
 
 /* Destroys the plan and its device block and graph.  NULL is a no-op. */
 ndgi_status ndgi_pages_plan_destroy(ndgi_pages_plan *plan);

@@ -58,18 +58,22 @@ SIGNATURES = [
     ("ndgi_version", C.c_char_p, []),
     ("ndgi_last_error", C.c_int, [C.c_char_p, _sz]),
     ("ndgi_check", C.c_int, [_vp]),
+    ("ndgi_workspace_check", C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    ("ndgi_debug_workspace_inject", C.c_int, [_vp, C.c_int, _vp, _i32, _vp]),
     ("ndgi_prepare_workspace_size", _sz, [_vp, C.c_int]),
     ("ndgi_prepare", C.c_int, [_vp, C.c_int, _vp, _sz, _vp]),
     ("ndgi_calibrate_fp8", C.c_int, [_vp, _vp, _i64, _vp, _vp]),
     ("ndgi_prepare_fp8", C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     ("ndgi_fp8_unpack", C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     ("ndgi_decode_points", C.c_int, [_vp, C.c_int, _vp, _vp, _i64, _vp, _vp]),
+    ("ndgi_decode_points_path", C.c_int32, [_vp, C.c_int, _i64]),
     ("ndgi_host_pipe_staging_size", _sz, [_i64]),
     ("ndgi_host_pipe_create", C.c_int, [_i64, _vp, _sz, _vp]),
     ("ndgi_decode_points_host", C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _i64, _vp, _vp]),
     ("ndgi_host_pipe_destroy", C.c_int, [_vp]),
     ("ndgi_debug_features", C.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     ("ndgi_debug_features_tc", C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
+    ("ndgi_debug_features_cache", C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
     ("ndgi_pages_plan_create", C.c_int, [_vp, _vp, _i32, C.c_int, _i32, _i32, _vp, _i64, _i64, _vp]),
     ("ndgi_decode_pages", C.c_int, [_vp, _vp, _vp, _vp]),
     ("ndgi_pages_autotune", C.c_int, [_vp, _vp, _vp, _i32, _vp]),
@@ -77,6 +81,7 @@ SIGNATURES = [
     ("ndgi_pages_plan_destroy", C.c_int, [_vp]),
     ("ndgi_pages_plan_info", C.c_int, [_vp, _vp]),
     ("ndgi_pages_plan_set_shape", C.c_int, [_vp, _i32, _i32, _i32]),
+    ("ndgi_pages_plan_set_debug", C.c_int, [_vp, _i32]),
     ("ndgi_decode_pages_static", C.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _i64, _i64, _vp, _vp]),
     ("ndgi_bc_pack", C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     ("ndgi_fit_forward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),

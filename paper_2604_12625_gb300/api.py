@@ -83,6 +83,20 @@ class Model:
         return self.ws[precision]
 
 
+def ndgi_workspace_check(model, precision, stream=None):
+    """(status, error word) of the point decodes that used the model's prepared workspace; clears the word."""
+    err = C.c_int32(0)
+    st = lib().ndgi_workspace_check(C.byref(model.desc), _prec(precision), _p(model.workspace(precision)),
+                                    C.byref(err), _stream(stream))
+    return st, err.value
+
+
+def ndgi_debug_workspace_inject(model, precision, flags, stream=None):
+    """Test hook: flags = 1 makes point decodes with this workspace take their timeout path; 0 = normal."""
+    check(lib().ndgi_debug_workspace_inject(C.byref(model.desc), _prec(precision), _p(model.workspace(precision)),
+                                            int(flags), _stream(stream)))
+
+
 def ndgi_version():
     return lib().ndgi_version().decode()
 
@@ -226,6 +240,23 @@ def ndgi_debug_features_tc(model, uvt, precision="fp16", stream=None):
     return x
 
 
+def ndgi_debug_features_cache(model, uvt, precision="fp16", stream=None):
+    """x [n][cs+ct] float32 of the cache path's gather (FP16 decoded-texel cache, half2 blend)."""
+    uvt = _need(uvt, torch.float32, "uvt")
+    n = uvt.shape[0]
+    x = torch.empty((n, model.cs + model.ct), dtype=torch.float32, device=uvt.device)
+    ws = model.workspace(precision)
+    check(lib().ndgi_debug_features_cache(C.byref(model.desc), _p(ws), _p(uvt), n, _p(x), _stream(stream)))
+    return x
+
+
+def ndgi_decode_points_path(model, precision, n):
+    """'direct', 'cache' (four-lane kernel) or 'cache_ws' (warp-specialised kernel): how a point decode of n
+    queries gathers."""
+    return ("direct", "cache", "cache_ws")[lib().ndgi_decode_points_path(C.byref(model.desc), _prec(precision),
+                                                                        int(n))]
+
+
 # ---------------------------------------------------------------------------
 # Pages
 # ---------------------------------------------------------------------------
@@ -283,6 +314,10 @@ class PagesPlan:
         err = C.c_int32(0)
         st = lib().ndgi_pages_check(self.handle, C.byref(err), _stream(stream))
         return st, err.value
+
+    def set_debug(self, flags):
+        """Test hook: 1 = the tensor-core decodes take their timeout path before any MMA; 0 = normal."""
+        check(lib().ndgi_pages_plan_set_debug(self.handle, int(flags)))
 
     def close(self):
         if self.handle:

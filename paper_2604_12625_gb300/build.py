@@ -61,7 +61,9 @@ def build(force=False, verbose=False, extra=()):
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(compile_one, jobs))
     objs = [os.path.join(objdir, os.path.basename(s) + ".o") for s in sources]
-    if jobs or force or not os.path.exists(LIB):
+    # relink when anything was compiled, or when an object is newer than the
+    # library (a previous link failed after its objects were built)
+    if jobs or force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -91,10 +91,49 @@ ndgi_status ndgi_check(void* stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "ndgi_check");
-  const int dev_err = tc_take_error();
-  if (dev_err < 0) return set_error(NDGI_ERR_CUDA, "ndgi_check: cannot read the device error word");
-  if (dev_err) return set_error(NDGI_ERR_TIMEOUT, "ndgi_check: a tensor-core barrier wait timed out (0x%x)", dev_err);
   return NDGI_OK;
+}
+
+// Writes one int of device memory on the stream (no host memory is read after the launch returns).
+__global__ void k_set_word(int* p, int v) { *p = v; }
+
+ndgi_status ndgi_workspace_check(const ndgi_model_desc* model, ndgi_precision precision, const void* ws,
+                                 int32_t* device_error, void* stream) {
+  ndgi_status st = check_model(model, "ndgi_workspace_check");
+  if (st != NDGI_OK) return st;
+  if ((precision != NDGI_FP16 && precision != NDGI_BF16) || !tc_supported(model->cs, model->ct, model->hidden))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_workspace_check: needs an FP16/BF16 workspace of a built shape");
+  if (!ws || !aligned(ws, 256)) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_workspace_check: ws missing or unaligned");
+  int* w = reinterpret_cast<int*>(static_cast<unsigned char*>(const_cast<void*>(ws)) +
+                                  tc_error_offset(model->cs, model->ct, model->hidden));
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t err = 0;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&err, w, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && err) {
+    k_set_word<<<1, 1, 0, s>>>(w, 0);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) return cuda_status(e, "ndgi_workspace_check");
+  if (device_error) *device_error = err;
+  if (err & kErrTimeout)
+    return set_error(NDGI_ERR_TIMEOUT, "ndgi_workspace_check: a tensor-core barrier wait timed out (0x%x)", err);
+  return NDGI_OK;
+}
+
+ndgi_status ndgi_debug_workspace_inject(const ndgi_model_desc* model, ndgi_precision precision, void* ws,
+                                        int32_t flags, void* stream) {
+  ndgi_status st = check_model(model, "ndgi_debug_workspace_inject");
+  if (st != NDGI_OK) return st;
+  if ((precision != NDGI_FP16 && precision != NDGI_BF16) || !tc_supported(model->cs, model->ct, model->hidden))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_debug_workspace_inject: needs an FP16/BF16 workspace");
+  if (!ws || !aligned(ws, 256) || (flags & ~kDbgInjectTimeout))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_debug_workspace_inject: bad workspace or flags");
+  int* w = reinterpret_cast<int*>(static_cast<unsigned char*>(ws) + tc_error_offset(model->cs, model->ct,
+                                                                                     model->hidden)) + 1;
+  k_set_word<<<1, 1, 0, (cudaStream_t)stream>>>(w, flags);
+  return cuda_status(cudaGetLastError(), "ndgi_debug_workspace_inject");
 }
 
 size_t ndgi_prepare_workspace_size(const ndgi_model_desc* model, ndgi_precision precision) {
@@ -184,8 +223,14 @@ ndgi_status ndgi_prepare(const ndgi_model_desc* model, ndgi_precision precision,
                      "ndgi_prepare");
 }
 
-ndgi_status ndgi_decode_points(const ndgi_model_desc* model, ndgi_precision precision, const void* ws,
-                               const float* uvt, int64_t n, float* rgb, void* stream) {
+}  // extern "C"
+
+namespace ndgi {
+
+// The point decode with an explicit gather policy (kPointsAuto for the ABI
+// call; the host-buffer pipe builds the decoded-texel cache once per call).
+ndgi_status decode_points_mode(const ndgi_model_desc* model, ndgi_precision precision, const void* ws,
+                               const float* uvt, int64_t n, float* rgb, void* stream, int mode) {
   ndgi_status st = check_model(model, "ndgi_decode_points");
   if (st != NDGI_OK) return st;
   if (n < 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_decode_points: n < 0");
@@ -202,12 +247,45 @@ ndgi_status ndgi_decode_points(const ndgi_model_desc* model, ndgi_precision prec
                        model->cs, model->ct, model->hidden);
     if (!ws || !aligned(ws, 256))
       return set_error(NDGI_ERR_INVALID_ARG, "ndgi_decode_points: ws (from ndgi_prepare) missing or unaligned");
-    return cuda_status(launch_tc_points(m, precision == NDGI_BF16, ws, uvt, n, rgb, (cudaStream_t)stream),
+    return cuda_status(launch_tc_points(m, precision == NDGI_BF16, ws, uvt, n, rgb, (cudaStream_t)stream, mode),
                        "ndgi_decode_points");
   }
   if (precision == NDGI_FP8_E4M3)
     return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_decode_points: FP8 is built for the page decode only");
   return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_decode_points: precision %d not supported", (int)precision);
+}
+
+}  // namespace ndgi
+
+extern "C" {
+
+ndgi_status ndgi_decode_points(const ndgi_model_desc* model, ndgi_precision precision, const void* ws,
+                               const float* uvt, int64_t n, float* rgb, void* stream) {
+  return decode_points_mode(model, precision, ws, uvt, n, rgb, stream, kPointsAuto);
+}
+
+int32_t ndgi_decode_points_path(const ndgi_model_desc* model, ndgi_precision precision, int64_t n) {
+  if (!model || (precision != NDGI_FP16 && precision != NDGI_BF16)) return 0;
+  if (!tc_supported(model->cs, model->ct, model->hidden)) return 0;
+  if (!tc_points_cache_path(to_dev(*model), n, kPointsAuto)) return 0;
+  return tc_points_ws_built(model->cs, model->ct, model->hidden) ? 2 : 1;
+}
+
+ndgi_status ndgi_debug_features_cache(const ndgi_model_desc* model, const void* ws, const float* uvt, int64_t n,
+                                      float* x, void* stream) {
+  ndgi_status st = check_model(model, "ndgi_debug_features_cache");
+  if (st != NDGI_OK) return st;
+  if (n < 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_debug_features_cache: n < 0");
+  if (n == 0) return NDGI_OK;
+  if (!uvt || !x || !ws || !aligned(ws, 256))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_debug_features_cache: NULL argument or unaligned workspace");
+  if (!tc_supported(model->cs, model->ct, model->hidden))
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_debug_features_cache: tensor-core shape not built");
+  const DevModel m = to_dev(*model);
+  if (!tc_points_cache_path(m, n, kPointsBuild))
+    return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_debug_features_cache: the map's cache exceeds 64 MiB");
+  return cuda_status(launch_debug_features_cache(m, ws, uvt, n, x, (cudaStream_t)stream),
+                     "ndgi_debug_features_cache");
 }
 
 ndgi_status ndgi_debug_features(const ndgi_model_desc* model, const float* uvt, int64_t n, float* x, int32_t* p35,
@@ -362,7 +440,7 @@ ndgi_status ndgi_pages_plan_create(const ndgi_model_desc* models, const void* co
   const size_t models_bytes = sizeof(DevModel) * n_models;
   const size_t ws_off = (models_bytes + 255) / 256 * 256;
   const size_t ctr_off = ws_off + (sizeof(void*) * n_models + 255) / 256 * 256;
-  const size_t total = ctr_off + 256;
+  const size_t total = ctr_off + 256;   // work counter at +0, error word at +64, debug word at +128
   cudaError_t e = cudaMalloc(&p->dblock, total);
   if (e != cudaSuccess) {
     delete p;
@@ -393,6 +471,7 @@ ndgi_status ndgi_pages_plan_create(const ndgi_model_desc* models, const void* co
   p->ctx.phys_h = phys_h;
   p->ctx.work_counter = reinterpret_cast<unsigned int*>(base + ctr_off);
   p->ctx.error_word = reinterpret_cast<int*>(base + ctr_off + 64);
+  p->ctx.debug_word = reinterpret_cast<const int*>(base + ctr_off + 128);
   p->simt_grid = num_sms() * 8;
   p->shape = tc_default_pages_shape();
   *plan = p;
@@ -465,8 +544,18 @@ ndgi_status ndgi_pages_check(ndgi_pages_plan* plan, int32_t* device_error, void*
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e, "ndgi_pages_check");
   if (device_error) *device_error = err;
+  if (err & kErrTimeout)
+    return set_error(NDGI_ERR_TIMEOUT, "ndgi_decode_pages: a tensor-core barrier wait timed out (0x%x)", err);
   if (err) return set_error(NDGI_ERR_DEVICE_CHECK, "ndgi_decode_pages: device checks rejected requests (0x%x)", err);
   return NDGI_OK;
+}
+
+ndgi_status ndgi_pages_plan_set_debug(ndgi_pages_plan* plan, int32_t flags) {
+  if (!plan || (flags & ~kDbgInjectTimeout))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_set_debug: bad plan or flags");
+  const int v = flags;
+  return cuda_status(cudaMemcpy(const_cast<int*>(plan->ctx.debug_word), &v, sizeof(int), cudaMemcpyHostToDevice),
+                     "ndgi_pages_plan_set_debug");
 }
 
 ndgi_status ndgi_pages_plan_info(const ndgi_pages_plan* plan, int32_t info[4]) {

@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "ndgi_internal.h"
+#include "tc_decode.h"
 
 namespace {
 constexpr int kBufs = 3;
@@ -128,6 +129,11 @@ ndgi_status ndgi_decode_points_host(ndgi_host_pipe* p, const ndgi_model_desc* mo
   NDGI_TRY(cudaStreamWaitEvent(p->in, p->start, 0));
   NDGI_TRY(cudaStreamWaitEvent(p->out, p->start, 0));
   if (p->used) NDGI_TRY(cudaStreamWaitEvent(p->in, p->fin, 0));
+  // the decoded-texel cache (when the whole call qualifies) is built once, by
+  // the first chunk's decode, and reused by the others on the same stream
+  const bool cached = (precision == NDGI_FP16 || precision == NDGI_BF16) && model &&
+                      tc_supported(model->cs, model->ct, model->hidden) &&
+                      tc_points_cache_path(to_dev(*model), n, kPointsAuto);
   int64_t off = 0;
   for (int64_t k = 0; off < n; ++k) {
     const int b = (int)(k % kBufs);
@@ -139,7 +145,8 @@ ndgi_status ndgi_decode_points_host(ndgi_host_pipe* p, const ndgi_model_desc* mo
     NDGI_TRY(cudaMemcpyAsync(q_dev, uvt_host + 3 * off, (size_t)len * 12, cudaMemcpyHostToDevice, p->in));
     NDGI_TRY(cudaEventRecord(p->loaded[b], p->in));
     NDGI_TRY(cudaStreamWaitEvent(s, p->loaded[b], 0));
-    const ndgi_status st = ndgi_decode_points(model, precision, ws, q_dev, len, r_dev, stream);
+    const int mode = cached ? (k == 0 ? kPointsBuild : kPointsReuse) : kPointsDirect;
+    const ndgi_status st = decode_points_mode(model, precision, ws, q_dev, len, r_dev, stream, mode);
     if (st != NDGI_OK) return fail(st);
     NDGI_TRY(cudaEventRecord(p->decoded[b], s));
     NDGI_TRY(cudaStreamWaitEvent(p->out, p->decoded[b], 0));

@@ -44,6 +44,10 @@ int num_sms();
 // Host-side checks of a model descriptor common to every decode (NDGI_OK or the status it set).
 ndgi_status check_model(const ndgi_model_desc* m, const char* who);
 
+// The point decode with an explicit gather policy (a kPoints* value of tc_decode.h).
+ndgi_status decode_points_mode(const ndgi_model_desc* model, ndgi_precision precision, const void* ws,
+                               const float* uvt, int64_t n, float* rgb, void* stream, int mode);
+
 // ---- FP32 CUDA-core decode (decode_simt.cu) ----
 bool simt_supported(int cs, int ct, int hidden);
 cudaError_t launch_points_f32(const DevModel& m, const float* uvt, int64_t n, float* rgb, cudaStream_t s);
@@ -61,8 +65,17 @@ struct PagesCtx {
   void* phys;
   int64_t phys_w, phys_h;
   unsigned int* work_counter;   // device
-  int* error_word;              // device
+  int* error_word;              // device: bits 0-3 rejected requests, kErrTimeout a timed-out wait
+  const int* debug_word;        // device or NULL: bit 0 makes the tensor-core kernels' first wait run out
 };
+
+// Error-word bit latched by a tensor-core kernel whose bounded wait ran out
+// (pages: in the plan's error word; points: in the prepared workspace's word).
+constexpr int kErrTimeout = 16;
+// Debug-word bit: each lane's first wait uses a short limit on a barrier that
+// nothing arrives at, before any MMA is issued or tensor memory is touched by
+// an MMA, so the kernel takes its timeout path (test of that path).
+constexpr int kDbgInjectTimeout = 1;
 cudaError_t launch_pages_f32(const PagesCtx& c, int cs, int ct, int hidden, const ndgi_page_req* reqs,
                              const int32_t* n_dev, int grid, cudaStream_t s);
 

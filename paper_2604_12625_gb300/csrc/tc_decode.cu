@@ -40,187 +40,11 @@
 // bits of each bias.
 //
 // Every mbarrier wait is bounded; a timeout is latched in a device error word
-// that ndgi_check reports, and the CTA unwinds and frees its tensor memory.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
-#include <algorithm>
-#include <cstring>
-#include <type_traits>
-
-#include "ndgi_internal.h"
-#include "bc4.cuh"
-#include "gather.cuh"
-#include "tc_decode.h"
-#include "umma.cuh"
+// the caller owns (the prepared workspace for points, the plan's block for
+// pages), and the CTA unwinds and frees its tensor memory.
+#include "tc_engine.cuh"
 
 namespace ndgi {
-
-// Device error word of the tensor-core kernels (bit 0: an mbarrier wait timed out).
-static __device__ int g_tc_error;
-
-constexpr int kLaneThreads = 128;
-
-// Operand kinds of the tensor-core decode.
-constexpr int kF16 = 0, kBF16 = 1, kE4M3 = 2;
-
-// ---------------------------------------------------------------------------
-// Weight image (built by ndgi_prepare), identical layout in global and shared
-// memory so a CTA copies it with 16-byte loads.
-// ---------------------------------------------------------------------------
-template <int CS, int CT, int H>
-struct TcLayout {
-  static constexpr int CIN = CS + CT;
-  static constexpr int K1P = ((CIN + 1 + 15) / 16) * 16;   // points: inputs + ones column (b1)
-  static constexpr int K1G = ((CS + 2 + 15) / 16) * 16;    // pages: spatial channels + two ones columns (b1' hi, lo)
-  static constexpr int K2 = H + 16;                        // hidden + ones column (b2 / b3)
-  static constexpr int N3 = 16;                            // output layer N (3 used)
-  static constexpr uint32_t kB2 = 0;                       // [H][K2]     K-major, column H = b2
-  static constexpr uint32_t kB3 = kB2 + H * K2 * 2;        // [16][K2]    rows 3..15 zero, column H = b3
-  static constexpr uint32_t kShared = kB3 + N3 * K2 * 2;   // end of the part both kernels use
-  static constexpr uint32_t kB1P = kShared;                // [H][K1P]    points layer 1, column CIN = b1
-  static constexpr uint32_t kB1G = kB1P + H * K1P * 2;     // [H][K1G]    pages layer 1 (spatial; bias columns per request)
-  static constexpr uint32_t kW1T = kB1G + H * K1G * 2;     // [CT][H] f32 stored temporal weights
-  static constexpr uint32_t kB1 = kW1T + CT * H * 4;       // [H] f32 stored b1
-  static constexpr uint32_t kWsBytes = kB1 + H * 4;
-  static constexpr uint32_t kSliceOff = (kWsBytes + 255) / 256 * 256;   // then the texel-sliced BC4 copy (points)
-  static constexpr int EB = 2;                             // bytes per operand element
-  static constexpr uint32_t kTmemCols = H <= 32 ? 32 : (H <= 64 ? 64 : 128);
-  static_assert(H % 16 == 0 && H <= 128, "hidden width must be a multiple of 16, at most 128");
-  static_assert(kShared % 16 == 0 && kB1G % 16 == 0 && kW1T % 16 == 0, "16-byte granular image");
-};
-
-// FP8 scales of one model (the tail of its FP8 image), all powers of two:
-// layer-1 inputs are quantised in units a1, layer-1 outputs (= layer-2
-// inputs) are in units a2, the RGB accumulator in units `out`.
-struct Fp8Scales {
-  float a1, inv_a1, inv_a2, out;
-  uint32_t ones2, ones3;   // A-side ones word of layers 2 / 3: E4M3 code of v in bytes 0..2, byte 3 zero
-  float a2;
-  uint32_t status;         // bit 0: a bias needs a ones value above 256; bit 1: 1/a1 too large for FP16
-  float s1, s2, s3, a3;    // weight scales and the layer-2 output unit
-  float v2, v3, pad0, pad1;
-};
-static_assert(sizeof(Fp8Scales) == 64, "FP8 scale block");
-
-// FP8 (E4M3) image for the page decode: one-byte codes, a K step of 32.
-// Layer 1 contracts the 16 spatial channels plus three ones columns that
-// carry the per-request bias b1' (K = 32); layers 2 and 3 carry their biases
-// the same way in K2 = H + 32.
-template <int CS, int CT, int H>
-struct TcLayout8 {
-  static constexpr int EB = 1;
-  static constexpr int K1G = 32;
-  static constexpr int K2 = H + 32;
-  static constexpr int N3 = 16;
-  static constexpr uint32_t kB2 = 0;                       // [H][K2]  codes of W2^T / s2; columns H..H+2 = b2 terms
-  static constexpr uint32_t kB3 = kB2 + H * K2;            // [16][K2] codes of W3^T / s3; columns H..H+2 = b3 terms
-  static constexpr uint32_t kShared = kB3 + N3 * K2;
-  static constexpr uint32_t kB1G = kShared;                // [H][K1G] codes of W1_s^T / s1; b1' terms per request
-  static constexpr uint32_t kW1T = kB1G + H * K1G;         // [CT][H] f32 stored temporal weights s1 e4m3(W1_t / s1)
-  static constexpr uint32_t kB1 = kW1T + CT * H * 4;       // [H] f32 b1
-  static constexpr uint32_t kScale = kB1 + H * 4;          // Fp8Scales
-  static constexpr uint32_t kWsBytes = kScale + sizeof(Fp8Scales);
-  static constexpr uint32_t kSliceOff = (kWsBytes + 255) / 256 * 256;   // then the texel-sliced BC4 copy
-  static_assert(CS + 3 <= K1G && H % 32 == 0 && H <= 128, "FP8 pages: cs <= 29, hidden a multiple of 32");
-  static_assert(kShared % 16 == 0 && kW1T % 16 == 0 && kScale % 16 == 0 && kWsBytes % 16 == 0, "granularity");
-};
-
-// ---- E4M3 helpers ----------------------------------------------------------
-// Two floats -> two E4M3 codes (nearest even, saturating at +-448), `lo` in bits 0..7.
-__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
-  uint16_t d;
-  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
-  return d;
-}
-__device__ __forceinline__ uint32_t e4m3x2_relu(float lo, float hi) {
-  uint16_t d;
-  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
-  return d;
-}
-// Packed half2 -> two E4M3 codes, the low half in bits 0..7.
-__device__ __forceinline__ uint32_t e4m3x2_h(uint32_t h2) {
-  uint16_t d;
-  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(d) : "r"(h2));
-  return d;
-}
-// Value of an E4M3 code, from the format (exact in FP32): exponent field e,
-// mantissa m: (1 + m/8) 2^(e-7), or m/8 2^-6 when e = 0.
-__device__ __forceinline__ float e4m3_value(uint32_t c) {
-  const uint32_t e = (c >> 3) & 15u, m = c & 7u;
-  const float v = e == 0 ? (float)m * 0x1p-9f : __uint_as_float(((e + 120u) << 23) | (m << 20));
-  return (c & 0x80u) ? -v : v;
-}
-// Smallest power of two P with y <= 448 P (1 for y <= 0 or not finite); the
-// comparisons are exact.
-__device__ float fp8_p2(float y) {
-  if (!(y > 0.0f) || !(y <= 3.4e38f)) return 1.0f;
-  int e;
-  frexpf(y / 448.0f, &e);
-  float P = ldexpf(1.0f, e);
-  while (y > 448.0f * P) P *= 2.0f;
-  while (y <= 448.0f * (P * 0.5f)) P *= 0.5f;
-  return P;
-}
-// beta / v as three E4M3 terms t1 + t2 + t3 (each the rounding of what the
-// previous terms left; the residuals are exact in FP32): codes in bytes 0..2.
-__device__ uint32_t fp8_terms(float beta, float v) {
-  const float r0 = beta * (1.0f / v);
-  const uint32_t c1 = e4m3x2(r0, 0.0f) & 0xFFu;
-  const float r1 = __fsub_rn(r0, e4m3_value(c1));
-  const uint32_t c2 = e4m3x2(r1, 0.0f) & 0xFFu;
-  const float r2 = __fsub_rn(r1, e4m3_value(c2));
-  const uint32_t c3 = e4m3x2(r2, 0.0f) & 0xFFu;
-  return c1 | (c2 << 8) | (c3 << 16);
-}
-// E4M3 code of a power of two 2^k, k in -6..8.
-__device__ __forceinline__ uint32_t e4m3_pow2_code(float v) {
-  int e;
-  frexpf(v, &e);
-  return (uint32_t)(e - 1 + 7) << 3;
-}
-
-template <bool BF16>
-__device__ __forceinline__ uint16_t to_bits(float x) {
-  if (BF16) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    return *reinterpret_cast<const uint16_t*>(&h);
-  }
-  const __half h = __float2half_rn(x);
-  return *reinterpret_cast<const uint16_t*>(&h);
-}
-
-template <bool BF16>
-__device__ __forceinline__ float round_stored(float x) {
-  if (BF16) return __bfloat162float(__float2bfloat16_rn(x));
-  return __half2float(__float2half_rn(x));
-}
-
-// Two floats -> packed pair, `lo` in the low half.
-template <bool BF16>
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  uint32_t d;
-  if (BF16) asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  else asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  return d;
-}
-// Same with ReLU fused into the conversion.
-template <bool BF16>
-__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
-  uint32_t d;
-  if (BF16) asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  else asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  return d;
-}
-
-// Stored b3 of an FP16/BF16 image (column H of the B3 tile) as FP32.
-template <bool BF16>
-__device__ __forceinline__ float stored_b3(const unsigned char* b3_img, int n, int H, int K2) {
-  const uint16_t b = *reinterpret_cast<const uint16_t*>(b3_img + kmajor_offset(n, H, K2));
-  if (BF16) return __uint_as_float((uint32_t)b << 16);
-  return __half2float(__ushort_as_half(b));
-}
-
 template <int CS, int CT, int H, bool BF16>
 __global__ void k_tc_prepare(DevModel m, unsigned char* __restrict__ ws) {
   using L = TcLayout<CS, CT, H>;
@@ -248,6 +72,10 @@ __global__ void k_tc_prepare(DevModel m, unsigned char* __restrict__ ws) {
   for (int i = tid; i < CT * H; i += nt)
     reinterpret_cast<float*>(ws + L::kW1T)[i] = round_stored<BF16>(m.w1[(CS + i / H) * H + i % H]);
   for (int i = tid; i < H; i += nt) reinterpret_cast<float*>(ws + L::kB1)[i] = round_stored<BF16>(m.b1[i]);
+  if (tid == 0) {
+    *reinterpret_cast<int*>(ws + L::kErrOff) = 0;
+    *reinterpret_cast<int*>(ws + L::kDbgOff) = 0;
+  }
 }
 
 // FP8 image from the FP32 master weights and the calibration maxima
@@ -338,495 +166,6 @@ __global__ void __launch_bounds__(256) k_tc_prepare8(DevModel m, float m1, float
     reinterpret_cast<float*>(ws + L::kW1T)[i] =
         s1 * e4m3_value(e4m3x2(m.w1[(CS + i / H) * H + i % H] * (1.0f / s1), 0.0f) & 0xFFu);
   for (int i = tid; i < H; i += 256) reinterpret_cast<float*>(ws + L::kB1)[i] = m.b1[i];
-}
-
-// ---------------------------------------------------------------------------
-// tcgen05 helpers specific to this file
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr));
-}
-// Barrier over the 128 threads of lane `wg` (ids 1.. ; 0 is __syncthreads).
-__device__ __forceinline__ void lane_sync(int wg) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + wg), "r"(kLaneThreads) : "memory");
-}
-// Lane barrier that also returns whether any of the lane's threads passed v = true.
-__device__ __forceinline__ bool lane_any(int wg, bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, %2, %3, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(1 + wg), "r"(kLaneThreads)
-      : "memory");
-  return r != 0;
-}
-constexpr uint32_t tmem_alloc_cols(int cols) {
-  return cols <= 32 ? 32u : (cols <= 64 ? 64u : (cols <= 128 ? 128u : (cols <= 256 ? 256u : 512u)));
-}
-
-// ---------------------------------------------------------------------------
-// One lane's MLP engine with SL tile slots.
-//
-// A slot is one 128-row tile in flight: a region of tensor memory and an
-// mbarrier.  Its columns (FP16 example, H = 64):
-//   [0, H)             accumulator D of layers 1 and 2 (FP32)
-//   [H, H + K2/2)      A operand of layer 2 (ReLU(H1), then the ones column
-//                      that carries b2 in the K padding) and of layer 3
-//                      (ReLU(H2) only: b3 is added when D3 is read)
-//   [kD3Col, +16)      layer-3 accumulator (N = 16, 3 used)
-//   [kA1Col, ...)      A operand of layer 1 (features, bias ones columns)
-// Layer 3 of a tile and layer 1 of the slot's next tile touch disjoint
-// columns, so they are issued back to back under one commit: a tile costs
-// two MMA round trips (layer 1 with the previous tile's layer 3, then
-// layer 2), not three.  D3 shares columns with the tail of the layer-2 A
-// region only across time: each thread reads its D3 row before it writes
-// its next layer-2 row.
-// All operands but the small weight tiles B live in tensor memory, written
-// from registers with tcgen05.st.  Every thread of the lane waits on the
-// slot's mbarrier itself (no barrier round trip after completion); a wait
-// that times out is carried to the lane's next barrier, where the lane
-// decides uniformly to stop.  The thread that issues (one per lane, in a
-// different warp of each lane so the four issuers sit on different SM
-// sub-partitions) waits like the others.
-// P: kF16 / kBF16 (kind::f16, K step 16) or kE4M3 (kind::f8f6f4, K step 32);
-// either way a K step is 32 bytes of a row: 8 TMEM columns, 256 B of B.
-// E4M3 keeps b3 in the K padding (three E4M3 terms), as for layer 2.
-// ---------------------------------------------------------------------------
-constexpr uint64_t kDescK = 256 >> 4;   // B descriptor start-address step per K step (256 B)
-
-template <int H, int P, int K1, int SL>
-struct Engine {
-  static constexpr bool BF16 = P == kBF16, F8 = P == kE4M3;
-  static constexpr int KS = F8 ? 32 : 16;                    // K elements per MMA
-  static constexpr int EB = F8 ? 1 : 2;                      // bytes per element
-  static constexpr int K2 = H + KS;                          // layer 2: hidden + the bias K step
-  static constexpr int K3 = F8 ? K2 : H;                     // layer 3 (FP16/BF16: b3 added on read)
-  static constexpr uint32_t kACol = H;                       // hidden A region starts after D
-  static constexpr int kA1Words = K1 * EB / 4;               // 32-bit words of a layer-1 row
-  static constexpr uint32_t kA2End = kACol + K2 * EB / 4;   // end of the hidden A region
-  // Merged layout: D3 after the layer-3 A columns, the layer-1 rows after D3.
-  static constexpr uint32_t kD3Merged = (kACol + K3 * EB / 4 + 15) / 16 * 16;
-  static constexpr uint32_t kA1Merged = kD3Merged + 16 > kA2End ? kD3Merged + 16 : kA2End;
-  // Layer 3 is merged with the next tile's layer 1 only when that layout
-  // fits a quarter of the SM's tensor memory (the kernels run four slots per
-  // CTA); otherwise D3 goes to D's columns and the layer-1 rows follow the
-  // hidden A region.  Not merged: 32 inputs at H = 64.
-  static constexpr bool kMerge = kA1Merged + kA1Words <= 128;
-  static constexpr uint32_t kD3Col = kMerge ? kD3Merged : 0u;
-  static constexpr uint32_t kA1Col = kMerge ? kA1Merged : kA2End;
-  static constexpr uint32_t kSlotCols = tmem_alloc_cols(kA1Col + kA1Words);
-  static_assert(!F8 || H % 32 == 0, "FP8 epilogue works on 32-column chunks");
-  int wg, t, it;         // lane, thread in lane, the lane's issuing thread
-  bool late;             // a wait of this thread timed out
-  uint32_t tmem[SL];     // slot base, lane 0
-  uint32_t lane_off;     // this warp's lane quadrant, in the TMEM address
-  uint64_t* bar[SL];
-  uint32_t phase[SL];
-  uint64_t db1, db2, db3;
-  const float* b3;       // shared: stored b3 (FP16/BF16)
-
-  template <int KSTEPS, int N>
-  __device__ __forceinline__ void mma(int s, uint32_t d_col, uint32_t a_col, uint64_t b_desc) {
-#pragma unroll
-    for (int ks = 0; ks < KSTEPS; ++ks) {
-      if constexpr (F8)
-        umma_f8_ts(tmem[s] + d_col, tmem[s] + a_col + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, false),
-                   ks > 0 ? 1u : 0u);
-      else
-        umma_f16_ts(tmem[s] + d_col, tmem[s] + a_col + 8u * ks, b_desc + kDescK * ks, idesc_f16(128, N, BF16),
-                    ks > 0 ? 1u : 0u);
-    }
-  }
-  // Make this lane's tcgen05.st writes visible and meet at the lane barrier;
-  // false (uniform over the lane) if any of its threads saw a wait time out.
-  __device__ __forceinline__ bool publish() {
-    tmem_st_wait();
-    tc_fence_before();
-    return !lane_any(wg, late);
-  }
-  __device__ __forceinline__ bool layer1(int s) {
-    if (!publish()) return false;
-    if (t == it) {
-      tc_fence_after();
-      mma<K1 / KS, H>(s, 0u, kA1Col, db1);
-      umma_commit(bar[s]);
-    }
-    return true;
-  }
-  __device__ __forceinline__ bool layer2(int s) {
-    if (!publish()) return false;
-    if (t == it) {
-      tc_fence_after();
-      mma<K2 / KS, H>(s, 0u, kACol, db2);
-      umma_commit(bar[s]);
-    }
-    return true;
-  }
-  // Layer 3 of the slot's tile and, if `next` (lane-uniform; only with
-  // kMerge), layer 1 of the slot's next tile, whose rows are already in the
-  // layer-1 columns.
-  __device__ __forceinline__ bool layer3(int s, bool next) {
-    if (!publish()) return false;
-    if (t == it) {
-      tc_fence_after();
-      mma<K3 / KS, 16>(s, kD3Col, kACol, db3);
-      if (kMerge && next) mma<K1 / KS, H>(s, 0u, kA1Col, db1);
-      umma_commit(bar[s]);
-    }
-    return true;
-  }
-  // Waits (bounded) for slot s's MMAs; returns this thread's own result,
-  // which callers use for bookkeeping only (never to branch the lane).
-  __device__ __forceinline__ bool wait(int s) {
-    const bool ok = mbar_wait(bar[s], phase[s]);
-    if (ok) phase[s] ^= 1u;
-    late = late || !ok;
-    tc_fence_after();
-    return ok;
-  }
-  // Layer-1 row of this thread: kA1Words packed words (once the slot's
-  // previous layer-1 MMA has completed).
-  __device__ __forceinline__ void write_a1(int s, const uint32_t* w) {
-    const uint32_t a = tmem[s] + lane_off + kA1Col;
-#pragma unroll
-    for (int c = 0; c < kA1Words; c += 8) {
-      if (c + 16 <= kA1Words && (c % 16) == 0) {
-        uint32_t r[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) r[j] = w[c + j];
-        tmem_st16(a + c, r);
-        c += 8;
-      } else {
-        uint32_t r[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) r[j] = w[c + j];
-        tmem_st8(a + c, r);
-      }
-    }
-  }
-  // Slot s: this thread's row of D -> ReLU -> FP16/BF16/E4M3 -> the hidden A
-  // tile; with ONES also the bias ones columns (for FP8 `ones` holds the
-  // three codes of the next layer's ones value; FP16/BF16 use 1.0).
-  template <bool ONES>
-  __device__ __forceinline__ void epilogue(int s, uint32_t ones = 0u) {
-    const uint32_t d = tmem[s] + lane_off, a = d + kACol;
-    if constexpr (F8) {
-#pragma unroll
-      for (int c = 0; c < H; c += 32) {
-        uint32_t r[32], w[8];
-        tmem_ld32(d + c, r);
-        tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          w[j] = e4m3x2_relu(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1])) |
-                 (e4m3x2_relu(__uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])) << 16);
-        tmem_st8(a + c / 4, w);
-      }
-      if constexpr (ONES) {
-        const uint32_t ow[8] = {ones, 0, 0, 0, 0, 0, 0, 0};
-        tmem_st8(a + H / 4, ow);
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < H; c += 32) {
-        if (H - c >= 32) {
-          uint32_t r[32], w[16];
-          tmem_ld32(d + c, r);
-          tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-          tmem_st16(a + c / 2, w);
-        } else {
-          uint32_t r[16], w[8];
-          tmem_ld16(d + c, r);
-          tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-          tmem_st8(a + c / 2, w);
-        }
-      }
-      if constexpr (ONES) {
-        const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
-        const uint32_t ow[8] = {one, 0, 0, 0, 0, 0, 0, 0};
-        tmem_st8(a + H / 2, ow);
-      }
-    }
-  }
-  // The same in 16-column chunks (fewer live registers; FP16/BF16 only).
-  template <bool ONES>
-  __device__ __forceinline__ void epilogue16(int s) {
-    static_assert(!F8 && H % 16 == 0, "16-column FP16/BF16 epilogue");
-    const uint32_t d = tmem[s] + lane_off, a = d + kACol;
-#pragma unroll
-    for (int c = 0; c < H; c += 16) {
-      uint32_t r[16], w[8];
-      tmem_ld16(d + c, r);
-      tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < 8; ++j) w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-      tmem_st8(a + c / 2, w);
-    }
-    if constexpr (ONES) {
-      const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
-      const uint32_t ow[8] = {one, 0, 0, 0, 0, 0, 0, 0};
-      tmem_st8(a + H / 2, ow);
-    }
-  }
-  // Slot s after layer 3: this thread's RGB (FP16/BF16: + stored b3; E4M3:
-  // still in the output unit, the caller scales it).
-  __device__ __forceinline__ void output(int s, float& y0, float& y1, float& y2) {
-    uint32_t r[4];
-    tmem_ld4(tmem[s] + lane_off + kD3Col, r);
-    tmem_ld_wait();
-    y0 = __uint_as_float(r[0]);
-    y1 = __uint_as_float(r[1]);
-    y2 = __uint_as_float(r[2]);
-    if constexpr (!F8) {
-      y0 += b3[0];
-      y1 += b3[1];
-      y2 += b3[2];
-    }
-  }
-};
-
-// CTA set-up: TMEM for all slots, one mbarrier per slot.
-template <int NSLOTS, int COLS>
-__device__ __forceinline__ uint32_t cta_setup(uint64_t* bars, uint32_t* slot, int tid) {
-  if ((tid >> 5) == 0) {
-    tmem_alloc(slot, tmem_alloc_cols(NSLOTS * COLS));
-    tmem_relinquish();
-  }
-  if (tid == 0) {
-    for (int i = 0; i < NSLOTS; ++i) mbar_init(&bars[i], 1);
-    mbar_fence_init();
-  }
-  fence_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  return *slot;
-}
-
-// CTA end.  A thread whose wait timed out latches the error word; the issuer
-// of each lane first waits (bounded) for the MMAs it has not seen complete,
-// so the tensor memory is freed with nothing in flight.
-template <int NSLOTS, int COLS, typename E, int SL>
-__device__ __forceinline__ void cta_teardown(uint32_t tbase, E& e, const bool (&inflight)[SL], bool timed_out,
-                                             int tid) {
-  if (timed_out || e.late) atomicOr(&g_tc_error, 1);
-  if (e.t == e.it) {
-    for (int s = 0; s < SL; ++s)
-      if (inflight[s] && !mbar_wait(e.bar[s], e.phase[s])) atomicOr(&g_tc_error, 1);
-  }
-  tc_fence_before();
-  __syncthreads();
-  if ((tid >> 5) == 0) {
-    tc_fence_after();
-    tmem_dealloc(tbase, tmem_alloc_cols(NSLOTS * COLS));
-  }
-}
-
-__device__ __forceinline__ void copy16(unsigned char* dst, const unsigned char* src, uint32_t bytes, int tid,
-                                       int nthreads) {
-  for (uint32_t i = tid * 16; i < bytes; i += nthreads * 16)
-    *reinterpret_cast<uint4*>(dst + i) = *reinterpret_cast<const uint4*>(src + i);
-}
-
-template <int H, int P, int K1, int SL>
-__device__ __forceinline__ void engine_init(Engine<H, P, K1, SL>& e, uint32_t tbase, uint64_t* bars, int tid,
-                                            uint32_t b1_smem, uint32_t b2_smem, uint32_t b3_smem) {
-  using E = Engine<H, P, K1, SL>;
-  e.wg = tid >> 7;
-  e.t = tid & (kLaneThreads - 1);
-  e.it = 32 * (e.wg & 3);
-  e.late = false;
-  e.b3 = nullptr;
-  e.lane_off = (uint32_t)(((e.t >> 5) * 32) << 16);
-#pragma unroll
-  for (int s = 0; s < SL; ++s) {
-    e.tmem[s] = tbase + (uint32_t)((SL * e.wg + s) * E::kSlotCols);
-    e.bar[s] = &bars[SL * e.wg + s];
-    e.phase[s] = 0;
-  }
-  e.db1 = sdesc(b1_smem, 128u, K1 * E::EB * 8u);       // 8-row group stride: (row bytes / 16) x 128 B
-  e.db2 = sdesc(b2_smem, 128u, E::K2 * E::EB * 8u);
-  e.db3 = sdesc(b3_smem, 128u, E::K2 * E::EB * 8u);
-}
-
-// ---------------------------------------------------------------------------
-// Random-access points
-// ---------------------------------------------------------------------------
-template <int CS, int CT, int H>
-struct PointsSmem {
-  using L = TcLayout<CS, CT, H>;
-  static constexpr uint32_t kW = 0;                                  // shared part of the image
-  static constexpr uint32_t kB1 = kW + L::kShared;                   // points B1
-  static constexpr uint32_t kLut = kB1 + H * L::K1P * 2;             // 16 x uint2 palette table
-  static constexpr uint32_t kBytes = kLut + 128;
-};
-
-// Layer-1 words of one query: features, the ones column for b1, zeros.
-template <int CIN, int K1, bool BF16>
-__device__ __forceinline__ void pack_a1(const float (&x)[CIN], uint32_t (&w)[K1 / 2]) {
-#pragma unroll
-  for (int j = 0; j < K1 / 2; ++j) {
-    float v[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int k = 2 * j + e;
-      v[e] = k < CIN ? x[k < CIN ? k : 0] : (k == CIN ? 1.0f : 0.0f);
-    }
-    w[j] = pack2<BF16>(v[0], v[1]);
-  }
-}
-
-template <int CS, int CT, int H, bool BF16, int NWG, int SL>
-__global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_points_tc(DevModel m, const unsigned char* __restrict__ ws,
-                                                                    const float* __restrict__ uvt, int64_t n,
-                                                                    float* __restrict__ rgb) {
-  using L = TcLayout<CS, CT, H>;
-  using S = PointsSmem<CS, CT, H>;
-  constexpr int P = BF16 ? kBF16 : kF16;
-  using E = Engine<H, P, L::K1P, SL>;
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint64_t bars[SL * NWG];
-  __shared__ uint32_t slot;
-  const int tid = threadIdx.x;
-  copy16(sm + S::kW, ws, L::kShared, tid, kLaneThreads * NWG);
-  copy16(sm + S::kB1, ws + L::kB1P, H * L::K1P * 2, tid, kLaneThreads * NWG);
-  const uint2* lut = reinterpret_cast<const uint2*>(sm + S::kLut);
-  init_p35_lut_sliced(reinterpret_cast<uint2*>(sm + S::kLut), tid);
-  const uint8_t* sliced = ws + L::kSliceOff;
-  __shared__ float s_b3[3];
-  if (tid < 3) s_b3[tid] = stored_b3<BF16>(ws + L::kB3, tid, H, L::K2);
-  const uint32_t tbase = cta_setup<SL * NWG, E::kSlotCols>(bars, &slot, tid);
-  const uint32_t base = smem_addr(sm);
-  E e;
-  engine_init<H, P, L::K1P, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
-  const int t = e.t;
-  // inflight[s]: slot s has MMAs issued and not yet waited for.
-  bool inflight[SL], timed_out = false;
-#pragma unroll
-  for (int s = 0; s < SL; ++s) inflight[s] = false;
-  const int64_t tiles = (n + 127) / 128;
-  const int64_t lanes = (int64_t)gridDim.x * NWG, lane_id = (int64_t)blockIdx.x * NWG + e.wg;
-  const int64_t qstep = (int64_t)SL * lanes * 128;   // from a slot's tile to its next tile, per query
-  // Each slot's next query coordinates are loaded one tile ahead, so their
-  // DRAM latency overlaps the current tile.  (Prefetching the next tile's
-  // block lines into L1 as well measured 6% slower.)
-  float nu[SL], nv[SL], nt[SL];
-#pragma unroll
-  for (int s = 0; s < SL; ++s) {
-    const int64_t q0 = (lane_id + (int64_t)s * lanes) * 128 + t;
-    nu[s] = nv[s] = nt[s] = 0.0f;
-    if (q0 < n) {
-      nu[s] = __ldcs(uvt + 3 * q0);
-      nv[s] = __ldcs(uvt + 3 * q0 + 1);
-      nt[s] = __ldcs(uvt + 3 * q0 + 2);
-    }
-  }
-  // One tile in flight per lane, software-pipelined: the next tile's gather
-  // runs while this tile's layer 2 is on the tensor core, and its layer 1 is
-  // issued with this tile's layer 3 (two MMA round trips per tile):
-  //   [wait: layer 1 (+ previous layer 3)] [previous RGB out] [ReLU -> layer 2]
-  //   [gather the next tile] [wait: layer 2] [ReLU -> layer 3 + next layer 1]
-  static_assert(SL == 1, "the point decode pipelines one tile per lane");
-  static_assert(SL * NWG * E::kSlotCols <= 512, "slots exceed the SM's tensor memory");
-  e.b3 = s_b3;
-  // Gathers tile `tl` into the slot's layer-1 columns (their previous MMA has completed).
-  auto produce = [&](int64_t tl) {
-    const int64_t q = tl * 128 + t, qn = q + qstep;
-    const float qu = nu[0], qv = nv[0], qt = nt[0];
-    if (qn < n) {
-      nu[0] = __ldcs(uvt + 3 * qn);
-      nv[0] = __ldcs(uvt + 3 * qn + 1);
-      nt[0] = __ldcs(uvt + 3 * qn + 2);
-    }
-    float x[L::CIN];
-    if (q < n) {
-      gather_sliced<CS, CT>(m, sliced, qu, qv, qt, x, lut);
-    } else {
-#pragma unroll
-      for (int k = 0; k < L::CIN; ++k) x[k] = 0.0f;
-    }
-    uint32_t w[L::K1P / 2];
-    pack_a1<L::CIN, L::K1P, BF16>(x, w);
-    e.write_a1(0, w);
-  };
-  int64_t tile = lane_id;
-  if (tile < tiles) {
-    produce(tile);
-    e.layer1(0);   // no wait has run yet: cannot report a timeout
-    inflight[0] = true;
-    int64_t q_cur = tile * 128 + t, q_prev = -1;
-    tile += lanes;
-    for (;;) {
-      inflight[0] = !e.wait(0);   // layer 1 of q_cur (and layer 3 of q_prev)
-      if (q_prev >= 0) {   // false only on the first tile, for every thread (tcgen05.ld is warp-wide)
-        float y0, y1, y2;
-        e.output(0, y0, y1, y2);
-        if (q_prev < n) {
-          rgb[3 * q_prev] = y0;
-          rgb[3 * q_prev + 1] = y1;
-          rgb[3 * q_prev + 2] = y2;
-        }
-      }
-      e.template epilogue<true>(0);
-      if (!e.layer2(0)) {
-        timed_out = true;
-        break;
-      }
-      inflight[0] = true;
-      const bool more = tile < tiles;
-      if (more) produce(tile);
-      inflight[0] = !e.wait(0);   // layer 2
-      e.template epilogue<false>(0);
-      if (!e.layer3(0, more)) {
-        timed_out = true;
-        break;
-      }
-      inflight[0] = true;
-      if constexpr (!E::kMerge) {   // layer 3 alone, then the next tile's layer 1
-        inflight[0] = !e.wait(0);
-        float y0, y1, y2;
-        e.output(0, y0, y1, y2);
-        if (q_cur < n) {
-          rgb[3 * q_cur] = y0;
-          rgb[3 * q_cur + 1] = y1;
-          rgb[3 * q_cur + 2] = y2;
-        }
-        if (!more) break;
-        if (!e.layer1(0)) {
-          timed_out = true;
-          break;
-        }
-        inflight[0] = true;
-      } else {
-        q_prev = q_cur;
-        if (!more) break;
-      }
-      q_cur = tile * 128 + t;
-      tile += lanes;
-    }
-    if (E::kMerge && !timed_out) {   // the last tile's layer 3
-      inflight[0] = !e.wait(0);
-      float y0, y1, y2;
-      e.output(0, y0, y1, y2);
-      if (q_prev < n) {
-        rgb[3 * q_prev] = y0;
-        rgb[3 * q_prev + 1] = y1;
-        rgb[3 * q_prev + 2] = y2;
-      }
-    }
-  }
-  cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -1139,6 +478,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   const uint32_t base = smem_addr(sm);
   E e;
   engine_init<H, P, L::K1G, SL>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
+  if (c.debug_word && (*c.debug_word & kDbgInjectTimeout)) inject_timeout(e);
   e.b3 = st.b3;
   const int wg = e.wg, t = e.t;
   unsigned char* lb = sm + S::kLanes + wg * S::kLaneBytes;
@@ -1345,7 +685,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
     // every lane must be done with the weights and b1' before the next request
     if (__syncthreads_or(timed_out || e.late)) break;
   }
-  cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid);
+  cta_teardown<SL * NWG, E::kSlotCols>(tbase, e, inflight, timed_out, tid, c.error_word);
 }
 
 // ---------------------------------------------------------------------------
@@ -1368,33 +708,11 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
 // are issued, so every named barrier still sees all its threads and the CTA
 // drains quickly with the error latched.
 // ---------------------------------------------------------------------------
-constexpr int kWsLanes = 4;
 // Look-ahead of the warp-specialised producer's ring decode: batches of up to
 // five rows, each decoded while the consumer runs the previous tile's MMA
 // chain; a quadrant's first batch holds only the first tile's rows, so the
 // first MMA starts early.
 constexpr int kWsDecodeAhead = 4;
-
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-__device__ __forceinline__ void named_arrive(int id, int nthreads) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-// Bounded wait that gives up at once when the CTA has aborted; false if it
-// did not see the phase complete.
-__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t& phase, volatile int* abort) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
-    if (mbar_try_wait(bar, phase)) {
-      phase ^= 1u;
-      tc_fence_after();
-      return true;
-    }
-    if (*abort) return false;
-  }
-  *abort = 1;
-  return false;
-}
 
 template <int CS, int CT, int H, int P>
 __global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
@@ -1447,7 +765,7 @@ __global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
   E e;   // this lane's slot, seen from either warpgroup
   e.wg = lane;
   e.t = t;
-  e.it = 32 * lane;
+  e.it = 32 * ((lane + 1) & (NL - 1));   // issuers in warps 1, 2, 3, 0 of their lanes: none in the CTA's warp 0
   e.late = false;
   e.b3 = st.b3;
   e.lane_off = (uint32_t)(((t >> 5) * 32) << 16);
@@ -1458,6 +776,13 @@ __global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
   e.db2 = sdesc(base + S::kW + L::kB2, 128u, E::K2 * E::EB * 8u);
   e.db3 = sdesc(base + S::kW + L::kB3, 128u, E::K2 * E::EB * 8u);
   const bool issuer = !producer && t == e.it;
+  if (tid == 0 && c.debug_word && (*c.debug_word & kDbgInjectTimeout)) {
+    // injected timeout: a short wait on a phase nothing completes, then the real abort path
+    bool done = false;
+    for (uint32_t i = 0; i < kInjectSpin && !done; ++i) done = mbar_try_wait_for(&bar1[0], 0u, kInjectHintNs) != 0;
+    if (!done) *abort = 1;
+  }
+  __syncthreads();
   uint32_t ph1 = 0, ph2 = 0;   // parity of the next bar1 / bar2 phase this thread waits for
   bool out1 = false, out2 = false;   // issuer: a commit whose completion it has not seen
   unsigned char* lb = sm + S::kLanes + lane * S::kLaneBytes;
@@ -1531,7 +856,12 @@ __global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
           e.write_a1(0, w);
           tmem_st_wait();
           tc_fence_before();
-          named_arrive(bar_ready, 2 * kLaneThreads);
+          // Normally the producer cannot get ahead (it waited for this slot's previous
+          // layer 1), so arriving is enough; once the CTA has aborted its waits return
+          // at once, and it must sync instead so that it never arrives twice before
+          // the consumer's sync of the same barrier generation.
+          if (*abort) named_sync(bar_ready, 2 * kLaneThreads);
+          else named_arrive(bar_ready, 2 * kLaneThreads);
           // the next tile's rows are decoded while the consumer runs this tile's MMA chain
           if (tile + 1 < ntiles) {
             decode_for(tile + 1);
@@ -1618,10 +948,10 @@ __global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
   // teardown: an issuer that gave up waiting waits (bounded) for its MMAs
   // before the tensor memory is freed
   if (issuer) {
-    if (out1 && !mbar_wait(&bar1[lane], ph1)) atomicOr(&g_tc_error, 1);
-    if (out2 && !mbar_wait(&bar2[lane], ph2)) atomicOr(&g_tc_error, 1);
+    if (out1 && !mbar_wait(&bar1[lane], ph1)) atomicOr(c.error_word, kErrTimeout);
+    if (out2 && !mbar_wait(&bar2[lane], ph2)) atomicOr(c.error_word, kErrTimeout);
   }
-  if (tid == 0 && *abort) atomicOr(&g_tc_error, 1);
+  if (tid == 0 && *abort) atomicOr(c.error_word, kErrTimeout);
   tc_fence_before();
   __syncthreads();
   if ((tid >> 5) == 0) {
@@ -1630,36 +960,9 @@ __global__ void __launch_bounds__(2 * kLaneThreads * kWsLanes, 1)
   }
 }
 
-// The tensor-core point decode's feature gather alone (on the texel-sliced
-// copy in a prepared workspace), for validation.
-template <int CS, int CT, int H>
-__global__ void __launch_bounds__(128) k_debug_features_tc(DevModel m, const unsigned char* __restrict__ ws,
-                                                           const float* __restrict__ uvt, int64_t n,
-                                                           float* __restrict__ xo) {
-  __shared__ uint2 lut[16];
-  init_p35_lut_sliced(lut, threadIdx.x);
-  __syncthreads();
-  const uint8_t* sliced = ws + TcLayout<CS, CT, H>::kSliceOff;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float x[CS + CT];
-    gather_sliced<CS, CT>(m, sliced, uvt[3 * i], uvt[3 * i + 1], uvt[3 * i + 2], x, lut);
-#pragma unroll
-    for (int c = 0; c < CS + CT; ++c) xo[i * (CS + CT) + c] = x[c];
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Dispatch
 // ---------------------------------------------------------------------------
-#define NDGI_TC_SHAPES(X) \
-  X(4, 4, 16)             \
-  X(8, 8, 16)             \
-  X(8, 8, 32)             \
-  X(16, 8, 16)            \
-  X(16, 8, 32)            \
-  X(16, 8, 64)            \
-  X(16, 16, 64)
-
 bool tc_supported(int cs, int ct, int hidden) {
 #define X(A, B, C) if (cs == A && ct == B && hidden == C) return true;
   NDGI_TC_SHAPES(X)
@@ -1670,9 +973,13 @@ bool tc_supported(int cs, int ct, int hidden) {
 bool tc_pages_supported(int cs, int ct, int hidden) { return tc_supported(cs, ct, hidden) && cs == 16; }
 
 size_t tc_workspace_bytes(int cs, int ct, int hidden, int feat_w, int feat_h) {
-  const size_t nblocks = (size_t)(feat_w / 4) * (size_t)(feat_h / 4);
-#define X(A, B, C) \
-  if (cs == A && ct == B && hidden == C) return TcLayout<A, B, C>::kSliceOff + nblocks * Sliced<A>::BLOCK;
+  const size_t cache = points_cache_bytes(cs, feat_w, feat_h);
+#define X(A, B, C)                                                                                          \
+  if (cs == A && ct == B && hidden == C) {                                                                  \
+    const size_t off = points_cache_offset<A, B, C>(feat_w, feat_h);                                        \
+    return cache ? off + cache                                                                              \
+                 : TcLayout<A, B, C>::kSliceOff + (size_t)(feat_w / 4) * (size_t)(feat_h / 4) * Sliced<A>::BLOCK; \
+  }
   NDGI_TC_SHAPES(X)
 #undef X
   return 0;
@@ -1690,44 +997,6 @@ cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream
     k_slice_features<A><<<grid > 0 ? grid : 1, 256, 0, s>>>(                                             \
         m.bc4, nblocks, static_cast<unsigned char*>(ws) + TcLayout<A, B, C>::kSliceOff);                 \
     return cudaGetLastError();                                                                           \
-  }
-  NDGI_TC_SHAPES(X)
-#undef X
-  return cudaErrorInvalidValue;
-}
-
-// A tensor-core CTA allocates most of its SM's tensor memory for the whole
-// (persistent) kernel, so a second CTA placed on the same SM would block in
-// tcgen05.alloc until the first exits.  Asking for more than half of the
-// SM's shared memory keeps the placement at one CTA per SM.
-constexpr uint32_t kOneCtaPerSmSmem = 116 * 1024;
-constexpr uint32_t tc_smem(uint32_t need) { return need > kOneCtaPerSmSmem ? need : kOneCtaPerSmSmem; }
-
-template <typename K>
-static cudaError_t set_smem(K kern, uint32_t bytes) {
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// Points: 4 lanes x 1 slot per CTA, one CTA per SM (4 tiles in flight: the
-// tensor memory holds 4 slots of 128 columns).
-constexpr int kPointsLanes = 4, kPointsSlots = 1;
-
-cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const float* uvt, int64_t n, float* rgb,
-                             cudaStream_t s) {
-  const int64_t tiles = (n + 127) / 128;
-  const int64_t need = (tiles + kPointsLanes * kPointsSlots - 1) / (kPointsLanes * kPointsSlots);
-  const int64_t cap = num_sms();
-  const int grid = (int)(need < cap ? need : cap);
-#define X(A, B, C)                                                                                              \
-  if (m.cs == A && m.ct == B && m.hidden == C) {                                                                \
-    using S = PointsSmem<A, B, C>;                                                                              \
-    auto kern = bf16 ? k_points_tc<A, B, C, true, kPointsLanes, kPointsSlots>                                   \
-                     : k_points_tc<A, B, C, false, kPointsLanes, kPointsSlots>;                                 \
-    const uint32_t smem = tc_smem(S::kBytes);                                                                   \
-    cudaError_t e = set_smem(kern, smem);                                                                       \
-    if (e != cudaSuccess) return e;                                                                             \
-    kern<<<grid, kLaneThreads * kPointsLanes, smem, s>>>(m, static_cast<const unsigned char*>(ws), uvt, n, rgb); \
-    return cudaGetLastError();                                                                                  \
   }
   NDGI_TC_SHAPES(X)
 #undef X
@@ -1895,20 +1164,6 @@ cudaError_t launch_tc_prepare8(const DevModel& m, const float act_max[3], void* 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_debug_features_tc(const DevModel& m, const void* ws, const float* uvt, int64_t n, float* x,
-                                     cudaStream_t s) {
-  const int64_t blocks = (n + 127) / 128;
-  const int grid = (int)std::min<int64_t>(blocks > 0 ? blocks : 1, (int64_t)num_sms() * 16);
-#define X(A, B, C)                                                                                              \
-  if (m.cs == A && m.ct == B && m.hidden == C) {                                                                \
-    k_debug_features_tc<A, B, C><<<grid, 128, 0, s>>>(m, static_cast<const unsigned char*>(ws), uvt, n, x);     \
-    return cudaGetLastError();                                                                                  \
-  }
-  NDGI_TC_SHAPES(X)
-#undef X
-  return cudaErrorInvalidValue;
-}
-
 uint32_t tc_fp8_status_offset(int cs, int ct, int hidden) {
 #define X(A, B, C) if (cs == A && ct == B && hidden == C) return fp8_status_offset<A, B, C>();
   NDGI_TC_SHAPES(X)
@@ -1922,14 +1177,12 @@ std::vector<TcPagesShape> tc_pages_candidates(int) {
   return {TcPagesShape{1, 4, 1}, TcPagesShape{1, 2, 2}, TcPagesShape{1, 2 * kWsLanes, 1}};
 }
 
-int tc_take_error() {
-  int h = 0;
-  if (cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int)) != cudaSuccess) return -1;
-  if (h) {
-    const int z = 0;
-    cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int));
-  }
-  return h;
+uint32_t tc_error_offset(int cs, int ct, int hidden) {
+#define X(A, B, C) if (cs == A && ct == B && hidden == C) return TcLayout<A, B, C>::kErrOff;
+  NDGI_TC_SHAPES(X)
+#undef X
+  return 0;
 }
 
 }  // namespace ndgi
+

@@ -23,8 +23,21 @@ cudaError_t launch_debug_features_tc(const DevModel& m, const void* ws, const fl
 // feature planes the point decode reads.
 size_t tc_workspace_bytes(int cs, int ct, int hidden, int feat_w, int feat_h);
 cudaError_t launch_tc_prepare(const DevModel& m, bool bf16, void* ws, cudaStream_t s);
+// Point decode gather policy: kPointsAuto decodes through the decoded-texel
+// cache (built first, in the same call) when the workspace has one and the
+// call has at least feat_w * feat_h / 2 queries, else directly;
+// kPointsBuild / kPointsReuse force the cache path, building the cache or
+// reusing the one an earlier call on the same stream built from the same
+// workspace; kPointsDirect forces the direct gather.
+enum { kPointsAuto = 0, kPointsBuild = 1, kPointsReuse = 2, kPointsDirect = 3 };
+bool tc_points_cache_path(const DevModel& m, int64_t n, int mode);
+// The cache path runs the warp-specialised point kernel for this shape (else the four-lane one).
+bool tc_points_ws_built(int cs, int ct, int hidden);
 cudaError_t launch_tc_points(const DevModel& m, bool bf16, const void* ws, const float* uvt, int64_t n, float* rgb,
-                             cudaStream_t s);
+                             cudaStream_t s, int mode);
+// The cache path's gather alone (builds the cache, then x [n][cs+ct]).
+cudaError_t launch_debug_features_cache(const DevModel& m, const void* ws, const float* uvt, int64_t n, float* x,
+                                        cudaStream_t s);
 // staged: every model's features are at most half its lightmap resolution.
 // prec: 0 FP16, 1 BF16, 2 E4M3 (the workspace then comes from launch_tc_prepare8).
 cudaError_t launch_tc_pages(const PagesCtx& c, int prec, int cs, int ct, int hidden, const TcPagesShape& shape,
@@ -40,8 +53,8 @@ uint32_t tc_fp8_status_offset(int cs, int ct, int hidden);
 // returns the number of floats (written only if len is enough).
 size_t tc_fp8_unpack(int cs, int ct, int hidden, const unsigned char* image, float* out, size_t len);
 TcPagesShape tc_default_pages_shape();
-// Reads and clears the tensor-core kernels' device error word (-1 if unreadable).
-int tc_take_error();
+// Byte offset of the error word (then the debug word) in an FP16/BF16 workspace.
+uint32_t tc_error_offset(int cs, int ct, int hidden);
 std::vector<TcPagesShape> tc_pages_candidates(int sms);
 
 }  // namespace ndgi

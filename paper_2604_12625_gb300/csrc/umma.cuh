@@ -14,9 +14,17 @@
 
 namespace ndgi {
 
-// Iterations of a bounded mbarrier wait (each try_wait may itself suspend
-// for a while); past this the caller reports NDGI_ERR_TIMEOUT and unwinds.
-constexpr uint32_t kSpinLimit = 1u << 22;
+// A bounded mbarrier wait gives up after kWaitLimitNs of wall time (read from
+// %globaltimer once the first poll has failed); the caller then reports
+// NDGI_ERR_TIMEOUT and unwinds.  A try_wait that finds its phase incomplete
+// suspends the thread until the phase completes or a time limit passes.  The
+// first poll of a wait uses the hardware's own limit (the fastest form when
+// the phase completes while the thread sleeps, measured); every later poll
+// passes kPollHintNs, so a wait lasts at most one hardware limit plus
+// kWaitLimitNs.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+constexpr uint32_t kPollHintNs = 100000u;          // 0.1 ms
+constexpr uint32_t kSpinLimit = 1u << 22;          // safety cap on the polls
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -31,6 +39,7 @@ __device__ __forceinline__ void mbar_fence_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// try_wait with the hardware's own suspension limit.
 __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -43,11 +52,40 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity
   return ok;
 }
 
+// try_wait that suspends at most `hint_ns` nanoseconds when the phase is incomplete.
+__device__ __forceinline__ uint32_t mbar_try_wait_for(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The slow path of a bounded wait: polls with a bounded suspension until the
+// phase completes or kWaitLimitNs have passed; false on timeout.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait_for(bar, parity, kPollHintNs)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return false;
+}
+
 // Waits for the phase with the given parity to complete; false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_slow(bar, parity);
 }
 
 // Generic-proxy shared-memory writes -> visible to the tensor core (async proxy).

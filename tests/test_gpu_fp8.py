@@ -81,14 +81,19 @@ def test_fp8_exact_model_is_bit_exact(ndgi):
     plan.close()
 
 
+TIGHT = (1e-2, 2e-2, 5e-2)
+
+
 def page_errors(got, ref, reqs):
-    """Per request: (max, rms) of |got - ref| over RGB, relative to the page's range."""
+    """Per request: (max, rms, then the share of values above each TIGHT bound) of |got - ref| over RGB,
+    relative to the page's range."""
     out = []
     for r in reqs:
         sl = (slice(r["dst_y"], r["dst_y"] + r["h"]), slice(r["dst_x"], r["dst_x"] + r["w"]))
         a, b = got[sl][..., :3].astype(np.float64), ref[sl][..., :3]
         rng = max(b.max() - b.min(), 1e-6)
-        out.append((np.abs(a - b).max() / rng, np.sqrt(((a - b) ** 2).mean()) / rng))
+        d = np.abs(a - b) / rng
+        out.append((d.max(), np.sqrt((d ** 2).mean()), *[(d > x).mean() for x in TIGHT]))
     return np.array(out)
 
 
@@ -120,9 +125,13 @@ def test_fp8_pages_error_distribution(ndgi, ct):
     ref = oracle.decode_pages(maps, reqs, 1024, 1024, precision="fp8", act_max=am, fill=0.0)
     e = page_errors(got, ref, reqs)
     e32 = page_errors(got, oracle.decode_pages(maps, reqs, 1024, 1024, precision="fp32", fill=0.0), reqs)
-    print(f"ct={ct}: vs oracle FP8 max {e[:, 0].max():.3e} rms {e[:, 1].mean():.3e}; "
-          f"vs FP32 master max {e32[:, 0].max():.3e} rms {e32[:, 1].mean():.3e}")
-    # rounding flips of single activations give isolated errors of a few percent; the bulk agrees closely
+    share = [float(np.average(e[:, 2 + i], weights=reqs["w"] * reqs["h"])) for i in range(len(TIGHT))]
+    print(f"ct={ct}: vs oracle FP8 max {e[:, 0].max():.3e} rms {e[:, 1].mean():.3e} share above "
+          + ", ".join(f"{x:g}: {v:.2e}" for x, v in zip(TIGHT, share))
+          + f"; vs FP32 master max {e32[:, 0].max():.3e} rms {e32[:, 1].mean():.3e}")
+    # rounding flips of single activations (one E4M3 step, 6-12% of the value) give errors around 1e-2 of the
+    # range; the bulk agrees closely and large errors are rare
+    assert share[0] <= 0.06 and share[2] <= 0.01
     assert e[:, 1].mean() <= 0.01 and e[:, 0].max() <= 0.2
     assert e32[:, 1].mean() <= 0.08
 

@@ -281,3 +281,27 @@ def test_tc_pages_mirror_address_mode(ndgi, shape):
     ref = oracle.decode_pages(maps, reqs, 512, 512, precision="fp16")
     assert page_err(phys.cpu().numpy(), ref, reqs) <= GATE["fp16"]
     plan.close()
+
+
+@pytest.mark.parametrize("hidden", [32, 16])
+def test_tc_pages_other_hidden_widths(ndgi, hidden):
+    # the page kernels at the other built hidden widths: the warp-specialised kernel equals the 4 x 1 kernel
+    # bit for bit, and both meet the FP16 gate against the oracle
+    sizes = (256, 512)
+    maps = synth.page_models(47, sizes=sizes, hidden=hidden, temporal_dtype="f16")
+    models = [ndgi.Model.from_arrays(m) for m in maps]
+    phys = torch.zeros((512, 512, 4), dtype=torch.float32, device="cuda")
+    plan = ndgi.PagesPlan(models, "fp16", 64, phys)
+    reqs = synth.ragged_page_requests(48, sizes, 16, slots_x=4, slot=128)
+    r, n = ndgi.page_requests_to_device(reqs)
+    out = {}
+    for shape in ((1, 4, 1), (1, 8, 1)):
+        plan.set_shape(*shape)
+        phys.zero_()
+        plan.decode(r, n)
+        assert plan.check() == (0, 0)
+        out[shape] = phys.cpu().numpy()
+    assert np.array_equal(out[(1, 4, 1)], out[(1, 8, 1)])
+    ref = oracle.decode_pages(maps, reqs, 512, 512, precision="fp16", fill=0.0)
+    assert page_err(out[(1, 8, 1)], ref, reqs) <= GATE["fp16"]
+    plan.close()
