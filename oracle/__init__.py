@@ -101,6 +101,11 @@ def lib():
             L.om_fp8_weights.argtypes = [vp, vp, vp, vp, vp]
             L.om_fp8_calibrate.argtypes = [vp, vp, i64, vp]
             L.om_decode_pages_fp8.argtypes = [vp, vp, vp, i32, vp, i64, C.c_int]
+            L.om_gelu.argtypes = [f64]
+            L.om_gelu.restype = f64
+            L.om_hybrid_gamma.argtypes = [f64, vp]
+            L.om_hybrid_decode_points.argtypes = [vp, vp, i64, vp, vp, C.c_int]
+            L.om_hybrid_decode_pages.argtypes = [vp, i32, vp, i32, vp, i64, i64, C.c_int]
             L.om_splitmix64_next.argtypes = [C.c_uint64]
             L.om_splitmix64_next.restype = C.c_uint64
             _lib = L
@@ -157,6 +162,72 @@ class Model:
                         _ptr(self.bc4), int(m["t_count"]), self.ct, _ptr(self.temporal), self.hidden,
                         _ptr(self.w["w1"]), _ptr(self.w["b1"]), _ptr(self.w["w2"]), _ptr(self.w["b2"]),
                         _ptr(self.w["w3"]), _ptr(self.w["b3"]), int(m.get("address_mode", 0)))
+
+
+class _Hybrid(C.Structure):
+    _fields_ = [("lm_w", C.c_int32), ("lm_h", C.c_int32), ("uv_w", C.c_int32), ("uv_h", C.c_int32),
+                ("uv_bc4", C.c_void_p), ("vol_w", C.c_int32), ("vol_h", C.c_int32), ("vol_t", C.c_int32),
+                ("vol_bc4", C.c_void_p), ("ut_w", C.c_int32), ("ut_t", C.c_int32), ("ut", C.c_void_p),
+                ("vt_h", C.c_int32), ("vt_t", C.c_int32), ("vt", C.c_void_p), ("hidden", C.c_int32),
+                ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+
+
+class HybridModel:
+    """A hybrid-feature-map model (dict from synth.hybrid_model) held in oracle form."""
+
+    def __init__(self, m, precision="fp32"):
+        self.src = m
+        self.hidden = int(m["hidden"])
+        assert self.hidden <= lib().om_max_hidden()
+        self.arr = {k: _c(m[k], np.uint8) for k in ("uv_bc4", "vol_bc4", "ut", "vt")}
+        w = stored_weights(m, precision)
+        self.w = {k: _c(v, np.float64) for k, v in w.items()}
+        vol_t, vol_h, vol_w = (int(d) for d in m["vol_shape"])
+        self.s = _Hybrid(int(m["lm_w"]), int(m["lm_h"]), int(m["uv_w"]), int(m["uv_h"]), _ptr(self.arr["uv_bc4"]),
+                         vol_w, vol_h, vol_t, _ptr(self.arr["vol_bc4"]),
+                         int(m["ut"].shape[1]), int(m["ut"].shape[0]), _ptr(self.arr["ut"]),
+                         int(m["vt"].shape[1]), int(m["vt"].shape[0]), _ptr(self.arr["vt"]), self.hidden,
+                         _ptr(self.w["w1"]), _ptr(self.w["b1"]), _ptr(self.w["w2"]), _ptr(self.w["b2"]),
+                         _ptr(self.w["w3"]), _ptr(self.w["b3"]), int(m.get("address_mode", 0)))
+
+
+def _hybrid(m, precision="fp32"):
+    return m if isinstance(m, HybridModel) else HybridModel(m, precision)
+
+
+def gelu(x):
+    """GELU x Phi(x) of each value (FP64)."""
+    f = lib().om_gelu
+    return np.array([f(float(v)) for v in np.asarray(x, np.float64).reshape(-1)]).reshape(np.shape(x))
+
+
+def hybrid_gamma(t):
+    """The time code gamma(t) of Eq. 4, [4]."""
+    g = np.zeros(4, np.float64)
+    lib().om_hybrid_gamma(float(t), _ptr(g))
+    return g
+
+
+def hybrid_decode_points(m, uvt, precision="fp32", nthreads=None, features=False):
+    """FP64 RGB [n][3] of the hybrid decoder at each (u, v, t); with features=True also the inputs [n][16]."""
+    M = _hybrid(m, precision)
+    q = _c(uvt, np.float32).reshape(-1, 3)
+    y = np.zeros((q.shape[0], 3), np.float64)
+    x = np.zeros((q.shape[0], 16), np.float64) if features else None
+    lib().om_hybrid_decode_points(C.byref(M.s), _ptr(q), q.shape[0], _ptr(y), _ptr(x), nthreads or nthreads_default())
+    return (y, x) if features else y
+
+
+def hybrid_decode_pages(models, reqs, phys_w, phys_h, precision="fp32", nthreads=None, fill=np.nan):
+    """FP64 RGBA physical texture [phys_h][phys_w][4] of hybrid-model page requests; untouched texels = fill."""
+    r = np.ascontiguousarray(reqs)
+    out = np.full((phys_h, phys_w, 4), fill, np.float64)
+    Ms = [_hybrid(m, precision) for m in models]
+    arr = (_Hybrid * len(Ms))(*[M.s for M in Ms])
+    lib().om_hybrid_decode_pages(arr, len(Ms), r.ctypes.data_as(C.c_void_p), len(r), _ptr(out), phys_w, phys_h,
+                                 nthreads or nthreads_default())
+    return out
 
 
 def _model(m, precision="fp32"):

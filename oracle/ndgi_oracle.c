@@ -172,12 +172,16 @@ void om_features(const om_model *m, double u, double v, double t, double *x, int
   }
 }
 
-/* Dense layer y = act(x W + b), W stored [in][out]. */
-static void om_dense(const double *x, int in, const double *W, const double *b, int out, int relu, double *y) {
+/* GELU of the full decoder's hidden layers (Sec. 4): x Phi(x), Phi the
+ * standard normal CDF, written with the C library's erf. */
+double om_gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+
+/* Dense layer y = act(x W + b), W stored [in][out]; act 0 = none, 1 = ReLU, 2 = GELU. */
+static void om_dense(const double *x, int in, const double *W, const double *b, int out, int act, double *y) {
   for (int o = 0; o < out; ++o) {
     double z = b[o];
     for (int i = 0; i < in; ++i) z += x[i] * W[(size_t)i * out + o];
-    y[o] = (relu && !(z > 0.0)) ? 0.0 : z;
+    y[o] = act == 2 ? om_gelu(z) : ((act == 1 && !(z > 0.0)) ? 0.0 : z);
   }
 }
 
@@ -737,5 +741,143 @@ void om_fit_draw(uint64_t seed, int64_t step, int64_t first, int64_t n, int32_t 
     uvt[3 * i] = (float)(((double)ix + 0.5) / (double)lm_w);
     uvt[3 * i + 1] = (float)(((double)iy + 0.5) / (double)lm_h);
     uvt[3 * i + 2] = (float)ldexp((double)(z2 >> 40), -24);
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Hybrid feature map decoder (Sec. 3.3, Eq. 4-5; Sec. 4)                  */
+/* ---------------------------------------------------------------------- */
+/*
+ * The paper's full decoder.  Four feature maps (Eq. 5): a low-resolution 3D
+ * map F3D over (u, v, t) with 4 channels, sampled trilinearly (V_uvt); the
+ * tri-plane F_uv (4 channels), F_ut and F_vt (2 channels each), each sampled
+ * bilinearly at the projection of (u, v, t) onto its plane.  The decoder
+ * input is [V_uvt, V_uv, V_ut, V_vt, gamma(t)] (16 values, Eq. 4) and the
+ * MLP has two GELU hidden layers and a linear RGB output (Sec. 4).
+ * Readings (the paper fixes none of these):
+ *   - F_uv and every t-slice of F3D are four BC4 planes (the BC stand-in of
+ *     this library for the paper's four-channel BC7), value P35/8925 as
+ *     above, layout [h/4][w/4][4][8]; F3D slices are stored one after another;
+ *   - F_ut and F_vt are UNORM8 (the paper's 8-bit planes), value byte/255,
+ *     layout [t][x][2] (x = u for F_ut, v for F_vt);
+ *   - every axis uses the texel-centre convention; u and v follow the
+ *     model's address mode, t (in [0, 1]) clamps to the edge slices.
+ */
+typedef struct {
+  int32_t lm_w, lm_h;                       /* lightmap (tile) size          */
+  int32_t uv_w, uv_h;                       /* F_uv                          */
+  const uint8_t *uv_bc4;
+  int32_t vol_w, vol_h, vol_t;              /* F3D                           */
+  const uint8_t *vol_bc4;
+  int32_t ut_w, ut_t;                       /* F_ut                          */
+  const uint8_t *ut;
+  int32_t vt_h, vt_t;                       /* F_vt                          */
+  const uint8_t *vt;
+  int32_t hidden;                           /* MLP 16 -> hidden -> hidden -> 3 */
+  const double *w1, *b1, *w2, *b2, *w3, *b3;
+  int32_t address_mode;
+} om_hybrid;
+
+/* Bilinear sample at (u, v) of four BC4 planes [h/4][w/4][4][8]. */
+static void om_bc4x4_bilinear(const uint8_t *bc4, int w, int h, double u, double v, int mode, double *out) {
+  int x0, x1, y0, y1;
+  double fx, fy;
+  om_bilinear_setup(u, w, mode, &x0, &x1, &fx);
+  om_bilinear_setup(v, h, mode, &y0, &y1, &fy);
+  const int bw = w / 4;
+  const int tx[4] = {x0, x1, x0, x1}, ty[4] = {y0, y0, y1, y1};
+  for (int c = 0; c < 4; ++c) {
+    double f[4];
+    for (int q = 0; q < 4; ++q) {
+      const uint8_t *blk = bc4 + ((size_t)((ty[q] >> 2) * bw + (tx[q] >> 2)) * 4 + c) * 8;
+      f[q] = om_p35_value(om_bc4_p35(blk, (ty[q] & 3) * 4 + (tx[q] & 3)));
+    }
+    out[c] = (1.0 - fy) * ((1.0 - fx) * f[0] + fx * f[1]) + fy * ((1.0 - fx) * f[2] + fx * f[3]);
+  }
+}
+
+/* Bilinear sample of a two-channel UNORM8 plane [ny][nx][2] at (s, r): s
+ * along x with address mode `mode`, r along y (time) clamped. */
+static void om_u8x2_bilinear(const uint8_t *p, int nx, int ny, double s, double r, int mode, double *out) {
+  int x0, x1, y0, y1;
+  double fx, fy;
+  om_bilinear_setup(s, nx, mode, &x0, &x1, &fx);
+  om_bilinear_setup(r, ny, 0, &y0, &y1, &fy);
+  for (int c = 0; c < 2; ++c) {
+    const double f00 = p[((size_t)y0 * nx + x0) * 2 + c] / 255.0, f10 = p[((size_t)y0 * nx + x1) * 2 + c] / 255.0;
+    const double f01 = p[((size_t)y1 * nx + x0) * 2 + c] / 255.0, f11 = p[((size_t)y1 * nx + x1) * 2 + c] / 255.0;
+    out[c] = (1.0 - fy) * ((1.0 - fx) * f00 + fx * f10) + fy * ((1.0 - fx) * f01 + fx * f11);
+  }
+}
+
+/* Positional code of time, Eq. 4: [sin(pi t), cos(pi t), sin(2 pi t), cos(2 pi t)]. */
+void om_hybrid_gamma(double t, double *g) {
+  const double pi = 3.14159265358979323846;
+  g[0] = sin(pi * t);
+  g[1] = cos(pi * t);
+  g[2] = sin(2.0 * pi * t);
+  g[3] = cos(2.0 * pi * t);
+}
+
+/* Decoder input x[16] = [V_uvt (4), V_uv (4), V_ut (2), V_vt (2), gamma(t) (4)] (Eq. 4). */
+void om_hybrid_features(const om_hybrid *m, double u, double v, double t, double *x) {
+  /* trilinear: the two t-slices around t, each sampled bilinearly at (u, v), then linear in t */
+  int z0, z1;
+  double fz, a[4], b[4];
+  om_bilinear_setup(t, m->vol_t, 0, &z0, &z1, &fz);
+  const size_t slice = (size_t)(m->vol_h / 4) * (size_t)(m->vol_w / 4) * 32;
+  om_bc4x4_bilinear(m->vol_bc4 + (size_t)z0 * slice, m->vol_w, m->vol_h, u, v, m->address_mode, a);
+  om_bc4x4_bilinear(m->vol_bc4 + (size_t)z1 * slice, m->vol_w, m->vol_h, u, v, m->address_mode, b);
+  for (int c = 0; c < 4; ++c) x[c] = (1.0 - fz) * a[c] + fz * b[c];
+  om_bc4x4_bilinear(m->uv_bc4, m->uv_w, m->uv_h, u, v, m->address_mode, x + 4);
+  om_u8x2_bilinear(m->ut, m->ut_w, m->ut_t, u, t, m->address_mode, x + 8);
+  om_u8x2_bilinear(m->vt, m->vt_h, m->vt_t, v, t, m->address_mode, x + 10);
+  om_hybrid_gamma(t, x + 12);
+}
+
+/* Decoder G_Phi: 16 -> hidden (GELU) -> hidden (GELU) -> 3 (linear), Sec. 4. */
+void om_hybrid_mlp(const om_hybrid *m, const double *x, double *rgb) {
+  double h1[256], h2[256];
+  om_dense(x, 16, m->w1, m->b1, m->hidden, 2, h1);
+  om_dense(h1, m->hidden, m->w2, m->b2, m->hidden, 2, h2);
+  om_dense(h2, m->hidden, m->w3, m->b3, 3, 0, rgb);
+}
+
+/* I(u_i, v_i, t_i) = G_Phi(features) for n queries; x (may be NULL) receives the inputs [n][16]. */
+void om_hybrid_decode_points(const om_hybrid *m, const float *uvt, int64_t n, double *rgb, double *x, int nthreads) {
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+  for (int64_t i = 0; i < n; ++i) {
+    double f[16];
+    om_hybrid_features(m, (double)uvt[3 * i], (double)uvt[3 * i + 1], (double)uvt[3 * i + 2], f);
+    if (x) memcpy(x + 16 * i, f, sizeof f);
+    om_hybrid_mlp(m, f, rgb + 3 * i);
+  }
+}
+
+/* Page decode with hybrid models (Sec. 3.5): as om_decode_pages, texel
+ * (x0+i, y0+j) of each request at ((x0+i+0.5)/lm_w, (y0+j+0.5)/lm_h, t) of the
+ * request's model, RGBA (A = 1) into phys[phys_h][phys_w][4]. */
+void om_hybrid_decode_pages(const om_hybrid *models, int32_t n_models, const om_page_req *reqs, int32_t n,
+                            double *phys, int64_t phys_w, int64_t phys_h, int nthreads) {
+  (void)n_models;
+  (void)phys_h;
+  for (int32_t r = 0; r < n; ++r) {
+    const om_page_req *q = &reqs[r];
+    const om_hybrid *m = &models[q->model];
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int32_t jj = 0; jj < q->h; ++jj) {
+      double f[16], rgb[3];
+      for (int32_t ii = 0; ii < q->w; ++ii) {
+        const double u = ((double)(q->x0 + ii) + 0.5) / (double)m->lm_w;
+        const double v = ((double)(q->y0 + jj) + 0.5) / (double)m->lm_h;
+        om_hybrid_features(m, u, v, (double)q->t, f);
+        om_hybrid_mlp(m, f, rgb);
+        double *o = phys + ((int64_t)(q->dst_y + jj) * phys_w + (q->dst_x + ii)) * 4;
+        o[0] = rgb[0];
+        o[1] = rgb[1];
+        o[2] = rgb[2];
+        o[3] = 1.0;
+      }
+    }
   }
 }

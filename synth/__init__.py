@@ -242,3 +242,52 @@ def fit_samples(seed, n, width, height, t_count, keyframe_every=4):
     s[:, 1] = (iy + 0.5) / height
     s[:, 2] = t
     return s
+
+
+# --------------------------------------------------------------------------
+# Hybrid feature map models (the paper's full decoder, Sec. 3.3 and Sec. 4)
+# --------------------------------------------------------------------------
+
+# Profiles of the paper's configuration table: F3D resolution (x 12 t-slices x 4
+# channels) and hidden width, for one 128 x 128 tile of a 26-lightmap set whose
+# other maps have the sizes of the paper's feature-map table (F_uv 128^2 x 4,
+# F_ut and F_vt 64 x 24 x 2).
+HYBRID_PROFILES = {"L": (16, 16), "M": (32, 16), "H": (64, 16), "M.64": (32, 64)}
+HYBRID_TILE = dict(lm=128, uv=128, vol_t=12, ut=(64, 24), vt=(64, 24), n_lightmaps=26)
+
+
+def hybrid_model(seed, lm_w, lm_h, uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, vt_h, vt_t, hidden,
+                 address_mode=0):
+    """One hybrid model: uniform random BC4 blocks for F_uv and every F3D t-slice
+    (4 planes each), uniform random bytes for the UNORM8 planes F_ut [ut_t][ut_w][2]
+    and F_vt [vt_t][vt_h][2], and a Xavier MLP 16 -> hidden -> hidden -> 3."""
+    rng = _rng(seed)
+    uv = bc4_planes(rng, uv_w, uv_h, 4)
+    vol = np.stack([bc4_planes(rng, vol_w, vol_h, 4) for _ in range(vol_t)])
+    ut = np.frombuffer(rng.bytes(ut_t * ut_w * 2), dtype=np.uint8).reshape(ut_t, ut_w, 2).copy()
+    vt = np.frombuffer(rng.bytes(vt_t * vt_h * 2), dtype=np.uint8).reshape(vt_t, vt_h, 2).copy()
+    m = dict(kind="hybrid", lm_w=lm_w, lm_h=lm_h, uv_w=uv_w, uv_h=uv_h, uv_bc4=uv,
+             vol_shape=(vol_t, vol_h, vol_w), vol_bc4=vol, ut=ut, vt=vt, hidden=hidden,
+             address_mode=address_mode)
+    m.update(xavier_mlp(rng, 16, hidden, 3))
+    return m
+
+
+def hybrid_tile_model(seed, profile="M.64", address_mode=0):
+    """A 128 x 128 tile model of one of the paper's profiles (L, M, H, M.64)."""
+    r, hidden = HYBRID_PROFILES[profile]
+    T = HYBRID_TILE
+    return hybrid_model(seed, T["lm"], T["lm"], T["uv"], T["uv"], r, r, T["vol_t"], T["ut"][0], T["ut"][1],
+                        T["vt"][0], T["vt"][1], hidden, address_mode)
+
+
+def hybrid_tile_requests(seed, n_tiles, n_req, slots_x=64, page=128):
+    """n_req whole-tile page requests over n_tiles tile models (request i decodes
+    tile model (a seeded uniform draw) at its own t ~ U[0,1) into slot i)."""
+    rng = _rng(seed)
+    tiles = rng.integers(0, n_tiles, n_req)
+    ts = rng.random(n_req, dtype=np.float32)
+    req = np.zeros(n_req, dtype=PAGE_REQ_DTYPE)
+    for i in range(n_req):
+        req[i] = (int(tiles[i]), 0, 0, page, page, ts[i], (i % slots_x) * page, (i // slots_x) * page)
+    return req
