@@ -464,6 +464,69 @@ def bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank):
     return out
 
 
+HYBRID_WORKLOAD = ("hybrid pages: 4096 tile models of the paper's M.64 profile (F_uv 128^2x4 and F3D 32^2x12x4 as "
+                   "BC4 planes, F_ut/F_vt 64x24x2 UNORM8, gamma(t), MLP 16-64-64-3 GELU), one frame = 4096 whole "
+                   "128^2 tile pages, each its own uniform tile and t ~ U[0,1); RGBA16F 8192^2 texture")
+HYBRID_FLOP_PER_TEXEL = 2 * (16 * 64 + 64 * 64 + 64 * 3)   # 10,624
+
+
+def hybrid_frame_bytes(n_req, n_models_touched, model_bytes, out_bytes_per_texel=8):
+    """Algorithmic DRAM bytes of one hybrid frame: each touched model once plus the output texels."""
+    return n_models_touched * model_bytes + n_req * 128 * 128 * out_bytes_per_texel
+
+
+def bench_hybrid(args, ndgi, torch, peaks, peak_kind, timed, rank):
+    """The paper's full decoder over per-tile models: one step = one frame of 4096 tile pages."""
+    s = synth.hybrid_tile_set(90, 4096, "M.64")
+    models = ndgi.HybridModel.from_set(s)
+    reqs = synth.hybrid_tile_requests(91, 4096, 4096, slots_x=64)
+    r_dev, _ = ndgi.page_requests_to_device(reqs)
+    phys = torch.empty((8192, 8192, 4), dtype=torch.float16, device="cuda")
+    texels = len(reqs) * 128 * 128
+    out = {"workload": HYBRID_WORKLOAD, "texels_per_frame": texels}
+    for prec in ("fp16", "fp32"):
+        ndgi.hybrid_prepare_set(models, prec)
+        table = ndgi.HybridTable(models, prec)
+        steps = max(3, min(args.steps, 20)) if prec == "fp16" else 3
+        ms, clocks = timed(lambda: table.decode(r_dev, len(reqs), phys), steps, 2, sample_clocks=(prec == "fp16"))
+        st, word = table.check()
+        entry = {"value": job_value(texels, args.world, ms / steps), "unit": "Gtexels/s", "ms_per_frame": ms / steps,
+                 "device_error_word": word, "device_check": "ok" if st == 0 else f"status {st}"}
+        if prec == "fp16":
+            entry["clocks"] = clocks
+        if rank == 0:
+            import oracle
+            pick = np.random.default_rng(93).choice(len(reqs), 4, replace=False)
+            used = sorted(set(int(reqs[i]["model"]) for i in pick))
+            remap = {mi: k for k, mi in enumerate(used)}
+            sub = reqs[pick].copy()
+            sub["model"] = [remap[int(mi)] for mi in sub["model"]]
+            ref = oracle.hybrid_decode_pages([synth.hybrid_tile_of(s, mi) for mi in used], sub, 8192, 8192,
+                                             precision=prec, fill=0.0)
+            got = phys.float().cpu().numpy()
+            worst = 0.0
+            for q in sub:
+                sl = (slice(q["dst_y"], q["dst_y"] + 128), slice(q["dst_x"], q["dst_x"] + 128))
+                a, b = got[sl][..., :3].astype(np.float64), ref[sl][..., :3]
+                worst = max(worst, float(np.abs(a - b).max() / (b.max() - b.min())))
+            entry["max_err_over_page_range"] = worst
+            entry["err_sample"] = "4 seeded requests, per-page range; RGBA16F storage rounding included"
+        out[prec] = entry
+        table.close()
+    m0 = s
+    model_bytes = sum(int(np.prod(m0[k].shape[1:])) * m0[k].itemsize for k in ("uv_bc4", "vol_bc4", "ut", "vt")) + \
+        sum(int(np.prod(m0[k].shape[1:])) * 2 for k in ("w1", "b1", "w2", "b2", "w3", "b3"))
+    touched = len(set(int(x) for x in reqs["model"]))
+    out["roofline"] = two_term_roofline(texels, HYBRID_FLOP_PER_TEXEL, hybrid_frame_bytes(len(reqs), touched,
+                                        model_bytes), out["fp16"]["ms_per_frame"] * 1e-3, peaks, peak_kind)
+    out["roofline"].update({"kernel": "k_hybrid_pages_tc", "flop_per_texel": HYBRID_FLOP_PER_TEXEL,
+                            "models_touched": touched})
+    out["vs_fp32_plain"] = out["fp16"]["value"] / out["fp32"]["value"]
+    del phys
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -475,6 +538,7 @@ def main():
     ap.add_argument("--no-pages", action="store_true", help="skip the page-decode measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the fit and scale measurements")
     ap.add_argument("--no-scale", action="store_true", help="skip the 16384^2 scale frame")
+    ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid-decoder page frame")
     ap.add_argument("--fit-steps", type=int, default=2000, help="fit steps (2000 = the fit workload)")
     ap.add_argument("--queries-log2", type=int, default=24,
                     help="point queries per step = 2^this (24 = the headline workload; smaller for profiling)")
@@ -613,11 +677,13 @@ def main():
     pages = None
     if not args.no_pages:
         pages = bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank)
-    fit = scale = None
+    fit = scale = hybrid = None
     if not args.no_extra:
         if not args.no_scale:
             scale = bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank)
         fit = bench_fit(args, ndgi, torch)
+        if not args.no_hybrid:
+            hybrid = bench_hybrid(args, ndgi, torch, peaks, peak_kind, timed, rank)
 
     if rank != 0:
         if dist is not None:
@@ -668,8 +734,14 @@ def main():
                             "streams", "matches_device_decode": e2e_ok},
         "ms_per_step_median_of_20": ms_median,
         "gpu_launches": args.steps, "clocks": clocks,
-        "fit": fit, "scale": scale, "pages": pages,
+        "fit": fit, "scale": scale, "hybrid": hybrid, "pages": pages,
     }
+    if hybrid is not None:
+        h16, hr = hybrid["fp16"], hybrid["roofline"]
+        line["hybrid_m64_fp16"] = {
+            "value": h16["value"], "unit": "Gtexels/s", "ms_per_frame": h16["ms_per_frame"], "frac": hr["frac"],
+            "bound": hr["bound"], "max_err_over_page_range": h16.get("max_err_over_page_range"),
+            "vs_fp32_plain": hybrid["vs_fp32_plain"], "device_check": h16["device_check"]}
     if pages is not None:
         # the batched page decode (the configuration the >= 60 % roofline target is stated on), in brief, last
         p16, rf = pages["fp16"], pages["roofline"]

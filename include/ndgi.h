@@ -530,6 +530,133 @@ size_t ndgi_encode_fit_workspace_size(const ndgi_fit_params *params, const ndgi_
 ndgi_status ndgi_encode_fit(const ndgi_fit_params *params, const uint16_t *targets, const ndgi_fit_config *cfg,
                             int32_t step_offset, void *ws, size_t ws_bytes, double *loss_log, void *stream);
 
+
+/* ======================================================================
+ * Hybrid feature map decoder: the paper's full decoder (Sec. 3.3, Eq. 4-5;
+ * Sec. 4).  Four feature maps per model (Eq. 5): a low-resolution 3D map
+ * F3D over (u, v, t) with 4 channels, sampled trilinearly (V_uvt), and the
+ * tri-plane F_uv (4 channels), F_ut and F_vt (2 channels each), each sampled
+ * bilinearly at the projection of (u, v, t) onto its plane.  The decoder
+ * G_Phi takes [V_uvt, V_uv, V_ut, V_vt, gamma(t)] (16 inputs; Eq. 4,
+ * gamma(t) = [sin pi t, cos pi t, sin 2 pi t, cos 2 pi t]) through two GELU
+ * hidden layers (GELU(x) = x Phi(x), the exact erf form) to linear RGB.
+ * Storage (this library's readings of what the paper leaves open):
+ *   - F_uv and each t-slice of F3D are four BC4 planes (the BC stand-in of
+ *     this library for the paper's four-channel BC7), block layout as
+ *     ndgi_model_desc's bc4 with cs = 4; F3D slices follow one another;
+ *   - F_ut and F_vt are UNORM8 (value byte / 255), layout [t][x][2];
+ *   - texel-centre convention on every axis; u and v follow address_mode,
+ *     the t axis (t in [0, 1]) clamps to its edge texels.
+ * ====================================================================== */
+
+/*
+ * A hybrid model; a view, every pointer device memory owned by the caller.
+ *   lm_w, lm_h              lightmap (tile) size: page texels -> (u, v)
+ *   uv_w, uv_h, uv_bc4      F_uv: sizes multiples of 4, [uv_h/4][uv_w/4][4][8]
+ *   vol_w, vol_h, vol_t     F3D: slice sizes multiples of 4, vol_t slices,
+ *   vol_bc4                 [vol_t][vol_h/4][vol_w/4][4][8]
+ *   ut_w, ut_t, ut          F_ut: [ut_t][ut_w][2] bytes
+ *   vt_h, vt_t, vt          F_vt: [vt_t][vt_h][2] bytes
+ *   hidden                  16, 32 or 64 (both hidden layers)
+ *   w1 [16][hidden], b1, w2 [hidden][hidden], b2, w3 [hidden][3], b3: FP32 [in][out]
+ *   address_mode            0 clamp, 1 mirrored repeat (u and v axes)
+ * uv_bc4 and vol_bc4 must be 16-byte aligned, ut and vt 2-byte aligned.
+ */
+typedef struct {
+  int32_t lm_w, lm_h;
+  int32_t uv_w, uv_h;
+  const uint8_t *uv_bc4;
+  int32_t vol_w, vol_h, vol_t;
+  const uint8_t *vol_bc4;
+  int32_t ut_w, ut_t;
+  const uint8_t *ut;
+  int32_t vt_h, vt_t;
+  const uint8_t *vt;
+  int32_t hidden;
+  const float *w1, *b1, *w2, *b2, *w3, *b3;
+  int32_t address_mode;
+} ndgi_hybrid_desc;
+
+/*
+ * Bytes of device workspace ndgi_hybrid_prepare needs for `precision`: the
+ * MLP weights re-packed for the tensor-core decode plus the decode's error
+ * and debug words.  0 for NDGI_FP32 (which needs none).
+ */
+size_t ndgi_hybrid_workspace_size(const ndgi_hybrid_desc *model, ndgi_precision precision);
+
+/*
+ * Writes the tensor-core image of the model's MLP (NDGI_FP16 or NDGI_BF16)
+ * into ws (device, 256-byte aligned, ndgi_hybrid_workspace_size bytes) and
+ * clears its error word.  Re-run after changing the weights.
+ */
+ndgi_status ndgi_hybrid_prepare(const ndgi_hybrid_desc *model, ndgi_precision precision, void *ws, void *stream);
+
+/*
+ * Random-access decode at n queries: rgb[i] = G_Phi(features(u_i, v_i, t_i))
+ * (Eq. 4).  uvt: [n][3] FP32 (device); rgb: [n][3] FP32 (device).
+ * NDGI_FP32 runs the FP32 CUDA-core decode (ws unused, may be NULL);
+ * NDGI_FP16 / NDGI_BF16 the tensor-core decode with the prepared ws (features
+ * and hidden activations rounded to the operand type, FP32 accumulation).
+ * A timed-out tensor-core wait latches bit 4 in ws's error word
+ * (ndgi_hybrid_workspace_check).
+ */
+ndgi_status ndgi_hybrid_decode_points(const ndgi_hybrid_desc *model, ndgi_precision precision, const void *ws,
+                                      const float *uvt, int64_t n, float *rgb, void *stream);
+
+/* Reads and clears the error word of a prepared hybrid workspace (as ndgi_workspace_check). */
+ndgi_status ndgi_hybrid_workspace_check(const ndgi_hybrid_desc *model, ndgi_precision precision, const void *ws,
+                                        int32_t *device_error, void *stream);
+
+/*
+ * A device table of hybrid models for the page decode (Sec. 3.5: one model
+ * per tile, each request names its tile's model).  Created from n_models
+ * host descriptors that share `hidden`; ws[i] (host array of device
+ * pointers) is model i's prepared workspace for an FP16/BF16 table, NULL for
+ * NDGI_FP32.  The table copies the descriptors (the arrays they point to
+ * must outlive it) and owns a device block with its error and debug words.
+ */
+typedef struct ndgi_hybrid_table ndgi_hybrid_table;
+ndgi_status ndgi_hybrid_table_create(const ndgi_hybrid_desc *models, const void *const *ws, int32_t n_models,
+                                     ndgi_precision precision, ndgi_hybrid_table **out);
+ndgi_status ndgi_hybrid_table_destroy(ndgi_hybrid_table *table);
+
+/*
+ * Page decode with hybrid models: texel (x0+i, y0+j) of each request is
+ * decoded at ((x0+i+0.5)/lm_w, (y0+j+0.5)/lm_h, t) with the request's model
+ * and t, and written as RGBA (A = 1) to phys (device, [phys_h][phys_w][4] of
+ * RGBA32F or RGBA16F) at (dst_x+i, dst_y+j).  reqs: n requests (device).
+ * The host checks n, phys and format; the device checks each request
+ * (model index, rectangle inside the lightmap and the physical texture)
+ * and skips a bad one, latching bit 0 of the table's error word.
+ */
+ndgi_status ndgi_hybrid_decode_pages(ndgi_hybrid_table *table, const ndgi_page_req *reqs, int32_t n, void *phys,
+                                     int64_t phys_w, int64_t phys_h, ndgi_out_format format, void *stream);
+
+/*
+ * Test hook for the timeout path (no paper counterpart): flags = 1 makes the
+ * later tensor-core decodes that use ws (point decodes; with `model` and
+ * `precision` describing it) and/or `table` (page decodes) take their real
+ * timeout path before any MMA, as ndgi_debug_workspace_inject does; 0
+ * restores normal decodes.  Either of ws and table may be NULL.
+ */
+ndgi_status ndgi_hybrid_debug_inject(const ndgi_hybrid_desc *model, ndgi_precision precision, void *ws,
+                                     ndgi_hybrid_table *table, int32_t flags, void *stream);
+
+/* Synchronises, reads and clears the table's error word (bit 0 bad request, bit 4 timeout). */
+ndgi_status ndgi_hybrid_table_check(ndgi_hybrid_table *table, int32_t *device_error, void *stream);
+
+/*
+ * Storage of a hybrid model in bits per lightmap texel, the paper's accounting
+ * (Table "compression" and Table "config"): the BC-compressed maps F_uv and
+ * F3D at bc_bits_per_texel bits per texel of all four channels (8 for BC7,
+ * the paper's format; 16 for this library's four BC4 planes), F_ut and F_vt
+ * at 8 bits per value, and the MLP's parameters at mlp_bits (16 for FP16),
+ * divided by lm_w * lm_h * n_lightmaps texels.  Host only; -1 on a bad
+ * argument.
+ */
+double ndgi_model_bpp(const ndgi_hybrid_desc *model, int32_t n_lightmaps, int32_t bc_bits_per_texel,
+                      int32_t mlp_bits);
+
 #ifdef __cplusplus
 }
 #endif

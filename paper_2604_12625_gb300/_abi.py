@@ -33,6 +33,15 @@ class PageReq(C.Structure):
                 ("h", C.c_int32), ("t", C.c_float), ("dst_x", C.c_int32), ("dst_y", C.c_int32)]
 
 
+class HybridDesc(C.Structure):
+    _fields_ = [("lm_w", C.c_int32), ("lm_h", C.c_int32), ("uv_w", C.c_int32), ("uv_h", C.c_int32),
+                ("uv_bc4", C.c_void_p), ("vol_w", C.c_int32), ("vol_h", C.c_int32), ("vol_t", C.c_int32),
+                ("vol_bc4", C.c_void_p), ("ut_w", C.c_int32), ("ut_t", C.c_int32), ("ut", C.c_void_p),
+                ("vt_h", C.c_int32), ("vt_t", C.c_int32), ("vt", C.c_void_p), ("hidden", C.c_int32),
+                ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+
+
 FIT_TENSORS = ("ea", "eb", "w", "temporal", "w1", "b1", "w2", "b2", "w3", "b3")
 
 
@@ -88,6 +97,16 @@ SIGNATURES = [
     ("ndgi_fit_backward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),
     ("ndgi_encode_fit_workspace_size", _sz, [_vp, _vp]),
     ("ndgi_encode_fit", C.c_int, [_vp, _vp, _vp, _i32, _vp, _sz, _vp, _vp]),
+    ("ndgi_hybrid_workspace_size", _sz, [_vp, C.c_int]),
+    ("ndgi_hybrid_prepare", C.c_int, [_vp, C.c_int, _vp, _vp]),
+    ("ndgi_hybrid_decode_points", C.c_int, [_vp, C.c_int, _vp, _vp, _i64, _vp, _vp]),
+    ("ndgi_hybrid_workspace_check", C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    ("ndgi_hybrid_debug_inject", C.c_int, [_vp, C.c_int, _vp, _vp, _i32, _vp]),
+    ("ndgi_hybrid_table_create", C.c_int, [_vp, _vp, _i32, C.c_int, _vp]),
+    ("ndgi_hybrid_table_destroy", C.c_int, [_vp]),
+    ("ndgi_hybrid_decode_pages", C.c_int, [_vp, _vp, _i32, _vp, _i64, _i64, C.c_int, _vp]),
+    ("ndgi_hybrid_table_check", C.c_int, [_vp, _vp, _vp]),
+    ("ndgi_model_bpp", C.c_double, [_vp, _i32, _i32, _i32]),
 ]
 
 _lib = None

@@ -457,3 +457,164 @@ def ndgi_encode_fit(state, targets, cfg, step_offset=0, ws=None, loss_log=None, 
     check(lib().ndgi_encode_fit(C.byref(state.params), _p(targets), C.byref(cfg), int(step_offset), _p(ws),
                                 ws.numel(), _p(loss_log), _stream(stream)))
     return ws, loss_log
+
+
+# ---------------------------------------------------------------------------
+# Hybrid feature map decoder (the paper's full decoder)
+# ---------------------------------------------------------------------------
+class HybridModel:
+    """A hybrid model resident on the GPU plus its ndgi_hybrid_desc.
+
+    Tensors: uv_bc4 uint8 [uv_h/4][uv_w/4][4][8], vol_bc4 uint8
+    [vol_t][vol_h/4][vol_w/4][4][8], ut uint8 [ut_t][ut_w][2], vt uint8
+    [vt_t][vt_h][2], MLP weights float32 [in][out] (w1 [16][hidden]).
+    Prepared tensor-core workspaces are kept per precision in ``self.ws``.
+    """
+
+    def __init__(self, lm_w, lm_h, uv_bc4, vol_bc4, ut, vt, w1, b1, w2, b2, w3, b3, address_mode=0):
+        self.lm_w, self.lm_h = int(lm_w), int(lm_h)
+        self.uv_bc4 = _need(uv_bc4, torch.uint8, "uv_bc4")
+        self.vol_bc4 = _need(vol_bc4, torch.uint8, "vol_bc4")
+        self.ut = _need(ut, torch.uint8, "ut")
+        self.vt = _need(vt, torch.uint8, "vt")
+        bh, bw, four, eight = uv_bc4.shape
+        assert four == 4 and eight == 8
+        vt_, vbh, vbw, four, eight = vol_bc4.shape
+        assert four == 4 and eight == 8
+        self.w = {k: _need(v, torch.float32, k) for k, v in
+                  dict(w1=w1, b1=b1, w2=w2, b2=b2, w3=w3, b3=b3).items()}
+        self.hidden = w2.shape[0]
+        self.address_mode = int(address_mode)
+        self.desc = A.HybridDesc(self.lm_w, self.lm_h, bw * 4, bh * 4, uv_bc4.data_ptr(), vbw * 4, vbh * 4, vt_,
+                                 vol_bc4.data_ptr(), ut.shape[1], ut.shape[0], ut.data_ptr(), vt.shape[1],
+                                 vt.shape[0], vt.data_ptr(), self.hidden,
+                                 *[self.w[k].data_ptr() for k in ("w1", "b1", "w2", "b2", "w3", "b3")],
+                                 self.address_mode)
+        self.ws = {}
+
+    @classmethod
+    def from_arrays(cls, m, device="cuda"):
+        """From a dict of numpy arrays (the layout of synth.hybrid_model)."""
+        def t(a):
+            return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return cls(m["lm_w"], m["lm_h"], t(m["uv_bc4"]), t(m["vol_bc4"]), t(m["ut"]), t(m["vt"]), t(m["w1"]),
+                   t(m["b1"]), t(m["w2"]), t(m["b2"]), t(m["w3"]), t(m["b3"]), m.get("address_mode", 0))
+
+    @classmethod
+    def from_set(cls, s, device="cuda"):
+        """All models of a stacked set (synth.hybrid_tile_set) as views into one device tensor per array."""
+        big = {k: torch.from_numpy(np.ascontiguousarray(s[k])).to(device)
+               for k in ("uv_bc4", "vol_bc4", "ut", "vt", "w1", "b1", "w2", "b2", "w3", "b3")}
+        return [cls(s["lm_w"], s["lm_h"], *[big[k][i] for k in ("uv_bc4", "vol_bc4", "ut", "vt", "w1", "b1", "w2",
+                                                               "b2", "w3", "b3")], s.get("address_mode", 0))
+                for i in range(int(s["n_tiles"]))]
+
+    def workspace(self, precision):
+        precision = _prec(precision)
+        if precision == A.NDGI_FP32:
+            return None
+        if precision not in self.ws:
+            self.ws[precision] = ndgi_hybrid_prepare(self, precision)
+        return self.ws[precision]
+
+
+def hybrid_prepare_set(models, precision, stream=None):
+    """Prepares every model of a list into slices of one device workspace tensor (256-byte aligned)."""
+    precision = _prec(precision)
+    if precision == A.NDGI_FP32:
+        return None
+    n = ndgi_hybrid_workspace_size(models[0], precision)
+    ws = torch.empty(n * len(models), dtype=torch.uint8, device=models[0].uv_bc4.device)
+    for i, m in enumerate(models):
+        m.ws[precision] = ndgi_hybrid_prepare(m, precision, ws[i * n:(i + 1) * n], stream)
+    return ws
+
+
+def ndgi_hybrid_workspace_size(model, precision):
+    return int(lib().ndgi_hybrid_workspace_size(C.byref(model.desc), _prec(precision)))
+
+
+def ndgi_hybrid_prepare(model, precision, ws=None, stream=None):
+    """Packs the hybrid model's MLP for a tensor-core decode; returns the workspace tensor."""
+    n = ndgi_hybrid_workspace_size(model, precision)
+    if ws is None:
+        ws = torch.empty(max(n, 256), dtype=torch.uint8, device=model.uv_bc4.device)
+    check(lib().ndgi_hybrid_prepare(C.byref(model.desc), _prec(precision), _p(ws), _stream(stream)))
+    return ws
+
+
+def ndgi_hybrid_decode_points(model, uvt, precision="fp32", out=None, stream=None):
+    """rgb [n][3] float32 of the hybrid decoder at queries uvt [n][3] float32."""
+    _need(uvt, torch.float32, "uvt")
+    n = uvt.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=uvt.device)
+    check(lib().ndgi_hybrid_decode_points(C.byref(model.desc), _prec(precision), _p(model.workspace(precision)),
+                                          _p(uvt), n, _p(out), _stream(stream)))
+    return out
+
+
+def ndgi_hybrid_workspace_check(model, precision, stream=None):
+    """(status, error word) of the hybrid point decodes that used the model's workspace; clears the word."""
+    err = C.c_int32(0)
+    st = lib().ndgi_hybrid_workspace_check(C.byref(model.desc), _prec(precision), _p(model.workspace(precision)),
+                                           C.byref(err), _stream(stream))
+    return st, err.value
+
+
+def ndgi_hybrid_debug_inject(model=None, precision="fp16", table=None, flags=1, stream=None):
+    """Test hook: flags = 1 makes the tensor-core decodes that use the model's workspace and/or the table take
+    their timeout path before any MMA; 0 = normal."""
+    desc = C.byref(model.desc) if model is not None else None
+    ws = _p(model.workspace(precision)) if model is not None else None
+    check(lib().ndgi_hybrid_debug_inject(desc, _prec(precision), ws, table.handle if table is not None else None,
+                                         int(flags), _stream(stream)))
+
+
+class HybridTable:
+    """ndgi_hybrid_table_* wrapper: the device table of hybrid models of a page decode."""
+
+    def __init__(self, models, precision):
+        self.models = list(models)
+        self.precision = _prec(precision)
+        descs = (A.HybridDesc * len(self.models))(*[m.desc for m in self.models])
+        ws = [m.workspace(self.precision) for m in self.models]
+        ws_arr = (C.c_void_p * len(ws))(*[w.data_ptr() if w is not None else None for w in ws])
+        self._keep = (descs, ws_arr, ws)
+        h = C.c_void_p()
+        check(lib().ndgi_hybrid_table_create(descs, ws_arr, len(self.models), self.precision, C.byref(h)))
+        self.handle = h
+
+    def decode(self, reqs, n, phys, stream=None):
+        """Decodes n requests (int32 [n][8] CUDA tensor) into phys ([h][w][4] float32 or float16)."""
+        if phys.dtype == torch.float32:
+            fmt = A.NDGI_RGBA32F
+        elif phys.dtype == torch.float16:
+            fmt = A.NDGI_RGBA16F
+        else:
+            raise ValueError("phys must be float32 or float16 RGBA")
+        assert phys.is_cuda and phys.is_contiguous() and phys.shape[-1] == 4
+        check(lib().ndgi_hybrid_decode_pages(self.handle, _p(reqs), int(n), _p(phys), phys.shape[1], phys.shape[0],
+                                             fmt, _stream(stream)))
+
+    def check(self, stream=None):
+        err = C.c_int32(0)
+        st = lib().ndgi_hybrid_table_check(self.handle, C.byref(err), _stream(stream))
+        return st, err.value
+
+    def close(self):
+        if self.handle:
+            check(lib().ndgi_hybrid_table_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ndgi_model_bpp(desc, n_lightmaps, bc_bits_per_texel=8, mlp_bits=16):
+    """Bits per lightmap texel of a hybrid model's storage (host only; desc an A.HybridDesc or HybridModel)."""
+    d = desc.desc if isinstance(desc, HybridModel) else desc
+    return float(lib().ndgi_model_bpp(C.byref(d), int(n_lightmaps), int(bc_bits_per_texel), int(mlp_bits)))

@@ -1,0 +1,791 @@
+// Hybrid feature map decoder: the paper's full decoder (Sec. 3.3, Eq. 4-5;
+// Sec. 4).  Per query (u, v, t):
+//   V_uvt  trilinear sample of F3D (4 BC4 planes per t-slice): the two
+//          slices around t, each bilinear at (u, v), then linear in t;
+//   V_uv   bilinear sample of F_uv (4 BC4 planes);
+//   V_ut   bilinear sample of the UNORM8 plane F_ut at (u, t), 2 channels;
+//   V_vt   bilinear sample of F_vt at (v, t), 2 channels;
+//   gamma  [sin pi t, cos pi t, sin 2 pi t, cos 2 pi t];
+// x = [V_uvt, V_uv, V_ut, V_vt, gamma] (16 values) -> GELU(x W1 + b1) ->
+// GELU(. W2 + b2) -> . W3 + b3.
+//
+// Two decodes share the FP32 feature gather:
+//   - CUDA cores, FP32 throughout (k_hybrid_points_f32 / k_hybrid_pages_f32);
+//   - tensor cores (k_hybrid_tc): the 16 features and the ones column that
+//     carries b1 are one K = 32 FP16/BF16 row of tensor memory per query, and
+//     the three layers run on the per-lane engine of tc_engine.cuh with the
+//     GELU epilogue; the next tile's gather overlaps this tile's layer 2, and
+//     layer 3 goes out with the next tile's layer 1 (two MMA round trips per
+//     tile).  For pages each request's model image is staged in shared memory
+//     once per request and the CTA's four lanes split the request's tiles.
+#include <vector>
+
+#include "hybrid.h"
+#include "tc_engine.cuh"
+
+namespace ndgi {
+
+// ---------------------------------------------------------------------------
+// Feature gather (FP32)
+// ---------------------------------------------------------------------------
+
+// Bilinear sample of four BC4 planes [h/4][bw][4][8] at taps (x0|x1, y0|y1):
+// a tap's four planes are one 32-byte block line (two 16-byte loads).
+__device__ __forceinline__ void bc4x4_bilinear(const uint8_t* __restrict__ bc4, int bw, int x0, int x1, int y0,
+                                               int y1, float fx, float fy, const uint2* lut, float* out) {
+  const int tx[4] = {x0, x1, x0, x1}, ty[4] = {y0, y0, y1, y1};
+  float f[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint4* line = reinterpret_cast<const uint4*>(bc4 + ((size_t)(ty[q] >> 2) * bw + (tx[q] >> 2)) * 32);
+    const uint4 a = __ldg(line), b = __ldg(line + 1);
+    const uint32_t shift = 16u + 3u * (uint32_t)(((ty[q] & 3) << 2) | (tx[q] & 3));
+    f[q][0] = p35_value(bc4_p35_lut(a.x, a.y, shift, lut));
+    f[q][1] = p35_value(bc4_p35_lut(a.z, a.w, shift, lut));
+    f[q][2] = p35_value(bc4_p35_lut(b.x, b.y, shift, lut));
+    f[q][3] = p35_value(bc4_p35_lut(b.z, b.w, shift, lut));
+  }
+  const float gx = 1.0f - fx, gy = 1.0f - fy;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out[c] = gy * (gx * f[0][c] + fx * f[1][c]) + fy * (gx * f[2][c] + fx * f[3][c]);
+}
+
+// Bilinear sample of a two-channel UNORM8 plane [ny][nx][2] (one 16-bit load per tap).
+__device__ __forceinline__ void u8x2_bilinear(const uint8_t* __restrict__ p, int nx, int x0, int x1, int y0, int y1,
+                                              float fx, float fy, float* out) {
+  const unsigned short* w = reinterpret_cast<const unsigned short*>(p);
+  const uint32_t q00 = __ldg(w + (size_t)y0 * nx + x0), q10 = __ldg(w + (size_t)y0 * nx + x1);
+  const uint32_t q01 = __ldg(w + (size_t)y1 * nx + x0), q11 = __ldg(w + (size_t)y1 * nx + x1);
+  const float gx = 1.0f - fx, gy = 1.0f - fy, s = 1.0f / 255.0f;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int sh = 8 * c;
+    const float f00 = (float)((q00 >> sh) & 255u) * s, f10 = (float)((q10 >> sh) & 255u) * s;
+    const float f01 = (float)((q01 >> sh) & 255u) * s, f11 = (float)((q11 >> sh) & 255u) * s;
+    out[c] = gy * (gx * f00 + fx * f10) + fy * (gx * f01 + fx * f11);
+  }
+}
+
+// The decoder input x[16] at (u, v, t) (Eq. 4); lut: init_p35_lut's table.
+__device__ __forceinline__ void hybrid_features(const DevHybrid& m, float u, float v, float t, float (&x)[16],
+                                                const uint2* lut) {
+  const int mode = m.address_mode;
+  int x0, x1, y0, y1, z0, z1;
+  float fx, fy, fz;
+  axis_setup(u, m.vol_w, mode, x0, x1, fx);
+  axis_setup(v, m.vol_h, mode, y0, y1, fy);
+  axis_setup(t, m.vol_t, 0, z0, z1, fz);
+  const size_t slice = (size_t)(m.vol_h / 4) * (size_t)(m.vol_w / 4) * 32;
+  float a[4], b[4];
+  bc4x4_bilinear(m.vol + (size_t)z0 * slice, m.vol_w / 4, x0, x1, y0, y1, fx, fy, lut, a);
+  bc4x4_bilinear(m.vol + (size_t)z1 * slice, m.vol_w / 4, x0, x1, y0, y1, fx, fy, lut, b);
+  const float gz = 1.0f - fz;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) x[c] = gz * a[c] + fz * b[c];
+  axis_setup(u, m.uv_w, mode, x0, x1, fx);
+  axis_setup(v, m.uv_h, mode, y0, y1, fy);
+  bc4x4_bilinear(m.uv, m.uv_w / 4, x0, x1, y0, y1, fx, fy, lut, x + 4);
+  axis_setup(u, m.ut_w, mode, x0, x1, fx);
+  axis_setup(t, m.ut_t, 0, y0, y1, fy);
+  u8x2_bilinear(m.ut, m.ut_w, x0, x1, y0, y1, fx, fy, x + 8);
+  axis_setup(v, m.vt_h, mode, x0, x1, fx);
+  axis_setup(t, m.vt_t, 0, y0, y1, fy);
+  u8x2_bilinear(m.vt, m.vt_h, x0, x1, y0, y1, fx, fy, x + 10);
+  sincospif(t, &x[12], &x[13]);
+  sincospif(2.0f * t, &x[14], &x[15]);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 CUDA-core decode
+// ---------------------------------------------------------------------------
+
+// Shared-memory copy of one model's MLP: w1 [16][H], b1, w2 [H][H], b2, w3 [H][3], b3.
+template <int H>
+struct HybridMlp32 {
+  static constexpr int kW1 = 0, kB1 = 16 * H, kW2 = kB1 + H, kB2 = kW2 + H * H, kW3 = kB2 + H, kB3 = kW3 + 3 * H;
+  static constexpr int kFloats = kB3 + 3;
+};
+
+template <int H>
+__device__ __forceinline__ void load_mlp32(const DevHybrid& m, float* sw, int tid, int nt) {
+  using M = HybridMlp32<H>;
+  for (int i = tid; i < 16 * H; i += nt) sw[M::kW1 + i] = m.w1[i];
+  for (int i = tid; i < H * H; i += nt) sw[M::kW2 + i] = m.w2[i];
+  for (int i = tid; i < 3 * H; i += nt) sw[M::kW3 + i] = m.w3[i];
+  for (int i = tid; i < H; i += nt) {
+    sw[M::kB1 + i] = m.b1[i];
+    sw[M::kB2 + i] = m.b2[i];
+  }
+  if (tid < 3) sw[M::kB3 + tid] = m.b3[tid];
+}
+
+// Layer 1 one hidden unit at a time, each folded into the layer-2
+// accumulators as soon as it is known (H + 16 live values, not 2H).
+template <int H>
+__device__ __forceinline__ void mlp32(const float* sw, const float (&x)[16], float& r0, float& r1, float& r2) {
+  using M = HybridMlp32<H>;
+  float z2[H];
+#pragma unroll
+  for (int o = 0; o < H; ++o) z2[o] = sw[M::kB2 + o];
+#pragma unroll 1
+  for (int i = 0; i < H; ++i) {
+    float z = sw[M::kB1 + i];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) z = fmaf(x[k], sw[M::kW1 + k * H + i], z);
+    const float h = gelu(z);
+#pragma unroll
+    for (int o = 0; o < H; ++o) z2[o] = fmaf(h, sw[M::kW2 + i * H + o], z2[o]);
+  }
+  r0 = sw[M::kB3 + 0];
+  r1 = sw[M::kB3 + 1];
+  r2 = sw[M::kB3 + 2];
+#pragma unroll
+  for (int o = 0; o < H; ++o) {
+    const float h = gelu(z2[o]);
+    r0 = fmaf(h, sw[M::kW3 + 3 * o + 0], r0);
+    r1 = fmaf(h, sw[M::kW3 + 3 * o + 1], r1);
+    r2 = fmaf(h, sw[M::kW3 + 3 * o + 2], r2);
+  }
+}
+
+template <int H>
+__global__ void __launch_bounds__(256) k_hybrid_points_f32(DevHybrid m, const float* __restrict__ uvt, int64_t n,
+                                                           float* __restrict__ rgb) {
+  __shared__ float sw[HybridMlp32<H>::kFloats];
+  __shared__ uint2 lut[16];
+  load_mlp32<H>(m, sw, threadIdx.x, blockDim.x);
+  init_p35_lut(lut, threadIdx.x);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float x[16];
+    hybrid_features(m, __ldcs(uvt + 3 * i), __ldcs(uvt + 3 * i + 1), __ldcs(uvt + 3 * i + 2), x, lut);
+    float r0, r1, r2;
+    mlp32<H>(sw, x, r0, r1, r2);
+    __stcs(rgb + 3 * i, r0);
+    __stcs(rgb + 3 * i + 1, r1);
+    __stcs(rgb + 3 * i + 2, r2);
+  }
+}
+
+// A request is decoded only if its model index and both rectangles are valid.
+__device__ __forceinline__ bool hybrid_req_ok(const ndgi_page_req& r, const DevHybrid* models, int n_models,
+                                              int64_t phys_w, int64_t phys_h) {
+  if (r.model < 0 || r.model >= n_models) return false;
+  const DevHybrid& m = models[r.model];
+  return r.w >= 1 && r.w <= 128 && r.h >= 1 && r.h <= 128 && r.x0 >= 0 && r.y0 >= 0 && r.x0 + r.w <= m.lm_w &&
+         r.y0 + r.h <= m.lm_h && r.dst_x >= 0 && r.dst_y >= 0 && r.dst_x + r.w <= phys_w && r.dst_y + r.h <= phys_h;
+}
+
+__device__ __forceinline__ void put_texel(void* phys, int fmt, int64_t o, float y0, float y1, float y2) {
+  if (fmt == NDGI_RGBA32F) {
+    __stcs(reinterpret_cast<float4*>(phys) + o, make_float4(y0, y1, y2, 1.0f));
+  } else {
+    __stcs(reinterpret_cast<uint2*>(phys) + o, make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f)));
+  }
+}
+
+// One request per CTA at a time (its model's MLP staged in shared memory).
+template <int H>
+__global__ void __launch_bounds__(256) k_hybrid_pages_f32(HybridPagesCtx c, const ndgi_page_req* __restrict__ reqs,
+                                                          int n) {
+  __shared__ float sw[HybridMlp32<H>::kFloats];
+  __shared__ uint2 lut[16];
+  init_p35_lut(lut, threadIdx.x);
+  for (int ri = blockIdx.x; ri < n; ri += gridDim.x) {
+    const ndgi_page_req r = reqs[ri];
+    const bool ok = hybrid_req_ok(r, c.models, c.n_models, c.phys_w, c.phys_h);
+    __syncthreads();   // the previous request's texels are done with sw
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(c.error_word, 1);
+      continue;
+    }
+    const DevHybrid m = c.models[r.model];
+    load_mlp32<H>(m, sw, threadIdx.x, blockDim.x);
+    __syncthreads();
+    for (int i = threadIdx.x; i < r.w * r.h; i += blockDim.x) {
+      const int ix = i % r.w, iy = i / r.w;
+      const float u = ((float)(r.x0 + ix) + 0.5f) / (float)m.lm_w;
+      const float v = ((float)(r.y0 + iy) + 0.5f) / (float)m.lm_h;
+      float x[16];
+      hybrid_features(m, u, v, r.t, x, lut);
+      float y0, y1, y2;
+      mlp32<H>(sw, x, y0, y1, y2);
+      put_texel(c.phys, c.fmt, (int64_t)(r.dst_y + iy) * c.phys_w + (r.dst_x + ix), y0, y1, y2);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core decode (FP16/BF16 operands, FP32 accumulation)
+// ---------------------------------------------------------------------------
+// The model image is the point-decode layout of tc_engine.cuh with 16 inputs
+// and no temporal line: B2 [H][H+16] (column H = b2), B3 [16][H+16] (rows 0..2
+// = W3^T, column H = b3), B1 [H][32] (columns 0..15 = W1^T, column 16 = b1),
+// then the error and debug words.
+template <int H>
+using HybridLayout = TcLayout<16, 0, H>;
+
+template <int H>
+struct HybridSmem {
+  using L = HybridLayout<H>;
+  static constexpr uint32_t kW = 0;                    // B2, B3
+  static constexpr uint32_t kB1 = L::kShared;          // B1
+  static constexpr uint32_t kBytes = kB1 + H * L::K1P * 2;
+};
+
+constexpr int kHybLanes = 4;
+
+template <int H, bool BF16>
+__global__ void k_hybrid_prepare(DevHybrid m, unsigned char* __restrict__ ws) {
+  using L = HybridLayout<H>;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int i = tid; i < H * L::K2; i += nt) {
+    const int n = i / L::K2, k = i % L::K2;
+    const float v = k < H ? m.w2[k * H + n] : (k == H ? m.b2[n] : 0.0f);
+    *reinterpret_cast<uint16_t*>(ws + L::kB2 + kmajor_offset(n, k, L::K2)) = to_bits<BF16>(v);
+  }
+  for (int i = tid; i < L::N3 * L::K2; i += nt) {
+    const int n = i / L::K2, k = i % L::K2;
+    const float v = n >= 3 ? 0.0f : (k < H ? m.w3[k * 3 + n] : (k == H ? m.b3[n] : 0.0f));
+    *reinterpret_cast<uint16_t*>(ws + L::kB3 + kmajor_offset(n, k, L::K2)) = to_bits<BF16>(v);
+  }
+  for (int i = tid; i < H * L::K1P; i += nt) {
+    const int n = i / L::K1P, k = i % L::K1P;
+    const float v = k < 16 ? m.w1[k * H + n] : (k == 16 ? m.b1[n] : 0.0f);
+    *reinterpret_cast<uint16_t*>(ws + L::kB1P + kmajor_offset(n, k, L::K1P)) = to_bits<BF16>(v);
+  }
+  if (tid == 0) {
+    *reinterpret_cast<int*>(ws + L::kErrOff) = 0;
+    *reinterpret_cast<int*>(ws + L::kDbgOff) = 0;
+  }
+}
+
+// Layer-1 row: the 16 features, then 1 (column 16, carries b1), then zeros.
+template <bool BF16>
+__device__ __forceinline__ void hybrid_pack_a1(const float (&x)[16], uint32_t (&w)[16]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) w[k] = pack2<BF16>(x[2 * k], x[2 * k + 1]);
+  w[8] = BF16 ? 0x3F80u : 0x3C00u;
+#pragma unroll
+  for (int k = 9; k < 16; ++k) w[k] = 0u;
+}
+
+// One lane's tiles first, first + step, ... (< tiles) through the three
+// layers, software-pipelined: the next tile's gather runs while this tile's
+// layer 2 is on the tensor core, and its layer 1 is issued with this tile's
+// layer 3.  gather(tile, w) gives this thread's layer-1 row, emit(tile, rgb)
+// takes its result.  Returns false once a wait of the lane has timed out.
+template <typename E, typename G, typename O>
+__device__ __forceinline__ bool hybrid_lane_run(E& e, int64_t first, int64_t step, int64_t tiles, G&& gather,
+                                                O&& emit, bool& inflight) {
+  static_assert(E::kMerge, "layer 3 and the next layer 1 share one commit");
+  if (first >= tiles) return true;
+  {
+    uint32_t w[E::kA1Words];
+    gather(first, w);
+    e.write_a1(0, w);
+  }
+  if (!e.layer1(0)) return false;
+  inflight = true;
+  int64_t cur = first, prev = -1, next = first + step;
+  for (;;) {
+    inflight = !e.wait(0);   // layer 1 of cur (and layer 3 of prev)
+    if (prev >= 0) {         // lane-uniform: false on the first tile only
+      float y0, y1, y2;
+      e.output(0, y0, y1, y2);   // D3 is read before the layer-2 rows overwrite its columns
+      emit(prev, y0, y1, y2);
+    }
+    e.template epilogue_gelu<true>(0);
+    if (!e.layer2(0)) return false;
+    inflight = true;
+    const bool more = next < tiles;
+    if (more) {
+      uint32_t w[E::kA1Words];
+      gather(next, w);
+      e.write_a1(0, w);
+    }
+    inflight = !e.wait(0);   // layer 2
+    e.template epilogue_gelu<false>(0);
+    if (!e.layer3(0, more)) return false;
+    inflight = true;
+    if (!more) break;
+    prev = cur;
+    cur = next;
+    next += step;
+  }
+  inflight = !e.wait(0);     // the last layer 3
+  float y0, y1, y2;
+  e.output(0, y0, y1, y2);
+  emit(cur, y0, y1, y2);
+  return true;
+}
+
+template <int H, bool BF16>
+__global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
+    k_hybrid_points_tc(DevHybrid m, const float* __restrict__ uvt, int64_t n, float* __restrict__ rgb) {
+  using L = HybridLayout<H>;
+  using S = HybridSmem<H>;
+  constexpr int P = BF16 ? kBF16 : kF16;
+  using E = Engine<H, P, L::K1P, 1>;
+  static_assert(kHybLanes * E::kSlotCols <= 512, "slots exceed the SM's tensor memory");
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t bars[kHybLanes];
+  __shared__ uint32_t slot;
+  __shared__ uint2 lut[16];
+  __shared__ float s_b3[3];
+  const int tid = threadIdx.x;
+  copy16(sm + S::kW, m.ws, L::kShared, tid, blockDim.x);
+  copy16(sm + S::kB1, m.ws + L::kB1P, H * L::K1P * 2, tid, blockDim.x);
+  init_p35_lut(lut, tid);
+  if (tid < 3) s_b3[tid] = stored_b3<BF16>(m.ws + L::kB3, tid, H, L::K2);
+  const uint32_t tbase = cta_setup<kHybLanes, E::kSlotCols>(bars, &slot, tid);
+  const uint32_t base = smem_addr(sm);
+  E e;
+  engine_init<H, P, L::K1P, 1>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
+  e.b3 = s_b3;
+  int* err = reinterpret_cast<int*>(m.ws + L::kErrOff);
+  if (*reinterpret_cast<const int*>(m.ws + L::kDbgOff) & kDbgInjectTimeout) inject_timeout(e);
+  const int t = e.t;
+  auto gather = [&](int64_t tl, uint32_t (&w)[16]) {
+    const int64_t q = tl * 128 + t;
+    float x[16];
+    if (q < n) {
+      hybrid_features(m, __ldcs(uvt + 3 * q), __ldcs(uvt + 3 * q + 1), __ldcs(uvt + 3 * q + 2), x, lut);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) x[k] = 0.0f;
+    }
+    hybrid_pack_a1<BF16>(x, w);
+  };
+  auto emit = [&](int64_t tl, float y0, float y1, float y2) {
+    const int64_t q = tl * 128 + t;
+    if (q < n) {
+      __stcs(rgb + 3 * q, y0);
+      __stcs(rgb + 3 * q + 1, y1);
+      __stcs(rgb + 3 * q + 2, y2);
+    }
+  };
+  bool inflight[1] = {false};
+  const bool ok = hybrid_lane_run(e, (int64_t)blockIdx.x * kHybLanes + e.wg, (int64_t)gridDim.x * kHybLanes,
+                                  (n + 127) / 128, gather, emit, inflight[0]);
+  cta_teardown<kHybLanes, E::kSlotCols, E, 1>(tbase, e, inflight, !ok, tid, err);
+}
+
+// Pages: one request per CTA at a time; its model's image is staged in shared
+// memory, then the four lanes take the request's 128-texel tiles in turn
+// (texel k of the request is (k mod w, k div w)).
+template <int H, bool BF16>
+__global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
+    k_hybrid_pages_tc(HybridPagesCtx c, const ndgi_page_req* __restrict__ reqs, int n) {
+  using L = HybridLayout<H>;
+  using S = HybridSmem<H>;
+  constexpr int P = BF16 ? kBF16 : kF16;
+  using E = Engine<H, P, L::K1P, 1>;
+  static_assert(kHybLanes * E::kSlotCols <= 512, "slots exceed the SM's tensor memory");
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t bars[kHybLanes];
+  __shared__ uint32_t slot;
+  __shared__ uint2 lut[16];
+  __shared__ float s_b3[3];
+  const int tid = threadIdx.x;
+  init_p35_lut(lut, tid);
+  const uint32_t tbase = cta_setup<kHybLanes, E::kSlotCols>(bars, &slot, tid);
+  const uint32_t base = smem_addr(sm);
+  E e;
+  engine_init<H, P, L::K1P, 1>(e, tbase, bars, tid, base + S::kB1, base + S::kW + L::kB2, base + S::kW + L::kB3);
+  e.b3 = s_b3;
+  if (c.debug_word && (*c.debug_word & kDbgInjectTimeout)) inject_timeout(e);
+  const int t = e.t;
+  bool inflight[1] = {false}, stopped = false;
+  for (int ri = blockIdx.x; ri < n; ri += gridDim.x) {
+    const ndgi_page_req r = reqs[ri];
+    const bool ok = hybrid_req_ok(r, c.models, c.n_models, c.phys_w, c.phys_h);
+    tc_fence_before();
+    __syncthreads();   // every lane is done with the previous request's image
+    if (!ok) {
+      if (tid == 0) atomicOr(c.error_word, 1);
+      continue;
+    }
+    const DevHybrid& m = c.models[r.model];
+    copy16(sm + S::kW, m.ws, L::kShared, tid, blockDim.x);
+    copy16(sm + S::kB1, m.ws + L::kB1P, H * L::K1P * 2, tid, blockDim.x);
+    if (tid < 3) s_b3[tid] = stored_b3<BF16>(m.ws + L::kB3, tid, H, L::K2);
+    fence_async_smem();
+    __syncthreads();
+    tc_fence_after();
+    if (stopped) continue;
+    const int texels = r.w * r.h;
+    auto gather = [&](int64_t tl, uint32_t (&w)[16]) {
+      const int k = (int)tl * 128 + t;
+      float x[16];
+      if (k < texels) {
+        const int ix = k % r.w, iy = k / r.w;
+        const float u = ((float)(r.x0 + ix) + 0.5f) / (float)m.lm_w;
+        const float v = ((float)(r.y0 + iy) + 0.5f) / (float)m.lm_h;
+        hybrid_features(m, u, v, r.t, x, lut);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = 0.0f;
+      }
+      hybrid_pack_a1<BF16>(x, w);
+    };
+    auto emit = [&](int64_t tl, float y0, float y1, float y2) {
+      const int k = (int)tl * 128 + t;
+      if (k < texels)
+        put_texel(c.phys, c.fmt, (int64_t)(r.dst_y + k / r.w) * c.phys_w + (r.dst_x + k % r.w), y0, y1, y2);
+    };
+    stopped = !hybrid_lane_run(e, e.wg, kHybLanes, (texels + 127) / 128, gather, emit, inflight[0]);
+  }
+  cta_teardown<kHybLanes, E::kSlotCols, E, 1>(tbase, e, inflight, stopped, tid, c.error_word);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+#define NDGI_HYBRID_HIDDEN(X) X(16) X(32) X(64)
+
+bool hybrid_hidden_ok(int hidden) {
+#define X(H) if (hidden == H) return true;
+  NDGI_HYBRID_HIDDEN(X)
+#undef X
+  return false;
+}
+
+size_t hybrid_ws_bytes(int hidden) {
+#define X(H) if (hidden == H) return (HybridLayout<H>::kWsBytes + 16 + 255) / 256 * 256;
+  NDGI_HYBRID_HIDDEN(X)
+#undef X
+  return 0;
+}
+
+int hybrid_err_offset(int hidden) {
+#define X(H) if (hidden == H) return (int)HybridLayout<H>::kErrOff;
+  NDGI_HYBRID_HIDDEN(X)
+#undef X
+  return -1;
+}
+
+cudaError_t launch_hybrid_prepare(const DevHybrid& m, bool bf16, cudaStream_t s) {
+#define X(H)                                                                      \
+  if (m.hidden == H) {                                                            \
+    if (bf16) k_hybrid_prepare<H, true><<<8, 256, 0, s>>>(m, m.ws);               \
+    else k_hybrid_prepare<H, false><<<8, 256, 0, s>>>(m, m.ws);                   \
+    return cudaGetLastError();                                                    \
+  }
+  NDGI_HYBRID_HIDDEN(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+template <typename K>
+static cudaError_t launch_tc_kernel(K kern, uint32_t smem, int grid, cudaStream_t s, void** args) {
+  cudaError_t e = set_smem(kern, tc_smem(smem));
+  if (e != cudaSuccess) return e;
+  return cudaLaunchKernel((const void*)kern, dim3(grid), dim3(kLaneThreads * kHybLanes), args, tc_smem(smem), s);
+}
+
+// prec: 0 FP32, 1 FP16, 2 BF16.
+cudaError_t launch_hybrid_points(const DevHybrid& m, int prec, const float* uvt, int64_t n, float* rgb,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+#define X(H)                                                                                            \
+  if (m.hidden == H) {                                                                                  \
+    if (prec == 0) {                                                                                    \
+      const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);                \
+      k_hybrid_points_f32<H><<<grid, 256, 0, s>>>(m, uvt, n, rgb);                                      \
+      return cudaGetLastError();                                                                        \
+    }                                                                                                   \
+    const int grid = (int)std::min<int64_t>(((n + 127) / 128 + kHybLanes - 1) / kHybLanes, num_sms()); \
+    DevHybrid mm = m;                                                                                   \
+    const float* a1 = uvt;                                                                              \
+    int64_t a2 = n;                                                                                     \
+    float* a3 = rgb;                                                                                    \
+    void* args[] = {&mm, &a1, &a2, &a3};                                                                \
+    return launch_tc_kernel(prec == 2 ? k_hybrid_points_tc<H, true> : k_hybrid_points_tc<H, false>,     \
+                            HybridSmem<H>::kBytes, grid, s, args);                                      \
+  }
+  NDGI_HYBRID_HIDDEN(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_hybrid_pages(const HybridPagesCtx& c, int hidden, int prec, const ndgi_page_req* reqs, int n,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+#define X(H)                                                                                       \
+  if (hidden == H) {                                                                               \
+    if (prec == 0) {                                                                               \
+      const int grid = std::min(n, num_sms() * 8);                                                 \
+      k_hybrid_pages_f32<H><<<grid, 256, 0, s>>>(c, reqs, n);                                      \
+      return cudaGetLastError();                                                                   \
+    }                                                                                              \
+    HybridPagesCtx cc = c;                                                                         \
+    const ndgi_page_req* a1 = reqs;                                                                \
+    int a2 = n;                                                                                    \
+    void* args[] = {&cc, &a1, &a2};                                                                \
+    return launch_tc_kernel(prec == 2 ? k_hybrid_pages_tc<H, true> : k_hybrid_pages_tc<H, false>,  \
+                            HybridSmem<H>::kBytes, std::min(n, num_sms()), s, args);               \
+  }
+  NDGI_HYBRID_HIDDEN(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ndgi
+
+// ---------------------------------------------------------------------------
+// C ABI (include/ndgi.h, hybrid feature map decoder)
+// ---------------------------------------------------------------------------
+using ndgi::DevHybrid;
+using ndgi::HybridPagesCtx;
+using ndgi::set_error;
+using ndgi::cuda_status;
+
+struct ndgi_hybrid_table {
+  DevHybrid* d_models = nullptr;   // device copy of the descriptors
+  int* d_words = nullptr;          // device: error word, debug word
+  int n_models = 0, hidden = 0, prec = 0;
+};
+
+namespace {
+
+bool is_aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// The dimension checks shared by every hybrid call (device pointers unchecked).
+ndgi_status check_hybrid_dims(const ndgi_hybrid_desc* m, const char* who) {
+  if (!m) return set_error(NDGI_ERR_INVALID_ARG, "%s: model is NULL", who);
+  if (m->lm_w <= 0 || m->lm_h <= 0) return set_error(NDGI_ERR_INVALID_ARG, "%s: lightmap size must be > 0", who);
+  if (m->uv_w <= 0 || m->uv_h <= 0 || m->uv_w % 4 || m->uv_h % 4 || m->vol_w <= 0 || m->vol_h <= 0 ||
+      m->vol_w % 4 || m->vol_h % 4 || m->vol_t <= 0)
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: F_uv and F3D slice sizes must be positive multiples of 4", who);
+  if (m->ut_w <= 0 || m->ut_t <= 0 || m->vt_h <= 0 || m->vt_t <= 0)
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: F_ut / F_vt sizes must be > 0", who);
+  if ((int64_t)m->uv_w * m->uv_h > ((int64_t)1 << 30) || (int64_t)m->vol_w * m->vol_h * m->vol_t > ((int64_t)1 << 30) ||
+      (int64_t)m->ut_w * m->ut_t > ((int64_t)1 << 28) || (int64_t)m->vt_h * m->vt_t > ((int64_t)1 << 28))
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: a feature map is too large", who);
+  if (!ndgi::hybrid_hidden_ok(m->hidden))
+    return set_error(NDGI_ERR_UNSUPPORTED, "%s: hidden width %d not built (16, 32, 64)", who, m->hidden);
+  if (m->address_mode != 0 && m->address_mode != 1)
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: address_mode must be 0 or 1", who);
+  return NDGI_OK;
+}
+
+ndgi_status check_hybrid(const ndgi_hybrid_desc* m, const char* who) {
+  ndgi_status st = check_hybrid_dims(m, who);
+  if (st != NDGI_OK) return st;
+  if (!m->uv_bc4 || !m->vol_bc4 || !m->ut || !m->vt || !m->w1 || !m->b1 || !m->w2 || !m->b2 || !m->w3 || !m->b3)
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: a model array is NULL", who);
+  if (!is_aligned(m->uv_bc4, 16) || !is_aligned(m->vol_bc4, 16) || !is_aligned(m->ut, 2) || !is_aligned(m->vt, 2))
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: BC4 arrays must be 16-byte and UNORM8 planes 2-byte aligned", who);
+  return NDGI_OK;
+}
+
+DevHybrid to_dev_hybrid(const ndgi_hybrid_desc& d, const void* ws) {
+  DevHybrid m;
+  m.lm_w = d.lm_w;
+  m.lm_h = d.lm_h;
+  m.uv_w = d.uv_w;
+  m.uv_h = d.uv_h;
+  m.uv = d.uv_bc4;
+  m.vol_w = d.vol_w;
+  m.vol_h = d.vol_h;
+  m.vol_t = d.vol_t;
+  m.vol = d.vol_bc4;
+  m.ut_w = d.ut_w;
+  m.ut_t = d.ut_t;
+  m.ut = d.ut;
+  m.vt_h = d.vt_h;
+  m.vt_t = d.vt_t;
+  m.vt = d.vt;
+  m.hidden = d.hidden;
+  m.w1 = d.w1;
+  m.b1 = d.b1;
+  m.w2 = d.w2;
+  m.b2 = d.b2;
+  m.w3 = d.w3;
+  m.b3 = d.b3;
+  m.address_mode = d.address_mode;
+  m.ws = static_cast<unsigned char*>(const_cast<void*>(ws));
+  return m;
+}
+
+// 0 FP32, 1 FP16, 2 BF16, -1 not supported by the hybrid decode.
+int hybrid_prec(ndgi_precision p) { return p == NDGI_FP32 ? 0 : p == NDGI_FP16 ? 1 : p == NDGI_BF16 ? 2 : -1; }
+
+}  // namespace
+
+extern "C" {
+
+size_t ndgi_hybrid_workspace_size(const ndgi_hybrid_desc* model, ndgi_precision precision) {
+  if (check_hybrid_dims(model, "ndgi_hybrid_workspace_size") != NDGI_OK) return 0;
+  const int p = hybrid_prec(precision);
+  return p > 0 ? ndgi::hybrid_ws_bytes(model->hidden) : 0;
+}
+
+ndgi_status ndgi_hybrid_prepare(const ndgi_hybrid_desc* model, ndgi_precision precision, void* ws, void* stream) {
+  ndgi_status st = check_hybrid(model, "ndgi_hybrid_prepare");
+  if (st != NDGI_OK) return st;
+  const int p = hybrid_prec(precision);
+  if (p < 0) return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_hybrid_prepare: precision not built for hybrid models");
+  if (p == 0) return NDGI_OK;
+  if (!ws || !is_aligned(ws, 256))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_prepare: ws is NULL or not 256-byte aligned");
+  return cuda_status(ndgi::launch_hybrid_prepare(to_dev_hybrid(*model, ws), p == 2, (cudaStream_t)stream),
+                     "ndgi_hybrid_prepare");
+}
+
+ndgi_status ndgi_hybrid_decode_points(const ndgi_hybrid_desc* model, ndgi_precision precision, const void* ws,
+                                      const float* uvt, int64_t n, float* rgb, void* stream) {
+  ndgi_status st = check_hybrid(model, "ndgi_hybrid_decode_points");
+  if (st != NDGI_OK) return st;
+  if (n < 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_points: n < 0");
+  if (n == 0) return NDGI_OK;
+  if (!uvt || !rgb) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_points: uvt or rgb is NULL");
+  if (!is_aligned(uvt, 4) || !is_aligned(rgb, 4))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_points: uvt and rgb must be 4-byte aligned");
+  const int p = hybrid_prec(precision);
+  if (p < 0) return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_hybrid_decode_points: precision not built for hybrid models");
+  if (p > 0 && (!ws || !is_aligned(ws, 256)))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_points: FP16/BF16 need the prepared workspace");
+  return cuda_status(ndgi::launch_hybrid_points(to_dev_hybrid(*model, ws), p, uvt, n, rgb, (cudaStream_t)stream),
+                     "ndgi_hybrid_decode_points");
+}
+
+ndgi_status ndgi_hybrid_workspace_check(const ndgi_hybrid_desc* model, ndgi_precision precision, const void* ws,
+                                        int32_t* device_error, void* stream) {
+  ndgi_status st = check_hybrid_dims(model, "ndgi_hybrid_workspace_check");
+  if (st != NDGI_OK) return st;
+  if (hybrid_prec(precision) <= 0 || !ws)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_workspace_check: needs an FP16/BF16 workspace");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_status(e, "ndgi_hybrid_workspace_check");
+  int word = 0;
+  unsigned char* w = static_cast<unsigned char*>(const_cast<void*>(ws)) + ndgi::hybrid_err_offset(model->hidden);
+  e = cudaMemcpy(&word, w, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word != 0) e = cudaMemset(w, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_status(e, "ndgi_hybrid_workspace_check");
+  if (device_error) *device_error = word;
+  if (word & ndgi::kErrTimeout) return set_error(NDGI_ERR_TIMEOUT, "ndgi_hybrid_workspace_check: a wait timed out");
+  return NDGI_OK;
+}
+
+ndgi_status ndgi_hybrid_debug_inject(const ndgi_hybrid_desc* model, ndgi_precision precision, void* ws,
+                                     ndgi_hybrid_table* table, int32_t flags, void* stream) {
+  if (ws) {
+    ndgi_status st = check_hybrid_dims(model, "ndgi_hybrid_debug_inject");
+    if (st != NDGI_OK) return st;
+    if (hybrid_prec(precision) <= 0)
+      return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_debug_inject: needs an FP16/BF16 workspace");
+    const int off = ndgi::hybrid_err_offset(model->hidden) + 4;
+    cudaError_t e = cudaMemcpyAsync(static_cast<unsigned char*>(ws) + off, &flags, sizeof(int),
+                                    cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e, "ndgi_hybrid_debug_inject");
+  }
+  if (table) {
+    cudaError_t e = cudaMemcpy(table->d_words + 1, &flags, sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_status(e, "ndgi_hybrid_debug_inject");
+  }
+  return NDGI_OK;
+}
+
+ndgi_status ndgi_hybrid_table_create(const ndgi_hybrid_desc* models, const void* const* ws, int32_t n_models,
+                                     ndgi_precision precision, ndgi_hybrid_table** out) {
+  if (!out) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_table_create: out is NULL");
+  *out = nullptr;
+  if (!models || n_models <= 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_table_create: no models");
+  const int p = hybrid_prec(precision);
+  if (p < 0) return set_error(NDGI_ERR_UNSUPPORTED, "ndgi_hybrid_table_create: precision not built for hybrid models");
+  std::vector<DevHybrid> h(n_models);
+  for (int i = 0; i < n_models; ++i) {
+    ndgi_status st = check_hybrid(&models[i], "ndgi_hybrid_table_create");
+    if (st != NDGI_OK) return st;
+    if (models[i].hidden != models[0].hidden)
+      return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_table_create: models differ in hidden width");
+    const void* w = nullptr;
+    if (p > 0) {
+      if (!ws || !ws[i] || !is_aligned(ws[i], 256))
+        return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_table_create: model %d has no prepared workspace", i);
+      w = ws[i];
+    }
+    h[i] = to_dev_hybrid(models[i], w);
+  }
+  auto* t = new ndgi_hybrid_table;
+  t->n_models = n_models;
+  t->hidden = models[0].hidden;
+  t->prec = p;
+  cudaError_t e = cudaMalloc(&t->d_models, sizeof(DevHybrid) * n_models);
+  if (e == cudaSuccess) e = cudaMalloc(&t->d_words, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(t->d_models, h.data(), sizeof(DevHybrid) * n_models, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(t->d_words, 0, 2 * sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(t->d_models);
+    cudaFree(t->d_words);
+    delete t;
+    return cuda_status(e, "ndgi_hybrid_table_create");
+  }
+  *out = t;
+  return NDGI_OK;
+}
+
+ndgi_status ndgi_hybrid_table_destroy(ndgi_hybrid_table* table) {
+  if (!table) return NDGI_OK;
+  cudaFree(table->d_models);
+  cudaFree(table->d_words);
+  delete table;
+  return NDGI_OK;
+}
+
+ndgi_status ndgi_hybrid_decode_pages(ndgi_hybrid_table* table, const ndgi_page_req* reqs, int32_t n, void* phys,
+                                     int64_t phys_w, int64_t phys_h, ndgi_out_format format, void* stream) {
+  if (!table) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: table is NULL");
+  if (n < 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: n < 0");
+  if (n == 0) return NDGI_OK;
+  if (!reqs || !phys) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: reqs or phys is NULL");
+  if (phys_w <= 0 || phys_h <= 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: empty phys");
+  if (format != NDGI_RGBA32F && format != NDGI_RGBA16F)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: unknown output format");
+  if (!is_aligned(phys, format == NDGI_RGBA32F ? 16 : 8) || !is_aligned(reqs, 4))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: phys or reqs misaligned");
+  HybridPagesCtx c;
+  c.models = table->d_models;
+  c.n_models = table->n_models;
+  c.phys = phys;
+  c.phys_w = phys_w;
+  c.phys_h = phys_h;
+  c.fmt = (int)format;
+  c.error_word = table->d_words;
+  c.debug_word = table->d_words + 1;
+  return cuda_status(ndgi::launch_hybrid_pages(c, table->hidden, table->prec, reqs, n, (cudaStream_t)stream),
+                     "ndgi_hybrid_decode_pages");
+}
+
+ndgi_status ndgi_hybrid_table_check(ndgi_hybrid_table* table, int32_t* device_error, void* stream) {
+  if (!table) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_table_check: table is NULL");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  int word = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&word, table->d_words, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word != 0) e = cudaMemset(table->d_words, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_status(e, "ndgi_hybrid_table_check");
+  if (device_error) *device_error = word;
+  if (word & ndgi::kErrTimeout) return set_error(NDGI_ERR_TIMEOUT, "ndgi_hybrid_table_check: a wait timed out");
+  if (word) return set_error(NDGI_ERR_DEVICE_CHECK, "ndgi_hybrid_table_check: a request was rejected (0x%x)", word);
+  return NDGI_OK;
+}
+
+double ndgi_model_bpp(const ndgi_hybrid_desc* model, int32_t n_lightmaps, int32_t bc_bits_per_texel,
+                      int32_t mlp_bits) {
+  if (!model || n_lightmaps <= 0 || bc_bits_per_texel <= 0 || mlp_bits <= 0) return -1.0;
+  if (model->lm_w <= 0 || model->lm_h <= 0 || model->uv_w <= 0 || model->uv_h <= 0 || model->vol_w <= 0 ||
+      model->vol_h <= 0 || model->vol_t <= 0 || model->ut_w <= 0 || model->ut_t <= 0 || model->vt_h <= 0 ||
+      model->vt_t <= 0 || model->hidden <= 0)
+    return -1.0;
+  const double H = model->hidden;
+  const double bc_texels = (double)model->uv_w * model->uv_h + (double)model->vol_w * model->vol_h * model->vol_t;
+  const double u8_values = 2.0 * model->ut_w * model->ut_t + 2.0 * model->vt_h * model->vt_t;
+  const double params = (16.0 * H + H) + (H * H + H) + (3.0 * H + 3.0);
+  const double bits = bc_texels * bc_bits_per_texel + u8_values * 8.0 + params * mlp_bits;
+  return bits / ((double)model->lm_w * model->lm_h * n_lightmaps);
+}
+
+}  // extern "C"

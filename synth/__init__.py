@@ -291,3 +291,22 @@ def hybrid_tile_requests(seed, n_tiles, n_req, slots_x=64, page=128):
     for i in range(n_req):
         req[i] = (int(tiles[i]), 0, 0, page, page, ts[i], (i % slots_x) * page, (i // slots_x) * page)
     return req
+
+
+def hybrid_tile_set(seed, n_tiles, profile="M.64"):
+    """n_tiles tile models of one profile, stacked along a leading axis (model i
+    is hybrid_tile_model(seed * 100003 + i, profile)); see hybrid_tile_of."""
+    ms = [hybrid_tile_model(seed * 100003 + i, profile) for i in range(n_tiles)]
+    out = {k: np.stack([m[k] for m in ms]) for k in ("uv_bc4", "vol_bc4", "ut", "vt", "w1", "b1", "w2", "b2",
+                                                    "w3", "b3")}
+    out.update({k: ms[0][k] for k in ("kind", "lm_w", "lm_h", "uv_w", "uv_h", "vol_shape", "hidden",
+                                      "address_mode")})
+    out["n_tiles"] = n_tiles
+    return out
+
+
+def hybrid_tile_of(s, i):
+    """Model i of a hybrid_tile_set as a single-model dict."""
+    m = {k: s[k][i] for k in ("uv_bc4", "vol_bc4", "ut", "vt", "w1", "b1", "w2", "b2", "w3", "b3")}
+    m.update({k: s[k] for k in ("kind", "lm_w", "lm_h", "uv_w", "uv_h", "vol_shape", "hidden", "address_mode")})
+    return m
