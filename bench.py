@@ -42,11 +42,11 @@ METRIC = "Gtexels/s decoded (BC fetch+temporal lerp+MLP), FP16-TC vs FP32 plain 
 # the ones captured: the hash below is compared at run time and the figure drops to null once they change.
 TRAFFIC_SOURCES = ("tc_decode.cu", "tc_points.cu", "tc_engine.cuh", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h")
 NCU_TRAFFIC = {
-    "k_points_tc": {"src": "295f8b14bfbe4b34", "read": 111222272, "write": 44345344, "units": 1 << 23,
-                    "profile": "profiles/k_points_tc_points_2048_atlas.md"},
-    "k_pages_tc": {"src": "295f8b14bfbe4b34", "read": 19536384, "write": 76227584, "units": 1024 * 128 * 128,
+    "k_points_ws": {"src": "bd4dd243d8b953d9", "read": 134403328, "write": 81934080, "units": 1 << 23,
+                    "profile": "profiles/k_points_ws_points_2048_atlas.md"},
+    "k_pages_tc": {"src": "bd4dd243d8b953d9", "read": 19511808, "write": 75702016, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_tc_pages_8_lightmaps.md"},
-    "k_pages_ws": {"src": "295f8b14bfbe4b34", "read": 19198464, "write": 75885056, "units": 1024 * 128 * 128,
+    "k_pages_ws": {"src": "bd4dd243d8b953d9", "read": 19168000, "write": 76241152, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_ws_pages_8_lightmaps.md"},
 }
 

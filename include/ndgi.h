@@ -646,6 +646,14 @@ ndgi_status ndgi_hybrid_debug_inject(const ndgi_hybrid_desc *model, ndgi_precisi
 ndgi_status ndgi_hybrid_table_check(ndgi_hybrid_table *table, int32_t *device_error, void *stream);
 
 /*
+ * Test hook: y[i] = GELU(x[i]) on the device (x, y: n FP32, device) as the
+ * FP32 decodes evaluate it (fast = 0: CUDA's erff) or as the tensor-core
+ * epilogues do (fast = 1: the erfc form of Abramowitz & Stegun 7.1.28, one
+ * approximate reciprocal; |error| <= 2e-6 (1 + |x|)).
+ */
+ndgi_status ndgi_debug_gelu(const float *x, int64_t n, float *y, int32_t fast, void *stream);
+
+/*
  * Storage of a hybrid model in bits per lightmap texel, the paper's accounting
  * (Table "compression" and Table "config"): the BC-compressed maps F_uv and
  * F3D at bc_bits_per_texel bits per texel of all four channels (8 for BC7,

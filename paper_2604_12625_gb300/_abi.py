@@ -106,6 +106,7 @@ SIGNATURES = [
     ("ndgi_hybrid_table_destroy", C.c_int, [_vp]),
     ("ndgi_hybrid_decode_pages", C.c_int, [_vp, _vp, _i32, _vp, _i64, _i64, C.c_int, _vp]),
     ("ndgi_hybrid_table_check", C.c_int, [_vp, _vp, _vp]),
+    ("ndgi_debug_gelu", C.c_int, [_vp, _i64, _vp, _i32, _vp]),
     ("ndgi_model_bpp", C.c_double, [_vp, _i32, _i32, _i32]),
 ]
 

@@ -618,3 +618,11 @@ def ndgi_model_bpp(desc, n_lightmaps, bc_bits_per_texel=8, mlp_bits=16):
     """Bits per lightmap texel of a hybrid model's storage (host only; desc an A.HybridDesc or HybridModel)."""
     d = desc.desc if isinstance(desc, HybridModel) else desc
     return float(lib().ndgi_model_bpp(C.byref(d), int(n_lightmaps), int(bc_bits_per_texel), int(mlp_bits)))
+
+
+def ndgi_debug_gelu(x, fast=True, stream=None):
+    """GELU of a float32 CUDA tensor as the tensor-core epilogues (fast) or the FP32 decodes evaluate it."""
+    _need(x, torch.float32, "x")
+    y = torch.empty_like(x)
+    check(lib().ndgi_debug_gelu(_p(x), x.numel(), _p(y), int(bool(fast)), _stream(stream)))
+    return y

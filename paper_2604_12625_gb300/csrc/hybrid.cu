@@ -25,6 +25,35 @@
 
 namespace ndgi {
 
+// GELU(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2, the exact form, with the
+// CUDA math library's erff (the FP32 decodes).
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+// The same for the tensor-core epilogues, whose results are rounded to
+// FP16/BF16 right after: Phi from the complementary-error-function form of
+// Abramowitz & Stegun 7.1.28, erf(z) = 1 - (1 + a1 z + ... + a6 z^6)^-16 for
+// z >= 0 with |error| <= 3e-7.  Then 1 - Phi(|x|) = erfc(z) / 2 =
+// (2^(1/16) P(z))^-16, z = |x| / sqrt 2, so the 2^(1/16) goes into the
+// coefficients and the rest is one approximate reciprocal and four squarings;
+// GELU(x) = x - x erfc/2 for x >= 0 and x erfc/2 below.
+__device__ __forceinline__ float gelu_fast(float x) {
+  constexpr float k = 1.0442737824274138f;   // 2^(1/16)
+  const float z = fabsf(x) * 0.70710678118654752f;
+  float p = fmaf(k * 0.0000430638f, z, k * 0.0002765672f);
+  p = fmaf(p, z, k * 0.0001520143f);
+  p = fmaf(p, z, k * 0.0092705272f);
+  p = fmaf(p, z, k * 0.0422820123f);
+  p = fmaf(p, z, k * 0.0705230784f);
+  p = fmaf(p, z, k);
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+  r *= r;
+  r *= r;
+  r *= r;
+  r *= r;   // erfc(z) / 2
+  return x >= 0.0f ? fmaf(-x, r, x) : x * r;
+}
+
 // ---------------------------------------------------------------------------
 // Feature gather (FP32)
 // ---------------------------------------------------------------------------
@@ -225,12 +254,27 @@ __global__ void __launch_bounds__(256) k_hybrid_pages_f32(HybridPagesCtx c, cons
 template <int H>
 using HybridLayout = TcLayout<16, 0, H>;
 
+// One column (u) or row (v) of a page request: its F3D and F_uv taps and
+// fractions along that axis, and its V_ut (columns) or V_vt (rows).
+struct HybAxis {
+  int v0, v1;   // F3D taps
+  float vf;
+  int u0, u1;   // F_uv taps
+  float uf;
+  float p0, p1;
+};
+constexpr int kHybVolSide = 48;   // largest F3D footprint side staged in shared memory
+
 template <int H>
 struct HybridSmem {
   using L = HybridLayout<H>;
   static constexpr uint32_t kW = 0;                    // B2, B3
   static constexpr uint32_t kB1 = L::kShared;          // B1
-  static constexpr uint32_t kBytes = kB1 + H * L::K1P * 2;
+  static constexpr uint32_t kPoints = kB1 + H * L::K1P * 2;   // end of the point kernel's part
+  static constexpr uint32_t kCols = (kPoints + 15) / 16 * 16;  // pages: HybAxis [128] per column
+  static constexpr uint32_t kRows = kCols + 128 * sizeof(HybAxis);
+  static constexpr uint32_t kVol = kRows + 128 * sizeof(HybAxis);   // float4 [footprint] of F3D at t
+  static constexpr uint32_t kPages = kVol + kHybVolSide * kHybVolSide * 16;
 };
 
 constexpr int kHybLanes = 4;
@@ -270,6 +314,32 @@ __device__ __forceinline__ void hybrid_pack_a1(const float (&x)[16], uint32_t (&
   for (int k = 9; k < 16; ++k) w[k] = 0u;
 }
 
+// Slot s of a lane's engine: this thread's layer-1/2 accumulator row -> GELU ->
+// FP16/BF16 -> the hidden A tile, 16 columns at a time; with ONES also the
+// ones column that carries the next layer's bias (the engine's ReLU epilogue
+// with GELU in its place).
+template <bool ONES, typename E>
+__device__ __forceinline__ void epilogue_gelu(E& e, int s) {
+  static_assert(!E::F8 && E::kACol % 16 == 0, "16-column FP16/BF16 epilogue");
+  constexpr int H = (int)E::kACol;
+  const uint32_t d = e.tmem[s] + e.lane_off, a = d + E::kACol;
+#pragma unroll
+  for (int c = 0; c < H; c += 16) {
+    uint32_t r[16], w[8];
+    tmem_ld16(d + c, r);
+    tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      w[j] = pack2<E::BF16>(gelu_fast(__uint_as_float(r[2 * j])), gelu_fast(__uint_as_float(r[2 * j + 1])));
+    tmem_st8(a + c / 2, w);
+  }
+  if constexpr (ONES) {
+    const uint32_t one = E::BF16 ? 0x3F80u : 0x3C00u;
+    const uint32_t ow[8] = {one, 0, 0, 0, 0, 0, 0, 0};
+    tmem_st8(a + H / 2, ow);
+  }
+}
+
 // One lane's tiles first, first + step, ... (< tiles) through the three
 // layers, software-pipelined: the next tile's gather runs while this tile's
 // layer 2 is on the tensor core, and its layer 1 is issued with this tile's
@@ -295,7 +365,7 @@ __device__ __forceinline__ bool hybrid_lane_run(E& e, int64_t first, int64_t ste
       e.output(0, y0, y1, y2);   // D3 is read before the layer-2 rows overwrite its columns
       emit(prev, y0, y1, y2);
     }
-    e.template epilogue_gelu<true>(0);
+    epilogue_gelu<true>(e, 0);
     if (!e.layer2(0)) return false;
     inflight = true;
     const bool more = next < tiles;
@@ -305,7 +375,7 @@ __device__ __forceinline__ bool hybrid_lane_run(E& e, int64_t first, int64_t ste
       e.write_a1(0, w);
     }
     inflight = !e.wait(0);   // layer 2
-    e.template epilogue_gelu<false>(0);
+    epilogue_gelu<false>(e, 0);
     if (!e.layer3(0, more)) return false;
     inflight = true;
     if (!more) break;
@@ -371,8 +441,33 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
   cta_teardown<kHybLanes, E::kSlotCols, E, 1>(tbase, e, inflight, !ok, tid, err);
 }
 
-// Pages: one request per CTA at a time; its model's image is staged in shared
-// memory, then the four lanes take the request's 128-texel tiles in turn
+// F3D texel (x, y) of slices z0 and z1 blended at fz, all four channels.
+__device__ __forceinline__ float4 vol_texel(const DevHybrid& m, int x, int y, int z0, int z1, float fz,
+                                            const uint2* lut) {
+  const size_t slice = (size_t)(m.vol_h / 4) * (size_t)(m.vol_w / 4) * 32;
+  const size_t off = ((size_t)(y >> 2) * (m.vol_w / 4) + (x >> 2)) * 32;
+  const uint32_t shift = 16u + 3u * (uint32_t)(((y & 3) << 2) | (x & 3));
+  const uint4* la = reinterpret_cast<const uint4*>(m.vol + (size_t)z0 * slice + off);
+  const uint4* lb = reinterpret_cast<const uint4*>(m.vol + (size_t)z1 * slice + off);
+  const uint4 a0 = __ldg(la), a1 = __ldg(la + 1), b0 = __ldg(lb), b1 = __ldg(lb + 1);
+  const float gz = 1.0f - fz;
+  float4 v;
+  v.x = gz * p35_value(bc4_p35_lut(a0.x, a0.y, shift, lut)) + fz * p35_value(bc4_p35_lut(b0.x, b0.y, shift, lut));
+  v.y = gz * p35_value(bc4_p35_lut(a0.z, a0.w, shift, lut)) + fz * p35_value(bc4_p35_lut(b0.z, b0.w, shift, lut));
+  v.z = gz * p35_value(bc4_p35_lut(a1.x, a1.y, shift, lut)) + fz * p35_value(bc4_p35_lut(b1.x, b1.y, shift, lut));
+  v.w = gz * p35_value(bc4_p35_lut(a1.z, a1.w, shift, lut)) + fz * p35_value(bc4_p35_lut(b1.z, b1.w, shift, lut));
+  return v;
+}
+
+// Pages: one request per CTA at a time.  Per request the CTA stages its
+// model's image in shared memory and, once for the whole page, everything
+// that depends on one axis only: per column the F3D and F_uv taps along u and
+// V_ut, per row the same along v and V_vt, gamma(t), and (when the page's F3D
+// footprint is at most 48 x 48 texels) the F3D texels it touches, already
+// blended between the two slices around t.  A texel then costs one bilinear
+// step over staged F3D values and one BC4 bilinear sample of F_uv (one tap
+// where both fractions are zero, as at texel centres of an F_uv of the
+// lightmap's size).  The four lanes take the page's 128-texel tiles in turn
 // (texel k of the request is (k mod w, k div w)).
 template <int H, bool BF16>
 __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
@@ -386,7 +481,11 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
   __shared__ uint64_t bars[kHybLanes];
   __shared__ uint32_t slot;
   __shared__ uint2 lut[16];
-  __shared__ float s_b3[3];
+  __shared__ float s_b3[3], s_gamma[4], s_fz;
+  __shared__ int s_z[2], s_lo[2], s_hi[2];
+  HybAxis* cols = reinterpret_cast<HybAxis*>(sm + S::kCols);
+  HybAxis* rows = reinterpret_cast<HybAxis*>(sm + S::kRows);
+  float4* vol = reinterpret_cast<float4*>(sm + S::kVol);
   const int tid = threadIdx.x;
   init_p35_lut(lut, tid);
   const uint32_t tbase = cta_setup<kHybLanes, E::kSlotCols>(bars, &slot, tid);
@@ -401,7 +500,7 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
     const ndgi_page_req r = reqs[ri];
     const bool ok = hybrid_req_ok(r, c.models, c.n_models, c.phys_w, c.phys_h);
     tc_fence_before();
-    __syncthreads();   // every lane is done with the previous request's image
+    __syncthreads();   // every lane is done with the previous request's image and tables
     if (!ok) {
       if (tid == 0) atomicOr(c.error_word, 1);
       continue;
@@ -410,6 +509,42 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
     copy16(sm + S::kW, m.ws, L::kShared, tid, blockDim.x);
     copy16(sm + S::kB1, m.ws + L::kB1P, H * L::K1P * 2, tid, blockDim.x);
     if (tid < 3) s_b3[tid] = stored_b3<BF16>(m.ws + L::kB3, tid, H, L::K2);
+    if (tid == 0) {
+      s_lo[0] = s_lo[1] = 0x7fffffff;
+      s_hi[0] = s_hi[1] = -1;
+    }
+    __syncthreads();
+    // ---- per-axis tables, gamma(t) and the F3D slice pair ----
+    const int mode = m.address_mode;
+    if (tid < r.w || (tid >= 128 && tid - 128 < r.h)) {
+      const bool col = tid < 128;
+      const int i = col ? tid : tid - 128;
+      const float coord = col ? ((float)(r.x0 + i) + 0.5f) / (float)m.lm_w : ((float)(r.y0 + i) + 0.5f) / (float)m.lm_h;
+      HybAxis a;
+      axis_setup(coord, col ? m.vol_w : m.vol_h, mode, a.v0, a.v1, a.vf);
+      axis_setup(coord, col ? m.uv_w : m.uv_h, mode, a.u0, a.u1, a.uf);
+      int x0, x1, y0, y1;
+      float fx, fy, pv[2];
+      axis_setup(coord, col ? m.ut_w : m.vt_h, mode, x0, x1, fx);
+      axis_setup(r.t, col ? m.ut_t : m.vt_t, 0, y0, y1, fy);
+      u8x2_bilinear(col ? m.ut : m.vt, col ? m.ut_w : m.vt_h, x0, x1, y0, y1, fx, fy, pv);
+      a.p0 = pv[0];
+      a.p1 = pv[1];
+      (col ? cols : rows)[i] = a;
+      atomicMin(&s_lo[col ? 0 : 1], min(a.v0, a.v1));
+      atomicMax(&s_hi[col ? 0 : 1], max(a.v0, a.v1));
+    } else if (tid == 256) {
+      sincospif(r.t, &s_gamma[0], &s_gamma[1]);
+      sincospif(2.0f * r.t, &s_gamma[2], &s_gamma[3]);
+      axis_setup(r.t, m.vol_t, 0, s_z[0], s_z[1], s_fz);
+    }
+    __syncthreads();
+    const int lx = s_lo[0], ly = s_lo[1], fw = s_hi[0] - lx + 1, fh = s_hi[1] - ly + 1;
+    const bool staged = fw <= kHybVolSide && fh <= kHybVolSide;
+    const int z0 = s_z[0], z1 = s_z[1];
+    const float fz = s_fz;
+    if (staged)
+      for (int i = tid; i < fw * fh; i += blockDim.x) vol[i] = vol_texel(m, lx + i % fw, ly + i / fw, z0, z1, fz, lut);
     fence_async_smem();
     __syncthreads();
     tc_fence_after();
@@ -419,10 +554,42 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
       const int k = (int)tl * 128 + t;
       float x[16];
       if (k < texels) {
-        const int ix = k % r.w, iy = k / r.w;
-        const float u = ((float)(r.x0 + ix) + 0.5f) / (float)m.lm_w;
-        const float v = ((float)(r.y0 + iy) + 0.5f) / (float)m.lm_h;
-        hybrid_features(m, u, v, r.t, x, lut);
+        const HybAxis& cx = cols[k % r.w];
+        const HybAxis& cy = rows[k / r.w];
+        if (staged) {
+          const float4 q00 = vol[(cy.v0 - ly) * fw + (cx.v0 - lx)], q10 = vol[(cy.v0 - ly) * fw + (cx.v1 - lx)];
+          const float4 q01 = vol[(cy.v1 - ly) * fw + (cx.v0 - lx)], q11 = vol[(cy.v1 - ly) * fw + (cx.v1 - lx)];
+          const float gx = 1.0f - cx.vf, gy = 1.0f - cy.vf, fx = cx.vf, fy = cy.vf;
+          x[0] = gy * (gx * q00.x + fx * q10.x) + fy * (gx * q01.x + fx * q11.x);
+          x[1] = gy * (gx * q00.y + fx * q10.y) + fy * (gx * q01.y + fx * q11.y);
+          x[2] = gy * (gx * q00.z + fx * q10.z) + fy * (gx * q01.z + fx * q11.z);
+          x[3] = gy * (gx * q00.w + fx * q10.w) + fy * (gx * q01.w + fx * q11.w);
+        } else {
+          const size_t slice = (size_t)(m.vol_h / 4) * (size_t)(m.vol_w / 4) * 32;
+          float a[4], b[4];
+          bc4x4_bilinear(m.vol + (size_t)z0 * slice, m.vol_w / 4, cx.v0, cx.v1, cy.v0, cy.v1, cx.vf, cy.vf, lut, a);
+          bc4x4_bilinear(m.vol + (size_t)z1 * slice, m.vol_w / 4, cx.v0, cx.v1, cy.v0, cy.v1, cx.vf, cy.vf, lut, b);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) x[j] = (1.0f - fz) * a[j] + fz * b[j];
+        }
+        if (cx.uf == 0.0f && cy.uf == 0.0f) {   // one tap (its weight is 1)
+          const uint4* line = reinterpret_cast<const uint4*>(m.uv + ((size_t)(cy.u0 >> 2) * (m.uv_w / 4) +
+                                                                     (cx.u0 >> 2)) * 32);
+          const uint4 a = __ldg(line), b = __ldg(line + 1);
+          const uint32_t shift = 16u + 3u * (uint32_t)(((cy.u0 & 3) << 2) | (cx.u0 & 3));
+          x[4] = p35_value(bc4_p35_lut(a.x, a.y, shift, lut));
+          x[5] = p35_value(bc4_p35_lut(a.z, a.w, shift, lut));
+          x[6] = p35_value(bc4_p35_lut(b.x, b.y, shift, lut));
+          x[7] = p35_value(bc4_p35_lut(b.z, b.w, shift, lut));
+        } else {
+          bc4x4_bilinear(m.uv, m.uv_w / 4, cx.u0, cx.u1, cy.u0, cy.u1, cx.uf, cy.uf, lut, x + 4);
+        }
+        x[8] = cx.p0;
+        x[9] = cx.p1;
+        x[10] = cy.p0;
+        x[11] = cy.p1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[12 + j] = s_gamma[j];
       } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) x[j] = 0.0f;
@@ -437,6 +604,11 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
     stopped = !hybrid_lane_run(e, e.wg, kHybLanes, (texels + 127) / 128, gather, emit, inflight[0]);
   }
   cta_teardown<kHybLanes, E::kSlotCols, E, 1>(tbase, e, inflight, stopped, tid, c.error_word);
+}
+
+__global__ void k_debug_gelu(const float* __restrict__ x, int64_t n, float* __restrict__ y, int fast) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fast ? gelu_fast(x[i]) : gelu(x[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -502,7 +674,7 @@ cudaError_t launch_hybrid_points(const DevHybrid& m, int prec, const float* uvt,
     float* a3 = rgb;                                                                                    \
     void* args[] = {&mm, &a1, &a2, &a3};                                                                \
     return launch_tc_kernel(prec == 2 ? k_hybrid_points_tc<H, true> : k_hybrid_points_tc<H, false>,     \
-                            HybridSmem<H>::kBytes, grid, s, args);                                      \
+                            HybridSmem<H>::kPoints, grid, s, args);                                     \
   }
   NDGI_HYBRID_HIDDEN(X)
 #undef X
@@ -524,7 +696,7 @@ cudaError_t launch_hybrid_pages(const HybridPagesCtx& c, int hidden, int prec, c
     int a2 = n;                                                                                    \
     void* args[] = {&cc, &a1, &a2};                                                                \
     return launch_tc_kernel(prec == 2 ? k_hybrid_pages_tc<H, true> : k_hybrid_pages_tc<H, false>,  \
-                            HybridSmem<H>::kBytes, std::min(n, num_sms()), s, args);               \
+                            HybridSmem<H>::kPages, std::min(n, num_sms()), s, args);               \
   }
   NDGI_HYBRID_HIDDEN(X)
 #undef X
@@ -771,6 +943,15 @@ ndgi_status ndgi_hybrid_table_check(ndgi_hybrid_table* table, int32_t* device_er
   if (word & ndgi::kErrTimeout) return set_error(NDGI_ERR_TIMEOUT, "ndgi_hybrid_table_check: a wait timed out");
   if (word) return set_error(NDGI_ERR_DEVICE_CHECK, "ndgi_hybrid_table_check: a request was rejected (0x%x)", word);
   return NDGI_OK;
+}
+
+ndgi_status ndgi_debug_gelu(const float* x, int64_t n, float* y, int32_t fast, void* stream) {
+  if (n < 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_debug_gelu: n < 0");
+  if (n == 0) return NDGI_OK;
+  if (!x || !y) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_debug_gelu: x or y is NULL");
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ndgi::num_sms() * 8);
+  ndgi::k_debug_gelu<<<grid, 256, 0, (cudaStream_t)stream>>>(x, n, y, fast);
+  return cuda_status(cudaGetLastError(), "ndgi_debug_gelu");
 }
 
 double ndgi_model_bpp(const ndgi_hybrid_desc* model, int32_t n_lightmaps, int32_t bc_bits_per_texel,

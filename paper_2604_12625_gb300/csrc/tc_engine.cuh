@@ -186,10 +186,6 @@ __device__ __forceinline__ float stored_b3(const unsigned char* b3_img, int n, i
   return __half2float(__ushort_as_half(b));
 }
 
-// GELU(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2, the exact form, with the
-// CUDA math library's erff.
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
-
 // ---------------------------------------------------------------------------
 // tcgen05 helpers specific to this file
 // ---------------------------------------------------------------------------
@@ -421,28 +417,6 @@ struct Engine {
       tmem_ld_wait();
 #pragma unroll
       for (int j = 0; j < 8; ++j) w[j] = pack2_relu<BF16>(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-      tmem_st8(a + c / 2, w);
-    }
-    if constexpr (ONES) {
-      const uint32_t one = BF16 ? 0x3F80u : 0x3C00u;
-      const uint32_t ow[8] = {one, 0, 0, 0, 0, 0, 0, 0};
-      tmem_st8(a + H / 2, ow);
-    }
-  }
-  // The same with GELU in place of ReLU (the hybrid decoder's hidden
-  // activation), 16 columns at a time; FP16/BF16 only.
-  template <bool ONES>
-  __device__ __forceinline__ void epilogue_gelu(int s) {
-    static_assert(!F8 && H % 16 == 0, "16-column FP16/BF16 epilogue");
-    const uint32_t d = tmem[s] + lane_off, a = d + kACol;
-#pragma unroll
-    for (int c = 0; c < H; c += 16) {
-      uint32_t r[16], w[8];
-      tmem_ld16(d + c, r);
-      tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        w[j] = pack2<BF16>(gelu(__uint_as_float(r[2 * j])), gelu(__uint_as_float(r[2 * j + 1])));
       tmem_st8(a + c / 2, w);
     }
     if constexpr (ONES) {

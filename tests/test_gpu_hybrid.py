@@ -219,3 +219,36 @@ def test_full_frame_sampled(ndgi):
     print(f"hybrid full frame, {len(sub)} sampled pages: max|err|/page range = {err:.3e}")
     assert err <= GATE["fp16"]
     table.close()
+
+
+@pytest.mark.parametrize("fast", [False, True])
+def test_gelu_on_device_against_oracle(ndgi, fast):
+    # exact form (erff) within a few FP32 ulps; the epilogue's A&S 7.1.28 form within 2e-6 (1 + |x|)
+    x = np.concatenate([np.linspace(-12, 12, 200_001), [0.0, -0.0, 1e-30, -1e-30, 30.0, -30.0, 1e4, -1e4]])
+    x = x.astype(np.float32)
+    y = ndgi.ndgi_debug_gelu(torch.from_numpy(x).cuda(), fast=fast).cpu().numpy().astype(np.float64)
+    ref = oracle.gelu(x.astype(np.float64))
+    bound = 2e-6 * (1 + np.abs(x)) if fast else 4e-7 * (1 + np.abs(x))
+    err = np.abs(y - ref)
+    print(f"gelu fast={fast}: max |err| / (1 + |x|) = {np.max(err / (1 + np.abs(x))):.3e}")
+    assert np.all(err <= bound)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_pages_unstaged_volume_and_fractional_uv(ndgi, prec):
+    # F3D 256^2 (a page's footprint exceeds the 48^2 staging: the per-texel gather runs) and F_uv at half the
+    # lightmap's resolution (non-zero fractions at texel centres: the full bilinear sample runs)
+    maps = [synth.hybrid_model(100 + i, 128, 128, 64, 64, 256, 256, 12, 64, 24, 64, 24, 64, address_mode=i)
+            for i in range(2)]
+    models = [ndgi.HybridModel.from_arrays(m) for m in maps]
+    table = ndgi.HybridTable(models, prec)
+    reqs = ragged_requests(101, 2, 6, 3)
+    phys = torch.zeros((2 * 128, 3 * 128, 4), dtype=torch.float32, device="cuda")
+    r, _ = ndgi.page_requests_to_device(reqs)
+    table.decode(r, len(reqs), phys)
+    assert table.check() == (0, 0)
+    ref = oracle.hybrid_decode_pages(maps, reqs, 3 * 128, 2 * 128, precision=prec, fill=0.0)
+    err = page_err(phys.cpu().numpy(), ref, reqs)
+    print(f"hybrid pages unstaged {prec}: max|err|/page range = {err:.3e}")
+    assert err <= GATE[prec]
+    table.close()
