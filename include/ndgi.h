@@ -73,6 +73,13 @@ typedef enum {
  *   w1 [cs+ct][hidden], b1 [hidden], w2 [hidden][hidden], b2 [hidden],
  *   w3 [hidden][3], b3 [3]: FP32, row-major [in][out]
  *   address_mode     0 = clamp to edge, 1 = mirrored repeat (spatial axes)
+ *   key_t            NULL: keyframes at t_j = j/t_count; else [t_count] FP32
+ *                    keyframe times 0 <= t_0 < ... < t_(T-1) < 1 (Sec. 3.1:
+ *                    non-uniform, e.g. denser around a light-switch event):
+ *                    t (periodic, period 1) interpolates the two rows of the
+ *                    segment holding it, the last segment running from
+ *                    t_(T-1) to t_0 + 1.  Times that break the order give
+ *                    unspecified (but in-bounds) results.
  */
 typedef struct {
   int32_t lm_w, lm_h;
@@ -84,6 +91,7 @@ typedef struct {
   int32_t hidden;
   const float *w1, *b1, *w2, *b2, *w3, *b3;
   int32_t address_mode;
+  const float *key_t;
 } ndgi_model_desc;
 
 /* Library version string (static storage). */
@@ -395,6 +403,27 @@ ndgi_status ndgi_pages_plan_set_shape(ndgi_pages_plan *plan, int32_t ctas_per_sm
  */
 ndgi_status ndgi_pages_plan_set_debug(ndgi_pages_plan *plan, int32_t flags);
 
+/*
+ * Test hook for the FP8 page decode's rounding accounting (no paper
+ * counterpart).  With dump != NULL (device, 16-byte aligned,
+ * ndgi_pages_fp8_dump_size bytes), later decodes of this FP8 plan with the
+ * 4 x 1 launch shape copy the operands of one tile into dump: the first 2 x 64
+ * texels (rows y0, y0+1, columns x0..x0+63; thread t is texel (t mod 64,
+ * t div 64)) of request number `item` of the frame.  Layout, 32-bit words:
+ *   [128][R], R = 8 + 2H + 2Q + 4, Q = (H + 32) / 4, per texel row t:
+ *     A1 (8 words: the 32 E4M3 codes of the layer-1 row: 16 features in
+ *        units a1, the three ones codes of v1, zeros),
+ *     D1 (H FP32: the layer-1 accumulator, in units a2),
+ *     A2 (Q words: the layer-2 row, H codes then the ones codes),
+ *     D2 (H FP32, units a3), A3 (Q words), D3 (4 FP32: RGB in units out, pad);
+ *   then vt [ct] FP32 (the request's quantised temporal features) and
+ *   b1t [H] (bytes 0..2: the three E4M3 terms of b1' / (a2 v1) per output).
+ * dump = NULL turns it off.  This call and ndgi_pages_plan_set_debug each
+ * set the whole debug state.
+ */
+size_t ndgi_pages_fp8_dump_size(const ndgi_pages_plan *plan);
+ndgi_status ndgi_pages_plan_set_fp8_dump(ndgi_pages_plan *plan, int32_t item, void *dump);
+
 /* Destroys the plan and its device block and graph.  NULL is a no-op. */
 ndgi_status ndgi_pages_plan_destroy(ndgi_pages_plan *plan);
 
@@ -463,6 +492,7 @@ typedef struct {
   int32_t lm_w, lm_h, feat_w, feat_h, cs, t_count, ct, hidden;
   float *ea, *eb, *w, *temporal, *w1, *b1, *w2, *b2, *w3, *b3;
   int32_t address_mode;
+  const float *key_t;           /* keyframe times as in ndgi_model_desc, or NULL */
 } ndgi_fit_params;
 
 /* Gradient buffers shaped like ndgi_fit_params' tensors (FP32, device). */
@@ -647,9 +677,10 @@ ndgi_status ndgi_hybrid_table_check(ndgi_hybrid_table *table, int32_t *device_er
 
 /*
  * Test hook: y[i] = GELU(x[i]) on the device (x, y: n FP32, device) as the
- * FP32 decodes evaluate it (fast = 0: CUDA's erff) or as the tensor-core
- * epilogues do (fast = 1: the erfc form of Abramowitz & Stegun 7.1.28, one
- * approximate reciprocal; |error| <= 2e-6 (1 + |x|)).
+ * FP32 decodes evaluate it (fast = 0: CUDA's erff) or in the erfc form of
+ * Abramowitz & Stegun 7.1.28 with one approximate reciprocal (|error| <=
+ * 2e-6 (1 + |x|)): fast = 1 scalar, fast = 2 the packed FP32-pair form the
+ * tensor-core epilogues use (the same roundings element for element).
  */
 ndgi_status ndgi_debug_gelu(const float *x, int64_t n, float *y, int32_t fast, void *stream);
 
@@ -664,6 +695,27 @@ ndgi_status ndgi_debug_gelu(const float *x, int64_t n, float *y, int32_t fast, v
  */
 double ndgi_model_bpp(const ndgi_hybrid_desc *model, int32_t n_lightmaps, int32_t bc_bits_per_texel,
                       int32_t mlp_bits);
+
+/* ======================================================================
+ * Quality metrics (supplement S4.2)
+ * ====================================================================== */
+
+/*
+ * Tiled, mask-aware PSNR and SSIM of n_maps decoded lightmaps against their
+ * references: pred, ref [n_maps][h][w][channels] FP32 (device); mask
+ * [n_maps][h][w] bytes (device; non-zero = valid texel) or NULL (all valid).
+ * Each map is cut into tile x tile tiles (partial tiles at the right and
+ * bottom keep their own size).  Per tile, over its valid texels: L = max -
+ * min of the reference (all channels); PSNR = 10 log10(L^2 / MSE); SSIM =
+ * Wang et al.'s index with an 11 x 11 Gaussian window (sigma 1.5, weights
+ * normalised, biased covariances), C1 = (0.01 L)^2, C2 = (0.03 L)^2, at every
+ * valid texel whose window lies inside the tile, averaged over those texels
+ * and the channels.  psnr, ssim: [n_maps][ceil(h/tile)][ceil(w/tile)] FP64
+ * (device); a tile with no valid texel (for SSIM: no valid centre) gets NaN,
+ * a tile with zero error PSNR = +inf.  channels 1..4.
+ */
+ndgi_status ndgi_tile_metrics(const float *pred, const float *ref, const uint8_t *mask, int32_t n_maps, int32_t h,
+                              int32_t w, int32_t channels, int32_t tile, double *psnr, double *ssim, void *stream);
 
 #ifdef __cplusplus
 }

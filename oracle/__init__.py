@@ -45,7 +45,7 @@ class _Model(C.Structure):
                 ("cs", C.c_int32), ("bc4", C.c_void_p), ("t_count", C.c_int32), ("ct", C.c_int32),
                 ("temporal", C.c_void_p), ("hidden", C.c_int32),
                 ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
-                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32), ("key_t", C.c_void_p)]
 
 
 class _PageReq(C.Structure):
@@ -58,7 +58,7 @@ class _FitParams(C.Structure):
                 ("cs", C.c_int32), ("t_count", C.c_int32), ("ct", C.c_int32), ("hidden", C.c_int32),
                 ("ea", C.c_void_p), ("eb", C.c_void_p), ("w", C.c_void_p), ("temporal", C.c_void_p),
                 ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
-                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32), ("key_t", C.c_void_p)]
 
 
 class _FitGrads(C.Structure):
@@ -91,7 +91,7 @@ def lib():
             L.om_fit_backward.restype = f64
             L.om_adam.argtypes = [vp, vp, vp, vp, i64, i32, f64, f64, f64, f64, i32]
             L.om_fit_draw.argtypes = [C.c_uint64, i64, i64, i64, i32, i32, vp, vp]
-            L.om_temporal_weights.argtypes = [f64, i32, vp, vp, vp]
+            L.om_temporal_weights.argtypes = [f64, i32, vp, vp, vp, vp]
             L.om_max_hidden.restype = C.c_int
             L.om_e4m3_batch.argtypes = [vp, i64, vp, vp]
             L.om_p2.argtypes = [f64]
@@ -106,6 +106,7 @@ def lib():
             L.om_hybrid_gamma.argtypes = [f64, vp]
             L.om_hybrid_decode_points.argtypes = [vp, vp, i64, vp, vp, C.c_int]
             L.om_hybrid_decode_pages.argtypes = [vp, i32, vp, i32, vp, i64, i64, C.c_int]
+            L.om_tile_metrics.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
             L.om_splitmix64_next.argtypes = [C.c_uint64]
             L.om_splitmix64_next.restype = C.c_uint64
             _lib = L
@@ -147,6 +148,12 @@ def stored_weights(m, precision):
     raise ValueError(precision)
 
 
+def _key_times(m):
+    """Keyframe times of a model or fit dict (FP32 values as FP64), or None for uniform keyframes j/T."""
+    k = m.get("key_t") if isinstance(m, dict) else None
+    return None if k is None else _c(np.asarray(k, np.float32).astype(np.float64), np.float64)
+
+
 class Model:
     """A decodable model (dict from synth.model) held in oracle form."""
 
@@ -156,12 +163,14 @@ class Model:
         assert self.hidden <= lib().om_max_hidden()
         self.bc4 = _c(m["bc4"], np.uint8)
         self.temporal = _c(np.asarray(m["temporal"]).astype(np.float64), np.float64)
+        self.key_t = _key_times(m)
         w = stored_weights(m, precision)
         self.w = {k: _c(v, np.float64) for k, v in w.items()}
         self.s = _Model(int(m["lm_w"]), int(m["lm_h"]), int(m["feat_w"]), int(m["feat_h"]), self.cs,
                         _ptr(self.bc4), int(m["t_count"]), self.ct, _ptr(self.temporal), self.hidden,
                         _ptr(self.w["w1"]), _ptr(self.w["b1"]), _ptr(self.w["w2"]), _ptr(self.w["b2"]),
-                        _ptr(self.w["w3"]), _ptr(self.w["b3"]), int(m.get("address_mode", 0)))
+                        _ptr(self.w["w3"]), _ptr(self.w["b3"]), int(m.get("address_mode", 0)),
+                        _ptr(self.key_t))
 
 
 class _Hybrid(C.Structure):
@@ -386,8 +395,9 @@ class FitParams:
         T, ct = self.a["temporal"].shape
         H = self.a["w2"].shape[0]
         self.dims = dict(lm_w=lm_w, lm_h=lm_h, feat_w=bw * 4, feat_h=bh * 4, cs=cs, t_count=T, ct=ct, hidden=H)
+        self.key_t = _key_times(p)
         self.s = _FitParams(lm_w, lm_h, bw * 4, bh * 4, cs, T, ct, H,
-                            *[_ptr(self.a[k]) for k in FIT_KEYS], int(p.get("address_mode", 0)))
+                            *[_ptr(self.a[k]) for k in FIT_KEYS], int(p.get("address_mode", 0)), _ptr(self.key_t))
 
 
 def fit_forward(params, uvt, lm_w, lm_h, relaxed=False, want_signs=False):
@@ -431,21 +441,39 @@ def fit_draw(seed, step, n, lm_w, lm_h, first=0):
     return texel, uvt
 
 
-def temporal_weights(t, t_count):
-    """(j0, j1, alpha) of time t: keyframes at j / t_count, periodic (the decode's temporal lerp)."""
+def temporal_weights(t, t_count, key_t=None):
+    """(j0, j1, alpha) of time t: keyframes at j / t_count or at the times key_t, periodic (the decode's
+    temporal lerp)."""
     j0, j1, a = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
-    lib().om_temporal_weights(float(t), int(t_count), C.byref(j0), C.byref(j1), C.byref(a))
+    k = None if key_t is None else _c(np.asarray(key_t, np.float32).astype(np.float64), np.float64)
+    lib().om_temporal_weights(float(t), int(t_count), _ptr(k), C.byref(j0), C.byref(j1), C.byref(a))
     return j0.value, j1.value, a.value
 
 
-def fit_targets_at(targets, texel, uvt):
+def fit_targets_at(targets, texel, uvt, key_t=None):
     """Target of each fit sample: the keyframe targets [T][H][W][3] at its texel, interpolated linearly in t
     between the two keyframes around it (the lightmap at time t is the interpolation of its keyframes,
     Eq. 2), in FP64."""
     T = targets.shape[0]
     out = np.zeros((texel.shape[0], 3), np.float64)
     for i in range(texel.shape[0]):
-        j0, j1, a = temporal_weights(float(uvt[i, 2]), T)
+        j0, j1, a = temporal_weights(float(uvt[i, 2]), T, key_t)
         ix, iy = int(texel[i, 0]), int(texel[i, 1])
         out[i] = (1.0 - a) * targets[j0, iy, ix].astype(np.float64) + a * targets[j1, iy, ix].astype(np.float64)
     return out
+
+
+def tile_metrics(pred, ref, mask=None, tile=128):
+    """Per-tile (PSNR, SSIM) of lightmaps [n][h][w][c] (or [h][w][c]) under an optional mask [n][h][w]."""
+    p = _c(pred, np.float64)
+    q = _c(ref, np.float64)
+    if p.ndim == 3:
+        p, q = p[None], q[None]
+        mask = None if mask is None else np.asarray(mask)[None]
+    n, h, w, c = p.shape
+    m = None if mask is None else _c(np.asarray(mask) != 0, np.uint8)
+    ty, tx = (h + tile - 1) // tile, (w + tile - 1) // tile
+    ps = np.zeros((n, ty, tx), np.float64)
+    ss = np.zeros((n, ty, tx), np.float64)
+    lib().om_tile_metrics(_ptr(p), _ptr(q), _ptr(m), n, h, w, c, tile, _ptr(ps), _ptr(ss))
+    return ps, ss

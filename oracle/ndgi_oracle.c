@@ -48,6 +48,7 @@ typedef struct {
   int32_t hidden;                /* MLP: (cs+ct) -> hidden -> hidden -> 3  */
   const double *w1, *b1, *w2, *b2, *w3, *b3; /* [in][out] row-major       */
   int32_t address_mode;          /* 0 clamp, 1 mirrored repeat             */
+  const double *key_t;           /* keyframe times [t_count] or NULL (j/T) */
 } om_model;
 
 typedef struct {
@@ -118,21 +119,40 @@ static void om_bilinear_setup(double coord, int size, int mode, int *t0, int *t1
   *t1 = om_address((int)fl + 1, size, mode);
 }
 
-/* Temporal interpolation setup: keyframes at j/T, periodic in t. */
-static void om_temporal_setup(double t, int T, int *j0, int *j1, double *alpha) {
-  double s = t * (double)T;
-  double fl = floor(s);
-  *alpha = s - fl;
-  long j = (long)fl % T;
-  if (j < 0) j += T;
-  *j0 = (int)j;
-  *j1 = (int)((j + 1) % T);
+/*
+ * Temporal interpolation setup (Eq. 2 applied to the temporal features),
+ * periodic in t with period 1.  Keyframes at t_j = j/T, or, with key_t, at
+ * the given times 0 <= key_t[0] < ... < key_t[T-1] < 1 (Sec. 3.1: the t_i may
+ * be non-uniform, denser around light-switch events): t lies in the segment
+ * [t_j, t_j1) with j1 = (j+1) mod T, the last segment running from
+ * key_t[T-1] to key_t[0] + 1, and alpha is its position in that segment.
+ */
+static void om_temporal_setup(double t, int T, const double *key_t, int *j0, int *j1, double *alpha) {
+  if (!key_t) {
+    double s = t * (double)T;
+    double fl = floor(s);
+    *alpha = s - fl;
+    long j = (long)fl % T;
+    if (j < 0) j += T;
+    *j0 = (int)j;
+    *j1 = (int)((j + 1) % T);
+    return;
+  }
+  double s = t - floor(t);
+  int j = T - 1;
+  for (int i = 0; i + 1 < T; ++i)
+    if (key_t[i] <= s && s < key_t[i + 1]) j = i;
+  double start = key_t[j], end = j + 1 < T ? key_t[j + 1] : key_t[0] + 1.0;
+  if (j == T - 1 && s < key_t[0]) s += 1.0;   /* the wrap segment, past the period's end */
+  *j0 = j;
+  *j1 = (j + 1) % T;
+  *alpha = (s - start) / (end - start);
 }
 
 /* The keyframe segment of t: rows j0, j1 and the lerp weight alpha (exported for the fit's targets). */
-void om_temporal_weights(double t, int32_t T, int32_t *j0, int32_t *j1, double *alpha) {
+void om_temporal_weights(double t, int32_t T, const double *key_t, int32_t *j0, int32_t *j1, double *alpha) {
   int a, b;
-  om_temporal_setup(t, T, &a, &b, alpha);
+  om_temporal_setup(t, T, key_t, &a, &b, alpha);
   *j0 = a;
   *j1 = b;
 }
@@ -164,7 +184,7 @@ void om_features(const om_model *m, double u, double v, double t, double *x, int
   }
   int j0, j1;
   double a;
-  om_temporal_setup(t, m->t_count, &j0, &j1, &a);
+  om_temporal_setup(t, m->t_count, m->key_t, &j0, &j1, &a);
   for (int c = 0; c < m->ct; ++c) {
     double k0 = m->temporal[(size_t)j0 * m->ct + c];
     double k1 = m->temporal[(size_t)j1 * m->ct + c];
@@ -494,6 +514,7 @@ typedef struct {
   const float *temporal;         /* [t_count][ct]                           */
   const float *w1, *b1, *w2, *b2, *w3, *b3;
   int32_t address_mode;
+  const double *key_t;           /* keyframe times [t_count] or NULL (j/T) */
 } om_fit_params;
 
 typedef struct {
@@ -551,7 +572,7 @@ static void om_fit_sample_forward(const om_fit_params *P, double u, double v, do
   }
   int j0, j1;
   double al;
-  om_temporal_setup(t, P->t_count, &j0, &j1, &al);
+  om_temporal_setup(t, P->t_count, P->key_t, &j0, &j1, &al);
   for (int c = 0; c < ct; ++c)
     x[cs + c] = (1.0 - al) * (double)P->temporal[(size_t)j0 * ct + c] + al * (double)P->temporal[(size_t)j1 * ct + c];
   for (int o = 0; o < H; ++o) {
@@ -658,7 +679,7 @@ double om_fit_backward(const om_fit_params *P, const float *uvt, const double *t
     /* v_t = (1 - alpha) K[j0] + alpha K[j1]: the gradient splits between the two rows */
     int j0, j1;
     double al;
-    om_temporal_setup(t, P->t_count, &j0, &j1, &al);
+    om_temporal_setup(t, P->t_count, P->key_t, &j0, &j1, &al);
     for (int c = 0; c < ct; ++c) {
       G->temporal[(size_t)j0 * ct + c] += (1.0 - al) * gx[cs + c];
       G->temporal[(size_t)j1 * ct + c] += al * gx[cs + c];
@@ -877,6 +898,92 @@ void om_hybrid_decode_pages(const om_hybrid *models, int32_t n_models, const om_
         o[1] = rgb[1];
         o[2] = rgb[2];
         o[3] = 1.0;
+      }
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Tiled, mask-aware quality metrics (supplement S4.2)                     */
+/* ---------------------------------------------------------------------- */
+/*
+ * Each lightmap [h][w][c] is cut into non-overlapping tile x tile tiles
+ * (partial tiles at the right and bottom edges keep their own size).  For a
+ * tile, over the texels whose mask is non-zero (mask NULL: all):
+ *   L     = max - min of the reference over those texels and all channels;
+ *   PSNR  = 10 log10(L^2 / MSE), MSE over those texels and all channels;
+ *   SSIM  = the mean over channels and over those texels p of Wang et al.'s
+ *           SSIM(p) = (2 mx my + C1)(2 sxy + C2) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)),
+ *           with Gaussian-weighted means and (biased) covariances over the
+ *           11 x 11 window centred on p (sigma 1.5, weights normalised),
+ *           C1 = (0.01 L)^2, C2 = (0.03 L)^2, for centres whose window lies
+ *           inside the tile.
+ * A tile with no such texel gets NaN; MSE = 0 gives +inf.
+ * Outputs [n_maps][ceil(h/tile)][ceil(w/tile)].
+ */
+void om_tile_metrics(const double *pred, const double *ref, const uint8_t *mask, int32_t n_maps, int32_t h,
+                     int32_t w, int32_t c, int32_t tile, double *psnr, double *ssim) {
+  const int R = 5;
+  double g[11], gs = 0.0;
+  for (int i = 0; i < 11; ++i) {
+    g[i] = exp(-(double)((i - R) * (i - R)) / (2.0 * 1.5 * 1.5));
+    gs += g[i];
+  }
+  for (int i = 0; i < 11; ++i) g[i] /= gs;
+  const int ty_n = (h + tile - 1) / tile, tx_n = (w + tile - 1) / tile;
+  for (int mi = 0; mi < n_maps; ++mi) {
+    const double *P = pred + (size_t)mi * h * w * c, *Q = ref + (size_t)mi * h * w * c;
+    const uint8_t *M = mask ? mask + (size_t)mi * h * w : NULL;
+    for (int ty = 0; ty < ty_n; ++ty) {
+      for (int tx = 0; tx < tx_n; ++tx) {
+        const int y0 = ty * tile, x0 = tx * tile;
+        const int y1 = y0 + tile < h ? y0 + tile : h, x1 = x0 + tile < w ? x0 + tile : w;
+        double lo = INFINITY, hi = -INFINITY, se = 0.0;
+        long cnt = 0;
+        for (int y = y0; y < y1; ++y)
+          for (int x = x0; x < x1; ++x) {
+            if (M && !M[(size_t)y * w + x]) continue;
+            ++cnt;
+            for (int k = 0; k < c; ++k) {
+              const double q = Q[((size_t)y * w + x) * c + k], d = P[((size_t)y * w + x) * c + k] - q;
+              lo = fmin(lo, q);
+              hi = fmax(hi, q);
+              se += d * d;
+            }
+          }
+        const size_t o = ((size_t)mi * ty_n + ty) * tx_n + tx;
+        if (cnt == 0) {
+          psnr[o] = NAN;
+          ssim[o] = NAN;
+          continue;
+        }
+        const double L = hi - lo, mse = se / ((double)cnt * c);
+        psnr[o] = mse > 0.0 ? 10.0 * log10(L * L / mse) : INFINITY;
+        const double C1 = (0.01 * L) * (0.01 * L), C2 = (0.03 * L) * (0.03 * L);
+        double acc = 0.0;
+        long ns = 0;
+        for (int y = y0 + R; y < y1 - R; ++y)
+          for (int x = x0 + R; x < x1 - R; ++x) {
+            if (M && !M[(size_t)y * w + x]) continue;
+            for (int k = 0; k < c; ++k) {
+              double mx = 0, my = 0, sxx = 0, syy = 0, sxy = 0;
+              for (int dy = -R; dy <= R; ++dy)
+                for (int dx = -R; dx <= R; ++dx) {
+                  const double wt = g[dy + R] * g[dx + R];
+                  const size_t e = ((size_t)(y + dy) * w + (x + dx)) * c + k;
+                  const double a = P[e], b = Q[e];
+                  mx += wt * a;
+                  my += wt * b;
+                  sxx += wt * a * a;
+                  syy += wt * b * b;
+                  sxy += wt * a * b;
+                }
+              const double vx = sxx - mx * mx, vy = syy - my * my, cxy = sxy - mx * my;
+              acc += ((2 * mx * my + C1) * (2 * cxy + C2)) / ((mx * mx + my * my + C1) * (vx + vy + C2));
+            }
+            ++ns;
+          }
+        ssim[o] = ns ? acc / ((double)ns * c) : NAN;
       }
     }
   }

@@ -25,7 +25,7 @@ class ModelDesc(C.Structure):
                 ("cs", C.c_int32), ("bc4", C.c_void_p), ("t_count", C.c_int32), ("ct", C.c_int32),
                 ("temporal", C.c_void_p), ("temporal_dtype", C.c_int32), ("hidden", C.c_int32),
                 ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
-                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32), ("key_t", C.c_void_p)]
 
 
 class PageReq(C.Structure):
@@ -48,7 +48,7 @@ FIT_TENSORS = ("ea", "eb", "w", "temporal", "w1", "b1", "w2", "b2", "w3", "b3")
 class FitParams(C.Structure):
     _fields_ = [("lm_w", C.c_int32), ("lm_h", C.c_int32), ("feat_w", C.c_int32), ("feat_h", C.c_int32),
                 ("cs", C.c_int32), ("t_count", C.c_int32), ("ct", C.c_int32), ("hidden", C.c_int32)] + \
-               [(k, C.c_void_p) for k in FIT_TENSORS] + [("address_mode", C.c_int32)]
+               [(k, C.c_void_p) for k in FIT_TENSORS] + [("address_mode", C.c_int32), ("key_t", C.c_void_p)]
 
 
 class FitGrads(C.Structure):
@@ -91,6 +91,8 @@ SIGNATURES = [
     ("ndgi_pages_plan_info", C.c_int, [_vp, _vp]),
     ("ndgi_pages_plan_set_shape", C.c_int, [_vp, _i32, _i32, _i32]),
     ("ndgi_pages_plan_set_debug", C.c_int, [_vp, _i32]),
+    ("ndgi_pages_fp8_dump_size", _sz, [_vp]),
+    ("ndgi_pages_plan_set_fp8_dump", C.c_int, [_vp, _i32, _vp]),
     ("ndgi_decode_pages_static", C.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _i64, _i64, _vp, _vp]),
     ("ndgi_bc_pack", C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     ("ndgi_fit_forward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
@@ -108,6 +110,7 @@ SIGNATURES = [
     ("ndgi_hybrid_table_check", C.c_int, [_vp, _vp, _vp]),
     ("ndgi_debug_gelu", C.c_int, [_vp, _i64, _vp, _i32, _vp]),
     ("ndgi_model_bpp", C.c_double, [_vp, _i32, _i32, _i32]),
+    ("ndgi_tile_metrics", C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp]),
 ]
 
 _lib = None

@@ -43,7 +43,7 @@ class Model:
     are kept per precision in ``self.ws``.
     """
 
-    def __init__(self, lm_w, lm_h, bc4, temporal, w1, b1, w2, b2, w3, b3, address_mode=0):
+    def __init__(self, lm_w, lm_h, bc4, temporal, w1, b1, w2, b2, w3, b3, address_mode=0, key_t=None):
         self.lm_w, self.lm_h = int(lm_w), int(lm_h)
         self.bc4 = _need(bc4, torch.uint8, "bc4")
         bh, bw, cs, eight = bc4.shape
@@ -57,11 +57,12 @@ class Model:
                   dict(w1=w1, b1=b1, w2=w2, b2=b2, w3=w3, b3=b3).items()}
         self.hidden = w2.shape[0]
         self.address_mode = int(address_mode)
+        self.key_t = None if key_t is None else _need(key_t, torch.float32, "key_t")
         self.desc = A.ModelDesc(self.lm_w, self.lm_h, self.feat_w, self.feat_h, self.cs, self.bc4.data_ptr(),
                                 self.t_count, self.ct, self.temporal.data_ptr(),
                                 A.NDGI_FP16 if temporal.dtype == torch.float16 else A.NDGI_FP32, self.hidden,
                                 *[self.w[k].data_ptr() for k in ("w1", "b1", "w2", "b2", "w3", "b3")],
-                                self.address_mode)
+                                self.address_mode, _p(self.key_t))
         self.ws = {}
 
     @classmethod
@@ -69,8 +70,10 @@ class Model:
         """From a dict of numpy arrays (the layout of synth.model)."""
         def t(a):
             return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        key_t = m.get("key_t")
         return cls(m["lm_w"], m["lm_h"], t(m["bc4"]), t(m["temporal"]), t(m["w1"]), t(m["b1"]), t(m["w2"]),
-                   t(m["b2"]), t(m["w3"]), t(m["b3"]), m.get("address_mode", 0))
+                   t(m["b2"]), t(m["w3"]), t(m["b3"]), m.get("address_mode", 0),
+                   None if key_t is None else t(np.asarray(key_t, np.float32)))
 
     def workspace(self, precision):
         precision = _prec(precision)
@@ -319,6 +322,13 @@ class PagesPlan:
         """Test hook: 1 = the tensor-core decodes take their timeout path before any MMA; 0 = normal."""
         check(lib().ndgi_pages_plan_set_debug(self.handle, int(flags)))
 
+    def set_fp8_dump(self, item, dump=None):
+        """Test hook: operands of one tile of request `item` into `dump` (uint8 CUDA tensor; None = off)."""
+        check(lib().ndgi_pages_plan_set_fp8_dump(self.handle, int(item), _p(dump)))
+
+    def fp8_dump_size(self):
+        return int(lib().ndgi_pages_fp8_dump_size(self.handle))
+
     def close(self):
         if self.handle:
             check(lib().ndgi_pages_plan_destroy(self.handle))
@@ -363,20 +373,25 @@ def ndgi_bc_pack(ea, eb, w, out=None, stream=None):
 class FitState:
     """Trainable parameters of the fit (float32 CUDA tensors) and their struct."""
 
-    def __init__(self, tensors, lm_w, lm_h, address_mode=0):
+    def __init__(self, tensors, lm_w, lm_h, address_mode=0, key_t=None):
         self.t = {k: _need(tensors[k], torch.float32, k) for k in A.FIT_TENSORS}
+        self.key_t = None if key_t is None else _need(key_t, torch.float32, "key_t")
         bh, bw, cs = self.t["ea"].shape
         T, ct = self.t["temporal"].shape
         H = self.t["w2"].shape[0]
         self.lm_w, self.lm_h = int(lm_w), int(lm_h)
         self.dims = dict(feat_w=bw * 4, feat_h=bh * 4, cs=cs, t_count=T, ct=ct, hidden=H)
         self.params = A.FitParams(self.lm_w, self.lm_h, bw * 4, bh * 4, cs, T, ct, H,
-                                  *[self.t[k].data_ptr() for k in A.FIT_TENSORS], int(address_mode))
+                                  *[self.t[k].data_ptr() for k in A.FIT_TENSORS], int(address_mode),
+                                  _p(self.key_t))
+        self.address_mode = int(address_mode)
 
     @classmethod
     def from_arrays(cls, p, lm_w, lm_h, device="cuda"):
+        key_t = p.get("key_t")
         return cls({k: torch.from_numpy(np.ascontiguousarray(p[k], np.float32)).to(device) for k in A.FIT_TENSORS},
-                   lm_w, lm_h, p.get("address_mode", 0))
+                   lm_w, lm_h, p.get("address_mode", 0),
+                   None if key_t is None else torch.from_numpy(np.ascontiguousarray(key_t, np.float32)).to(device))
 
     def zeros_like(self):
         return {k: torch.zeros_like(v) for k, v in self.t.items()}
@@ -409,12 +424,14 @@ class NdgiDecodeFunction(torch.autograd.Function):
     BC4 forward of ndgi_fit_forward and the hand-written CUDA backward of
     ndgi_fit_backward (through the MLP, the temporal and bilinear sampling
     and the BC4 quantisation, treated as identity).  Inputs after the four
-    settings are the FIT_TENSORS in order; the queries carry no gradient."""
+    settings and the keyframe times are the FIT_TENSORS in order; the queries
+    carry no gradient."""
 
     @staticmethod
-    def forward(ctx, uvt, relaxed, lm_w, lm_h, address_mode, *tensors):
-        state = FitState(dict(zip(A.FIT_TENSORS, tensors)), lm_w, lm_h, address_mode)
+    def forward(ctx, uvt, relaxed, lm_w, lm_h, address_mode, key_t, *tensors):
+        state = FitState(dict(zip(A.FIT_TENSORS, tensors)), lm_w, lm_h, address_mode, key_t)
         ctx.save_for_backward(uvt, *tensors)
+        ctx.key_t = key_t
         ctx.settings = (bool(relaxed), int(lm_w), int(lm_h), int(address_mode))
         return ndgi_fit_forward(state, uvt, relaxed)
 
@@ -422,16 +439,17 @@ class NdgiDecodeFunction(torch.autograd.Function):
     def backward(ctx, grad_rgb):
         uvt, *tensors = ctx.saved_tensors
         relaxed, lm_w, lm_h, address_mode = ctx.settings
-        state = FitState(dict(zip(A.FIT_TENSORS, tensors)), lm_w, lm_h, address_mode)
+        state = FitState(dict(zip(A.FIT_TENSORS, tensors)), lm_w, lm_h, address_mode, ctx.key_t)
         grads = ndgi_fit_backward(state, uvt, grad_rgb.contiguous(), relaxed=relaxed)
-        return (None, None, None, None, None) + tuple(grads[k] for k in A.FIT_TENSORS)
+        return (None, None, None, None, None, None) + tuple(grads[k] for k in A.FIT_TENSORS)
 
 
-def ndgi_decode_fit(params, uvt, lm_w, lm_h, relaxed=False, address_mode=0):
+def ndgi_decode_fit(params, uvt, lm_w, lm_h, relaxed=False, address_mode=0, key_t=None):
     """rgb [n][3] of the fit's decode at arbitrary queries uvt [n][3] float32 (u, v, t), differentiable
     w.r.t. params (dict of float32 CUDA tensors keyed by FIT_TENSORS), through the temporal interpolation
-    at fractional t as well as the MLP, the bilinear gather and the straight-through BC4 quantisation."""
-    return NdgiDecodeFunction.apply(uvt, relaxed, lm_w, lm_h, address_mode,
+    at fractional t as well as the MLP, the bilinear gather and the straight-through BC4 quantisation.
+    key_t: keyframe times (float32 CUDA tensor [T]) or None for j / T."""
+    return NdgiDecodeFunction.apply(uvt, relaxed, lm_w, lm_h, address_mode, key_t,
                                     *[params[k] for k in A.FIT_TENSORS])
 
 
@@ -620,9 +638,29 @@ def ndgi_model_bpp(desc, n_lightmaps, bc_bits_per_texel=8, mlp_bits=16):
     return float(lib().ndgi_model_bpp(C.byref(d), int(n_lightmaps), int(bc_bits_per_texel), int(mlp_bits)))
 
 
-def ndgi_debug_gelu(x, fast=True, stream=None):
-    """GELU of a float32 CUDA tensor as the tensor-core epilogues (fast) or the FP32 decodes evaluate it."""
+def ndgi_debug_gelu(x, fast=1, stream=None):
+    """GELU of a float32 CUDA tensor: fast = 0 as the FP32 decodes evaluate it (erff), 1 the scalar erfc form,
+    2 the packed-pair form the tensor-core epilogues use."""
     _need(x, torch.float32, "x")
     y = torch.empty_like(x)
-    check(lib().ndgi_debug_gelu(_p(x), x.numel(), _p(y), int(bool(fast)), _stream(stream)))
+    check(lib().ndgi_debug_gelu(_p(x), x.numel(), _p(y), int(fast), _stream(stream)))
     return y
+
+
+def ndgi_tile_metrics(pred, ref, mask=None, tile=128, stream=None):
+    """Per-tile (PSNR, SSIM) FP64 tensors [n][ceil(h/tile)][ceil(w/tile)] of float32 CUDA maps [n][h][w][c]
+    (or [h][w][c]) under an optional uint8/bool mask [n][h][w]."""
+    if pred.dim() == 3:
+        pred, ref = pred[None], ref[None]
+        mask = None if mask is None else mask[None]
+    _need(pred, torch.float32, "pred")
+    _need(ref, torch.float32, "ref")
+    if mask is not None:
+        mask = mask.to(torch.uint8).contiguous()
+    n, h, w, c = pred.shape
+    ty, tx = (h + tile - 1) // tile, (w + tile - 1) // tile
+    ps = torch.empty((n, ty, tx), dtype=torch.float64, device=pred.device)
+    ss = torch.empty_like(ps)
+    check(lib().ndgi_tile_metrics(_p(pred), _p(ref), _p(mask), n, h, w, c, int(tile), _p(ps), _p(ss),
+                                  _stream(stream)))
+    return ps, ss

@@ -558,6 +558,25 @@ ndgi_status ndgi_pages_plan_set_debug(ndgi_pages_plan* plan, int32_t flags) {
                      "ndgi_pages_plan_set_debug");
 }
 
+size_t ndgi_pages_fp8_dump_size(const ndgi_pages_plan* plan) {
+  if (!plan || plan->precision != NDGI_FP8_E4M3) return 0;
+  return sizeof(uint32_t) * ((size_t)kLaneThreadsHost * fp8_dump_row_words(plan->hidden) + plan->ct + plan->hidden);
+}
+
+ndgi_status ndgi_pages_plan_set_fp8_dump(ndgi_pages_plan* plan, int32_t item, void* dump) {
+  if (!plan || plan->precision != NDGI_FP8_E4M3)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_set_fp8_dump: needs an FP8 plan");
+  if (dump && (item < 0 || !aligned(dump, 16)))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_set_fp8_dump: bad item or unaligned buffer");
+  struct {
+    int flags, item;
+    void* ptr;
+  } w = {dump ? kDbgDumpFp8 : 0, dump ? item : -1, dump};
+  static_assert(sizeof(w) == 16, "debug block layout");
+  return cuda_status(cudaMemcpy(const_cast<int*>(plan->ctx.debug_word), &w, sizeof(w), cudaMemcpyHostToDevice),
+                     "ndgi_pages_plan_set_fp8_dump");
+}
+
 ndgi_status ndgi_pages_plan_info(const ndgi_pages_plan* plan, int32_t info[4]) {
   if (!plan || !info) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_pages_plan_info: NULL argument");
   info[0] = plan->precision;

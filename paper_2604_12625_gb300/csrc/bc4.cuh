@@ -132,6 +132,45 @@ __device__ __forceinline__ void temporal_setup(float t, int T, int& j0, int& j1,
   alpha = fr;
 }
 
+// The same with keyframes at given times 0 <= key_t[0] < ... < key_t[T-1] < 1
+// (Sec. 3.1 allows non-uniform times), periodic with period 1: t lies in the
+// segment [key_t[j], key_t[j1]) (the last one runs from key_t[T-1] to
+// key_t[0] + 1) and alpha is its position there.  key_t == nullptr: uniform
+// keyframes j/T (temporal_setup).  The search takes at most log2(T) steps
+// and stays in bounds whatever the times hold.
+__device__ __forceinline__ void temporal_setup_k(float t, int T, const float* key_t, int& j0, int& j1, float& alpha) {
+  if (key_t == nullptr) {
+    temporal_setup(t, T, j0, j1, alpha);
+    return;
+  }
+  float s = __fsub_rn(t, floorf(t));
+  if (!(s >= 0.0f && s < 1.0f)) s = 0.0f;   // not finite, or t just below an integer (s rounds to 1)
+  const float k0 = __ldg(key_t);
+  int j = -1;
+  if (s >= k0) {   // largest j with key_t[j] <= s
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(key_t + mid) <= s) lo = mid;
+      else hi = mid - 1;
+    }
+    j = lo;
+  }
+  float start, end;
+  if (j < 0 || j == T - 1) {   // the wrap segment
+    start = __ldg(key_t + T - 1);
+    end = __fadd_rn(k0, 1.0f);
+    if (j < 0) s = __fadd_rn(s, 1.0f);
+    j = T - 1;
+  } else {
+    start = __ldg(key_t + j);
+    end = __ldg(key_t + j + 1);
+  }
+  j0 = j;
+  j1 = j + 1 == T ? 0 : j + 1;
+  alpha = fminf(fmaxf(__fdiv_rn(__fsub_rn(s, start), __fsub_rn(end, start)), 0.0f), 1.0f);
+}
+
 __device__ __forceinline__ float load_temporal(const void* base, int f16, int idx) {
   if (f16) return __half2float(reinterpret_cast<const __half*>(base)[idx]);
   return reinterpret_cast<const float*>(base)[idx];

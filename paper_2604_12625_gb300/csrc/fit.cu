@@ -29,6 +29,7 @@ constexpr int kFitTile = 128;
 
 struct FitArgs {
   int lm_w, lm_h, feat_w, feat_h, cs, bw, t_count, ct, hidden, address_mode;
+  const float* key_t;           // keyframe times [t_count] or null (j / t_count)
   const float *ea, *eb, *w, *temporal, *w1, *b1, *w2, *b2, *w3, *b3;
   float *g_ea, *g_eb, *g_w, *g_temporal, *g_w1, *g_b1, *g_w2, *g_b2, *g_w3, *g_b3;
   int relaxed;
@@ -170,7 +171,7 @@ __device__ __forceinline__ void fit_gather(const FitArgs& a, float u, float v, f
   }
   int j0, j1;
   float al;
-  temporal_setup(tq, a.t_count, j0, j1, al);
+  temporal_setup_k(tq, a.t_count, a.key_t, j0, j1, al);
   const float ga = 1.0f - al;
 #pragma unroll
   for (int c = 0; c < CT; ++c) x[CS + c] = ga * a.temporal[j0 * CT + c] + al * a.temporal[j1 * CT + c];
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
     }
     int j0, j1;
     float al;
-    temporal_setup(tq, a.t_count, j0, j1, al);
+    temporal_setup_k(tq, a.t_count, a.key_t, j0, j1, al);
     // ---- A1: features (spatial channels q*SC.., temporal q*TC.. of this thread) ----
     {
       TapInfo t[4];
@@ -825,6 +826,7 @@ static FitArgs make_args(const ndgi_fit_params* p) {
   a.lm_w = p->lm_w; a.lm_h = p->lm_h; a.feat_w = p->feat_w; a.feat_h = p->feat_h; a.cs = p->cs;
   a.bw = p->feat_w / 4; a.t_count = p->t_count; a.ct = p->ct; a.hidden = p->hidden;
   a.address_mode = p->address_mode;
+  a.key_t = p->key_t;
   a.ea = p->ea; a.eb = p->eb; a.w = p->w; a.temporal = p->temporal;
   a.w1 = p->w1; a.b1 = p->b1; a.w2 = p->w2; a.b2 = p->b2; a.w3 = p->w3; a.b3 = p->b3;
   return a;

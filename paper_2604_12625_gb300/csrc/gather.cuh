@@ -100,7 +100,7 @@ __device__ __forceinline__ void gather_f32(const DevModel& m, float u, float v, 
   }
   int j0, j1;
   float a;
-  temporal_setup(t, m.t_count, j0, j1, a);
+  temporal_setup_k(t, m.t_count, m.key_t, j0, j1, a);
   const float ga = 1.0f - a;
 #pragma unroll
   for (int c = 0; c < CT; ++c) {
@@ -186,7 +186,7 @@ __device__ __forceinline__ void gather_tc(const DevModel& m, float u, float v, f
   }
   int j0, j1;
   float a;
-  temporal_setup(t, m.t_count, j0, j1, a);
+  temporal_setup_k(t, m.t_count, m.key_t, j0, j1, a);
   const float ga = 1.0f - a;
   const bool vec = (reinterpret_cast<uintptr_t>(m.temporal) & 15u) == 0u;
   if (CT % 8 == 0 && m.temporal_f16 && vec) {
@@ -342,7 +342,7 @@ __device__ __forceinline__ void gather_sliced(const DevModel& m, const uint8_t* 
   sliced_plane<CS, CT, 0>(ew, ix, wq, x, lut);
   int j0, j1;
   float a;
-  temporal_setup(t, m.t_count, j0, j1, a);
+  temporal_setup_k(t, m.t_count, m.key_t, j0, j1, a);
   const float ga = 1.0f - a;
   const bool vec = (reinterpret_cast<uintptr_t>(m.temporal) & 15u) == 0u;
   if (CT % 8 == 0 && m.temporal_f16 && vec) {

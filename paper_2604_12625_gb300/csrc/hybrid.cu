@@ -314,6 +314,55 @@ __device__ __forceinline__ void hybrid_pack_a1(const float (&x)[16], uint32_t (&
   for (int k = 9; k < 16; ++k) w[k] = 0u;
 }
 
+// Two GELUs with the packed FP32 pair instructions of sm_100+ (fma.rn.f32x2,
+// mul.rn.f32x2): the arithmetic of gelu_fast element for element, in half
+// the FMA-pipe instructions (the reciprocals stay scalar).
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float2 gelu_fast2(float a, float b) {
+  constexpr float k = 1.0442737824274138f;   // 2^(1/16), as in gelu_fast
+  const uint64_t z = f2_pack(fabsf(a) * 0.70710678118654752f, fabsf(b) * 0.70710678118654752f);
+  uint64_t p = f2_fma(f2_pack(k * 0.0000430638f, k * 0.0000430638f), z,
+                      f2_pack(k * 0.0002765672f, k * 0.0002765672f));
+  p = f2_fma(p, z, f2_pack(k * 0.0001520143f, k * 0.0001520143f));
+  p = f2_fma(p, z, f2_pack(k * 0.0092705272f, k * 0.0092705272f));
+  p = f2_fma(p, z, f2_pack(k * 0.0422820123f, k * 0.0422820123f));
+  p = f2_fma(p, z, f2_pack(k * 0.0705230784f, k * 0.0705230784f));
+  p = f2_fma(p, z, f2_pack(k, k));
+  float pa, pb, ra, rb;
+  f2_unpack(p, pa, pb);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ra) : "f"(pa));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rb) : "f"(pb));
+  uint64_t r = f2_pack(ra, rb);
+  r = f2_mul(r, r);
+  r = f2_mul(r, r);
+  r = f2_mul(r, r);
+  r = f2_mul(r, r);   // erfc(z) / 2
+  f2_unpack(r, ra, rb);
+  // x >= 0: x - x r = fma(x, -r, x); x < 0: x r = fma(x, r, 0)
+  const float sa = __uint_as_float(__float_as_uint(ra) ^ (~__float_as_uint(a) & 0x80000000u));
+  const float sb = __uint_as_float(__float_as_uint(rb) ^ (~__float_as_uint(b) & 0x80000000u));
+  float ya, yb;
+  f2_unpack(f2_fma(f2_pack(a, b), f2_pack(sa, sb), f2_pack(fmaxf(a, 0.0f), fmaxf(b, 0.0f))), ya, yb);
+  return make_float2(ya, yb);
+}
+
 // Slot s of a lane's engine: this thread's layer-1/2 accumulator row -> GELU ->
 // FP16/BF16 -> the hidden A tile, 16 columns at a time; with ONES also the
 // ones column that carries the next layer's bias (the engine's ReLU epilogue
@@ -329,8 +378,10 @@ __device__ __forceinline__ void epilogue_gelu(E& e, int s) {
     tmem_ld16(d + c, r);
     tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      w[j] = pack2<E::BF16>(gelu_fast(__uint_as_float(r[2 * j])), gelu_fast(__uint_as_float(r[2 * j + 1])));
+    for (int j = 0; j < 8; ++j) {
+      const float2 g = gelu_fast2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+      w[j] = pack2<E::BF16>(g.x, g.y);
+    }
     tmem_st8(a + c / 2, w);
   }
   if constexpr (ONES) {
@@ -608,7 +659,7 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
 
 __global__ void k_debug_gelu(const float* __restrict__ x, int64_t n, float* __restrict__ y, int fast) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = fast ? gelu_fast(x[i]) : gelu(x[i]);
+    y[i] = fast == 2 ? gelu_fast2(x[i], 0.0f).x : (fast ? gelu_fast(x[i]) : gelu(x[i]));
 }
 
 // ---------------------------------------------------------------------------

@@ -21,6 +21,7 @@ struct DevModel {
   const float *w1, *b1, *w2, *b2, *w3, *b3;
   int address_mode;
   float sx, sy;        // feat_w / lm_w, feat_h / lm_h (page texel -> feature coordinate)
+  const float* key_t;  // keyframe times [t_count] or null (j / t_count)
 };
 
 inline DevModel to_dev(const ndgi_model_desc& d) {
@@ -32,6 +33,7 @@ inline DevModel to_dev(const ndgi_model_desc& d) {
   m.address_mode = d.address_mode;
   m.sx = (float)d.feat_w / (float)d.lm_w;
   m.sy = (float)d.feat_h / (float)d.lm_h;
+  m.key_t = d.key_t;
   return m;
 }
 
@@ -76,6 +78,13 @@ constexpr int kErrTimeout = 16;
 // nothing arrives at, before any MMA is issued or tensor memory is touched by
 // an MMA, so the kernel takes its timeout path (test of that path).
 constexpr int kDbgInjectTimeout = 1;
+// Debug-word bit: the FP8 4x1 page kernel copies the operands and accumulators
+// of one tile (request debug_word[1], its first 2 x 64 texels) to the device
+// buffer whose address is stored at debug_word + 2 (layout: ndgi_pages_plan_set_fp8_dump).
+constexpr int kDbgDumpFp8 = 2;
+// Words per texel row of that dump: A1 (8), D1 (H), A2 ((H+32)/4), D2 (H), A3 ((H+32)/4), D3 (4).
+constexpr int fp8_dump_row_words(int H) { return 8 + 2 * H + 2 * ((H + 32) / 4) + 4; }
+constexpr int kLaneThreadsHost = 128;   // texel rows of one tile (the dump's row count)
 cudaError_t launch_pages_f32(const PagesCtx& c, int cs, int ct, int hidden, const ndgi_page_req* reqs,
                              const int32_t* n_dev, int grid, cudaStream_t s);
 

@@ -393,7 +393,7 @@ __device__ __forceinline__ int page_take_request(const PagesCtx& c, const ndgi_p
   if (tid < CT) {
     int j0, j1;
     float a;
-    temporal_setup(r.t, m.t_count, j0, j1, a);
+    temporal_setup_k(r.t, m.t_count, m.key_t, j0, j1, a);
     float vt = (1.0f - a) * load_temporal(m.temporal, m.temporal_f16, j0 * CT + tid) +
                a * load_temporal(m.temporal, m.temporal_f16, j1 * CT + tid);
     if constexpr (F8) vt = sc->a1 * e4m3_value(e4m3x2(vt * sc->inv_a1, 0.0f) & 0xFFu);
@@ -481,6 +481,28 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
   if (c.debug_word && (*c.debug_word & kDbgInjectTimeout)) inject_timeout(e);
   e.b3 = st.b3;
   const int wg = e.wg, t = e.t;
+  // FP8 operand dump (test hook, off unless the plan's debug word asks for it)
+  uint32_t* dump = nullptr;
+  int dump_item = -1;
+  if constexpr (F8) {
+    if (c.debug_word && (c.debug_word[0] & kDbgDumpFp8)) {
+      dump_item = c.debug_word[1];
+      dump = *reinterpret_cast<uint32_t* const*>(c.debug_word + 2);
+    }
+  }
+  constexpr int kDumpRow = fp8_dump_row_words(H), kDumpQ = (H + 32) / 4;
+  // Copies nw words of this thread's tensor-memory row from column col to
+  // word off of its dump row (warp-uniform: tcgen05.ld is warp-wide).
+  auto dump_tmem = [&](uint32_t col, int nw, int off) {
+    tmem_st_wait();
+    for (int k = 0; k < nw; k += 4) {
+      uint32_t v[4];
+      tmem_ld4(e.tmem[0] + e.lane_off + col + (uint32_t)k, v);
+      tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dump[t * kDumpRow + off + k + j] = v[j];
+    }
+  };
   unsigned char* lb = sm + S::kLanes + wg * S::kLaneBytes;
   unsigned char* ring = lb + S::kRing;
   int4* rowtab = reinterpret_cast<int4*>(lb + S::kRowTab);
@@ -496,6 +518,7 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
     const DevModel& m = c.models[r.model];
     // ---- lane: 64 x 64 quadrants of the request; a tile = 64 columns x 2 rows ----
     for (int quad = wg; quad < 4 && !timed_out; quad += NWG) {
+      const bool dumping = F8 && dump != nullptr && st.item == dump_item && quad == 0;   // lane-uniform
       const int ox = (quad & 1) * kQuad, oy = (quad >> 1) * kQuad;
       const int qw = min(kQuad, r.w - ox), qh = min(kQuad, r.h - oy);
       if (qw <= 0 || qh <= 0) continue;
@@ -571,6 +594,15 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
         }
         a1_bias_words<CS, P, NW>(w, F8 ? st.ones1 : 0u);
         e.write_a1(s, w);
+        if constexpr (F8) {
+          if (dumping && tl == 0) {
+#pragma unroll
+            for (int j = 0; j < NW; ++j) dump[t * kDumpRow + j] = w[j];
+            uint32_t* tail = dump + kLaneThreads * kDumpRow;
+            if (t < CT) tail[t] = __float_as_uint(st.vt[t]);
+            if (t < H) tail[CT + t] = *reinterpret_cast<const uint32_t*>(sm + S::kB1 + kmajor_offset8(t, CS, L::K1G));
+          }
+        }
         return orow;
       };
       // Reads slot s's RGB (every thread: tcgen05.ld is warp-wide) and stores
@@ -606,8 +638,15 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
           inflight[0] = true;
           for (int tile = 1;; ++tile) {
             inflight[0] = !e.wait(0);   // layer 1 (+ the previous tile's layer 3)
+            if constexpr (F8) {
+              if (dumping && tile == 1) dump_tmem(0u, H, 8);                              // D1
+              if (dumping && tile == 2) dump_tmem(E::kD3Col, 4, 8 + 2 * H + 2 * kDumpQ);   // D3
+            }
             if (pending) store(0, prev);
             e.template epilogue<true>(0, F8 ? sc->ones2 : 0u);
+            if constexpr (F8) {
+              if (dumping && tile == 1) dump_tmem(E::kACol, kDumpQ, 8 + H);               // A2
+            }
             if (!e.layer2(0)) {
               timed_out = true;
               break;
@@ -616,7 +655,13 @@ __global__ void __launch_bounds__(kLaneThreads* NWG, 1) k_pages_tc(PagesCtx c, c
             const bool more = tile < ntiles;
             const int next_row = more ? produce(0, tile) : -1;
             inflight[0] = !e.wait(0);   // layer 2
+            if constexpr (F8) {
+              if (dumping && tile == 1) dump_tmem(0u, H, 8 + H + kDumpQ);                 // D2
+            }
             e.template epilogue<F8>(0, F8 ? sc->ones3 : 0u);
+            if constexpr (F8) {
+              if (dumping && tile == 1) dump_tmem(E::kACol, kDumpQ, 8 + 2 * H + kDumpQ);   // A3
+            }
             if (!e.layer3(0, more)) {
               timed_out = true;
               break;

@@ -124,7 +124,7 @@ template <int CT>
 __device__ __forceinline__ void gather_temporal(const DevModel& m, float t, float (&xt)[CT]) {
   int j0, j1;
   float a;
-  temporal_setup(t, m.t_count, j0, j1, a);
+  temporal_setup_k(t, m.t_count, m.key_t, j0, j1, a);
   const float ga = 1.0f - a;
   const bool vec = (reinterpret_cast<uintptr_t>(m.temporal) & 15u) == 0u;
   if (CT % 8 == 0 && m.temporal_f16 && vec) {

@@ -310,3 +310,63 @@ def hybrid_tile_of(s, i):
     m = {k: s[k][i] for k in ("uv_bc4", "vol_bc4", "ut", "vt", "w1", "b1", "w2", "b2", "w3", "b3")}
     m.update({k: s[k] for k in ("kind", "lm_w", "lm_h", "uv_w", "uv_h", "vol_shape", "hidden", "address_mode")})
     return m
+
+
+# --------------------------------------------------------------------------
+# Non-uniform keyframes with a light-switch event (Sec. 3.1, supplement S4.1)
+# --------------------------------------------------------------------------
+
+def switch_key_times(n_hourly=24, t_switch=0.73, gap=1.0 / 96):
+    """Keyframe times of a day baked hourly (j / n_hourly) plus two extra sets
+    around a light-switch event at t_switch (t_switch -+ gap): float32, sorted,
+    n_hourly + 2 values in [0, 1)."""
+    t = np.concatenate([np.arange(n_hourly) / n_hourly, [t_switch - gap, t_switch + gap]])
+    t = np.unique(np.mod(t, 1.0).astype(np.float32))
+    assert t.size == n_hourly + 2
+    return t
+
+
+def fit_targets_at_times(seed, width, height, times, n_gauss=32, ambient=0.05, t_on=0.73, t_off=0.9,
+                         lamp_amp=6.0, lamp_sigma=24.0):
+    """Procedural HDR lightmaps FP16 [T][H][W][3] at the given times: the
+    Gaussian sun-lit blobs of fit_targets (with cos(2 pi t + phi) at the actual
+    t) plus a local lamp, a Gaussian of amplitude lamp_amp at a seeded
+    position, switched on for t_on <= t < t_off (a light-switch event)."""
+    rng = _rng(seed)
+    cx, cy = rng.uniform(0, width, n_gauss), rng.uniform(0, height, n_gauss)
+    sig = rng.uniform(8.0, 64.0, n_gauss)
+    amp = rng.uniform(0.0, 1.0, (n_gauss, 3)) * 4.0
+    phi = rng.uniform(0.0, 2 * np.pi, n_gauss)
+    lx, ly = rng.uniform(0.2, 0.8) * width, rng.uniform(0.2, 0.8) * height
+    lamp_rgb = np.array([1.0, 0.8, 0.5]) * lamp_amp
+    xs = np.arange(width, dtype=np.float64) + 0.5
+    ys = np.arange(height, dtype=np.float64) + 0.5
+    times = np.asarray(times, np.float64)
+    out = np.empty((len(times), height, width, 3), dtype=np.float16)
+    lamp = (np.exp(-((ys[:, None] - ly) ** 2 + (xs[None, :] - lx) ** 2) / (2 * lamp_sigma ** 2)))[:, :, None] * lamp_rgb
+    for j, t in enumerate(times):
+        acc = np.full((height, width, 3), ambient, np.float64)
+        sun = np.maximum(0.0, np.cos(2 * np.pi * t + phi))
+        for g in range(n_gauss):
+            if sun[g] == 0.0:
+                continue
+            gx = np.exp(-((xs - cx[g]) ** 2) / (2 * sig[g] ** 2))
+            gy = np.exp(-((ys - cy[g]) ** 2) / (2 * sig[g] ** 2))
+            acc += (gy[:, None] * gx[None, :])[:, :, None] * (amp[g] * sun[g])
+        if t_on <= t < t_off:
+            acc += lamp
+        out[j] = acc.astype(np.float16)
+    return out
+
+
+def lightmap_mask(seed, width, height, n_islands=12, fill=0.7):
+    """Validity mask [H][W] uint8 of a UV-packed lightmap: rectangular charts
+    (seeded islands) covering about `fill` of the texels, 1 = valid."""
+    rng = _rng(seed)
+    m = np.zeros((height, width), np.uint8)
+    while m.mean() < fill:
+        w = int(rng.integers(width // 16, width // 3))
+        h = int(rng.integers(height // 16, height // 3))
+        x, y = int(rng.integers(0, width - w)), int(rng.integers(0, height - h))
+        m[y:y + h, x:x + w] = 1
+    return m

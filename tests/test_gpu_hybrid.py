@@ -221,7 +221,7 @@ def test_full_frame_sampled(ndgi):
     table.close()
 
 
-@pytest.mark.parametrize("fast", [False, True])
+@pytest.mark.parametrize("fast", [0, 1, 2])
 def test_gelu_on_device_against_oracle(ndgi, fast):
     # exact form (erff) within a few FP32 ulps; the epilogue's A&S 7.1.28 form within 2e-6 (1 + |x|)
     x = np.concatenate([np.linspace(-12, 12, 200_001), [0.0, -0.0, 1e-30, -1e-30, 30.0, -30.0, 1e4, -1e4]])
@@ -232,6 +232,9 @@ def test_gelu_on_device_against_oracle(ndgi, fast):
     err = np.abs(y - ref)
     print(f"gelu fast={fast}: max |err| / (1 + |x|) = {np.max(err / (1 + np.abs(x))):.3e}")
     assert np.all(err <= bound)
+    if fast == 2:   # the packed form rounds exactly as the scalar form
+        y1 = ndgi.ndgi_debug_gelu(torch.from_numpy(x).cuda(), fast=1).cpu().numpy()
+        assert np.array_equal(y.astype(np.float32), y1)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
