@@ -560,6 +560,23 @@ size_t ndgi_encode_fit_workspace_size(const ndgi_fit_params *params, const ndgi_
 ndgi_status ndgi_encode_fit(const ndgi_fit_params *params, const uint16_t *targets, const ndgi_fit_config *cfg,
                             int32_t step_offset, void *ws, size_t ws_bytes, double *loss_log, void *stream);
 
+/*
+ * Batched per-tile fit (Sec. 3.5 trains one model per virtual-texture tile;
+ * Sec. 4 fits thousands of them side by side): ndgi_encode_fit for n_models
+ * models of the same shape in one launch per step.  Each of params' ten
+ * tensors holds the n_models models one after another (model m's tensor at
+ * m times its single-model size), as do targets ([n_models][t_count][lm_h]
+ * [lm_w][3] FP16); params' sizes are those of one model, and all models share
+ * key_t.  Model m draws its samples as ndgi_encode_fit does with seed + m.
+ * cfg->batch samples per model and step; loss_log holds the mean over all
+ * models' samples.  ws: ndgi_encode_fit_batch_workspace_size bytes.
+ */
+size_t ndgi_encode_fit_batch_workspace_size(const ndgi_fit_params *params, int32_t n_models,
+                                            const ndgi_fit_config *cfg);
+ndgi_status ndgi_encode_fit_batch(const ndgi_fit_params *params, int32_t n_models, const uint16_t *targets,
+                                  const ndgi_fit_config *cfg, int32_t step_offset, void *ws, size_t ws_bytes,
+                                  double *loss_log, void *stream);
+
 
 /* ======================================================================
  * Hybrid feature map decoder: the paper's full decoder (Sec. 3.3, Eq. 4-5;
@@ -671,6 +688,18 @@ ndgi_status ndgi_hybrid_decode_pages(ndgi_hybrid_table *table, const ndgi_page_r
  */
 ndgi_status ndgi_hybrid_debug_inject(const ndgi_hybrid_desc *model, ndgi_precision precision, void *ws,
                                      ndgi_hybrid_table *table, int32_t flags, void *stream);
+
+/*
+ * Mirrored tile border (supplement S3: each tile is stored with a small
+ * border, e.g. 4 texels per edge, with the same mirrored padding used in
+ * training, so that hardware filtering is seamless): later page decodes with
+ * this table write (w + 2 border) x (h + 2 border) texels per request, at
+ * (dst_x - border, dst_y - border); padded texel i of a row or column of n
+ * texels decodes tile texel i - border reflected into [0, n) with the edge
+ * texel repeated (-1 -> 0, n -> n - 1).  border 0..8 (default 0); a request
+ * needs border <= w, h and its padded destination inside the texture.
+ */
+ndgi_status ndgi_hybrid_table_set_border(ndgi_hybrid_table *table, int32_t border);
 
 /* Synchronises, reads and clears the table's error word (bit 0 bad request, bit 4 timeout). */
 ndgi_status ndgi_hybrid_table_check(ndgi_hybrid_table *table, int32_t *device_error, void *stream);

@@ -105,7 +105,7 @@ def lib():
             L.om_gelu.restype = f64
             L.om_hybrid_gamma.argtypes = [f64, vp]
             L.om_hybrid_decode_points.argtypes = [vp, vp, i64, vp, vp, C.c_int]
-            L.om_hybrid_decode_pages.argtypes = [vp, i32, vp, i32, vp, i64, i64, C.c_int]
+            L.om_hybrid_decode_pages.argtypes = [vp, i32, vp, i32, vp, i64, i64, i32, C.c_int]
             L.om_tile_metrics.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
             L.om_splitmix64_next.argtypes = [C.c_uint64]
             L.om_splitmix64_next.restype = C.c_uint64
@@ -228,14 +228,15 @@ def hybrid_decode_points(m, uvt, precision="fp32", nthreads=None, features=False
     return (y, x) if features else y
 
 
-def hybrid_decode_pages(models, reqs, phys_w, phys_h, precision="fp32", nthreads=None, fill=np.nan):
-    """FP64 RGBA physical texture [phys_h][phys_w][4] of hybrid-model page requests; untouched texels = fill."""
+def hybrid_decode_pages(models, reqs, phys_w, phys_h, precision="fp32", nthreads=None, fill=np.nan, border=0):
+    """FP64 RGBA physical texture [phys_h][phys_w][4] of hybrid-model page requests (with a mirrored tile border
+    of `border` texels per edge); untouched texels = fill."""
     r = np.ascontiguousarray(reqs)
     out = np.full((phys_h, phys_w, 4), fill, np.float64)
     Ms = [_hybrid(m, precision) for m in models]
     arr = (_Hybrid * len(Ms))(*[M.s for M in Ms])
     lib().om_hybrid_decode_pages(arr, len(Ms), r.ctypes.data_as(C.c_void_p), len(r), _ptr(out), phys_w, phys_h,
-                                 nthreads or nthreads_default())
+                                 int(border), nthreads or nthreads_default())
     return out
 
 

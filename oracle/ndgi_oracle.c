@@ -875,25 +875,37 @@ void om_hybrid_decode_points(const om_hybrid *m, const float *uvt, int64_t n, do
   }
 }
 
+/* Tile texel of padded index i (of n + 2b) under the mirrored border of
+ * supplement S3: reflect i - b into [0, n), the edge texel repeated. */
+static int om_border_mirror(int i, int n, int b) {
+  int k = i - b;
+  if (k < 0) return -1 - k;
+  if (k >= n) return 2 * n - 1 - k;
+  return k;
+}
+
 /* Page decode with hybrid models (Sec. 3.5): as om_decode_pages, texel
  * (x0+i, y0+j) of each request at ((x0+i+0.5)/lm_w, (y0+j+0.5)/lm_h, t) of the
- * request's model, RGBA (A = 1) into phys[phys_h][phys_w][4]. */
+ * request's model, RGBA (A = 1) into phys[phys_h][phys_w][4].  With a border
+ * b > 0 each request covers (w + 2b) x (h + 2b) texels from (dst_x - b,
+ * dst_y - b), the border texels mirrored from the tile (supplement S3). */
 void om_hybrid_decode_pages(const om_hybrid *models, int32_t n_models, const om_page_req *reqs, int32_t n,
-                            double *phys, int64_t phys_w, int64_t phys_h, int nthreads) {
+                            double *phys, int64_t phys_w, int64_t phys_h, int32_t border, int nthreads) {
   (void)n_models;
   (void)phys_h;
+  const int b = border;
   for (int32_t r = 0; r < n; ++r) {
     const om_page_req *q = &reqs[r];
     const om_hybrid *m = &models[q->model];
 #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
-    for (int32_t jj = 0; jj < q->h; ++jj) {
+    for (int32_t jj = 0; jj < q->h + 2 * b; ++jj) {
       double f[16], rgb[3];
-      for (int32_t ii = 0; ii < q->w; ++ii) {
-        const double u = ((double)(q->x0 + ii) + 0.5) / (double)m->lm_w;
-        const double v = ((double)(q->y0 + jj) + 0.5) / (double)m->lm_h;
+      for (int32_t ii = 0; ii < q->w + 2 * b; ++ii) {
+        const double u = ((double)(q->x0 + om_border_mirror(ii, q->w, b)) + 0.5) / (double)m->lm_w;
+        const double v = ((double)(q->y0 + om_border_mirror(jj, q->h, b)) + 0.5) / (double)m->lm_h;
         om_hybrid_features(m, u, v, (double)q->t, f);
         om_hybrid_mlp(m, f, rgb);
-        double *o = phys + ((int64_t)(q->dst_y + jj) * phys_w + (q->dst_x + ii)) * 4;
+        double *o = phys + ((int64_t)(q->dst_y - b + jj) * phys_w + (q->dst_x - b + ii)) * 4;
         o[0] = rgb[0];
         o[1] = rgb[1];
         o[2] = rgb[2];

@@ -99,6 +99,8 @@ SIGNATURES = [
     ("ndgi_fit_backward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),
     ("ndgi_encode_fit_workspace_size", _sz, [_vp, _vp]),
     ("ndgi_encode_fit", C.c_int, [_vp, _vp, _vp, _i32, _vp, _sz, _vp, _vp]),
+    ("ndgi_encode_fit_batch_workspace_size", _sz, [_vp, _i32, _vp]),
+    ("ndgi_encode_fit_batch", C.c_int, [_vp, _i32, _vp, _vp, _i32, _vp, _sz, _vp, _vp]),
     ("ndgi_hybrid_workspace_size", _sz, [_vp, C.c_int]),
     ("ndgi_hybrid_prepare", C.c_int, [_vp, C.c_int, _vp, _vp]),
     ("ndgi_hybrid_decode_points", C.c_int, [_vp, C.c_int, _vp, _vp, _i64, _vp, _vp]),
@@ -108,6 +110,7 @@ SIGNATURES = [
     ("ndgi_hybrid_table_destroy", C.c_int, [_vp]),
     ("ndgi_hybrid_decode_pages", C.c_int, [_vp, _vp, _i32, _vp, _i64, _i64, C.c_int, _vp]),
     ("ndgi_hybrid_table_check", C.c_int, [_vp, _vp, _vp]),
+    ("ndgi_hybrid_table_set_border", C.c_int, [_vp, _i32]),
     ("ndgi_debug_gelu", C.c_int, [_vp, _i64, _vp, _i32, _vp]),
     ("ndgi_model_bpp", C.c_double, [_vp, _i32, _i32, _i32]),
     ("ndgi_tile_metrics", C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp]),

@@ -620,6 +620,10 @@ class HybridTable:
         st = lib().ndgi_hybrid_table_check(self.handle, C.byref(err), _stream(stream))
         return st, err.value
 
+    def set_border(self, border):
+        """Mirrored tile border (texels per edge, 0..8) of later page decodes."""
+        check(lib().ndgi_hybrid_table_set_border(self.handle, int(border)))
+
     def close(self):
         if self.handle:
             check(lib().ndgi_hybrid_table_destroy(self.handle))
@@ -664,3 +668,48 @@ def ndgi_tile_metrics(pred, ref, mask=None, tile=128, stream=None):
     check(lib().ndgi_tile_metrics(_p(pred), _p(ref), _p(mask), n, h, w, c, int(tile), _p(ps), _p(ss),
                                   _stream(stream)))
     return ps, ss
+
+
+class FitBatch:
+    """n_models fit parameter sets of one shape, stacked along a leading axis (float32 CUDA tensors
+    [n_models][...] per FIT_TENSORS key), for ndgi_encode_fit_batch."""
+
+    def __init__(self, tensors, lm_w, lm_h, address_mode=0, key_t=None):
+        self.t = {k: _need(tensors[k], torch.float32, k) for k in A.FIT_TENSORS}
+        self.n_models = int(self.t["ea"].shape[0])
+        assert all(int(v.shape[0]) == self.n_models for v in self.t.values())
+        self.key_t = None if key_t is None else _need(key_t, torch.float32, "key_t")
+        _, bh, bw, cs = self.t["ea"].shape
+        _, T, ct = self.t["temporal"].shape
+        H = self.t["w2"].shape[1]
+        self.lm_w, self.lm_h = int(lm_w), int(lm_h)
+        self.params = A.FitParams(self.lm_w, self.lm_h, bw * 4, bh * 4, cs, T, ct, H,
+                                  *[self.t[k].data_ptr() for k in A.FIT_TENSORS], int(address_mode),
+                                  _p(self.key_t))
+
+    @classmethod
+    def from_arrays(cls, ps, lm_w, lm_h, key_t=None, device="cuda"):
+        """From a list of fit dicts (synth.fit_init)."""
+        t = {k: torch.from_numpy(np.ascontiguousarray(np.stack([p[k] for p in ps]), np.float32)).to(device)
+             for k in A.FIT_TENSORS}
+        return cls(t, lm_w, lm_h, ps[0].get("address_mode", 0),
+                   None if key_t is None else torch.from_numpy(np.asarray(key_t, np.float32)).to(device))
+
+    def model(self, m):
+        """Model m's tensors (views)."""
+        return {k: v[m] for k, v in self.t.items()}
+
+
+def ndgi_encode_fit_batch(batch, targets, cfg, step_offset=0, ws=None, loss_log=None, stream=None):
+    """cfg.steps Adam steps of every model of a FitBatch in place.  targets: float16
+    [n_models][T][lm_h][lm_w][3] CUDA.  Returns (ws, loss_log)."""
+    _need(targets, torch.float16, "targets")
+    n = int(lib().ndgi_encode_fit_batch_workspace_size(C.byref(batch.params), batch.n_models, C.byref(cfg)))
+    if ws is None:
+        ws = torch.empty(n, dtype=torch.uint8, device=targets.device)
+    if loss_log is None and cfg.loss_every > 0:
+        loss_log = torch.zeros((cfg.steps + cfg.loss_every - 1) // cfg.loss_every, dtype=torch.float64,
+                               device=targets.device)
+    check(lib().ndgi_encode_fit_batch(C.byref(batch.params), batch.n_models, _p(targets), C.byref(cfg),
+                                      int(step_offset), _p(ws), ws.numel(), _p(loss_log), _stream(stream)))
+    return ws, loss_log

@@ -42,7 +42,40 @@ struct FitArgs {
   uint64_t seed;                // mode 1
   const int64_t* step;          // mode 1: device step counter
   double* loss_acc;             // mode 1: sum of squared errors
+  int n_models;                 // mode 1: models trained side by side (CTA row blockIdx.y = model)
+  int64_t ms[10];               // per-model element count of each tensor (and of its gradient)
+  int64_t tgt_stride;           // per-model element count of the targets
 };
+
+// Batched fit (mode 1): the ten tensors, their gradients and the targets hold
+// n_models models one after another; CTA row m trains model m, drawing its
+// samples with seed + m.
+__device__ __forceinline__ void fit_select_model(FitArgs& a) {
+  const int64_t m = blockIdx.y;
+  if (m == 0) return;
+  a.ea += m * a.ms[0];
+  a.eb += m * a.ms[1];
+  a.w += m * a.ms[2];
+  a.temporal += m * a.ms[3];
+  a.w1 += m * a.ms[4];
+  a.b1 += m * a.ms[5];
+  a.w2 += m * a.ms[6];
+  a.b2 += m * a.ms[7];
+  a.w3 += m * a.ms[8];
+  a.b3 += m * a.ms[9];
+  a.g_ea += m * a.ms[0];
+  a.g_eb += m * a.ms[1];
+  a.g_w += m * a.ms[2];
+  a.g_temporal += m * a.ms[3];
+  a.g_w1 += m * a.ms[4];
+  a.g_b1 += m * a.ms[5];
+  a.g_w2 += m * a.ms[6];
+  a.g_b2 += m * a.ms[7];
+  a.g_w3 += m * a.ms[8];
+  a.g_b3 += m * a.ms[9];
+  a.targets += m * a.tgt_stride;
+  a.seed += (uint64_t)m;
+}
 
 // ---------------------------------------------------------------------------
 // Counter-based sample stream: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014).
@@ -213,7 +246,8 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_forward(FitArgs a, float* _
 // ---------------------------------------------------------------------------
 // Backward (persistent, tiles of kFitTile samples, kFitQ threads per sample).
 // MODE 0: samples + dL/drgb given.  MODE 1: samples drawn on device, dL/drgb
-// from the MSE against the FP16 targets, FP64 loss accumulated.
+// from the MSE against the FP16 targets, FP64 loss accumulated.  MODE 2: MODE 1
+// for a batch of stacked models (CTA row blockIdx.y = model; fit_select_model).
 //
 // Each sample's forward and backward is split over kFitQ = 4 threads (q),
 // each computing HQ = H/4 of the hidden units, which gives 16 warps per SM
@@ -266,8 +300,10 @@ __device__ __forceinline__ void lds(const float* p, float (&v)[N]) {
 }
 
 template <int CS, int CT, int H, int MODE>
-__global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a_in) {
   using L = FitSmem<CS, CT, H>;
+  FitArgs a = a_in;
+  if constexpr (MODE == 2) fit_select_model(a);
   constexpr int CIN = CS + CT;
   constexpr int LX = L::LX, LH = L::LH, HS = L::HS, HQ = L::HQ;
   constexpr int SC = CS / kFitQ, TC = CT / kFitQ;   // spatial / temporal channels per thread of a sample
@@ -328,7 +364,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
   for (int k = 0; k < K1; ++k) acc1[k] = 0.0f;
   double loss = 0.0;
   int64_t step = 0;
-  if (MODE == 1) step = *a.step;
+  if (MODE != 0) step = *a.step;
 
   const int64_t n_tiles = (a.n + kFitTile - 1) / kFitTile;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -683,7 +719,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_fit_backward(FitArgs a) {
   else if (tid < 3 * H + 3) atomicAdd(&a.g_b3[tid - 3 * H], acc3);
   __syncthreads();
   for (int i = tid; i < a.t_count * CT; i += kBwdThreads) atomicAdd(&a.g_temporal[i], sGK[i]);
-  if (MODE == 1) {
+  if (MODE != 0) {
     for (int off = 16; off > 0; off >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, off);
     if ((tid & 31) == 0) atomicAdd(a.loss_acc, loss);
   }
@@ -774,15 +810,18 @@ static cudaError_t launch_fit_backward(const FitArgs& args, int mode, cudaStream
   a.vec_red = ((reinterpret_cast<uintptr_t>(a.g_ea) | reinterpret_cast<uintptr_t>(a.g_eb)) & 15u) == 0u;
   a.vec_ld = ((reinterpret_cast<uintptr_t>(a.ea) | reinterpret_cast<uintptr_t>(a.eb)) & 15u) == 0u;
   const int64_t tiles = (a.n + kFitTile - 1) / kFitTile;
-  const int64_t cap = num_sms();
+  const int models = a.n_models > 0 ? a.n_models : 1;
+  // about two CTAs per SM in all (one model: one per SM), at most one per tile
+  const int64_t cap = models == 1 ? (int64_t)num_sms() : ((int64_t)num_sms() * 2 + models - 1) / models;
   const int grid = (int)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
 #define X(A, B, C)                                                                                   \
   if (a.cs == A && a.ct == B && a.hidden == C) {                                                     \
     const size_t smem = fit_smem_bytes<A, B, C>(a.t_count);                                          \
-    auto kern = mode == 0 ? k_fit_backward<A, B, C, 0> : k_fit_backward<A, B, C, 1>;                  \
+    auto kern = mode == 0 ? k_fit_backward<A, B, C, 0>                                               \
+                          : (models > 1 ? k_fit_backward<A, B, C, 2> : k_fit_backward<A, B, C, 1>);    \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                  \
-    kern<<<grid, kBwdThreads, smem, s>>>(a);                                                         \
+    kern<<<dim3(grid, mode == 0 ? 1 : models), kBwdThreads, smem, s>>>(a);                           \
     return cudaGetLastError();                                                                       \
   }
   NDGI_FIT_SHAPES(X)
@@ -827,6 +866,7 @@ static FitArgs make_args(const ndgi_fit_params* p) {
   a.bw = p->feat_w / 4; a.t_count = p->t_count; a.ct = p->ct; a.hidden = p->hidden;
   a.address_mode = p->address_mode;
   a.key_t = p->key_t;
+  a.n_models = 1;
   a.ea = p->ea; a.eb = p->eb; a.w = p->w; a.temporal = p->temporal;
   a.w1 = p->w1; a.b1 = p->b1; a.w2 = p->w2; a.b2 = p->b2; a.w3 = p->w3; a.b3 = p->b3;
   return a;
@@ -884,32 +924,43 @@ ndgi_status ndgi_fit_backward(const ndgi_fit_params* params, const float* uvt, i
   return cuda_status(launch_fit_backward(a, 0, (cudaStream_t)stream), "ndgi_fit_backward");
 }
 
-size_t ndgi_encode_fit_workspace_size(const ndgi_fit_params* params, const ndgi_fit_config* cfg) {
+size_t ndgi_encode_fit_batch_workspace_size(const ndgi_fit_params* params, int32_t n_models,
+                                            const ndgi_fit_config* cfg) {
   (void)cfg;
-  if (!params) return 0;
+  if (!params || n_models < 1) return 0;
   int64_t n[10];
   fit_sizes(params, n);
   int64_t tot = 0;
-  for (int k = 0; k < 10; ++k) tot += n[k];
+  for (int k = 0; k < 10; ++k) tot += n[k] * n_models;
   return 256 + 3 * round256((size_t)tot * sizeof(float));
 }
 
-ndgi_status ndgi_encode_fit(const ndgi_fit_params* params, const uint16_t* targets, const ndgi_fit_config* cfg,
-                            int32_t step_offset, void* ws, size_t ws_bytes, double* loss_log, void* stream) {
+size_t ndgi_encode_fit_workspace_size(const ndgi_fit_params* params, const ndgi_fit_config* cfg) {
+  return ndgi_encode_fit_batch_workspace_size(params, 1, cfg);
+}
+
+}  // extern "C"
+
+namespace ndgi {
+static ndgi_status encode_fit(const ndgi_fit_params* params, int32_t n_models, const uint16_t* targets,
+                              const ndgi_fit_config* cfg, int32_t step_offset, void* ws, size_t ws_bytes,
+                              double* loss_log, void* stream) {
   ndgi_status st = check_fit(params, "ndgi_encode_fit");
   if (st != NDGI_OK) return st;
+  if (n_models < 1) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit_batch: n_models < 1");
   if (!cfg || !targets || !ws) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit: NULL argument");
   if (cfg->steps < 0 || cfg->batch <= 0 || cfg->freeze_steps < 0 || cfg->loss_every < 0 || step_offset < 0)
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit: bad config");
   if (!(cfg->lr > 0.0f) || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit: bad optimiser settings");
-  const size_t need = ndgi_encode_fit_workspace_size(params, cfg);
+  const size_t need = ndgi_encode_fit_batch_workspace_size(params, n_models, cfg);
   if (ws_bytes < need || ((uintptr_t)ws % 256))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit: ws must be 256-byte aligned with >= %zu bytes", need);
   if (cfg->steps == 0) return NDGI_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  int64_t n[10];
-  fit_sizes(params, n);
+  int64_t n[10], per_model[10];
+  fit_sizes(params, per_model);
+  for (int k = 0; k < 10; ++k) n[k] = per_model[k] * n_models;
   int64_t tot = 0;
   AdamTable t{};
   float* pp[10] = {params->ea, params->eb, params->w, params->temporal, params->w1,
@@ -952,6 +1003,9 @@ ndgi_status ndgi_encode_fit(const ndgi_fit_params* params, const uint16_t* targe
   a.seed = cfg->seed;
   a.step = d_step;
   a.loss_acc = d_loss;
+  a.n_models = n_models;
+  for (int k = 0; k < 10; ++k) a.ms[k] = per_model[k];
+  a.tgt_stride = (int64_t)params->t_count * params->lm_h * params->lm_w * 3;
   float* gp[10];
   for (int k = 0; k < 10; ++k) gp[k] = g + t.off[k];
   a.g_ea = gp[0]; a.g_eb = gp[1]; a.g_w = gp[2]; a.g_temporal = gp[3]; a.g_w1 = gp[4];
@@ -978,7 +1032,8 @@ ndgi_status ndgi_encode_fit(const ndgi_fit_params* params, const uint16_t* targe
       le = cudaGetLastError();
     }
     if (le == cudaSuccess) {
-      k_fit_step_end<<<1, 1, 0, cs_>>>(d_step, d_local, d_loss, loss_log, cfg->loss_every, cfg->batch);
+      k_fit_step_end<<<1, 1, 0, cs_>>>(d_step, d_local, d_loss, loss_log, cfg->loss_every,
+                                       (int64_t)cfg->batch * n_models);
       le = cudaGetLastError();
     }
     e = cudaStreamEndCapture(cs_, &graph);
@@ -990,6 +1045,20 @@ ndgi_status ndgi_encode_fit(const ndgi_fit_params* params, const uint16_t* targe
   if (exec) cudaGraphExecDestroy(exec);
   cudaStreamDestroy(cs_);
   return cuda_status(e, "ndgi_encode_fit");
+}
+}  // namespace ndgi
+
+extern "C" {
+
+ndgi_status ndgi_encode_fit(const ndgi_fit_params* params, const uint16_t* targets, const ndgi_fit_config* cfg,
+                            int32_t step_offset, void* ws, size_t ws_bytes, double* loss_log, void* stream) {
+  return ndgi::encode_fit(params, 1, targets, cfg, step_offset, ws, ws_bytes, loss_log, stream);
+}
+
+ndgi_status ndgi_encode_fit_batch(const ndgi_fit_params* params, int32_t n_models, const uint16_t* targets,
+                                  const ndgi_fit_config* cfg, int32_t step_offset, void* ws, size_t ws_bytes,
+                                  double* loss_log, void* stream) {
+  return ndgi::encode_fit(params, n_models, targets, cfg, step_offset, ws, ws_bytes, loss_log, stream);
 }
 
 }  // extern "C"

@@ -196,13 +196,23 @@ __global__ void __launch_bounds__(256) k_hybrid_points_f32(DevHybrid m, const fl
   }
 }
 
-// A request is decoded only if its model index and both rectangles are valid.
+// A request is decoded only if its model index and both rectangles are valid
+// (the destination including the border b on every side, b <= w, h).
 __device__ __forceinline__ bool hybrid_req_ok(const ndgi_page_req& r, const DevHybrid* models, int n_models,
-                                              int64_t phys_w, int64_t phys_h) {
+                                              int64_t phys_w, int64_t phys_h, int b) {
   if (r.model < 0 || r.model >= n_models) return false;
   const DevHybrid& m = models[r.model];
-  return r.w >= 1 && r.w <= 128 && r.h >= 1 && r.h <= 128 && r.x0 >= 0 && r.y0 >= 0 && r.x0 + r.w <= m.lm_w &&
-         r.y0 + r.h <= m.lm_h && r.dst_x >= 0 && r.dst_y >= 0 && r.dst_x + r.w <= phys_w && r.dst_y + r.h <= phys_h;
+  return r.w >= 1 && r.w <= 128 && r.h >= 1 && r.h <= 128 && b <= r.w && b <= r.h && r.x0 >= 0 && r.y0 >= 0 &&
+         r.x0 + r.w <= m.lm_w && r.y0 + r.h <= m.lm_h && r.dst_x - b >= 0 && r.dst_y - b >= 0 &&
+         r.dst_x + r.w + b <= phys_w && r.dst_y + r.h + b <= phys_h;
+}
+
+// Mirrored tile border (supplement S3): texel i of a request's padded row or
+// column, i in [0, n + 2b), is tile texel i - b reflected into [0, n) with
+// the edge texel repeated (-1 -> 0, n -> n - 1).
+__device__ __forceinline__ int border_mirror(int i, int n, int b) {
+  const int k = i - b;
+  return k < 0 ? -1 - k : (k >= n ? 2 * n - 1 - k : k);
 }
 
 __device__ __forceinline__ void put_texel(void* phys, int fmt, int64_t o, float y0, float y1, float y2) {
@@ -222,7 +232,7 @@ __global__ void __launch_bounds__(256) k_hybrid_pages_f32(HybridPagesCtx c, cons
   init_p35_lut(lut, threadIdx.x);
   for (int ri = blockIdx.x; ri < n; ri += gridDim.x) {
     const ndgi_page_req r = reqs[ri];
-    const bool ok = hybrid_req_ok(r, c.models, c.n_models, c.phys_w, c.phys_h);
+    const bool ok = hybrid_req_ok(r, c.models, c.n_models, c.phys_w, c.phys_h, c.border);
     __syncthreads();   // the previous request's texels are done with sw
     if (!ok) {
       if (threadIdx.x == 0) atomicOr(c.error_word, 1);
@@ -231,15 +241,16 @@ __global__ void __launch_bounds__(256) k_hybrid_pages_f32(HybridPagesCtx c, cons
     const DevHybrid m = c.models[r.model];
     load_mlp32<H>(m, sw, threadIdx.x, blockDim.x);
     __syncthreads();
-    for (int i = threadIdx.x; i < r.w * r.h; i += blockDim.x) {
-      const int ix = i % r.w, iy = i / r.w;
-      const float u = ((float)(r.x0 + ix) + 0.5f) / (float)m.lm_w;
-      const float v = ((float)(r.y0 + iy) + 0.5f) / (float)m.lm_h;
+    const int b = c.border, pw = r.w + 2 * b, ph = r.h + 2 * b;
+    for (int i = threadIdx.x; i < pw * ph; i += blockDim.x) {
+      const int ix = i % pw, iy = i / pw;
+      const float u = ((float)(r.x0 + border_mirror(ix, r.w, b)) + 0.5f) / (float)m.lm_w;
+      const float v = ((float)(r.y0 + border_mirror(iy, r.h, b)) + 0.5f) / (float)m.lm_h;
       float x[16];
       hybrid_features(m, u, v, r.t, x, lut);
       float y0, y1, y2;
       mlp32<H>(sw, x, y0, y1, y2);
-      put_texel(c.phys, c.fmt, (int64_t)(r.dst_y + iy) * c.phys_w + (r.dst_x + ix), y0, y1, y2);
+      put_texel(c.phys, c.fmt, (int64_t)(r.dst_y - b + iy) * c.phys_w + (r.dst_x - b + ix), y0, y1, y2);
     }
   }
 }
@@ -264,6 +275,8 @@ struct HybAxis {
   float p0, p1;
 };
 constexpr int kHybVolSide = 48;   // largest F3D footprint side staged in shared memory
+constexpr int kHybBorderMax = 8;  // largest mirrored tile border
+constexpr int kHybAxisMax = 128 + 2 * kHybBorderMax;   // entries of a per-axis table
 
 template <int H>
 struct HybridSmem {
@@ -272,8 +285,8 @@ struct HybridSmem {
   static constexpr uint32_t kB1 = L::kShared;          // B1
   static constexpr uint32_t kPoints = kB1 + H * L::K1P * 2;   // end of the point kernel's part
   static constexpr uint32_t kCols = (kPoints + 15) / 16 * 16;  // pages: HybAxis [128] per column
-  static constexpr uint32_t kRows = kCols + 128 * sizeof(HybAxis);
-  static constexpr uint32_t kVol = kRows + 128 * sizeof(HybAxis);   // float4 [footprint] of F3D at t
+  static constexpr uint32_t kRows = kCols + kHybAxisMax * sizeof(HybAxis);
+  static constexpr uint32_t kVol = kRows + kHybAxisMax * sizeof(HybAxis);   // float4 [footprint] of F3D at t
   static constexpr uint32_t kPages = kVol + kHybVolSide * kHybVolSide * 16;
 };
 
@@ -549,7 +562,7 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
   bool inflight[1] = {false}, stopped = false;
   for (int ri = blockIdx.x; ri < n; ri += gridDim.x) {
     const ndgi_page_req r = reqs[ri];
-    const bool ok = hybrid_req_ok(r, c.models, c.n_models, c.phys_w, c.phys_h);
+    const bool ok = hybrid_req_ok(r, c.models, c.n_models, c.phys_w, c.phys_h, c.border);
     tc_fence_before();
     __syncthreads();   // every lane is done with the previous request's image and tables
     if (!ok) {
@@ -567,10 +580,12 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
     __syncthreads();
     // ---- per-axis tables, gamma(t) and the F3D slice pair ----
     const int mode = m.address_mode;
-    if (tid < r.w || (tid >= 128 && tid - 128 < r.h)) {
-      const bool col = tid < 128;
-      const int i = col ? tid : tid - 128;
-      const float coord = col ? ((float)(r.x0 + i) + 0.5f) / (float)m.lm_w : ((float)(r.y0 + i) + 0.5f) / (float)m.lm_h;
+    const int b = c.border, pw = r.w + 2 * b, ph = r.h + 2 * b;
+    if (tid < pw || (tid >= kHybAxisMax && tid - kHybAxisMax < ph)) {
+      const bool col = tid < kHybAxisMax;
+      const int i = col ? tid : tid - kHybAxisMax;
+      const float coord = col ? ((float)(r.x0 + border_mirror(i, r.w, b)) + 0.5f) / (float)m.lm_w
+                              : ((float)(r.y0 + border_mirror(i, r.h, b)) + 0.5f) / (float)m.lm_h;
       HybAxis a;
       axis_setup(coord, col ? m.vol_w : m.vol_h, mode, a.v0, a.v1, a.vf);
       axis_setup(coord, col ? m.uv_w : m.uv_h, mode, a.u0, a.u1, a.uf);
@@ -584,7 +599,7 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
       (col ? cols : rows)[i] = a;
       atomicMin(&s_lo[col ? 0 : 1], min(a.v0, a.v1));
       atomicMax(&s_hi[col ? 0 : 1], max(a.v0, a.v1));
-    } else if (tid == 256) {
+    } else if (tid == 2 * kHybAxisMax) {
       sincospif(r.t, &s_gamma[0], &s_gamma[1]);
       sincospif(2.0f * r.t, &s_gamma[2], &s_gamma[3]);
       axis_setup(r.t, m.vol_t, 0, s_z[0], s_z[1], s_fz);
@@ -600,13 +615,13 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
     __syncthreads();
     tc_fence_after();
     if (stopped) continue;
-    const int texels = r.w * r.h;
+    const int texels = pw * ph;
     auto gather = [&](int64_t tl, uint32_t (&w)[16]) {
       const int k = (int)tl * 128 + t;
       float x[16];
       if (k < texels) {
-        const HybAxis& cx = cols[k % r.w];
-        const HybAxis& cy = rows[k / r.w];
+        const HybAxis& cx = cols[k % pw];
+        const HybAxis& cy = rows[k / pw];
         if (staged) {
           const float4 q00 = vol[(cy.v0 - ly) * fw + (cx.v0 - lx)], q10 = vol[(cy.v0 - ly) * fw + (cx.v1 - lx)];
           const float4 q01 = vol[(cy.v1 - ly) * fw + (cx.v0 - lx)], q11 = vol[(cy.v1 - ly) * fw + (cx.v1 - lx)];
@@ -650,7 +665,7 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
     auto emit = [&](int64_t tl, float y0, float y1, float y2) {
       const int k = (int)tl * 128 + t;
       if (k < texels)
-        put_texel(c.phys, c.fmt, (int64_t)(r.dst_y + k / r.w) * c.phys_w + (r.dst_x + k % r.w), y0, y1, y2);
+        put_texel(c.phys, c.fmt, (int64_t)(r.dst_y - b + k / pw) * c.phys_w + (r.dst_x - b + k % pw), y0, y1, y2);
     };
     stopped = !hybrid_lane_run(e, e.wg, kHybLanes, (texels + 127) / 128, gather, emit, inflight[0]);
   }
@@ -768,6 +783,7 @@ struct ndgi_hybrid_table {
   DevHybrid* d_models = nullptr;   // device copy of the descriptors
   int* d_words = nullptr;          // device: error word, debug word
   int n_models = 0, hidden = 0, prec = 0;
+  int border = 0;                  // mirrored tile border of every page (texels per edge)
 };
 
 namespace {
@@ -979,8 +995,17 @@ ndgi_status ndgi_hybrid_decode_pages(ndgi_hybrid_table* table, const ndgi_page_r
   c.fmt = (int)format;
   c.error_word = table->d_words;
   c.debug_word = table->d_words + 1;
+  c.border = table->border;
   return cuda_status(ndgi::launch_hybrid_pages(c, table->hidden, table->prec, reqs, n, (cudaStream_t)stream),
                      "ndgi_hybrid_decode_pages");
+}
+
+ndgi_status ndgi_hybrid_table_set_border(ndgi_hybrid_table* table, int32_t border) {
+  if (!table || border < 0 || border > ndgi::kHybBorderMax)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_table_set_border: bad table or border (0..%d)",
+                     ndgi::kHybBorderMax);
+  table->border = border;
+  return NDGI_OK;
 }
 
 ndgi_status ndgi_hybrid_table_check(ndgi_hybrid_table* table, int32_t* device_error, void* stream) {

@@ -30,6 +30,7 @@ struct HybridPagesCtx {
   int fmt;                   // ndgi_out_format
   int* error_word;           // bit 0 bad request, bit 4 timeout
   const int* debug_word;     // kDbgInjectTimeout
+  int border;                // mirrored tile border (texels per edge), 0..8
 };
 
 }  // namespace ndgi

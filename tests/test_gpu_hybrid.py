@@ -255,3 +255,42 @@ def test_pages_unstaged_volume_and_fractional_uv(ndgi, prec):
     print(f"hybrid pages unstaged {prec}: max|err|/page range = {err:.3e}")
     assert err <= GATE[prec]
     table.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_pages_with_mirrored_border(ndgi, prec):
+    # a 4-texel mirrored border per edge (supplement S3): (w + 8) x (h + 8) texels per request
+    s = synth.hybrid_tile_set(130, 3, "M.64")
+    models = ndgi.HybridModel.from_set(s)
+    ndgi.hybrid_prepare_set(models, prec)
+    table = ndgi.HybridTable(models, prec)
+    table.set_border(4)
+    reqs = ragged_requests(131, 3, 6, 3)
+    reqs["w"] = np.maximum(reqs["w"], 4)
+    reqs["h"] = np.maximum(reqs["h"], 4)
+    reqs["x0"] = np.minimum(reqs["x0"], 128 - reqs["w"])
+    reqs["y0"] = np.minimum(reqs["y0"], 128 - reqs["h"])
+    reqs["dst_x"] = (np.arange(6) % 3) * 144 + 4
+    reqs["dst_y"] = (np.arange(6) // 3) * 144 + 4
+    phys = torch.zeros((2 * 144, 3 * 144, 4), dtype=torch.float32, device="cuda")
+    r, _ = ndgi.page_requests_to_device(reqs)
+    table.decode(r, len(reqs), phys)
+    assert table.check() == (0, 0)
+    maps = [synth.hybrid_tile_of(s, i) for i in range(3)]
+    ref = oracle.hybrid_decode_pages(maps, reqs, 3 * 144, 2 * 144, precision=prec, fill=0.0, border=4)
+    got = phys.cpu().numpy()
+    padded = reqs.copy()
+    padded["dst_x"] -= 4
+    padded["dst_y"] -= 4
+    padded["w"] += 8
+    padded["h"] += 8
+    err = page_err(got, ref, padded)
+    print(f"hybrid pages with border {prec}: max|err|/page range = {err:.3e}")
+    assert err <= GATE[prec]
+    assert np.array_equal(got[..., 3], ref[..., 3])
+    # a request narrower than the border is rejected, the others decode
+    reqs[2]["w"] = 3
+    r, _ = ndgi.page_requests_to_device(reqs)
+    table.decode(r, len(reqs), phys)
+    assert table.check()[1] == 1
+    table.close()

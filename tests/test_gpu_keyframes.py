@@ -42,9 +42,11 @@ def queries(n, seed):
     return q
 
 
-@pytest.mark.parametrize("prec,n", [("fp32", 20_000), ("fp16", 20_000), ("fp16", 300_000)])
-def test_points_with_switch_keyframes(ndgi, prec, n):
-    m = model(120)
+@pytest.mark.parametrize("prec,n,feat", [("fp32", 20_000, 128), ("fp16", 20_000, 128), ("fp16", 300_000, 128),
+                                         ("fp16", 20_000, 1024)])
+def test_points_with_switch_keyframes(ndgi, prec, n, feat):
+    # feat 1024 with 20,000 queries takes the direct tensor-core gather, the others the decoded-texel cache
+    m = model(120, feat=feat, lm=2 * feat)
     mod = ndgi.Model.from_arrays(m)
     q = queries(n, 121)
     got = ndgi.ndgi_decode_points(mod, torch.from_numpy(q).cuda(), prec).cpu().numpy()

@@ -15,7 +15,8 @@ own formula:
   that keep every hidden pre-activation far above zero (GELU = identity to
   FP64 precision, so the network is a plain matrix product), and its
   activation through hidden units whose pre-activation is exactly +-1;
-- the page decode against the point decode at texel centres.
+- the page decode against the point decode at texel centres, and its
+  mirrored tile border against NumPy's symmetric padding of the interior.
 """
 import numpy as np
 import pytest
@@ -199,3 +200,19 @@ def test_pages_equal_points_at_texel_centres():
         assert np.all(got[sl][..., 3] == 1.0)
         covered[sl] = True
     assert np.all(np.isnan(got[~covered]))
+
+
+@pytest.mark.parametrize("b", [1, 4])
+def test_page_border_is_symmetric_padding(b):
+    models = [synth.hybrid_model(29, 64, 64, 64, 64, 16, 16, 6, 20, 9, 28, 7, 16)]
+    reqs = np.zeros(2, dtype=synth.PAGE_REQ_DTYPE)
+    reqs[0] = (0, 3, 7, 20, 13, np.float32(0.4), b, b)
+    reqs[1] = (0, 40, 50, 24, 14, np.float32(0.8), 40 + b, b)
+    W, H = 80, 24
+    plain = oracle.hybrid_decode_pages(models, reqs, W, H, fill=0.0)
+    padded = oracle.hybrid_decode_pages(models, reqs, W, H, fill=0.0, border=b)
+    for r in reqs:
+        inner = plain[r["dst_y"]:r["dst_y"] + r["h"], r["dst_x"]:r["dst_x"] + r["w"]]
+        want = np.pad(inner, ((b, b), (b, b), (0, 0)), mode="symmetric")
+        got = padded[r["dst_y"] - b:r["dst_y"] + r["h"] + b, r["dst_x"] - b:r["dst_x"] + r["w"] + b]
+        assert np.array_equal(got, want)
