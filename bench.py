@@ -40,14 +40,17 @@ METRIC = "Gtexels/s decoded (BC fetch+temporal lerp+MLP), FP16-TC vs FP32 plain 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of a smaller case
 # of the same kernel, scaled to a full launch by the units processed.  Valid only while the kernel sources are
 # the ones captured: the hash below is compared at run time and the figure drops to null once they change.
-TRAFFIC_SOURCES = ("tc_decode.cu", "tc_points.cu", "tc_engine.cuh", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h")
+TRAFFIC_SOURCES = ("tc_decode.cu", "tc_points.cu", "tc_engine.cuh", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h",
+                   "hybrid.cu", "hybrid.h")
 NCU_TRAFFIC = {
-    "k_points_ws": {"src": "bd4dd243d8b953d9", "read": 134403328, "write": 81934080, "units": 1 << 23,
+    "k_points_ws": {"src": "35a0c4ee7c58d1e9", "read": 134407936, "write": 81475584, "units": 1 << 23,
                     "profile": "profiles/k_points_ws_points_2048_atlas.md"},
-    "k_pages_tc": {"src": "bd4dd243d8b953d9", "read": 19511808, "write": 75702016, "units": 1024 * 128 * 128,
+    "k_pages_tc": {"src": "35a0c4ee7c58d1e9", "read": 19674624, "write": 75905280, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_tc_pages_8_lightmaps.md"},
-    "k_pages_ws": {"src": "bd4dd243d8b953d9", "read": 19168000, "write": 76241152, "units": 1024 * 128 * 128,
+    "k_pages_ws": {"src": "35a0c4ee7c58d1e9", "read": 19192576, "write": 76340736, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_ws_pages_8_lightmaps.md"},
+    "k_hybrid_pages_tc": {"src": "35a0c4ee7c58d1e9", "read": 188086272, "write": 477627904, "units": 4096 * 128 * 128,
+                          "profile": "profiles/k_hybrid_pages_tc_m64_4096_tiles.md"},
 }
 
 
@@ -609,7 +612,7 @@ def bench_hybrid(args, ndgi, torch, peaks, peak_kind, timed, rank):
     out["roofline"] = two_term_roofline(texels, HYBRID_FLOP_PER_TEXEL, hybrid_frame_bytes(len(reqs), touched,
                                         model_bytes), out["fp16"]["ms_per_frame"] * 1e-3, peaks, peak_kind)
     out["roofline"].update({"kernel": "k_hybrid_pages_tc", "flop_per_texel": HYBRID_FLOP_PER_TEXEL,
-                            "models_touched": touched})
+                            "models_touched": touched, "traffic": traffic_for("k_hybrid_pages_tc", texels)})
     out["vs_fp32_plain"] = out["fp16"]["value"] / out["fp32"]["value"]
     del phys
     torch.cuda.empty_cache()
