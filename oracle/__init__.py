@@ -107,6 +107,9 @@ def lib():
             L.om_hybrid_decode_points.argtypes = [vp, vp, i64, vp, vp, C.c_int]
             L.om_hybrid_decode_pages.argtypes = [vp, i32, vp, i32, vp, i64, i64, i32, C.c_int]
             L.om_tile_metrics.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
+            L.om_hfit_forward.argtypes = [vp, vp, i64, C.c_int, vp]
+            L.om_hfit_backward.argtypes = [vp, vp, vp, i64, C.c_int, vp]
+            L.om_hfit_backward.restype = f64
             L.om_splitmix64_next.argtypes = [C.c_uint64]
             L.om_splitmix64_next.restype = C.c_uint64
             _lib = L
@@ -478,3 +481,53 @@ def tile_metrics(pred, ref, mask=None, tile=128):
     ss = np.zeros((n, ty, tx), np.float64)
     lib().om_tile_metrics(_ptr(p), _ptr(q), _ptr(m), n, h, w, c, tile, _ptr(ps), _ptr(ss))
     return ps, ss
+
+
+# --------------------------------------------------------------------------
+# Fit of the hybrid decoder
+# --------------------------------------------------------------------------
+
+HFIT_KEYS = ("uv_ea", "uv_eb", "uv_wt", "vol_ea", "vol_eb", "vol_wt", "ut", "vt", "w1", "b1", "w2", "b2", "w3", "b3")
+
+
+class _HFitParams(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("lm_w", "lm_h", "uv_w", "uv_h", "vol_w", "vol_h", "vol_t", "ut_w", "ut_t",
+                                         "vt_h", "vt_t", "hidden", "address_mode")] + \
+               [(k, C.c_void_p) for k in HFIT_KEYS]
+
+
+class _HFitGrads(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in HFIT_KEYS]
+
+
+class HFitParams:
+    """Hybrid-fit parameters (dict from synth.hybrid_fit_init) in oracle form."""
+
+    def __init__(self, p):
+        self.a = {k: _c(p[k], np.float32) for k in HFIT_KEYS}
+        vt_, vh, vw = (int(d) for d in p["vol_shape"])
+        ut_t, ut_w, _ = self.a["ut"].shape
+        vt_t, vt_h, _ = self.a["vt"].shape
+        self.s = _HFitParams(int(p["lm_w"]), int(p["lm_h"]), int(p["uv_w"]), int(p["uv_h"]), vw, vh, vt_, ut_w, ut_t,
+                             vt_h, vt_t, int(p["hidden"]), int(p.get("address_mode", 0)),
+                             *[_ptr(self.a[k]) for k in HFIT_KEYS])
+
+
+def hfit_forward(p, uvt, relaxed=False):
+    """rgb [n][3] of the hybrid fit's straight-through (or relaxed) forward at queries uvt [n][3]."""
+    P = p if isinstance(p, HFitParams) else HFitParams(p)
+    q = _c(uvt, np.float32).reshape(-1, 3)
+    y = np.zeros((q.shape[0], 3), np.float64)
+    lib().om_hfit_forward(C.byref(P.s), _ptr(q), q.shape[0], int(relaxed), _ptr(y))
+    return y
+
+
+def hfit_backward(p, uvt, target, relaxed=False):
+    """(loss, gradients dict) of the MSE at queries uvt against target [n][3] (FP64)."""
+    P = p if isinstance(p, HFitParams) else HFitParams(p)
+    q = _c(uvt, np.float32).reshape(-1, 3)
+    tg = _c(target, np.float64).reshape(-1, 3)
+    g = {k: np.zeros(P.a[k].shape, np.float64) for k in HFIT_KEYS}
+    G = _HFitGrads(*[_ptr(g[k]) for k in HFIT_KEYS])
+    loss = lib().om_hfit_backward(C.byref(P.s), _ptr(q), _ptr(tg), q.shape[0], int(relaxed), C.byref(G))
+    return loss, g

@@ -1000,3 +1000,224 @@ void om_tile_metrics(const double *pred, const double *ref, const uint8_t *mask,
     }
   }
 }
+
+/* ---------------------------------------------------------------------- */
+/* Fit of the hybrid decoder (Sec. 3.4 with the decoder of Sec. 3.3)       */
+/* ---------------------------------------------------------------------- */
+/*
+ * Parameters: the BC-simulated maps F_uv and F3D as endpoints (ea, eb) per
+ * block and channel and a weight per texel, Eq. 6-7, with the straight-
+ * through quantisers of the simple fit (om_sim_value: A = q255(ea), B =
+ * q255(eb), k = q7(w), value P35/8925); F_ut and F_vt as continuous values
+ * (UNORM8 after training); the MLP.  The forward is the hybrid decode
+ * (om_hybrid_features, om_hybrid_mlp) on those values.  Reading: no additive
+ * noise (the paper's quantisation noise during training is a regulariser this
+ * deterministic fit leaves out).
+ */
+typedef struct {
+  int32_t lm_w, lm_h, uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, vt_h, vt_t, hidden, address_mode;
+  const float *uv_ea, *uv_eb, *uv_wt;       /* [uv_h/4][uv_w/4][4], same, [..][4][16]           */
+  const float *vol_ea, *vol_eb, *vol_wt;    /* [vol_t][vol_h/4][vol_w/4][4], same, [..][4][16]  */
+  const float *ut, *vt;                     /* [ut_t][ut_w][2], [vt_t][vt_h][2]                   */
+  const float *w1, *b1, *w2, *b2, *w3, *b3;
+} om_hfit_params;
+
+typedef struct {
+  double *uv_ea, *uv_eb, *uv_wt, *vol_ea, *vol_eb, *vol_wt, *ut, *vt, *w1, *b1, *w2, *b2, *w3, *b3;
+} om_hfit_grads;
+
+/* STE value of texel p of block entry bc (channel included) and its chain-rule factors. */
+static double om_hsim(const float *ea, const float *eb, const float *w, int64_t bc, int p, int relaxed,
+                      double *dea, double *deb, double *dw) {
+  const float a = ea[bc], b = eb[bc], ww = w[bc * 16 + p];
+  if (relaxed) {
+    *dea = 1.0 - (double)ww;
+    *deb = (double)ww;
+    *dw = (double)b - (double)a;
+    return (1.0 - (double)ww) * a + (double)ww * b;
+  }
+  const int A = om_q255(a), B = om_q255(b), k = om_q7(ww);
+  *dea = 1.0 - k / 7.0;
+  *deb = k / 7.0;
+  *dw = B / 255.0 - A / 255.0;
+  return (double)om_p35_value(5 * ((7 - k) * A + k * B));
+}
+
+/* The taps of one sample: for each feature input k, up to 8 (map, entry, texel, weight) contributions. */
+typedef struct {
+  int map;        /* 0 F3D, 1 F_uv, 2 F_ut, 3 F_vt */
+  int64_t e;      /* BC entry (block * 4 + channel) or value index */
+  int p;          /* texel in the block (BC maps) */
+  double wt;      /* interpolation weight */
+} om_htap;
+
+static int om_hfit_taps(const om_hfit_params *P, double u, double v, double t, om_htap tap[16][8], int cnt[16]) {
+  int x0, x1, y0, y1, z0, z1;
+  double fx, fy, fz;
+  for (int k = 0; k < 16; ++k) cnt[k] = 0;
+  /* F3D: trilinear over the two slices around t */
+  om_bilinear_setup(u, P->vol_w, P->address_mode, &x0, &x1, &fx);
+  om_bilinear_setup(v, P->vol_h, P->address_mode, &y0, &y1, &fy);
+  om_bilinear_setup(t, P->vol_t, 0, &z0, &z1, &fz);
+  const int tx[4] = {x0, x1, x0, x1}, ty[4] = {y0, y0, y1, y1};
+  const double wb[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+  const int64_t bws = P->vol_w / 4, nbs = (int64_t)(P->vol_h / 4) * bws;
+  for (int c = 0; c < 4; ++c)
+    for (int zz = 0; zz < 2; ++zz)
+      for (int q = 0; q < 4; ++q) {
+        om_htap *h = &tap[c][cnt[c]++];
+        h->map = 0;
+        h->e = (((zz ? z1 : z0) * nbs + (int64_t)(ty[q] >> 2) * bws + (tx[q] >> 2)) * 4 + c);
+        h->p = (ty[q] & 3) * 4 + (tx[q] & 3);
+        h->wt = (zz ? fz : 1 - fz) * wb[q];
+      }
+  /* F_uv: bilinear */
+  om_bilinear_setup(u, P->uv_w, P->address_mode, &x0, &x1, &fx);
+  om_bilinear_setup(v, P->uv_h, P->address_mode, &y0, &y1, &fy);
+  const int ux[4] = {x0, x1, x0, x1}, uy[4] = {y0, y0, y1, y1};
+  const double wu[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+  const int64_t bwu = P->uv_w / 4;
+  for (int c = 0; c < 4; ++c)
+    for (int q = 0; q < 4; ++q) {
+      om_htap *h = &tap[4 + c][cnt[4 + c]++];
+      h->map = 1;
+      h->e = ((int64_t)(uy[q] >> 2) * bwu + (ux[q] >> 2)) * 4 + c;
+      h->p = (uy[q] & 3) * 4 + (ux[q] & 3);
+      h->wt = wu[q];
+    }
+  /* F_ut at (u, t), F_vt at (v, t): bilinear over continuous values */
+  for (int pl = 0; pl < 2; ++pl) {
+    const int nx = pl ? P->vt_h : P->ut_w, nt = pl ? P->vt_t : P->ut_t;
+    om_bilinear_setup(pl ? v : u, nx, P->address_mode, &x0, &x1, &fx);
+    om_bilinear_setup(t, nt, 0, &y0, &y1, &fy);
+    const int px[4] = {x0, x1, x0, x1}, py[4] = {y0, y0, y1, y1};
+    const double wp[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+    for (int c = 0; c < 2; ++c)
+      for (int q = 0; q < 4; ++q) {
+        om_htap *h = &tap[8 + 2 * pl + c][cnt[8 + 2 * pl + c]++];
+        h->map = 2 + pl;
+        h->e = ((int64_t)py[q] * nx + px[q]) * 2 + c;
+        h->p = 0;
+        h->wt = wp[q];
+      }
+  }
+  return 0;
+}
+
+static double om_htap_value(const om_hfit_params *P, const om_htap *h, int relaxed, double *d0, double *d1,
+                            double *d2) {
+  if (h->map == 0) return om_hsim(P->vol_ea, P->vol_eb, P->vol_wt, h->e, h->p, relaxed, d0, d1, d2);
+  if (h->map == 1) return om_hsim(P->uv_ea, P->uv_eb, P->uv_wt, h->e, h->p, relaxed, d0, d1, d2);
+  *d0 = 1.0;
+  return (double)(h->map == 2 ? P->ut : P->vt)[h->e];
+}
+
+/* One sample's forward: inputs x[16], pre-activations, activations, RGB. */
+static void om_hfit_sample(const om_hfit_params *P, double u, double v, double t, int relaxed, double *x,
+                           double *z1, double *h1, double *z2, double *h2, double *y) {
+  om_htap tap[16][8];
+  int cnt[16];
+  om_hfit_taps(P, u, v, t, tap, cnt);
+  for (int k = 0; k < 12; ++k) {
+    double acc = 0.0, d0, d1, d2;
+    for (int i = 0; i < cnt[k]; ++i) acc += tap[k][i].wt * om_htap_value(P, &tap[k][i], relaxed, &d0, &d1, &d2);
+    x[k] = acc;
+  }
+  om_hybrid_gamma(t, x + 12);
+  const int H = P->hidden;
+  for (int o = 0; o < H; ++o) {
+    double z = P->b1[o];
+    for (int i = 0; i < 16; ++i) z += x[i] * (double)P->w1[(size_t)i * H + o];
+    z1[o] = z;
+    h1[o] = om_gelu(z);
+  }
+  for (int o = 0; o < H; ++o) {
+    double z = P->b2[o];
+    for (int i = 0; i < H; ++i) z += h1[i] * (double)P->w2[(size_t)i * H + o];
+    z2[o] = z;
+    h2[o] = om_gelu(z);
+  }
+  for (int o = 0; o < 3; ++o) {
+    double z = P->b3[o];
+    for (int i = 0; i < H; ++i) z += h2[i] * (double)P->w3[(size_t)i * 3 + o];
+    y[o] = z;
+  }
+}
+
+/* d GELU / dz = Phi(z) + z phi(z). */
+static double om_gelu_grad(double z) {
+  return 0.5 * (1.0 + erf(z / sqrt(2.0))) + z * exp(-0.5 * z * z) / sqrt(2.0 * 3.14159265358979323846);
+}
+
+void om_hfit_forward(const om_hfit_params *P, const float *uvt, int64_t n, int relaxed, double *rgb) {
+  for (int64_t s = 0; s < n; ++s) {
+    double x[16], z1[256], h1[256], z2[256], h2[256];
+    om_hfit_sample(P, uvt[3 * s], uvt[3 * s + 1], uvt[3 * s + 2], relaxed, x, z1, h1, z2, h2, rgb + 3 * s);
+  }
+}
+
+/* Analytic FP64 gradient of the MSE (accumulated into G; callers zero it); returns the loss. */
+double om_hfit_backward(const om_hfit_params *P, const float *uvt, const double *target, int64_t n, int relaxed,
+                        om_hfit_grads *G) {
+  const int H = P->hidden;
+  double loss = 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    const double u = uvt[3 * s], v = uvt[3 * s + 1], t = uvt[3 * s + 2];
+    double x[16], z1[256], h1[256], z2[256], h2[256], y[3], dy[3], gz2[256], gz1[256], gx[16];
+    om_hfit_sample(P, u, v, t, relaxed, x, z1, h1, z2, h2, y);
+    for (int o = 0; o < 3; ++o) {
+      const double d = y[o] - target[3 * s + o];
+      loss += d * d;
+      dy[o] = 2.0 * d / (3.0 * (double)n);
+      G->b3[o] += dy[o];
+    }
+    for (int i = 0; i < H; ++i) {
+      double acc = 0.0;
+      for (int o = 0; o < 3; ++o) {
+        G->w3[(size_t)i * 3 + o] += h2[i] * dy[o];
+        acc += (double)P->w3[(size_t)i * 3 + o] * dy[o];
+      }
+      gz2[i] = acc * om_gelu_grad(z2[i]);
+    }
+    for (int o = 0; o < H; ++o) G->b2[o] += gz2[o];
+    for (int i = 0; i < H; ++i) {
+      double acc = 0.0;
+      for (int o = 0; o < H; ++o) {
+        G->w2[(size_t)i * H + o] += h1[i] * gz2[o];
+        acc += (double)P->w2[(size_t)i * H + o] * gz2[o];
+      }
+      gz1[i] = acc * om_gelu_grad(z1[i]);
+    }
+    for (int o = 0; o < H; ++o) G->b1[o] += gz1[o];
+    for (int i = 0; i < 16; ++i) {
+      double acc = 0.0;
+      for (int o = 0; o < H; ++o) {
+        G->w1[(size_t)i * H + o] += x[i] * gz1[o];
+        acc += (double)P->w1[(size_t)i * H + o] * gz1[o];
+      }
+      gx[i] = acc;
+    }
+    om_htap tap[16][8];
+    int cnt[16];
+    om_hfit_taps(P, u, v, t, tap, cnt);
+    for (int k = 0; k < 12; ++k)
+      for (int i = 0; i < cnt[k]; ++i) {
+        const om_htap *h = &tap[k][i];
+        double d0, d1, d2;
+        om_htap_value(P, h, relaxed, &d0, &d1, &d2);
+        const double g = h->wt * gx[k];
+        if (h->map == 0) {
+          G->vol_ea[h->e] += d0 * g;
+          G->vol_eb[h->e] += d1 * g;
+          G->vol_wt[h->e * 16 + h->p] += d2 * g;
+        } else if (h->map == 1) {
+          G->uv_ea[h->e] += d0 * g;
+          G->uv_eb[h->e] += d1 * g;
+          G->uv_wt[h->e * 16 + h->p] += d2 * g;
+        } else {
+          (h->map == 2 ? G->ut : G->vt)[h->e] += g;
+        }
+      }
+  }
+  return loss / (3.0 * (double)n);
+}

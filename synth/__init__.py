@@ -370,3 +370,22 @@ def lightmap_mask(seed, width, height, n_islands=12, fill=0.7):
         x, y = int(rng.integers(0, width - w)), int(rng.integers(0, height - h))
         m[y:y + h, x:x + w] = 1
     return m
+
+
+
+def hybrid_fit_init(seed, lm_w, lm_h, uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, vt_h, vt_t, hidden,
+                    address_mode=0):
+    """Initial parameters of a hybrid-decoder fit: endpoints and weights U(0,1) per block and channel of F_uv
+    and of every F3D slice, F_ut / F_vt values U(0,1), Xavier MLP 16 -> hidden -> hidden -> 3."""
+    rng = _rng(seed)
+    ubh, ubw, vbh, vbw = uv_h // 4, uv_w // 4, vol_h // 4, vol_w // 4
+    p = dict(lm_w=lm_w, lm_h=lm_h, uv_w=uv_w, uv_h=uv_h, vol_shape=(vol_t, vol_h, vol_w), hidden=hidden,
+             address_mode=address_mode,
+             uv_ea=rng.random((ubh, ubw, 4), dtype=np.float32), uv_eb=rng.random((ubh, ubw, 4), dtype=np.float32),
+             uv_wt=rng.random((ubh, ubw, 4, 16), dtype=np.float32),
+             vol_ea=rng.random((vol_t, vbh, vbw, 4), dtype=np.float32),
+             vol_eb=rng.random((vol_t, vbh, vbw, 4), dtype=np.float32),
+             vol_wt=rng.random((vol_t, vbh, vbw, 4, 16), dtype=np.float32),
+             ut=rng.random((ut_t, ut_w, 2), dtype=np.float32), vt=rng.random((vt_t, vt_h, 2), dtype=np.float32))
+    p.update(xavier_mlp(rng, 16, hidden, 3))
+    return p

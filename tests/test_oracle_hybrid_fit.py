@@ -1,0 +1,69 @@
+"""Pins of the oracle's hybrid-decoder fit (Sec. 3.4's BC simulation, Eq. 6-7,
+applied to the decoder of Sec. 3.3):
+
+- the straight-through forward equals the pinned hybrid decode of the same
+  model with F_uv and every F3D slice packed to BC4 (decode of pack = the
+  forward), on F_ut / F_vt values that UNORM8 stores exactly;
+- the analytic gradient matches FP64 central finite differences of the
+  continuous relaxation (GELU is smooth, so no kink handling), norm-wise per
+  tensor and elementwise with a 1e-6 floor.
+"""
+import numpy as np
+
+import oracle
+import synth
+
+KEYS = oracle.HFIT_KEYS
+
+
+def problem(seed=0, hidden=16):
+    p = synth.hybrid_fit_init(seed, 32, 32, 32, 32, 8, 8, 6, 16, 5, 16, 5, hidden)
+    rng = np.random.default_rng(seed + 1)
+    q = synth.random_queries(seed + 2, 300)
+    q[:10, :2] = rng.uniform(-0.3, 1.3, (10, 2)).astype(np.float32)
+    tgt = rng.normal(size=(300, 3))
+    return p, q, tgt
+
+
+def test_forward_equals_decode_of_packed_model():
+    p, q, _ = problem(1)
+    p["ut"] = (np.round(p["ut"] * 255) / 255).astype(np.float32)
+    p["vt"] = (np.round(p["vt"] * 255) / 255).astype(np.float32)
+    vt_, vh, vw = p["vol_shape"]
+    m = dict(kind="hybrid", lm_w=32, lm_h=32, uv_w=32, uv_h=32, vol_shape=p["vol_shape"], hidden=p["hidden"],
+             address_mode=0,
+             uv_bc4=oracle.bc_pack(p["uv_ea"], p["uv_eb"], p["uv_wt"]),
+             vol_bc4=np.stack([oracle.bc_pack(p["vol_ea"][k], p["vol_eb"][k], p["vol_wt"][k]) for k in range(vt_)]),
+             ut=np.round(p["ut"] * 255).astype(np.uint8), vt=np.round(p["vt"] * 255).astype(np.uint8),
+             **{k: p[k] for k in ("w1", "b1", "w2", "b2", "w3", "b3")})
+    y_fit = oracle.hfit_forward(p, q)
+    y_dec = oracle.hybrid_decode_points(m, q)
+    # equal up to the FP32 storage of the 8-bit values k/255 in the fit (a few 1e-8)
+    assert np.allclose(y_fit, y_dec, rtol=0, atol=1e-6)
+    assert not np.allclose(y_fit, oracle.hfit_forward(p, q, relaxed=True), atol=1e-6)   # the quantisers act
+
+
+def test_backward_matches_finite_differences_relaxed():
+    p, q, tgt = problem(3)
+    loss, g = oracle.hfit_backward(p, q, tgt, relaxed=True)
+    rng = np.random.default_rng(4)
+    h = 1e-3
+
+    def loss_at(k, i, val):
+        pp = dict(p)
+        arr = p[k].copy().reshape(-1)
+        arr[i] = val
+        pp[k] = arr.reshape(p[k].shape)
+        return np.mean((oracle.hfit_forward(pp, q, relaxed=True) - tgt) ** 2), float(arr[i])
+
+    for k in KEYS:
+        flat = p[k].reshape(-1)
+        idx = rng.choice(flat.size, min(flat.size, 12), replace=False)
+        fd = np.zeros(idx.size)
+        for j, i in enumerate(idx):
+            lp, vp = loss_at(k, i, np.float32(float(flat[i]) + h))
+            lm, vm = loss_at(k, i, np.float32(float(flat[i]) - h))
+            fd[j] = (lp - lm) / (vp - vm)                       # the realised FP32 step
+        an = g[k].reshape(-1)[idx]
+        assert np.linalg.norm(an - fd) <= 2e-3 * max(np.linalg.norm(an), 1e-9), k
+        assert np.all(np.abs(an - fd) <= 2e-3 * np.abs(an) + 1e-6), k
