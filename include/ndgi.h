@@ -726,6 +726,67 @@ double ndgi_model_bpp(const ndgi_hybrid_desc *model, int32_t n_lightmaps, int32_
                       int32_t mlp_bits);
 
 /* ======================================================================
+ * Fit of the hybrid decoder (Sec. 3.4's BC simulation applied to the
+ * decoder of Sec. 3.3; Sec. 4 training)
+ * ====================================================================== */
+
+/*
+ * Trainable parameters of one hybrid model (FP32, device, row-major):
+ *   uv_ea, uv_eb [uv_h/4][uv_w/4][4], uv_wt [uv_h/4][uv_w/4][4][16]   F_uv as BC
+ *       endpoints per block and channel and a weight per texel (Eq. 6-7);
+ *   vol_ea, vol_eb [vol_t][vol_h/4][vol_w/4][4], vol_wt [..][4][16]    F3D likewise;
+ *   ut [ut_t][ut_w][2], vt [vt_t][vt_h][2]                             F_ut, F_vt values;
+ *   w1 [16][hidden], b1, w2 [hidden][hidden], b2, w3 [hidden][3], b3   the MLP.
+ * The forward is the hybrid decode with F_uv and F3D read through the
+ * straight-through quantisers of ndgi_fit_forward (A = q255(ea), B =
+ * q255(eb), k = q7(w), value P35 / 8925; relaxed = 1: (1 - w) ea + w eb) and
+ * F_ut / F_vt used as given; GELU(x) = x Phi(x) in FP32 (CUDA's erff).
+ * Pack a result with ndgi_bc_pack (cs = 4; per F3D slice) and round F_ut /
+ * F_vt to UNORM8.  hidden 16, 32 or 64.
+ */
+typedef struct {
+  int32_t lm_w, lm_h;
+  int32_t uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, vt_h, vt_t;
+  int32_t hidden, address_mode;
+  float *uv_ea, *uv_eb, *uv_wt, *vol_ea, *vol_eb, *vol_wt, *ut, *vt, *w1, *b1, *w2, *b2, *w3, *b3;
+} ndgi_hybrid_fit_params;
+
+/* Gradient buffers in ndgi_hybrid_fit_params' tensor order (FP32, device). */
+typedef struct {
+  float *g[14];
+} ndgi_hybrid_fit_grads;
+
+/* rgb [n][3] of the forward at queries uvt [n][3] (device). */
+ndgi_status ndgi_hybrid_fit_forward(const ndgi_hybrid_fit_params *params, const float *uvt, int64_t n,
+                                    int32_t relaxed, float *rgb, void *stream);
+
+/*
+ * Given dL/drgb [n][3], ADDS dL/dparam into *grads (caller zeroes them):
+ * through the MLP (GELU'(z) = Phi(z) + z phi(z)), the trilinear F3D, the
+ * bilinear F_uv / F_ut / F_vt samples and the straight-through quantisers
+ * (dL/dea += (1 - q(w)) g, dL/deb += q(w) g, dL/dw += (q(eb) - q(ea)) g).
+ * FP32 atomics: results vary in the last bits.
+ */
+ndgi_status ndgi_hybrid_fit_backward(const ndgi_hybrid_fit_params *params, const float *uvt, int64_t n,
+                                     int32_t relaxed, const float *grad_rgb, const ndgi_hybrid_fit_grads *grads,
+                                     void *stream);
+
+/*
+ * Runs cfg->steps Adam steps of the L2 fit of a hybrid model on device, as
+ * ndgi_encode_fit: cfg->batch samples per step drawn with the same
+ * counter-based generator (texel and t), targets [t_count][lm_h][lm_w][3]
+ * FP16 (device) at the keyframe times (key_t, device, or NULL for j /
+ * t_count) interpolated linearly at t, the feature maps projected onto
+ * [0, 1] and frozen for the last cfg->freeze_steps steps (the final stage
+ * fine-tunes the MLP alone, Sec. 4).  ws: ndgi_hybrid_encode_fit_workspace_size
+ * bytes (Adam moments; keep it to resume with step_offset).
+ */
+size_t ndgi_hybrid_encode_fit_workspace_size(const ndgi_hybrid_fit_params *params, const ndgi_fit_config *cfg);
+ndgi_status ndgi_hybrid_encode_fit(const ndgi_hybrid_fit_params *params, const uint16_t *targets, int32_t t_count,
+                                   const float *key_t, const ndgi_fit_config *cfg, int32_t step_offset, void *ws,
+                                   size_t ws_bytes, double *loss_log, void *stream);
+
+/* ======================================================================
  * Quality metrics (supplement S4.2)
  * ====================================================================== */
 

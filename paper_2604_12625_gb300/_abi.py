@@ -42,6 +42,20 @@ class HybridDesc(C.Structure):
                 ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
 
 
+HFIT_TENSORS = ("uv_ea", "uv_eb", "uv_wt", "vol_ea", "vol_eb", "vol_wt", "ut", "vt", "w1", "b1", "w2", "b2", "w3",
+                "b3")
+
+
+class HybridFitParams(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("lm_w", "lm_h", "uv_w", "uv_h", "vol_w", "vol_h", "vol_t", "ut_w", "ut_t",
+                                         "vt_h", "vt_t", "hidden", "address_mode")] + \
+               [(k, C.c_void_p) for k in HFIT_TENSORS]
+
+
+class HybridFitGrads(C.Structure):
+    _fields_ = [("g", C.c_void_p * 14)]
+
+
 FIT_TENSORS = ("ea", "eb", "w", "temporal", "w1", "b1", "w2", "b2", "w3", "b3")
 
 
@@ -114,6 +128,10 @@ SIGNATURES = [
     ("ndgi_debug_gelu", C.c_int, [_vp, _i64, _vp, _i32, _vp]),
     ("ndgi_model_bpp", C.c_double, [_vp, _i32, _i32, _i32]),
     ("ndgi_tile_metrics", C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp]),
+    ("ndgi_hybrid_fit_forward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
+    ("ndgi_hybrid_fit_backward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),
+    ("ndgi_hybrid_encode_fit_workspace_size", _sz, [_vp, _vp]),
+    ("ndgi_hybrid_encode_fit", C.c_int, [_vp, _vp, _i32, _vp, _vp, _i32, _vp, _sz, _vp, _vp]),
 ]
 
 _lib = None

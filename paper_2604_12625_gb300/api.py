@@ -713,3 +713,67 @@ def ndgi_encode_fit_batch(batch, targets, cfg, step_offset=0, ws=None, loss_log=
     check(lib().ndgi_encode_fit_batch(C.byref(batch.params), batch.n_models, _p(targets), C.byref(cfg),
                                       int(step_offset), _p(ws), ws.numel(), _p(loss_log), _stream(stream)))
     return ws, loss_log
+
+
+# ---------------------------------------------------------------------------
+# Fit of the hybrid decoder
+# ---------------------------------------------------------------------------
+class HybridFitState:
+    """Trainable parameters of a hybrid model (float32 CUDA tensors keyed by HFIT_TENSORS) and their struct."""
+
+    def __init__(self, tensors, lm_w, lm_h, address_mode=0):
+        self.t = {k: _need(tensors[k], torch.float32, k) for k in A.HFIT_TENSORS}
+        ubh, ubw, four = self.t["uv_ea"].shape
+        vt_, vbh, vbw, four = self.t["vol_ea"].shape
+        ut_t, ut_w, _ = self.t["ut"].shape
+        vt_t, vt_h, _ = self.t["vt"].shape
+        self.hidden = int(self.t["w2"].shape[0])
+        self.lm_w, self.lm_h = int(lm_w), int(lm_h)
+        self.params = A.HybridFitParams(self.lm_w, self.lm_h, ubw * 4, ubh * 4, vbw * 4, vbh * 4, vt_, ut_w, ut_t,
+                                        vt_h, vt_t, self.hidden, int(address_mode),
+                                        *[self.t[k].data_ptr() for k in A.HFIT_TENSORS])
+
+    @classmethod
+    def from_arrays(cls, p, device="cuda"):
+        """From a dict of numpy arrays (synth.hybrid_fit_init)."""
+        return cls({k: torch.from_numpy(np.ascontiguousarray(p[k], np.float32)).to(device) for k in A.HFIT_TENSORS},
+                   p["lm_w"], p["lm_h"], p.get("address_mode", 0))
+
+
+def ndgi_hybrid_fit_forward(state, uvt, relaxed=False, out=None, stream=None):
+    """rgb [n][3] of the hybrid fit's straight-through (or relaxed) forward at queries uvt [n][3] float32."""
+    _need(uvt, torch.float32, "uvt")
+    n = uvt.shape[0]
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=uvt.device)
+    check(lib().ndgi_hybrid_fit_forward(C.byref(state.params), _p(uvt), n, int(relaxed), _p(out), _stream(stream)))
+    return out
+
+
+def ndgi_hybrid_fit_backward(state, uvt, grad_rgb, grads=None, relaxed=False, stream=None):
+    """Gradients (dict of float32 tensors) of the loss whose dL/drgb is grad_rgb [n][3]; accumulated into grads
+    when given (zeroed buffers are allocated otherwise)."""
+    _need(uvt, torch.float32, "uvt")
+    _need(grad_rgb, torch.float32, "grad_rgb")
+    if grads is None:
+        grads = {k: torch.zeros_like(v) for k, v in state.t.items()}
+    gs = A.HybridFitGrads((C.c_void_p * 14)(*[grads[k].data_ptr() for k in A.HFIT_TENSORS]))
+    check(lib().ndgi_hybrid_fit_backward(C.byref(state.params), _p(uvt), uvt.shape[0], int(relaxed), _p(grad_rgb),
+                                         C.byref(gs), _stream(stream)))
+    return grads
+
+
+def ndgi_hybrid_encode_fit(state, targets, cfg, key_t=None, step_offset=0, ws=None, loss_log=None, stream=None):
+    """cfg.steps Adam steps of the hybrid fit in place on state's tensors.  targets: float16 [T][lm_h][lm_w][3]
+    CUDA at the keyframe times key_t (float32 CUDA [T]) or j / T.  Returns (ws, loss_log)."""
+    _need(targets, torch.float16, "targets")
+    n = int(lib().ndgi_hybrid_encode_fit_workspace_size(C.byref(state.params), C.byref(cfg)))
+    if ws is None:
+        ws = torch.empty(n, dtype=torch.uint8, device=targets.device)
+    if loss_log is None and cfg.loss_every > 0:
+        loss_log = torch.zeros((cfg.steps + cfg.loss_every - 1) // cfg.loss_every, dtype=torch.float64,
+                               device=targets.device)
+    check(lib().ndgi_hybrid_encode_fit(C.byref(state.params), _p(targets), int(targets.shape[0]), _p(key_t),
+                                       C.byref(cfg), int(step_offset), _p(ws), ws.numel(), _p(loss_log),
+                                       _stream(stream)))
+    return ws, loss_log

@@ -1,0 +1,121 @@
+"""GPU parity of the hybrid decoder's fit (Sec. 3.4's BC simulation applied to
+the decoder of Sec. 3.3) against the FP64 oracle (pinned against finite
+differences and the packed-model decode):
+
+- forward, straight-through and relaxed: <= 1e-5 of range;
+- backward: norm-wise relative error per tensor <= 1e-3, and elementwise
+  within 1e-3 of the tensor's largest gradient;
+- three Adam steps of the device loop against the oracle's loop on the same
+  sample stream and interpolated targets; a longer fit reduces the loss and
+  keeps the feature maps in [0, 1];
+- the decode of the trained model packed to BC4 / UNORM8 equals the fit's
+  straight-through forward.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _gpu import rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KEYS = oracle.HFIT_KEYS
+
+
+@pytest.fixture(scope="module")
+def ndgi():
+    import paper_2604_12625_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def params(seed, hidden=64):
+    return synth.hybrid_fit_init(seed, 64, 64, 64, 64, 16, 16, 6, 32, 8, 32, 8, hidden)
+
+
+@pytest.mark.parametrize("relaxed", [False, True])
+@pytest.mark.parametrize("hidden", [16, 64])
+def test_forward_matches_oracle(ndgi, relaxed, hidden):
+    p = params(1, hidden)
+    q = synth.random_queries(2, 20_000)
+    q[:2000, :2] = np.random.default_rng(3).uniform(-0.5, 1.5, (2000, 2)).astype(np.float32)
+    st = ndgi.HybridFitState.from_arrays(p)
+    y = ndgi.ndgi_hybrid_fit_forward(st, torch.from_numpy(q).cuda(), relaxed=relaxed).cpu().numpy()
+    assert rel_err(y, oracle.hfit_forward(p, q, relaxed=relaxed)) <= 1e-5
+
+
+@pytest.mark.parametrize("relaxed", [False, True])
+@pytest.mark.parametrize("hidden", [16, 32, 64])
+def test_backward_matches_oracle(ndgi, relaxed, hidden):
+    p = params(4, hidden)
+    n = 3000
+    q = synth.random_queries(5, n)
+    tgt = np.random.default_rng(6).normal(size=(n, 3))
+    st = ndgi.HybridFitState.from_arrays(p)
+    y = ndgi.ndgi_hybrid_fit_forward(st, torch.from_numpy(q).cuda(), relaxed=relaxed)
+    dy = (2.0 * (y.double() - torch.from_numpy(tgt).cuda()) / (3 * n)).float().contiguous()
+    g = ndgi.ndgi_hybrid_fit_backward(st, torch.from_numpy(q).cuda(), dy, relaxed=relaxed)
+    _, gr = oracle.hfit_backward(p, q, tgt, relaxed=relaxed)
+    for k in KEYS:
+        a = g[k].cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(a - gr[k]) <= 1e-3 * max(np.linalg.norm(gr[k]), 1e-30), k
+        assert np.abs(a - gr[k]).max() <= 1e-3 * max(np.abs(gr[k]).max(), 1e-30), k
+
+
+def test_encode_fit_matches_oracle_loop(ndgi):
+    p = params(7, 16)
+    lm, T, batch, seed = 64, 4, 2048, 55
+    targets = synth.fit_targets(8, lm, lm, T, n_gauss=6)
+    st = ndgi.HybridFitState.from_arrays(p)
+    cfg = ndgi.fit_config(steps=3, batch=batch, lr=1e-2, loss_every=1, seed=seed)
+    _, log = ndgi.ndgi_hybrid_encode_fit(st, torch.from_numpy(targets).cuda(), cfg)
+    torch.cuda.synchronize()
+    q = {k: np.asarray(p[k], np.float32).copy() for k in KEYS}
+    qd = dict(p)
+    mom = {k: (np.zeros(q[k].size), np.zeros(q[k].size)) for k in KEYS}
+    losses = []
+    for step in range(3):
+        texel, s = oracle.fit_draw(seed, step, batch, lm, lm)
+        tg = oracle.fit_targets_at(targets, texel, s)
+        qd.update(q)
+        loss, g = oracle.hfit_backward(qd, s, tg)
+        losses.append(loss)
+        for i, k in enumerate(KEYS):
+            oracle.adam(q[k].reshape(-1), g[k].reshape(-1), mom[k][0], mom[k][1], step + 1, 1e-2, project=i < 8)
+    assert np.allclose(log.cpu().numpy(), losses, rtol=1e-4)
+    for k in KEYS:
+        a = st.t[k].cpu().numpy()
+        close = np.mean(np.abs(a - q[k]) <= 1e-4 + 1e-3 * np.abs(q[k]))
+        assert close > 0.99, (k, close)
+
+
+def test_fit_reduces_loss_and_packs_to_its_forward(ndgi):
+    p = params(9, 64)
+    lm, T = 64, 8
+    keys = np.float32([0.0, 0.1, 0.25, 0.4, 0.5, 0.7, 0.8, 0.95])
+    targets = synth.fit_targets_at_times(10, lm, lm, keys, n_gauss=6, t_on=0.4, t_off=0.8)
+    st = ndgi.HybridFitState.from_arrays(p)
+    key_dev = torch.from_numpy(keys).cuda()
+    cfg = ndgi.fit_config(steps=300, batch=1 << 13, lr=1e-2, loss_every=30, freeze_steps=30, seed=11)
+    _, log = ndgi.ndgi_hybrid_encode_fit(st, torch.from_numpy(targets).cuda(), cfg, key_t=key_dev)
+    log = log.cpu().numpy()
+    assert log[-1] < 0.3 * log[0]
+    for k in ("uv_ea", "uv_eb", "uv_wt", "vol_ea", "vol_eb", "vol_wt", "ut", "vt"):
+        assert float(st.t[k].min()) >= 0.0 and float(st.t[k].max()) <= 1.0, k
+    # pack the trained maps (BC4 per map and per F3D slice, UNORM8 planes) and decode them
+    t = st.t
+    uv = ndgi.ndgi_bc_pack(t["uv_ea"], t["uv_eb"], t["uv_wt"])
+    vol = torch.stack([ndgi.ndgi_bc_pack(t["vol_ea"][k].contiguous(), t["vol_eb"][k].contiguous(),
+                                         t["vol_wt"][k].contiguous()) for k in range(t["vol_ea"].shape[0])])
+    ut = torch.round(t["ut"] * 255).to(torch.uint8)
+    vt = torch.round(t["vt"] * 255).to(torch.uint8)
+    hm = ndgi.HybridModel(lm, lm, uv, vol.contiguous(), ut, vt, *[t[k] for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    qq = torch.from_numpy(synth.random_queries(12, 20_000)).cuda()
+    dec = ndgi.ndgi_hybrid_decode_points(hm, qq, "fp32").cpu().numpy()
+    # the forward with F_ut / F_vt at their stored UNORM8 values
+    t["ut"].copy_(ut.float() / 255)
+    t["vt"].copy_(vt.float() / 255)
+    fwd = ndgi.ndgi_hybrid_fit_forward(st, qq).cpu().numpy()
+    assert rel_err(dec, fwd) <= 1e-5
