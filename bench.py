@@ -38,28 +38,35 @@ METRIC = "Gtexels/s decoded (BC fetch+temporal lerp+MLP), FP16-TC vs FP32 plain 
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of a smaller case
-# of the same kernel, scaled to a full launch by the units processed.  Valid only while the kernel sources are
-# the ones captured: the hash below is compared at run time and the figure drops to null once they change.
-TRAFFIC_SOURCES = ("tc_decode.cu", "tc_points.cu", "tc_engine.cuh", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h",
-                   "hybrid.cu", "hybrid.h")
+# of the same kernel, scaled to a full launch by the units processed.  Valid only while the kernel's sources are
+# the ones captured: each kernel's own source set is hashed at run time and its figure drops to null once the code
+# changes.
+_COMMON_SOURCES = ("tc_engine.cuh", "gather.cuh", "bc4.cuh", "umma.cuh", "ndgi_internal.h", "tc_decode.h")
+KERNEL_SOURCES = {
+    "k_points_ws": ("tc_points.cu",) + _COMMON_SOURCES,
+    "k_pages_tc": ("tc_decode.cu",) + _COMMON_SOURCES,
+    "k_pages_ws": ("tc_decode.cu",) + _COMMON_SOURCES,
+    "k_hybrid_pages_tc": ("hybrid.cu", "hybrid.h") + _COMMON_SOURCES,
+}
 NCU_TRAFFIC = {
-    "k_points_ws": {"src": "35a0c4ee7c58d1e9", "read": 134407936, "write": 81475584, "units": 1 << 23,
+    "k_points_ws": {"src": "dc313c105005e444", "read": 134407936, "write": 81475584, "units": 1 << 23,
                     "profile": "profiles/k_points_ws_points_2048_atlas.md"},
-    "k_pages_tc": {"src": "35a0c4ee7c58d1e9", "read": 19674624, "write": 75905280, "units": 1024 * 128 * 128,
+    "k_pages_tc": {"src": "f7fc86e019b63f3e", "read": 19674624, "write": 75905280, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_tc_pages_8_lightmaps.md"},
-    "k_pages_ws": {"src": "35a0c4ee7c58d1e9", "read": 19192576, "write": 76340736, "units": 1024 * 128 * 128,
+    "k_pages_ws": {"src": "f7fc86e019b63f3e", "read": 19192576, "write": 76340736, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_ws_pages_8_lightmaps.md"},
-    "k_hybrid_pages_tc": {"src": "35a0c4ee7c58d1e9", "read": 188086272, "write": 477627904, "units": 4096 * 128 * 128,
+    "k_hybrid_pages_tc": {"src": "41e312db4a7bbc31", "read": 188086272, "write": 477627904, "units": 4096 * 128 * 128,
                           "profile": "profiles/k_hybrid_pages_tc_m64_4096_tiles.md"},
 }
 
 
-def kernel_source_hash():
-    """Hash of the kernel sources' code (comments and blank space stripped, so a comment edit keeps the figure)."""
+def kernel_source_hash(kernel):
+    """Hash of a kernel's source files' code (comments and blank space stripped, so a comment edit keeps the
+    figure)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2604_12625_gb300", "csrc", f)) as fh:
             code = fh.read()
         code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
@@ -71,7 +78,7 @@ def kernel_source_hash():
 def traffic_for(kernel, units):
     """Scaled ncu DRAM bytes for one launch over `units` texels, or None if the kernel changed since capture."""
     rec = NCU_TRAFFIC.get(kernel)
-    if rec is None or rec["src"] != kernel_source_hash():
+    if rec is None or rec["src"] != kernel_source_hash(kernel):
         return None
     return (rec["read"] + rec["write"]) * units / rec["units"]
 
@@ -445,6 +452,57 @@ def bench_fit_batch(args, ndgi, torch):
             "psnr_db_last": float(10 * np.log10(rng * rng / max(log[-1], 1e-30))), "device_check": check_status(ndgi)}
 
 
+HYBRID_FIT_WORKLOAD = ("hybrid fit: one M.64 tile model (F_uv 128^2x4 and F3D 32^2x12x4 as BC endpoints + weights "
+                       "under the straight-through BC simulation, F_ut/F_vt 64x24x2, GELU MLP 16-64-64-3) against the "
+                       "top-left 128^2 crop of the fit workload's 24 keyframe targets; 1000 Adam steps of 2^16 "
+                       "samples at t ~ U[0,1) (targets interpolated between keyframes); then F_uv and F3D packed to "
+                       "BC4, F_ut/F_vt to UNORM8, and every keyframe decoded (FP32) and scored")
+
+
+def bench_hybrid_fit(args, ndgi, torch):
+    """The hybrid decoder's fit (ndgi_hybrid_encode_fit), then its packed model decoded at every keyframe."""
+    T, side = 24, 128
+    tg_np = np.ascontiguousarray(c3_targets()[:, :side, :side])
+    tg = torch.from_numpy(tg_np).cuda()
+    vol_side, vol_t, hidden = 32, 12, 64
+    p = synth.hybrid_fit_init(21, side, side, side, side, vol_side, vol_side, vol_t, 64, 24, 64, 24, hidden)
+    steps = max(20, min(1000, args.fit_steps // 2))
+    batch = 1 << 16
+    warm = ndgi.HybridFitState.from_arrays(p)
+    ndgi.ndgi_hybrid_encode_fit(warm, tg, ndgi.fit_config(steps=2, batch=batch, seed=1))
+    st = ndgi.HybridFitState.from_arrays(p)
+    cfg = ndgi.fit_config(steps=steps, batch=batch, lr=1e-2, freeze_steps=steps // 10,
+                          loss_every=max(1, steps // 5), seed=22)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, log = ndgi.ndgi_hybrid_encode_fit(st, tg, cfg)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    log = log.cpu().numpy()
+    t = st.t
+    uv = ndgi.ndgi_bc_pack(t["uv_ea"], t["uv_eb"], t["uv_wt"])
+    vol = torch.stack([ndgi.ndgi_bc_pack(t["vol_ea"][k].contiguous(), t["vol_eb"][k].contiguous(),
+                                         t["vol_wt"][k].contiguous()) for k in range(vol_t)]).contiguous()
+    ut = torch.round(t["ut"] * 255).to(torch.uint8)
+    vt = torch.round(t["vt"] * 255).to(torch.uint8)
+    hm = ndgi.HybridModel(side, side, uv, vol, ut, vt, *[t[k] for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    keys = np.arange(T, dtype=np.float32) / T
+    q = torch.from_numpy(synth.texel_queries(side, side, keys)).cuda()
+    rgb = ndgi.ndgi_hybrid_decode_points(hm, q.reshape(-1, 3), "fp32").reshape(T, side, side, 3)
+    ref = tg.float()
+    rng = float(ref.max() - ref.min())
+    mse = float(((rgb - ref) ** 2).mean())
+    return {"workload": HYBRID_FIT_WORKLOAD.replace("1000 Adam", f"{steps} Adam"), "steps": steps,
+            "ms_per_step": ms / steps, "samples_per_s": steps * batch / (ms / 1e3),
+            "loss_first": float(log[0]), "loss_last": float(log[-1]),
+            "psnr_db_fit": float(10 * np.log10(rng * rng / max(log[-1], 1e-30))),
+            "psnr_db_packed_decode": float(10 * np.log10(rng * rng / max(mse, 1e-30))),
+            "device_check": check_status(ndgi)}
+
+
 QUALITY_WORKLOAD = ("quality: 256^2 lightmap, 26 non-uniform keyframes (24 hourly + 2 around a light switch at "
                     "t = 0.73; a lamp on for 0.73 <= t < 0.9), UV-chart mask (~70% valid); BC4 128^2x16, temporal "
                     "26x8, MLP 24-64-64-3; 1500 Adam steps of 2^18 samples, with BC simulation (STE) and without it "
@@ -800,7 +858,7 @@ def main():
     pages = None
     if not args.no_pages:
         pages = bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank)
-    fit = scale = hybrid = quality = fit_batch = None
+    fit = scale = hybrid = quality = fit_batch = hybrid_fit = None
     if not args.no_extra:
         if not args.no_scale:
             scale = bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank)
@@ -811,6 +869,8 @@ def main():
         if not args.no_hybrid:
             hybrid["profiles_1024"] = bench_hybrid_profiles(args, ndgi, torch, timed)
         fit_batch = bench_fit_batch(args, ndgi, torch)
+        if not args.no_hybrid:
+            hybrid_fit = bench_hybrid_fit(args, ndgi, torch)
 
     if rank != 0:
         if dist is not None:
@@ -861,7 +921,7 @@ def main():
                             "streams", "matches_device_decode": e2e_ok},
         "ms_per_step_median_of_20": ms_median,
         "gpu_launches": args.steps, "clocks": clocks,
-        "fit": fit, "fit_batch": fit_batch, "scale": scale, "hybrid": hybrid, "quality": quality, "pages": pages,
+        "fit": fit, "fit_batch": fit_batch, "hybrid_fit": hybrid_fit, "scale": scale, "hybrid": hybrid, "quality": quality, "pages": pages,
     }
     if hybrid is not None:
         h16, hr = hybrid["fp16"], hybrid["roofline"]
