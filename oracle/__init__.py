@@ -110,6 +110,16 @@ def lib():
             L.om_hfit_forward.argtypes = [vp, vp, i64, C.c_int, vp]
             L.om_hfit_backward.argtypes = [vp, vp, vp, i64, C.c_int, vp]
             L.om_hfit_backward.restype = f64
+            L.om_bc7_decode_block.argtypes = [vp, vp]
+            L.om_bc7_decode.argtypes = [vp, i32, i32, vp]
+            L.om_bc7_candidate.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+            L.om_bc7_candidate.restype = i64
+            L.om_bc7_encode_block.argtypes = [vp, vp]
+            L.om_bc7_encode_block.restype = i64
+            L.om_bc7_encode.argtypes = [vp, i32, i32, vp, C.c_int]
+            L.om_bc7_encode.restype = i64
+            L.om_bc7_subset.argtypes = [C.c_int, C.c_int, C.c_int]
+            L.om_bc7_anchor.argtypes = [C.c_int, C.c_int, C.c_int]
             L.om_splitmix64_next.argtypes = [C.c_uint64]
             L.om_splitmix64_next.restype = C.c_uint64
             _lib = L
@@ -182,7 +192,7 @@ class _Hybrid(C.Structure):
                 ("vol_bc4", C.c_void_p), ("ut_w", C.c_int32), ("ut_t", C.c_int32), ("ut", C.c_void_p),
                 ("vt_h", C.c_int32), ("vt_t", C.c_int32), ("vt", C.c_void_p), ("hidden", C.c_int32),
                 ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
-                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32), ("feat_format", C.c_int32)]
 
 
 class HybridModel:
@@ -192,7 +202,10 @@ class HybridModel:
         self.src = m
         self.hidden = int(m["hidden"])
         assert self.hidden <= lib().om_max_hidden()
-        self.arr = {k: _c(m[k], np.uint8) for k in ("uv_bc4", "vol_bc4", "ut", "vt")}
+        self.fmt = int(m.get("feat_format", 0))
+        uv, vol = ("uv_bc7", "vol_bc7") if self.fmt == 1 else ("uv_bc4", "vol_bc4")
+        self.arr = {k: _c(m[src], np.uint8) for k, src in (("uv_bc4", uv), ("vol_bc4", vol), ("ut", "ut"),
+                                                           ("vt", "vt"))}
         w = stored_weights(m, precision)
         self.w = {k: _c(v, np.float64) for k, v in w.items()}
         vol_t, vol_h, vol_w = (int(d) for d in m["vol_shape"])
@@ -201,7 +214,7 @@ class HybridModel:
                          int(m["ut"].shape[1]), int(m["ut"].shape[0]), _ptr(self.arr["ut"]),
                          int(m["vt"].shape[1]), int(m["vt"].shape[0]), _ptr(self.arr["vt"]), self.hidden,
                          _ptr(self.w["w1"]), _ptr(self.w["b1"]), _ptr(self.w["w2"]), _ptr(self.w["b2"]),
-                         _ptr(self.w["w3"]), _ptr(self.w["b3"]), int(m.get("address_mode", 0)))
+                         _ptr(self.w["w3"]), _ptr(self.w["b3"]), int(m.get("address_mode", 0)), self.fmt)
 
 
 def _hybrid(m, precision="fp32"):
@@ -531,3 +544,56 @@ def hfit_backward(p, uvt, target, relaxed=False):
     G = _HFitGrads(*[_ptr(g[k]) for k in HFIT_KEYS])
     loss = lib().om_hfit_backward(C.byref(P.s), _ptr(q), _ptr(tg), q.shape[0], int(relaxed), C.byref(G))
     return loss, g
+
+
+# --------------------------------------------------------------------------
+# BC7 blocks (the paper's storage format for F_uv and the F3D slices)
+# --------------------------------------------------------------------------
+
+def bc7_decode_block(blk):
+    """RGBA8 [16][4] of one 16-byte BC7 block (texel p = 4 row + col)."""
+    b = _c(np.asarray(blk, np.uint8).reshape(16), np.uint8)
+    out = np.zeros((16, 4), np.uint8)
+    lib().om_bc7_decode_block(_ptr(b), _ptr(out))
+    return out
+
+
+def bc7_decode(blocks, w, h):
+    """RGBA8 image [h][w][4] of BC7 blocks [h/4][w/4][16]."""
+    b = _c(blocks, np.uint8)
+    out = np.zeros((h, w, 4), np.uint8)
+    lib().om_bc7_decode(_ptr(b), int(w), int(h), _ptr(out))
+    return out
+
+
+def bc7_candidate(x, mode, part=0, rot=0, isb=0):
+    """(block, squared error) of one encoder candidate for the block x [16][4] uint8."""
+    xb = _c(np.asarray(x, np.uint8).reshape(16, 4), np.uint8)
+    blk = np.zeros(16, np.uint8)
+    err = lib().om_bc7_candidate(_ptr(xb), int(mode), int(part), int(rot), int(isb), _ptr(blk))
+    return blk, int(err)
+
+
+def bc7_encode_block(x):
+    """(block, squared error) of the encoder on x [16][4] uint8."""
+    xb = _c(np.asarray(x, np.uint8).reshape(16, 4), np.uint8)
+    blk = np.zeros(16, np.uint8)
+    err = lib().om_bc7_encode_block(_ptr(xb), _ptr(blk))
+    return blk, int(err)
+
+
+def bc7_encode(rgba, nthreads=None):
+    """(blocks [h/4][w/4][16], total squared error) of the encoder on an RGBA8 image [h][w][4]."""
+    x = _c(rgba, np.uint8)
+    h, w, _ = x.shape
+    out = np.zeros((h // 4, w // 4, 16), np.uint8)
+    err = lib().om_bc7_encode(_ptr(x), int(w), int(h), _ptr(out), nthreads or nthreads_default())
+    return out, int(err)
+
+
+def bc7_subset(ns, part, p):
+    return int(lib().om_bc7_subset(int(ns), int(part), int(p)))
+
+
+def bc7_anchor(ns, part, s):
+    return int(lib().om_bc7_anchor(int(ns), int(part), int(s)))

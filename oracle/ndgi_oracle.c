@@ -28,6 +28,10 @@
  *     k = q7(w) decided in FP32 as floor(min(max(s*x + 0.5, 0), s)); the
  *     backward treats the quantisers as identity and uses quantised factors.
  *
+ * The BC7 section states the paper's four-channel block format (decode) and
+ * this library's deterministic multi-mode encoder; the hybrid decoder reads
+ * F_uv and F3D either as four BC4 planes or as BC7.
+ *
  * All interpolation and MLP arithmetic is FP64.  Build with
  * -ffp-contract=off so the FP32 quantiser decisions are single roundings.
  */
@@ -766,6 +770,489 @@ void om_fit_draw(uint64_t seed, int64_t step, int64_t first, int64_t n, int32_t 
 }
 
 /* ---------------------------------------------------------------------- */
+/* BC7 blocks (the paper's storage for F_uv and the F3D slices, Sec. 3.2)  */
+/* ---------------------------------------------------------------------- */
+/*
+ * Plain statement of the BC7 (BPTC, UNORM) block format as published for
+ * Direct3D 11 and OpenGL (ARB_texture_compression_bptc).  A 16-byte block is
+ * read as a 128-bit little-endian bit string, fields LSB first:
+ *   mode     m + 1 bits: m zeros then a one (byte 0 == 0 is reserved and
+ *            decodes to (0, 0, 0, 0));
+ *   partition (PB bits), rotation (RB), index selector (ISB);
+ *   endpoint codes: channel-major (R, then G, B, then A when AB > 0), within
+ *            a channel subset-major, within a subset endpoint 0 then 1;
+ *   p-bits: one per endpoint (EPB, same subset/endpoint order) or one per
+ *            subset shared by its two endpoints (SPB); a p-bit is appended as
+ *            the code's new least significant bit for every channel;
+ *   primary indices (IB bits per texel, texel order 0..15, p = 4 row + col),
+ *            an anchor texel storing IB - 1 bits (its top bit is zero);
+ *   secondary indices (IB2 bits, modes 4 and 5), anchor texel 0.
+ * Anchors: texel 0 for subset 0; for two subsets the second subset's anchor
+ * is BC7_ANCHOR2[partition]; for three, BC7_ANCHOR3A / BC7_ANCHOR3B.
+ * An n-bit endpoint (p-bit included) expands to 8 bits by bit replication,
+ * (c << (8 - n)) | (c >> (2n - 8)); without alpha endpoints A = 255.
+ * A texel's value per channel is ((64 - w) e0 + w e1 + 32) >> 6 with w from
+ * the weight table of the index width.  Mode 4 with ISB = 1 takes colour
+ * from the 3-bit secondary and alpha from the 2-bit primary indices
+ * (ISB = 0: the other way round; mode 5: colour primary, alpha secondary).
+ * Rotation 1, 2, 3 swaps A with R, G, B after interpolation.
+ */
+typedef struct {
+  int ns, pb, rb, isb, cb, ab, epb, spb, ib, ib2;
+} om_bc7_mode;
+
+static const om_bc7_mode OM_BC7_MODES[8] = {
+    /*      NS PB RB ISB CB AB EPB SPB IB IB2 */
+    /* 0 */ {3, 4, 0, 0, 4, 0, 1, 0, 3, 0},
+    /* 1 */ {2, 6, 0, 0, 6, 0, 0, 1, 3, 0},
+    /* 2 */ {3, 6, 0, 0, 5, 0, 0, 0, 2, 0},
+    /* 3 */ {2, 6, 0, 0, 7, 0, 1, 0, 2, 0},
+    /* 4 */ {1, 0, 2, 1, 5, 6, 0, 0, 2, 3},
+    /* 5 */ {1, 0, 2, 0, 7, 8, 0, 0, 2, 2},
+    /* 6 */ {1, 0, 0, 0, 7, 7, 1, 0, 4, 0},
+    /* 7 */ {2, 6, 0, 0, 5, 5, 1, 0, 2, 0},
+};
+
+/* Subset of each texel (row-major, 4 rows of 4) for the 64 two-subset partitions. */
+static const char *const OM_BC7_PART2[64] = {
+    "0011001100110011", "0001000100010001", "0111011101110111", "0001001100110111",
+    "0000000100010011", "0011011101111111", "0001001101111111", "0000000100110111",
+    "0000000000010011", "0011011111111111", "0000000101111111", "0000000000010111",
+    "0001011111111111", "0000000011111111", "0000111111111111", "0000000000001111",
+    "0000100011101111", "0111000100000000", "0000000010001110", "0111001100010000",
+    "0011000100000000", "0000100011001110", "0000000010001100", "0111001100110001",
+    "0011000100010000", "0000100010001100", "0110011001100110", "0011011001101100",
+    "0001011111101000", "0000111111110000", "0111000110001110", "0011100110011100",
+    "0101010101010101", "0000111100001111", "0101101001011010", "0011001111001100",
+    "0011110000111100", "0101010110101010", "0110100101101001", "0101101010100101",
+    "0111001111001110", "0001001111001000", "0011001001001100", "0011101111011100",
+    "0110100110010110", "0011110011000011", "0110011010011001", "0000011001100000",
+    "0100111001000000", "0010011100100000", "0000001001110010", "0000010011100100",
+    "0110110010010011", "0011011011001001", "0110001110011100", "0011100111000110",
+    "0110110011001001", "0110001100111001", "0111111010000001", "0001100011100111",
+    "0000111100110011", "0011001111110000", "0010001011101110", "0100010001110111",
+};
+
+/* Subset of each texel for the 64 three-subset partitions. */
+static const char *const OM_BC7_PART3[64] = {
+    "0011001102212222", "0001001122112221", "0000200122112211", "0222002200110111",
+    "0000000011221122", "0011001100220022", "0022002211111111", "0011001122112211",
+    "0000000011112222", "0000111111112222", "0000111122222222", "0012001200120012",
+    "0112011201120112", "0122012201220122", "0011011211221222", "0011200122002220",
+    "0001001101121122", "0111001120012200", "0000112211221122", "0022002200221111",
+    "0111011102220222", "0001000122212221", "0000001101220122", "0000110022102210",
+    "0122012200110000", "0012001211222222", "0110122112210110", "0000011012211221",
+    "0022110211020022", "0110011020022222", "0011012201220011", "0000200022112221",
+    "0000000211221222", "0222002200120011", "0011001200220222", "0120012001200120",
+    "0000111122220000", "0120120120120120", "0120201212010120", "0011220011220011",
+    "0011112222000011", "0101010122222222", "0000000021212121", "0022112200221122",
+    "0022001100220011", "0220122102201221", "0101222222220101", "0000212121212121",
+    "0101010101012222", "0222011102220111", "0002111200021112", "0000211221122112",
+    "0222011101110222", "0002111211120002", "0110011001102222", "0000000021122112",
+    "0110011022222222", "0022001100110022", "0022112211220022", "0000000000002112",
+    "0002000100020001", "0222122202221222", "0101222222222222", "0111201122012220",
+};
+
+static const uint8_t OM_BC7_ANCHOR2[64] = {
+    15, 15, 15, 15, 15, 15, 15, 15, 15, 15, 15, 15, 15, 15, 15, 15,
+    15, 2,  8,  2,  2,  8,  8,  15, 2,  8,  2,  2,  8,  8,  2,  2,
+    15, 15, 6,  8,  2,  8,  15, 15, 2,  8,  2,  2,  2,  15, 15, 6,
+    6,  2,  6,  8,  15, 15, 2,  2,  15, 15, 15, 15, 15, 2,  2,  15,
+};
+static const uint8_t OM_BC7_ANCHOR3A[64] = {
+    3,  3,  15, 15, 8,  3,  15, 15, 8,  8,  6,  6,  6,  5,  3,  3,
+    3,  3,  8,  15, 3,  3,  6,  10, 5,  8,  8,  6,  8,  5,  15, 15,
+    8,  15, 3,  5,  6,  10, 8,  15, 15, 3,  15, 5,  15, 15, 15, 15,
+    3,  15, 5,  5,  5,  8,  5,  10, 5,  10, 8,  13, 15, 12, 3,  3,
+};
+static const uint8_t OM_BC7_ANCHOR3B[64] = {
+    15, 8,  8,  3,  15, 15, 3,  8,  15, 15, 15, 15, 15, 15, 15, 8,
+    15, 8,  15, 3,  15, 8,  15, 8,  3,  15, 6,  10, 15, 15, 10, 8,
+    15, 3,  15, 10, 10, 8,  9,  10, 6,  15, 8,  15, 3,  6,  6,  8,
+    15, 3,  15, 15, 15, 15, 15, 15, 15, 15, 15, 15, 3,  15, 15, 8,
+};
+
+static const int OM_BC7_W2[4] = {0, 21, 43, 64};
+static const int OM_BC7_W3[8] = {0, 9, 18, 27, 37, 46, 55, 64};
+static const int OM_BC7_W4[16] = {0, 4, 9, 13, 17, 21, 26, 30, 34, 38, 43, 47, 51, 55, 60, 64};
+
+static const int *om_bc7_weights(int bits) { return bits == 2 ? OM_BC7_W2 : bits == 3 ? OM_BC7_W3 : OM_BC7_W4; }
+
+/* Subset of texel p in partition `part` of a block with ns subsets. */
+int om_bc7_subset(int ns, int part, int p) {
+  if (ns == 2) return OM_BC7_PART2[part][p] - '0';
+  if (ns == 3) return OM_BC7_PART3[part][p] - '0';
+  return 0;
+}
+
+/* Anchor texel of subset s. */
+int om_bc7_anchor(int ns, int part, int s) {
+  if (s == 0) return 0;
+  if (ns == 2) return OM_BC7_ANCHOR2[part];
+  return s == 1 ? OM_BC7_ANCHOR3A[part] : OM_BC7_ANCHOR3B[part];
+}
+
+static int om_bc7_is_anchor(int ns, int part, int p) {
+  for (int s = 0; s < ns; ++s)
+    if (om_bc7_anchor(ns, part, s) == p) return 1;
+  return 0;
+}
+
+/* n bits of blk starting at bit *pos (LSB first), advancing *pos. */
+static int om_bits_get(const uint8_t *blk, int *pos, int n) {
+  int v = 0;
+  for (int i = 0; i < n; ++i, ++*pos) v |= ((blk[*pos >> 3] >> (*pos & 7)) & 1) << i;
+  return v;
+}
+
+static int om_bc7_expand(int c, int n) { return n >= 8 ? c : (c << (8 - n)) | (c >> (2 * n - 8)); }
+
+/* Decodes one block to rgba [16][4] (texel p = 4 row + col). */
+void om_bc7_decode_block(const uint8_t *blk, uint8_t *rgba) {
+  int mode = 0;
+  while (mode < 8 && !((blk[0] >> mode) & 1)) ++mode;
+  if (mode == 8) {
+    memset(rgba, 0, 64);
+    return;
+  }
+  const om_bc7_mode *M = &OM_BC7_MODES[mode];
+  int pos = mode + 1;
+  const int part = om_bits_get(blk, &pos, M->pb);
+  const int rot = om_bits_get(blk, &pos, M->rb);
+  const int isb = om_bits_get(blk, &pos, M->isb);
+  int code[3][2][4], bits[4] = {M->cb, M->cb, M->cb, M->ab};
+  const int nch = M->ab ? 4 : 3;
+  for (int c = 0; c < nch; ++c)
+    for (int s = 0; s < M->ns; ++s)
+      for (int e = 0; e < 2; ++e) code[s][e][c] = om_bits_get(blk, &pos, bits[c]);
+  if (M->epb) {
+    for (int s = 0; s < M->ns; ++s)
+      for (int e = 0; e < 2; ++e) {
+        const int p = om_bits_get(blk, &pos, 1);
+        for (int c = 0; c < nch; ++c) code[s][e][c] = (code[s][e][c] << 1) | p;
+      }
+  }
+  if (M->spb) {
+    for (int s = 0; s < M->ns; ++s) {
+      const int p = om_bits_get(blk, &pos, 1);
+      for (int e = 0; e < 2; ++e)
+        for (int c = 0; c < nch; ++c) code[s][e][c] = (code[s][e][c] << 1) | p;
+    }
+  }
+  const int pbit = (M->epb || M->spb) ? 1 : 0;
+  int ep[3][2][4];
+  for (int s = 0; s < M->ns; ++s)
+    for (int e = 0; e < 2; ++e)
+      for (int c = 0; c < 4; ++c)
+        ep[s][e][c] = c < nch ? om_bc7_expand(code[s][e][c], bits[c] + pbit) : 255;
+  int idx1[16], idx2[16] = {0};
+  for (int p = 0; p < 16; ++p) idx1[p] = om_bits_get(blk, &pos, M->ib - om_bc7_is_anchor(M->ns, part, p));
+  if (M->ib2)
+    for (int p = 0; p < 16; ++p) idx2[p] = om_bits_get(blk, &pos, M->ib2 - (p == 0));
+  for (int p = 0; p < 16; ++p) {
+    const int s = om_bc7_subset(M->ns, part, p);
+    int ic = idx1[p], bc = M->ib, ia = idx1[p], ba = M->ib;
+    if (M->ib2) {
+      if (isb) {
+        ic = idx2[p], bc = M->ib2;
+      } else {
+        ia = idx2[p], ba = M->ib2;
+      }
+    }
+    for (int c = 0; c < 4; ++c) {
+      const int w = c < 3 ? om_bc7_weights(bc)[ic] : om_bc7_weights(ba)[ia];
+      rgba[4 * p + c] = (uint8_t)(((64 - w) * ep[s][0][c] + w * ep[s][1][c] + 32) >> 6);
+    }
+    if (rot) {
+      const uint8_t t = rgba[4 * p + rot - 1];
+      rgba[4 * p + rot - 1] = rgba[4 * p + 3];
+      rgba[4 * p + 3] = t;
+    }
+  }
+}
+
+/* Decodes an image of blocks [h/4][w/4][16] to rgba [h][w][4]. */
+void om_bc7_decode(const uint8_t *blocks, int32_t w, int32_t h, uint8_t *rgba) {
+  const int bw = w / 4, bh = h / 4;
+  for (int by = 0; by < bh; ++by)
+    for (int bx = 0; bx < bw; ++bx) {
+      uint8_t px[64];
+      om_bc7_decode_block(blocks + ((size_t)by * bw + bx) * 16, px);
+      for (int p = 0; p < 16; ++p)
+        memcpy(rgba + (((size_t)(4 * by + p / 4)) * w + 4 * bx + p % 4) * 4, px + 4 * p, 4);
+    }
+}
+
+/*
+ * BC7 encoder.  The paper compresses the 8-bit quantised F_uv and F3D slices
+ * with "the BC7 compression algorithm ... using multiple modes" without
+ * fixing an encoder; this is the library's own, deterministic and
+ * integer-exact, so that both implementations give identical blocks.  For a
+ * block x[16][4]:
+ *   - candidates, in this order: mode 6; mode 5 with rotation 0..3; mode 4
+ *     with rotation 0..3 (outer) and index selector 0..1 (inner); mode 7
+ *     with partitions 0..63; when every alpha is 255 also mode 3 and mode 1
+ *     (partitions 0..63), mode 2 (0..63) and mode 0 (0..15);
+ *   - a rotation first swaps A with R, G or B of the input;
+ *   - endpoint groups: modes 4 and 5 code colour (RGB) and alpha (A) with
+ *     separate endpoints and indices; the other modes code all their
+ *     channels (RGBA for 6 and 7, RGB for 0..3) together;
+ *   - per subset and group, endpoint 0 is the per-channel minimum and
+ *     endpoint 1 the per-channel maximum of the subset's texels, each coded
+ *     by the nearest code per channel: without p-bits q = argmin
+ *     |expand(q, n) - v| (lowest q on ties); with a p-bit per endpoint, q(p)
+ *     likewise for p = 0 and 1 at n + 1 bits and p the one with the smaller
+ *     sum of squared errors over the endpoint's channels (0 on ties); with a
+ *     p-bit per subset (mode 1) the sum runs over both endpoints;
+ *   - every texel takes the palette index with the smallest squared error
+ *     over the group's channels (lowest index on ties);
+ *   - where an anchor texel's index has its top bit set, the group's
+ *     endpoints (p-bits included) are swapped and its indices i become
+ *     2^bits - 1 - i (the weight tables are symmetric: the texels do not
+ *     change);
+ *   - the error is the sum over texels and channels of the squared
+ *     difference between the decoded block and x; the first candidate with
+ *     the smallest error is kept.
+ */
+static int om_bc7_code(int v, int n, int p) {
+  int best = 0, be = 1 << 30;
+  for (int q = 0; q < (1 << n); ++q) {
+    const int x = p < 0 ? om_bc7_expand(q, n) : om_bc7_expand((q << 1) | p, n + 1);
+    const int e = abs(x - v);
+    if (e < be) {
+      be = e;
+      best = q;
+    }
+  }
+  return best;
+}
+
+static void om_bits_put(uint8_t *blk, int *pos, int n, int v) {
+  for (int i = 0; i < n; ++i, ++*pos)
+    if ((v >> i) & 1) blk[*pos >> 3] |= (uint8_t)(1u << (*pos & 7));
+}
+
+/* One candidate: writes its block and returns the squared error of its decode against x. */
+int64_t om_bc7_candidate(const uint8_t *x0, int mode, int part, int rot, int isb, uint8_t *blk) {
+  const om_bc7_mode *M = &OM_BC7_MODES[mode];
+  int x[16][4];
+  for (int p = 0; p < 16; ++p)
+    for (int c = 0; c < 4; ++c) x[p][c] = x0[4 * p + c];
+  if (rot)
+    for (int p = 0; p < 16; ++p) {
+      const int t = x[p][rot - 1];
+      x[p][rot - 1] = x[p][3];
+      x[p][3] = t;
+    }
+  const int split = mode == 4 || mode == 5;   /* separate colour and alpha groups */
+  const int ngroups = split ? 2 : 1;
+  const int nch = M->ab ? 4 : 3;
+  int g_lo[2], g_hi[2], g_ebits[2], g_ibits[2];
+  if (split) {
+    g_lo[0] = 0, g_hi[0] = 3, g_ebits[0] = M->cb;
+    g_lo[1] = 3, g_hi[1] = 4, g_ebits[1] = M->ab;
+    g_ibits[0] = mode == 4 ? (isb ? 3 : 2) : 2;
+    g_ibits[1] = mode == 4 ? (isb ? 2 : 3) : 2;
+  } else {
+    g_lo[0] = 0, g_hi[0] = nch, g_ebits[0] = M->cb, g_ibits[0] = M->ib;
+  }
+  int code[3][2][4] = {{{0}}}, pb[3][2] = {{0}}, idx[2][16] = {{0}};
+  for (int g = 0; g < ngroups; ++g) {
+    const int n = g_ebits[g], ib = g_ibits[g];
+    const int *wt = om_bc7_weights(ib);
+    for (int s = 0; s < M->ns; ++s) {
+      int lo[4], hi[4];
+      for (int c = g_lo[g]; c < g_hi[g]; ++c) {
+        lo[c] = 255;
+        hi[c] = 0;
+        for (int p = 0; p < 16; ++p)
+          if (om_bc7_subset(M->ns, part, p) == s) {
+            if (x[p][c] < lo[c]) lo[c] = x[p][c];
+            if (x[p][c] > hi[c]) hi[c] = x[p][c];
+          }
+      }
+      const int *tgt[2] = {lo, hi};
+      int val[2][4];
+      if (M->epb) {
+        for (int e = 0; e < 2; ++e) {
+          int best_p = 0;
+          int64_t best_err = -1;
+          for (int p = 0; p < 2; ++p) {
+            int64_t err = 0;
+            for (int c = g_lo[g]; c < g_hi[g]; ++c) {
+              const int d = om_bc7_expand((om_bc7_code(tgt[e][c], n, p) << 1) | p, n + 1) - tgt[e][c];
+              err += d * d;
+            }
+            if (best_err < 0 || err < best_err) {
+              best_err = err;
+              best_p = p;
+            }
+          }
+          pb[s][e] = best_p;
+          for (int c = g_lo[g]; c < g_hi[g]; ++c) {
+            code[s][e][c] = om_bc7_code(tgt[e][c], n, best_p);
+            val[e][c] = om_bc7_expand((code[s][e][c] << 1) | best_p, n + 1);
+          }
+        }
+      } else if (M->spb) {
+        int best_p = 0;
+        int64_t best_err = -1;
+        for (int p = 0; p < 2; ++p) {
+          int64_t err = 0;
+          for (int e = 0; e < 2; ++e)
+            for (int c = g_lo[g]; c < g_hi[g]; ++c) {
+              const int d = om_bc7_expand((om_bc7_code(tgt[e][c], n, p) << 1) | p, n + 1) - tgt[e][c];
+              err += d * d;
+            }
+          if (best_err < 0 || err < best_err) {
+            best_err = err;
+            best_p = p;
+          }
+        }
+        for (int e = 0; e < 2; ++e) {
+          pb[s][e] = best_p;
+          for (int c = g_lo[g]; c < g_hi[g]; ++c) {
+            code[s][e][c] = om_bc7_code(tgt[e][c], n, best_p);
+            val[e][c] = om_bc7_expand((code[s][e][c] << 1) | best_p, n + 1);
+          }
+        }
+      } else {
+        for (int e = 0; e < 2; ++e)
+          for (int c = g_lo[g]; c < g_hi[g]; ++c) {
+            code[s][e][c] = om_bc7_code(tgt[e][c], n, -1);
+            val[e][c] = om_bc7_expand(code[s][e][c], n);
+          }
+      }
+      /* indices */
+      for (int p = 0; p < 16; ++p) {
+        if (om_bc7_subset(M->ns, part, p) != s) continue;
+        int best_i = 0;
+        int64_t best_err = -1;
+        for (int i = 0; i < (1 << ib); ++i) {
+          int64_t err = 0;
+          for (int c = g_lo[g]; c < g_hi[g]; ++c) {
+            const int d = ((64 - wt[i]) * val[0][c] + wt[i] * val[1][c] + 32) / 64 - x[p][c];
+            err += d * d;
+          }
+          if (best_err < 0 || err < best_err) {
+            best_err = err;
+            best_i = i;
+          }
+        }
+        idx[g][p] = best_i;
+      }
+      /* anchor: its index must have a zero top bit */
+      const int a = split ? 0 : om_bc7_anchor(M->ns, part, s);
+      if (idx[g][a] >> (ib - 1)) {
+        for (int c = g_lo[g]; c < g_hi[g]; ++c) {
+          const int t = code[s][0][c];
+          code[s][0][c] = code[s][1][c];
+          code[s][1][c] = t;
+        }
+        if (!split) {
+          const int t = pb[s][0];
+          pb[s][0] = pb[s][1];
+          pb[s][1] = t;
+        }
+        for (int p = 0; p < 16; ++p)
+          if (om_bc7_subset(M->ns, part, p) == s) idx[g][p] = (1 << ib) - 1 - idx[g][p];
+      }
+    }
+  }
+  /* write the block */
+  memset(blk, 0, 16);
+  int pos = 0;
+  om_bits_put(blk, &pos, mode + 1, 1 << mode);
+  om_bits_put(blk, &pos, M->pb, part);
+  om_bits_put(blk, &pos, M->rb, rot);
+  om_bits_put(blk, &pos, M->isb, isb);
+  for (int c = 0; c < nch; ++c)
+    for (int s = 0; s < M->ns; ++s)
+      for (int e = 0; e < 2; ++e) om_bits_put(blk, &pos, c < 3 ? M->cb : M->ab, code[s][e][c]);
+  if (M->epb)
+    for (int s = 0; s < M->ns; ++s)
+      for (int e = 0; e < 2; ++e) om_bits_put(blk, &pos, 1, pb[s][e]);
+  if (M->spb)
+    for (int s = 0; s < M->ns; ++s) om_bits_put(blk, &pos, 1, pb[s][0]);
+  /* primary indices: colour group, or for mode 4 with isb = 1 the alpha group */
+  const int gp = (mode == 4 && isb) ? 1 : 0;
+  for (int p = 0; p < 16; ++p) om_bits_put(blk, &pos, M->ib - om_bc7_is_anchor(M->ns, part, p), idx[gp][p]);
+  if (M->ib2)
+    for (int p = 0; p < 16; ++p) om_bits_put(blk, &pos, M->ib2 - (p == 0), idx[1 - gp][p]);
+  if (pos != 128) return -1;
+  uint8_t dec[64];
+  om_bc7_decode_block(blk, dec);
+  int64_t err = 0;
+  for (int i = 0; i < 64; ++i) {
+    const int d = (int)dec[i] - (int)x0[i];
+    err += d * d;
+  }
+  return err;
+}
+
+/* Encodes one block rgba [16][4]; returns the squared error of its decode. */
+int64_t om_bc7_encode_block(const uint8_t *x, uint8_t *blk) {
+  int opaque = 1;
+  for (int p = 0; p < 16; ++p) opaque &= x[4 * p + 3] == 255;
+  int64_t best = -1;
+  uint8_t tmp[16];
+#define OM_TRY(MODE, PART, ROT, ISB)                                 \
+  do {                                                               \
+    const int64_t e_ = om_bc7_candidate(x, MODE, PART, ROT, ISB, tmp); \
+    if (e_ >= 0 && (best < 0 || e_ < best)) {                       \
+      best = e_;                                                     \
+      memcpy(blk, tmp, 16);                                          \
+    }                                                                \
+  } while (0)
+  OM_TRY(6, 0, 0, 0);
+  for (int r = 0; r < 4; ++r) OM_TRY(5, 0, r, 0);
+  for (int r = 0; r < 4; ++r)
+    for (int i = 0; i < 2; ++i) OM_TRY(4, 0, r, i);
+  for (int q = 0; q < 64; ++q) OM_TRY(7, q, 0, 0);
+  if (opaque) {
+    for (int q = 0; q < 64; ++q) OM_TRY(3, q, 0, 0);
+    for (int q = 0; q < 64; ++q) OM_TRY(1, q, 0, 0);
+    for (int q = 0; q < 64; ++q) OM_TRY(2, q, 0, 0);
+    for (int q = 0; q < 16; ++q) OM_TRY(0, q, 0, 0);
+  }
+#undef OM_TRY
+  return best;
+}
+
+/* Encodes rgba [h][w][4] (w, h multiples of 4) to blocks [h/4][w/4][16]; returns the total squared error. */
+int64_t om_bc7_encode(const uint8_t *rgba, int32_t w, int32_t h, uint8_t *blocks, int nthreads) {
+  const int bw = w / 4, nb = bw * (h / 4);
+  int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total) num_threads(nthreads > 0 ? nthreads : 1)
+  for (int b = 0; b < nb; ++b) {
+    const int by = b / bw, bx = b % bw;
+    uint8_t px[64];
+    for (int p = 0; p < 16; ++p)
+      memcpy(px + 4 * p, rgba + (((size_t)(4 * by + p / 4)) * w + 4 * bx + p % 4) * 4, 4);
+    total += om_bc7_encode_block(px, blocks + (size_t)b * 16);
+  }
+  return total;
+}
+
+/* Bilinear sample at (u, v) of a BC7 map [h/4][w/4][16]: four decoded taps, value byte / 255. */
+static void om_bc7_bilinear(const uint8_t *blocks, int w, int h, double u, double v, int mode, double *out) {
+  int x0, x1, y0, y1;
+  double fx, fy;
+  om_bilinear_setup(u, w, mode, &x0, &x1, &fx);
+  om_bilinear_setup(v, h, mode, &y0, &y1, &fy);
+  const int bw = w / 4;
+  const int tx[4] = {x0, x1, x0, x1}, ty[4] = {y0, y0, y1, y1};
+  double f[4][4];
+  for (int q = 0; q < 4; ++q) {
+    uint8_t px[64];
+    om_bc7_decode_block(blocks + ((size_t)(ty[q] >> 2) * bw + (tx[q] >> 2)) * 16, px);
+    for (int c = 0; c < 4; ++c) f[q][c] = px[4 * ((ty[q] & 3) * 4 + (tx[q] & 3)) + c] / 255.0;
+  }
+  for (int c = 0; c < 4; ++c)
+    out[c] = (1.0 - fy) * ((1.0 - fx) * f[0][c] + fx * f[1][c]) + fy * ((1.0 - fx) * f[2][c] + fx * f[3][c]);
+}
+
+/* ---------------------------------------------------------------------- */
 /* Hybrid feature map decoder (Sec. 3.3, Eq. 4-5; Sec. 4)                  */
 /* ---------------------------------------------------------------------- */
 /*
@@ -776,9 +1263,10 @@ void om_fit_draw(uint64_t seed, int64_t step, int64_t first, int64_t n, int32_t 
  * input is [V_uvt, V_uv, V_ut, V_vt, gamma(t)] (16 values, Eq. 4) and the
  * MLP has two GELU hidden layers and a linear RGB output (Sec. 4).
  * Readings (the paper fixes none of these):
- *   - F_uv and every t-slice of F3D are four BC4 planes (the BC stand-in of
- *     this library for the paper's four-channel BC7), value P35/8925 as
- *     above, layout [h/4][w/4][4][8]; F3D slices are stored one after another;
+ *   - F_uv and every t-slice of F3D are either four BC4 planes (format 0),
+ *     value P35/8925 as above, layout [h/4][w/4][4][8], or the paper's
+ *     four-channel BC7 (format 1), value byte/255, layout [h/4][w/4][16];
+ *     F3D slices are stored one after another;
  *   - F_ut and F_vt are UNORM8 (the paper's 8-bit planes), value byte/255,
  *     layout [t][x][2] (x = u for F_ut, v for F_vt);
  *   - every axis uses the texel-centre convention; u and v follow the
@@ -797,6 +1285,7 @@ typedef struct {
   int32_t hidden;                           /* MLP 16 -> hidden -> hidden -> 3 */
   const double *w1, *b1, *w2, *b2, *w3, *b3;
   int32_t address_mode;
+  int32_t feat_format;                      /* F_uv and F3D: 0 four BC4 planes, 1 BC7 */
 } om_hybrid;
 
 /* Bilinear sample at (u, v) of four BC4 planes [h/4][w/4][4][8]. */
@@ -846,11 +1335,13 @@ void om_hybrid_features(const om_hybrid *m, double u, double v, double t, double
   int z0, z1;
   double fz, a[4], b[4];
   om_bilinear_setup(t, m->vol_t, 0, &z0, &z1, &fz);
-  const size_t slice = (size_t)(m->vol_h / 4) * (size_t)(m->vol_w / 4) * 32;
-  om_bc4x4_bilinear(m->vol_bc4 + (size_t)z0 * slice, m->vol_w, m->vol_h, u, v, m->address_mode, a);
-  om_bc4x4_bilinear(m->vol_bc4 + (size_t)z1 * slice, m->vol_w, m->vol_h, u, v, m->address_mode, b);
+  const int bc7 = m->feat_format == 1;
+  void (*sample)(const uint8_t *, int, int, double, double, int, double *) = bc7 ? om_bc7_bilinear : om_bc4x4_bilinear;
+  const size_t slice = (size_t)(m->vol_h / 4) * (size_t)(m->vol_w / 4) * (bc7 ? 16 : 32);
+  sample(m->vol_bc4 + (size_t)z0 * slice, m->vol_w, m->vol_h, u, v, m->address_mode, a);
+  sample(m->vol_bc4 + (size_t)z1 * slice, m->vol_w, m->vol_h, u, v, m->address_mode, b);
   for (int c = 0; c < 4; ++c) x[c] = (1.0 - fz) * a[c] + fz * b[c];
-  om_bc4x4_bilinear(m->uv_bc4, m->uv_w, m->uv_h, u, v, m->address_mode, x + 4);
+  sample(m->uv_bc4, m->uv_w, m->uv_h, u, v, m->address_mode, x + 4);
   om_u8x2_bilinear(m->ut, m->ut_w, m->ut_t, u, t, m->address_mode, x + 8);
   om_u8x2_bilinear(m->vt, m->vt_h, m->vt_t, v, t, m->address_mode, x + 10);
   om_hybrid_gamma(t, x + 12);

@@ -256,19 +256,36 @@ HYBRID_PROFILES = {"L": (16, 16), "M": (32, 16), "H": (64, 16), "M.64": (32, 64)
 HYBRID_TILE = dict(lm=128, uv=128, vol_t=12, ut=(64, 24), vt=(64, 24), n_lightmaps=26)
 
 
+def bc7_blocks(rng, w, h):
+    """Random BC7 blocks [h/4][w/4][16] with every mode equally likely: uniform
+    random bytes whose first byte is rewritten to a mode header (m zero bits, a
+    one, then random bits)."""
+    b = np.frombuffer(rng.bytes((h // 4) * (w // 4) * 16), dtype=np.uint8).reshape(h // 4, w // 4, 16).copy()
+    mode = rng.integers(0, 8, (h // 4, w // 4))
+    head = (b[:, :, 0].astype(np.int64) << (mode + 1)) | (1 << mode)
+    b[:, :, 0] = (head & 255).astype(np.uint8)
+    return b
+
+
 def hybrid_model(seed, lm_w, lm_h, uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, vt_h, vt_t, hidden,
-                 address_mode=0):
+                 address_mode=0, feat_format=0):
     """One hybrid model: uniform random BC4 blocks for F_uv and every F3D t-slice
-    (4 planes each), uniform random bytes for the UNORM8 planes F_ut [ut_t][ut_w][2]
-    and F_vt [vt_t][vt_h][2], and a Xavier MLP 16 -> hidden -> hidden -> 3."""
+    (4 planes each; feat_format 1: random BC7 blocks, keys uv_bc7 / vol_bc7),
+    uniform random bytes for the UNORM8 planes F_ut [ut_t][ut_w][2] and F_vt
+    [vt_t][vt_h][2], and a Xavier MLP 16 -> hidden -> hidden -> 3."""
     rng = _rng(seed)
-    uv = bc4_planes(rng, uv_w, uv_h, 4)
-    vol = np.stack([bc4_planes(rng, vol_w, vol_h, 4) for _ in range(vol_t)])
+    if feat_format == 1:
+        uv = bc7_blocks(rng, uv_w, uv_h)
+        vol = np.stack([bc7_blocks(rng, vol_w, vol_h) for _ in range(vol_t)])
+    else:
+        uv = bc4_planes(rng, uv_w, uv_h, 4)
+        vol = np.stack([bc4_planes(rng, vol_w, vol_h, 4) for _ in range(vol_t)])
     ut = np.frombuffer(rng.bytes(ut_t * ut_w * 2), dtype=np.uint8).reshape(ut_t, ut_w, 2).copy()
     vt = np.frombuffer(rng.bytes(vt_t * vt_h * 2), dtype=np.uint8).reshape(vt_t, vt_h, 2).copy()
-    m = dict(kind="hybrid", lm_w=lm_w, lm_h=lm_h, uv_w=uv_w, uv_h=uv_h, uv_bc4=uv,
-             vol_shape=(vol_t, vol_h, vol_w), vol_bc4=vol, ut=ut, vt=vt, hidden=hidden,
-             address_mode=address_mode)
+    key = "bc7" if feat_format == 1 else "bc4"
+    m = {"kind": "hybrid", "lm_w": lm_w, "lm_h": lm_h, "uv_w": uv_w, "uv_h": uv_h, f"uv_{key}": uv,
+         "vol_shape": (vol_t, vol_h, vol_w), f"vol_{key}": vol, "ut": ut, "vt": vt, "hidden": hidden,
+         "address_mode": address_mode, "feat_format": feat_format}
     m.update(xavier_mlp(rng, 16, hidden, 3))
     return m
 
