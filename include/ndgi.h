@@ -474,6 +474,52 @@ ndgi_status ndgi_bc_pack(const float *ea, const float *eb, const float *w, int32
                          int32_t feat_h, uint8_t *bc4_out, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* BC7 (Sec. 3.2: F_uv and F3D quantised to 8 bits and BC7-compressed)     */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * BC7 compression of an RGBA8 image rgba [h][w][4] (w, h multiples of 4;
+ * several images of one width may be stacked along h, e.g. the F3D slices)
+ * into blocks [h/4][w/4][16].  The encoder is deterministic and integer-only:
+ * per block it tries, in order, mode 6; mode 5 with rotation 0..3; mode 4
+ * with rotation 0..3 and index selector 0..1; mode 7 with partitions 0..63;
+ * and, when every alpha of the block is 255, modes 3, 1, 2 (partitions
+ * 0..63) and mode 0 (partitions 0..15), keeping the first candidate with the
+ * smallest squared error.  A candidate takes per subset (and per colour /
+ * alpha group in modes 4, 5) the per-channel minimum and maximum as
+ * endpoints, each coded by its nearest code (lowest code on ties; a p-bit
+ * minimises the summed squared error, 0 on ties), and gives every texel its
+ * nearest palette entry (lowest index on ties).  If sq_err is not NULL the
+ * total squared error (over all texels and channels, in 8-bit units) is
+ * added to the device uint64 it points to.  Buffers are device memory,
+ * 16-byte aligned.  Errors: NDGI_ERR_INVALID_ARG (sizes, NULL, alignment).
+ */
+ndgi_status ndgi_bc7_encode(const uint8_t *rgba, int32_t w, int32_t h, uint8_t *blocks, uint64_t *sq_err,
+                            void *stream);
+
+/*
+ * BC7 decode of blocks [h/4][w/4][16] to rgba [h][w][4] (the BPTC UNORM
+ * format: all eight modes, two- and three-subset partitions, rotation and
+ * index selector; the reserved mode decodes to 0).  Device buffers, 16-byte
+ * aligned.
+ */
+ndgi_status ndgi_bc7_decode(const uint8_t *blocks, int32_t w, int32_t h, uint8_t *rgba, void *stream);
+
+/*
+ * 8-bit quantisation of four BC4 planes (a fit's F_uv or F3D slice packed by
+ * ndgi_bc_pack with cs = 4): rgba [h][w][4] = round(255 * P35 / 8925) per
+ * texel and plane, the input of ndgi_bc7_encode.  bc4 [h/4][w/4][4][8].
+ */
+ndgi_status ndgi_bc4x4_to_rgba8(const uint8_t *bc4, int32_t w, int32_t h, uint8_t *rgba, void *stream);
+
+/*
+ * Test reference: the same decode done by the GPU's texture unit (a BC7
+ * view of the blocks, point-sampled at texel centres).  Allocates a CUDA
+ * array and synchronises the stream; not for the decode path.
+ */
+ndgi_status ndgi_debug_bc7_hw_decode(const uint8_t *blocks, int32_t w, int32_t h, uint8_t *rgba, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Differentiable fit (Sec. 3.4 BC simulation, Sec. 4 training)           */
 /* ---------------------------------------------------------------------- */
 
@@ -588,9 +634,11 @@ ndgi_status ndgi_encode_fit_batch(const ndgi_fit_params *params, int32_t n_model
  * gamma(t) = [sin pi t, cos pi t, sin 2 pi t, cos 2 pi t]) through two GELU
  * hidden layers (GELU(x) = x Phi(x), the exact erf form) to linear RGB.
  * Storage (this library's readings of what the paper leaves open):
- *   - F_uv and each t-slice of F3D are four BC4 planes (the BC stand-in of
- *     this library for the paper's four-channel BC7), block layout as
- *     ndgi_model_desc's bc4 with cs = 4; F3D slices follow one another;
+ *   - F_uv and each t-slice of F3D are either four BC4 planes
+ *     (NDGI_FEAT_BC4X4: block layout as ndgi_model_desc's bc4 with cs = 4,
+ *     value P35 / 8925) or the paper's four-channel BC7 (NDGI_FEAT_BC7: one
+ *     16-byte block per 4x4 texels, value byte / 255); F3D slices follow one
+ *     another;
  *   - F_ut and F_vt are UNORM8 (value byte / 255), layout [t][x][2];
  *   - texel-centre convention on every axis; u and v follow address_mode,
  *     the t axis (t in [0, 1]) clamps to its edge texels.
@@ -600,15 +648,19 @@ ndgi_status ndgi_encode_fit_batch(const ndgi_fit_params *params, int32_t n_model
  * A hybrid model; a view, every pointer device memory owned by the caller.
  *   lm_w, lm_h              lightmap (tile) size: page texels -> (u, v)
  *   uv_w, uv_h, uv_bc4      F_uv: sizes multiples of 4, [uv_h/4][uv_w/4][4][8]
+ *                           (BC7: [uv_h/4][uv_w/4][16])
  *   vol_w, vol_h, vol_t     F3D: slice sizes multiples of 4, vol_t slices,
- *   vol_bc4                 [vol_t][vol_h/4][vol_w/4][4][8]
+ *   vol_bc4                 [vol_t][vol_h/4][vol_w/4][4][8] (BC7: [..][16])
  *   ut_w, ut_t, ut          F_ut: [ut_t][ut_w][2] bytes
  *   vt_h, vt_t, vt          F_vt: [vt_t][vt_h][2] bytes
  *   hidden                  16, 32 or 64 (both hidden layers)
  *   w1 [16][hidden], b1, w2 [hidden][hidden], b2, w3 [hidden][3], b3: FP32 [in][out]
  *   address_mode            0 clamp, 1 mirrored repeat (u and v axes)
+ *   feat_format             NDGI_FEAT_BC4X4 (0) or NDGI_FEAT_BC7 (1): the
+ *                           block format of F_uv and F3D
  * uv_bc4 and vol_bc4 must be 16-byte aligned, ut and vt 2-byte aligned.
  */
+enum { NDGI_FEAT_BC4X4 = 0, NDGI_FEAT_BC7 = 1 };
 typedef struct {
   int32_t lm_w, lm_h;
   int32_t uv_w, uv_h;
@@ -622,6 +674,7 @@ typedef struct {
   int32_t hidden;
   const float *w1, *b1, *w2, *b2, *w3, *b3;
   int32_t address_mode;
+  int32_t feat_format;
 } ndgi_hybrid_desc;
 
 /*
@@ -717,7 +770,8 @@ ndgi_status ndgi_debug_gelu(const float *x, int64_t n, float *y, int32_t fast, v
  * Storage of a hybrid model in bits per lightmap texel, the paper's accounting
  * (Table "compression" and Table "config"): the BC-compressed maps F_uv and
  * F3D at bc_bits_per_texel bits per texel of all four channels (8 for BC7,
- * the paper's format; 16 for this library's four BC4 planes), F_ut and F_vt
+ * the paper's format; 16 for four BC4 planes; <= 0: the model's
+ * feat_format decides), F_ut and F_vt
  * at 8 bits per value, and the MLP's parameters at mlp_bits (16 for FP16),
  * divided by lm_w * lm_h * n_lightmaps texels.  Host only; -1 on a bad
  * argument.

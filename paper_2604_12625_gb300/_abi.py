@@ -33,13 +33,16 @@ class PageReq(C.Structure):
                 ("h", C.c_int32), ("t", C.c_float), ("dst_x", C.c_int32), ("dst_y", C.c_int32)]
 
 
+NDGI_FEAT_BC4X4, NDGI_FEAT_BC7 = 0, 1
+
+
 class HybridDesc(C.Structure):
     _fields_ = [("lm_w", C.c_int32), ("lm_h", C.c_int32), ("uv_w", C.c_int32), ("uv_h", C.c_int32),
                 ("uv_bc4", C.c_void_p), ("vol_w", C.c_int32), ("vol_h", C.c_int32), ("vol_t", C.c_int32),
                 ("vol_bc4", C.c_void_p), ("ut_w", C.c_int32), ("ut_t", C.c_int32), ("ut", C.c_void_p),
                 ("vt_h", C.c_int32), ("vt_t", C.c_int32), ("vt", C.c_void_p), ("hidden", C.c_int32),
                 ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
-                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32)]
+                ("w3", C.c_void_p), ("b3", C.c_void_p), ("address_mode", C.c_int32), ("feat_format", C.c_int32)]
 
 
 HFIT_TENSORS = ("uv_ea", "uv_eb", "uv_wt", "vol_ea", "vol_eb", "vol_wt", "ut", "vt", "w1", "b1", "w2", "b2", "w3",
@@ -109,6 +112,10 @@ SIGNATURES = [
     ("ndgi_pages_plan_set_fp8_dump", C.c_int, [_vp, _i32, _vp]),
     ("ndgi_decode_pages_static", C.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _i64, _i64, _vp, _vp]),
     ("ndgi_bc_pack", C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    ("ndgi_bc7_encode", C.c_int, [_vp, _i32, _i32, _vp, _vp, _vp]),
+    ("ndgi_bc7_decode", C.c_int, [_vp, _i32, _i32, _vp, _vp]),
+    ("ndgi_bc4x4_to_rgba8", C.c_int, [_vp, _i32, _i32, _vp, _vp]),
+    ("ndgi_debug_bc7_hw_decode", C.c_int, [_vp, _i32, _i32, _vp, _vp]),
     ("ndgi_fit_forward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("ndgi_fit_backward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),
     ("ndgi_encode_fit_workspace_size", _sz, [_vp, _vp]),

@@ -495,10 +495,17 @@ class HybridModel:
         self.vol_bc4 = _need(vol_bc4, torch.uint8, "vol_bc4")
         self.ut = _need(ut, torch.uint8, "ut")
         self.vt = _need(vt, torch.uint8, "vt")
-        bh, bw, four, eight = uv_bc4.shape
-        assert four == 4 and eight == 8
-        vt_, vbh, vbw, four, eight = vol_bc4.shape
-        assert four == 4 and eight == 8
+        # block format from the shape: four BC4 planes [..][4][8] or BC7 [..][16]
+        self.feat_format = A.NDGI_FEAT_BC7 if uv_bc4.dim() == 3 else A.NDGI_FEAT_BC4X4
+        if self.feat_format == A.NDGI_FEAT_BC7:
+            bh, bw, sixteen = uv_bc4.shape
+            vt_, vbh, vbw, sixteen2 = vol_bc4.shape
+            assert sixteen == 16 and sixteen2 == 16
+        else:
+            bh, bw, four, eight = uv_bc4.shape
+            assert four == 4 and eight == 8
+            vt_, vbh, vbw, four, eight = vol_bc4.shape
+            assert four == 4 and eight == 8
         self.w = {k: _need(v, torch.float32, k) for k, v in
                   dict(w1=w1, b1=b1, w2=w2, b2=b2, w3=w3, b3=b3).items()}
         self.hidden = w2.shape[0]
@@ -507,7 +514,7 @@ class HybridModel:
                                  vol_bc4.data_ptr(), ut.shape[1], ut.shape[0], ut.data_ptr(), vt.shape[1],
                                  vt.shape[0], vt.data_ptr(), self.hidden,
                                  *[self.w[k].data_ptr() for k in ("w1", "b1", "w2", "b2", "w3", "b3")],
-                                 self.address_mode)
+                                 self.address_mode, self.feat_format)
         self.ws = {}
 
     @classmethod
@@ -515,16 +522,17 @@ class HybridModel:
         """From a dict of numpy arrays (the layout of synth.hybrid_model)."""
         def t(a):
             return torch.from_numpy(np.ascontiguousarray(a)).to(device)
-        return cls(m["lm_w"], m["lm_h"], t(m["uv_bc4"]), t(m["vol_bc4"]), t(m["ut"]), t(m["vt"]), t(m["w1"]),
+        uv, vol = ("uv_bc7", "vol_bc7") if m.get("feat_format", 0) == 1 else ("uv_bc4", "vol_bc4")
+        return cls(m["lm_w"], m["lm_h"], t(m[uv]), t(m[vol]), t(m["ut"]), t(m["vt"]), t(m["w1"]),
                    t(m["b1"]), t(m["w2"]), t(m["b2"]), t(m["w3"]), t(m["b3"]), m.get("address_mode", 0))
 
     @classmethod
     def from_set(cls, s, device="cuda"):
         """All models of a stacked set (synth.hybrid_tile_set) as views into one device tensor per array."""
-        big = {k: torch.from_numpy(np.ascontiguousarray(s[k])).to(device)
-               for k in ("uv_bc4", "vol_bc4", "ut", "vt", "w1", "b1", "w2", "b2", "w3", "b3")}
-        return [cls(s["lm_w"], s["lm_h"], *[big[k][i] for k in ("uv_bc4", "vol_bc4", "ut", "vt", "w1", "b1", "w2",
-                                                               "b2", "w3", "b3")], s.get("address_mode", 0))
+        uv, vol = ("uv_bc7", "vol_bc7") if s.get("feat_format", 0) == 1 else ("uv_bc4", "vol_bc4")
+        keys = (uv, vol, "ut", "vt", "w1", "b1", "w2", "b2", "w3", "b3")
+        big = {k: torch.from_numpy(np.ascontiguousarray(s[k])).to(device) for k in keys}
+        return [cls(s["lm_w"], s["lm_h"], *[big[k][i] for k in keys], s.get("address_mode", 0))
                 for i in range(int(s["n_tiles"]))]
 
     def workspace(self, precision):
@@ -777,3 +785,50 @@ def ndgi_hybrid_encode_fit(state, targets, cfg, key_t=None, step_offset=0, ws=No
                                        C.byref(cfg), int(step_offset), _p(ws), ws.numel(), _p(loss_log),
                                        _stream(stream)))
     return ws, loss_log
+
+
+# --------------------------------------------------------------------------
+# BC7 (the paper's block format for F_uv and F3D)
+# --------------------------------------------------------------------------
+
+def ndgi_bc7_encode(rgba, out=None, sq_err=None, stream=None):
+    """BC7 blocks uint8 [h/4][w/4][16] of an RGBA8 image uint8 [h][w][4] (CUDA); sq_err (int64 [1], CUDA), when
+    given, accumulates the total squared error."""
+    _need(rgba, torch.uint8, "rgba")
+    h, w, four = rgba.shape
+    assert four == 4
+    if out is None:
+        out = torch.empty((h // 4, w // 4, 16), dtype=torch.uint8, device=rgba.device)
+    check(lib().ndgi_bc7_encode(_p(rgba), w, h, _p(out), _p(sq_err), _stream(stream)))
+    return out
+
+
+def ndgi_bc7_decode(blocks, out=None, stream=None):
+    """RGBA8 [h][w][4] of BC7 blocks uint8 [h/4][w/4][16] (CUDA)."""
+    _need(blocks, torch.uint8, "blocks")
+    bh, bw, sixteen = blocks.shape
+    assert sixteen == 16
+    if out is None:
+        out = torch.empty((bh * 4, bw * 4, 4), dtype=torch.uint8, device=blocks.device)
+    check(lib().ndgi_bc7_decode(_p(blocks), bw * 4, bh * 4, _p(out), _stream(stream)))
+    return out
+
+
+def ndgi_bc4x4_to_rgba8(bc4, out=None, stream=None):
+    """RGBA8 [h][w][4] = round(255 P35 / 8925) of four BC4 planes uint8 [h/4][w/4][4][8] (CUDA)."""
+    _need(bc4, torch.uint8, "bc4")
+    bh, bw, four, eight = bc4.shape
+    assert four == 4 and eight == 8
+    if out is None:
+        out = torch.empty((bh * 4, bw * 4, 4), dtype=torch.uint8, device=bc4.device)
+    check(lib().ndgi_bc4x4_to_rgba8(_p(bc4), bw * 4, bh * 4, _p(out), _stream(stream)))
+    return out
+
+
+def ndgi_debug_bc7_hw_decode(blocks, stream=None):
+    """RGBA8 [h][w][4] of BC7 blocks decoded by the GPU's texture unit (test reference)."""
+    _need(blocks, torch.uint8, "blocks")
+    bh, bw, sixteen = blocks.shape
+    out = torch.empty((bh * 4, bw * 4, 4), dtype=torch.uint8, device=blocks.device)
+    check(lib().ndgi_debug_bc7_hw_decode(_p(blocks), bw * 4, bh * 4, _p(out), _stream(stream)))
+    return out

@@ -20,6 +20,7 @@
 //     once per request and the CTA's four lanes split the request's tiles.
 #include <vector>
 
+#include "bc7.cuh"
 #include "hybrid.h"
 #include "tc_engine.cuh"
 
@@ -79,6 +80,39 @@ __device__ __forceinline__ void bc4x4_bilinear(const uint8_t* __restrict__ bc4, 
   for (int c = 0; c < 4; ++c) out[c] = gy * (gx * f[0][c] + fx * f[1][c]) + fy * (gx * f[2][c] + fx * f[3][c]);
 }
 
+// Bilinear sample of a BC7 map [h/4][bw][16] at taps (x0|x1, y0|y1): each tap
+// one texel decode of its block, value byte / 255.
+__device__ __forceinline__ void u8x4_unpack(uint32_t v, float* out) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out[c] = (float)((v >> (8 * c)) & 255u) * (1.0f / 255.0f);
+}
+
+__device__ __forceinline__ void bc7_bilinear(const uint8_t* __restrict__ blocks, int bw, int x0, int x1, int y0,
+                                             int y1, float fx, float fy, float* out) {
+  const int tx[4] = {x0, x1, x0, x1}, ty[4] = {y0, y0, y1, y1};
+  float f[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(blocks + ((size_t)(ty[q] >> 2) * bw + (tx[q] >> 2)) * 16));
+    u8x4_unpack(bc7_texel(b, ((ty[q] & 3) << 2) | (tx[q] & 3)), f[q]);
+  }
+  const float gx = 1.0f - fx, gy = 1.0f - fy;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out[c] = gy * (gx * f[0][c] + fx * f[1][c]) + fy * (gx * f[2][c] + fx * f[3][c]);
+}
+
+// A four-channel map (F_uv or an F3D slice) in the model's block format.
+__device__ __forceinline__ void map4_bilinear(const DevHybrid& m, const uint8_t* __restrict__ base, int bw, int x0,
+                                              int x1, int y0, int y1, float fx, float fy, const uint2* lut,
+                                              float* out) {
+  if (m.bc7) bc7_bilinear(base, bw, x0, x1, y0, y1, fx, fy, out);
+  else bc4x4_bilinear(base, bw, x0, x1, y0, y1, fx, fy, lut, out);
+}
+
+__device__ __forceinline__ size_t vol_slice_bytes(const DevHybrid& m) {
+  return (size_t)(m.vol_h / 4) * (size_t)(m.vol_w / 4) * (m.bc7 ? 16 : 32);
+}
+
 // Bilinear sample of a two-channel UNORM8 plane [ny][nx][2] (one 16-bit load per tap).
 __device__ __forceinline__ void u8x2_bilinear(const uint8_t* __restrict__ p, int nx, int x0, int x1, int y0, int y1,
                                               float fx, float fy, float* out) {
@@ -104,16 +138,16 @@ __device__ __forceinline__ void hybrid_features(const DevHybrid& m, float u, flo
   axis_setup(u, m.vol_w, mode, x0, x1, fx);
   axis_setup(v, m.vol_h, mode, y0, y1, fy);
   axis_setup(t, m.vol_t, 0, z0, z1, fz);
-  const size_t slice = (size_t)(m.vol_h / 4) * (size_t)(m.vol_w / 4) * 32;
+  const size_t slice = vol_slice_bytes(m);
   float a[4], b[4];
-  bc4x4_bilinear(m.vol + (size_t)z0 * slice, m.vol_w / 4, x0, x1, y0, y1, fx, fy, lut, a);
-  bc4x4_bilinear(m.vol + (size_t)z1 * slice, m.vol_w / 4, x0, x1, y0, y1, fx, fy, lut, b);
+  map4_bilinear(m, m.vol + (size_t)z0 * slice, m.vol_w / 4, x0, x1, y0, y1, fx, fy, lut, a);
+  map4_bilinear(m, m.vol + (size_t)z1 * slice, m.vol_w / 4, x0, x1, y0, y1, fx, fy, lut, b);
   const float gz = 1.0f - fz;
 #pragma unroll
   for (int c = 0; c < 4; ++c) x[c] = gz * a[c] + fz * b[c];
   axis_setup(u, m.uv_w, mode, x0, x1, fx);
   axis_setup(v, m.uv_h, mode, y0, y1, fy);
-  bc4x4_bilinear(m.uv, m.uv_w / 4, x0, x1, y0, y1, fx, fy, lut, x + 4);
+  map4_bilinear(m, m.uv, m.uv_w / 4, x0, x1, y0, y1, fx, fy, lut, x + 4);
   axis_setup(u, m.ut_w, mode, x0, x1, fx);
   axis_setup(t, m.ut_t, 0, y0, y1, fy);
   u8x2_bilinear(m.ut, m.ut_w, x0, x1, y0, y1, fx, fy, x + 8);
@@ -508,6 +542,15 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
 // F3D texel (x, y) of slices z0 and z1 blended at fz, all four channels.
 __device__ __forceinline__ float4 vol_texel(const DevHybrid& m, int x, int y, int z0, int z1, float fz,
                                             const uint2* lut) {
+  if (m.bc7) {
+    const size_t slice = vol_slice_bytes(m), off = ((size_t)(y >> 2) * (m.vol_w / 4) + (x >> 2)) * 16;
+    const int p = ((y & 3) << 2) | (x & 3);
+    float a[4], b[4];
+    u8x4_unpack(bc7_texel(__ldg(reinterpret_cast<const uint4*>(m.vol + (size_t)z0 * slice + off)), p), a);
+    u8x4_unpack(bc7_texel(__ldg(reinterpret_cast<const uint4*>(m.vol + (size_t)z1 * slice + off)), p), b);
+    const float gz = 1.0f - fz;
+    return make_float4(gz * a[0] + fz * b[0], gz * a[1] + fz * b[1], gz * a[2] + fz * b[2], gz * a[3] + fz * b[3]);
+  }
   const size_t slice = (size_t)(m.vol_h / 4) * (size_t)(m.vol_w / 4) * 32;
   const size_t off = ((size_t)(y >> 2) * (m.vol_w / 4) + (x >> 2)) * 32;
   const uint32_t shift = 16u + 3u * (uint32_t)(((y & 3) << 2) | (x & 3));
@@ -631,14 +674,22 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
           x[2] = gy * (gx * q00.z + fx * q10.z) + fy * (gx * q01.z + fx * q11.z);
           x[3] = gy * (gx * q00.w + fx * q10.w) + fy * (gx * q01.w + fx * q11.w);
         } else {
-          const size_t slice = (size_t)(m.vol_h / 4) * (size_t)(m.vol_w / 4) * 32;
+          const size_t slice = vol_slice_bytes(m);
           float a[4], b[4];
-          bc4x4_bilinear(m.vol + (size_t)z0 * slice, m.vol_w / 4, cx.v0, cx.v1, cy.v0, cy.v1, cx.vf, cy.vf, lut, a);
-          bc4x4_bilinear(m.vol + (size_t)z1 * slice, m.vol_w / 4, cx.v0, cx.v1, cy.v0, cy.v1, cx.vf, cy.vf, lut, b);
+          map4_bilinear(m, m.vol + (size_t)z0 * slice, m.vol_w / 4, cx.v0, cx.v1, cy.v0, cy.v1, cx.vf, cy.vf, lut, a);
+          map4_bilinear(m, m.vol + (size_t)z1 * slice, m.vol_w / 4, cx.v0, cx.v1, cy.v0, cy.v1, cx.vf, cy.vf, lut, b);
 #pragma unroll
           for (int j = 0; j < 4; ++j) x[j] = (1.0f - fz) * a[j] + fz * b[j];
         }
-        if (cx.uf == 0.0f && cy.uf == 0.0f) {   // one tap (its weight is 1)
+        if (m.bc7) {
+          if (cx.uf == 0.0f && cy.uf == 0.0f) {
+            const uint4 blk = __ldg(reinterpret_cast<const uint4*>(m.uv + ((size_t)(cy.u0 >> 2) * (m.uv_w / 4) +
+                                                                         (cx.u0 >> 2)) * 16));
+            u8x4_unpack(bc7_texel(blk, ((cy.u0 & 3) << 2) | (cx.u0 & 3)), x + 4);
+          } else {
+            bc7_bilinear(m.uv, m.uv_w / 4, cx.u0, cx.u1, cy.u0, cy.u1, cx.uf, cy.uf, x + 4);
+          }
+        } else if (cx.uf == 0.0f && cy.uf == 0.0f) {   // one tap (its weight is 1)
           const uint4* line = reinterpret_cast<const uint4*>(m.uv + ((size_t)(cy.u0 >> 2) * (m.uv_w / 4) +
                                                                      (cx.u0 >> 2)) * 32);
           const uint4 a = __ldg(line), b = __ldg(line + 1);
@@ -806,6 +857,8 @@ ndgi_status check_hybrid_dims(const ndgi_hybrid_desc* m, const char* who) {
     return set_error(NDGI_ERR_UNSUPPORTED, "%s: hidden width %d not built (16, 32, 64)", who, m->hidden);
   if (m->address_mode != 0 && m->address_mode != 1)
     return set_error(NDGI_ERR_INVALID_ARG, "%s: address_mode must be 0 or 1", who);
+  if (m->feat_format != NDGI_FEAT_BC4X4 && m->feat_format != NDGI_FEAT_BC7)
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: feat_format must be NDGI_FEAT_BC4X4 or NDGI_FEAT_BC7", who);
   return NDGI_OK;
 }
 
@@ -815,7 +868,7 @@ ndgi_status check_hybrid(const ndgi_hybrid_desc* m, const char* who) {
   if (!m->uv_bc4 || !m->vol_bc4 || !m->ut || !m->vt || !m->w1 || !m->b1 || !m->w2 || !m->b2 || !m->w3 || !m->b3)
     return set_error(NDGI_ERR_INVALID_ARG, "%s: a model array is NULL", who);
   if (!is_aligned(m->uv_bc4, 16) || !is_aligned(m->vol_bc4, 16) || !is_aligned(m->ut, 2) || !is_aligned(m->vt, 2))
-    return set_error(NDGI_ERR_INVALID_ARG, "%s: BC4 arrays must be 16-byte and UNORM8 planes 2-byte aligned", who);
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: BC arrays must be 16-byte and UNORM8 planes 2-byte aligned", who);
   return NDGI_OK;
 }
 
@@ -844,6 +897,7 @@ DevHybrid to_dev_hybrid(const ndgi_hybrid_desc& d, const void* ws) {
   m.w3 = d.w3;
   m.b3 = d.b3;
   m.address_mode = d.address_mode;
+  m.bc7 = d.feat_format == NDGI_FEAT_BC7;
   m.ws = static_cast<unsigned char*>(const_cast<void*>(ws));
   return m;
 }
@@ -1032,7 +1086,8 @@ ndgi_status ndgi_debug_gelu(const float* x, int64_t n, float* y, int32_t fast, v
 
 double ndgi_model_bpp(const ndgi_hybrid_desc* model, int32_t n_lightmaps, int32_t bc_bits_per_texel,
                       int32_t mlp_bits) {
-  if (!model || n_lightmaps <= 0 || bc_bits_per_texel <= 0 || mlp_bits <= 0) return -1.0;
+  if (!model || n_lightmaps <= 0 || mlp_bits <= 0) return -1.0;
+  if (bc_bits_per_texel <= 0) bc_bits_per_texel = model->feat_format == NDGI_FEAT_BC7 ? 8 : 16;
   if (model->lm_w <= 0 || model->lm_h <= 0 || model->uv_w <= 0 || model->uv_h <= 0 || model->vol_w <= 0 ||
       model->vol_h <= 0 || model->vol_t <= 0 || model->ut_w <= 0 || model->ut_t <= 0 || model->vt_h <= 0 ||
       model->vt_t <= 0 || model->hidden <= 0)

@@ -18,6 +18,7 @@ struct DevHybrid {
   int hidden;
   const float *w1, *b1, *w2, *b2, *w3, *b3;
   int address_mode;
+  int bc7;             // F_uv and F3D are BC7 blocks (else four BC4 planes)
   unsigned char* ws;   // FP16/BF16 image and error/debug words, or null (FP32)
 };
 
