@@ -506,7 +506,7 @@ HFIT_KEYS = ("uv_ea", "uv_eb", "uv_wt", "vol_ea", "vol_eb", "vol_wt", "ut", "vt"
 class _HFitParams(C.Structure):
     _fields_ = [(k, C.c_int32) for k in ("lm_w", "lm_h", "uv_w", "uv_h", "vol_w", "vol_h", "vol_t", "ut_w", "ut_t",
                                          "vt_h", "vt_t", "hidden", "address_mode")] + \
-               [(k, C.c_void_p) for k in HFIT_KEYS]
+               [(k, C.c_void_p) for k in HFIT_KEYS] + [("shared_w", C.c_int32)]
 
 
 class _HFitGrads(C.Structure):
@@ -514,7 +514,8 @@ class _HFitGrads(C.Structure):
 
 
 class HFitParams:
-    """Hybrid-fit parameters (dict from synth.hybrid_fit_init) in oracle form."""
+    """Hybrid-fit parameters (dict from synth.hybrid_fit_init) in oracle form.  A weight tensor uv_wt of shape
+    [uv_h/4][uv_w/4][16] (vol_wt [vol_t][..][16]) selects Eq. 7's weight per texel shared by the channels."""
 
     def __init__(self, p):
         self.a = {k: _c(p[k], np.float32) for k in HFIT_KEYS}
@@ -523,7 +524,7 @@ class HFitParams:
         vt_t, vt_h, _ = self.a["vt"].shape
         self.s = _HFitParams(int(p["lm_w"]), int(p["lm_h"]), int(p["uv_w"]), int(p["uv_h"]), vw, vh, vt_, ut_w, ut_t,
                              vt_h, vt_t, int(p["hidden"]), int(p.get("address_mode", 0)),
-                             *[_ptr(self.a[k]) for k in HFIT_KEYS])
+                             *[_ptr(self.a[k]) for k in HFIT_KEYS], int(self.a["uv_wt"].ndim == 3))
 
 
 def hfit_forward(p, uvt, relaxed=False):

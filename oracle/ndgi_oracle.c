@@ -998,7 +998,11 @@ void om_bc7_decode(const uint8_t *blocks, int32_t w, int32_t h, uint8_t *rgba) {
  *     separate endpoints and indices; the other modes code all their
  *     channels (RGBA for 6 and 7, RGB for 0..3) together;
  *   - per subset and group, endpoint 0 is the per-channel minimum and
- *     endpoint 1 the per-channel maximum of the subset's texels, each coded
+ *     endpoint 1 the per-channel maximum of the subset's texels, except that
+ *     a channel whose integer covariance n sum(x_c x_r) - sum(x_c) sum(x_r)
+ *     with the group's channel r of largest range (lowest index on ties) is
+ *     negative takes its maximum at endpoint 0 and minimum at endpoint 1
+ *     (the box diagonal along the data); each endpoint is coded
  *     by the nearest code per channel: without p-bits q = argmin
  *     |expand(q, n) - v| (lowest q on ties); with a p-bit per endpoint, q(p)
  *     likewise for p = 0 and 1 at n + 1 bits and p the one with the smaller
@@ -1070,6 +1074,31 @@ int64_t om_bc7_candidate(const uint8_t *x0, int mode, int part, int rot, int isb
             if (x[p][c] < lo[c]) lo[c] = x[p][c];
             if (x[p][c] > hi[c]) hi[c] = x[p][c];
           }
+      }
+      /* orient the box diagonal along the data: the channel r of largest range (lowest c on ties) runs from
+       * its minimum to its maximum; another channel runs the other way when its covariance with r is negative */
+      int r = g_lo[g];
+      for (int c = g_lo[g]; c < g_hi[g]; ++c)
+        if (hi[c] - lo[c] > hi[r] - lo[r]) r = c;
+      int cnt = 0, sr = 0;
+      for (int p = 0; p < 16; ++p)
+        if (om_bc7_subset(M->ns, part, p) == s) {
+          ++cnt;
+          sr += x[p][r];
+        }
+      for (int c = g_lo[g]; c < g_hi[g]; ++c) {
+        if (c == r) continue;
+        int sc = 0, scr = 0;
+        for (int p = 0; p < 16; ++p)
+          if (om_bc7_subset(M->ns, part, p) == s) {
+            sc += x[p][c];
+            scr += x[p][c] * x[p][r];
+          }
+        if (cnt * scr - sc * sr < 0) {
+          const int t = lo[c];
+          lo[c] = hi[c];
+          hi[c] = t;
+        }
       }
       const int *tgt[2] = {lo, hi};
       int val[2][4];
@@ -1504,6 +1533,13 @@ void om_tile_metrics(const double *pred, const double *ref, const uint8_t *mask,
  * (om_hybrid_features, om_hybrid_mlp) on those values.  Reading: no additive
  * noise (the paper's quantisation noise during training is a regulariser this
  * deterministic fit leaves out).
+ *
+ * With shared_w = 1 the maps follow Eq. 7 literally: one weight per texel,
+ * shared by the block's four channels (w [..][16]), simulated as BC7's
+ * single-subset interpolation: A = q255(ea), B = q255(eb), k = q15(w), BC7's
+ * 4-bit weight W = W4[k], value ((64 - W) A + W B + 32) >> 6 over 255; the
+ * backward takes dea = 1 - W/64, deb = W/64 and dw = (B - A)/255 per channel,
+ * the weight's gradient summed over the channels.
  */
 typedef struct {
   int32_t lm_w, lm_h, uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, vt_h, vt_t, hidden, address_mode;
@@ -1511,6 +1547,7 @@ typedef struct {
   const float *vol_ea, *vol_eb, *vol_wt;    /* [vol_t][vol_h/4][vol_w/4][4], same, [..][4][16]  */
   const float *ut, *vt;                     /* [ut_t][ut_w][2], [vt_t][vt_h][2]                   */
   const float *w1, *b1, *w2, *b2, *w3, *b3;
+  int32_t shared_w;                         /* 1: Eq. 7's weight per texel, shared by the channels */
 } om_hfit_params;
 
 typedef struct {
@@ -1518,14 +1555,23 @@ typedef struct {
 } om_hfit_grads;
 
 /* STE value of texel p of block entry bc (channel included) and its chain-rule factors. */
+static int64_t om_hw_index(int shared, int64_t bc, int p) { return (shared ? bc / 4 : bc) * 16 + p; }
+
 static double om_hsim(const float *ea, const float *eb, const float *w, int64_t bc, int p, int relaxed,
-                      double *dea, double *deb, double *dw) {
-  const float a = ea[bc], b = eb[bc], ww = w[bc * 16 + p];
+                      int shared, double *dea, double *deb, double *dw) {
+  const float a = ea[bc], b = eb[bc], ww = w[om_hw_index(shared, bc, p)];
   if (relaxed) {
     *dea = 1.0 - (double)ww;
     *deb = (double)ww;
     *dw = (double)b - (double)a;
     return (1.0 - (double)ww) * a + (double)ww * b;
+  }
+  if (shared) {
+    const int A = om_q255(a), B = om_q255(b), W = OM_BC7_W4[om_quant(ww, 15.0f)];
+    *dea = 1.0 - W / 64.0;
+    *deb = W / 64.0;
+    *dw = B / 255.0 - A / 255.0;
+    return (double)(((64 - W) * A + W * B + 32) >> 6) / 255.0;
   }
   const int A = om_q255(a), B = om_q255(b), k = om_q7(ww);
   *dea = 1.0 - k / 7.0;
@@ -1597,8 +1643,8 @@ static int om_hfit_taps(const om_hfit_params *P, double u, double v, double t, o
 
 static double om_htap_value(const om_hfit_params *P, const om_htap *h, int relaxed, double *d0, double *d1,
                             double *d2) {
-  if (h->map == 0) return om_hsim(P->vol_ea, P->vol_eb, P->vol_wt, h->e, h->p, relaxed, d0, d1, d2);
-  if (h->map == 1) return om_hsim(P->uv_ea, P->uv_eb, P->uv_wt, h->e, h->p, relaxed, d0, d1, d2);
+  if (h->map == 0) return om_hsim(P->vol_ea, P->vol_eb, P->vol_wt, h->e, h->p, relaxed, P->shared_w, d0, d1, d2);
+  if (h->map == 1) return om_hsim(P->uv_ea, P->uv_eb, P->uv_wt, h->e, h->p, relaxed, P->shared_w, d0, d1, d2);
   *d0 = 1.0;
   return (double)(h->map == 2 ? P->ut : P->vt)[h->e];
 }
@@ -1700,11 +1746,11 @@ double om_hfit_backward(const om_hfit_params *P, const float *uvt, const double 
         if (h->map == 0) {
           G->vol_ea[h->e] += d0 * g;
           G->vol_eb[h->e] += d1 * g;
-          G->vol_wt[h->e * 16 + h->p] += d2 * g;
+          G->vol_wt[om_hw_index(P->shared_w, h->e, h->p)] += d2 * g;
         } else if (h->map == 1) {
           G->uv_ea[h->e] += d0 * g;
           G->uv_eb[h->e] += d1 * g;
-          G->uv_wt[h->e * 16 + h->p] += d2 * g;
+          G->uv_wt[om_hw_index(P->shared_w, h->e, h->p)] += d2 * g;
         } else {
           (h->map == 2 ? G->ut : G->vt)[h->e] += g;
         }

@@ -290,12 +290,12 @@ def hybrid_model(seed, lm_w, lm_h, uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, 
     return m
 
 
-def hybrid_tile_model(seed, profile="M.64", address_mode=0):
+def hybrid_tile_model(seed, profile="M.64", address_mode=0, feat_format=0):
     """A 128 x 128 tile model of one of the paper's profiles (L, M, H, M.64)."""
     r, hidden = HYBRID_PROFILES[profile]
     T = HYBRID_TILE
     return hybrid_model(seed, T["lm"], T["lm"], T["uv"], T["uv"], r, r, T["vol_t"], T["ut"][0], T["ut"][1],
-                        T["vt"][0], T["vt"][1], hidden, address_mode)
+                        T["vt"][0], T["vt"][1], hidden, address_mode, feat_format)
 
 
 def hybrid_tile_requests(seed, n_tiles, n_req, slots_x=64, page=128):
@@ -310,22 +310,28 @@ def hybrid_tile_requests(seed, n_tiles, n_req, slots_x=64, page=128):
     return req
 
 
-def hybrid_tile_set(seed, n_tiles, profile="M.64"):
+def _hybrid_keys(feat_format):
+    blk = ("uv_bc7", "vol_bc7") if feat_format == 1 else ("uv_bc4", "vol_bc4")
+    return blk + ("ut", "vt", "w1", "b1", "w2", "b2", "w3", "b3")
+
+
+def hybrid_tile_set(seed, n_tiles, profile="M.64", feat_format=0):
     """n_tiles tile models of one profile, stacked along a leading axis (model i
     is hybrid_tile_model(seed * 100003 + i, profile)); see hybrid_tile_of."""
-    ms = [hybrid_tile_model(seed * 100003 + i, profile) for i in range(n_tiles)]
-    out = {k: np.stack([m[k] for m in ms]) for k in ("uv_bc4", "vol_bc4", "ut", "vt", "w1", "b1", "w2", "b2",
-                                                    "w3", "b3")}
+    ms = [hybrid_tile_model(seed * 100003 + i, profile, feat_format=feat_format) for i in range(n_tiles)]
+    out = {k: np.stack([m[k] for m in ms]) for k in _hybrid_keys(feat_format)}
     out.update({k: ms[0][k] for k in ("kind", "lm_w", "lm_h", "uv_w", "uv_h", "vol_shape", "hidden",
-                                      "address_mode")})
+                                      "address_mode", "feat_format")})
     out["n_tiles"] = n_tiles
     return out
 
 
 def hybrid_tile_of(s, i):
     """Model i of a hybrid_tile_set as a single-model dict."""
-    m = {k: s[k][i] for k in ("uv_bc4", "vol_bc4", "ut", "vt", "w1", "b1", "w2", "b2", "w3", "b3")}
+    fmt = s.get("feat_format", 0)
+    m = {k: s[k][i] for k in _hybrid_keys(fmt)}
     m.update({k: s[k] for k in ("kind", "lm_w", "lm_h", "uv_w", "uv_h", "vol_shape", "hidden", "address_mode")})
+    m["feat_format"] = fmt
     return m
 
 
@@ -391,18 +397,20 @@ def lightmap_mask(seed, width, height, n_islands=12, fill=0.7):
 
 
 def hybrid_fit_init(seed, lm_w, lm_h, uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, vt_h, vt_t, hidden,
-                    address_mode=0):
+                    address_mode=0, shared_w=False):
     """Initial parameters of a hybrid-decoder fit: endpoints and weights U(0,1) per block and channel of F_uv
-    and of every F3D slice, F_ut / F_vt values U(0,1), Xavier MLP 16 -> hidden -> hidden -> 3."""
+    and of every F3D slice (shared_w: one weight per texel for all four channels, Eq. 7), F_ut / F_vt values
+    U(0,1), Xavier MLP 16 -> hidden -> hidden -> 3."""
     rng = _rng(seed)
     ubh, ubw, vbh, vbw = uv_h // 4, uv_w // 4, vol_h // 4, vol_w // 4
+    wc = () if shared_w else (4,)
     p = dict(lm_w=lm_w, lm_h=lm_h, uv_w=uv_w, uv_h=uv_h, vol_shape=(vol_t, vol_h, vol_w), hidden=hidden,
              address_mode=address_mode,
              uv_ea=rng.random((ubh, ubw, 4), dtype=np.float32), uv_eb=rng.random((ubh, ubw, 4), dtype=np.float32),
-             uv_wt=rng.random((ubh, ubw, 4, 16), dtype=np.float32),
+             uv_wt=rng.random((ubh, ubw) + wc + (16,), dtype=np.float32),
              vol_ea=rng.random((vol_t, vbh, vbw, 4), dtype=np.float32),
              vol_eb=rng.random((vol_t, vbh, vbw, 4), dtype=np.float32),
-             vol_wt=rng.random((vol_t, vbh, vbw, 4, 16), dtype=np.float32),
+             vol_wt=rng.random((vol_t, vbh, vbw) + wc + (16,), dtype=np.float32),
              ut=rng.random((ut_t, ut_w, 2), dtype=np.float32), vt=rng.random((vt_t, vt_h, 2), dtype=np.float32))
     p.update(xavier_mlp(rng, 16, hidden, 3))
     return p

@@ -67,3 +67,78 @@ def test_backward_matches_finite_differences_relaxed():
         an = g[k].reshape(-1)[idx]
         assert np.linalg.norm(an - fd) <= 2e-3 * max(np.linalg.norm(an), 1e-9), k
         assert np.all(np.abs(an - fd) <= 2e-3 * np.abs(an) + 1e-6), k
+
+
+# --------------------------------------------------------------------------
+# Eq. 7 with one weight per texel shared by the channels (the BC7 simulation)
+# --------------------------------------------------------------------------
+
+def shared_problem(seed=0, hidden=16):
+    p = synth.hybrid_fit_init(seed, 32, 32, 32, 32, 8, 8, 6, 16, 5, 16, 5, hidden, shared_w=True)
+    rng = np.random.default_rng(seed + 1)
+    q = synth.random_queries(seed + 2, 300)
+    q[:10, :2] = rng.uniform(-0.3, 1.3, (10, 2)).astype(np.float32)
+    return p, q, rng.normal(size=(300, 3))
+
+
+def mode6_blocks(ea, eb, w):
+    """BC7 mode-6 blocks [..][16] of 8-bit even endpoints 255 ea, 255 eb (codes / 2, p-bits 0) and 4-bit
+    indices 15 w, written field by field (the anchor texel's index kept below 8 by swapping the endpoints)."""
+    from test_oracle_bc7 import write_block
+    lead = ea.shape[:-1]
+    out = np.zeros(lead + (16,), np.uint8)
+    for i in np.ndindex(*lead):
+        A = np.rint(ea[i] * 255).astype(int)
+        B = np.rint(eb[i] * 255).astype(int)
+        k = np.rint(w[i] * 15).astype(int)
+        if k[0] >= 8:
+            A, B, k = B, A, 15 - k
+        out[i] = write_block(6, 0, 0, 0, [[[int(v) for v in A // 2], [int(v) for v in B // 2]]], [[0, 0]],
+                             [int(v) for v in k], [0] * 16)
+    return out
+
+
+def test_shared_weight_forward_equals_bc7_decode():
+    p, q, _ = shared_problem(5)
+    rng = np.random.default_rng(6)
+    for key in ("uv", "vol"):
+        ea, eb, w = p[f"{key}_ea"], p[f"{key}_eb"], p[f"{key}_wt"]
+        p[f"{key}_ea"] = (2 * rng.integers(0, 128, ea.shape) / 255).astype(np.float32)
+        p[f"{key}_eb"] = (2 * rng.integers(0, 128, eb.shape) / 255).astype(np.float32)
+        p[f"{key}_wt"] = (rng.integers(0, 16, w.shape) / 15).astype(np.float32)
+    p["ut"] = (np.round(p["ut"] * 255) / 255).astype(np.float32)
+    p["vt"] = (np.round(p["vt"] * 255) / 255).astype(np.float32)
+    m = dict(kind="hybrid", lm_w=32, lm_h=32, uv_w=32, uv_h=32, vol_shape=p["vol_shape"], hidden=p["hidden"],
+             address_mode=0, feat_format=1,
+             uv_bc7=mode6_blocks(p["uv_ea"], p["uv_eb"], p["uv_wt"]),
+             vol_bc7=mode6_blocks(p["vol_ea"], p["vol_eb"], p["vol_wt"]),
+             ut=np.round(p["ut"] * 255).astype(np.uint8), vt=np.round(p["vt"] * 255).astype(np.uint8),
+             **{k: p[k] for k in ("w1", "b1", "w2", "b2", "w3", "b3")})
+    y_fit = oracle.hfit_forward(p, q)
+    y_dec = oracle.hybrid_decode_points(m, q)
+    assert np.allclose(y_fit, y_dec, rtol=0, atol=1e-6)
+    assert not np.allclose(y_fit, oracle.hfit_forward(p, q, relaxed=True), atol=1e-6)
+
+
+def test_shared_weight_backward_matches_finite_differences():
+    p, q, tgt = shared_problem(7)
+    loss, g = oracle.hfit_backward(p, q, tgt, relaxed=True)
+    rng = np.random.default_rng(8)
+    h = 1e-3
+    for k in ("uv_ea", "uv_eb", "uv_wt", "vol_ea", "vol_eb", "vol_wt", "w1"):
+        flat = p[k].reshape(-1)
+        assert g[k].shape == p[k].shape
+        idx = rng.choice(flat.size, 12, replace=False)
+        fd = np.zeros(idx.size)
+        for j, i in enumerate(idx):
+            vals = []
+            for s in (+1, -1):
+                pp = dict(p)
+                arr = flat.copy()
+                arr[i] = np.float32(float(flat[i]) + s * h)
+                pp[k] = arr.reshape(p[k].shape)
+                vals.append((np.mean((oracle.hfit_forward(pp, q, relaxed=True) - tgt) ** 2), float(arr[i])))
+            fd[j] = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+        an = g[k].reshape(-1)[idx]
+        assert np.linalg.norm(an - fd) <= 2e-3 * max(np.linalg.norm(an), 1e-9), k
+        assert np.all(np.abs(an - fd) <= 2e-3 * np.abs(an) + 1e-6), k
