@@ -107,8 +107,9 @@ def lib():
             L.om_hybrid_decode_points.argtypes = [vp, vp, i64, vp, vp, C.c_int]
             L.om_hybrid_decode_pages.argtypes = [vp, i32, vp, i32, vp, i64, i64, i32, C.c_int]
             L.om_tile_metrics.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
-            L.om_hfit_forward.argtypes = [vp, vp, i64, C.c_int, vp]
-            L.om_hfit_backward.argtypes = [vp, vp, vp, i64, C.c_int, vp]
+            L.om_hfit_forward.argtypes = [vp, vp, i64, C.c_int, vp, vp]
+            L.om_hfit_backward.argtypes = [vp, vp, vp, vp, i64, C.c_int, vp]
+            L.om_fit_noise.argtypes = [C.c_uint64, i64, i64, i64, f64, vp]
             L.om_hfit_backward.restype = f64
             L.om_bc7_decode_block.argtypes = [vp, vp]
             L.om_bc7_decode.argtypes = [vp, i32, i32, vp]
@@ -119,6 +120,7 @@ def lib():
             L.om_bc7_encode.argtypes = [vp, i32, i32, vp, C.c_int]
             L.om_bc7_encode.restype = i64
             L.om_bc7_subset.argtypes = [C.c_int, C.c_int, C.c_int]
+            L.om_bc_sim7_rgba8.argtypes = [vp, vp, vp, i32, i32, vp]
             L.om_bc7_anchor.argtypes = [C.c_int, C.c_int, C.c_int]
             L.om_splitmix64_next.argtypes = [C.c_uint64]
             L.om_splitmix64_next.restype = C.c_uint64
@@ -527,23 +529,33 @@ class HFitParams:
                              *[_ptr(self.a[k]) for k in HFIT_KEYS], int(self.a["uv_wt"].ndim == 3))
 
 
-def hfit_forward(p, uvt, relaxed=False):
-    """rgb [n][3] of the hybrid fit's straight-through (or relaxed) forward at queries uvt [n][3]."""
+def fit_noise(seed, step, n, alpha, first=0):
+    """The training-time quantisation noise [n][12] of the hybrid fit's samples first.. of one step."""
+    out = np.zeros((n, 12), np.float64)
+    lib().om_fit_noise(C.c_uint64(seed), int(step), int(first), int(n), float(alpha), _ptr(out))
+    return out
+
+
+def hfit_forward(p, uvt, relaxed=False, noise=None):
+    """rgb [n][3] of the hybrid fit's straight-through (or relaxed) forward at queries uvt [n][3] (with the
+    inputs' additive noise [n][12] when given)."""
     P = p if isinstance(p, HFitParams) else HFitParams(p)
     q = _c(uvt, np.float32).reshape(-1, 3)
     y = np.zeros((q.shape[0], 3), np.float64)
-    lib().om_hfit_forward(C.byref(P.s), _ptr(q), q.shape[0], int(relaxed), _ptr(y))
+    nz = None if noise is None else _c(noise, np.float64)
+    lib().om_hfit_forward(C.byref(P.s), _ptr(q), q.shape[0], int(relaxed), _ptr(nz), _ptr(y))
     return y
 
 
-def hfit_backward(p, uvt, target, relaxed=False):
+def hfit_backward(p, uvt, target, relaxed=False, noise=None):
     """(loss, gradients dict) of the MSE at queries uvt against target [n][3] (FP64)."""
     P = p if isinstance(p, HFitParams) else HFitParams(p)
     q = _c(uvt, np.float32).reshape(-1, 3)
     tg = _c(target, np.float64).reshape(-1, 3)
     g = {k: np.zeros(P.a[k].shape, np.float64) for k in HFIT_KEYS}
     G = _HFitGrads(*[_ptr(g[k]) for k in HFIT_KEYS])
-    loss = lib().om_hfit_backward(C.byref(P.s), _ptr(q), _ptr(tg), q.shape[0], int(relaxed), C.byref(G))
+    nz = None if noise is None else _c(noise, np.float64)
+    loss = lib().om_hfit_backward(C.byref(P.s), _ptr(q), _ptr(tg), _ptr(nz), q.shape[0], int(relaxed), C.byref(G))
     return loss, g
 
 
@@ -598,3 +610,13 @@ def bc7_subset(ns, part, p):
 
 def bc7_anchor(ns, part, s):
     return int(lib().om_bc7_anchor(int(ns), int(part), int(s)))
+
+
+def bc_sim7_rgba8(ea, eb, w):
+    """RGBA8 [h][w][4] of a shared-weight BC simulation: ea, eb [h/4][w/4][4], w [h/4][w/4][16] (float32)."""
+    a, b, ww = _c(ea, np.float32), _c(eb, np.float32), _c(w, np.float32)
+    bw = a.shape[-2]
+    bh = a.size // (bw * 4)                 # leading axes (F3D slices) stacked along the height
+    out = np.zeros((bh * 4, bw * 4, 4), np.uint8)
+    lib().om_bc_sim7_rgba8(_ptr(a), _ptr(b), _ptr(ww), bw * 4, bh * 4, _ptr(out))
+    return out

@@ -1263,6 +1263,23 @@ int64_t om_bc7_encode(const uint8_t *rgba, int32_t w, int32_t h, uint8_t *blocks
   return total;
 }
 
+/* 8-bit export of a shared-weight BC simulation (the hybrid fit with shared_w):
+ * texel value ((64 - W) A + W B + 32) >> 6, A = q255(ea), B = q255(eb), W the
+ * 4-bit BC7 weight of index q15(w); ea, eb [h/4][w/4][4], w [h/4][w/4][16]. */
+void om_bc_sim7_rgba8(const float *ea, const float *eb, const float *w, int32_t width, int32_t height,
+                      uint8_t *rgba) {
+  const int bw = width / 4;
+  for (int y = 0; y < height; ++y)
+    for (int x = 0; x < width; ++x) {
+      const int64_t b = (int64_t)(y / 4) * bw + x / 4;
+      const int W = OM_BC7_W4[om_quant(w[b * 16 + (y % 4) * 4 + x % 4], 15.0f)];
+      for (int c = 0; c < 4; ++c) {
+        const int A = om_q255(ea[b * 4 + c]), B = om_q255(eb[b * 4 + c]);
+        rgba[((int64_t)y * width + x) * 4 + c] = (uint8_t)(((64 - W) * A + W * B + 32) >> 6);
+      }
+    }
+}
+
 /* Bilinear sample at (u, v) of a BC7 map [h/4][w/4][16]: four decoded taps, value byte / 255. */
 static void om_bc7_bilinear(const uint8_t *blocks, int w, int h, double u, double v, int mode, double *out) {
   int x0, x1, y0, y1;
@@ -1554,6 +1571,26 @@ typedef struct {
   double *uv_ea, *uv_eb, *uv_wt, *vol_ea, *vol_eb, *vol_wt, *ut, *vt, *w1, *b1, *w2, *b2, *w3, *b3;
 } om_hfit_grads;
 
+/*
+ * Training-time quantisation noise (Sec. 3.2: V' = V + U(-0.5, 0.5) alpha on
+ * the sampled vectors; alpha = 1/256 for the 8-bit maps).  Counter-based, so
+ * that any implementation draws the same numbers: for sample i of global step
+ * s and input k < 12, z = splitmix64(b + k g) with g = 0x9E3779B97F4A7C15 and
+ * b = (seed XOR 0x6E6F697365) + 12 ((s << 32) + i) g (wrapping), and the
+ * noise is alpha ((z >> 40) 2^-24 - 1/2).  noise [n][12] for samples first..
+ */
+void om_fit_noise(uint64_t seed, int64_t step, int64_t first, int64_t n, double alpha, double *noise) {
+  const uint64_t g = 0x9E3779B97F4A7C15ull;
+  for (int64_t i = 0; i < n; ++i) {
+    const uint64_t ctr = ((uint64_t)step << 32) + (uint64_t)(first + i);
+    const uint64_t b = (seed ^ 0x6E6F697365ull) + 12ull * ctr * g;
+    for (int k = 0; k < 12; ++k) {
+      const uint64_t z = om_splitmix64(b + (uint64_t)k * g);
+      noise[12 * i + k] = alpha * (ldexp((double)(z >> 40), -24) - 0.5);
+    }
+  }
+}
+
 /* STE value of texel p of block entry bc (channel included) and its chain-rule factors. */
 static int64_t om_hw_index(int shared, int64_t bc, int p) { return (shared ? bc / 4 : bc) * 16 + p; }
 
@@ -1650,15 +1687,15 @@ static double om_htap_value(const om_hfit_params *P, const om_htap *h, int relax
 }
 
 /* One sample's forward: inputs x[16], pre-activations, activations, RGB. */
-static void om_hfit_sample(const om_hfit_params *P, double u, double v, double t, int relaxed, double *x,
-                           double *z1, double *h1, double *z2, double *h2, double *y) {
+static void om_hfit_sample(const om_hfit_params *P, double u, double v, double t, int relaxed, const double *noise,
+                           double *x, double *z1, double *h1, double *z2, double *h2, double *y) {
   om_htap tap[16][8];
   int cnt[16];
   om_hfit_taps(P, u, v, t, tap, cnt);
   for (int k = 0; k < 12; ++k) {
     double acc = 0.0, d0, d1, d2;
     for (int i = 0; i < cnt[k]; ++i) acc += tap[k][i].wt * om_htap_value(P, &tap[k][i], relaxed, &d0, &d1, &d2);
-    x[k] = acc;
+    x[k] = acc + (noise ? noise[k] : 0.0);   /* V' = V + noise (the training-time quantisation noise) */
   }
   om_hybrid_gamma(t, x + 12);
   const int H = P->hidden;
@@ -1686,22 +1723,25 @@ static double om_gelu_grad(double z) {
   return 0.5 * (1.0 + erf(z / sqrt(2.0))) + z * exp(-0.5 * z * z) / sqrt(2.0 * 3.14159265358979323846);
 }
 
-void om_hfit_forward(const om_hfit_params *P, const float *uvt, int64_t n, int relaxed, double *rgb) {
+void om_hfit_forward(const om_hfit_params *P, const float *uvt, int64_t n, int relaxed, const double *noise,
+                     double *rgb) {
   for (int64_t s = 0; s < n; ++s) {
     double x[16], z1[256], h1[256], z2[256], h2[256];
-    om_hfit_sample(P, uvt[3 * s], uvt[3 * s + 1], uvt[3 * s + 2], relaxed, x, z1, h1, z2, h2, rgb + 3 * s);
+    om_hfit_sample(P, uvt[3 * s], uvt[3 * s + 1], uvt[3 * s + 2], relaxed, noise ? noise + 12 * s : NULL, x, z1,
+                   h1, z2, h2, rgb + 3 * s);
   }
 }
 
 /* Analytic FP64 gradient of the MSE (accumulated into G; callers zero it); returns the loss. */
-double om_hfit_backward(const om_hfit_params *P, const float *uvt, const double *target, int64_t n, int relaxed,
+double om_hfit_backward(const om_hfit_params *P, const float *uvt, const double *target, const double *noise,
+                        int64_t n, int relaxed,
                         om_hfit_grads *G) {
   const int H = P->hidden;
   double loss = 0.0;
   for (int64_t s = 0; s < n; ++s) {
     const double u = uvt[3 * s], v = uvt[3 * s + 1], t = uvt[3 * s + 2];
     double x[16], z1[256], h1[256], z2[256], h2[256], y[3], dy[3], gz2[256], gz1[256], gx[16];
-    om_hfit_sample(P, u, v, t, relaxed, x, z1, h1, z2, h2, y);
+    om_hfit_sample(P, u, v, t, relaxed, noise ? noise + 12 * s : NULL, x, z1, h1, z2, h2, y);
     for (int o = 0; o < 3; ++o) {
       const double d = y[o] - target[3 * s + o];
       loss += d * d;

@@ -9,6 +9,7 @@ applied to the decoder of Sec. 3.3):
   tensor and elementwise with a 1e-6 floor.
 """
 import numpy as np
+import pytest
 
 import oracle
 import synth
@@ -142,3 +143,47 @@ def test_shared_weight_backward_matches_finite_differences():
         an = g[k].reshape(-1)[idx]
         assert np.linalg.norm(an - fd) <= 2e-3 * max(np.linalg.norm(an), 1e-9), k
         assert np.all(np.abs(an - fd) <= 2e-3 * np.abs(an) + 1e-6), k
+
+
+# --------------------------------------------------------------------------
+# Training-time quantisation noise on the sampled vectors (Sec. 3.2)
+# --------------------------------------------------------------------------
+
+def test_noise_draws_are_uniform_and_deterministic():
+    a = 1.0 / 256
+    nz = oracle.fit_noise(5, 3, 20_000, a)
+    assert nz.shape == (20_000, 12)
+    assert np.all(nz >= -a / 2) and np.all(nz < a / 2)
+    assert np.array_equal(nz, oracle.fit_noise(5, 3, 20_000, a))
+    assert np.array_equal(nz[100:200], oracle.fit_noise(5, 3, 100, a, first=100))
+    assert not np.array_equal(nz, oracle.fit_noise(5, 4, 20_000, a))
+    stats = pytest.importorskip("scipy.stats")
+    for k in (0, 5, 11):
+        assert stats.kstest(nz[:, k] / a + 0.5, "uniform").pvalue > 1e-3
+    assert abs(np.corrcoef(nz[:, 0], nz[:, 1])[0, 1]) < 0.05
+
+
+def test_noise_is_an_additive_input_shift():
+    """A constant noise c on input k is a shift of the first layer's bias by c W1[k] (a linear layer)."""
+    p, q, tgt = problem(9)
+    c, k = 0.01, 5
+    nz = np.zeros((q.shape[0], 12))
+    nz[:, k] = c
+    pb = dict(p)
+    pb["b1"] = (p["b1"].astype(np.float64) + c * p["w1"][k].astype(np.float64)).astype(np.float32)
+    y_n = oracle.hfit_forward(p, q, noise=nz)
+    assert np.allclose(y_n, oracle.hfit_forward(pb, q), rtol=0, atol=1e-6)   # b1 stored in FP32
+    assert not np.allclose(y_n, oracle.hfit_forward(p, q), atol=1e-6)
+    # the gradient with a random noise array matches finite differences of the same noisy loss
+    nz = oracle.fit_noise(2, 0, q.shape[0], 1.0 / 256)
+    _, g = oracle.hfit_backward(p, q, tgt, relaxed=True, noise=nz)
+    flat = p["uv_ea"].reshape(-1)
+    for i in (0, 7, 33):
+        vals = []
+        for s in (+1, -1):
+            arr = flat.copy()
+            arr[i] = np.float32(float(flat[i]) + s * 1e-3)
+            pp = dict(p, uv_ea=arr.reshape(p["uv_ea"].shape))
+            vals.append((np.mean((oracle.hfit_forward(pp, q, relaxed=True, noise=nz) - tgt) ** 2), float(arr[i])))
+        fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+        assert abs(g["uv_ea"].reshape(-1)[i] - fd) <= 2e-3 * abs(fd) + 1e-6
