@@ -121,6 +121,7 @@ def lib():
             L.om_bc7_encode.restype = i64
             L.om_bc7_subset.argtypes = [C.c_int, C.c_int, C.c_int]
             L.om_bc_sim7_rgba8.argtypes = [vp, vp, vp, i32, i32, vp]
+            L.om_bc7_pack_sim.argtypes = [vp, vp, vp, i64, vp]
             L.om_bc7_anchor.argtypes = [C.c_int, C.c_int, C.c_int]
             L.om_splitmix64_next.argtypes = [C.c_uint64]
             L.om_splitmix64_next.restype = C.c_uint64
@@ -619,4 +620,13 @@ def bc_sim7_rgba8(ea, eb, w):
     bh = a.size // (bw * 4)                 # leading axes (F3D slices) stacked along the height
     out = np.zeros((bh * 4, bw * 4, 4), np.uint8)
     lib().om_bc_sim7_rgba8(_ptr(a), _ptr(b), _ptr(ww), bw * 4, bh * 4, _ptr(out))
+    return out
+
+
+def bc7_pack_sim(ea, eb, w):
+    """Exact BC7 mode-6 blocks [..][16] of a shared-weight BC simulation (ea, eb [..][4], w [..][16])."""
+    a, b, ww = _c(ea, np.float32), _c(eb, np.float32), _c(w, np.float32)
+    nb = a.size // 4
+    out = np.zeros(a.shape[:-1] + (16,), np.uint8)
+    lib().om_bc7_pack_sim(_ptr(a), _ptr(b), _ptr(ww), nb, _ptr(out))
     return out

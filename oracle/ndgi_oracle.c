@@ -1263,9 +1263,25 @@ int64_t om_bc7_encode(const uint8_t *rgba, int32_t w, int32_t h, uint8_t *blocks
   return total;
 }
 
+/* Mode-6 endpoint: p-bit and 8-bit values E[4] of the endpoint e[4] (the hybrid fit's shared-weight simulation, below). */
+static int om_mode6_endpoint(const float *e, int *E) {
+  int q[4], odd = 0;
+  for (int c = 0; c < 4; ++c) {
+    q[c] = om_q255(e[c]);
+    odd += q[c] & 1;
+  }
+  const int p = odd > 2;
+  for (int c = 0; c < 4; ++c) {
+    const int h = (q[c] - p) >> 1;
+    E[c] = 2 * (h < 0 ? 0 : h) + p;
+  }
+  return p;
+}
+
 /* 8-bit export of a shared-weight BC simulation (the hybrid fit with shared_w):
- * texel value ((64 - W) A + W B + 32) >> 6, A = q255(ea), B = q255(eb), W the
- * 4-bit BC7 weight of index q15(w); ea, eb [h/4][w/4][4], w [h/4][w/4][16]. */
+ * texel value ((64 - W) A + W B + 32) >> 6 with the mode-6 endpoints A, B of
+ * ea, eb and W the 4-bit BC7 weight of index q15(w); ea, eb [h/4][w/4][4],
+ * w [h/4][w/4][16]. */
 void om_bc_sim7_rgba8(const float *ea, const float *eb, const float *w, int32_t width, int32_t height,
                       uint8_t *rgba) {
   const int bw = width / 4;
@@ -1273,11 +1289,46 @@ void om_bc_sim7_rgba8(const float *ea, const float *eb, const float *w, int32_t 
     for (int x = 0; x < width; ++x) {
       const int64_t b = (int64_t)(y / 4) * bw + x / 4;
       const int W = OM_BC7_W4[om_quant(w[b * 16 + (y % 4) * 4 + x % 4], 15.0f)];
-      for (int c = 0; c < 4; ++c) {
-        const int A = om_q255(ea[b * 4 + c]), B = om_q255(eb[b * 4 + c]);
-        rgba[((int64_t)y * width + x) * 4 + c] = (uint8_t)(((64 - W) * A + W * B + 32) >> 6);
-      }
+      int A[4], B[4];
+      om_mode6_endpoint(ea + b * 4, A);
+      om_mode6_endpoint(eb + b * 4, B);
+      for (int c = 0; c < 4; ++c) rgba[((int64_t)y * width + x) * 4 + c] = (uint8_t)(((64 - W) * A[c] + W * B[c] + 32) >> 6);
     }
+}
+
+/* Exact BC7 mode-6 blocks of a shared-weight BC simulation: endpoint codes
+ * E_c >> 1 and p-bits of the mode-6 endpoints, indices q15(w); where texel
+ * 0's index is 8 or more the endpoints (with their p-bits) swap and every
+ * index k becomes 15 - k (the 4-bit weights are symmetric).  ea, eb
+ * [nb][4], w [nb][16] -> blocks [nb][16]. */
+void om_bc7_pack_sim(const float *ea, const float *eb, const float *w, int64_t nb, uint8_t *blocks) {
+  for (int64_t b = 0; b < nb; ++b) {
+    int A[4], B[4], k[16];
+    int pa = om_mode6_endpoint(ea + 4 * b, A), pb = om_mode6_endpoint(eb + 4 * b, B);
+    for (int p = 0; p < 16; ++p) k[p] = om_quant(w[16 * b + p], 15.0f);
+    if (k[0] >= 8) {
+      for (int c = 0; c < 4; ++c) {
+        const int t = A[c];
+        A[c] = B[c];
+        B[c] = t;
+      }
+      const int t = pa;
+      pa = pb;
+      pb = t;
+      for (int p = 0; p < 16; ++p) k[p] = 15 - k[p];
+    }
+    uint8_t *blk = blocks + 16 * b;
+    memset(blk, 0, 16);
+    int pos = 0;
+    om_bits_put(blk, &pos, 7, 1 << 6);
+    for (int c = 0; c < 4; ++c) {
+      om_bits_put(blk, &pos, 7, A[c] >> 1);
+      om_bits_put(blk, &pos, 7, B[c] >> 1);
+    }
+    om_bits_put(blk, &pos, 1, pa);
+    om_bits_put(blk, &pos, 1, pb);
+    for (int p = 0; p < 16; ++p) om_bits_put(blk, &pos, p == 0 ? 3 : 4, k[p]);
+  }
 }
 
 /* Bilinear sample at (u, v) of a BC7 map [h/4][w/4][16]: four decoded taps, value byte / 255. */
@@ -1552,11 +1603,16 @@ void om_tile_metrics(const double *pred, const double *ref, const uint8_t *mask,
  * deterministic fit leaves out).
  *
  * With shared_w = 1 the maps follow Eq. 7 literally: one weight per texel,
- * shared by the block's four channels (w [..][16]), simulated as BC7's
- * single-subset interpolation: A = q255(ea), B = q255(eb), k = q15(w), BC7's
- * 4-bit weight W = W4[k], value ((64 - W) A + W B + 32) >> 6 over 255; the
- * backward takes dea = 1 - W/64, deb = W/64 and dw = (B - A)/255 per channel,
- * the weight's gradient summed over the channels.
+ * shared by the block's four channels (w [..][16]), simulated as BC7 mode 6
+ * (one subset, RGBA endpoints of 7 bits plus a p-bit shared by the
+ * endpoint's four channels, 4-bit indices): an endpoint's channels are first
+ * quantised to 8 bits, q255(e_c); its p-bit is their majority parity (0 on a
+ * 2-2 tie) and each channel keeps the nearest value of that parity, the lower
+ * on a tie: E_c = 2 max(0, (q255(e_c) - p) >> 1) + p; k = q15(w) and W =
+ * W4[k]; value ((64 - W) A + W B + 32) >> 6 over 255.  The backward takes
+ * dea = 1 - W/64, deb = W/64 and dw = (B - A)/255 per channel, the weight's
+ * gradient summed over the channels.  Such maps are exactly mode-6 blocks
+ * (om_bc7_pack_sim).
  */
 typedef struct {
   int32_t lm_w, lm_h, uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, vt_h, vt_t, hidden, address_mode;
@@ -1594,9 +1650,11 @@ void om_fit_noise(uint64_t seed, int64_t step, int64_t first, int64_t n, double 
 /* STE value of texel p of block entry bc (channel included) and its chain-rule factors. */
 static int64_t om_hw_index(int shared, int64_t bc, int p) { return (shared ? bc / 4 : bc) * 16 + p; }
 
+
 static double om_hsim(const float *ea, const float *eb, const float *w, int64_t bc, int p, int relaxed,
                       int shared, double *dea, double *deb, double *dw) {
   const float a = ea[bc], b = eb[bc], ww = w[om_hw_index(shared, bc, p)];
+  const int64_t b4 = bc & ~(int64_t)3;   /* the block's first channel */
   if (relaxed) {
     *dea = 1.0 - (double)ww;
     *deb = (double)ww;
@@ -1604,7 +1662,10 @@ static double om_hsim(const float *ea, const float *eb, const float *w, int64_t 
     return (1.0 - (double)ww) * a + (double)ww * b;
   }
   if (shared) {
-    const int A = om_q255(a), B = om_q255(b), W = OM_BC7_W4[om_quant(ww, 15.0f)];
+    int EA[4], EB[4];
+    om_mode6_endpoint(ea + b4, EA);
+    om_mode6_endpoint(eb + b4, EB);
+    const int A = EA[bc - b4], B = EB[bc - b4], W = OM_BC7_W4[om_quant(ww, 15.0f)];
     *dea = 1.0 - W / 64.0;
     *deb = W / 64.0;
     *dw = B / 255.0 - A / 255.0;

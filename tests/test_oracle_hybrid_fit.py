@@ -187,3 +187,40 @@ def test_noise_is_an_additive_input_shift():
             vals.append((np.mean((oracle.hfit_forward(pp, q, relaxed=True, noise=nz) - tgt) ** 2), float(arr[i])))
         fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
         assert abs(g["uv_ea"].reshape(-1)[i] - fd) <= 2e-3 * abs(fd) + 1e-6
+
+
+def test_shared_weight_maps_are_exact_mode6_blocks():
+    """The shared-weight simulation's texels are exactly the BC7 decode of its mode-6 pack, on random
+    parameters, and the fit's forward equals the hybrid decode of the packed model."""
+    p, q, _ = shared_problem(11)
+    for key in ("uv", "vol"):
+        ea, eb, w = p[f"{key}_ea"], p[f"{key}_eb"], p[f"{key}_wt"]
+        blocks = oracle.bc7_pack_sim(ea, eb, w)
+        assert blocks.shape == ea.shape[:-1] + (16,)
+        assert np.all((blocks[..., 0] & 0x7F) == 64)                     # mode 6 everywhere
+        bh, bw = ea.shape[-3], ea.shape[-2]
+        dec = oracle.bc7_decode(blocks.reshape(-1, bw, 16), 4 * bw, blocks.size // (16 * bw) * 4)
+        assert np.array_equal(dec, oracle.bc_sim7_rgba8(ea, eb, w))
+    p["ut"] = (np.round(p["ut"] * 255) / 255).astype(np.float32)
+    p["vt"] = (np.round(p["vt"] * 255) / 255).astype(np.float32)
+    m = dict(kind="hybrid", lm_w=32, lm_h=32, uv_w=32, uv_h=32, vol_shape=p["vol_shape"], hidden=p["hidden"],
+             address_mode=0, feat_format=1,
+             uv_bc7=oracle.bc7_pack_sim(p["uv_ea"], p["uv_eb"], p["uv_wt"]),
+             vol_bc7=oracle.bc7_pack_sim(p["vol_ea"], p["vol_eb"], p["vol_wt"]),
+             ut=np.round(p["ut"] * 255).astype(np.uint8), vt=np.round(p["vt"] * 255).astype(np.uint8),
+             **{k: p[k] for k in ("w1", "b1", "w2", "b2", "w3", "b3")})
+    assert np.allclose(oracle.hfit_forward(p, q), oracle.hybrid_decode_points(m, q), rtol=0, atol=1e-6)
+
+
+def test_mode6_endpoint_parity_rule():
+    """An endpoint keeps the 8-bit values of its majority parity exactly and moves the others by one level."""
+    p, _, _ = shared_problem(12)
+    ea = p["uv_ea"][:1, :1].copy()
+    ea[0, 0] = np.float32([10, 12, 14, 15]) / 255              # three even: p = 0, the odd 15 -> 14
+    eb = p["uv_eb"][:1, :1].copy()
+    eb[0, 0] = np.float32([11, 13, 200, 0]) / 255              # 2-2 tie: p = 0; 11 -> 10, 13 -> 12
+    w = np.zeros((1, 1, 16), np.float32)
+    w[0, 0, 1] = 1.0                                           # texel 1 at index 15 (endpoint 1)
+    rgba = oracle.bc_sim7_rgba8(ea, eb, w)
+    assert list(rgba[0, 0]) == [10, 12, 14, 14]
+    assert list(rgba[0, 1]) == [10, 12, 200, 0]
