@@ -46,7 +46,7 @@ KERNEL_SOURCES = {
     "k_points_ws": ("tc_points.cu",) + _COMMON_SOURCES,
     "k_pages_tc": ("tc_decode.cu",) + _COMMON_SOURCES,
     "k_pages_ws": ("tc_decode.cu",) + _COMMON_SOURCES,
-    "k_hybrid_pages_tc": ("hybrid.cu", "hybrid.h") + _COMMON_SOURCES,
+    "k_hybrid_pages_tc": ("hybrid.cu", "hybrid.h", "bc7.cuh") + _COMMON_SOURCES,
 }
 NCU_TRAFFIC = {
     "k_points_ws": {"src": "dc313c105005e444", "read": 134407936, "write": 81475584, "units": 1 << 23,
@@ -453,54 +453,99 @@ def bench_fit_batch(args, ndgi, torch):
 
 
 HYBRID_FIT_WORKLOAD = ("hybrid fit: one M.64 tile model (F_uv 128^2x4 and F3D 32^2x12x4 as BC endpoints + weights "
-                       "under the straight-through BC simulation, F_ut/F_vt 64x24x2, GELU MLP 16-64-64-3) against the "
-                       "top-left 128^2 crop of the fit workload's 24 keyframe targets; 1000 Adam steps of 2^16 "
-                       "samples at t ~ U[0,1) (targets interpolated between keyframes); then F_uv and F3D packed to "
-                       "BC4, F_ut/F_vt to UNORM8, and every keyframe decoded (FP32) and scored")
+                       "under the straight-through BC simulation: four BC4 planes with a weight per channel, or "
+                       "Eq. 7's weight per texel shared by the channels read as BC7's single-subset interpolation; "
+                       "F_ut/F_vt 64x24x2, GELU MLP 16-64-64-3) against the top-left 128^2 crop of the fit "
+                       "workload's 24 keyframe targets; 1000 Adam steps of 2^16 samples at t ~ U[0,1) (targets "
+                       "interpolated between keyframes); then the maps quantised to 8 bits and BC7-compressed, "
+                       "F_ut/F_vt to UNORM8, and every keyframe decoded (FP32) and scored")
 
 
-def bench_hybrid_fit(args, ndgi, torch):
-    """The hybrid decoder's fit (ndgi_hybrid_encode_fit), then its packed model decoded at every keyframe."""
-    T, side = 24, 128
-    tg_np = np.ascontiguousarray(c3_targets()[:, :side, :side])
-    tg = torch.from_numpy(tg_np).cuda()
-    vol_side, vol_t, hidden = 32, 12, 64
-    p = synth.hybrid_fit_init(21, side, side, side, side, vol_side, vol_side, vol_t, 64, 24, 64, 24, hidden)
-    steps = max(20, min(1000, args.fit_steps // 2))
-    batch = 1 << 16
-    warm = ndgi.HybridFitState.from_arrays(p)
-    ndgi.ndgi_hybrid_encode_fit(warm, tg, ndgi.fit_config(steps=2, batch=batch, seed=1))
-    st = ndgi.HybridFitState.from_arrays(p)
-    cfg = ndgi.fit_config(steps=steps, batch=batch, lr=1e-2, freeze_steps=steps // 10,
-                          loss_every=max(1, steps // 5), seed=22)
-    torch.cuda.synchronize()
+def _bc7_export(ndgi, torch, uv8, vol8, vol_t, vol_side):
+    """BC7 blocks of the 8-bit maps (F3D slices stacked along the height), their squared error and encode time."""
+    sq = torch.zeros(2, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    _, log = ndgi.ndgi_hybrid_encode_fit(st, tg, cfg)
+    uv7 = ndgi.ndgi_bc7_encode(uv8, sq_err=sq[0:1])
+    vol7 = ndgi.ndgi_bc7_encode(vol8, sq_err=sq[1:2]).reshape(vol_t, vol_side // 4, vol_side // 4, 16).contiguous()
     e1.record(stream)
     e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    log = log.cpu().numpy()
-    t = st.t
-    uv = ndgi.ndgi_bc_pack(t["uv_ea"], t["uv_eb"], t["uv_wt"])
-    vol = torch.stack([ndgi.ndgi_bc_pack(t["vol_ea"][k].contiguous(), t["vol_eb"][k].contiguous(),
-                                         t["vol_wt"][k].contiguous()) for k in range(vol_t)]).contiguous()
-    ut = torch.round(t["ut"] * 255).to(torch.uint8)
-    vt = torch.round(t["vt"] * 255).to(torch.uint8)
-    hm = ndgi.HybridModel(side, side, uv, vol, ut, vt, *[t[k] for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
-    keys = np.arange(T, dtype=np.float32) / T
-    q = torch.from_numpy(synth.texel_queries(side, side, keys)).cuda()
-    rgb = ndgi.ndgi_hybrid_decode_points(hm, q.reshape(-1, 3), "fp32").reshape(T, side, side, 3)
+    n = uv8.numel() + vol8.numel()
+    return uv7, vol7, float(np.sqrt(float(sq.sum().item()) / n)), e0.elapsed_time(e1), n // 64
+
+
+def bench_hybrid_fit(args, ndgi, torch):
+    """The hybrid decoder's fit (ndgi_hybrid_encode_fit) with both BC simulations, then the paper's export (8-bit
+    maps BC7-compressed) decoded at every keyframe."""
+    T, side = 24, 128
+    tg = torch.from_numpy(np.ascontiguousarray(c3_targets()[:, :side, :side])).cuda()
     ref = tg.float()
     rng = float(ref.max() - ref.min())
-    mse = float(((rgb - ref) ** 2).mean())
-    return {"workload": HYBRID_FIT_WORKLOAD.replace("1000 Adam", f"{steps} Adam"), "steps": steps,
-            "ms_per_step": ms / steps, "samples_per_s": steps * batch / (ms / 1e3),
-            "loss_first": float(log[0]), "loss_last": float(log[-1]),
-            "psnr_db_fit": float(10 * np.log10(rng * rng / max(log[-1], 1e-30))),
-            "psnr_db_packed_decode": float(10 * np.log10(rng * rng / max(mse, 1e-30))),
-            "device_check": check_status(ndgi)}
+    vol_side, vol_t, hidden = 32, 12, 64
+    steps = max(20, min(1000, args.fit_steps // 2))
+    batch = 1 << 16
+    keys = np.arange(T, dtype=np.float32) / T
+    q = torch.from_numpy(synth.texel_queries(side, side, keys)).cuda().reshape(-1, 3)
+    mlp = ("w1", "b1", "w2", "b2", "w3", "b3")
+
+    def psnr(hm):
+        rgb = ndgi.ndgi_hybrid_decode_points(hm, q, "fp32").reshape(T, side, side, 3)
+        return float(10 * np.log10(rng * rng / max(float(((rgb - ref) ** 2).mean()), 1e-30)))
+
+    out = {"workload": HYBRID_FIT_WORKLOAD.replace("1000 Adam", f"{steps} Adam"), "steps": steps}
+    for name, shared, noise in (("bc4x4", False, 0.0), ("eq7_shared_weight", True, 0.0),
+                                ("eq7_shared_weight_noise", True, 1.0 / 256)):
+        p = synth.hybrid_fit_init(21, side, side, side, side, vol_side, vol_side, vol_t, 64, 24, 64, 24, hidden,
+                                  shared_w=shared)
+        warm = ndgi.HybridFitState.from_arrays(p)
+        ndgi.ndgi_hybrid_encode_fit(warm, tg, ndgi.fit_config(steps=2, batch=batch, seed=1))
+        st = ndgi.HybridFitState.from_arrays(p)
+        cfg = ndgi.fit_config(steps=steps, batch=batch, lr=1e-2, freeze_steps=steps // 10,
+                              loss_every=max(1, steps // 5), seed=22, noise_alpha=noise)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, log = ndgi.ndgi_hybrid_encode_fit(st, tg, cfg)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        log = log.cpu().numpy()
+        t = st.t
+        ut = torch.round(t["ut"] * 255).to(torch.uint8)
+        vt = torch.round(t["vt"] * 255).to(torch.uint8)
+        entry = {"noise_alpha": noise, "ms_per_step": ms / steps, "samples_per_s": steps * batch / (ms / 1e3),
+                 "loss_first": float(log[0]), "loss_last": float(log[-1]),
+                 "psnr_db_fit": float(10 * np.log10(rng * rng / max(log[-1], 1e-30)))}
+        if shared:
+            # exact: the maps are mode-6 blocks
+            hm6 = ndgi.HybridModel(side, side, ndgi.ndgi_bc7_pack_sim(t["uv_ea"], t["uv_eb"], t["uv_wt"]),
+                                   ndgi.ndgi_bc7_pack_sim(t["vol_ea"], t["vol_eb"], t["vol_wt"]), ut, vt,
+                                   *[t[k] for k in mlp])
+            entry["psnr_db_mode6_pack_decode"] = psnr(hm6)
+            entry["bpp_bc7"] = ndgi.ndgi_model_bpp(hm6, 1, 0, 16)
+            uv8 = ndgi.ndgi_bc_sim7_to_rgba8(t["uv_ea"], t["uv_eb"], t["uv_wt"])
+            vol8 = ndgi.ndgi_bc_sim7_to_rgba8(t["vol_ea"], t["vol_eb"], t["vol_wt"])
+            export = "the shared-weight simulation's 8-bit texels (ndgi_bc_sim7_to_rgba8), then ndgi_bc7_encode"
+        else:
+            uv = ndgi.ndgi_bc_pack(t["uv_ea"], t["uv_eb"], t["uv_wt"])
+            vol = torch.stack([ndgi.ndgi_bc_pack(t["vol_ea"][k].contiguous(), t["vol_eb"][k].contiguous(),
+                                                 t["vol_wt"][k].contiguous()) for k in range(vol_t)]).contiguous()
+            hm = ndgi.HybridModel(side, side, uv, vol, ut, vt, *[t[k] for k in mlp])
+            entry["psnr_db_bc4x4_decode"] = psnr(hm)
+            entry["bpp_bc4x4"] = ndgi.ndgi_model_bpp(hm, 1, 0, 16)
+            uv8 = ndgi.ndgi_bc4x4_to_rgba8(uv)
+            vol8 = torch.cat([ndgi.ndgi_bc4x4_to_rgba8(vol[k].contiguous()) for k in range(vol_t)], 0)
+            export = "BC4-simulated values rounded to 8 bits (ndgi_bc4x4_to_rgba8), then ndgi_bc7_encode"
+        uv7, vol7, rms, enc_ms, nblk = _bc7_export(ndgi, torch, uv8, vol8, vol_t, vol_side)
+        hm7 = ndgi.HybridModel(side, side, uv7, vol7, ut, vt, *[t[k] for k in mlp])
+        entry["bc7_export"] = {"psnr_db_decode": psnr(hm7), "bpp": ndgi.ndgi_model_bpp(hm7, 1, 0, 16),
+                               "rms_8bit_levels": rms, "encode_ms": enc_ms,
+                               "encode_blocks_per_s": nblk / (enc_ms / 1e3), "export": export}
+        out[name] = entry
+    out["device_check"] = check_status(ndgi)
+    return out
 
 
 QUALITY_WORKLOAD = ("quality: 256^2 lightmap, 26 non-uniform keyframes (24 hourly + 2 around a light switch at "
@@ -672,6 +717,40 @@ def bench_hybrid(args, ndgi, torch, peaks, peak_kind, timed, rank):
     out["roofline"].update({"kernel": "k_hybrid_pages_tc", "flop_per_texel": HYBRID_FLOP_PER_TEXEL,
                             "models_touched": touched, "traffic": traffic_for("k_hybrid_pages_tc", texels)})
     out["vs_fp32_plain"] = out["fp16"]["value"] / out["fp32"]["value"]
+    # the same frame with the paper's BC7 maps (random blocks, every mode equally likely), FP16 tensor cores
+    s7 = synth.hybrid_tile_set(94, 4096, "M.64", feat_format=1)
+    models7 = ndgi.HybridModel.from_set(s7)
+    ndgi.hybrid_prepare_set(models7, "fp16")
+    table = ndgi.HybridTable(models7, "fp16")
+    steps = max(3, min(args.steps, 20))
+    ms, _ = timed(lambda: table.decode(r_dev, len(reqs), phys), steps, 2)
+    st, word = table.check()
+    entry = {"value": job_value(texels, args.world, ms / steps), "unit": "Gtexels/s", "ms_per_frame": ms / steps,
+             "device_error_word": word, "device_check": "ok" if st == 0 else f"status {st}",
+             "maps": "F_uv 128^2 and F3D 32^2x12 as BC7 (16 B per 4x4 block, modes uniform)"}
+    if rank == 0:
+        import oracle
+        pick = np.random.default_rng(95).choice(len(reqs), 4, replace=False)
+        used = sorted(set(int(reqs[i]["model"]) for i in pick))
+        remap = {mi: k for k, mi in enumerate(used)}
+        sub = reqs[pick].copy()
+        sub["model"] = [remap[int(mi)] for mi in sub["model"]]
+        ref = oracle.hybrid_decode_pages([synth.hybrid_tile_of(s7, mi) for mi in used], sub, 8192, 8192,
+                                         precision="fp16", fill=0.0)
+        got = phys.float().cpu().numpy()
+        worst = 0.0
+        for q in sub:
+            sl = (slice(q["dst_y"], q["dst_y"] + 128), slice(q["dst_x"], q["dst_x"] + 128))
+            a, b = got[sl][..., :3].astype(np.float64), ref[sl][..., :3]
+            worst = max(worst, float(np.abs(a - b).max() / (b.max() - b.min())))
+        entry["max_err_over_page_range"] = worst
+    bytes7 = sum(int(np.prod(s7[k].shape[1:])) * s7[k].itemsize for k in ("uv_bc7", "vol_bc7", "ut", "vt")) + \
+        sum(int(np.prod(s7[k].shape[1:])) * 2 for k in ("w1", "b1", "w2", "b2", "w3", "b3"))
+    entry["roofline"] = two_term_roofline(texels, HYBRID_FLOP_PER_TEXEL, hybrid_frame_bytes(len(reqs), touched,
+                                          bytes7), ms / steps * 1e-3, peaks, peak_kind)
+    out["fp16_bc7"] = entry
+    table.close()
+    del models7, s7
     del phys
     torch.cuda.empty_cache()
     return out
@@ -928,7 +1007,8 @@ def main():
         line["hybrid_m64_fp16"] = {
             "value": h16["value"], "unit": "Gtexels/s", "ms_per_frame": h16["ms_per_frame"], "frac": hr["frac"],
             "bound": hr["bound"], "max_err_over_page_range": h16.get("max_err_over_page_range"),
-            "vs_fp32_plain": hybrid["vs_fp32_plain"], "device_check": h16["device_check"]}
+            "vs_fp32_plain": hybrid["vs_fp32_plain"], "device_check": h16["device_check"],
+            "bc7_value": hybrid["fp16_bc7"]["value"]}
     if pages is not None:
         # the batched page decode (the configuration the >= 60 % roofline target is stated on), in brief, last
         p16, rf = pages["fp16"], pages["roofline"]

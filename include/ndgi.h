@@ -487,7 +487,8 @@ ndgi_status ndgi_bc_pack(const float *ea, const float *eb, const float *w, int32
  * 0..63) and mode 0 (partitions 0..15), keeping the first candidate with the
  * smallest squared error.  A candidate takes per subset (and per colour /
  * alpha group in modes 4, 5) the per-channel minimum and maximum as
- * endpoints, each coded by its nearest code (lowest code on ties; a p-bit
+ * endpoints, a channel swapped between them when its integer covariance
+ * with the widest channel is negative, each coded by its nearest code (lowest code on ties; a p-bit
  * minimises the summed squared error, 0 on ties), and gives every texel its
  * nearest palette entry (lowest index on ties).  If sq_err is not NULL the
  * total squared error (over all texels and channels, in 8-bit units) is
@@ -511,6 +512,29 @@ ndgi_status ndgi_bc7_decode(const uint8_t *blocks, int32_t w, int32_t h, uint8_t
  * texel and plane, the input of ndgi_bc7_encode.  bc4 [h/4][w/4][4][8].
  */
 ndgi_status ndgi_bc4x4_to_rgba8(const uint8_t *bc4, int32_t w, int32_t h, uint8_t *rgba, void *stream);
+
+/*
+ * 8-bit export of a map fitted with the shared-weight BC simulation
+ * (ndgi_hybrid_fit_params.shared_w = 1): rgba [height][width][4], texel p of
+ * block b = ((64 - W) A + W B + 32) >> 6 per channel with A, B the mode-6
+ * endpoints of ea[b], eb[b] (ndgi_hybrid_fit_params, shared_w), W the 4-bit
+ * BC7 weight of index q15(w[b][p]).  ea, eb
+ * [height/4][width/4][4], w [height/4][width/4][16] FP32 (F3D slices stacked
+ * along height); device buffers, 16-byte aligned.  The input of
+ * ndgi_bc7_encode.
+ */
+ndgi_status ndgi_bc_sim7_to_rgba8(const float *ea, const float *eb, const float *w, int32_t width, int32_t height,
+                                  uint8_t *rgba, void *stream);
+
+/*
+ * Exact BC7 mode-6 blocks [n_blocks][16] of a shared-weight BC simulation
+ * (ea, eb [n_blocks][4], w [n_blocks][16] FP32): endpoint codes and p-bits of
+ * the mode-6 endpoints, indices q15(w); where texel 0's index is 8 or more
+ * the endpoints swap and index k becomes 15 - k.  The blocks decode to
+ * ndgi_bc_sim7_to_rgba8's texels.  Device buffers, 16-byte aligned.
+ */
+ndgi_status ndgi_bc7_pack_sim(const float *ea, const float *eb, const float *w, int64_t n_blocks, uint8_t *blocks,
+                              void *stream);
 
 /*
  * Test reference: the same decode done by the GPU's texture unit (a BC7
@@ -577,6 +601,12 @@ typedef struct {
   int32_t loss_every;         /* FP64 loss logged every k steps (0 = never) */
   uint64_t seed;              /* sample stream (counter-based SplitMix64)   */
   int32_t relaxed;            /* 1 = no BC quantisation in the forward      */
+  float noise_alpha;          /* hybrid fit: V' = V + U(-1/2, 1/2) alpha on the 12 sampled map inputs (the
+                                 training-time quantisation noise; 1/256 for 8-bit maps; 0 = off).  The
+                                 draws are counter-based: for sample i of global step s and input k,
+                                 z = splitmix64(b + k g), b = (seed ^ 0x6E6F697365) + 12 ((s << 32) + i) g,
+                                 g = 0x9E3779B97F4A7C15, noise = alpha ((z >> 40) 2^-24 - 1/2).  The simple
+                                 fit ignores it.                                                          */
 } ndgi_fit_config;
 
 /* Bytes of device workspace ndgi_encode_fit needs. */
@@ -797,12 +827,22 @@ double ndgi_model_bpp(const ndgi_hybrid_desc *model, int32_t n_lightmaps, int32_
  * F_ut / F_vt used as given; GELU(x) = x Phi(x) in FP32 (CUDA's erff).
  * Pack a result with ndgi_bc_pack (cs = 4; per F3D slice) and round F_ut /
  * F_vt to UNORM8.  hidden 16, 32 or 64.
+ * shared_w = 1 follows Eq. 7 literally: one weight per texel shared by the
+ * four channels (uv_wt [uv_h/4][uv_w/4][16], vol_wt [vol_t][..][16]), read as
+ * BC7 mode 6: the mode-6 endpoints A, B of ea, eb (each channel q255, then
+ * the endpoint's p-bit = the majority parity of its four channels, 0 on a
+ * 2-2 tie, and each channel the nearest value of that parity, the lower on a
+ * tie), W = the 4-bit BC7 weight of index q15(w), value ((64 - W) A + W B +
+ * 32) >> 6 over 255 (relaxed: (1 - w) ea + w eb).  Export exactly with
+ * ndgi_bc7_pack_sim, or as the paper does (8-bit maps re-encoded) with
+ * ndgi_bc_sim7_to_rgba8 and ndgi_bc7_encode.
  */
 typedef struct {
   int32_t lm_w, lm_h;
   int32_t uv_w, uv_h, vol_w, vol_h, vol_t, ut_w, ut_t, vt_h, vt_t;
   int32_t hidden, address_mode;
   float *uv_ea, *uv_eb, *uv_wt, *vol_ea, *vol_eb, *vol_wt, *ut, *vt, *w1, *b1, *w2, *b2, *w3, *b3;
+  int32_t shared_w;
 } ndgi_hybrid_fit_params;
 
 /* Gradient buffers in ndgi_hybrid_fit_params' tensor order (FP32, device). */

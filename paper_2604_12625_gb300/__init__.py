@@ -14,7 +14,8 @@ from .api import (  # noqa: F401
     ndgi_debug_workspace_inject, ndgi_debug_features_cache, ndgi_decode_points_path, HybridModel, HybridTable,
     ndgi_hybrid_workspace_size, ndgi_hybrid_prepare, ndgi_hybrid_decode_points, ndgi_hybrid_workspace_check,
     ndgi_hybrid_debug_inject, ndgi_model_bpp, hybrid_prepare_set, ndgi_debug_gelu,
-    ndgi_tile_metrics, ndgi_bc7_encode, ndgi_bc7_decode, ndgi_bc4x4_to_rgba8, ndgi_debug_bc7_hw_decode,
+    ndgi_tile_metrics, ndgi_bc7_encode, ndgi_bc7_decode, ndgi_bc4x4_to_rgba8, ndgi_debug_bc7_hw_decode, ndgi_bc_sim7_to_rgba8,
+    ndgi_bc7_pack_sim,
     FitBatch, ndgi_encode_fit_batch, HybridFitState, ndgi_hybrid_fit_forward,
     ndgi_hybrid_fit_backward, ndgi_hybrid_encode_fit)
 

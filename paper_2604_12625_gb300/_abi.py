@@ -52,7 +52,7 @@ HFIT_TENSORS = ("uv_ea", "uv_eb", "uv_wt", "vol_ea", "vol_eb", "vol_wt", "ut", "
 class HybridFitParams(C.Structure):
     _fields_ = [(k, C.c_int32) for k in ("lm_w", "lm_h", "uv_w", "uv_h", "vol_w", "vol_h", "vol_t", "ut_w", "ut_t",
                                          "vt_h", "vt_t", "hidden", "address_mode")] + \
-               [(k, C.c_void_p) for k in HFIT_TENSORS]
+               [(k, C.c_void_p) for k in HFIT_TENSORS] + [("shared_w", C.c_int32)]
 
 
 class HybridFitGrads(C.Structure):
@@ -75,7 +75,7 @@ class FitGrads(C.Structure):
 class FitConfig(C.Structure):
     _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
                 ("beta2", C.c_float), ("eps", C.c_float), ("freeze_steps", C.c_int32), ("loss_every", C.c_int32),
-                ("seed", C.c_uint64), ("relaxed", C.c_int32)]
+                ("seed", C.c_uint64), ("relaxed", C.c_int32), ("noise_alpha", C.c_float)]
 
 
 # (name, restype, argtypes) of every exported entry point in include/ndgi.h
@@ -116,6 +116,8 @@ SIGNATURES = [
     ("ndgi_bc7_decode", C.c_int, [_vp, _i32, _i32, _vp, _vp]),
     ("ndgi_bc4x4_to_rgba8", C.c_int, [_vp, _i32, _i32, _vp, _vp]),
     ("ndgi_debug_bc7_hw_decode", C.c_int, [_vp, _i32, _i32, _vp, _vp]),
+    ("ndgi_bc_sim7_to_rgba8", C.c_int, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    ("ndgi_bc7_pack_sim", C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp]),
     ("ndgi_fit_forward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("ndgi_fit_backward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),
     ("ndgi_encode_fit_workspace_size", _sz, [_vp, _vp]),

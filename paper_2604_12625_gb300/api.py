@@ -454,9 +454,9 @@ def ndgi_decode_fit(params, uvt, lm_w, lm_h, relaxed=False, address_mode=0, key_
 
 
 def fit_config(steps, batch, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, freeze_steps=0, loss_every=0, seed=0,
-               relaxed=False):
+               relaxed=False, noise_alpha=0.0):
     return A.FitConfig(int(steps), int(batch), float(lr), float(beta1), float(beta2), float(eps), int(freeze_steps),
-                       int(loss_every), int(seed), int(relaxed))
+                       int(loss_every), int(seed), int(relaxed), float(noise_alpha))
 
 
 def ndgi_encode_fit_workspace_size(state, cfg):
@@ -737,9 +737,10 @@ class HybridFitState:
         vt_t, vt_h, _ = self.t["vt"].shape
         self.hidden = int(self.t["w2"].shape[0])
         self.lm_w, self.lm_h = int(lm_w), int(lm_h)
+        self.shared_w = self.t["uv_wt"].dim() == 3       # [uv_h/4][uv_w/4][16]: Eq. 7's weight per texel
         self.params = A.HybridFitParams(self.lm_w, self.lm_h, ubw * 4, ubh * 4, vbw * 4, vbh * 4, vt_, ut_w, ut_t,
                                         vt_h, vt_t, self.hidden, int(address_mode),
-                                        *[self.t[k].data_ptr() for k in A.HFIT_TENSORS])
+                                        *[self.t[k].data_ptr() for k in A.HFIT_TENSORS], int(self.shared_w))
 
     @classmethod
     def from_arrays(cls, p, device="cuda"):
@@ -831,4 +832,27 @@ def ndgi_debug_bc7_hw_decode(blocks, stream=None):
     bh, bw, sixteen = blocks.shape
     out = torch.empty((bh * 4, bw * 4, 4), dtype=torch.uint8, device=blocks.device)
     check(lib().ndgi_debug_bc7_hw_decode(_p(blocks), bw * 4, bh * 4, _p(out), _stream(stream)))
+    return out
+
+
+def ndgi_bc_sim7_to_rgba8(ea, eb, w, out=None, stream=None):
+    """RGBA8 [h][w][4] of a shared-weight BC-simulated map: ea, eb float32 [..][h/4][w/4][4], w [..][h/4][w/4][16]
+    (CUDA; leading axes, e.g. F3D slices, stacked along the height)."""
+    for t, name in ((ea, "ea"), (eb, "eb"), (w, "w")):
+        _need(t, torch.float32, name)
+    bw = ea.shape[-2]
+    bh = ea.numel() // (bw * 4)
+    if out is None:
+        out = torch.empty((bh * 4, bw * 4, 4), dtype=torch.uint8, device=ea.device)
+    check(lib().ndgi_bc_sim7_to_rgba8(_p(ea), _p(eb), _p(w), bw * 4, bh * 4, _p(out), _stream(stream)))
+    return out
+
+
+def ndgi_bc7_pack_sim(ea, eb, w, out=None, stream=None):
+    """Exact BC7 mode-6 blocks uint8 [..][16] of a shared-weight BC-simulated map (ea, eb [..][4], w [..][16])."""
+    for t, name in ((ea, "ea"), (eb, "eb"), (w, "w")):
+        _need(t, torch.float32, name)
+    if out is None:
+        out = torch.empty(tuple(ea.shape[:-1]) + (16,), dtype=torch.uint8, device=ea.device)
+    check(lib().ndgi_bc7_pack_sim(_p(ea), _p(eb), _p(w), ea.numel() // 4, _p(out), _stream(stream)))
     return out

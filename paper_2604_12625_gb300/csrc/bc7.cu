@@ -8,8 +8,10 @@
 //   selector 0..1; mode 7 with partitions 0..63; for blocks whose alpha is
 //   255 everywhere also modes 3, 1, 2 (partitions 0..63) and 0 (0..15).
 // Per candidate, subset and endpoint group (colour and alpha separately in
-// modes 4 and 5), the endpoints are the per-channel minimum and maximum of
-// the subset's texels, each coded by its nearest code (a 256-entry table per
+// modes 4 and 5), the endpoints are the corners of the subset's per-channel
+// bounding box on the diagonal along the data (a channel runs from maximum to
+// minimum when its integer covariance with the widest channel is negative),
+// each coded by its nearest code (a 256-entry table per
 // code width and p-bit, built per CTA by exhaustive search, lowest code on
 // ties; a p-bit per endpoint or per subset picks the smaller summed squared
 // error, 0 on ties); each texel takes its nearest palette entry (lowest index
@@ -18,6 +20,7 @@
 // (swap a group's endpoints and mirror its indices when an anchor index has
 // its top bit set, which leaves the decoded texels unchanged).
 #include "ndgi_internal.h"
+#include "bc4.cuh"
 #include "bc7.cuh"
 
 namespace ndgi {
@@ -110,6 +113,29 @@ __device__ int bc7_try(const uint32_t (&x0)[16], int mode, int part, int rot, in
           hi[c] = max(hi[c], v);
         }
       }
+      // the box diagonal along the data: channel r of largest range runs low to high, another channel high to
+      // low when its integer covariance with r is negative
+      int r = c0;
+      for (int c = c0; c < c1; ++c)
+        if (hi[c] - lo[c] > hi[r] - lo[r]) r = c;
+      int cnt = 0, sr = 0, sc[4] = {0, 0, 0, 0}, scr[4] = {0, 0, 0, 0};
+      for (int p = 0; p < 16; ++p) {
+        if ((int)((sub >> (2 * p)) & 3u) != s) continue;
+        const int vr = chan(x[p], r);
+        ++cnt;
+        sr += vr;
+        for (int c = c0; c < c1; ++c) {
+          const int v = chan(x[p], c);
+          sc[c] += v;
+          scr[c] += v * vr;
+        }
+      }
+      for (int c = c0; c < c1; ++c)
+        if (c != r && cnt * scr[c] - sc[c] * sr < 0) {
+          const int t = lo[c];
+          lo[c] = hi[c];
+          hi[c] = t;
+        }
       int val[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
       if (M.epb || M.spb) {
         int pe[2] = {0, 0};
@@ -316,6 +342,81 @@ __global__ void k_bc4x4_to_rgba8(const uint4* __restrict__ bc4, int bw, int64_t 
   }
 }
 
+// 8-bit export of a shared-weight BC simulation (Eq. 7 with one weight per
+// texel): texel value ((64 - W) A + W B + 32) >> 6 per channel with A, B the
+// mode-6 endpoints of ea, eb and W the 4-bit BC7 weight of index q15(w).  One
+// thread per block.
+__device__ __forceinline__ int mode6_endpoint(const float* __restrict__ e, int (&E)[4]) {
+  int q[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) q[c] = quant(__ldg(e + c), 255.0f);
+  return bc7_mode6_endpoint(q, E);
+}
+
+__global__ void k_bc_sim7_to_rgba8(const float* __restrict__ ea, const float* __restrict__ eb,
+                                   const float* __restrict__ w, int bw, int64_t n_blocks, uint4* __restrict__ rgba) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    int A[4], B[4];
+    mode6_endpoint(ea + 4 * b, A);
+    mode6_endpoint(eb + 4 * b, B);
+    const int64_t by = b / bw, bx = b % bw;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      uint32_t o[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int W = bc7_weight(quant(__ldg(w + 16 * b + 4 * r + q), 15.0f), 4);
+        uint32_t v = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v |= (uint32_t)(((64 - W) * A[c] + W * B[c] + 32) >> 6) << (8 * c);
+        o[q] = v;
+      }
+      rgba[(4 * by + r) * bw + bx] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+  }
+}
+
+// Exact mode-6 blocks of a shared-weight BC simulation: the mode-6 endpoint
+// codes and p-bits, indices q15(w); where texel 0's index is 8 or more the
+// endpoints swap and every index k becomes 15 - k (symmetric weights).
+__global__ void k_bc7_pack_sim(const float* __restrict__ ea, const float* __restrict__ eb,
+                               const float* __restrict__ w, int64_t n_blocks, uint4* __restrict__ out) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    int A[4], B[4], k[16];
+    int pa = mode6_endpoint(ea + 4 * b, A), pb = mode6_endpoint(eb + 4 * b, B);
+#pragma unroll
+    for (int p = 0; p < 16; ++p) k[p] = quant(__ldg(w + 16 * b + p), 15.0f);
+    if (k[0] >= 8) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int t = A[c];
+        A[c] = B[c];
+        B[c] = t;
+      }
+      const int t = pa;
+      pa = pb;
+      pb = t;
+#pragma unroll
+      for (int p = 0; p < 16; ++p) k[p] = 15 - k[p];
+    }
+    uint64_t lo = 0, hi = 0;
+    int pos = 0;
+    put_bits(lo, hi, pos, 7, 1u << 6);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      put_bits(lo, hi, pos, 7, (uint32_t)(A[c] >> 1));
+      put_bits(lo, hi, pos, 7, (uint32_t)(B[c] >> 1));
+    }
+    put_bits(lo, hi, pos, 1, (uint32_t)pa);
+    put_bits(lo, hi, pos, 1, (uint32_t)pb);
+#pragma unroll
+    for (int p = 0; p < 16; ++p) put_bits(lo, hi, pos, p == 0 ? 3 : 4, (uint32_t)k[p]);
+    out[b] = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+  }
+}
+
 // Fixed-function reference: the texture unit's own BC7 decode, point-sampled at texel centres.
 __global__ void k_bc7_tex_fetch(cudaTextureObject_t tex, int w, int h, uint32_t* __restrict__ rgba) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -378,6 +479,31 @@ ndgi_status ndgi_bc4x4_to_rgba8(const uint8_t* bc4, int32_t w, int32_t h, uint8_
   k_bc4x4_to_rgba8<<<grid_for(n, 256, 16), 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const uint4*>(bc4), bw,
                                                                              n, reinterpret_cast<uint4*>(rgba));
   return cuda_status(cudaGetLastError(), "ndgi_bc4x4_to_rgba8");
+}
+
+ndgi_status ndgi_bc_sim7_to_rgba8(const float* ea, const float* eb, const float* w, int32_t width, int32_t height,
+                                  uint8_t* rgba, void* stream) {
+  ndgi_status st = check_image(ea, rgba, width, height, "ndgi_bc_sim7_to_rgba8");
+  if (st != NDGI_OK) return st;
+  if (!eb || !w || (uintptr_t)eb % 16 || (uintptr_t)w % 16)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_bc_sim7_to_rgba8: eb and w must be non-NULL and 16-byte aligned");
+  const int bw = width / 4;
+  const int64_t n = (int64_t)bw * (height / 4);
+  k_bc_sim7_to_rgba8<<<grid_for(n, 256, 16), 256, 0, (cudaStream_t)stream>>>(ea, eb, w, bw, n,
+                                                                              reinterpret_cast<uint4*>(rgba));
+  return cuda_status(cudaGetLastError(), "ndgi_bc_sim7_to_rgba8");
+}
+
+ndgi_status ndgi_bc7_pack_sim(const float* ea, const float* eb, const float* w, int64_t n_blocks, uint8_t* blocks,
+                              void* stream) {
+  if (!ea || !eb || !w || !blocks || n_blocks < 0)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_bc7_pack_sim: NULL buffer or n_blocks < 0");
+  if ((uintptr_t)ea % 16 || (uintptr_t)eb % 16 || (uintptr_t)w % 16 || (uintptr_t)blocks % 16)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_bc7_pack_sim: buffers must be 16-byte aligned");
+  if (n_blocks == 0) return NDGI_OK;
+  k_bc7_pack_sim<<<grid_for(n_blocks, 256, 16), 256, 0, (cudaStream_t)stream>>>(ea, eb, w, n_blocks,
+                                                                                 reinterpret_cast<uint4*>(blocks));
+  return cuda_status(cudaGetLastError(), "ndgi_bc7_pack_sim");
 }
 
 ndgi_status ndgi_debug_bc7_hw_decode(const uint8_t* blocks, int32_t w, int32_t h, uint8_t* rgba, void* stream) {

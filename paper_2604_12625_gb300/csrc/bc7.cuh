@@ -117,6 +117,20 @@ __device__ __forceinline__ uint32_t bc7_bits(uint64_t lo, uint64_t hi, int pos, 
 
 __device__ __forceinline__ int bc7_expand(int c, int n) { return n >= 8 ? c : (c << (8 - n)) | (c >> (2 * n - 8)); }
 
+// Mode-6 endpoint of 8-bit channel values q[4]: the p-bit is their majority
+// parity (0 on a 2-2 tie), each channel the nearest value of that parity (the
+// lower on a tie).  Returns p; E[c] = 2 max(0, (q[c] - p) >> 1) + p.
+__host__ __device__ __forceinline__ int bc7_mode6_endpoint(const int (&q)[4], int (&E)[4]) {
+  const int odd = (q[0] & 1) + (q[1] & 1) + (q[2] & 1) + (q[3] & 1);
+  const int p = odd > 2 ? 1 : 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int h = (q[c] - p) >> 1;
+    E[c] = 2 * (h < 0 ? 0 : h) + p;
+  }
+  return p;
+}
+
 // Interpolation weight of index i of a b-bit index (b = 2, 3, 4).
 __device__ __forceinline__ int bc7_weight(int i, int b) {
   const float r = b == 2 ? 64.0f / 3.0f : b == 3 ? 64.0f / 7.0f : 64.0f / 15.0f;

@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 
 #include "bc4.cuh"
+#include "bc7.cuh"
 #include "ndgi_internal.h"
 #include "sampler.cuh"
 
@@ -28,6 +29,8 @@ struct HFitArgs {
   const float* p[14];   // uv_ea, uv_eb, uv_wt, vol_ea, vol_eb, vol_wt, ut, vt, w1, b1, w2, b2, w3, b3
   float* g[14];         // gradients, same order
   int relaxed;
+  int shared_w;            // Eq. 7's weight per texel shared by the four channels (BC7 simulation)
+  float noise_alpha;       // mode 1: training-time quantisation noise on the 12 sampled map inputs
   int64_t n;
   const float* uvt;        // mode 0: queries [n][3]
   const float* grad_rgb;   // mode 0: dL/drgb [n][3]
@@ -41,14 +44,41 @@ struct HFitArgs {
 enum { kUvEa, kUvEb, kUvWt, kVolEa, kVolEb, kVolWt, kUt, kVt, kW1, kB1, kW2, kB2, kW3, kB3 };
 
 // Straight-through value of texel p of BC entry e (block * 4 + channel) and its factors.
+// Index of texel p's weight for BC entry e: per channel, or per block with shared weights.
+__device__ __forceinline__ int64_t hfit_widx(int shared, int64_t e, int p) { return (shared ? e >> 2 : e) * 16 + p; }
+
 __device__ __forceinline__ float hfit_sim(const float* ea, const float* eb, const float* wt, int64_t e, int p,
-                                          int relaxed, float& dea, float& deb, float& dw) {
-  const float a = __ldg(ea + e), b = __ldg(eb + e), w = __ldg(wt + e * 16 + p);
+                                          int relaxed, int shared, float& dea, float& deb, float& dw) {
+  const float a = __ldg(ea + e), b = __ldg(eb + e), w = __ldg(wt + hfit_widx(shared, e, p));
   if (relaxed) {
     dea = 1.0f - w;
     deb = w;
     dw = b - a;
     return (1.0f - w) * a + w * b;
+  }
+  if (shared) {   // BC7 mode 6: mode-6 endpoints and the 4-bit weight of index q15(w)
+    const int64_t b4 = e & ~(int64_t)3;
+    int qa[4], qb[4], EA[4], EB[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      qa[c] = quant(__ldg(ea + b4 + c), 255.0f);
+      qb[c] = quant(__ldg(eb + b4 + c), 255.0f);
+    }
+    bc7_mode6_endpoint(qa, EA);
+    bc7_mode6_endpoint(qb, EB);
+    const int ch = (int)(e - b4);
+    int A = EA[0], B = EB[0];
+#pragma unroll
+    for (int c = 1; c < 4; ++c)
+      if (ch == c) {
+        A = EA[c];
+        B = EB[c];
+      }
+    const int W = bc7_weight(quant(w, 15.0f), 4);
+    dea = 1.0f - (float)W / 64.0f;
+    deb = (float)W / 64.0f;
+    dw = (float)B / 255.0f - (float)A / 255.0f;
+    return (float)(((64 - W) * A + W * B + 32) >> 6) * (1.0f / 255.0f);
   }
   const int A = quant(a, 255.0f), B = quant(b, 255.0f), k = quant(w, 7.0f);
   dea = 1.0f - (float)k / 7.0f;
@@ -112,8 +142,8 @@ __device__ __forceinline__ void hfit_for_each_tap(const HFitArgs& a, float u, fl
 
 __device__ __forceinline__ float hfit_value(const HFitArgs& a, int map, int64_t e, int p, float& d0, float& d1,
                                             float& d2) {
-  if (map == 0) return hfit_sim(a.p[kVolEa], a.p[kVolEb], a.p[kVolWt], e, p, a.relaxed, d0, d1, d2);
-  if (map == 1) return hfit_sim(a.p[kUvEa], a.p[kUvEb], a.p[kUvWt], e, p, a.relaxed, d0, d1, d2);
+  if (map == 0) return hfit_sim(a.p[kVolEa], a.p[kVolEb], a.p[kVolWt], e, p, a.relaxed, a.shared_w, d0, d1, d2);
+  if (map == 1) return hfit_sim(a.p[kUvEa], a.p[kUvEb], a.p[kUvWt], e, p, a.relaxed, a.shared_w, d0, d1, d2);
   d0 = 1.0f;
   d1 = d2 = 0.0f;
   return __ldg(a.p[map == 2 ? kUt : kVt] + e);
@@ -141,11 +171,11 @@ __device__ __forceinline__ void hfit_scatter(const HFitArgs& a, float u, float v
     if (map == 0) {
       atomicAdd(a.g[kVolEa] + e, d0 * g);
       atomicAdd(a.g[kVolEb] + e, d1 * g);
-      atomicAdd(a.g[kVolWt] + e * 16 + p, d2 * g);
+      atomicAdd(a.g[kVolWt] + hfit_widx(a.shared_w, e, p), d2 * g);
     } else if (map == 1) {
       atomicAdd(a.g[kUvEa] + e, d0 * g);
       atomicAdd(a.g[kUvEb] + e, d1 * g);
-      atomicAdd(a.g[kUvWt] + e * 16 + p, d2 * g);
+      atomicAdd(a.g[kUvWt] + hfit_widx(a.shared_w, e, p), d2 * g);
     } else {
       atomicAdd(a.g[map == 2 ? kUt : kVt] + e, g);
     }
@@ -267,6 +297,15 @@ __global__ void __launch_bounds__(kHfTile, 1) k_hfit_backward(HFitArgs a) {
     // ---- forward of this thread's sample ----
     float x[16];
     hfit_inputs(a, u, v, t, x);
+    if (MODE == 1 && valid && a.noise_alpha > 0.0f) {   // V' = V + U(-1/2, 1/2) alpha
+      const uint64_t g = 0x9E3779B97F4A7C15ull;
+      const uint64_t b = (a.seed ^ 0x6E6F697365ull) + 12ull * (((uint64_t)step << 32) + (uint64_t)s) * g;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const uint64_t z = splitmix64(b + (uint64_t)k * g);
+        x[k] += a.noise_alpha * ((float)(uint32_t)(z >> 40) * 0x1p-24f - 0.5f);
+      }
+    }
 #pragma unroll
     for (int k = 0; k < 16; ++k) xr[k] = x[k];
     for (int o = 0; o < H; ++o) {
@@ -497,8 +536,9 @@ static cudaError_t launch_hfit_backward(const HFitArgs& a, int mode, cudaStream_
 static void hfit_sizes(const ndgi_hybrid_fit_params* p, int64_t (&n)[14]) {
   const int64_t ub = (int64_t)(p->uv_h / 4) * (p->uv_w / 4) * 4, vb = (int64_t)p->vol_t * (p->vol_h / 4) * (p->vol_w / 4) * 4;
   const int64_t H = p->hidden;
-  n[kUvEa] = ub; n[kUvEb] = ub; n[kUvWt] = ub * 16;
-  n[kVolEa] = vb; n[kVolEb] = vb; n[kVolWt] = vb * 16;
+  const int64_t wpb = p->shared_w ? 4 : 16;   // weights per BC entry (block x channel)
+  n[kUvEa] = ub; n[kUvEb] = ub; n[kUvWt] = ub * wpb;
+  n[kVolEa] = vb; n[kVolEb] = vb; n[kVolWt] = vb * wpb;
   n[kUt] = (int64_t)p->ut_t * p->ut_w * 2; n[kVt] = (int64_t)p->vt_t * p->vt_h * 2;
   n[kW1] = 16 * H; n[kB1] = H; n[kW2] = H * H; n[kB2] = H; n[kW3] = 3 * H; n[kB3] = 3;
 }
@@ -525,6 +565,7 @@ static HFitArgs make_hfit_args(const ndgi_hybrid_fit_params* p) {
   a.lm_w = p->lm_w; a.lm_h = p->lm_h; a.uv_w = p->uv_w; a.uv_h = p->uv_h; a.vol_w = p->vol_w; a.vol_h = p->vol_h;
   a.vol_t = p->vol_t; a.ut_w = p->ut_w; a.ut_t = p->ut_t; a.vt_h = p->vt_h; a.vt_t = p->vt_t; a.hidden = p->hidden;
   a.address_mode = p->address_mode;
+  a.shared_w = p->shared_w != 0;
   float* const q[14] = {p->uv_ea, p->uv_eb, p->uv_wt, p->vol_ea, p->vol_eb, p->vol_wt, p->ut,
                         p->vt,    p->w1,    p->b1,    p->w2,     p->b2,     p->w3,     p->b3};
   for (int k = 0; k < 14; ++k) a.p[k] = q[k];
@@ -593,6 +634,8 @@ ndgi_status ndgi_hybrid_encode_fit(const ndgi_hybrid_fit_params* params, const u
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_encode_fit: bad config");
   if (!(cfg->lr > 0.0f) || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_encode_fit: bad optimiser settings");
+  if (!(cfg->noise_alpha >= 0.0f && cfg->noise_alpha <= 1.0f))
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_encode_fit: noise_alpha must be in [0, 1]");
   const size_t need = ndgi_hybrid_encode_fit_workspace_size(params, cfg);
   if (ws_bytes < need || ((uintptr_t)ws % 256))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_encode_fit: ws must be 256-byte aligned with >= %zu bytes",
@@ -635,6 +678,7 @@ ndgi_status ndgi_hybrid_encode_fit(const ndgi_hybrid_fit_params* params, const u
   t.eps = cfg->eps;
   for (int k = 0; k < 14; ++k) a.g[k] = g + t.off[k];
   a.relaxed = cfg->relaxed != 0;
+  a.noise_alpha = cfg->noise_alpha;
   a.n = cfg->batch;
   a.targets = reinterpret_cast<const __half*>(targets);
   a.t_count = t_count;

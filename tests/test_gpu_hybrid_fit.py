@@ -31,14 +31,15 @@ def ndgi():
     return m
 
 
-def params(seed, hidden=64):
-    return synth.hybrid_fit_init(seed, 64, 64, 64, 64, 16, 16, 6, 32, 8, 32, 8, hidden)
+def params(seed, hidden=64, shared=False):
+    return synth.hybrid_fit_init(seed, 64, 64, 64, 64, 16, 16, 6, 32, 8, 32, 8, hidden, shared_w=shared)
 
 
+@pytest.mark.parametrize("shared", [False, True])
 @pytest.mark.parametrize("relaxed", [False, True])
 @pytest.mark.parametrize("hidden", [16, 64])
-def test_forward_matches_oracle(ndgi, relaxed, hidden):
-    p = params(1, hidden)
+def test_forward_matches_oracle(ndgi, relaxed, hidden, shared):
+    p = params(1, hidden, shared)
     q = synth.random_queries(2, 20_000)
     q[:2000, :2] = np.random.default_rng(3).uniform(-0.5, 1.5, (2000, 2)).astype(np.float32)
     st = ndgi.HybridFitState.from_arrays(p)
@@ -46,10 +47,11 @@ def test_forward_matches_oracle(ndgi, relaxed, hidden):
     assert rel_err(y, oracle.hfit_forward(p, q, relaxed=relaxed)) <= 1e-5
 
 
+@pytest.mark.parametrize("shared", [False, True])
 @pytest.mark.parametrize("relaxed", [False, True])
 @pytest.mark.parametrize("hidden", [16, 32, 64])
-def test_backward_matches_oracle(ndgi, relaxed, hidden):
-    p = params(4, hidden)
+def test_backward_matches_oracle(ndgi, relaxed, hidden, shared):
+    p = params(4, hidden, shared)
     n = 3000
     q = synth.random_queries(5, n)
     tgt = np.random.default_rng(6).normal(size=(n, 3))
@@ -64,12 +66,13 @@ def test_backward_matches_oracle(ndgi, relaxed, hidden):
         assert np.abs(a - gr[k]).max() <= 1e-3 * max(np.abs(gr[k]).max(), 1e-30), k
 
 
-def test_encode_fit_matches_oracle_loop(ndgi):
-    p = params(7, 16)
+@pytest.mark.parametrize("shared,noise", [(False, 0.0), (True, 0.0), (True, 1.0 / 256)])
+def test_encode_fit_matches_oracle_loop(ndgi, shared, noise):
+    p = params(7, 16, shared)
     lm, T, batch, seed = 64, 4, 2048, 55
     targets = synth.fit_targets(8, lm, lm, T, n_gauss=6)
     st = ndgi.HybridFitState.from_arrays(p)
-    cfg = ndgi.fit_config(steps=3, batch=batch, lr=1e-2, loss_every=1, seed=seed)
+    cfg = ndgi.fit_config(steps=3, batch=batch, lr=1e-2, loss_every=1, seed=seed, noise_alpha=noise)
     _, log = ndgi.ndgi_hybrid_encode_fit(st, torch.from_numpy(targets).cuda(), cfg)
     torch.cuda.synchronize()
     q = {k: np.asarray(p[k], np.float32).copy() for k in KEYS}
@@ -80,7 +83,8 @@ def test_encode_fit_matches_oracle_loop(ndgi):
         texel, s = oracle.fit_draw(seed, step, batch, lm, lm)
         tg = oracle.fit_targets_at(targets, texel, s)
         qd.update(q)
-        loss, g = oracle.hfit_backward(qd, s, tg)
+        nz = oracle.fit_noise(seed, step, batch, noise) if noise else None
+        loss, g = oracle.hfit_backward(qd, s, tg, noise=nz)
         losses.append(loss)
         for i, k in enumerate(KEYS):
             oracle.adam(q[k].reshape(-1), g[k].reshape(-1), mom[k][0], mom[k][1], step + 1, 1e-2, project=i < 8)
@@ -115,6 +119,45 @@ def test_fit_reduces_loss_and_packs_to_its_forward(ndgi):
     qq = torch.from_numpy(synth.random_queries(12, 20_000)).cuda()
     dec = ndgi.ndgi_hybrid_decode_points(hm, qq, "fp32").cpu().numpy()
     # the forward with F_ut / F_vt at their stored UNORM8 values
+    t["ut"].copy_(ut.float() / 255)
+    t["vt"].copy_(vt.float() / 255)
+    fwd = ndgi.ndgi_hybrid_fit_forward(st, qq).cpu().numpy()
+    assert rel_err(dec, fwd) <= 1e-5
+
+
+def test_shared_weight_export_matches_oracle(ndgi):
+    p = params(12, 16, shared=True)
+    t = {k: torch.from_numpy(np.ascontiguousarray(p[k])).cuda() for k in ("uv_ea", "uv_eb", "uv_wt", "vol_ea",
+                                                                           "vol_eb", "vol_wt")}
+    uv = ndgi.ndgi_bc_sim7_to_rgba8(t["uv_ea"], t["uv_eb"], t["uv_wt"]).cpu().numpy()
+    assert np.array_equal(uv, oracle.bc_sim7_rgba8(p["uv_ea"], p["uv_eb"], p["uv_wt"]))
+    vol = ndgi.ndgi_bc_sim7_to_rgba8(t["vol_ea"], t["vol_eb"], t["vol_wt"]).cpu().numpy()
+    assert vol.shape == (6 * 16, 16, 4)
+    assert np.array_equal(vol, oracle.bc_sim7_rgba8(p["vol_ea"], p["vol_eb"], p["vol_wt"]))
+    for key, img in (("uv", uv), ("vol", vol)):
+        blk = ndgi.ndgi_bc7_pack_sim(t[f"{key}_ea"], t[f"{key}_eb"], t[f"{key}_wt"])
+        assert np.array_equal(blk.cpu().numpy(), oracle.bc7_pack_sim(p[f"{key}_ea"], p[f"{key}_eb"], p[f"{key}_wt"]))
+        bw = blk.shape[-2]
+        dec = ndgi.ndgi_bc7_decode(blk.reshape(-1, bw, 16)).cpu().numpy()
+        assert np.array_equal(dec, img)                       # the pack is exact
+
+
+def test_shared_weight_fit_packs_exactly_to_bc7(ndgi):
+    p = params(13, 64, shared=True)
+    lm, T = 64, 8
+    targets = synth.fit_targets(14, lm, lm, T, n_gauss=6)
+    st = ndgi.HybridFitState.from_arrays(p)
+    cfg = ndgi.fit_config(steps=200, batch=1 << 13, lr=1e-2, loss_every=50, seed=15, noise_alpha=1.0 / 256)
+    _, log = ndgi.ndgi_hybrid_encode_fit(st, torch.from_numpy(targets).cuda(), cfg)
+    assert log[-1] < 0.5 * log[0]
+    t = st.t
+    uv = ndgi.ndgi_bc7_pack_sim(t["uv_ea"], t["uv_eb"], t["uv_wt"])
+    vol = ndgi.ndgi_bc7_pack_sim(t["vol_ea"], t["vol_eb"], t["vol_wt"])
+    ut = torch.round(t["ut"] * 255).to(torch.uint8)
+    vt = torch.round(t["vt"] * 255).to(torch.uint8)
+    hm = ndgi.HybridModel(lm, lm, uv, vol, ut, vt, *[t[k] for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+    qq = torch.from_numpy(synth.random_queries(16, 20_000)).cuda()
+    dec = ndgi.ndgi_hybrid_decode_points(hm, qq, "fp32").cpu().numpy()
     t["ut"].copy_(ut.float() / 255)
     t["vt"].copy_(vt.float() / 255)
     fwd = ndgi.ndgi_hybrid_fit_forward(st, qq).cpu().numpy()
