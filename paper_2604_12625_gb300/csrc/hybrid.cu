@@ -311,6 +311,7 @@ struct HybAxis {
 constexpr int kHybVolSide = 48;   // largest F3D footprint side staged in shared memory
 constexpr int kHybBorderMax = 8;  // largest mirrored tile border
 constexpr int kHybAxisMax = 128 + 2 * kHybBorderMax;   // entries of a per-axis table
+constexpr int kHybUvSide = kHybAxisMax + 1;   // largest BC7 F_uv footprint side staged (decoded) in shared memory
 
 template <int H>
 struct HybridSmem {
@@ -321,7 +322,9 @@ struct HybridSmem {
   static constexpr uint32_t kCols = (kPoints + 15) / 16 * 16;  // pages: HybAxis [128] per column
   static constexpr uint32_t kRows = kCols + kHybAxisMax * sizeof(HybAxis);
   static constexpr uint32_t kVol = kRows + kHybAxisMax * sizeof(HybAxis);   // float4 [footprint] of F3D at t
-  static constexpr uint32_t kPages = kVol + kHybVolSide * kHybVolSide * 16;
+  static constexpr uint32_t kUv = kVol + kHybVolSide * kHybVolSide * 16;     // RGBA8 [footprint] of a BC7 F_uv
+  static constexpr uint32_t kPages = kUv;                                     // tables with BC4 maps only
+  static constexpr uint32_t kPagesBc7 = kUv + kHybUvSide * kHybUvSide * 4;
 };
 
 constexpr int kHybLanes = 4;
@@ -576,7 +579,7 @@ __device__ __forceinline__ float4 vol_texel(const DevHybrid& m, int x, int y, in
 // where both fractions are zero, as at texel centres of an F_uv of the
 // lightmap's size).  The four lanes take the page's 128-texel tiles in turn
 // (texel k of the request is (k mod w, k div w)).
-template <int H, bool BF16>
+template <int H, bool BF16, bool BC7>
 __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
     k_hybrid_pages_tc(HybridPagesCtx c, const ndgi_page_req* __restrict__ reqs, int n) {
   using L = HybridLayout<H>;
@@ -589,7 +592,8 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
   __shared__ uint32_t slot;
   __shared__ uint2 lut[16];
   __shared__ float s_b3[3], s_gamma[4], s_fz;
-  __shared__ int s_z[2], s_lo[2], s_hi[2];
+  __shared__ int s_z[2], s_lo[2], s_hi[2], s_ulo[2], s_uhi[2];
+  uint32_t* uvs = reinterpret_cast<uint32_t*>(sm + S::kUv);
   HybAxis* cols = reinterpret_cast<HybAxis*>(sm + S::kCols);
   HybAxis* rows = reinterpret_cast<HybAxis*>(sm + S::kRows);
   float4* vol = reinterpret_cast<float4*>(sm + S::kVol);
@@ -617,8 +621,8 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
     copy16(sm + S::kB1, m.ws + L::kB1P, H * L::K1P * 2, tid, blockDim.x);
     if (tid < 3) s_b3[tid] = stored_b3<BF16>(m.ws + L::kB3, tid, H, L::K2);
     if (tid == 0) {
-      s_lo[0] = s_lo[1] = 0x7fffffff;
-      s_hi[0] = s_hi[1] = -1;
+      s_lo[0] = s_lo[1] = s_ulo[0] = s_ulo[1] = 0x7fffffff;
+      s_hi[0] = s_hi[1] = s_uhi[0] = s_uhi[1] = -1;
     }
     __syncthreads();
     // ---- per-axis tables, gamma(t) and the F3D slice pair ----
@@ -642,6 +646,10 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
       (col ? cols : rows)[i] = a;
       atomicMin(&s_lo[col ? 0 : 1], min(a.v0, a.v1));
       atomicMax(&s_hi[col ? 0 : 1], max(a.v0, a.v1));
+      if (BC7) {
+        atomicMin(&s_ulo[col ? 0 : 1], min(a.u0, a.u1));
+        atomicMax(&s_uhi[col ? 0 : 1], max(a.u0, a.u1));
+      }
     } else if (tid == 2 * kHybAxisMax) {
       sincospif(r.t, &s_gamma[0], &s_gamma[1]);
       sincospif(2.0f * r.t, &s_gamma[2], &s_gamma[3]);
@@ -654,6 +662,23 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
     const float fz = s_fz;
     if (staged)
       for (int i = tid; i < fw * fh; i += blockDim.x) vol[i] = vol_texel(m, lx + i % fw, ly + i / fw, z0, z1, fz, lut);
+    // a BC7 F_uv: the page's footprint decoded once, whole blocks at a time, as RGBA8
+    const int ulx = s_ulo[0], uly = s_ulo[1], ufw = s_uhi[0] - ulx + 1, ufh = s_uhi[1] - uly + 1;
+    const bool uv_staged = BC7 && m.bc7 && ufw <= kHybUvSide && ufh <= kHybUvSide;
+    if (uv_staged) {
+      const int bx0 = ulx >> 2, by0 = uly >> 2, nbx = (s_uhi[0] >> 2) - bx0 + 1;
+      const int nb = nbx * ((s_uhi[1] >> 2) - by0 + 1);
+      for (int i = tid; i < nb; i += blockDim.x) {
+        const int bx = bx0 + i % nbx, by = by0 + i / nbx;
+        uint32_t px[16];
+        bc7_block(__ldg(reinterpret_cast<const uint4*>(m.uv + ((size_t)by * (m.uv_w / 4) + bx) * 16)), px);
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+          const int xx = 4 * bx + (p & 3) - ulx, yy = 4 * by + (p >> 2) - uly;
+          if (xx >= 0 && xx < ufw && yy >= 0 && yy < ufh) uvs[yy * ufw + xx] = px[p];
+        }
+      }
+    }
     fence_async_smem();
     __syncthreads();
     tc_fence_after();
@@ -681,7 +706,23 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
 #pragma unroll
           for (int j = 0; j < 4; ++j) x[j] = (1.0f - fz) * a[j] + fz * b[j];
         }
-        if (m.bc7) {
+        if (BC7 && uv_staged) {
+          const uint32_t* r0 = uvs + (cy.u0 - uly) * ufw - ulx;
+          if (cx.uf == 0.0f && cy.uf == 0.0f) {
+            u8x4_unpack(r0[cx.u0], x + 4);
+          } else {
+            const uint32_t* r1 = uvs + (cy.u1 - uly) * ufw - ulx;
+            float f[4][4];
+            u8x4_unpack(r0[cx.u0], f[0]);
+            u8x4_unpack(r0[cx.u1], f[1]);
+            u8x4_unpack(r1[cx.u0], f[2]);
+            u8x4_unpack(r1[cx.u1], f[3]);
+            const float gx = 1.0f - cx.uf, gy = 1.0f - cy.uf;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              x[4 + c] = gy * (gx * f[0][c] + cx.uf * f[1][c]) + cy.uf * (gx * f[2][c] + cx.uf * f[3][c]);
+          }
+        } else if (BC7 && m.bc7) {
           if (cx.uf == 0.0f && cy.uf == 0.0f) {
             const uint4 blk = __ldg(reinterpret_cast<const uint4*>(m.uv + ((size_t)(cy.u0 >> 2) * (m.uv_w / 4) +
                                                                          (cx.u0 >> 2)) * 16));
@@ -812,8 +853,10 @@ cudaError_t launch_hybrid_pages(const HybridPagesCtx& c, int hidden, int prec, c
     const ndgi_page_req* a1 = reqs;                                                                \
     int a2 = n;                                                                                    \
     void* args[] = {&cc, &a1, &a2};                                                                \
-    return launch_tc_kernel(prec == 2 ? k_hybrid_pages_tc<H, true> : k_hybrid_pages_tc<H, false>,  \
-                            HybridSmem<H>::kPages, std::min(n, num_sms()), s, args);               \
+    auto kern = c.uv_stage ? (prec == 2 ? k_hybrid_pages_tc<H, true, true> : k_hybrid_pages_tc<H, false, true>)   \
+                           : (prec == 2 ? k_hybrid_pages_tc<H, true, false> : k_hybrid_pages_tc<H, false, false>); \
+    return launch_tc_kernel(kern, c.uv_stage ? HybridSmem<H>::kPagesBc7 : HybridSmem<H>::kPages,             \
+                            std::min(n, num_sms()), s, args);                                      \
   }
   NDGI_HYBRID_HIDDEN(X)
 #undef X
@@ -835,6 +878,7 @@ struct ndgi_hybrid_table {
   int* d_words = nullptr;          // device: error word, debug word
   int n_models = 0, hidden = 0, prec = 0;
   int border = 0;                  // mirrored tile border of every page (texels per edge)
+  int any_bc7 = 0;                 // some model holds BC7 maps
 };
 
 namespace {
@@ -1006,6 +1050,7 @@ ndgi_status ndgi_hybrid_table_create(const ndgi_hybrid_desc* models, const void*
   auto* t = new ndgi_hybrid_table;
   t->n_models = n_models;
   t->hidden = models[0].hidden;
+  for (int i = 0; i < n_models; ++i) t->any_bc7 |= models[i].feat_format == NDGI_FEAT_BC7;
   t->prec = p;
   cudaError_t e = cudaMalloc(&t->d_models, sizeof(DevHybrid) * n_models);
   if (e == cudaSuccess) e = cudaMalloc(&t->d_words, 2 * sizeof(int));
@@ -1050,6 +1095,7 @@ ndgi_status ndgi_hybrid_decode_pages(ndgi_hybrid_table* table, const ndgi_page_r
   c.error_word = table->d_words;
   c.debug_word = table->d_words + 1;
   c.border = table->border;
+  c.uv_stage = table->any_bc7;
   return cuda_status(ndgi::launch_hybrid_pages(c, table->hidden, table->prec, reqs, n, (cudaStream_t)stream),
                      "ndgi_hybrid_decode_pages");
 }

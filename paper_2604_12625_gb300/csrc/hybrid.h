@@ -32,6 +32,7 @@ struct HybridPagesCtx {
   int* error_word;           // bit 0 bad request, bit 4 timeout
   const int* debug_word;     // kDbgInjectTimeout
   int border;                // mirrored tile border (texels per edge), 0..8
+  int uv_stage;              // some model holds a BC7 F_uv: the launch carries the decoded-footprint buffer
 };
 
 }  // namespace ndgi
