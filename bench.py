@@ -47,6 +47,7 @@ KERNEL_SOURCES = {
     "k_pages_tc": ("tc_decode.cu",) + _COMMON_SOURCES,
     "k_pages_ws": ("tc_decode.cu",) + _COMMON_SOURCES,
     "k_hybrid_pages_tc": ("hybrid.cu", "hybrid.h", "bc7.cuh") + _COMMON_SOURCES,
+    "k_hybrid_pages_tc_bc7": ("hybrid.cu", "hybrid.h", "bc7.cuh") + _COMMON_SOURCES,
 }
 NCU_TRAFFIC = {
     "k_points_ws": {"src": "dc313c105005e444", "read": 134407936, "write": 81475584, "units": 1 << 23,
@@ -55,8 +56,10 @@ NCU_TRAFFIC = {
                    "profile": "profiles/k_pages_tc_pages_8_lightmaps.md"},
     "k_pages_ws": {"src": "f7fc86e019b63f3e", "read": 19192576, "write": 76340736, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_ws_pages_8_lightmaps.md"},
-    "k_hybrid_pages_tc": {"src": "41e312db4a7bbc31", "read": 188086272, "write": 477627904, "units": 4096 * 128 * 128,
+    "k_hybrid_pages_tc": {"src": "881cf993db1296fa", "read": 187824128, "write": 476729856, "units": 4096 * 128 * 128,
                           "profile": "profiles/k_hybrid_pages_tc_m64_4096_tiles.md"},
+    "k_hybrid_pages_tc_bc7": {"src": "881cf993db1296fa", "read": 117325056, "write": 476722176, "units": 4096 * 128 * 128,
+                              "profile": "profiles/k_hybrid_pages_tc_bc7_m64_4096_tiles.md"},
 }
 
 
@@ -748,6 +751,8 @@ def bench_hybrid(args, ndgi, torch, peaks, peak_kind, timed, rank):
         sum(int(np.prod(s7[k].shape[1:])) * 2 for k in ("w1", "b1", "w2", "b2", "w3", "b3"))
     entry["roofline"] = two_term_roofline(texels, HYBRID_FLOP_PER_TEXEL, hybrid_frame_bytes(len(reqs), touched,
                                           bytes7), ms / steps * 1e-3, peaks, peak_kind)
+    entry["roofline"].update({"kernel": "k_hybrid_pages_tc (BC7 instantiation)",
+                              "traffic": traffic_for("k_hybrid_pages_tc_bc7", texels)})
     out["fp16_bc7"] = entry
     table.close()
     del models7, s7
