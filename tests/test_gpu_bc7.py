@@ -194,3 +194,59 @@ def test_hybrid_bc7_bpp(ndgi):
     L = A.lib()
     assert L.ndgi_model_bpp(C.byref(hm7.desc), 26, 0, 16) == L.ndgi_model_bpp(C.byref(hm7.desc), 26, 8, 16)
     assert L.ndgi_model_bpp(C.byref(hm4.desc), 26, 0, 16) == L.ndgi_model_bpp(C.byref(hm4.desc), 26, 16, 16)
+
+
+def test_hybrid_bc7_pages_timeout_path(ndgi):
+    """The BC7 instantiation of the tensor-core page kernel takes the same bounded timeout path (injected before
+    any MMA), latches it in the table's word only, and the next frame decodes correctly."""
+    from paper_2604_12625_gb300 import _abi as A
+    from test_gpu_hybrid import GATE, page_err, ragged_requests
+    s = synth.hybrid_tile_set(160, 2, "M.64", feat_format=1)
+    models = ndgi.HybridModel.from_set(s)
+    ndgi.hybrid_prepare_set(models, "fp16")
+    table = ndgi.HybridTable(models, "fp16")
+    reqs = ragged_requests(161, 2, 4, 2)
+    r, _ = ndgi.page_requests_to_device(reqs)
+    phys = torch.zeros((2 * 128, 2 * 128, 4), dtype=torch.float32, device="cuda")
+    ndgi.ndgi_hybrid_debug_inject(None, "fp16", table=table, flags=1)
+    table.decode(r, len(reqs), phys)
+    st, word = table.check()
+    assert st == A.NDGI_ERR_TIMEOUT and word & 16
+    ndgi.ndgi_hybrid_debug_inject(None, "fp16", table=table, flags=0)
+    table.decode(r, len(reqs), phys)
+    assert table.check() == (0, 0)
+    maps = [synth.hybrid_tile_of(s, i) for i in range(2)]
+    ref = oracle.hybrid_decode_pages(maps, reqs, 2 * 128, 2 * 128, precision="fp16", fill=0.0)
+    assert page_err(phys.cpu().numpy(), ref, reqs) <= GATE["fp16"]
+    table.close()
+
+
+def test_hybrid_bc7_full_frame_sampled(ndgi):
+    """The benchmark's BC7 frame (4096 M.64 tile models, whole-tile requests, RGBA16F) on sampled requests."""
+    from test_gpu_hybrid import GATE
+    s = synth.hybrid_tile_set(94, 4096, "M.64", feat_format=1)
+    models = ndgi.HybridModel.from_set(s)
+    ndgi.hybrid_prepare_set(models, "fp16")
+    table = ndgi.HybridTable(models, "fp16")
+    reqs = synth.hybrid_tile_requests(91, 4096, 4096, slots_x=64)
+    r, _ = ndgi.page_requests_to_device(reqs)
+    phys = torch.zeros((8192, 8192, 4), dtype=torch.float16, device="cuda")
+    table.decode(r, len(reqs), phys)
+    assert table.check() == (0, 0)
+    pick = np.random.default_rng(162).choice(len(reqs), 6, replace=False)
+    used = sorted(set(int(reqs[i]["model"]) for i in pick))
+    remap = {mi: k for k, mi in enumerate(used)}
+    sub = reqs[pick].copy()
+    sub["model"] = [remap[int(mi)] for mi in sub["model"]]
+    ref = oracle.hybrid_decode_pages([synth.hybrid_tile_of(s, mi) for mi in used], sub, 8192, 8192,
+                                     precision="fp16", fill=0.0)
+    got = phys.float().cpu().numpy()
+    for q in sub:
+        sl = (slice(q["dst_y"], q["dst_y"] + 128), slice(q["dst_x"], q["dst_x"] + 128))
+        a, b = got[sl][..., :3].astype(np.float64), ref[sl][..., :3]
+        err = float(np.abs(a - b).max() / (b.max() - b.min()))
+        # FP16 path gate plus the RGBA16F storage rounding of each value
+        assert np.all(np.abs(a - b) <= GATE["fp16"] * (b.max() - b.min()) + np.abs(b) * 2.0 ** -11), err
+    table.close()
+    del phys
+    torch.cuda.empty_cache()
