@@ -551,6 +551,66 @@ def bench_hybrid_fit(args, ndgi, torch):
     return out
 
 
+HYBRID_FIT_BATCH_WORKLOAD = ("batched hybrid fit: the fit workload's 1024^2 x 24 keyframe targets cut into 64 tiles "
+                             "of 128^2, one M.64 model per tile (Eq. 7 shared-weight BC7 mode-6 simulation, noise "
+                             "1/256), all 64 fitted in one launch per step, 2^13 samples per model and step, 300 "
+                             "Adam steps; then every tile packed exactly to BC7, F_ut/F_vt to UNORM8, and the whole "
+                             "1024^2 lightmap decoded (FP32 page decode, one 128^2 page per tile) at every keyframe")
+
+
+def bench_hybrid_fit_batch(args, ndgi, torch):
+    """Per-tile hybrid models fitted side by side (ndgi_hybrid_encode_fit_batch), then the lightmap decoded from
+    their exact BC7 packs."""
+    T, side, tiles = 24, 128, 8
+    full = c3_targets()
+    tg = full.reshape(T, tiles, side, tiles, side, 3).transpose(1, 3, 0, 2, 4, 5).reshape(tiles * tiles, T, side,
+                                                                                         side, 3)
+    tg = torch.from_numpy(np.ascontiguousarray(tg)).cuda()
+    ps = [synth.hybrid_fit_init(500 + i, side, side, side, side, 32, 32, 12, 64, 24, 64, 24, 64, shared_w=True)
+          for i in range(tiles * tiles)]
+    steps = max(10, min(300, args.fit_steps // 6))
+    batch = 1 << 13
+    warm = ndgi.HybridFitBatch.from_arrays(ps[:2])
+    ndgi.ndgi_hybrid_encode_fit_batch(warm, tg[:2].contiguous(), ndgi.fit_config(steps=2, batch=batch, seed=1))
+    fb = ndgi.HybridFitBatch.from_arrays(ps)
+    cfg = ndgi.fit_config(steps=steps, batch=batch, lr=1e-2, freeze_steps=steps // 10, loss_every=max(1, steps // 5),
+                          seed=23, noise_alpha=1.0 / 256)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, log = ndgi.ndgi_hybrid_encode_fit_batch(fb, tg, cfg)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    log = log.cpu().numpy()
+    t = fb.t
+    uv = ndgi.ndgi_bc7_pack_sim(t["uv_ea"], t["uv_eb"], t["uv_wt"])
+    vol = ndgi.ndgi_bc7_pack_sim(t["vol_ea"], t["vol_eb"], t["vol_wt"])
+    ut = torch.round(t["ut"] * 255).to(torch.uint8)
+    vt = torch.round(t["vt"] * 255).to(torch.uint8)
+    models = [ndgi.HybridModel(side, side, uv[i], vol[i], ut[i], vt[i],
+                               *[t[k][i] for k in ("w1", "b1", "w2", "b2", "w3", "b3")]) for i in range(tiles * tiles)]
+    table = ndgi.HybridTable(models, "fp32")
+    phys = torch.zeros((tiles * side, tiles * side, 4), dtype=torch.float32, device="cuda")
+    mse = 0.0
+    for j in range(T):
+        reqs = np.zeros(tiles * tiles, dtype=synth.PAGE_REQ_DTYPE)
+        for i in range(tiles * tiles):
+            reqs[i] = (i, 0, 0, side, side, np.float32(j / T), (i % tiles) * side, (i // tiles) * side)
+        r, _ = ndgi.page_requests_to_device(reqs)
+        table.decode(r, len(reqs), phys)
+        mse += float(((phys[..., :3] - torch.from_numpy(full[j]).cuda().float()) ** 2).mean()) / T
+    table.close()
+    rng = float(full.max()) - float(full.min())
+    return {"workload": HYBRID_FIT_BATCH_WORKLOAD.replace("300 Adam", f"{steps} Adam"), "models": tiles * tiles,
+            "steps": steps, "ms_per_step": ms / steps, "samples_per_s": steps * batch * tiles * tiles / (ms / 1e3),
+            "loss_first": float(log[0]), "loss_last": float(log[-1]),
+            "psnr_db_fit": float(10 * np.log10(rng * rng / max(log[-1], 1e-30))),
+            "psnr_db_bc7_decode_1024": float(10 * np.log10(rng * rng / max(mse, 1e-30))),
+            "bpp_bc7_per_tile": ndgi.ndgi_model_bpp(models[0], 1, 0, 16), "device_check": check_status(ndgi)}
+
+
 QUALITY_WORKLOAD = ("quality: 256^2 lightmap, 26 non-uniform keyframes (24 hourly + 2 around a light switch at "
                     "t = 0.73; a lamp on for 0.73 <= t < 0.9), UV-chart mask (~70% valid); BC4 128^2x16, temporal "
                     "26x8, MLP 24-64-64-3; 1500 Adam steps of 2^18 samples, with BC simulation (STE) and without it "
@@ -942,7 +1002,7 @@ def main():
     pages = None
     if not args.no_pages:
         pages = bench_pages(args, ndgi, torch, peaks, peak_kind, timed, rank)
-    fit = scale = hybrid = quality = fit_batch = hybrid_fit = None
+    fit = scale = hybrid = quality = fit_batch = hybrid_fit = hybrid_fit_batch = None
     if not args.no_extra:
         if not args.no_scale:
             scale = bench_scale(args, ndgi, torch, peaks, peak_kind, timed, rank)
@@ -955,6 +1015,7 @@ def main():
         fit_batch = bench_fit_batch(args, ndgi, torch)
         if not args.no_hybrid:
             hybrid_fit = bench_hybrid_fit(args, ndgi, torch)
+            hybrid_fit_batch = bench_hybrid_fit_batch(args, ndgi, torch)
 
     if rank != 0:
         if dist is not None:
@@ -1005,7 +1066,7 @@ def main():
                             "streams", "matches_device_decode": e2e_ok},
         "ms_per_step_median_of_20": ms_median,
         "gpu_launches": args.steps, "clocks": clocks,
-        "fit": fit, "fit_batch": fit_batch, "hybrid_fit": hybrid_fit, "scale": scale, "hybrid": hybrid, "quality": quality, "pages": pages,
+        "fit": fit, "fit_batch": fit_batch, "hybrid_fit": hybrid_fit, "hybrid_fit_batch": hybrid_fit_batch, "scale": scale, "hybrid": hybrid, "quality": quality, "pages": pages,
     }
     if hybrid is not None:
         h16, hr = hybrid["fp16"], hybrid["roofline"]

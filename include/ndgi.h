@@ -880,6 +880,25 @@ ndgi_status ndgi_hybrid_encode_fit(const ndgi_hybrid_fit_params *params, const u
                                    const float *key_t, const ndgi_fit_config *cfg, int32_t step_offset, void *ws,
                                    size_t ws_bytes, double *loss_log, void *stream);
 
+/*
+ * Batched per-tile fit of hybrid models (Sec. 4 trains thousands of per-tile
+ * models side by side): ndgi_hybrid_encode_fit for n_models models of one
+ * shape in one launch per step.  Each of params' fourteen tensors holds the
+ * n_models models one after another (model m at m times its single-model
+ * size), as do targets ([n_models][t_count][lm_h][lm_w][3] FP16); params'
+ * sizes are those of one model, and all models share key_t.  Model m draws
+ * its samples (and training noise) as ndgi_hybrid_encode_fit does with
+ * seed + m.  cfg->batch samples per model and step; loss_log holds the mean
+ * over all models' samples.  ws: ndgi_hybrid_encode_fit_batch_workspace_size
+ * bytes (the Adam moments of all models).
+ */
+size_t ndgi_hybrid_encode_fit_batch_workspace_size(const ndgi_hybrid_fit_params *params, int32_t n_models,
+                                                   const ndgi_fit_config *cfg);
+ndgi_status ndgi_hybrid_encode_fit_batch(const ndgi_hybrid_fit_params *params, int32_t n_models,
+                                         const uint16_t *targets, int32_t t_count, const float *key_t,
+                                         const ndgi_fit_config *cfg, int32_t step_offset, void *ws, size_t ws_bytes,
+                                         double *loss_log, void *stream);
+
 /* ======================================================================
  * Quality metrics (supplement S4.2)
  * ====================================================================== */

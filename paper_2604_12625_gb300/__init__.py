@@ -17,5 +17,6 @@ from .api import (  # noqa: F401
     ndgi_tile_metrics, ndgi_bc7_encode, ndgi_bc7_decode, ndgi_bc4x4_to_rgba8, ndgi_debug_bc7_hw_decode, ndgi_bc_sim7_to_rgba8,
     ndgi_bc7_pack_sim,
     FitBatch, ndgi_encode_fit_batch, HybridFitState, ndgi_hybrid_fit_forward,
-    ndgi_hybrid_fit_backward, ndgi_hybrid_encode_fit)
+    ndgi_hybrid_fit_backward, ndgi_hybrid_encode_fit,
+    HybridFitBatch, ndgi_hybrid_encode_fit_batch)
 

@@ -141,6 +141,8 @@ SIGNATURES = [
     ("ndgi_hybrid_fit_backward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp]),
     ("ndgi_hybrid_encode_fit_workspace_size", _sz, [_vp, _vp]),
     ("ndgi_hybrid_encode_fit", C.c_int, [_vp, _vp, _i32, _vp, _vp, _i32, _vp, _sz, _vp, _vp]),
+    ("ndgi_hybrid_encode_fit_batch_workspace_size", C.c_size_t, [_vp, _i32, _vp]),
+    ("ndgi_hybrid_encode_fit_batch", C.c_int, [_vp, _i32, _vp, _i32, _vp, _vp, _i32, _vp, C.c_size_t, _vp, _vp]),
 ]
 
 _lib = None

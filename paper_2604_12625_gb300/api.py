@@ -726,27 +726,52 @@ def ndgi_encode_fit_batch(batch, targets, cfg, step_offset=0, ws=None, loss_log=
 # ---------------------------------------------------------------------------
 # Fit of the hybrid decoder
 # ---------------------------------------------------------------------------
+def _hfit_params(t, lm_w, lm_h, address_mode, lead=0):
+    """ndgi_hybrid_fit_params of one model's shape (tensor shapes read past `lead` leading axes)."""
+    ubh, ubw = t["uv_ea"].shape[lead:lead + 2]
+    vt_, vbh, vbw = t["vol_ea"].shape[lead:lead + 3]
+    ut_t, ut_w = t["ut"].shape[lead:lead + 2]
+    vt_t, vt_h = t["vt"].shape[lead:lead + 2]
+    hidden = int(t["w2"].shape[lead])
+    shared = t["uv_wt"].dim() - lead == 3       # [uv_h/4][uv_w/4][16]: Eq. 7's weight per texel
+    return A.HybridFitParams(int(lm_w), int(lm_h), ubw * 4, ubh * 4, vbw * 4, vbh * 4, vt_, ut_w, ut_t, vt_h, vt_t,
+                             hidden, int(address_mode), *[t[k].data_ptr() for k in A.HFIT_TENSORS],
+                             int(shared)), hidden, shared
+
+
 class HybridFitState:
     """Trainable parameters of a hybrid model (float32 CUDA tensors keyed by HFIT_TENSORS) and their struct."""
 
     def __init__(self, tensors, lm_w, lm_h, address_mode=0):
         self.t = {k: _need(tensors[k], torch.float32, k) for k in A.HFIT_TENSORS}
-        ubh, ubw, four = self.t["uv_ea"].shape
-        vt_, vbh, vbw, four = self.t["vol_ea"].shape
-        ut_t, ut_w, _ = self.t["ut"].shape
-        vt_t, vt_h, _ = self.t["vt"].shape
-        self.hidden = int(self.t["w2"].shape[0])
         self.lm_w, self.lm_h = int(lm_w), int(lm_h)
-        self.shared_w = self.t["uv_wt"].dim() == 3       # [uv_h/4][uv_w/4][16]: Eq. 7's weight per texel
-        self.params = A.HybridFitParams(self.lm_w, self.lm_h, ubw * 4, ubh * 4, vbw * 4, vbh * 4, vt_, ut_w, ut_t,
-                                        vt_h, vt_t, self.hidden, int(address_mode),
-                                        *[self.t[k].data_ptr() for k in A.HFIT_TENSORS], int(self.shared_w))
+        self.params, self.hidden, self.shared_w = _hfit_params(self.t, lm_w, lm_h, address_mode)
 
     @classmethod
     def from_arrays(cls, p, device="cuda"):
         """From a dict of numpy arrays (synth.hybrid_fit_init)."""
         return cls({k: torch.from_numpy(np.ascontiguousarray(p[k], np.float32)).to(device) for k in A.HFIT_TENSORS},
                    p["lm_w"], p["lm_h"], p.get("address_mode", 0))
+
+
+class HybridFitBatch:
+    """n_models hybrid models of one shape, each tensor stacked along a leading model axis."""
+
+    def __init__(self, tensors, lm_w, lm_h, address_mode=0):
+        self.t = {k: _need(tensors[k], torch.float32, k) for k in A.HFIT_TENSORS}
+        self.n_models = int(self.t["w1"].shape[0])
+        self.lm_w, self.lm_h = int(lm_w), int(lm_h)
+        self.params, self.hidden, self.shared_w = _hfit_params(self.t, lm_w, lm_h, address_mode, lead=1)
+
+    @classmethod
+    def from_arrays(cls, ps, device="cuda"):
+        """From a list of dicts of numpy arrays (synth.hybrid_fit_init), one per model."""
+        return cls({k: torch.from_numpy(np.ascontiguousarray(np.stack([p[k] for p in ps]), np.float32)).to(device)
+                    for k in A.HFIT_TENSORS}, ps[0]["lm_w"], ps[0]["lm_h"], ps[0].get("address_mode", 0))
+
+    def model(self, i):
+        """Model i's tensors (views)."""
+        return {k: v[i] for k, v in self.t.items()}
 
 
 def ndgi_hybrid_fit_forward(state, uvt, relaxed=False, out=None, stream=None):
@@ -856,3 +881,21 @@ def ndgi_bc7_pack_sim(ea, eb, w, out=None, stream=None):
         out = torch.empty(tuple(ea.shape[:-1]) + (16,), dtype=torch.uint8, device=ea.device)
     check(lib().ndgi_bc7_pack_sim(_p(ea), _p(eb), _p(w), ea.numel() // 4, _p(out), _stream(stream)))
     return out
+
+
+def ndgi_hybrid_encode_fit_batch(batch, targets, cfg, key_t=None, step_offset=0, ws=None, loss_log=None,
+                                 stream=None):
+    """cfg.steps Adam steps of every model of a HybridFitBatch in place, one launch per step.  targets: float16
+    [n_models][T][lm_h][lm_w][3] CUDA at the keyframe times key_t (float32 CUDA [T]) or j / T.
+    Returns (ws, loss_log)."""
+    _need(targets, torch.float16, "targets")
+    n = int(lib().ndgi_hybrid_encode_fit_batch_workspace_size(C.byref(batch.params), batch.n_models, C.byref(cfg)))
+    if ws is None:
+        ws = torch.empty(n, dtype=torch.uint8, device=targets.device)
+    if loss_log is None and cfg.loss_every > 0:
+        loss_log = torch.zeros((cfg.steps + cfg.loss_every - 1) // cfg.loss_every, dtype=torch.float64,
+                               device=targets.device)
+    check(lib().ndgi_hybrid_encode_fit_batch(C.byref(batch.params), batch.n_models, _p(targets),
+                                             int(targets.shape[1]), _p(key_t), C.byref(cfg), int(step_offset),
+                                             _p(ws), ws.numel(), _p(loss_log), _stream(stream)))
+    return ws, loss_log

@@ -17,6 +17,8 @@
 // generator) and takes the MSE against keyframe targets interpolated at t.
 #include <cuda_fp16.h>
 
+#include <climits>
+
 #include "bc4.cuh"
 #include "bc7.cuh"
 #include "ndgi_internal.h"
@@ -40,7 +42,23 @@ struct HFitArgs {
   uint64_t seed;
   const int64_t* step;
   double* loss_acc;
+  int64_t ms[14];          // batched fit: elements of each tensor per model (model m at m * ms[k])
+  int64_t tgt_stride;      // batched fit: target elements per model
 };
+
+// Batched fit: CTA row m trains model m of the stacked tensors, with samples
+// (and noise) drawn from seed + m.
+__device__ __forceinline__ void hfit_select_model(HFitArgs& a) {
+  const int64_t m = blockIdx.y;
+  if (m == 0) return;
+#pragma unroll
+  for (int k = 0; k < 14; ++k) {
+    a.p[k] += m * a.ms[k];
+    a.g[k] += m * a.ms[k];
+  }
+  a.targets += m * a.tgt_stride;
+  a.seed += (uint64_t)m;
+}
 enum { kUvEa, kUvEb, kUvWt, kVolEa, kVolEb, kVolWt, kUt, kVt, kW1, kB1, kW2, kB2, kW3, kB3 };
 
 // Straight-through value of texel p of BC entry e (block * 4 + channel) and its factors.
@@ -242,8 +260,10 @@ struct HFitSmem {
 };
 
 template <int H, int MODE>
-__global__ void __launch_bounds__(kHfTile, 1) k_hfit_backward(HFitArgs a) {
+__global__ void __launch_bounds__(kHfTile, 1) k_hfit_backward(HFitArgs a_in) {
   using S = HFitSmem<H>;
+  HFitArgs a = a_in;
+  if (MODE == 1) hfit_select_model(a);
   constexpr int R = S::R;
   constexpr int E2 = (H * H + kHfTile - 1) / kHfTile, E1 = (16 * H + kHfTile - 1) / kHfTile;
   constexpr int E3 = (3 * H + 3 + kHfTile - 1) / kHfTile;   // dW3 entries, then db3
@@ -485,7 +505,7 @@ __global__ void k_hfit_adam(HAdam t) {
 
 __global__ void k_hfit_step_end(int64_t* step, int64_t* local, const double* loss_acc, double* loss_log, int every,
                                 int64_t batch) {
-  const int64_t l = *local;
+  const int64_t l = *local;   // batch: samples of the step over all models
   if (loss_log && every > 0 && l % every == 0) loss_log[l / every] = *loss_acc / (3.0 * (double)batch);
   *local = l + 1;
   *step = *step + 1;
@@ -515,9 +535,18 @@ static cudaError_t launch_hfit_forward(const HFitArgs& a, float* rgb, cudaStream
   return cudaErrorInvalidValue;
 }
 
-static cudaError_t launch_hfit_backward(const HFitArgs& a, int mode, cudaStream_t s) {
-  const int64_t tiles = (a.n + kHfTile - 1) / kHfTile;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms()));
+static cudaError_t launch_hfit_backward(const HFitArgs& a, int mode, cudaStream_t s, int n_models = 1) {
+  const int64_t tiles = (a.n + kHfTile - 1) / kHfTile, sms = num_sms();
+  // CTAs per model (one CTA per SM): the count with the fewest waves x tiles per CTA
+  int64_t per_model = 1, best = INT64_MAX;
+  for (int64_t c = 1; c <= std::min<int64_t>(tiles, std::max<int64_t>(1, 2 * sms / n_models + 1)); ++c) {
+    const int64_t cost = ((c * n_models + sms - 1) / sms) * ((tiles + c - 1) / c);
+    if (cost < best) {
+      best = cost;
+      per_model = c;
+    }
+  }
+  const dim3 grid((unsigned)per_model, (unsigned)n_models);
 #define X(H)                                                                                          \
   if (a.hidden == H) {                                                                                \
     const size_t smem = sizeof(float) * HFitSmem<H>::kFloats;                                         \
@@ -574,6 +603,114 @@ static HFitArgs make_hfit_args(const ndgi_hybrid_fit_params* p) {
 
 static size_t round256h(size_t b) { return (b + 255) / 256 * 256; }
 
+static size_t hfit_ws_bytes(const ndgi_hybrid_fit_params* params, int32_t n_models) {
+  if (!params || n_models < 1) return 0;
+  int64_t n[14];
+  hfit_sizes(params, n);
+  int64_t tot = 0;
+  for (int k = 0; k < 14; ++k) tot += n[k];
+  return 256 + 3 * round256h((size_t)tot * n_models * sizeof(float));
+}
+
+static ndgi_status hybrid_encode_fit(const ndgi_hybrid_fit_params* params, int32_t n_models, const uint16_t* targets,
+                                     int32_t t_count, const float* key_t, const ndgi_fit_config* cfg,
+                                     int32_t step_offset, void* ws, size_t ws_bytes, double* loss_log, void* stream,
+                                     const char* who) {
+  ndgi_status st = check_hfit(params, who);
+  if (st != NDGI_OK) return st;
+  if (n_models < 1) return set_error(NDGI_ERR_INVALID_ARG, "%s: n_models < 1", who);
+  if (!cfg || !targets || !ws || t_count <= 0) return set_error(NDGI_ERR_INVALID_ARG, "%s: bad argument", who);
+  if (cfg->steps < 0 || cfg->batch <= 0 || cfg->freeze_steps < 0 || cfg->loss_every < 0 || step_offset < 0)
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: bad config", who);
+  if (!(cfg->lr > 0.0f) || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f))
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: bad optimiser settings", who);
+  if (!(cfg->noise_alpha >= 0.0f && cfg->noise_alpha <= 1.0f))
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: noise_alpha must be in [0, 1]", who);
+  const size_t need = hfit_ws_bytes(params, n_models);
+  if (ws_bytes < need || ((uintptr_t)ws % 256))
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: ws must be 256-byte aligned with >= %zu bytes", who, need);
+  if (cfg->steps == 0) return NDGI_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t n[14];
+  hfit_sizes(params, n);
+  HFitArgs a = make_hfit_args(params);
+  HAdam t{};
+  int64_t tot = 0;
+  for (int k = 0; k < 14; ++k) {
+    a.ms[k] = n[k];
+    t.p[k] = const_cast<float*>(a.p[k]);
+    t.off[k] = tot;
+    tot += n[k] * n_models;   // each tensor holds the n_models models one after another
+  }
+  a.tgt_stride = (int64_t)t_count * params->lm_h * params->lm_w * 3;
+  t.off[14] = tot;
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  int64_t* d_step = reinterpret_cast<int64_t*>(base);
+  int64_t* d_local = d_step + 1;
+  double* d_loss = reinterpret_cast<double*>(base + 16);
+  const size_t tb = round256h((size_t)tot * sizeof(float));
+  float* g = reinterpret_cast<float*>(base + 256);
+  float* m = reinterpret_cast<float*>(base + 256 + tb);
+  float* v = reinterpret_cast<float*>(base + 256 + 2 * tb);
+  const int64_t init[2] = {step_offset, 0};
+  cudaError_t e = cudaMemcpyAsync(d_step, init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // `init` lives on this stack frame
+  if (e == cudaSuccess && step_offset == 0) e = cudaMemsetAsync(m, 0, 2 * tb, s);
+  if (e != cudaSuccess) return cuda_status(e, who);
+  t.g = g;
+  t.m = m;
+  t.v = v;
+  t.step = d_step;
+  t.local = d_local;
+  t.freeze_from = (int64_t)cfg->steps - cfg->freeze_steps;
+  t.lr = cfg->lr;
+  t.beta1 = cfg->beta1;
+  t.beta2 = cfg->beta2;
+  t.eps = cfg->eps;
+  for (int k = 0; k < 14; ++k) a.g[k] = g + t.off[k];
+  a.relaxed = cfg->relaxed != 0;
+  a.noise_alpha = cfg->noise_alpha;
+  a.n = cfg->batch;
+  a.targets = reinterpret_cast<const __half*>(targets);
+  a.t_count = t_count;
+  a.key_t = key_t;
+  a.seed = cfg->seed;
+  a.step = d_step;
+  a.loss_acc = d_loss;
+  // one step captured as a graph (zero grads and loss, backward, Adam, counters) and replayed
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_status(e, who);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  cudaError_t le = cudaSuccess;
+  if (e == cudaSuccess) {
+    le = cudaMemsetAsync(g, 0, (size_t)tot * sizeof(float), cs);
+    if (le == cudaSuccess) le = cudaMemsetAsync(d_loss, 0, sizeof(double), cs);
+    if (le == cudaSuccess) le = launch_hfit_backward(a, 1, cs, n_models);
+    if (le == cudaSuccess) {
+      const int64_t blocks = std::min<int64_t>((tot + 255) / 256, (int64_t)num_sms() * 8);
+      k_hfit_adam<<<(int)std::max<int64_t>(blocks, 1), 256, 0, cs>>>(t);
+      le = cudaGetLastError();
+    }
+    if (le == cudaSuccess) {
+      k_hfit_step_end<<<1, 1, 0, cs>>>(d_step, d_local, d_loss, loss_log, cfg->loss_every,
+                                       (int64_t)cfg->batch * n_models);
+      le = cudaGetLastError();
+    }
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  if (le != cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  for (int i = 0; e == cudaSuccess && i < cfg->steps; ++i) e = cudaGraphLaunch(exec, s);
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaStreamDestroy(cs);
+  return cuda_status(e, who);
+}
+
+
 }  // namespace ndgi
 
 using namespace ndgi;
@@ -616,106 +753,28 @@ ndgi_status ndgi_hybrid_fit_backward(const ndgi_hybrid_fit_params* params, const
 
 size_t ndgi_hybrid_encode_fit_workspace_size(const ndgi_hybrid_fit_params* params, const ndgi_fit_config* cfg) {
   (void)cfg;
-  if (!params) return 0;
-  int64_t n[14];
-  hfit_sizes(params, n);
-  int64_t tot = 0;
-  for (int k = 0; k < 14; ++k) tot += n[k];
-  return 256 + 3 * round256h((size_t)tot * sizeof(float));
+  return hfit_ws_bytes(params, 1);
+}
+
+size_t ndgi_hybrid_encode_fit_batch_workspace_size(const ndgi_hybrid_fit_params* params, int32_t n_models,
+                                                   const ndgi_fit_config* cfg) {
+  (void)cfg;
+  return hfit_ws_bytes(params, n_models);
 }
 
 ndgi_status ndgi_hybrid_encode_fit(const ndgi_hybrid_fit_params* params, const uint16_t* targets, int32_t t_count,
                                    const float* key_t, const ndgi_fit_config* cfg, int32_t step_offset, void* ws,
                                    size_t ws_bytes, double* loss_log, void* stream) {
-  ndgi_status st = check_hfit(params, "ndgi_hybrid_encode_fit");
-  if (st != NDGI_OK) return st;
-  if (!cfg || !targets || !ws || t_count <= 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_encode_fit: bad argument");
-  if (cfg->steps < 0 || cfg->batch <= 0 || cfg->freeze_steps < 0 || cfg->loss_every < 0 || step_offset < 0)
-    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_encode_fit: bad config");
-  if (!(cfg->lr > 0.0f) || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f))
-    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_encode_fit: bad optimiser settings");
-  if (!(cfg->noise_alpha >= 0.0f && cfg->noise_alpha <= 1.0f))
-    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_encode_fit: noise_alpha must be in [0, 1]");
-  const size_t need = ndgi_hybrid_encode_fit_workspace_size(params, cfg);
-  if (ws_bytes < need || ((uintptr_t)ws % 256))
-    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_encode_fit: ws must be 256-byte aligned with >= %zu bytes",
-                     need);
-  if (cfg->steps == 0) return NDGI_OK;
-  cudaStream_t s = (cudaStream_t)stream;
-  int64_t n[14];
-  hfit_sizes(params, n);
-  HFitArgs a = make_hfit_args(params);
-  HAdam t{};
-  int64_t tot = 0;
-  for (int k = 0; k < 14; ++k) {
-    t.p[k] = const_cast<float*>(a.p[k]);
-    t.off[k] = tot;
-    tot += n[k];
-  }
-  t.off[14] = tot;
-  unsigned char* base = static_cast<unsigned char*>(ws);
-  int64_t* d_step = reinterpret_cast<int64_t*>(base);
-  int64_t* d_local = d_step + 1;
-  double* d_loss = reinterpret_cast<double*>(base + 16);
-  const size_t tb = round256h((size_t)tot * sizeof(float));
-  float* g = reinterpret_cast<float*>(base + 256);
-  float* m = reinterpret_cast<float*>(base + 256 + tb);
-  float* v = reinterpret_cast<float*>(base + 256 + 2 * tb);
-  const int64_t init[2] = {step_offset, 0};
-  cudaError_t e = cudaMemcpyAsync(d_step, init, sizeof(init), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // `init` lives on this stack frame
-  if (e == cudaSuccess && step_offset == 0) e = cudaMemsetAsync(m, 0, 2 * tb, s);
-  if (e != cudaSuccess) return cuda_status(e, "ndgi_hybrid_encode_fit: init");
-  t.g = g;
-  t.m = m;
-  t.v = v;
-  t.step = d_step;
-  t.local = d_local;
-  t.freeze_from = (int64_t)cfg->steps - cfg->freeze_steps;
-  t.lr = cfg->lr;
-  t.beta1 = cfg->beta1;
-  t.beta2 = cfg->beta2;
-  t.eps = cfg->eps;
-  for (int k = 0; k < 14; ++k) a.g[k] = g + t.off[k];
-  a.relaxed = cfg->relaxed != 0;
-  a.noise_alpha = cfg->noise_alpha;
-  a.n = cfg->batch;
-  a.targets = reinterpret_cast<const __half*>(targets);
-  a.t_count = t_count;
-  a.key_t = key_t;
-  a.seed = cfg->seed;
-  a.step = d_step;
-  a.loss_acc = d_loss;
-  // one step captured as a graph (zero grads and loss, backward, Adam, counters) and replayed
-  cudaStream_t cs = nullptr;
-  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  if (e != cudaSuccess) return cuda_status(e, "ndgi_hybrid_encode_fit: stream");
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  cudaError_t le = cudaSuccess;
-  if (e == cudaSuccess) {
-    le = cudaMemsetAsync(g, 0, (size_t)tot * sizeof(float), cs);
-    if (le == cudaSuccess) le = cudaMemsetAsync(d_loss, 0, sizeof(double), cs);
-    if (le == cudaSuccess) le = launch_hfit_backward(a, 1, cs);
-    if (le == cudaSuccess) {
-      const int64_t blocks = std::min<int64_t>((tot + 255) / 256, (int64_t)num_sms() * 8);
-      k_hfit_adam<<<(int)std::max<int64_t>(blocks, 1), 256, 0, cs>>>(t);
-      le = cudaGetLastError();
-    }
-    if (le == cudaSuccess) {
-      k_hfit_step_end<<<1, 1, 0, cs>>>(d_step, d_local, d_loss, loss_log, cfg->loss_every, cfg->batch);
-      le = cudaGetLastError();
-    }
-    e = cudaStreamEndCapture(cs, &graph);
-  }
-  if (le != cudaSuccess) e = le;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
-  for (int i = 0; e == cudaSuccess && i < cfg->steps; ++i) e = cudaGraphLaunch(exec, s);
-  if (exec) cudaGraphExecDestroy(exec);
-  cudaStreamDestroy(cs);
-  return cuda_status(e, "ndgi_hybrid_encode_fit");
+  return hybrid_encode_fit(params, 1, targets, t_count, key_t, cfg, step_offset, ws, ws_bytes, loss_log, stream,
+                           "ndgi_hybrid_encode_fit");
+}
+
+ndgi_status ndgi_hybrid_encode_fit_batch(const ndgi_hybrid_fit_params* params, int32_t n_models,
+                                         const uint16_t* targets, int32_t t_count, const float* key_t,
+                                         const ndgi_fit_config* cfg, int32_t step_offset, void* ws, size_t ws_bytes,
+                                         double* loss_log, void* stream) {
+  return hybrid_encode_fit(params, n_models, targets, t_count, key_t, cfg, step_offset, ws, ws_bytes, loss_log,
+                           stream, "ndgi_hybrid_encode_fit_batch");
 }
 
 }  // extern "C"

@@ -162,3 +162,54 @@ def test_shared_weight_fit_packs_exactly_to_bc7(ndgi):
     t["vt"].copy_(vt.float() / 255)
     fwd = ndgi.ndgi_hybrid_fit_forward(st, qq).cpu().numpy()
     assert rel_err(dec, fwd) <= 1e-5
+
+
+@pytest.mark.parametrize("shared,noise", [(False, 0.0), (True, 1.0 / 256)])
+def test_batched_fit_matches_oracle_loops(ndgi, shared, noise):
+    """Three stacked models, two steps: each model follows the oracle's loop with its own stream (seed + m)."""
+    n_models, lm, T, batch, seed = 3, 64, 4, 1024, 70
+    ps = [params(71 + m, 16, shared) for m in range(n_models)]
+    targets = np.stack([synth.fit_targets(80 + m, lm, lm, T, n_gauss=6) for m in range(n_models)])
+    fb = ndgi.HybridFitBatch.from_arrays(ps)
+    cfg = ndgi.fit_config(steps=2, batch=batch, lr=1e-2, loss_every=1, seed=seed, noise_alpha=noise)
+    _, log = ndgi.ndgi_hybrid_encode_fit_batch(fb, torch.from_numpy(targets).cuda(), cfg)
+    torch.cuda.synchronize()
+    losses = np.zeros(2)
+    for m in range(n_models):
+        q = {k: np.asarray(ps[m][k], np.float32).copy() for k in KEYS}
+        qd = dict(ps[m])
+        mom = {k: (np.zeros(q[k].size), np.zeros(q[k].size)) for k in KEYS}
+        for step in range(2):
+            texel, s = oracle.fit_draw(seed + m, step, batch, lm, lm)
+            tg = oracle.fit_targets_at(targets[m], texel, s)
+            qd.update(q)
+            nz = oracle.fit_noise(seed + m, step, batch, noise) if noise else None
+            loss, g = oracle.hfit_backward(qd, s, tg, noise=nz)
+            losses[step] += loss / n_models
+            for i, k in enumerate(KEYS):
+                oracle.adam(q[k].reshape(-1), g[k].reshape(-1), mom[k][0], mom[k][1], step + 1, 1e-2,
+                            project=i < 8)
+        got = fb.model(m)
+        for k in KEYS:
+            a = got[k].cpu().numpy()
+            close = np.mean(np.abs(a - q[k]) <= 1e-4 + 1e-3 * np.abs(q[k]))
+            assert close > 0.99, (m, k, close)
+    assert np.allclose(log.cpu().numpy(), losses, rtol=1e-4)
+
+
+def test_batched_fit_equals_separate_fits(ndgi):
+    n_models, lm, T, batch, seed = 2, 64, 4, 4096, 90
+    ps = [params(91 + m, 64, True) for m in range(n_models)]
+    targets = np.stack([synth.fit_targets(95 + m, lm, lm, T, n_gauss=6) for m in range(n_models)])
+    cfg = ndgi.fit_config(steps=20, batch=batch, lr=1e-2, loss_every=20, seed=seed)
+    fb = ndgi.HybridFitBatch.from_arrays(ps)
+    ndgi.ndgi_hybrid_encode_fit_batch(fb, torch.from_numpy(targets).cuda(), cfg)
+    for m in range(n_models):
+        st = ndgi.HybridFitState.from_arrays(ps[m])
+        cfg_m = ndgi.fit_config(steps=20, batch=batch, lr=1e-2, loss_every=20, seed=seed + m)
+        ndgi.ndgi_hybrid_encode_fit(st, torch.from_numpy(targets[m]).cuda(), cfg_m)
+        got = fb.model(m)
+        for k in KEYS:
+            a, b = got[k].cpu().numpy(), st.t[k].cpu().numpy()
+            close = np.mean(np.abs(a - b) <= 1e-4 + 1e-3 * np.abs(b))   # FP32 atomics order only
+            assert close > 0.99, (m, k, close)
