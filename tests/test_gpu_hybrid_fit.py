@@ -213,3 +213,22 @@ def test_batched_fit_equals_separate_fits(ndgi):
             a, b = got[k].cpu().numpy(), st.t[k].cpu().numpy()
             close = np.mean(np.abs(a - b) <= 1e-4 + 1e-3 * np.abs(b))   # FP32 atomics order only
             assert close > 0.99, (m, k, close)
+
+
+def test_fit_resumes_from_its_workspace(ndgi):
+    """Two calls of 3 steps (the second with step_offset = 3 and the first call's workspace, which holds the Adam
+    moments) follow the same trajectory as one call of 6 steps: same samples, same bias corrections."""
+    p = params(17, 16, shared=True)
+    lm, T = 64, 4
+    targets = torch.from_numpy(synth.fit_targets(18, lm, lm, T, n_gauss=6)).cuda()
+    one = ndgi.HybridFitState.from_arrays(p)
+    _, log1 = ndgi.ndgi_hybrid_encode_fit(one, targets, ndgi.fit_config(steps=6, batch=2048, loss_every=1, seed=19))
+    two = ndgi.HybridFitState.from_arrays(p)
+    ws, log_a = ndgi.ndgi_hybrid_encode_fit(two, targets, ndgi.fit_config(steps=3, batch=2048, loss_every=1,
+                                                                          seed=19))
+    _, log_b = ndgi.ndgi_hybrid_encode_fit(two, targets, ndgi.fit_config(steps=3, batch=2048, loss_every=1, seed=19),
+                                           step_offset=3, ws=ws)
+    assert np.allclose(np.concatenate([log_a.cpu().numpy(), log_b.cpu().numpy()]), log1.cpu().numpy(), rtol=1e-5)
+    for k in KEYS:
+        a, b = one.t[k].cpu().numpy(), two.t[k].cpu().numpy()
+        assert np.mean(np.abs(a - b) <= 1e-5 + 1e-4 * np.abs(b)) > 0.99, k
