@@ -167,11 +167,13 @@ __device__ __forceinline__ float hfit_value(const HFitArgs& a, int map, int64_t 
   return __ldg(a.p[map == 2 ? kUt : kVt] + e);
 }
 
-// The decoder input x[16] of a query.
-__device__ __forceinline__ void hfit_inputs(const HFitArgs& a, float u, float v, float t, float (&x)[16]) {
+// The decoder input x[16] of a query; with q >= 0 only the inputs k with
+// k % 4 == q (the others are left 0).
+__device__ __forceinline__ void hfit_inputs(const HFitArgs& a, float u, float v, float t, float (&x)[16], int q = -1) {
 #pragma unroll
   for (int k = 0; k < 12; ++k) x[k] = 0.0f;
   hfit_for_each_tap(a, u, v, t, [&](int k, int map, int64_t e, int p, float w) {
+    if (q >= 0 && (k & 3) != q) return;
     float d0, d1, d2;
     x[k] = fmaf(w, hfit_value(a, map, e, p, d0, d1, d2), x[k]);
   });
@@ -179,9 +181,12 @@ __device__ __forceinline__ void hfit_inputs(const HFitArgs& a, float u, float v,
   sincospif(2.0f * t, &x[14], &x[15]);
 }
 
-// Scatters dL/dx[k] (k < 12) to the feature-map parameters of the query's taps.
-__device__ __forceinline__ void hfit_scatter(const HFitArgs& a, float u, float v, float t, const float (&gx)[16]) {
+// Scatters dL/dx[k] (k < 12) to the feature-map parameters of the query's taps
+// (with q >= 0 only the inputs k with k % 4 == q).
+__device__ __forceinline__ void hfit_scatter(const HFitArgs& a, float u, float v, float t, const float (&gx)[16],
+                                             int q = -1) {
   hfit_for_each_tap(a, u, v, t, [&](int k, int map, int64_t e, int p, float w) {
+    if (q >= 0 && (k & 3) != q) return;
     float d0, d1, d2;
     hfit_value(a, map, e, p, d0, d1, d2);
     const float g = w * gx[k];
@@ -239,17 +244,34 @@ __global__ void __launch_bounds__(128) k_hfit_forward(HFitArgs a, float* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Backward: tiles of kHfTile samples, one thread per sample.
+// Backward: tiles of kHfTile samples, kHfQ = 4 threads per sample.  Thread
+// (r, q) of sample r owns hidden units q H/4 .. (q+1) H/4 - 1 of both layers
+// and the feature inputs k with k % 4 == q (their BC simulation, noise and
+// gradient scatter).  A sample's four threads are adjacent lanes of one warp:
+// the per-sample rows in shared memory are exchanged with __syncwarp between
+// the layers.  Then the whole CTA forms the tile's weight gradients as sums
+// over the samples, each thread owning fixed entries in registers across
+// tiles, added to global memory once at the end.
 // ---------------------------------------------------------------------------
 constexpr int kHfTile = 128;
+constexpr int kHfQ = 4;
+constexpr int kHfThreads = kHfTile * kHfQ;
 
 // Shared memory: the MLP (forward and backward), then per-sample rows padded
-// to H + 1 floats (conflict-free column access): inputs, h1, z1 -> dz1,
-// z2 -> dz2, h2, dL/drgb.
+// to H + 4 floats (whole float4s; the 8 samples of a warp hit 8 distinct
+// banks): inputs, h1, z1 -> dz1, z2 -> dz2, h2, dL/drgb.
 template <int H>
 struct HFitSmem {
-  static constexpr int R = H + 1;
-  static constexpr int kW1 = 0, kB1 = kW1 + 16 * H, kW2 = kB1 + H, kB2 = kW2 + H * H, kW3 = kB2 + H, kB3 = kW3 + 3 * H;
+  static constexpr int R = H + 4;
+  static constexpr int HQ = H / kHfQ;
+  static constexpr int HS = H + 4 * kHfQ;   // skewed weight row: each quarter's HQ columns + 4 padding floats
+  __host__ __device__ static constexpr int skew(int o) { return o + 4 * (o / HQ); }
+  static constexpr int kW1 = 0;                     // [16][HS]  W1, skewed columns
+  static constexpr int kB1 = kW1 + 16 * HS;
+  static constexpr int kW2 = kB1 + H;               // [H][HS]   W2 (row = input), skewed columns
+  static constexpr int kW2t = kW2 + H * HS;         // [H][HS]   W2^T (row = output), skewed columns
+  static constexpr int kB2 = kW2t + H * HS;
+  static constexpr int kW3 = kB2 + H, kB3 = kW3 + 3 * H;
   static constexpr int kX = kB3 + 4;                    // [tile][17]
   static constexpr int kH1 = kX + kHfTile * 17;
   static constexpr int kZ1 = kH1 + kHfTile * R;
@@ -260,19 +282,27 @@ struct HFitSmem {
 };
 
 template <int H, int MODE>
-__global__ void __launch_bounds__(kHfTile, 1) k_hfit_backward(HFitArgs a_in) {
+__global__ void __launch_bounds__(kHfThreads, 1) k_hfit_backward(HFitArgs a_in) {
   using S = HFitSmem<H>;
   HFitArgs a = a_in;
   if (MODE == 1) hfit_select_model(a);
-  constexpr int R = S::R;
-  constexpr int E2 = (H * H + kHfTile - 1) / kHfTile, E1 = (16 * H + kHfTile - 1) / kHfTile;
-  constexpr int E3 = (3 * H + 3 + kHfTile - 1) / kHfTile;   // dW3 entries, then db3
+  constexpr int R = S::R, HQ = H / kHfQ;
+  constexpr bool kBlocked = H == 64;   // dW2 as 2 x 4 register blocks per thread (512 threads x 8 = 64 x 64)
+  static_assert(!kBlocked || (S::kZ2 % 4 == 0 && S::R % 4 == 0), "float4-aligned dZ2 rows");
+  constexpr int E2 = (H * H + kHfThreads - 1) / kHfThreads, E1 = (16 * H + kHfThreads - 1) / kHfThreads;
+  constexpr int E3 = (3 * H + 3 + kHfThreads - 1) / kHfThreads;   // dW3 entries, then db3
   extern __shared__ float sm[];
   const int tid = threadIdx.x;
-  for (int i = tid; i < 16 * H; i += kHfTile) sm[S::kW1 + i] = a.p[kW1][i];
-  for (int i = tid; i < H * H; i += kHfTile) sm[S::kW2 + i] = a.p[kW2][i];
-  for (int i = tid; i < 3 * H; i += kHfTile) sm[S::kW3 + i] = a.p[kW3][i];
-  for (int i = tid; i < H; i += kHfTile) {
+  constexpr int HS = S::HS;
+  for (int i = tid; i < 16 * H; i += kHfThreads) sm[S::kW1 + (i / H) * HS + S::skew(i % H)] = a.p[kW1][i];
+  for (int i = tid; i < H * H; i += kHfThreads) {
+    const int ri = i / H, co = i % H;   // W2[ri][co]: input ri, output co
+    const float w = a.p[kW2][i];
+    sm[S::kW2 + ri * HS + S::skew(co)] = w;
+    sm[S::kW2t + co * HS + S::skew(ri)] = w;
+  }
+  for (int i = tid; i < 3 * H; i += kHfThreads) sm[S::kW3 + i] = a.p[kW3][i];
+  for (int i = tid; i < H; i += kHfThreads) {
     sm[S::kB1 + i] = a.p[kB1][i];
     sm[S::kB2 + i] = a.p[kB2][i];
   }
@@ -280,13 +310,16 @@ __global__ void __launch_bounds__(kHfTile, 1) k_hfit_backward(HFitArgs a_in) {
   __syncthreads();
   const float* sW1 = sm + S::kW1;
   const float* sW2 = sm + S::kW2;
+  const float* sW2t = sm + S::kW2t;
   const float* sW3 = sm + S::kW3;
-  float* xr = sm + S::kX + tid * 17;
-  float* h1 = sm + S::kH1 + tid * R;
-  float* z1 = sm + S::kZ1 + tid * R;
-  float* z2 = sm + S::kZ2 + tid * R;
-  float* h2 = sm + S::kH2 + tid * R;
-  float* dyr = sm + S::kDY + tid * 4;
+  const int r = tid / kHfQ, q = tid % kHfQ, o0 = q * HQ, c0 = S::skew(o0);
+  static_assert(HQ % 4 == 0, "float4 blocks of a quarter's units");
+  float* xr = sm + S::kX + r * 17;
+  float* h1 = sm + S::kH1 + r * R;
+  float* z1 = sm + S::kZ1 + r * R;
+  float* z2 = sm + S::kZ2 + r * R;
+  float* h2 = sm + S::kH2 + r * R;
+  float* dyr = sm + S::kDY + r * 4;
   float acc2[E2], acc1[E1], acc3[E3], accb1 = 0.0f, accb2 = 0.0f;
 #pragma unroll
   for (int j = 0; j < E3; ++j) acc3[j] = 0.0f;
@@ -299,8 +332,8 @@ __global__ void __launch_bounds__(kHfTile, 1) k_hfit_backward(HFitArgs a_in) {
   if (MODE == 1) step = *a.step;
   const int64_t tiles = (a.n + kHfTile - 1) / kHfTile;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t s = tile * kHfTile + tid;
-    const bool valid = s < a.n;
+    const int64_t s = tile * kHfTile + r;
+    const bool valid = s < a.n;   // uniform over the sample's four threads
     float u = 0.5f, v = 0.5f, t = 0.0f;
     int ix = 0, iy = 0;
     if (valid) {
@@ -314,36 +347,81 @@ __global__ void __launch_bounds__(kHfTile, 1) k_hfit_backward(HFitArgs a_in) {
         v = ((float)iy + 0.5f) / (float)a.lm_h;
       }
     }
-    // ---- forward of this thread's sample ----
-    float x[16];
-    hfit_inputs(a, u, v, t, x);
-    if (MODE == 1 && valid && a.noise_alpha > 0.0f) {   // V' = V + U(-1/2, 1/2) alpha
-      const uint64_t g = 0x9E3779B97F4A7C15ull;
-      const uint64_t b = (a.seed ^ 0x6E6F697365ull) + 12ull * (((uint64_t)step << 32) + (uint64_t)s) * g;
+    // ---- this thread's inputs k = q, q + 4, q + 8 (and gamma component 12 + q) ----
+    {
+      float x[16];
+      hfit_inputs(a, u, v, t, x, q);
+      if (MODE == 1 && valid && a.noise_alpha > 0.0f) {   // V' = V + U(-1/2, 1/2) alpha
+        const uint64_t g = 0x9E3779B97F4A7C15ull;
+        const uint64_t b = (a.seed ^ 0x6E6F697365ull) + 12ull * (((uint64_t)step << 32) + (uint64_t)s) * g;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        const uint64_t z = splitmix64(b + (uint64_t)k * g);
-        x[k] += a.noise_alpha * ((float)(uint32_t)(z >> 40) * 0x1p-24f - 0.5f);
+        for (int k = 0; k < 12; ++k)
+          if ((k & 3) == q) {
+            const uint64_t z = splitmix64(b + (uint64_t)k * g);
+            x[k] += a.noise_alpha * ((float)(uint32_t)(z >> 40) * 0x1p-24f - 0.5f);
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if ((k & 3) == q) xr[k] = x[k];
+    }
+    __syncwarp();
+    // ---- layer 1 and layer 2 for this thread's units; the output's partial sums ----
+    {
+      float acc[HQ];
+#pragma unroll
+      for (int u1 = 0; u1 < HQ; ++u1) acc[u1] = sm[S::kB1 + o0 + u1];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float xv = xr[k];
+#pragma unroll
+        for (int u4 = 0; u4 < HQ / 4; ++u4) {
+          const float4 w = *reinterpret_cast<const float4*>(sW1 + k * HS + c0 + 4 * u4);
+          acc[4 * u4] = fmaf(xv, w.x, acc[4 * u4]);
+          acc[4 * u4 + 1] = fmaf(xv, w.y, acc[4 * u4 + 1]);
+          acc[4 * u4 + 2] = fmaf(xv, w.z, acc[4 * u4 + 2]);
+          acc[4 * u4 + 3] = fmaf(xv, w.w, acc[4 * u4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int u1 = 0; u1 < HQ; ++u1) {
+        z1[o0 + u1] = acc[u1];
+        h1[o0 + u1] = gelu32(acc[u1]);
+      }
+    }
+    __syncwarp();
+    float y[3] = {0.0f, 0.0f, 0.0f};
+    {
+      float acc[HQ];
+#pragma unroll
+      for (int u1 = 0; u1 < HQ; ++u1) acc[u1] = sm[S::kB2 + o0 + u1];
+#pragma unroll 4
+      for (int i = 0; i < H; ++i) {
+        const float hv = h1[i];
+#pragma unroll
+        for (int u4 = 0; u4 < HQ / 4; ++u4) {
+          const float4 w = *reinterpret_cast<const float4*>(sW2 + i * HS + c0 + 4 * u4);
+          acc[4 * u4] = fmaf(hv, w.x, acc[4 * u4]);
+          acc[4 * u4 + 1] = fmaf(hv, w.y, acc[4 * u4 + 1]);
+          acc[4 * u4 + 2] = fmaf(hv, w.z, acc[4 * u4 + 2]);
+          acc[4 * u4 + 3] = fmaf(hv, w.w, acc[4 * u4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int u1 = 0; u1 < HQ; ++u1) {
+        const int o = o0 + u1;
+        z2[o] = acc[u1];
+        const float hh = gelu32(acc[u1]);
+        h2[o] = hh;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, sW3[o * 3 + c], y[c]);
       }
     }
 #pragma unroll
-    for (int k = 0; k < 16; ++k) xr[k] = x[k];
-    for (int o = 0; o < H; ++o) {
-      float z = sm[S::kB1 + o];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) z = fmaf(x[k], sW1[k * H + o], z);
-      z1[o] = z;
-      h1[o] = gelu32(z);
-    }
-    float y[3] = {sm[S::kB3], sm[S::kB3 + 1], sm[S::kB3 + 2]};
-    for (int o = 0; o < H; ++o) {
-      float z = sm[S::kB2 + o];
-      for (int i = 0; i < H; ++i) z = fmaf(h1[i], sW2[i * H + o], z);
-      z2[o] = z;
-      const float hh = gelu32(z);
-      h2[o] = hh;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, sW3[o * 3 + c], y[c]);
+    for (int c = 0; c < 3; ++c) {   // the four quarters' partial outputs
+      y[c] += __shfl_xor_sync(0xffffffffu, y[c], 1);
+      y[c] += __shfl_xor_sync(0xffffffffu, y[c], 2);
+      y[c] += sm[S::kB3 + c];
     }
     float dy[3] = {0.0f, 0.0f, 0.0f};
     if (valid) {
@@ -360,84 +438,132 @@ __global__ void __launch_bounds__(kHfTile, 1) k_hfit_backward(HFitArgs a_in) {
           const float tg = (1.0f - al) * __half2float(a.targets[j0 * plane + px + c]) +
                            al * __half2float(a.targets[j1 * plane + px + c]);
           const float d = y[c] - tg;
-          loss += (double)d * d;
+          if (q == 0) loss += (double)d * d;
           dy[c] = 2.0f * d / (3.0f * (float)a.n);
         }
       }
     }
+    if (q == 0) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dyr[c] = dy[c];
-    // ---- backward of its activations ----
-    for (int o = 0; o < H; ++o) {
+      for (int c = 0; c < 3; ++c) dyr[c] = dy[c];
+    }
+    // ---- backward of the activations: dz2 and dz1 for this thread's units ----
+    for (int u1 = 0; u1 < HQ; ++u1) {
+      const int o = o0 + u1;
       const float dh = sW3[o * 3] * dy[0] + sW3[o * 3 + 1] * dy[1] + sW3[o * 3 + 2] * dy[2];
       z2[o] = dh * gelu32_grad(z2[o]);   // z2 -> dz2
     }
-    for (int i = 0; i < H; ++i) {
-      float dh = 0.0f;
-      for (int o = 0; o < H; ++o) dh = fmaf(sW2[i * H + o], z2[o], dh);
-      z1[i] = dh * gelu32_grad(z1[i]);   // z1 -> dz1
-    }
-    float gx[16];
+    __syncwarp();
+    {
+      float acc[HQ];   // dh1 for this thread's units i: sum over o of W2[i][o] dz2[o]
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      float g = 0.0f;
-      for (int o = 0; o < H; ++o) g = fmaf(sW1[k * H + o], z1[o], g);
-      gx[k] = g;
+      for (int u1 = 0; u1 < HQ; ++u1) acc[u1] = 0.0f;
+#pragma unroll 4
+      for (int o = 0; o < H; ++o) {
+        const float gz = z2[o];
+#pragma unroll
+        for (int u4 = 0; u4 < HQ / 4; ++u4) {
+          const float4 w = *reinterpret_cast<const float4*>(sW2t + o * HS + c0 + 4 * u4);
+          acc[4 * u4] = fmaf(gz, w.x, acc[4 * u4]);
+          acc[4 * u4 + 1] = fmaf(gz, w.y, acc[4 * u4 + 1]);
+          acc[4 * u4 + 2] = fmaf(gz, w.z, acc[4 * u4 + 2]);
+          acc[4 * u4 + 3] = fmaf(gz, w.w, acc[4 * u4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int u1 = 0; u1 < HQ; ++u1) z1[o0 + u1] = acc[u1] * gelu32_grad(z1[o0 + u1]);   // z1 -> dz1
     }
-    if (valid) hfit_scatter(a, u, v, t, gx);
+    __syncwarp();
+    {
+      float gx[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        float g = 0.0f;
+        if ((k & 3) == q && k < 12)
+          for (int o = 0; o < H; ++o) g = fmaf(sW1[k * HS + S::skew(o)], z1[o], g);
+        gx[k] = g;
+      }
+      if (valid) hfit_scatter(a, u, v, t, gx, q);
+    }
     __syncthreads();
     // ---- the tile's weight gradients: sums over its samples ----
+    if constexpr (kBlocked) {   // thread (ib, ob): dW2[2 ib .. 2 ib + 1][4 ob .. 4 ob + 3]
+      const int i0 = 2 * (tid >> 4), ob = 4 * (tid & 15);
+      float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+      for (int rr = 0; rr < kHfTile; ++rr) {
+        const float ha = sm[S::kH1 + rr * R + i0], hb = sm[S::kH1 + rr * R + i0 + 1];
+        const float4 z = *reinterpret_cast<const float4*>(sm + S::kZ2 + rr * R + ob);
+        acc[0] = fmaf(ha, z.x, acc[0]);
+        acc[1] = fmaf(ha, z.y, acc[1]);
+        acc[2] = fmaf(ha, z.z, acc[2]);
+        acc[3] = fmaf(ha, z.w, acc[3]);
+        acc[4] = fmaf(hb, z.x, acc[4]);
+        acc[5] = fmaf(hb, z.y, acc[5]);
+        acc[6] = fmaf(hb, z.z, acc[6]);
+        acc[7] = fmaf(hb, z.w, acc[7]);
+      }
 #pragma unroll
-    for (int j = 0; j < E2; ++j) {
-      const int e = tid + kHfTile * j;
-      if (e < H * H) {
-        const int i = e / H, o = e % H;
-        float acc = 0.0f;
-        for (int r = 0; r < kHfTile; ++r) acc = fmaf(sm[S::kH1 + r * R + i], sm[S::kZ2 + r * R + o], acc);
-        acc2[j] += acc;
+      for (int j = 0; j < 8; ++j) acc2[j] += acc[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < E2; ++j) {
+        const int e = tid + kHfThreads * j;
+        if (e < H * H) {
+          const int i = e / H, o = e % H;
+          float acc = 0.0f;
+          for (int rr = 0; rr < kHfTile; ++rr) acc = fmaf(sm[S::kH1 + rr * R + i], sm[S::kZ2 + rr * R + o], acc);
+          acc2[j] += acc;
+        }
       }
     }
 #pragma unroll
     for (int j = 0; j < E1; ++j) {
-      const int e = tid + kHfTile * j;
+      const int e = tid + kHfThreads * j;
       if (e < 16 * H) {
         const int k = e / H, o = e % H;
         float acc = 0.0f;
-        for (int r = 0; r < kHfTile; ++r) acc = fmaf(sm[S::kX + r * 17 + k], sm[S::kZ1 + r * R + o], acc);
+        for (int rr = 0; rr < kHfTile; ++rr) acc = fmaf(sm[S::kX + rr * 17 + k], sm[S::kZ1 + rr * R + o], acc);
         acc1[j] += acc;
       }
     }
     if (tid < H) {
       float b1 = 0.0f, b2 = 0.0f;
-      for (int r = 0; r < kHfTile; ++r) {
-        b1 += sm[S::kZ1 + r * R + tid];
-        b2 += sm[S::kZ2 + r * R + tid];
+      for (int rr = 0; rr < kHfTile; ++rr) {
+        b1 += sm[S::kZ1 + rr * R + tid];
+        b2 += sm[S::kZ2 + rr * R + tid];
       }
       accb1 += b1;
       accb2 += b2;
     }
 #pragma unroll
     for (int j = 0; j < E3; ++j) {
-      const int e = tid + kHfTile * j;
+      const int e = tid + kHfThreads * j;
       float g = 0.0f;
       if (e < 3 * H) {
         const int o = e / 3, c = e % 3;
-        for (int r = 0; r < kHfTile; ++r) g = fmaf(sm[S::kH2 + r * R + o], sm[S::kDY + r * 4 + c], g);
+        for (int rr = 0; rr < kHfTile; ++rr) g = fmaf(sm[S::kH2 + rr * R + o], sm[S::kDY + rr * 4 + c], g);
       } else if (e < 3 * H + 3) {
-        for (int r = 0; r < kHfTile; ++r) g += sm[S::kDY + r * 4 + (e - 3 * H)];
+        for (int rr = 0; rr < kHfTile; ++rr) g += sm[S::kDY + rr * 4 + (e - 3 * H)];
       }
       acc3[j] += g;
     }
     __syncthreads();   // the rows are rewritten by the next tile
   }
+  if constexpr (kBlocked) {
+    const int i0 = 2 * (tid >> 4), ob = 4 * (tid & 15);
 #pragma unroll
-  for (int j = 0; j < E2; ++j) {
-    const int e = tid + kHfTile * j;
-    if (e < H * H) atomicAdd(a.g[kW2] + e, acc2[j]);
+    for (int j = 0; j < 8; ++j) atomicAdd(a.g[kW2] + (i0 + j / 4) * H + ob + (j % 4), acc2[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < E2; ++j) {
+      const int e = tid + kHfThreads * j;
+      if (e < H * H) atomicAdd(a.g[kW2] + e, acc2[j]);
+    }
   }
 #pragma unroll
   for (int j = 0; j < E1; ++j) {
-    const int e = tid + kHfTile * j;
+    const int e = tid + kHfThreads * j;
     if (e < 16 * H) atomicAdd(a.g[kW1] + e, acc1[j]);
   }
   if (tid < H) {
@@ -446,7 +572,7 @@ __global__ void __launch_bounds__(kHfTile, 1) k_hfit_backward(HFitArgs a_in) {
   }
 #pragma unroll
   for (int j = 0; j < E3; ++j) {
-    const int e = tid + kHfTile * j;
+    const int e = tid + kHfThreads * j;
     if (e < 3 * H) atomicAdd(a.g[kW3] + e, acc3[j]);
     else if (e < 3 * H + 3) atomicAdd(a.g[kB3] + (e - 3 * H), acc3[j]);
   }
@@ -553,7 +679,7 @@ static cudaError_t launch_hfit_backward(const HFitArgs& a, int mode, cudaStream_
     auto kern = mode == 0 ? k_hfit_backward<H, 0> : k_hfit_backward<H, 1>;                             \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                   \
-    kern<<<grid, kHfTile, smem, s>>>(a);                                                              \
+    kern<<<grid, kHfThreads, smem, s>>>(a);                                                              \
     return cudaGetLastError();                                                                        \
   }
   NDGI_HFIT_HIDDEN(X)
