@@ -789,10 +789,11 @@ ndgi_status ndgi_hybrid_table_check(ndgi_hybrid_table *table, int32_t *device_er
 
 /*
  * Test hook: y[i] = GELU(x[i]) on the device (x, y: n FP32, device) as the
- * FP32 decodes evaluate it (fast = 0: CUDA's erff) or in the erfc form of
+ * FP32 decodes evaluate it (fast = 0: CUDA's erff), in the erfc form of
  * Abramowitz & Stegun 7.1.28 with one approximate reciprocal (|error| <=
- * 2e-6 (1 + |x|)): fast = 1 scalar, fast = 2 the packed FP32-pair form the
- * tensor-core epilogues use (the same roundings element for element).
+ * 2e-6 (1 + |x|)): fast = 1 scalar, fast = 2 packed FP32 pairs; or fast = 3:
+ * the polynomial form the FP16 / BF16 tensor-core epilogues use,
+ * x/2 (1 + t P(t^2)), t = clamp(x, -4.5, 4.5), |error| <= 4.5e-5 + 4e-6 |x|.
  */
 ndgi_status ndgi_debug_gelu(const float *x, int64_t n, float *y, int32_t fast, void *stream);
 

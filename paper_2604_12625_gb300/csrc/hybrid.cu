@@ -413,6 +413,34 @@ __device__ __forceinline__ float2 gelu_fast2(float a, float b) {
   return make_float2(ya, yb);
 }
 
+// GELU of two values for the FP16 / BF16 epilogues: x/2 (1 + t P(t^2)) with
+// t = clamp(x, -4.5, 4.5) and P of degree 8 in t^2 approximating
+// erf(t / sqrt 2) / t (weighted least squares towards minimax; the
+// coefficients and their check come from csrc/gelu_poly_fit.py), in the
+// packed FP32-pair instructions.  |error| <= 4.5e-5 + 4e-6 |x| (the clamp
+// leaves |x| erfc(4.5 / sqrt 2) / 2 beyond 4.5), far below the FP16 rounding
+// of the result (|x| 2^-12).
+__device__ __forceinline__ float2 gelu_poly2(float a, float b) {
+  constexpr float c0 = 0.7974528670310974f, c1 = -0.13199074566364288f, c2 = 0.019172420725226402f;
+  constexpr float c3 = -0.002073553390800953f, c4 = 0.00016233573842328042f, c5 = -8.838639587338548e-06f;
+  constexpr float c6 = 3.1406239031639416e-07f, c7 = -6.496896798324769e-09f, c8 = 5.903861427514201e-11f;
+  const uint64_t t = f2_pack(fminf(fmaxf(a, -4.5f), 4.5f), fminf(fmaxf(b, -4.5f), 4.5f));
+  const uint64_t s = f2_mul(t, t);
+  uint64_t p = f2_fma(f2_pack(c8, c8), s, f2_pack(c7, c7));
+  p = f2_fma(p, s, f2_pack(c6, c6));
+  p = f2_fma(p, s, f2_pack(c5, c5));
+  p = f2_fma(p, s, f2_pack(c4, c4));
+  p = f2_fma(p, s, f2_pack(c3, c3));
+  p = f2_fma(p, s, f2_pack(c2, c2));
+  p = f2_fma(p, s, f2_pack(c1, c1));
+  p = f2_fma(p, s, f2_pack(c0, c0));
+  const uint64_t e = f2_mul(t, p);                               // erf(x / sqrt 2)
+  const uint64_t h = f2_mul(f2_pack(a, b), f2_pack(0.5f, 0.5f));   // x / 2
+  float ya, yb;
+  f2_unpack(f2_fma(h, e, h), ya, yb);
+  return make_float2(ya, yb);
+}
+
 // Slot s of a lane's engine: this thread's layer-1/2 accumulator row -> GELU ->
 // FP16/BF16 -> the hidden A tile, 16 columns at a time; with ONES also the
 // ones column that carries the next layer's bias (the engine's ReLU epilogue
@@ -429,7 +457,7 @@ __device__ __forceinline__ void epilogue_gelu(E& e, int s) {
     tmem_ld_wait();
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const float2 g = gelu_fast2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+      const float2 g = gelu_poly2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
       w[j] = pack2<E::BF16>(g.x, g.y);
     }
     tmem_st8(a + c / 2, w);
@@ -766,7 +794,8 @@ __global__ void __launch_bounds__(kLaneThreads* kHybLanes, 1)
 
 __global__ void k_debug_gelu(const float* __restrict__ x, int64_t n, float* __restrict__ y, int fast) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = fast == 2 ? gelu_fast2(x[i], 0.0f).x : (fast ? gelu_fast(x[i]) : gelu(x[i]));
+    y[i] = fast == 3 ? gelu_poly2(x[i], 0.0f).x
+                     : fast == 2 ? gelu_fast2(x[i], 0.0f).x : (fast ? gelu_fast(x[i]) : gelu(x[i]));
 }
 
 // ---------------------------------------------------------------------------

@@ -221,14 +221,17 @@ def test_full_frame_sampled(ndgi):
     table.close()
 
 
-@pytest.mark.parametrize("fast", [0, 1, 2])
+@pytest.mark.parametrize("fast", [0, 1, 2, 3])
 def test_gelu_on_device_against_oracle(ndgi, fast):
-    # exact form (erff) within a few FP32 ulps; the epilogue's A&S 7.1.28 form within 2e-6 (1 + |x|)
+    # exact form (erff) within a few FP32 ulps; the A&S 7.1.28 forms within 2e-6 (1 + |x|); the epilogues'
+    # polynomial form within 4.5e-5 + 4e-6 |x| (beyond the clamp at 4.5 the error grows as
+    # |x| erfc(4.5 / sqrt 2) / 2 = 3.4e-6 |x|): far below FP16's rounding of the result, |x| 2^-12
     x = np.concatenate([np.linspace(-12, 12, 200_001), [0.0, -0.0, 1e-30, -1e-30, 30.0, -30.0, 1e4, -1e4]])
     x = x.astype(np.float32)
     y = ndgi.ndgi_debug_gelu(torch.from_numpy(x).cuda(), fast=fast).cpu().numpy().astype(np.float64)
     ref = oracle.gelu(x.astype(np.float64))
-    bound = 2e-6 * (1 + np.abs(x)) if fast else 4e-7 * (1 + np.abs(x))
+    bound = {0: 4e-7 * (1 + np.abs(x)), 1: 2e-6 * (1 + np.abs(x)), 2: 2e-6 * (1 + np.abs(x)),
+             3: 4.5e-5 + 4e-6 * np.abs(x)}[fast]
     err = np.abs(y - ref)
     print(f"gelu fast={fast}: max |err| / (1 + |x|) = {np.max(err / (1 + np.abs(x))):.3e}")
     assert np.all(err <= bound)
