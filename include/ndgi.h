@@ -322,7 +322,10 @@ typedef struct {
 
 typedef enum {
   NDGI_RGBA32F = 0,           /* 16 bytes per texel, A = 1                 */
-  NDGI_RGBA16F = 1            /* 8 bytes per texel, A = 1                  */
+  NDGI_RGBA16F = 1,           /* 8 bytes per texel, A = 1                  */
+  NDGI_RGBA8 = 2              /* 4 bytes per texel, UNORM: round(255 clamp(y, 0, 1)), A = 255; hybrid
+                                 tables only (the paper's 8-bit, 4-channel physical texture, which holds
+                                 the model's normalised output) */
 } ndgi_out_format;
 
 typedef struct ndgi_pages_plan ndgi_pages_plan;
@@ -754,7 +757,8 @@ ndgi_status ndgi_hybrid_table_destroy(ndgi_hybrid_table *table);
  * Page decode with hybrid models: texel (x0+i, y0+j) of each request is
  * decoded at ((x0+i+0.5)/lm_w, (y0+j+0.5)/lm_h, t) with the request's model
  * and t, and written as RGBA (A = 1) to phys (device, [phys_h][phys_w][4] of
- * RGBA32F or RGBA16F) at (dst_x+i, dst_y+j).  reqs: n requests (device).
+ * RGBA32F, RGBA16F or RGBA8 UNORM) at (dst_x+i, dst_y+j).  reqs: n requests
+ * (device).
  * The host checks n, phys and format; the device checks each request
  * (model index, rectangle inside the lightmap and the physical texture)
  * and skips a bad one, latching bit 0 of the table's error word.

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libndgi.so")
 NDGI_OK, NDGI_ERR_INVALID_ARG, NDGI_ERR_UNSUPPORTED, NDGI_ERR_CUDA, NDGI_ERR_OOM, NDGI_ERR_TIMEOUT, \
     NDGI_ERR_DEVICE_CHECK = range(7)
 NDGI_FP32, NDGI_FP16, NDGI_BF16, NDGI_FP8_E4M3 = range(4)
-NDGI_RGBA32F, NDGI_RGBA16F = 0, 1
+NDGI_RGBA32F, NDGI_RGBA16F, NDGI_RGBA8 = 0, 1, 2
 PRECISIONS = {"fp32": NDGI_FP32, "fp16": NDGI_FP16, "bf16": NDGI_BF16, "fp8": NDGI_FP8_E4M3}
 STATUS_NAMES = {0: "NDGI_OK", 1: "NDGI_ERR_INVALID_ARG", 2: "NDGI_ERR_UNSUPPORTED", 3: "NDGI_ERR_CUDA",
                 4: "NDGI_ERR_OOM", 5: "NDGI_ERR_TIMEOUT", 6: "NDGI_ERR_DEVICE_CHECK"}

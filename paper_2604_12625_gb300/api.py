@@ -287,7 +287,7 @@ class PagesPlan:
         elif phys.dtype == torch.float16:
             fmt = A.NDGI_RGBA16F
         else:
-            raise ValueError("phys must be float32 or float16 RGBA")
+            raise ValueError("phys must be float32, float16 or uint8 RGBA")
         assert phys.is_cuda and phys.is_contiguous() and phys.shape[-1] == 4
         descs = (A.ModelDesc * len(self.models))(*[m.desc for m in self.models])
         ws = [m.workspace(self.precision) for m in self.models]
@@ -612,11 +612,13 @@ class HybridTable:
         self.handle = h
 
     def decode(self, reqs, n, phys, stream=None):
-        """Decodes n requests (int32 [n][8] CUDA tensor) into phys ([h][w][4] float32 or float16)."""
+        """Decodes n requests (int32 [n][8] CUDA tensor) into phys ([h][w][4] float32, float16 or uint8 UNORM)."""
         if phys.dtype == torch.float32:
             fmt = A.NDGI_RGBA32F
         elif phys.dtype == torch.float16:
             fmt = A.NDGI_RGBA16F
+        elif phys.dtype == torch.uint8:
+            fmt = A.NDGI_RGBA8
         else:
             raise ValueError("phys must be float32 or float16 RGBA")
         assert phys.is_cuda and phys.is_contiguous() and phys.shape[-1] == 4

@@ -249,9 +249,15 @@ __device__ __forceinline__ int border_mirror(int i, int n, int b) {
   return k < 0 ? -1 - k : (k >= n ? 2 * n - 1 - k : k);
 }
 
+__device__ __forceinline__ uint32_t unorm8(float y) {
+  return (uint32_t)__float2int_rn(__saturatef(y) * 255.0f);
+}
+
 __device__ __forceinline__ void put_texel(void* phys, int fmt, int64_t o, float y0, float y1, float y2) {
   if (fmt == NDGI_RGBA32F) {
     __stcs(reinterpret_cast<float4*>(phys) + o, make_float4(y0, y1, y2, 1.0f));
+  } else if (fmt == NDGI_RGBA8) {
+    __stcs(reinterpret_cast<unsigned int*>(phys) + o, unorm8(y0) | (unorm8(y1) << 8) | (unorm8(y2) << 16) | 0xFF000000u);
   } else {
     __stcs(reinterpret_cast<uint2*>(phys) + o, make_uint2(pack2<false>(y0, y1), pack2<false>(y2, 1.0f)));
   }
@@ -1110,9 +1116,9 @@ ndgi_status ndgi_hybrid_decode_pages(ndgi_hybrid_table* table, const ndgi_page_r
   if (n == 0) return NDGI_OK;
   if (!reqs || !phys) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: reqs or phys is NULL");
   if (phys_w <= 0 || phys_h <= 0) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: empty phys");
-  if (format != NDGI_RGBA32F && format != NDGI_RGBA16F)
+  if (format != NDGI_RGBA32F && format != NDGI_RGBA16F && format != NDGI_RGBA8)
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: unknown output format");
-  if (!is_aligned(phys, format == NDGI_RGBA32F ? 16 : 8) || !is_aligned(reqs, 4))
+  if (!is_aligned(phys, format == NDGI_RGBA32F ? 16 : format == NDGI_RGBA16F ? 8 : 4) || !is_aligned(reqs, 4))
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_hybrid_decode_pages: phys or reqs misaligned");
   HybridPagesCtx c;
   c.models = table->d_models;

@@ -250,3 +250,37 @@ def test_hybrid_bc7_full_frame_sampled(ndgi):
     table.close()
     del phys
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("fmt_bc7", [False, True])
+def test_hybrid_pages_rgba8_output(ndgi, fmt_bc7):
+    """RGBA8 UNORM output (the paper's 8-bit, 4-channel physical texture): each byte is the FP16 decode's value
+    clamped to [0, 1] and rounded to 8 bits, so it lies within the FP16 gate plus half a level of the oracle's
+    value; A = 255; texels outside the requests stay untouched."""
+    from test_gpu_hybrid import GATE, ragged_requests
+    maps = [synth.hybrid_model(170 + i, 128, 128, 128, 128, 32, 32, 12, 64, 24, 64, 24, 64,
+                               feat_format=1 if fmt_bc7 else 0) for i in range(2)]
+    for m in maps:   # outputs mostly inside [0, 1]: scale the last layer down and centre it
+        m["w3"] = (m["w3"] * 0.1).astype(np.float32)
+        m["b3"] = np.full(3, 0.5, np.float32)
+    models = [ndgi.HybridModel.from_arrays(m) for m in maps]
+    table = ndgi.HybridTable(models, "fp16")
+    reqs = ragged_requests(171, 2, 6, 3)
+    r, _ = ndgi.page_requests_to_device(reqs)
+    phys = torch.full((2 * 128, 3 * 128, 4), 7, dtype=torch.uint8, device="cuda")
+    table.decode(r, len(reqs), phys)
+    assert table.check() == (0, 0)
+    got = phys.cpu().numpy()
+    ref = oracle.hybrid_decode_pages(maps, reqs, 3 * 128, 2 * 128, precision="fp16", fill=np.nan)
+    inside = ~np.isnan(ref[..., 0])
+    assert np.all(got[~inside] == 7)
+    assert np.all(got[inside][:, 3] == 255)
+    for q in reqs:
+        sl = (slice(q["dst_y"], q["dst_y"] + q["h"]), slice(q["dst_x"], q["dst_x"] + q["w"]))
+        b = ref[sl][..., :3]
+        rng = max(float(b.max() - b.min()), 1e-3)
+        a = got[sl][..., :3].astype(np.float64) / 255.0
+        assert np.all(np.abs(a - np.clip(b, 0, 1)) <= GATE["fp16"] * rng + 0.5 / 255 + 1e-6)
+    inside_vals = ref[inside][:, :3]
+    assert 0.2 < np.mean((inside_vals > 0) & (inside_vals < 1))   # the test exercises the unclamped range
+    table.close()
