@@ -56,9 +56,9 @@ NCU_TRAFFIC = {
                    "profile": "profiles/k_pages_tc_pages_8_lightmaps.md"},
     "k_pages_ws": {"src": "f7fc86e019b63f3e", "read": 19192576, "write": 76340736, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_ws_pages_8_lightmaps.md"},
-    "k_hybrid_pages_tc": {"src": "d6bb648b2c022d7a", "read": 187439360, "write": 476844032, "units": 4096 * 128 * 128,
+    "k_hybrid_pages_tc": {"src": "5166b039c9dbcda4", "read": 188844544, "write": 476816640, "units": 4096 * 128 * 128,
                           "profile": "profiles/k_hybrid_pages_tc_m64_4096_tiles.md"},
-    "k_hybrid_pages_tc_bc7": {"src": "d6bb648b2c022d7a", "read": 115736320, "write": 476533504, "units": 4096 * 128 * 128,
+    "k_hybrid_pages_tc_bc7": {"src": "5166b039c9dbcda4", "read": 115540224, "write": 475685888, "units": 4096 * 128 * 128,
                               "profile": "profiles/k_hybrid_pages_tc_bc7_m64_4096_tiles.md"},
 }
 
