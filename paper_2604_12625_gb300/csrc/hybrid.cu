@@ -419,7 +419,7 @@ __device__ __forceinline__ float2 gelu_fast2(float a, float b) {
   return make_float2(ya, yb);
 }
 
-// GELU of two values for the FP16 / BF16 epilogues: x/2 (1 + t P(t^2)) with
+// GELU of two values for the FP16 / BF16 epilogues: x (1 + t P(t^2)) / 2 with
 // t = clamp(x, -4.5, 4.5) and P of degree 8 in t^2 approximating
 // erf(t / sqrt 2) / t (weighted least squares towards minimax; the
 // coefficients and their check come from csrc/gelu_poly_fit.py), in the
@@ -431,19 +431,20 @@ __device__ __forceinline__ float2 gelu_poly2(float a, float b) {
   constexpr float c3 = -0.002073553390800953f, c4 = 0.00016233573842328042f, c5 = -8.838639587338548e-06f;
   constexpr float c6 = 3.1406239031639416e-07f, c7 = -6.496896798324769e-09f, c8 = 5.903861427514201e-11f;
   const uint64_t t = f2_pack(fminf(fmaxf(a, -4.5f), 4.5f), fminf(fmaxf(b, -4.5f), 4.5f));
+  // Horner on the halved coefficients (exact: powers of two), so that
+  // 1/2 + t P(t^2) / 2 = Phi(x) takes one FMA and x Phi(x) one multiply.
   const uint64_t s = f2_mul(t, t);
-  uint64_t p = f2_fma(f2_pack(c8, c8), s, f2_pack(c7, c7));
-  p = f2_fma(p, s, f2_pack(c6, c6));
-  p = f2_fma(p, s, f2_pack(c5, c5));
-  p = f2_fma(p, s, f2_pack(c4, c4));
-  p = f2_fma(p, s, f2_pack(c3, c3));
-  p = f2_fma(p, s, f2_pack(c2, c2));
-  p = f2_fma(p, s, f2_pack(c1, c1));
-  p = f2_fma(p, s, f2_pack(c0, c0));
-  const uint64_t e = f2_mul(t, p);                               // erf(x / sqrt 2)
-  const uint64_t h = f2_mul(f2_pack(a, b), f2_pack(0.5f, 0.5f));   // x / 2
+  uint64_t p = f2_fma(f2_pack(0.5f * c8, 0.5f * c8), s, f2_pack(0.5f * c7, 0.5f * c7));
+  p = f2_fma(p, s, f2_pack(0.5f * c6, 0.5f * c6));
+  p = f2_fma(p, s, f2_pack(0.5f * c5, 0.5f * c5));
+  p = f2_fma(p, s, f2_pack(0.5f * c4, 0.5f * c4));
+  p = f2_fma(p, s, f2_pack(0.5f * c3, 0.5f * c3));
+  p = f2_fma(p, s, f2_pack(0.5f * c2, 0.5f * c2));
+  p = f2_fma(p, s, f2_pack(0.5f * c1, 0.5f * c1));
+  p = f2_fma(p, s, f2_pack(0.5f * c0, 0.5f * c0));
+  const uint64_t phi = f2_fma(t, p, f2_pack(0.5f, 0.5f));   // Phi(x)
   float ya, yb;
-  f2_unpack(f2_fma(h, e, h), ya, yb);
+  f2_unpack(f2_mul(f2_pack(a, b), phi), ya, yb);
   return make_float2(ya, yb);
 }
 
