@@ -56,9 +56,9 @@ NCU_TRAFFIC = {
                    "profile": "profiles/k_pages_tc_pages_8_lightmaps.md"},
     "k_pages_ws": {"src": "f7fc86e019b63f3e", "read": 19192576, "write": 76340736, "units": 1024 * 128 * 128,
                    "profile": "profiles/k_pages_ws_pages_8_lightmaps.md"},
-    "k_hybrid_pages_tc": {"src": "5166b039c9dbcda4", "read": 188844544, "write": 476816640, "units": 4096 * 128 * 128,
+    "k_hybrid_pages_tc": {"src": "fef791fc427035db", "read": 187109120, "write": 475889664, "units": 4096 * 128 * 128,
                           "profile": "profiles/k_hybrid_pages_tc_m64_4096_tiles.md"},
-    "k_hybrid_pages_tc_bc7": {"src": "5166b039c9dbcda4", "read": 115540224, "write": 475685888, "units": 4096 * 128 * 128,
+    "k_hybrid_pages_tc_bc7": {"src": "fef791fc427035db", "read": 116471296, "write": 475803392, "units": 4096 * 128 * 128,
                               "profile": "profiles/k_hybrid_pages_tc_bc7_m64_4096_tiles.md"},
 }
 
