@@ -477,7 +477,7 @@ ndgi_status ndgi_bc_pack(const float *ea, const float *eb, const float *w, int32
                          int32_t feat_h, uint8_t *bc4_out, void *stream);
 
 /* ---------------------------------------------------------------------- */
-/* BC7 (Sec. 3.2: F_uv and F3D quantised to 8 bits and BC7-compressed)     */
+/* BC7 (Sec. 3.4: F_uv and F3D quantised to 8 bits and BC7-compressed)     */
 /* ---------------------------------------------------------------------- */
 
 /*

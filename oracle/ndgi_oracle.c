@@ -770,7 +770,7 @@ void om_fit_draw(uint64_t seed, int64_t step, int64_t first, int64_t n, int32_t 
 }
 
 /* ---------------------------------------------------------------------- */
-/* BC7 blocks (the paper's storage for F_uv and the F3D slices, Sec. 3.2)  */
+/* BC7 blocks (the paper's storage for F_uv and the F3D slices, Sec. 3.4)  */
 /* ---------------------------------------------------------------------- */
 /*
  * Plain statement of the BC7 (BPTC, UNORM) block format as published for
@@ -1628,7 +1628,7 @@ typedef struct {
 } om_hfit_grads;
 
 /*
- * Training-time quantisation noise (Sec. 3.2: V' = V + U(-0.5, 0.5) alpha on
+ * Training-time quantisation noise (Sec. 3.4: V' = V + U(-0.5, 0.5) alpha on
  * the sampled vectors; alpha = 1/256 for the 8-bit maps).  Counter-based, so
  * that any implementation draws the same numbers: for sample i of global step
  * s and input k < 12, z = splitmix64(b + k g) with g = 0x9E3779B97F4A7C15 and

@@ -1,4 +1,4 @@
-// BC7 compression of the 8-bit quantised feature maps (Sec. 3.2: after
+// BC7 compression of the 8-bit quantised feature maps (Sec. 3.4: after
 // training, F_uv and every F3D slice are quantised to 8 bits and compressed
 // with BC7 using several modes) and BC7 decode.
 //

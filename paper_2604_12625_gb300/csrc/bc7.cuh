@@ -1,5 +1,5 @@
 // BC7 (BPTC, UNORM) block decode on the CUDA cores: the paper's storage
-// format for F_uv and the F3D slices (Sec. 3.2; supplement S2).
+// format for F_uv and the F3D slices (Sec. 3.4; supplement S2).
 //
 // A 16-byte block is a 128-bit little-endian bit string, fields LSB first:
 // mode (m zeros then a one), partition, rotation, index selector, endpoint

@@ -1,5 +1,5 @@
 """GPU parity of BC7 (the paper's block format for F_uv and the F3D slices,
-Sec. 3.2) against the oracle, and of the oracle against the GPU's own
+Sec. 3.4) against the oracle, and of the oracle against the GPU's own
 fixed-function BC7 decoder (the texture unit), an implementation of the
 format independent of both:
 

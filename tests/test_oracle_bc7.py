@@ -1,5 +1,5 @@
 """Pins of the oracle's BC7 block format and encoder (the paper's storage for
-F_uv and the F3D slices, Sec. 3.2 and supplement S2).
+F_uv and the F3D slices, Sec. 3.4 and supplement S2).
 
 What the format fixes and these tests check without the oracle's own code:
 - field widths: every mode's fields fill exactly 128 bits (every encoder

@@ -146,7 +146,7 @@ def test_shared_weight_backward_matches_finite_differences():
 
 
 # --------------------------------------------------------------------------
-# Training-time quantisation noise on the sampled vectors (Sec. 3.2)
+# Training-time quantisation noise on the sampled vectors (Sec. 3.4)
 # --------------------------------------------------------------------------
 
 def test_noise_draws_are_uniform_and_deterministic():
