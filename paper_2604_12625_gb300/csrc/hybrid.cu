@@ -423,9 +423,10 @@ __device__ __forceinline__ float2 gelu_fast2(float a, float b) {
 // t = clamp(x, -4.5, 4.5) and P of degree 8 in t^2 approximating
 // erf(t / sqrt 2) / t (weighted least squares towards minimax; the
 // coefficients and their check come from csrc/gelu_poly_fit.py), in the
-// packed FP32-pair instructions.  |error| <= 4.5e-5 + 4e-6 |x| (the clamp
-// leaves |x| erfc(4.5 / sqrt 2) / 2 beyond 4.5), far below the FP16 rounding
-// of the result (|x| 2^-12).
+// packed FP32-pair instructions.  |error| <= 4.5e-5 + 4e-6 |x| (beyond the
+// clamp Phi is held at its polynomial value at +-4.5, 1.4e-6 past 1 or 0,
+// i.e. within 4.9e-6 of Phi(x)), far below the FP16 rounding of the result
+// (|x| 2^-12).
 __device__ __forceinline__ float2 gelu_poly2(float a, float b) {
   constexpr float c0 = 0.7974528670310974f, c1 = -0.13199074566364288f, c2 = 0.019172420725226402f;
   constexpr float c3 = -0.002073553390800953f, c4 = 0.00016233573842328042f, c5 = -8.838639587338548e-06f;
