@@ -1076,7 +1076,10 @@ def main():
                 "pipeline": f"chunks of {args.e2e_chunk} queries; copy-in, decode and copy-out overlapped on three "
                             "streams", "matches_device_decode": e2e_ok},
         "ms_per_step_median_of_20": ms_median,
-        "gpu_launches": args.steps, "clocks": clocks,
+        "gpu_launches": args.steps * (2 if path in ("cache", "cache_ws") else 1),
+        "gpu_launches_per_step": ("k_feature_cache + " + roof["kernel"]) if path in ("cache", "cache_ws")
+                                 else roof["kernel"],
+        "clocks": clocks,
         "fit": fit, "fit_batch": fit_batch, "hybrid_fit": hybrid_fit, "hybrid_fit_batch": hybrid_fit_batch, "scale": scale, "hybrid": hybrid, "quality": quality, "pages": pages,
     }
     if hybrid is not None:
