@@ -495,8 +495,9 @@ ndgi_status ndgi_bc_pack(const float *ea, const float *eb, const float *w, int32
  * minimises the summed squared error, 0 on ties), and gives every texel its
  * nearest palette entry (lowest index on ties).  If sq_err is not NULL the
  * total squared error (over all texels and channels, in 8-bit units) is
- * added to the device uint64 it points to.  Buffers are device memory,
- * 16-byte aligned.  Errors: NDGI_ERR_INVALID_ARG (sizes, NULL, alignment).
+ * added to the device uint64 it points to (8-byte aligned).  The other
+ * buffers are device memory, 16-byte aligned.  Errors: NDGI_ERR_INVALID_ARG
+ * (sizes, NULL, alignment).
  */
 ndgi_status ndgi_bc7_encode(const uint8_t *rgba, int32_t w, int32_t h, uint8_t *blocks, uint64_t *sq_err,
                             void *stream);
@@ -632,7 +633,8 @@ size_t ndgi_encode_fit_workspace_size(const ndgi_fit_params *params, const ndgi_
  * and weights projected onto [0,1]).  step_offset continues a previous run
  * (Adam step numbering and sample stream).  Every loss_every steps the FP64
  * batch loss is written to loss_log[k] (device, double,
- * ceil(steps/loss_every) entries).  ws: device workspace of
+ * ceil(steps/loss_every) entries, 8-byte aligned; targets 2-byte aligned;
+ * NDGI_ERR_INVALID_ARG otherwise).  ws: device workspace of
  * ndgi_encode_fit_workspace_size bytes, holding the Adam moments (keep it
  * between calls to resume).  Pack the result with ndgi_bc_pack.
  */
@@ -878,7 +880,8 @@ ndgi_status ndgi_hybrid_fit_backward(const ndgi_hybrid_fit_params *params, const
  * t_count) interpolated linearly at t, the feature maps projected onto
  * [0, 1] and frozen for the last cfg->freeze_steps steps (the final stage
  * fine-tunes the MLP alone, Sec. 4).  ws: ndgi_hybrid_encode_fit_workspace_size
- * bytes (Adam moments; keep it to resume with step_offset).
+ * bytes (Adam moments; keep it to resume with step_offset).  targets must be
+ * 2-byte and loss_log 8-byte aligned (NDGI_ERR_INVALID_ARG otherwise).
  */
 size_t ndgi_hybrid_encode_fit_workspace_size(const ndgi_hybrid_fit_params *params, const ndgi_fit_config *cfg);
 ndgi_status ndgi_hybrid_encode_fit(const ndgi_hybrid_fit_params *params, const uint16_t *targets, int32_t t_count,
@@ -920,7 +923,8 @@ ndgi_status ndgi_hybrid_encode_fit_batch(const ndgi_hybrid_fit_params *params, i
  * valid texel whose window lies inside the tile, averaged over those texels
  * and the channels.  psnr, ssim: [n_maps][ceil(h/tile)][ceil(w/tile)] FP64
  * (device); a tile with no valid texel (for SSIM: no valid centre) gets NaN,
- * a tile with zero error PSNR = +inf.  channels 1..4.
+ * a tile with zero error PSNR = +inf.  channels 1..4.  pred and ref must be
+ * 4-byte and psnr, ssim 8-byte aligned (NDGI_ERR_INVALID_ARG otherwise).
  */
 ndgi_status ndgi_tile_metrics(const float *pred, const float *ref, const uint8_t *mask, int32_t n_maps, int32_t h,
                               int32_t w, int32_t channels, int32_t tile, double *psnr, double *ssim, void *stream);

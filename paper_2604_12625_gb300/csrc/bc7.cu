@@ -453,6 +453,8 @@ ndgi_status ndgi_bc7_encode(const uint8_t* rgba, int32_t w, int32_t h, uint8_t* 
                             void* stream) {
   ndgi_status st = check_image(rgba, blocks, w, h, "ndgi_bc7_encode");
   if (st != NDGI_OK) return st;
+  if ((uintptr_t)sq_err % 8)   // the 64-bit atomic accumulation needs an 8-byte aligned word
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_bc7_encode: sq_err must be 8-byte aligned");
   const int bw = w / 4;
   const int64_t n = (int64_t)bw * (h / 4);
   k_bc7_encode<<<grid_for(n, 128, 8), 128, 0, (cudaStream_t)stream>>>(

@@ -927,6 +927,8 @@ static ndgi_status encode_fit(const ndgi_fit_params* params, int32_t n_models, c
   if (st != NDGI_OK) return st;
   if (n_models < 1) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit_batch: n_models < 1");
   if (!cfg || !targets || !ws) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit: NULL argument");
+  if ((uintptr_t)targets % 2 || (uintptr_t)loss_log % 8)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit: targets must be 2-byte and loss_log 8-byte aligned");
   if (cfg->steps < 0 || cfg->batch <= 0 || cfg->freeze_steps < 0 || cfg->loss_every < 0 || step_offset < 0)
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit: bad config");
   if (!(cfg->lr > 0.0f) || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f))

@@ -746,6 +746,8 @@ static ndgi_status hybrid_encode_fit(const ndgi_hybrid_fit_params* params, int32
   if (st != NDGI_OK) return st;
   if (n_models < 1) return set_error(NDGI_ERR_INVALID_ARG, "%s: n_models < 1", who);
   if (!cfg || !targets || !ws || t_count <= 0) return set_error(NDGI_ERR_INVALID_ARG, "%s: bad argument", who);
+  if ((uintptr_t)targets % 2 || (uintptr_t)loss_log % 8)
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: targets must be 2-byte and loss_log 8-byte aligned", who);
   if (cfg->steps < 0 || cfg->batch <= 0 || cfg->freeze_steps < 0 || cfg->loss_every < 0 || step_offset < 0)
     return set_error(NDGI_ERR_INVALID_ARG, "%s: bad config", who);
   if (!(cfg->lr > 0.0f) || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f))

@@ -139,6 +139,8 @@ extern "C" ndgi_status ndgi_tile_metrics(const float* pred, const float* ref, co
   using ndgi::set_error;
   if (!pred || !ref || !psnr || !ssim)
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_tile_metrics: NULL argument");
+  if ((uintptr_t)pred % 4 || (uintptr_t)ref % 4 || (uintptr_t)psnr % 8 || (uintptr_t)ssim % 8)
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_tile_metrics: pred/ref must be 4-byte and psnr/ssim 8-byte aligned");
   if (n_maps <= 0 || h <= 0 || w <= 0 || channels < 1 || channels > 4 || tile < 1)
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_tile_metrics: bad sizes");
   const int64_t ty_n = (h + tile - 1) / tile, tx_n = (w + tile - 1) / tile;
