@@ -9,7 +9,6 @@
 
 #include "ndgi_internal.h"
 #include "tc_decode.h"
-#include "fit.h"
 
 namespace ndgi {
 

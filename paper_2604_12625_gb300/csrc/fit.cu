@@ -21,7 +21,6 @@
 #include "ndgi_internal.h"
 #include "sampler.cuh"
 #include "bc4.cuh"
-#include "fit.h"
 
 namespace ndgi {
 
