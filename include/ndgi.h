@@ -651,6 +651,8 @@ ndgi_status ndgi_encode_fit(const ndgi_fit_params *params, const uint16_t *targe
  * key_t.  Model m draws its samples as ndgi_encode_fit does with seed + m.
  * cfg->batch samples per model and step; loss_log holds the mean over all
  * models' samples.  ws: ndgi_encode_fit_batch_workspace_size bytes.
+ * 1 <= n_models <= 65535 (one row of CTAs per model); NDGI_ERR_INVALID_ARG
+ * otherwise.
  */
 size_t ndgi_encode_fit_batch_workspace_size(const ndgi_fit_params *params, int32_t n_models,
                                             const ndgi_fit_config *cfg);
@@ -898,7 +900,8 @@ ndgi_status ndgi_hybrid_encode_fit(const ndgi_hybrid_fit_params *params, const u
  * its samples (and training noise) as ndgi_hybrid_encode_fit does with
  * seed + m.  cfg->batch samples per model and step; loss_log holds the mean
  * over all models' samples.  ws: ndgi_hybrid_encode_fit_batch_workspace_size
- * bytes (the Adam moments of all models).
+ * bytes (the Adam moments of all models).  1 <= n_models <= 65535 (one row
+ * of CTAs per model); NDGI_ERR_INVALID_ARG otherwise.
  */
 size_t ndgi_hybrid_encode_fit_batch_workspace_size(const ndgi_hybrid_fit_params *params, int32_t n_models,
                                                    const ndgi_fit_config *cfg);

@@ -924,7 +924,8 @@ static ndgi_status encode_fit(const ndgi_fit_params* params, int32_t n_models, c
                               double* loss_log, void* stream) {
   ndgi_status st = check_fit(params, "ndgi_encode_fit");
   if (st != NDGI_OK) return st;
-  if (n_models < 1) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit_batch: n_models < 1");
+  if (n_models < 1 || n_models > 65535)   // one CTA row (grid y) per model
+    return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit_batch: n_models must be in 1..65535");
   if (!cfg || !targets || !ws) return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit: NULL argument");
   if ((uintptr_t)targets % 2 || (uintptr_t)loss_log % 8)
     return set_error(NDGI_ERR_INVALID_ARG, "ndgi_encode_fit: targets must be 2-byte and loss_log 8-byte aligned");

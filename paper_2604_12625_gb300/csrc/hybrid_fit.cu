@@ -744,7 +744,8 @@ static ndgi_status hybrid_encode_fit(const ndgi_hybrid_fit_params* params, int32
                                      const char* who) {
   ndgi_status st = check_hfit(params, who);
   if (st != NDGI_OK) return st;
-  if (n_models < 1) return set_error(NDGI_ERR_INVALID_ARG, "%s: n_models < 1", who);
+  if (n_models < 1 || n_models > 65535)   // one CTA row (grid y) per model
+    return set_error(NDGI_ERR_INVALID_ARG, "%s: n_models must be in 1..65535", who);
   if (!cfg || !targets || !ws || t_count <= 0) return set_error(NDGI_ERR_INVALID_ARG, "%s: bad argument", who);
   if ((uintptr_t)targets % 2 || (uintptr_t)loss_log % 8)
     return set_error(NDGI_ERR_INVALID_ARG, "%s: targets must be 2-byte and loss_log 8-byte aligned", who);

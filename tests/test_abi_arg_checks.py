@@ -62,3 +62,18 @@ def test_hybrid_encode_fit_targets_and_loss_log_alignment():
     rejected(L.ndgi_hybrid_encode_fit(C.byref(p), P, 24, None, C.byref(c), 0, P, 1 << 30, P + 4, None), FIT_MSG)
     rejected(L.ndgi_hybrid_encode_fit_batch(C.byref(p), 2, P, 24, None, C.byref(c), 0, P, 1 << 30, P + 4, None),
              FIT_MSG)
+
+
+def test_batched_fits_reject_more_models_than_grid_rows():
+    L = _abi.lib()
+    p = _abi.FitParams(lm_w=64, lm_h=64, feat_w=32, feat_h=32, cs=16, t_count=24, ct=8, hidden=64,
+                       **{k: P for k in _abi.FIT_TENSORS}, address_mode=0, key_t=None)
+    c = cfg()
+    for n in (0, 65536):
+        rejected(L.ndgi_encode_fit_batch(C.byref(p), n, P, C.byref(c), 0, P, 1 << 30, P, None), "1..65535")
+    h = _abi.HybridFitParams(lm_w=128, lm_h=128, uv_w=128, uv_h=128, vol_w=32, vol_h=32, vol_t=12, ut_w=64,
+                             ut_t=24, vt_h=64, vt_t=24, hidden=64, address_mode=0,
+                             **{k: P for k in _abi.HFIT_TENSORS}, shared_w=0)
+    for n in (0, 65536):
+        rejected(L.ndgi_hybrid_encode_fit_batch(C.byref(h), n, P, 24, None, C.byref(c), 0, P, 1 << 30, P, None),
+                 "1..65535")
